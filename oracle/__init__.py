@@ -1,0 +1,278 @@
+"""Plain FP64 CPU oracle of the coupled gas-liquid-dendrite LB step.
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The library path
+(``paper_2407_01651_gb300``) never imports it and shares no code with it.
+
+The arithmetic lives in ``pf_oracle.c`` (one site at a time, dense moment
+matrices, two passes per step).  This module only compiles it with gcc and
+marshals arrays through ctypes.  Two builds of the same source exist:
+``liboracle_d.so`` (double) and ``liboracle_z.so`` (double complex, the
+complex-step derivative with respect to one parameter).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pf_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+
+# Order of the oracle's parameter vector (enum in pf_oracle.c).
+PARAM_NAMES = (
+    "rho_l", "rho_g", "nu", "sigma", "W_phi", "M_phi", "beta_phi", "beta_psi",
+    "beta_inter", "W0", "tau0", "eps_s", "k", "D", "Omega", "g", "grad_eps",
+    "s_e", "s_eps", "grad_eps_at",
+)
+# Field order of or_get_fields.
+FIELDS = ("phi", "psi", "C", "U", "p", "vx", "vy", "mu")
+N_STATE_PLANES = 39
+
+_lock = threading.Lock()
+_libs: dict[str, ctypes.CDLL] = {}
+
+
+def build(force: bool = False) -> None:
+    """Compile both oracle builds with gcc (no fast-math, no FMA contraction,
+    OpenMP over lattice rows)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    for tag, extra in (("d", []), ("z", ["-DPF_ORACLE_Z"])):
+        out = os.path.join(_BUILD, f"liboracle_{tag}.so")
+        if (not force and os.path.exists(out)
+                and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+            continue
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fopenmp",
+               "-ffp-contract=off", *extra, _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, out)
+
+
+def _lib(tag: str) -> ctypes.CDLL:
+    with _lock:
+        if tag in _libs:
+            return _libs[tag]
+        build()
+        lib = ctypes.CDLL(os.path.join(_BUILD, f"liboracle_{tag}.so"))
+        P = ctypes.c_void_p
+        D = ctypes.POINTER(ctypes.c_double)
+        lib.or_new.restype = P
+        lib.or_new.argtypes = [ctypes.c_int, ctypes.c_int]
+        lib.or_free.argtypes = [P]
+        lib.or_set_params.argtypes = [P, D]
+        lib.or_perturb_param.argtypes = [P, ctypes.c_int, ctypes.c_double]
+        lib.or_set_window.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        lib.or_set_rho_bar.argtypes = [P, ctypes.c_double]
+        lib.or_get_rho_bar.restype = ctypes.c_double
+        lib.or_get_rho_bar.argtypes = [P]
+        lib.or_init_from_fields.argtypes = [P, D, D, D, D, D, D]
+        lib.or_set_orientation.argtypes = [P, D, ctypes.c_int]
+        lib.or_fields_from_spec.argtypes = [P, D, ctypes.c_int, ctypes.c_double, D,
+                                            ctypes.c_int, D, D, D]
+        lib.or_init_spec.restype = ctypes.c_int
+        lib.or_init_spec.argtypes = [P, D, ctypes.c_int, ctypes.c_double, D, ctypes.c_int]
+        lib.or_step.argtypes = [P, ctypes.c_int]
+        lib.or_get_fields.argtypes = [P, ctypes.c_uint, D]
+        lib.or_get_fields_im.argtypes = [P, ctypes.c_uint, D]
+        lib.or_get_state.argtypes = [P, D]
+        lib.or_diag.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, D]
+        lib.or_objective.argtypes = [P, D, D]
+        lib.or_aniso.argtypes = [ctypes.c_double] * 5 + [D]
+        lib.or_feq_ns.argtypes = [ctypes.c_double] * 4 + [D]
+        lib.or_heq_cac.argtypes = [ctypes.c_double] * 3 + [D]
+        lib.or_seq_sol.argtypes = [ctypes.c_double] * 3 + [D]
+        lib.or_collide9.argtypes = [D] * 5
+        lib.or_collide5.argtypes = [D] * 6
+        lib.or_stencil.argtypes = [D, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int, D]
+        lib.or_derived.argtypes = [P, D]
+        lib.or_pointwise.argtypes = [P, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, D]
+        lib.or_get_steps.restype = ctypes.c_long
+        lib.or_get_steps.argtypes = [P]
+        _libs[tag] = lib
+        return lib
+
+
+def _dp(a: np.ndarray | None):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+class Oracle:
+    """One periodic lattice (or a window of one) advanced by the FP64 oracle.
+
+    Arrays are row-major ``[y][x]``.  ``params`` is a dict keyed by
+    ``PARAM_NAMES``.  ``complex_step=True`` selects the complex build.
+    """
+
+    def __init__(self, nx: int, ny: int, params: dict, complex_step: bool = False,
+                 window: tuple[int, int, int, int] | None = None):
+        self.lib = _lib("z" if complex_step else "d")
+        self.nx, self.ny = int(nx), int(ny)
+        self.h = self.lib.or_new(self.nx, self.ny)
+        if not self.h:
+            raise MemoryError("oracle allocation failed")
+        pv = _f64([float(params[k]) for k in PARAM_NAMES])
+        self.lib.or_set_params(self.h, _dp(pv))
+        self._pv = pv
+        if window is not None:
+            NX, NY, x0, y0 = window
+            self.lib.or_set_window(self.h, NX, NY, x0, y0)
+        self.NY = window[1] if window is not None else self.ny
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.lib.or_free(h)
+            self.h = None
+
+    # -- set-up --------------------------------------------------------------
+    def perturb(self, name: str, h: float) -> None:
+        self.lib.or_perturb_param(self.h, PARAM_NAMES.index(name), float(h))
+
+    def set_rho_bar(self, rho_bar: float) -> None:
+        self.lib.or_set_rho_bar(self.h, float(rho_bar))
+
+    @property
+    def rho_bar(self) -> float:
+        return self.lib.or_get_rho_bar(self.h)
+
+    def init_spec(self, seeds, R_s: float, bubbles) -> None:
+        s = _f64(seeds).reshape(-1, 3) if len(seeds) else np.zeros((0, 3))
+        b = _f64(bubbles).reshape(-1, 3) if len(bubbles) else np.zeros((0, 3))
+        s = np.ascontiguousarray(s)
+        b = np.ascontiguousarray(b)
+        rc = self.lib.or_init_spec(self.h, _dp(s), len(s), float(R_s), _dp(b), len(b))
+        if rc != 0:
+            raise MemoryError("oracle init failed")
+
+    def fields_from_spec(self, seeds, R_s, bubbles):
+        s = np.ascontiguousarray(_f64(seeds).reshape(-1, 3))
+        b = np.ascontiguousarray(_f64(bubbles).reshape(-1, 3))
+        n = self.nx * self.ny
+        phi, psi, C = (np.empty(n), np.empty(n), np.empty(n))
+        self.lib.or_fields_from_spec(self.h, _dp(s), len(s), float(R_s), _dp(b), len(b),
+                                     _dp(phi), _dp(psi), _dp(C))
+        shp = (self.ny, self.nx)
+        return phi.reshape(shp), psi.reshape(shp), C.reshape(shp)
+
+    def set_orientation(self, seeds) -> None:
+        s = np.ascontiguousarray(_f64(seeds).reshape(-1, 3))
+        self.lib.or_set_orientation(self.h, _dp(s), len(s))
+
+    def init_fields(self, phi, psi, C, vx=None, vy=None, p=None) -> None:
+        arrs = [_f64(a).ravel() if a is not None else None for a in (phi, psi, C, vx, vy, p)]
+        self._keep = arrs
+        self.lib.or_init_from_fields(self.h, *[_dp(a) for a in arrs])
+
+    # -- run -----------------------------------------------------------------
+    def step(self, n: int = 1) -> None:
+        self.lib.or_step(self.h, int(n))
+
+    # -- outputs -------------------------------------------------------------
+    def fields(self, names=FIELDS, imag: bool = False) -> dict[str, np.ndarray]:
+        mask = 0
+        for nm in names:
+            mask |= 1 << FIELDS.index(nm)
+        sel = [nm for nm in FIELDS if mask & (1 << FIELDS.index(nm))]
+        out = np.empty(len(sel) * self.nx * self.ny)
+        fn = self.lib.or_get_fields_im if imag else self.lib.or_get_fields
+        fn(self.h, mask, _dp(out))
+        out = out.reshape(len(sel), self.ny, self.nx)
+        return {nm: out[i] for i, nm in enumerate(sel)}
+
+    def state(self) -> np.ndarray:
+        out = np.empty(N_STATE_PLANES * self.nx * self.ny)
+        self.lib.or_get_state(self.h, _dp(out))
+        return out.reshape(N_STATE_PLANES, self.ny, self.nx)
+
+    def diag(self, probe=(0.0, 0.0, 0.0, 0.0)) -> dict[str, float]:
+        out = np.zeros(12)
+        xc, yc, R, W = probe
+        self.lib.or_diag(self.h, float(xc), float(yc), float(R), float(W), _dp(out))
+        keys = ("sum_phi", "sum_C", "sum_hpsi", "gas", "gas_x", "gas_y", "p_in_sum",
+                "p_in_n", "p_out_sum", "p_out_n", "max_v", "nonfinite")
+        return dict(zip(keys, out.tolist()))
+
+    def derived(self) -> dict[str, float]:
+        out = np.zeros(8)
+        self.lib.or_derived(self.h, _dp(out))
+        keys = ("lambda_p", "Mc_inf", "theta_sys", "kappa", "fs_coef", "s_nu", "s_q", "s_phi")
+        return dict(zip(keys, out.tolist()))
+
+    def pointwise(self, phi, psi, C) -> tuple[float, float]:
+        """(U, Q_psi) at one site."""
+        out = np.zeros(2)
+        self.lib.or_pointwise(self.h, float(phi), float(psi), float(C), _dp(out))
+        return float(out[0]), float(out[1])
+
+    @property
+    def steps(self) -> int:
+        return self.lib.or_get_steps(self.h)
+
+    def objective(self) -> tuple[float, float]:
+        re = ctypes.c_double()
+        im = ctypes.c_double()
+        self.lib.or_objective(self.h, ctypes.byref(re), ctypes.byref(im))
+        return re.value, im.value
+
+
+# -- pointwise pieces (double build), used by the pin tests ------------------
+def aniso(gx, gy, theta, eps, geps=1e-6):
+    """(a_s, Nx, Ny, |grad psi|_reg) at gradient (gx, gy) for a grain at theta."""
+    out = np.zeros(4)
+    _lib("d").or_aniso(float(gx), float(gy), float(theta), float(eps), float(geps), _dp(out))
+    return out
+
+
+def feq_ns(p, rho, vx, vy):
+    out = np.zeros(9)
+    _lib("d").or_feq_ns(float(p), float(rho), float(vx), float(vy), _dp(out))
+    return out
+
+
+def heq_cac(phi, vx, vy):
+    out = np.zeros(9)
+    _lib("d").or_heq_cac(float(phi), float(vx), float(vy), _dp(out))
+    return out
+
+
+def seq_sol(C, jx, jy):
+    out = np.zeros(5)
+    _lib("d").or_seq_sol(float(C), float(jx), float(jy), _dp(out))
+    return out
+
+
+def collide9(f, feq, S, G):
+    args = [_f64(a) for a in (f, feq, S, G)]
+    out = np.zeros(9)
+    _lib("d").or_collide9(*[_dp(a) for a in args], _dp(out))
+    return out
+
+
+def collide5(f, feq, S, G, Fd):
+    args = [_f64(a) for a in (f, feq, S, G, Fd)]
+    out = np.zeros(5)
+    _lib("d").or_collide5(*[_dp(a) for a in args], _dp(out))
+    return out
+
+
+def stencil(X, x, y):
+    """(d_x X, d_y X, lap X) of a periodic [ny][nx] array at site (x, y)."""
+    X = _f64(X)
+    ny, nx = X.shape
+    out = np.zeros(3)
+    _lib("d").or_stencil(_dp(X), nx, ny, int(x), int(y), _dp(out))
+    return out
