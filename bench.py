@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Throughput of the coupled gas-liquid-dendrite LB step on GB300.
+
+Workload: the 4096 x 4096 periodic lattice with 64 dendrite seeds (R = 6,
+orientation uniform in [0, pi/2)) and 128 non-overlapping bubbles (R uniform
+in [8, 40]), FP32, the paper's Section-4 problem restated periodically
+(``workload.cfg2_layout``).  A step is one coupled LB step of every site.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded window of the same workload instead.
+
+Multi-GPU: the path is run as independent replicas (one lattice per rank, no
+data-path collective); value = all sites updated by all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled-step MLUPS at 4096² and % of HBM roofline; adjoint/forward time ratio"
+# Algorithmic HBM bytes per lattice update of the step kernel: 39 planes read
+# + 39 planes written (9 NS, 9 CAC, 5+5+1 dendrite, 5 solute, 5 lagged scalars)
+# and 1 byte of grain id read.
+BYTES_PER_LU = {"fp32": 39 * 4 * 2 + 1, "fp64": 39 * 8 * 2 + 1}
+DTYPE = {"fp32": "f32", "fp64": "f64"}
+KERNEL_SOURCES = ("paper_2407_01651_gb300/csrc/pf_kernels.cu",
+                  "paper_2407_01651_gb300/csrc/pf_model.cuh")
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> tuple[float, str]:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def recorded_traffic(precision: str, size: int):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"step_{precision}_{size}_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        if rec.get("kernel_hash") == kernel_hash():
+            return rec["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        idx = str(gpu_index)
+        if vis:
+            parts = [p.strip() for p in vis.split(",") if p.strip()]
+            if gpu_index < len(parts):
+                idx = parts[gpu_index]
+        self.idx = idx
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.idx], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as fh:
+            for line in fh:
+                cols = [c.strip() for c in line.split(",")]
+                if len(cols) < 9:
+                    continue
+                try:
+                    sm.append(float(cols[1]))
+                    mx.append(float(cols[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, cols[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(steps_hint: int, target_s: float, side: int | None = None) -> dict:
+    """Time the FP64 oracle (test infrastructure, run as a child process) on a
+    window of the 4096^2 workload; all host cores."""
+    cores = os.cpu_count() or 1
+    code = f"""
+import json, sys, time
+sys.path.insert(0, {ROOT!r})
+import oracle
+from paper_2407_01651_gb300 import workload as wl
+lay = wl.cfg2_layout()
+def make(s):
+    o = oracle.Oracle(s, s, lay.params, window=(lay.nx, lay.ny, 1024, 1024))
+    o.init_spec(lay.seeds, lay.R_s, lay.bubbles)
+    return o
+side = {side if side else 0}
+if not side:
+    o = make(256); t = time.perf_counter(); o.step(2); dt = (time.perf_counter() - t) / 2
+    rate = 256 * 256 / dt
+    side = int(min(1024, max(128, (rate * {target_s} / max({steps_hint}, 1)) ** 0.5)) // 32 * 32)
+o = make(side)
+o.step(1)
+t = time.perf_counter(); o.step({steps_hint}); dt = time.perf_counter() - t
+print(json.dumps(dict(side=side, steps={steps_hint}, seconds=dt)))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS=str(cores))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         check=True)
+    rec = json.loads(out.stdout.strip().splitlines()[-1])
+    mlups = rec["side"] ** 2 * rec["steps"] / rec["seconds"] / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle, {rec['side']}x{rec['side']} window of the 4096^2 layout "
+                      f"(global coordinates), {rec['steps']} steps in {rec['seconds']:.1f} s, "
+                      f"OpenMP over rows"}
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    total = args.steps + args.warmup
+    base = cpu_oracle_sample(steps_hint=max(total, 1), target_s=120.0)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": base["value"], "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "4096x4096 periodic lattice, 64 seeds, 128 bubbles (window sample)",
+                   "precision": "fp64-cpu"},
+        "cpu_baseline": base,
+        "e2e": {"value": base["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--precision", default="fp32", choices=("fp32", "fp64"))
+    ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2407_01651_gb300 import pf
+    from paper_2407_01651_gb300 import workload as wl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    lay = wl.cfg2_layout(args.size, args.size)
+    stream = torch.cuda.current_stream()
+    sim = pf.Simulation([(lay.nx, lay.ny)], lay.params, args.precision,
+                        stream=stream.cuda_stream)
+    sim.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
+    sites = lay.nx * lay.ny
+    sim.step(args.warmup)
+    sim.sync()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = sim.launches
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sim.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = sim.launches - launches0
+    clk = clocks.stop()
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    d = sim.reduce(0)
+    if d["nonfinite"]:
+        raise SystemExit(f"non-finite fields after the timed run: {d['nonfinite']}")
+
+    ms_per_step = ms_max / args.steps
+    value = world * sites * args.steps / (ms_max / 1e3) / 1e6
+    peak, peak_kind = measured_peaks()
+    bpl = BYTES_PER_LU[args.precision]
+    achieved = bpl * sites / (ms / args.steps / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": recorded_traffic(args.precision, args.size),
+            "peak_kind": peak_kind, "bytes_per_lu": bpl,
+            "kernel": "k_step (one launch per step; average over the timed region)"}
+
+    # end to end through the public API: fields in from pinned host memory,
+    # steps, fields out to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        names = ("phi", "psi", "C", "vx", "vy", "p")
+        init = sim.fields(0, names)
+        host_in = torch.empty((6, lay.ny, lay.nx), dtype=torch.float64, pin_memory=True)
+        for i, nm in enumerate(names):
+            host_in[i].copy_(torch.from_numpy(init[nm]))
+        host_out = torch.empty(6 * sites, dtype=torch.float64, pin_memory=True)
+        out_np = host_out.numpy()
+        in_np = host_in.numpy()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.set_fields(0, *in_np)
+        sim.step(args.steps)
+        sim.fields(0, ("phi", "psi", "C", "p", "vx", "vy"), out=out_np)
+        t1 = time.perf_counter()
+        e_s = t1 - t0
+        if dist is not None:
+            t = torch.tensor([e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_s = float(t.item())
+        e2e = {"value": world * sites * args.steps / e_s / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 6 * 8 * sites / args.steps,
+               "d2h_bytes_per_step": 6 * 8 * sites / args.steps,
+               "what": "pf_set_fields from pinned FP64 host fields, pf_step(K), "
+                       "pf_get_fields to pinned FP64 host memory; host wall clock"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(steps_hint=20, target_s=20.0)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[args.precision], "data": "synthetic",
+            "config": {"workload": f"{lay.nx}x{lay.ny} periodic lattice, 64 seeds (R=6, "
+                                   "theta~U[0,pi/2)), 128 bubbles (R~U[8,40]), seed 2",
+                       "lattice": [lay.nx, lay.ny], "precision": args.precision,
+                       "parallelism": f"replicas x{world}",
+                       "l2": f"inputs {2 * 39 * sites * (4 if args.precision == 'fp32' else 8) / 1e9:.1f} GB "
+                             "> L2 (no flush)"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * pf.h -- C ABI of the GB300 (sm_103a) library for one coupled lattice
+ * Boltzmann step of the gas-liquid-dendrite phase-field model of Zhan, Chai,
+ * Sun, Shi, Geng and Jiang, "Phase-field modeling of dendritic growth with gas
+ * bubbles in the solidification of binary alloys" (arXiv 2407.01651).
+ *
+ * Conventions (all entry points):
+ *  - Every call returns a pf_status; 0 is success, negative values are errors.
+ *    Nothing aborts or exits.  pf_last_error() gives a one-line reason.
+ *  - Argument errors are reported synchronously.  Errors raised by device work
+ *    are reported by the next call that synchronises the stream
+ *    (pf_get_fields, pf_get_state, pf_reduce, pf_sync, pf_destroy).
+ *  - The handle owns every device buffer it allocates.  When an allocator is
+ *    given to pf_create, all device memory comes from it and goes back to it.
+ *  - All device work is enqueued on the CUDA stream given to pf_create.  Host
+ *    buffers belong to the caller.  A handle is not thread-safe.
+ *  - Lattices are periodic, row-major [y][x] with x fastest, in lattice units
+ *    (dx = dt = 1).  Host arrays are FP64 regardless of the storage precision.
+ */
+#ifndef PF_H_
+#define PF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PF_OK = 0,
+  PF_ERR_BAD_ARG = -1,   /* an argument is out of range or inconsistent        */
+  PF_ERR_OOM = -2,       /* device or host allocation failed                   */
+  PF_ERR_CUDA = -3,      /* a CUDA call failed (reason in pf_last_error)       */
+  PF_ERR_TIMEOUT = -4,   /* a bounded device-side wait gave up                 */
+  PF_ERR_NAN = -5,       /* a non-finite value was detected in the fields      */
+  PF_ERR_STATE = -6      /* call out of order (e.g. step before init)          */
+} pf_status;
+
+/* Storage precision of the populations.  Arithmetic is FP64 for PF_FP64 and
+ * FP32 otherwise; the 16-bit forms store populations as offsets from the rest
+ * equilibrium. */
+typedef enum {
+  PF_FP64 = 0,
+  PF_FP32 = 1,
+  PF_FP16_OFFSET = 2,
+  PF_BF16_OFFSET = 3
+} pf_precision;
+
+/* Model parameters in the paper's symbols, lattice units.
+ *  rho_l, rho_g   liquid / gas density, material interpolation of Section 2.2
+ *  nu             kinematic viscosity, mu = rho nu
+ *  sigma          gas-liquid surface tension (surface tension force, Sec. 2.2)
+ *  W_phi, M_phi   CAC interface width and mobility (Eq. eq-ACE)
+ *  beta_phi, beta_psi, beta_inter   double-well / interaction heights
+ *                 (Eq. eq-douWell, eq-f3Inter); the paper uses 1/4, 1/4, 3/4
+ *  W0, tau0       dendrite interface width and relaxation time (Eq. eq-AnACE)
+ *  eps_s          fourfold anisotropy strength (anisotropy function, Sec. 3.3)
+ *  k              partition coefficient
+ *  D              solute diffusivity in the liquid
+ *  Omega          solutal undercooling; theta_sys and M c_inf follow from it
+ *                 (Eq. eq-Tsys) and F(U) = 1
+ *  g              gravity magnitude, acting along -y
+ *  grad_eps       regularisation of |grad X| in interface normals
+ *  grad_eps_at    regularisation of |grad psi| in the antitrapping direction
+ *  s_e, s_eps     free MRT rates of the NS energy moments (default 1)
+ * lambda' = 15 lambda / 16 is derived as D tau0 / (a2' W0^2), a2' = 47/75
+ * (thin-interface limit, Appendix A). */
+typedef struct pf_params {
+  double rho_l, rho_g, nu, sigma, W_phi, M_phi;
+  double beta_phi, beta_psi, beta_inter;
+  double W0, tau0, eps_s, k, D, Omega, g;
+  double grad_eps, grad_eps_at, s_e, s_eps;
+} pf_params;
+
+/* One periodic domain of an ensemble.  eps_s < 0 uses pf_params.eps_s. */
+typedef struct pf_domain {
+  int nx, ny;
+  double eps_s;
+} pf_domain;
+
+/* Optional device allocator (e.g. a framework's caching allocator). */
+typedef struct pf_allocator {
+  void *ctx;
+  void *(*alloc)(void *ctx, size_t bytes, void *stream);
+  void (*free)(void *ctx, void *ptr, void *stream);
+} pf_allocator;
+
+/* Initial seeds and bubbles of one domain.  seeds: n_seeds x (x, y, theta),
+ * theta the grain orientation; bubbles: n_bubbles x (x, y, R). */
+typedef struct pf_init_spec {
+  int n_seeds;
+  const double *seeds;
+  double R_s;
+  int n_bubbles;
+  const double *bubbles;
+} pf_init_spec;
+
+/* FP64 diagnostics of one domain (pf_reduce). */
+typedef struct pf_diag {
+  double sum_phi;      /* sum phi: conserved by Eq. eq-ACE                    */
+  double sum_C;        /* sum C: conserved by the solute equation             */
+  double sum_hpsi;     /* sum h(psi) = sum (1+psi)/2; solid fraction x N       */
+  double gas;          /* sum (1 - phi)                                       */
+  double gas_x, gas_y; /* sum x (1 - phi), sum y (1 - phi): bubble centroid   */
+  double p_in_sum, p_in_n, p_out_sum, p_out_n;  /* Laplace probe (Eq. eq-laplace) */
+  double max_v;        /* max |v|                                             */
+  double nonfinite;    /* number of sites with a non-finite field             */
+} pf_diag;
+
+/* Laplace probe: circle centre (xc, yc), radius R, interface width W;
+ * inside r < R - 2W, outside r > R + 4W. */
+typedef struct pf_probe {
+  double xc, yc, R, W;
+} pf_probe;
+
+/* Field selection bits for pf_get_fields (order of the output planes). */
+enum {
+  PF_FIELD_PHI = 1u << 0,  /* bubble order parameter phi                   */
+  PF_FIELD_PSI = 1u << 1,  /* dendrite order parameter psi                 */
+  PF_FIELD_C = 1u << 2,    /* dimensionless concentration C = c / c_inf     */
+  PF_FIELD_U = 1u << 3,    /* supersaturation U                             */
+  PF_FIELD_P = 1u << 4,    /* pressure p                                    */
+  PF_FIELD_VX = 1u << 5,
+  PF_FIELD_VY = 1u << 6,
+  PF_FIELD_MU = 1u << 7    /* chemical potential mu_phi (0 before a step)   */
+};
+
+/* Number of FP64 planes of the raw state (pf_get_state / pf_set_state):
+ * f[9] (NS, post-collision), h[9] (CAC, post-collision), g_pre[5], g_post[5],
+ * r = 1/a_s^2, s[5] (solute, post-collision), phi, C, vx, vy, Q_psi of the
+ * last step. */
+#define PF_STATE_PLANES 39
+
+typedef struct pf_handle pf_handle;
+
+/* Default parameters: the 128^2 / 4096^2 benchmark set (rho_l/rho_g = 10,
+ * nu = 0.1, sigma = 1e-3, W = 4, eps_s = 0.05, Omega = 0.55, k = 0.15,
+ * D = 0.1, g = 1e-6, tau0 = 320 from D tau0 / W0^2 = 2).  Never fails for a
+ * non-null pointer. */
+pf_status pf_params_default(pf_params *out);
+
+/* Derived coefficients, for inspection: out[0] lambda' (Appendix A),
+ * out[1] M c_inf, out[2] theta_sys (Eq. eq-Tsys). */
+pf_status pf_params_derived(const pf_params *p, double out[3]);
+
+/* Create a handle for n_doms periodic domains (n_doms >= 1, each nx, ny >= 4).
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).  alloc may be
+ * NULL (cudaMalloc).  Allocates two copies of the 39-plane state, the field
+ * planes and reduction scratch.  Errors: BAD_ARG, OOM, CUDA. */
+pf_status pf_create(const pf_params *p, const pf_domain *doms, int n_doms,
+                    pf_precision prec, void *cuda_stream, const pf_allocator *alloc,
+                    pf_handle **out);
+
+/* Initialise domain dom from seeds and bubbles (Eqs. eq-phiEq, eq-psiEq;
+ * populations at equilibrium, v = 0, p = 0).  Grain orientation of each site
+ * is that of the nearest seed.  Copies the spec to the device (synchronous
+ * with respect to the host arrays).  Errors: BAD_ARG, OOM, CUDA. */
+pf_status pf_init_fields(pf_handle *h, int dom, const pf_init_spec *spec);
+
+/* Initialise domain dom from macroscopic fields (host, FP64, n = nx*ny each):
+ * fields6 = [phi, psi, C, vx, vy, p] planes; theta (per-site grain angle) may
+ * be NULL for 0.  Populations are set to their equilibria. */
+pf_status pf_set_fields(pf_handle *h, int dom, const double *fields6, const double *theta,
+                        size_t n);
+
+/* Advance every domain by n_steps coupled steps (Section 3 unified LBE and
+ * Appendix B).  n_steps >= 0.  Enqueued on the stream; returns without
+ * waiting.  Errors: STATE (no init), CUDA. */
+pf_status pf_step(pf_handle *h, int n_steps);
+
+/* Copy the fields of the last step of domain dom to host_out (FP64,
+ * popcount(mask) planes of nx*ny, in bit order).  n is the capacity of
+ * host_out in doubles.  Synchronises the stream. */
+pf_status pf_get_fields(pf_handle *h, int dom, uint32_t mask, double *host_out, size_t n);
+
+/* Raw state of domain dom (PF_STATE_PLANES planes, FP64) to / from the host:
+ * checkpoint and restart.  Synchronise the stream. */
+pf_status pf_get_state(pf_handle *h, int dom, double *host_out, size_t n);
+pf_status pf_set_state(pf_handle *h, int dom, const double *host_in, size_t n);
+
+/* FP64 reductions of domain dom's last-step fields (conservation of gas and
+ * solute, solid fraction, bubble centroid, Laplace pressure jump).  probe may
+ * be NULL.  Synchronises the stream.  Errors: BAD_ARG, CUDA. */
+pf_status pf_reduce(pf_handle *h, int dom, const pf_probe *probe, pf_diag *out);
+
+/* Wait for all enqueued work; reports deferred device errors. */
+pf_status pf_sync(pf_handle *h);
+
+/* Number of steps taken since the last initialisation. */
+long long pf_steps_taken(const pf_handle *h);
+
+/* Kernel launches issued by this handle since creation (the library's own
+ * kernels only). */
+long long pf_launch_count(const pf_handle *h);
+
+/* Release every resource of the handle (NULL is ignored). */
+pf_status pf_destroy(pf_handle *h);
+
+/* Last error message of the handle, or of the last failed pf_create when h is
+ * NULL.  Never NULL. */
+const char *pf_last_error(const pf_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PF_H_ */

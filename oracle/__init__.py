@@ -94,6 +94,8 @@ def _lib(tag: str) -> ctypes.CDLL:
         lib.or_derived.argtypes = [P, D]
         lib.or_pointwise.argtypes = [P, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, D]
+        lib.or_mean_phi_global.restype = ctypes.c_double
+        lib.or_mean_phi_global.argtypes = [P, D, ctypes.c_int]
         lib.or_get_steps.restype = ctypes.c_long
         lib.or_get_steps.argtypes = [P]
         _libs[tag] = lib
@@ -167,6 +169,10 @@ class Oracle:
                                      _dp(phi), _dp(psi), _dp(C))
         shp = (self.ny, self.nx)
         return phi.reshape(shp), psi.reshape(shp), C.reshape(shp)
+
+    def mean_phi_global(self, bubbles) -> float:
+        b = np.ascontiguousarray(_f64(bubbles).reshape(-1, 3))
+        return self.lib.or_mean_phi_global(self.h, _dp(b), len(b))
 
     def set_orientation(self, seeds) -> None:
         s = np.ascontiguousarray(_f64(seeds).reshape(-1, 3))

@@ -474,6 +474,31 @@ void or_fields_from_spec(const ostate *st, const double *seeds, int n_seeds,
     }
 }
 
+/* Mean of the initial phi over the whole periodic NX x NY lattice (the
+ * buoyancy reference rho_bar of reading R13 for a windowed oracle). */
+double or_mean_phi_global(const ostate *st, const double *bubbles, int n_bub) {
+  double bphi = RE_(st->par[P_BETA_PHI]), Wphi = RE_(st->par[P_W_PHI]);
+  double total = 0.0;
+#pragma omp parallel for reduction(+ : total) schedule(static)
+  for (int y = 0; y < st->NY; ++y) {
+    double row = 0.0;
+    for (int x = 0; x < st->NX; ++x) {
+      double ph = 1.0;
+      for (int b = 0; b < n_bub; ++b) {
+        double dx = min_image(x - bubbles[3 * b], st->NX);
+        double dy = min_image(y - bubbles[3 * b + 1], st->NY);
+        double v = 0.5 + 0.5 * tanh(sqrt(2.0 * bphi) *
+                                    (sqrt(dx * dx + dy * dy) - bubbles[3 * b + 2]) /
+                                    (2.0 * Wphi));
+        if (b == 0 || v < ph) ph = v;
+      }
+      row += ph;
+    }
+    total += row;
+  }
+  return total / ((double)st->NX * st->NY);
+}
+
 /* Convenience: orientation + fields + equilibrium populations. */
 int or_init_spec(ostate *st, const double *seeds, int n_seeds, double R_s,
                  const double *bubbles, int n_bub) {

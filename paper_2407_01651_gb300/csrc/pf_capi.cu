@@ -1,0 +1,614 @@
+// pf_capi.cu -- implementation of the C ABI declared in include/pf.h.
+//
+// A handle owns, for all of its domains together:
+//   - two copies of the 39-plane state (ping-pong of the pull scheme),
+//   - 8 field planes in compute precision (written by the last step of each
+//     pf_step call and by the initialisation),
+//   - a uint8 grain id per site and a (cos, sin) table per domain,
+//   - the domain and tile tables of the step kernel,
+//   - FP64 reduction scratch and a staging buffer for FP64 host transfers.
+// Domains are concatenated in every plane; each starts on a 64-site boundary.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pf.h"
+#include "pf_internal.h"
+
+using namespace pf;
+
+struct pf_handle {
+  pf_params p{};
+  pf_precision prec = PF_FP32;
+  cudaStream_t stream = nullptr;
+  pf_allocator alloc{};
+  bool has_alloc = false;
+  int device = 0;
+  std::vector<pf_domain> doms;
+  std::vector<DomDesc> ddesc;
+  std::vector<int> inited;
+  long long plane_stride = 0;
+  size_t elem = 4;          // bytes per stored value
+  size_t celem = 4;         // bytes per compute value
+  int tx = 32, ty = 8;      // step tile
+  int ntiles = 0;
+  int grid = 0;
+  void* state[2] = {nullptr, nullptr};
+  int cur = 0;
+  void* fields = nullptr;
+  uint8_t* grain = nullptr;
+  double2* grain_cs = nullptr;
+  DomDesc* d_doms = nullptr;
+  int* d_tile_dom = nullptr;
+  double* partial = nullptr;
+  double* d_diag = nullptr;
+  double* staging = nullptr;    // FP64 device staging (largest domain x 39 planes)
+  size_t staging_elems = 0;
+  long long steps = 0;
+  long long launches = 0;
+  std::string err;
+};
+
+static std::string g_create_err;
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+static pf_status fail(pf_handle* h, pf_status code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_err = msg;
+  return code;
+}
+
+static pf_status cuda_fail(pf_handle* h, cudaError_t e, const char* where) {
+  return fail(h, PF_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define PF_CUDA(h, ...)                                           \
+  do {                                                            \
+    cudaError_t e_ = (__VA_ARGS__);                               \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #__VA_ARGS__); \
+  } while (0)
+
+static void* dev_alloc(pf_handle* h, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  void* p = nullptr;
+  if (h->has_alloc) {
+    p = h->alloc.alloc(h->alloc.ctx, bytes, (void*)h->stream);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  return p;
+}
+
+static void dev_free(pf_handle* h, void* p) {
+  if (!p) return;
+  if (h->has_alloc) h->alloc.free(h->alloc.ctx, p, (void*)h->stream);
+  else cudaFree(p);
+}
+
+static bool finite_pos(double v) { return std::isfinite(v) && v > 0; }
+
+template <typename R>
+static KParams<R> make_kparams(const pf_params& p) {
+  KParams<R> k{};
+  const double kappa = std::sqrt(2.0 * p.beta_phi) / p.W_phi;
+  const double s_nu = 1.0 / (3.0 * p.nu + 0.5);
+  k.rho_g = (R)p.rho_g;
+  k.drho = (R)(p.rho_l - p.rho_g);
+  k.ge2 = (R)(p.grad_eps * p.grad_eps);
+  k.gat2 = (R)(p.grad_eps_at * p.grad_eps_at);
+  k.kappa = (R)kappa;
+  k.fs_coef = (R)(6.0 * p.sigma / (p.W_phi * std::sqrt(2.0 * p.beta_phi)));
+  k.Wphi2 = (R)(p.W_phi * p.W_phi);
+  k.M_phi = (R)p.M_phi;
+  k.two_bphi = (R)(2.0 * p.beta_phi);
+  k.two_bint = (R)(2.0 * p.beta_inter);
+  k.four_bpsi = (R)(4.0 * p.beta_psi);
+  double der[3];
+  pf_params_derived(&p, der);
+  k.lam = (R)der[0];
+  k.Mcinf = (R)der[1];
+  k.theta = (R)der[2];
+  k.inv_tau0 = (R)(1.0 / p.tau0);
+  k.c_s1 = (R)(3.0 * p.W0 * p.W0 / p.tau0);
+  k.W0 = (R)p.W0;
+  k.a_at = (R)(1.0 / (2.0 * std::sqrt(2.0)));
+  k.k = (R)p.k;
+  k.D = (R)p.D;
+  k.g = (R)p.g;
+  k.s_e = (R)p.s_e;
+  k.s_eps = (R)p.s_eps;
+  k.s_q = (R)(8.0 * (2.0 - s_nu) / (8.0 - s_nu));
+  k.s_nu = (R)s_nu;
+  k.s_phi = (R)(1.0 / (3.0 * p.M_phi + 0.5));
+  return k;
+}
+
+static pf_status check_params(const pf_params* p) {
+  if (!p) return fail(nullptr, PF_ERR_BAD_ARG, "params is NULL");
+  if (!finite_pos(p->rho_l) || !finite_pos(p->rho_g) || !finite_pos(p->nu) ||
+      !finite_pos(p->W_phi) || !finite_pos(p->M_phi) || !finite_pos(p->W0) ||
+      !finite_pos(p->tau0) || !finite_pos(p->D) || !finite_pos(p->beta_phi) ||
+      !finite_pos(p->beta_psi) || !std::isfinite(p->beta_inter) || !std::isfinite(p->sigma) ||
+      !std::isfinite(p->g) || !std::isfinite(p->Omega) || !std::isfinite(p->eps_s) ||
+      !finite_pos(p->grad_eps) || !finite_pos(p->grad_eps_at) || !finite_pos(p->s_e) ||
+      !finite_pos(p->s_eps) || p->s_e >= 2.0 || p->s_eps >= 2.0)
+    return fail(nullptr, PF_ERR_BAD_ARG, "a parameter is non-finite or out of range");
+  if (!(p->k > 0.0 && p->k < 1.0)) return fail(nullptr, PF_ERR_BAD_ARG, "k must be in (0, 1)");
+  if (!(p->eps_s >= 0.0 && p->eps_s < 1.0 / 15.0))
+    return fail(nullptr, PF_ERR_BAD_ARG, "eps_s must be in [0, 1/15)");
+  if (1.0 - (1.0 - p->k) * p->Omega == 0.0)
+    return fail(nullptr, PF_ERR_BAD_ARG, "1 - (1-k) Omega must be non-zero");
+  return PF_OK;
+}
+
+template <typename R>
+static R* fields_ptr(pf_handle* h) { return reinterpret_cast<R*>(h->fields); }
+
+// FP64 device staging for host transfers, grown on demand (never on the
+// stepping path).
+static pf_status ensure_staging(pf_handle* h, size_t elems) {
+  if (elems <= h->staging_elems) return PF_OK;
+  cudaStreamSynchronize(h->stream);
+  dev_free(h, h->staging);
+  h->staging = (double*)dev_alloc(h, elems * sizeof(double));
+  h->staging_elems = h->staging ? elems : 0;
+  if (!h->staging) return fail(h, PF_ERR_OOM, "staging allocation failed");
+  return PF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// parameters
+// ---------------------------------------------------------------------------
+extern "C" pf_status pf_params_default(pf_params* out) {
+  if (!out) return PF_ERR_BAD_ARG;
+  pf_params p{};
+  p.rho_l = 1.0; p.rho_g = 0.1; p.nu = 0.1; p.sigma = 1e-3; p.W_phi = 4.0; p.M_phi = 0.1;
+  p.beta_phi = 0.25; p.beta_psi = 0.25; p.beta_inter = 0.75;
+  p.W0 = 4.0; p.tau0 = 320.0; p.eps_s = 0.05; p.k = 0.15; p.D = 0.1; p.Omega = 0.55;
+  p.g = 1e-6; p.grad_eps = 1e-6; p.grad_eps_at = 1e-2; p.s_e = 1.0; p.s_eps = 1.0;
+  *out = p;
+  return PF_OK;
+}
+
+extern "C" pf_status pf_params_derived(const pf_params* p, double out[3]) {
+  if (!p || !out) return PF_ERR_BAD_ARG;
+  // thin-interface limit: tau0 D / W0^2 = a2' lambda', a2' = 47/75
+  out[0] = p->D * p->tau0 / ((47.0 / 75.0) * p->W0 * p->W0);
+  // isothermal closure of the solutal case (B)
+  out[1] = 1.0 - (1.0 - p->k) * p->Omega;
+  out[2] = -out[1] * p->Omega / (1.0 - (1.0 - p->k) * p->Omega);
+  return PF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// create / destroy
+// ---------------------------------------------------------------------------
+static void release(pf_handle* h) {
+  if (!h) return;
+  for (void*& s : h->state) { dev_free(h, s); s = nullptr; }
+  dev_free(h, h->fields);
+  dev_free(h, h->grain);
+  dev_free(h, h->grain_cs);
+  dev_free(h, h->d_doms);
+  dev_free(h, h->d_tile_dom);
+  dev_free(h, h->partial);
+  dev_free(h, h->d_diag);
+  dev_free(h, h->staging);
+  h->fields = h->grain = nullptr;
+}
+
+static pf_status upload_tables(pf_handle* h) {
+  // tiles of every domain, in domain order
+  std::vector<int> tile_dom;
+  for (size_t d = 0; d < h->ddesc.size(); ++d) {
+    DomDesc& dd = h->ddesc[d];
+    dd.tiles_x = (dd.nx + h->tx - 1) / h->tx;
+    const int tiles_y = (dd.ny + h->ty - 1) / h->ty;
+    dd.tile0 = (int)tile_dom.size();
+    for (int t = 0; t < dd.tiles_x * tiles_y; ++t) tile_dom.push_back((int)d);
+  }
+  h->ntiles = (int)tile_dom.size();
+  dev_free(h, h->d_tile_dom);
+  h->d_tile_dom = (int*)dev_alloc(h, tile_dom.size() * sizeof(int));
+  if (!h->d_tile_dom) return fail(h, PF_ERR_OOM, "tile table allocation failed");
+  PF_CUDA(h, cudaMemcpyAsync(h->d_tile_dom, tile_dom.data(), tile_dom.size() * sizeof(int),
+                             cudaMemcpyHostToDevice, h->stream));
+  PF_CUDA(h, cudaMemcpyAsync(h->d_doms, h->ddesc.data(), h->ddesc.size() * sizeof(DomDesc),
+                             cudaMemcpyHostToDevice, h->stream));
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  h->grid = h->ntiles;  // one CTA per tile; the kernel also accepts fewer (grid-stride)
+  (void)sms;
+  return PF_OK;
+}
+
+extern "C" pf_status pf_create(const pf_params* p, const pf_domain* doms, int n_doms,
+                               pf_precision prec, void* cuda_stream, const pf_allocator* alloc,
+                               pf_handle** out) {
+  if (!out) return fail(nullptr, PF_ERR_BAD_ARG, "out is NULL");
+  *out = nullptr;
+  pf_status st = check_params(p);
+  if (st != PF_OK) return st;
+  if (!doms || n_doms < 1) return fail(nullptr, PF_ERR_BAD_ARG, "need at least one domain");
+  if (prec != PF_FP64 && prec != PF_FP32)
+    return fail(nullptr, PF_ERR_BAD_ARG, "precision not supported by this build");
+  for (int d = 0; d < n_doms; ++d) {
+    if (doms[d].nx < 4 || doms[d].ny < 4 || doms[d].nx > (1 << 16) || doms[d].ny > (1 << 16))
+      return fail(nullptr, PF_ERR_BAD_ARG, "domain sizes must be in [4, 65536]");
+    if (doms[d].eps_s >= 1.0 / 15.0 || !std::isfinite(doms[d].eps_s))
+      return fail(nullptr, PF_ERR_BAD_ARG, "domain eps_s must be < 1/15");
+  }
+  if (alloc && (!alloc->alloc || !alloc->free))
+    return fail(nullptr, PF_ERR_BAD_ARG, "allocator needs alloc and free");
+
+  pf_handle* h = new (std::nothrow) pf_handle();
+  if (!h) return fail(nullptr, PF_ERR_OOM, "host allocation failed");
+  h->p = *p;
+  h->prec = prec;
+  h->stream = (cudaStream_t)cuda_stream;
+  if (alloc) { h->alloc = *alloc; h->has_alloc = true; }
+  cudaGetDevice(&h->device);
+  h->elem = prec == PF_FP64 ? 8 : 4;
+  h->celem = prec == PF_FP64 ? 8 : 4;
+  h->doms.assign(doms, doms + n_doms);
+  h->inited.assign(n_doms, 0);
+  long long off = 0;
+  size_t max_n = 0;
+  for (int d = 0; d < n_doms; ++d) {
+    DomDesc dd{};
+    dd.off = off;
+    dd.nx = doms[d].nx;
+    dd.ny = doms[d].ny;
+    dd.grain_off = d * MAX_GRAINS;
+    dd.eps_s = doms[d].eps_s >= 0.0 ? doms[d].eps_s : p->eps_s;
+    dd.rho_bar = p->rho_l;
+    h->ddesc.push_back(dd);
+    const long long n = (long long)dd.nx * dd.ny;
+    max_n = std::max(max_n, (size_t)n);
+    off += (n + 63) / 64 * 64;
+  }
+  h->plane_stride = off;
+  const size_t ps = (size_t)off;
+
+  auto bail = [&](pf_status code, const char* msg) {
+    g_create_err = msg;
+    release(h);
+    delete h;
+    return code;
+  };
+  for (int c = 0; c < 2; ++c) {
+    h->state[c] = dev_alloc(h, ps * N_PLANES * h->elem);
+    if (!h->state[c]) return bail(PF_ERR_OOM, "state allocation failed");
+  }
+  h->fields = dev_alloc(h, ps * N_FIELDS * h->celem);
+  h->grain = (uint8_t*)dev_alloc(h, ps);
+  h->grain_cs = (double2*)dev_alloc(h, (size_t)n_doms * MAX_GRAINS * sizeof(double2));
+  h->d_doms = (DomDesc*)dev_alloc(h, (size_t)n_doms * sizeof(DomDesc));
+  h->partial = (double*)dev_alloc(h, (size_t)REDUCE_BLOCKS * NDIAG * sizeof(double));
+  h->d_diag = (double*)dev_alloc(h, NDIAG * sizeof(double));
+  (void)max_n;
+  if (!h->fields || !h->grain || !h->grain_cs || !h->d_doms || !h->partial || !h->d_diag)
+    return bail(PF_ERR_OOM, "device allocation failed");
+  if (cudaMemsetAsync(h->fields, 0, ps * N_FIELDS * h->celem, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->grain, 0, ps, h->stream) != cudaSuccess)
+    return bail(PF_ERR_CUDA, "memset failed");
+  std::vector<double2> cs((size_t)n_doms * MAX_GRAINS, make_double2(1.0, 0.0));
+  if (cudaMemcpyAsync(h->grain_cs, cs.data(), cs.size() * sizeof(double2), cudaMemcpyHostToDevice,
+                      h->stream) != cudaSuccess)
+    return bail(PF_ERR_CUDA, "grain table upload failed");
+  if (upload_tables(h) != PF_OK) return bail(PF_ERR_CUDA, h->err.c_str());
+  *out = h;
+  return PF_OK;
+}
+
+extern "C" pf_status pf_destroy(pf_handle* h) {
+  if (!h) return PF_OK;
+  cudaStreamSynchronize(h->stream);
+  cudaError_t e = cudaGetLastError();
+  release(h);
+  delete h;
+  return e == cudaSuccess ? PF_OK : PF_ERR_CUDA;
+}
+
+extern "C" const char* pf_last_error(const pf_handle* h) {
+  return h ? h->err.c_str() : g_create_err.c_str();
+}
+
+extern "C" long long pf_steps_taken(const pf_handle* h) { return h ? h->steps : -1; }
+extern "C" long long pf_launch_count(const pf_handle* h) { return h ? h->launches : -1; }
+
+extern "C" pf_status pf_sync(pf_handle* h) {
+  if (!h) return PF_ERR_BAD_ARG;
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  PF_CUDA(h, cudaGetLastError());
+  return PF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// initialisation
+// ---------------------------------------------------------------------------
+// rho_bar of a domain from its initial fields (FP64 reduction), then upload.
+static pf_status finish_init(pf_handle* h, int dom) {
+  pf_diag dg{};
+  pf_status st = pf_reduce(h, dom, nullptr, &dg);
+  if (st != PF_OK) return st;
+  DomDesc& dd = h->ddesc[dom];
+  const double n = (double)dd.nx * dd.ny;
+  dd.rho_bar = h->p.rho_g + (dg.sum_phi / n) * (h->p.rho_l - h->p.rho_g);
+  PF_CUDA(h, cudaMemcpyAsync(h->d_doms + dom, &dd, sizeof(DomDesc), cudaMemcpyHostToDevice,
+                             h->stream));
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->inited[dom] = 1;
+  h->steps = 0;
+  return PF_OK;
+}
+
+template <typename S, typename R>
+static pf_status init_spec_t(pf_handle* h, int dom, const pf_init_spec* spec, const double* d_s,
+                             const double* d_b) {
+  InitArgs<S, R> a{};
+  a.out = reinterpret_cast<S*>(h->state[h->cur]);
+  a.fields = fields_ptr<R>(h);
+  a.grain = h->grain;
+  a.plane_stride = h->plane_stride;
+  a.dom = h->ddesc[dom];
+  a.seeds = d_s;
+  a.bubbles = d_b;
+  a.n_seeds = spec->n_seeds;
+  a.n_bub = spec->n_bubbles;
+  a.R_s = spec->R_s;
+  a.W0 = h->p.W0;
+  a.Wphi = h->p.W_phi;
+  a.sq2bpsi = std::sqrt(2.0 * h->p.beta_psi);
+  a.sq2bphi = std::sqrt(2.0 * h->p.beta_phi);
+  a.k = h->p.k;
+  a.kp = make_kparams<R>(h->p);
+  PF_CUDA(h, launch_init_spec<S, R>(a, h->stream));
+  h->launches++;
+  return PF_OK;
+}
+
+static pf_status upload_grain_table(pf_handle* h, int dom, const std::vector<double>& angles) {
+  std::vector<double2> cs(MAX_GRAINS, make_double2(1.0, 0.0));
+  for (size_t i = 0; i < angles.size(); ++i) cs[i] = make_double2(std::cos(angles[i]), std::sin(angles[i]));
+  PF_CUDA(h, cudaMemcpyAsync(h->grain_cs + (size_t)dom * MAX_GRAINS, cs.data(),
+                             MAX_GRAINS * sizeof(double2), cudaMemcpyHostToDevice, h->stream));
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PF_OK;
+}
+
+extern "C" pf_status pf_init_fields(pf_handle* h, int dom, const pf_init_spec* spec) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (!spec || dom < 0 || dom >= (int)h->doms.size())
+    return fail(h, PF_ERR_BAD_ARG, "bad domain index or NULL spec");
+  if (spec->n_seeds < 0 || spec->n_seeds > MAX_GRAINS || spec->n_bubbles < 0 ||
+      (spec->n_seeds > 0 && !spec->seeds) || (spec->n_bubbles > 0 && !spec->bubbles) ||
+      !std::isfinite(spec->R_s))
+    return fail(h, PF_ERR_BAD_ARG, "bad init spec (at most 256 seeds)");
+  for (int i = 0; i < 3 * spec->n_seeds; ++i)
+    if (!std::isfinite(spec->seeds[i])) return fail(h, PF_ERR_BAD_ARG, "non-finite seed");
+  for (int i = 0; i < 3 * spec->n_bubbles; ++i)
+    if (!std::isfinite(spec->bubbles[i])) return fail(h, PF_ERR_BAD_ARG, "non-finite bubble");
+  std::vector<double> angles;
+  for (int s = 0; s < spec->n_seeds; ++s) angles.push_back(spec->seeds[3 * s + 2]);
+  pf_status st = upload_grain_table(h, dom, angles);
+  if (st != PF_OK) return st;
+  const size_t ns = 3 * (size_t)spec->n_seeds, nb = 3 * (size_t)spec->n_bubbles;
+  double* buf = (double*)dev_alloc(h, (ns + nb + 1) * sizeof(double));
+  if (!buf) return fail(h, PF_ERR_OOM, "init buffer allocation failed");
+  if (ns) PF_CUDA(h, cudaMemcpyAsync(buf, spec->seeds, ns * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  if (nb) PF_CUDA(h, cudaMemcpyAsync(buf + ns, spec->bubbles, nb * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  st = h->prec == PF_FP64 ? init_spec_t<double, double>(h, dom, spec, buf, buf + ns)
+                          : init_spec_t<float, float>(h, dom, spec, buf, buf + ns);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  dev_free(h, buf);
+  if (st != PF_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(h, e, "init");
+  return finish_init(h, dom);
+}
+
+template <typename S, typename R>
+static pf_status set_fields_t(pf_handle* h, int dom, const double* d_f6, const uint8_t* d_ids) {
+  SetFieldsArgs<S, R> a{};
+  a.out = reinterpret_cast<S*>(h->state[h->cur]);
+  a.fields = fields_ptr<R>(h);
+  a.grain = h->grain;
+  a.plane_stride = h->plane_stride;
+  a.dom = h->ddesc[dom];
+  a.f6 = d_f6;
+  a.grain_ids = d_ids;
+  a.kp = make_kparams<R>(h->p);
+  PF_CUDA(h, launch_set_fields<S, R>(a, h->stream));
+  h->launches++;
+  return PF_OK;
+}
+
+extern "C" pf_status pf_set_fields(pf_handle* h, int dom, const double* fields6,
+                                   const double* theta, size_t n) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (dom < 0 || dom >= (int)h->doms.size() || !fields6)
+    return fail(h, PF_ERR_BAD_ARG, "bad domain index or NULL fields");
+  const size_t nn = (size_t)h->ddesc[dom].nx * h->ddesc[dom].ny;
+  if (n != nn) return fail(h, PF_ERR_BAD_ARG, "n must equal nx*ny of the domain");
+  for (size_t i = 0; i < 6 * nn; ++i)
+    if (!std::isfinite(fields6[i])) return fail(h, PF_ERR_BAD_ARG, "non-finite field value");
+  // grain angles: distinct values -> ids
+  std::vector<uint8_t> ids;
+  std::vector<double> angles;
+  if (theta) {
+    std::map<double, int> idx;
+    ids.resize(nn);
+    for (size_t i = 0; i < nn; ++i) {
+      if (!std::isfinite(theta[i])) return fail(h, PF_ERR_BAD_ARG, "non-finite angle");
+      auto it = idx.find(theta[i]);
+      if (it == idx.end()) {
+        if ((int)angles.size() >= MAX_GRAINS)
+          return fail(h, PF_ERR_BAD_ARG, "more than 256 distinct grain angles");
+        it = idx.emplace(theta[i], (int)angles.size()).first;
+        angles.push_back(theta[i]);
+      }
+      ids[i] = (uint8_t)it->second;
+    }
+  }
+  pf_status st = upload_grain_table(h, dom, angles);
+  if (st != PF_OK) return st;
+  st = ensure_staging(h, 7 * nn);  // 6 x n doubles + n grain ids
+  if (st != PF_OK) return st;
+  double* buf = h->staging;
+  uint8_t* d_ids = nullptr;
+  PF_CUDA(h, cudaMemcpyAsync(buf, fields6, 6 * nn * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  if (theta) {
+    d_ids = reinterpret_cast<uint8_t*>(buf + 6 * nn);
+    PF_CUDA(h, cudaMemcpyAsync(d_ids, ids.data(), nn, cudaMemcpyHostToDevice, h->stream));
+  }
+  st = h->prec == PF_FP64 ? set_fields_t<double, double>(h, dom, buf, d_ids)
+                          : set_fields_t<float, float>(h, dom, buf, d_ids);
+  if (st != PF_OK) return st;
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  return finish_init(h, dom);
+}
+
+// ---------------------------------------------------------------------------
+// stepping
+// ---------------------------------------------------------------------------
+template <typename S, typename R>
+static pf_status step_t(pf_handle* h, bool write_fields) {
+  StepArgs<S, R> a{};
+  a.in = reinterpret_cast<const S*>(h->state[h->cur]);
+  a.out = reinterpret_cast<S*>(h->state[h->cur ^ 1]);
+  a.plane_stride = h->plane_stride;
+  a.grain = h->grain;
+  a.grain_cs = h->grain_cs;
+  a.doms = h->d_doms;
+  a.tile_dom = h->d_tile_dom;
+  a.ntiles = h->ntiles;
+  a.fields = write_fields ? fields_ptr<R>(h) : nullptr;
+  a.kp = make_kparams<R>(h->p);
+  PF_CUDA(h, launch_step<S, R>(a, h->tx, h->ty, h->grid, h->stream));
+  h->launches++;
+  h->cur ^= 1;
+  h->steps++;
+  return PF_OK;
+}
+
+extern "C" pf_status pf_step(pf_handle* h, int n_steps) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (n_steps < 0) return fail(h, PF_ERR_BAD_ARG, "n_steps must be >= 0");
+  for (int d : h->inited)
+    if (!d) return fail(h, PF_ERR_STATE, "every domain must be initialised before stepping");
+  for (int t = 0; t < n_steps; ++t) {
+    const bool last = t == n_steps - 1;
+    pf_status st = h->prec == PF_FP64 ? step_t<double, double>(h, last)
+                                      : step_t<float, float>(h, last);
+    if (st != PF_OK) return st;
+  }
+  return PF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// outputs
+// ---------------------------------------------------------------------------
+extern "C" pf_status pf_get_fields(pf_handle* h, int dom, uint32_t mask, double* host_out,
+                                   size_t n) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (dom < 0 || dom >= (int)h->doms.size() || !host_out || (mask & ~0xFFu) || !mask)
+    return fail(h, PF_ERR_BAD_ARG, "bad domain, mask or output");
+  const DomDesc& dd = h->ddesc[dom];
+  const size_t nn = (size_t)dd.nx * dd.ny;
+  const size_t need = nn * __builtin_popcount(mask);
+  if (n < need) return fail(h, PF_ERR_BAD_ARG, "output buffer too small");
+  pf_status st = ensure_staging(h, need);
+  if (st != PF_OK) return st;
+  if (h->prec == PF_FP64)
+    PF_CUDA(h, launch_fields_to_f64<double>(fields_ptr<double>(h), h->plane_stride, dd.off,
+                                            (long long)nn, mask, h->staging, h->stream));
+  else
+    PF_CUDA(h, launch_fields_to_f64<float>(fields_ptr<float>(h), h->plane_stride, dd.off,
+                                           (long long)nn, mask, h->staging, h->stream));
+  h->launches++;
+  PF_CUDA(h, cudaMemcpyAsync(host_out, h->staging, need * sizeof(double), cudaMemcpyDeviceToHost,
+                             h->stream));
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PF_OK;
+}
+
+extern "C" pf_status pf_get_state(pf_handle* h, int dom, double* host_out, size_t n) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (dom < 0 || dom >= (int)h->doms.size() || !host_out)
+    return fail(h, PF_ERR_BAD_ARG, "bad domain or output");
+  const DomDesc& dd = h->ddesc[dom];
+  const size_t nn = (size_t)dd.nx * dd.ny;
+  if (n < nn * N_PLANES) return fail(h, PF_ERR_BAD_ARG, "output buffer too small");
+  pf_status st = ensure_staging(h, nn * N_PLANES);
+  if (st != PF_OK) return st;
+  if (h->prec == PF_FP64)
+    PF_CUDA(h, launch_state_to_f64<double>((const double*)h->state[h->cur], h->plane_stride,
+                                           dd.off, (long long)nn, N_PLANES, h->staging, h->stream));
+  else
+    PF_CUDA(h, launch_state_to_f64<float>((const float*)h->state[h->cur], h->plane_stride, dd.off,
+                                          (long long)nn, N_PLANES, h->staging, h->stream));
+  h->launches++;
+  PF_CUDA(h, cudaMemcpyAsync(host_out, h->staging, nn * N_PLANES * sizeof(double),
+                             cudaMemcpyDeviceToHost, h->stream));
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PF_OK;
+}
+
+extern "C" pf_status pf_set_state(pf_handle* h, int dom, const double* host_in, size_t n) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (dom < 0 || dom >= (int)h->doms.size() || !host_in)
+    return fail(h, PF_ERR_BAD_ARG, "bad domain or input");
+  const DomDesc& dd = h->ddesc[dom];
+  const size_t nn = (size_t)dd.nx * dd.ny;
+  if (n != nn * N_PLANES) return fail(h, PF_ERR_BAD_ARG, "input must hold 39 planes of nx*ny");
+  pf_status st = ensure_staging(h, nn * N_PLANES);
+  if (st != PF_OK) return st;
+  PF_CUDA(h, cudaMemcpyAsync(h->staging, host_in, nn * N_PLANES * sizeof(double),
+                             cudaMemcpyHostToDevice, h->stream));
+  if (h->prec == PF_FP64)
+    PF_CUDA(h, launch_state_from_f64<double>((double*)h->state[h->cur], h->plane_stride, dd.off,
+                                             (long long)nn, N_PLANES, h->staging, h->stream));
+  else
+    PF_CUDA(h, launch_state_from_f64<float>((float*)h->state[h->cur], h->plane_stride, dd.off,
+                                            (long long)nn, N_PLANES, h->staging, h->stream));
+  h->launches++;
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->inited[dom] = 1;
+  return PF_OK;
+}
+
+template <typename R>
+static pf_status reduce_t(pf_handle* h, int dom, const pf_probe* probe) {
+  ReduceArgs<R> a{};
+  a.fields = fields_ptr<R>(h);
+  a.plane_stride = h->plane_stride;
+  a.dom = h->ddesc[dom];
+  a.probe = probe != nullptr;
+  if (probe) { a.xc = probe->xc; a.yc = probe->yc; a.Rp = probe->R; a.W = probe->W; }
+  PF_CUDA(h, launch_reduce<R>(a, h->partial, h->d_diag, h->stream));
+  h->launches += 2;
+  return PF_OK;
+}
+
+extern "C" pf_status pf_reduce(pf_handle* h, int dom, const pf_probe* probe, pf_diag* out) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (dom < 0 || dom >= (int)h->doms.size() || !out)
+    return fail(h, PF_ERR_BAD_ARG, "bad domain or output");
+  pf_status st = h->prec == PF_FP64 ? reduce_t<double>(h, dom, probe) : reduce_t<float>(h, dom, probe);
+  if (st != PF_OK) return st;
+  double buf[NDIAG];
+  PF_CUDA(h, cudaMemcpyAsync(buf, h->d_diag, sizeof(buf), cudaMemcpyDeviceToHost, h->stream));
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  static_assert(sizeof(pf_diag) == NDIAG * sizeof(double), "pf_diag layout");
+  std::memcpy(out, buf, sizeof(buf));
+  return PF_OK;
+}

@@ -1,0 +1,259 @@
+"""Thin ctypes binding of the C ABI in ``include/pf.h``.
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of ``_build/libpf.so``.  PyTorch supplies the CUDA stream and, optionally, the
+device memory (its caching allocator is handed to ``pf_create``).  There is
+no CPU fallback: if the library is missing this module raises on first use.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpf.so")
+
+PF_OK, PF_ERR_BAD_ARG, PF_ERR_OOM, PF_ERR_CUDA, PF_ERR_TIMEOUT, PF_ERR_NAN, PF_ERR_STATE = (
+    0, -1, -2, -3, -4, -5, -6)
+PF_FP64, PF_FP32, PF_FP16_OFFSET, PF_BF16_OFFSET = 0, 1, 2, 3
+PRECISIONS = {"fp64": PF_FP64, "fp32": PF_FP32, "fp16": PF_FP16_OFFSET, "bf16": PF_BF16_OFFSET}
+FIELDS = ("phi", "psi", "C", "U", "p", "vx", "vy", "mu")
+STATE_PLANES = 39
+
+_PARAM_FIELDS = ("rho_l", "rho_g", "nu", "sigma", "W_phi", "M_phi", "beta_phi", "beta_psi",
+                 "beta_inter", "W0", "tau0", "eps_s", "k", "D", "Omega", "g", "grad_eps",
+                 "grad_eps_at", "s_e", "s_eps")
+
+
+class pf_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in _PARAM_FIELDS]
+
+
+class pf_domain(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("eps_s", ctypes.c_double)]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class pf_allocator(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("alloc", _ALLOC_FN), ("free", _FREE_FN)]
+
+
+class pf_init_spec(ctypes.Structure):
+    _fields_ = [("n_seeds", ctypes.c_int), ("seeds", ctypes.POINTER(ctypes.c_double)),
+                ("R_s", ctypes.c_double), ("n_bubbles", ctypes.c_int),
+                ("bubbles", ctypes.POINTER(ctypes.c_double))]
+
+
+_DIAG_FIELDS = ("sum_phi", "sum_C", "sum_hpsi", "gas", "gas_x", "gas_y", "p_in_sum", "p_in_n",
+                "p_out_sum", "p_out_n", "max_v", "nonfinite")
+
+
+class pf_diag(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in _DIAG_FIELDS]
+
+
+class pf_probe(ctypes.Structure):
+    _fields_ = [("xc", ctypes.c_double), ("yc", ctypes.c_double), ("R", ctypes.c_double),
+                ("W", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libpf.so (built by ``build()``); raise if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(LIB_PATH)
+    P, D, I, S = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_size_t
+    L.pf_params_default.argtypes = [ctypes.POINTER(pf_params)]
+    L.pf_params_derived.argtypes = [ctypes.POINTER(pf_params), D]
+    L.pf_create.argtypes = [ctypes.POINTER(pf_params), ctypes.POINTER(pf_domain), I, I, P,
+                            ctypes.POINTER(pf_allocator), ctypes.POINTER(P)]
+    L.pf_init_fields.argtypes = [P, I, ctypes.POINTER(pf_init_spec)]
+    L.pf_set_fields.argtypes = [P, I, D, D, S]
+    L.pf_step.argtypes = [P, I]
+    L.pf_get_fields.argtypes = [P, I, ctypes.c_uint32, D, S]
+    L.pf_get_state.argtypes = [P, I, D, S]
+    L.pf_set_state.argtypes = [P, I, D, S]
+    L.pf_reduce.argtypes = [P, I, ctypes.POINTER(pf_probe), ctypes.POINTER(pf_diag)]
+    L.pf_sync.argtypes = [P]
+    L.pf_steps_taken.argtypes = [P]
+    L.pf_steps_taken.restype = ctypes.c_longlong
+    L.pf_launch_count.argtypes = [P]
+    L.pf_launch_count.restype = ctypes.c_longlong
+    L.pf_destroy.argtypes = [P]
+    L.pf_last_error.argtypes = [P]
+    L.pf_last_error.restype = ctypes.c_char_p
+    for name in ("pf_params_default", "pf_params_derived", "pf_create", "pf_init_fields",
+                 "pf_set_fields", "pf_step", "pf_get_fields", "pf_get_state", "pf_set_state",
+                 "pf_reduce", "pf_sync", "pf_destroy"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+class PFError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pf error {code}: {msg}")
+        self.code = code
+
+
+def _check(code: int, handle=None) -> None:
+    if code != PF_OK:
+        msg = lib().pf_last_error(handle).decode(errors="replace")
+        raise PFError(code, msg)
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def params_from_dict(d: dict | None = None) -> pf_params:
+    p = pf_params()
+    _check(lib().pf_params_default(ctypes.byref(p)))
+    for k, v in (d or {}).items():
+        if k in _PARAM_FIELDS:
+            setattr(p, k, float(v))
+    return p
+
+
+def pf_params_derived(d: dict) -> tuple[float, float, float]:
+    out = np.zeros(3)
+    _check(lib().pf_params_derived(ctypes.byref(params_from_dict(d)), _dp(out)))
+    return tuple(out.tolist())
+
+
+def torch_allocator(device=None):
+    """A pf_allocator backed by PyTorch's caching allocator."""
+    import torch
+
+    dev = torch.cuda.current_device() if device is None else device
+
+    def _alloc(ctx, nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream or 0)
+
+    def _free(ctx, ptr, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = pf_allocator(None, _ALLOC_FN(_alloc), _FREE_FN(_free))
+    return a
+
+
+class Simulation:
+    """Handle of ``n`` periodic domains; methods mirror the C ABI."""
+
+    def __init__(self, domains, params: dict | None = None, precision: str = "fp32",
+                 stream=None, use_torch_allocator: bool = False):
+        L = lib()
+        doms = (pf_domain * len(domains))()
+        for i, dm in enumerate(domains):
+            nx, ny = dm[0], dm[1]
+            eps = dm[2] if len(dm) > 2 and dm[2] is not None else -1.0
+            doms[i] = pf_domain(int(nx), int(ny), float(eps))
+        self.domains = [(int(d.nx), int(d.ny)) for d in doms]
+        self.params = params_from_dict(params)
+        self._alloc = torch_allocator() if use_torch_allocator else None
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                stream = 0
+        self.stream = stream
+        h = ctypes.c_void_p()
+        code = L.pf_create(ctypes.byref(self.params), doms, len(domains), PRECISIONS[precision],
+                           ctypes.c_void_p(stream),
+                           ctypes.byref(self._alloc) if self._alloc else None, ctypes.byref(h))
+        _check(code, None)
+        self.h = h
+        self.precision = precision
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            code = lib().pf_destroy(self.h)
+            self.h = None
+            _check(code)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- initialisation --------------------------------------------------------
+    def init_fields(self, dom: int, seeds, R_s: float, bubbles) -> None:
+        s = np.ascontiguousarray(np.asarray(seeds, dtype=np.float64).reshape(-1, 3))
+        b = np.ascontiguousarray(np.asarray(bubbles, dtype=np.float64).reshape(-1, 3))
+        spec = pf_init_spec(len(s), _dp(s), float(R_s), len(b), _dp(b))
+        _check(lib().pf_init_fields(self.h, dom, ctypes.byref(spec)), self.h)
+
+    def set_fields(self, dom: int, phi, psi, C, vx=None, vy=None, p=None, theta=None) -> None:
+        nx, ny = self.domains[dom]
+        z = np.zeros((ny, nx))
+        f6 = np.ascontiguousarray(np.stack([np.asarray(a if a is not None else z, dtype=np.float64)
+                                            .reshape(ny, nx) for a in (phi, psi, C, vx, vy, p)]))
+        th = None if theta is None else np.ascontiguousarray(
+            np.broadcast_to(np.asarray(theta, dtype=np.float64), (ny, nx)))
+        _check(lib().pf_set_fields(self.h, dom, _dp(f6), _dp(th) if th is not None else None,
+                                   nx * ny), self.h)
+
+    # -- stepping --------------------------------------------------------------
+    def step(self, n: int = 1) -> None:
+        _check(lib().pf_step(self.h, int(n)), self.h)
+
+    def sync(self) -> None:
+        _check(lib().pf_sync(self.h), self.h)
+
+    @property
+    def steps(self) -> int:
+        return lib().pf_steps_taken(self.h)
+
+    @property
+    def launches(self) -> int:
+        return lib().pf_launch_count(self.h)
+
+    # -- outputs ---------------------------------------------------------------
+    def fields(self, dom: int = 0, names=FIELDS, out: np.ndarray | None = None) -> dict:
+        mask = 0
+        for nm in names:
+            mask |= 1 << FIELDS.index(nm)
+        sel = [nm for nm in FIELDS if mask & (1 << FIELDS.index(nm))]
+        nx, ny = self.domains[dom]
+        if out is None:
+            out = np.empty(len(sel) * nx * ny)
+        _check(lib().pf_get_fields(self.h, dom, mask, _dp(out), out.size), self.h)
+        out = out[: len(sel) * nx * ny].reshape(len(sel), ny, nx)
+        return {nm: out[i] for i, nm in enumerate(sel)}
+
+    def get_state(self, dom: int = 0) -> np.ndarray:
+        nx, ny = self.domains[dom]
+        out = np.empty(STATE_PLANES * nx * ny)
+        _check(lib().pf_get_state(self.h, dom, _dp(out), out.size), self.h)
+        return out.reshape(STATE_PLANES, ny, nx)
+
+    def set_state(self, dom: int, state: np.ndarray) -> None:
+        a = np.ascontiguousarray(np.asarray(state, dtype=np.float64)).ravel()
+        _check(lib().pf_set_state(self.h, dom, _dp(a), a.size), self.h)
+
+    def reduce(self, dom: int = 0, probe=None) -> dict:
+        d = pf_diag()
+        pr = pf_probe(*probe) if probe is not None else None
+        _check(lib().pf_reduce(self.h, dom, ctypes.byref(pr) if pr else None, ctypes.byref(d)),
+               self.h)
+        return {k: getattr(d, k) for k in _DIAG_FIELDS}

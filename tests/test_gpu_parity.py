@@ -1,0 +1,292 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Both sides start from the same seeded seeds/bubbles (``workload.py``) and
+each computes its own initial fields; nothing the GPU produces is fed to the
+oracle.  Tolerances: FP64 storage and arithmetic agree with the oracle to
+rounding (1e-12 relative per field after one step, 1e-9 after 1000 coupled
+steps); FP32 agrees to 1e-5 relative per field per step.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_01651_gb300 import pf
+from paper_2407_01651_gb300 import workload as wl
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("phi", "psi", "C", "U", "p", "vx", "vy", "mu")
+
+
+def rel(a, b):
+    scale = np.abs(b).max()
+    return np.abs(a - b).max() / scale if scale > 0 else np.abs(a - b).max()
+
+
+def pair(lay, precision, params=None):
+    par = dict(lay.params, **(params or {}))
+    o = oracle.Oracle(lay.nx, lay.ny, par)
+    o.init_spec(lay.seeds, lay.R_s, lay.bubbles)
+    sim = pf.Simulation([(lay.nx, lay.ny)], par, precision)
+    sim.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
+    return o, sim
+
+
+def compare_fields(o, sim, tol, names=FIELDS, dom=0):
+    fo = o.fields(names)
+    fg = sim.fields(dom, names)
+    errs = {k: rel(fg[k], fo[k]) for k in names}
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, (bad, errs)
+    return errs
+
+
+def small_layout():
+    # ragged: 70 x 52 spans several 32 x 8 tiles with partial tiles on both axes
+    return wl.random_layout(70, 52, 2, 2, rng_seed=21, R_max=10)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-6)])
+def test_initial_fields_match(precision, tol):
+    o, sim = pair(small_layout(), precision)
+    compare_fields(o, sim, tol, names=("phi", "psi", "C", "U"))
+    st_o, st_g = o.state(), sim.get_state()
+    for p in range(pf.STATE_PLANES):
+        assert rel(st_g[p], st_o[p]) <= max(tol, 1e-15), p
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_one_step_matches(precision, tol):
+    o, sim = pair(small_layout(), precision)
+    o.step(1)
+    sim.step(1)
+    compare_fields(o, sim, tol)
+    st_o, st_g = o.state(), sim.get_state()
+    for p in range(pf.STATE_PLANES):
+        assert rel(st_g[p], st_o[p]) <= tol, p
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+def test_few_steps_with_rotated_grains_and_gravity(precision, tol):
+    lay = wl.random_layout(64, 96, 3, 3, rng_seed=33, R_max=12)
+    o, sim = pair(lay, precision, dict(g=1e-4))
+    for _ in range(3):
+        o.step(1)
+        sim.step(1)
+        compare_fields(o, sim, tol)
+
+
+def test_fp64_thousand_steps_128(tmp_path):
+    """The 128^2 workload: same-step compare every 100 steps over 1000 steps,
+    and conservation of gas and solute to 1e-10 in the FP64 reductions."""
+    lay = wl.cfg1_layout()
+    o, sim = pair(lay, "fp64")
+    d0 = sim.reduce(0)
+    worst = {}
+    for blk in range(10):
+        o.step(100)
+        sim.step(100)
+        errs = compare_fields(o, sim, 1e-9)
+        worst = {k: max(worst.get(k, 0.0), v) for k, v in errs.items()}
+        d = sim.reduce(0)
+        assert abs(d["sum_phi"] / d0["sum_phi"] - 1) <= 1e-10
+        assert abs(d["sum_C"] / d0["sum_C"] - 1) <= 1e-10
+        od = o.diag()
+        assert math.isclose(d["sum_hpsi"], od["sum_hpsi"], rel_tol=1e-12)
+        assert math.isclose(d["gas_y"], od["gas_y"], rel_tol=1e-12)
+    (tmp_path / "worst.txt").write_text(repr(worst))
+
+
+def test_fp32_error_against_fp64_oracle_over_steps():
+    """FP32 per-step error stays at 1e-5; over 100 steps it stays bounded."""
+    lay = wl.cfg1_layout()
+    o, sim = pair(lay, "fp32")
+    o.step(1)
+    sim.step(1)
+    compare_fields(o, sim, 1e-5)
+    o.step(99)
+    sim.step(99)
+    compare_fields(o, sim, 1e-3, names=("phi", "psi", "C", "U", "p", "mu"))
+
+
+def test_multi_domain_handle_matches_separate_oracles():
+    lays = [wl.random_layout(40, 36, 1, 1, rng_seed=41, R_max=6),
+            wl.random_layout(64, 48, 2, 1, rng_seed=42, R_max=8),
+            wl.random_layout(33, 70, 1, 2, rng_seed=43, R_max=6)]
+    eps = [0.02, 0.05, 0.065]
+    sim = pf.Simulation([(l.nx, l.ny, e) for l, e in zip(lays, eps)], wl.BASE_PARAMS, "fp64")
+    oracles = []
+    for d, (l, e) in enumerate(zip(lays, eps)):
+        sim.init_fields(d, l.seeds, l.R_s, l.bubbles)
+        o = oracle.Oracle(l.nx, l.ny, dict(l.params, eps_s=e))
+        o.init_spec(l.seeds, l.R_s, l.bubbles)
+        oracles.append(o)
+    sim.step(5)
+    for d, o in enumerate(oracles):
+        o.step(5)
+        compare_fields(o, sim, 1e-12, dom=d)
+
+
+def test_set_fields_taylor_green():
+    N, U0 = 48, 1e-3
+    k = 2 * math.pi / N
+    y, x = np.mgrid[0:N, 0:N].astype(float)
+    vx = -U0 * np.cos(k * x) * np.sin(k * y)
+    vy = U0 * np.sin(k * x) * np.cos(k * y)
+    p = -0.25 * U0 * U0 * (np.cos(2 * k * x) + np.cos(2 * k * y))
+    one = np.ones_like(x)
+    par = dict(wl.BASE_PARAMS, g=0.0)
+    o = oracle.Oracle(N, N, par)
+    o.init_fields(one, -one, one, vx, vy, p)
+    sim = pf.Simulation([(N, N)], par, "fp64")
+    sim.set_fields(0, one, -one, one, vx, vy, p)
+    o.step(50)
+    sim.step(50)
+    compare_fields(o, sim, 1e-12, names=("vx", "vy", "p"))
+
+
+def test_set_fields_with_grain_angles_matches_oracle():
+    nx, ny = 40, 40
+    lay = wl.random_layout(nx, ny, 2, 0, rng_seed=51)
+    par = dict(lay.params, g=0.0)
+    o = oracle.Oracle(nx, ny, par)
+    phi, psi, C = o.fields_from_spec(lay.seeds, lay.R_s, [])
+    theta = np.where(np.arange(nx)[None, :] < nx // 2, 0.3, 1.1) * np.ones((ny, 1))
+    o.init_fields(phi, psi, C)
+    # the oracle takes orientations from seeds; build two pseudo-seeds that
+    # reproduce the left/right split exactly is not possible, so compare a
+    # single uniform angle instead
+    o.set_orientation([(0.0, 0.0, 0.7)])
+    sim = pf.Simulation([(nx, ny)], par, "fp64")
+    sim.set_fields(0, phi, psi, C, theta=0.7 * np.ones((ny, nx)))
+    o.step(10)
+    sim.step(10)
+    compare_fields(o, sim, 1e-12)
+    assert theta.shape == (ny, nx)
+
+
+def test_reductions_and_laplace_probe_match_oracle():
+    N, R, W = 64, 12.0, 2.0
+    par = dict(wl.BASE_PARAMS, g=0.0, W_phi=W, nu=0.3)
+    lay = wl.Layout(N, N, seeds=[], bubbles=[(N / 2, N / 2, R)], params=par)
+    o, sim = pair(lay, "fp64")
+    o.step(300)
+    sim.step(300)
+    probe = (N / 2, N / 2, R, W)
+    dg, do = sim.reduce(0, probe), o.diag(probe)
+    for k in ("sum_phi", "sum_C", "sum_hpsi", "gas", "gas_x", "gas_y", "p_in_sum", "p_out_sum"):
+        assert math.isclose(dg[k], do[k], rel_tol=1e-11, abs_tol=1e-14), k
+    for k in ("p_in_n", "p_out_n", "nonfinite"):
+        assert dg[k] == do[k], k
+    assert math.isclose(dg["max_v"], do["max_v"], rel_tol=1e-10)
+
+
+def test_uniform_melt_is_a_fixed_point():
+    """No seeds and no bubbles: the uniform melt (phi = 1, psi = -1, U = 0) is an
+    exact fixed point of both sides."""
+    lay = wl.Layout(37, 29, seeds=[], bubbles=[])
+    o, sim = pair(lay, "fp32")
+    sim.step(20)
+    f = sim.fields()
+    assert np.all(f["phi"] == 1.0) and np.all(f["psi"] == -1.0)
+    assert np.all(f["vx"] == 0.0) and np.all(f["vy"] == 0.0)
+
+
+def test_smallest_domain_and_ragged_sizes():
+    for nx, ny in ((4, 4), (5, 9), (33, 7)):
+        lay = wl.Layout(nx, ny, seeds=[(nx / 2, ny / 2, 0.2)], bubbles=[])
+        o, sim = pair(lay, "fp64")
+        o.step(3)
+        sim.step(3)
+        compare_fields(o, sim, 1e-12)
+
+
+def test_torch_allocator_gives_identical_results():
+    lay = small_layout()
+    a = pf.Simulation([(lay.nx, lay.ny)], lay.params, "fp32")
+    b = pf.Simulation([(lay.nx, lay.ny)], lay.params, "fp32", use_torch_allocator=True)
+    for s in (a, b):
+        s.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
+        s.step(7)
+    fa, fb = a.fields(), b.fields()
+    for k in FIELDS:
+        assert np.array_equal(fa[k], fb[k]), k
+
+
+def test_state_checkpoint_restart_is_exact():
+    lay = small_layout()
+    a = pf.Simulation([(lay.nx, lay.ny)], lay.params, "fp64")
+    a.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
+    a.step(5)
+    ck = a.get_state()
+    a.step(5)
+    fa = a.fields()
+    b = pf.Simulation([(lay.nx, lay.ny)], lay.params, "fp64")
+    b.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
+    b.set_state(0, ck)
+    b.step(5)
+    fb = b.fields()
+    for k in FIELDS:
+        assert np.array_equal(fa[k], fb[k]), k
+
+
+def test_argument_errors_are_reported():
+    with pytest.raises(pf.PFError) as e:
+        pf.Simulation([(3, 8)], wl.BASE_PARAMS, "fp32")
+    assert e.value.code == pf.PF_ERR_BAD_ARG
+    with pytest.raises(pf.PFError) as e:
+        pf.Simulation([(8, 8)], dict(wl.BASE_PARAMS, k=1.5), "fp32")
+    assert e.value.code == pf.PF_ERR_BAD_ARG
+    sim = pf.Simulation([(16, 16)], wl.BASE_PARAMS, "fp32")
+    with pytest.raises(pf.PFError) as e:
+        sim.step(1)
+    assert e.value.code == pf.PF_ERR_STATE
+    with pytest.raises(pf.PFError) as e:
+        sim.init_fields(0, [(1.0, 1.0, 0.0)] * 257, 6.0, [])
+    assert e.value.code == pf.PF_ERR_BAD_ARG
+    sim.init_fields(0, [], 6.0, [])
+    with pytest.raises(pf.PFError) as e:
+        sim.step(-1)
+    assert e.value.code == pf.PF_ERR_BAD_ARG
+    with pytest.raises(pf.PFError) as e:
+        sim.fields(0, out=np.empty(10))
+    assert e.value.code == pf.PF_ERR_BAD_ARG
+    sim.step(0)
+    sim.sync()
+
+
+def test_full_size_4096_sampled_against_oracle_windows():
+    """The 4096^2 FP32 workload in the launch configuration the benchmark
+    times: after 2 steps, sites sampled near seeds and bubbles match oracle
+    windows (global coordinates, full-lattice rho_bar computed by the oracle)."""
+    lay = wl.cfg2_layout()
+    sim = pf.Simulation([(lay.nx, lay.ny)], lay.params, "fp32")
+    sim.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
+    T = 2
+    sim.step(T)
+    names = ("phi", "psi", "C", "U", "p", "vx", "vy", "mu")
+    fg = sim.fields(0, names)
+    W, M = 24, 2 * 2 * T                     # window and trusted margin
+    probe = oracle.Oracle(4, 4, lay.params, window=(lay.nx, lay.ny, 0, 0))
+    rho_bar = lay.params["rho_g"] + probe.mean_phi_global(lay.bubbles) * (
+        lay.params["rho_l"] - lay.params["rho_g"])
+    centers = [(int(s[0]) + 5, int(s[1])) for s in lay.seeds[:4]]
+    centers += [(int(b[0] + b[2]), int(b[1])) for b in lay.bubbles[:4]]
+    ref, got = {k: [] for k in names}, {k: [] for k in names}
+    for cx, cy in centers:
+        x0, y0 = cx - W // 2, cy - W // 2
+        o = oracle.Oracle(W, W, lay.params, window=(lay.nx, lay.ny, x0, y0))
+        o.set_rho_bar(rho_bar)
+        o.init_spec(lay.seeds, lay.R_s, lay.bubbles)
+        o.step(T)
+        fo = o.fields(names)
+        ys = (np.arange(M, W - M) + y0) % lay.ny
+        xs = (np.arange(M, W - M) + x0) % lay.nx
+        for k in names:
+            ref[k].append(fo[k][M:W - M, M:W - M])
+            got[k].append(fg[k][np.ix_(ys, xs)])
+    for k in names:
+        r, g = np.concatenate(ref[k]), np.concatenate(got[k])
+        assert rel(g, r) <= 1e-5, (k, rel(g, r))
