@@ -173,7 +173,7 @@ extern "C" pf_status pf_params_default(pf_params* out) {
   p.rho_l = 1.0; p.rho_g = 0.1; p.nu = 0.1; p.sigma = 1e-3; p.W_phi = 4.0; p.M_phi = 0.1;
   p.beta_phi = 0.25; p.beta_psi = 0.25; p.beta_inter = 0.75;
   p.W0 = 4.0; p.tau0 = 320.0; p.eps_s = 0.05; p.k = 0.15; p.D = 0.1; p.Omega = 0.55;
-  p.g = 1e-6; p.grad_eps = 1e-6; p.grad_eps_at = 1e-2; p.s_e = 1.0; p.s_eps = 1.0;
+  p.g = 1e-6; p.grad_eps = 1e-3; p.grad_eps_at = 1e-2; p.s_e = 1.0; p.s_eps = 1.0;
   *out = p;
   return PF_OK;
 }

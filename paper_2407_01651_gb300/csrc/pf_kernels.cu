@@ -30,6 +30,20 @@ __device__ __forceinline__ void st(S* __restrict__ p, long long i, R v) {
   p[i] = static_cast<S>(v);
 }
 
+// Compensated (Neumaier) accumulation: the zeroth moments phi, psi, C are sums
+// of 5 or 9 populations of similar size; in FP32 plain summation loses up to
+// ~8 ulp(phi), which the W_phi^2-weighted Laplacian in mu_phi then amplifies.
+template <typename R>
+struct CSum {
+  R s = R(0), c = R(0);
+  __device__ __forceinline__ void add(R v) {
+    const R t = s + v;
+    c += (fabs(s) >= fabs(v)) ? ((s - t) + v) : ((v - t) + s);
+    s = t;
+  }
+  __device__ __forceinline__ R value() const { return s + c; }
+};
+
 __device__ __forceinline__ int wrapi(int a, int n) {
   a %= n;
   return a < 0 ? a + n : a;
@@ -48,19 +62,19 @@ __device__ __forceinline__ void pulled_phi_psi(const StepArgs<S, R>& a, const Do
   const long long src[9] = {r0 + x, r0 + xm, rm + x, r0 + xp, rp + x,
                             rm + xm, rm + xp, rp + xp, rp + xm};
   const long long ps = a.plane_stride;
-  R s = R(0);
+  CSum<R> s;
 #pragma unroll
-  for (int i = 0; i < 9; ++i) s += ld<R>(a.in + (P_H + i) * ps, src[i]);
-  phi = s;
-  R t = R(0);
+  for (int i = 0; i < 9; ++i) s.add(ld<R>(a.in + (P_H + i) * ps, src[i]));
+  phi = s.value();
+  CSum<R> t;
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
     const R gold = ld<R>(a.in + (P_GPRE + i) * ps, src[0]);
     const R gpo = ld<R>(a.in + (P_GPOST + i) * ps, src[i]);
     const R rr = ld<R>(a.in + P_RR * ps, src[i]);
-    t += gold + (gpo - gold) * rr;
+    t.add(gold + (gpo - gold) * rr);
   }
-  psi = t;
+  psi = t.value();
 }
 
 template <typename S, typename R>
@@ -124,19 +138,28 @@ __global__ void __launch_bounds__(256) k_step(StepArgs<S, R> a) {
         s[i] = ld<R>(a.in + (P_S + i) * ps, src[i]);
       }
       const R phi = sphi[c], psi = spsi[c];
-      const R C = s[0] + s[1] + s[2] + s[3] + s[4];
+      R C;
+      {
+        CSum<R> cs;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) cs.add(s[i]);
+        C = cs.value();
+      }
       const R phio = ld<R>(a.in + P_PHIO * ps, site);
       const R Co = ld<R>(a.in + P_CO * ps, site);
       const R vxo = svx[c], vyo = svy[c];
       const R Qo = ld<R>(a.in + P_QO * ps, site);
 
-      // ---- isotropic stencils ----
+      // ---- isotropic stencils, on differences from the centre value so that
+      // FP32 keeps the bits of the (small) neighbour differences ----
       const R w1 = R(1.0 / 9.0), w2 = R(1.0 / 36.0);
       auto grad = [&](const R* X, R& gx, R& gy) {
-        const R e = X[c + 1], w = X[c - 1], n = X[c + SW], so = X[c - SW];
-        const R ne = X[c + SW + 1], nw = X[c + SW - 1], sw = X[c - SW - 1], se = X[c - SW + 1];
-        gx = R(3) * (w1 * (e - w) + w2 * (ne - nw - sw + se));
-        gy = R(3) * (w1 * (n - so) + w2 * (ne + nw - sw - se));
+        const R X0 = X[c];
+        const R e = X[c + 1] - X0, w = X[c - 1] - X0, n = X[c + SW] - X0, so = X[c - SW] - X0;
+        const R ne = X[c + SW + 1] - X0, nw = X[c + SW - 1] - X0;
+        const R sw = X[c - SW - 1] - X0, se = X[c - SW + 1] - X0;
+        gx = R(3) * (w1 * (e - w) + w2 * ((ne - sw) + (se - nw)));
+        gy = R(3) * (w1 * (n - so) + w2 * ((ne - sw) + (nw - se)));
       };
       R gpx, gpy, gsx, gsy, dvxx, dvxy, dvyx, dvyy;
       grad(sphi, gpx, gpy);
@@ -146,9 +169,10 @@ __global__ void __launch_bounds__(256) k_step(StepArgs<S, R> a) {
       R lphi;
       {
         const R X0 = sphi[c];
-        const R ax = sphi[c + 1] + sphi[c - 1] + sphi[c + SW] + sphi[c - SW] - R(4) * X0;
-        const R dg = sphi[c + SW + 1] + sphi[c + SW - 1] + sphi[c - SW - 1] + sphi[c - SW + 1] -
-                     R(4) * X0;
+        const R ax = ((sphi[c + 1] - X0) + (sphi[c - 1] - X0)) +
+                     ((sphi[c + SW] - X0) + (sphi[c - SW] - X0));
+        const R dg = ((sphi[c + SW + 1] - X0) + (sphi[c - SW - 1] - X0)) +
+                     ((sphi[c + SW - 1] - X0) + (sphi[c - SW + 1] - X0));
         lphi = R(6) * (w1 * ax + w2 * dg);
       }
 

@@ -23,7 +23,7 @@ _MASK = (1 << 64) - 1
 BASE_PARAMS = dict(
     rho_l=1.0, rho_g=0.1, nu=0.1, sigma=1e-3, W_phi=4.0, M_phi=0.1,
     beta_phi=0.25, beta_psi=0.25, beta_inter=0.75, W0=4.0, tau0=320.0,
-    eps_s=0.05, k=0.15, D=0.1, Omega=0.55, g=1e-6, grad_eps=1e-6,
+    eps_s=0.05, k=0.15, D=0.1, Omega=0.55, g=1e-6, grad_eps=1e-3,
     grad_eps_at=1e-2, s_e=1.0, s_eps=1.0,
 )
 SEED_RADIUS = 6.0
