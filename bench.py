@@ -145,7 +145,7 @@ side = {side if side else 0}
 if not side:
     o = make(256); t = time.perf_counter(); o.step(2); dt = (time.perf_counter() - t) / 2
     rate = 256 * 256 / dt
-    side = int(min(1024, max(128, (rate * {target_s} / max({steps_hint}, 1)) ** 0.5)) // 32 * 32)
+    side = int(min(2048, max(128, (rate * {target_s} / max({steps_hint}, 1)) ** 0.5)) // 32 * 32)
 o = make(side)
 o.step(1)
 t = time.perf_counter(); o.step({steps_hint}); dt = time.perf_counter() - t
@@ -192,6 +192,9 @@ def main() -> None:
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--precision", default="fp32", choices=("fp32", "fp64"))
     ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--variant", type=int, default=None, help="step kernel traversal")
+    ap.add_argument("--chunk", type=int, default=None, help="rows per y-march tile / tile a")
+    ap.add_argument("--tile-b", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -226,6 +229,8 @@ def main() -> None:
     sim = pf.Simulation([(lay.nx, lay.ny)], lay.params, args.precision,
                         stream=stream.cuda_stream)
     sim.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
+    if args.variant is not None:
+        sim.set_step_config(args.variant, args.chunk or 64, args.tile_b)
     sites = lay.nx * lay.ny
     sim.step(args.warmup)
     sim.sync()
@@ -295,7 +300,7 @@ def main() -> None:
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(steps_hint=20, target_s=20.0)
+        cpu = cpu_oracle_sample(steps_hint=40, target_s=20.0)
 
     if rank == 0:
         line = {
@@ -310,6 +315,7 @@ def main() -> None:
                        "l2": f"inputs {2 * 39 * sites * (4 if args.precision == 'fp32' else 8) / 1e9:.1f} GB "
                              "> L2 (no flush)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "step_config": list(sim.step_config()),
             "clocks": clk,
         }
         print(json.dumps(line))

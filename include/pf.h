@@ -169,6 +169,16 @@ pf_status pf_set_fields(pf_handle *h, int dom, const double *fields6, const doub
  * waiting.  Errors: STATE (no init), CUDA. */
 pf_status pf_step(pf_handle *h, int n_steps);
 
+/* Traversal of the step kernel (same arithmetic, results identical to
+ * rounding order): variant 0 = 2-D tiles of a x b sites (a a multiple of 32,
+ * a*b <= 256); variant 1 = column strips of 128 sites marched along y in
+ * tiles of a rows (b ignored; the default, a = 48).  Synchronises the stream
+ * and rebuilds the tile table.  Errors: BAD_ARG. */
+pf_status pf_set_step_config(pf_handle *h, int variant, int a, int b);
+
+/* Current traversal: out[0] variant, out[1] a, out[2] b. */
+pf_status pf_get_step_config(const pf_handle *h, int out[3]);
+
 /* Copy the fields of the last step of domain dom to host_out (FP64,
  * popcount(mask) planes of nx*ny, in bit order).  n is the capacity of
  * host_out in doubles.  Synchronises the stream. */

@@ -35,7 +35,9 @@ struct pf_handle {
   long long plane_stride = 0;
   size_t elem = 4;          // bytes per stored value
   size_t celem = 4;         // bytes per compute value
-  int tx = 32, ty = 8;      // step tile
+  int variant = STEP_YMARCH;  // step kernel traversal
+  int tx = 32, ty = 8;      // tile of the 2-D variant
+  int chunk = 48;           // rows per tile of the y-march variant (tuned at 4096^2)
   int ntiles = 0;
   int grid = 0;
   void* state[2] = {nullptr, nullptr};
@@ -210,8 +212,10 @@ static pf_status upload_tables(pf_handle* h) {
   std::vector<int> tile_dom;
   for (size_t d = 0; d < h->ddesc.size(); ++d) {
     DomDesc& dd = h->ddesc[d];
-    dd.tiles_x = (dd.nx + h->tx - 1) / h->tx;
-    const int tiles_y = (dd.ny + h->ty - 1) / h->ty;
+    const int tw = h->variant == STEP_YMARCH ? YM_W : h->tx;
+    const int th = h->variant == STEP_YMARCH ? h->chunk : h->ty;
+    dd.tiles_x = (dd.nx + tw - 1) / tw;
+    const int tiles_y = (dd.ny + th - 1) / th;
     dd.tile0 = (int)tile_dom.size();
     for (int t = 0; t < dd.tiles_x * tiles_y; ++t) tile_dom.push_back((int)d);
   }
@@ -491,12 +495,39 @@ static pf_status step_t(pf_handle* h, bool write_fields) {
   a.doms = h->d_doms;
   a.tile_dom = h->d_tile_dom;
   a.ntiles = h->ntiles;
+  a.chunk = h->chunk;
   a.fields = write_fields ? fields_ptr<R>(h) : nullptr;
   a.kp = make_kparams<R>(h->p);
-  PF_CUDA(h, launch_step<S, R>(a, h->tx, h->ty, h->grid, h->stream));
+  PF_CUDA(h, launch_step<S, R>(a, h->variant, h->tx, h->ty, h->grid, h->stream));
   h->launches++;
   h->cur ^= 1;
   h->steps++;
+  return PF_OK;
+}
+
+extern "C" pf_status pf_set_step_config(pf_handle* h, int variant, int a, int b) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (variant == STEP_TILE) {
+    if (a < 1 || b < 1 || a * b > 256 || a % 32 != 0)
+      return fail(h, PF_ERR_BAD_ARG, "tile variant needs tx a multiple of 32 and tx*ty <= 256");
+    h->tx = a;
+    h->ty = b;
+  } else if (variant == STEP_YMARCH) {
+    if (a < 1 || a > 65536) return fail(h, PF_ERR_BAD_ARG, "y-march chunk must be in [1, 65536]");
+    h->chunk = a;
+  } else {
+    return fail(h, PF_ERR_BAD_ARG, "unknown step variant");
+  }
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->variant = variant;
+  return upload_tables(h);
+}
+
+extern "C" pf_status pf_get_step_config(const pf_handle* h, int out[3]) {
+  if (!h || !out) return PF_ERR_BAD_ARG;
+  out[0] = h->variant;
+  out[1] = h->variant == STEP_YMARCH ? h->chunk : h->tx;
+  out[2] = h->variant == STEP_YMARCH ? 0 : h->ty;
   return PF_OK;
 }
 

@@ -13,6 +13,11 @@ constexpr int NDIAG = 12;            // entries of pf_diag
 constexpr int REDUCE_BLOCKS = 1024;  // blocks of the first reduction pass
 constexpr int MAX_GRAINS = 256;      // grain ids are uint8
 
+// Step kernel variants (same arithmetic, different traversal).
+enum StepVariant : int { STEP_TILE = 0, STEP_YMARCH = 1 };
+constexpr int YM_W = 128;            // interior columns of a y-march strip
+constexpr int YM_THREADS = YM_W + 32;  // + one warp whose lanes 0, 1 own the halo columns
+
 template <typename S, typename R>
 struct StepArgs {
   const S* __restrict__ in;     // state copy read this step
@@ -23,6 +28,7 @@ struct StepArgs {
   const DomDesc* __restrict__ doms;
   const int* __restrict__ tile_dom;     // domain of each tile
   int ntiles;
+  int chunk;                    // rows per y-march tile
   R* fields;                    // 8 field planes, or nullptr
   KParams<R> kp;
 };
@@ -63,7 +69,8 @@ struct ReduceArgs {
 };
 
 template <typename S, typename R>
-cudaError_t launch_step(const StepArgs<S, R>& a, int tx, int ty, int grid, cudaStream_t st);
+cudaError_t launch_step(const StepArgs<S, R>& a, int variant, int tx, int ty, int grid,
+                        cudaStream_t st);
 template <typename S, typename R>
 cudaError_t launch_init_spec(const InitArgs<S, R>& a, cudaStream_t st);
 template <typename S, typename R>

@@ -86,6 +86,8 @@ def lib() -> ctypes.CDLL:
     L.pf_get_state.argtypes = [P, I, D, S]
     L.pf_set_state.argtypes = [P, I, D, S]
     L.pf_reduce.argtypes = [P, I, ctypes.POINTER(pf_probe), ctypes.POINTER(pf_diag)]
+    L.pf_set_step_config.argtypes = [P, I, I, I]
+    L.pf_get_step_config.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
     L.pf_sync.argtypes = [P]
     L.pf_steps_taken.argtypes = [P]
     L.pf_steps_taken.restype = ctypes.c_longlong
@@ -96,7 +98,8 @@ def lib() -> ctypes.CDLL:
     L.pf_last_error.restype = ctypes.c_char_p
     for name in ("pf_params_default", "pf_params_derived", "pf_create", "pf_init_fields",
                  "pf_set_fields", "pf_step", "pf_get_fields", "pf_get_state", "pf_set_state",
-                 "pf_reduce", "pf_sync", "pf_destroy"):
+                 "pf_reduce", "pf_sync", "pf_destroy", "pf_set_step_config",
+                 "pf_get_step_config"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -216,6 +219,15 @@ class Simulation:
     # -- stepping --------------------------------------------------------------
     def step(self, n: int = 1) -> None:
         _check(lib().pf_step(self.h, int(n)), self.h)
+
+    def set_step_config(self, variant: int, a: int, b: int = 0) -> None:
+        """variant 0: 2-D tiles a x b; variant 1: y-march strips, a rows per tile."""
+        _check(lib().pf_set_step_config(self.h, int(variant), int(a), int(b)), self.h)
+
+    def step_config(self) -> tuple[int, int, int]:
+        out = (ctypes.c_int * 3)()
+        _check(lib().pf_get_step_config(self.h, out), self.h)
+        return tuple(out)
 
     def sync(self) -> None:
         _check(lib().pf_sync(self.h), self.h)
