@@ -204,6 +204,33 @@ long long pf_steps_taken(const pf_handle *h);
  * kernels only). */
 long long pf_launch_count(const pf_handle *h);
 
+/* FP64 diagnostics of a field stack without allocating any device memory.
+ * The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory, e.g. a plugin inside a host framework that owns the
+ * device-memory budget and only hands out buffers it allocated, or a loop
+ * that must not call cudaMalloc / cudaFree because they can synchronise the
+ * whole device.
+ *  fields       device pointer to field planes laid out as in a handle:
+ *               plane k (phi, psi, C, U, p, vx, vy, mu_phi in that order)
+ *               starts at fields + k * plane_stride elements; the lattice
+ *               (nx x ny, row-major) starts at element `offset` of each plane.
+ *               Only phi, psi, C, p, vx, vy are read.  Owned by the caller.
+ *  fields_fp64  nonzero: planes hold double; zero: float.
+ *  probe        Laplace probe or NULL; out: host pf_diag (same quantities and
+ *               order as pf_reduce).  cuda_stream: stream for the work.
+ * Scratch: a fixed file-scope device array of 1.5 MiB (16384 records of 12
+ * doubles) that every GPU loading the library holds until exit; lattices of
+ * more than 67,108,864 sites are rejected with PF_ERR_BAD_ARG.  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Calls share the array:
+ * calls that overlap on the GPU (other streams, other threads) race.  Nothing
+ * in it needs clearing, since every record read is written by the same call.
+ * Synchronises the stream.  Errors (message in pf_last_error(NULL)): BAD_ARG,
+ * CUDA. */
+pf_status pf_reduce_noalloc(const void *fields, int fields_fp64, long long plane_stride,
+                            long long offset, int nx, int ny, const pf_probe *probe,
+                            pf_diag *out, void *cuda_stream);
+
 /* Release every resource of the handle (NULL is ignored). */
 pf_status pf_destroy(pf_handle *h);
 

@@ -58,6 +58,8 @@ struct pf_handle {
 
 static std::string g_create_err;
 
+void pf::set_global_error(const std::string& msg) { g_create_err = msg; }
+
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------

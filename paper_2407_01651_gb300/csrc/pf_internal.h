@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "pf_model.cuh"
@@ -87,5 +88,8 @@ cudaError_t launch_fields_to_f64(const R* fields, long long ps, long long off, l
 template <typename R>
 cudaError_t launch_reduce(const ReduceArgs<R>& a, double* partial, double* out,
                           cudaStream_t st);
+
+// Message returned by pf_last_error(NULL) (entry points without a handle).
+void set_global_error(const std::string& msg);
 
 }  // namespace pf

@@ -88,6 +88,8 @@ def lib() -> ctypes.CDLL:
     L.pf_reduce.argtypes = [P, I, ctypes.POINTER(pf_probe), ctypes.POINTER(pf_diag)]
     L.pf_set_step_config.argtypes = [P, I, I, I]
     L.pf_get_step_config.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
+    L.pf_reduce_noalloc.argtypes = [P, I, ctypes.c_longlong, ctypes.c_longlong, I, I,
+                                    ctypes.POINTER(pf_probe), ctypes.POINTER(pf_diag), P]
     L.pf_sync.argtypes = [P]
     L.pf_steps_taken.argtypes = [P]
     L.pf_steps_taken.restype = ctypes.c_longlong
@@ -99,7 +101,7 @@ def lib() -> ctypes.CDLL:
     for name in ("pf_params_default", "pf_params_derived", "pf_create", "pf_init_fields",
                  "pf_set_fields", "pf_step", "pf_get_fields", "pf_get_state", "pf_set_state",
                  "pf_reduce", "pf_sync", "pf_destroy", "pf_set_step_config",
-                 "pf_get_step_config"):
+                 "pf_get_step_config", "pf_reduce_noalloc"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -134,6 +136,19 @@ def pf_params_derived(d: dict) -> tuple[float, float, float]:
     out = np.zeros(3)
     _check(lib().pf_params_derived(ctypes.byref(params_from_dict(d)), _dp(out)))
     return tuple(out.tolist())
+
+
+def pf_reduce_noalloc(fields_ptr: int, fp64: bool, plane_stride: int, offset: int, nx: int,
+                      ny: int, probe=None, stream: int = 0) -> dict:
+    """FP64 diagnostics of caller-owned device field planes; the library
+    allocates no device memory for it (see include/pf.h)."""
+    d = pf_diag()
+    pr = pf_probe(*probe) if probe is not None else None
+    _check(lib().pf_reduce_noalloc(ctypes.c_void_p(fields_ptr), int(bool(fp64)),
+                                   int(plane_stride), int(offset), int(nx), int(ny),
+                                   ctypes.byref(pr) if pr else None, ctypes.byref(d),
+                                   ctypes.c_void_p(stream)))
+    return {k: getattr(d, k) for k in _DIAG_FIELDS}
 
 
 def torch_allocator(device=None):
