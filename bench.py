@@ -31,9 +31,13 @@ METRIC = "coupled-step MLUPS at 4096² and % of HBM roofline; adjoint/forward ti
 # Algorithmic HBM bytes per lattice update of the step kernel: 39 planes read
 # + 39 planes written (9 NS, 9 CAC, 5+5+1 dendrite, 5 solute, 5 lagged scalars)
 # and 1 byte of grain id read.
-BYTES_PER_LU = {"fp32": 39 * 4 * 2 + 1, "fp64": 39 * 8 * 2 + 1}
-DTYPE = {"fp32": "f32", "fp64": "f64"}
-KERNEL_SOURCES = ("paper_2407_01651_gb300/csrc/pf_kernels.cu",
+# The 16-bit forms store the 33 population planes in 2 bytes and keep 7 lagged
+# scalars (with psi) in FP32.
+BYTES_PER_LU = {"fp32": 39 * 4 * 2 + 1, "fp64": 39 * 8 * 2 + 1,
+                "fp16": (33 * 2 + 7 * 4) * 2 + 1, "bf16": (33 * 2 + 7 * 4) * 2 + 1}
+DTYPE = {"fp32": "f32", "fp64": "f64", "fp16": "f16-storage/f32", "bf16": "bf16-storage/f32"}
+KERNEL_SOURCES = ("paper_2407_01651_gb300/csrc/pf_step.cu",
+                  "paper_2407_01651_gb300/csrc/pf_device.cuh",
                   "paper_2407_01651_gb300/csrc/pf_model.cuh")
 
 
@@ -190,7 +194,7 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--precision", default="fp32", choices=("fp32", "fp64"))
+    ap.add_argument("--precision", default="fp32", choices=("fp32", "fp64", "fp16", "bf16"))
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--variant", type=int, default=None, help="step kernel traversal")
     ap.add_argument("--chunk", type=int, default=None, help="rows per y-march tile / tile a")
@@ -312,7 +316,7 @@ def main() -> None:
                                    "theta~U[0,pi/2)), 128 bubbles (R~U[8,40]), seed 2",
                        "lattice": [lay.nx, lay.ny], "precision": args.precision,
                        "parallelism": f"replicas x{world}",
-                       "l2": f"inputs {2 * 39 * sites * (4 if args.precision == 'fp32' else 8) / 1e9:.1f} GB "
+                       "l2": f"inputs {(bpl - 1) * sites / 1e9:.1f} GB read+written per step "
                              "> L2 (no flush)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "step_config": list(sim.step_config()),

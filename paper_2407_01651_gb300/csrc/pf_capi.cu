@@ -17,6 +17,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "../../include/pf.h"
 #include "pf_internal.h"
 
@@ -40,7 +43,8 @@ struct pf_handle {
   int chunk = 48;           // rows per tile of the y-march variant (tuned at 4096^2)
   int ntiles = 0;
   int grid = 0;
-  void* state[2] = {nullptr, nullptr};
+  void* pop[2] = {nullptr, nullptr};   // population planes, storage type
+  void* aux[2] = {nullptr, nullptr};   // lagged-scalar planes, compute type
   int cur = 0;
   void* fields = nullptr;
   uint8_t* grain = nullptr;
@@ -63,6 +67,20 @@ void pf::set_global_error(const std::string& msg) { g_create_err = msg; }
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
+// Call f(S{}, R{}) with the storage and compute types of the handle.
+template <typename F>
+static pf_status dispatch(const pf_handle* h, F&& f) {
+  switch (h->prec) {
+    case PF_FP64: return f(double{}, double{});
+    case PF_FP32: return f(float{}, float{});
+    case PF_FP16_OFFSET: return f(__half{}, float{});
+    case PF_BF16_OFFSET: return f(__nv_bfloat16{}, float{});
+  }
+  return PF_ERR_BAD_ARG;
+}
+#define PF_TYPES(s_tag, r_tag)     \
+  using S = decltype(s_tag);       \
+  using R = decltype(r_tag);
 static pf_status fail(pf_handle* h, pf_status code, const std::string& msg) {
   if (h) h->err = msg;
   else g_create_err = msg;
@@ -197,7 +215,8 @@ extern "C" pf_status pf_params_derived(const pf_params* p, double out[3]) {
 // ---------------------------------------------------------------------------
 static void release(pf_handle* h) {
   if (!h) return;
-  for (void*& s : h->state) { dev_free(h, s); s = nullptr; }
+  for (void*& s : h->pop) { dev_free(h, s); s = nullptr; }
+  for (void*& s : h->aux) { dev_free(h, s); s = nullptr; }
   dev_free(h, h->fields);
   dev_free(h, h->grain);
   dev_free(h, h->grain_cs);
@@ -245,8 +264,8 @@ extern "C" pf_status pf_create(const pf_params* p, const pf_domain* doms, int n_
   pf_status st = check_params(p);
   if (st != PF_OK) return st;
   if (!doms || n_doms < 1) return fail(nullptr, PF_ERR_BAD_ARG, "need at least one domain");
-  if (prec != PF_FP64 && prec != PF_FP32)
-    return fail(nullptr, PF_ERR_BAD_ARG, "precision not supported by this build");
+  if (prec != PF_FP64 && prec != PF_FP32 && prec != PF_FP16_OFFSET && prec != PF_BF16_OFFSET)
+    return fail(nullptr, PF_ERR_BAD_ARG, "unknown precision");
   for (int d = 0; d < n_doms; ++d) {
     if (doms[d].nx < 4 || doms[d].ny < 4 || doms[d].nx > (1 << 16) || doms[d].ny > (1 << 16))
       return fail(nullptr, PF_ERR_BAD_ARG, "domain sizes must be in [4, 65536]");
@@ -263,7 +282,7 @@ extern "C" pf_status pf_create(const pf_params* p, const pf_domain* doms, int n_
   h->stream = (cudaStream_t)cuda_stream;
   if (alloc) { h->alloc = *alloc; h->has_alloc = true; }
   cudaGetDevice(&h->device);
-  h->elem = prec == PF_FP64 ? 8 : 4;
+  h->elem = prec == PF_FP64 ? 8 : (prec == PF_FP32 ? 4 : 2);
   h->celem = prec == PF_FP64 ? 8 : 4;
   h->doms.assign(doms, doms + n_doms);
   h->inited.assign(n_doms, 0);
@@ -292,8 +311,9 @@ extern "C" pf_status pf_create(const pf_params* p, const pf_domain* doms, int n_
     return code;
   };
   for (int c = 0; c < 2; ++c) {
-    h->state[c] = dev_alloc(h, ps * N_PLANES * h->elem);
-    if (!h->state[c]) return bail(PF_ERR_OOM, "state allocation failed");
+    h->pop[c] = dev_alloc(h, ps * N_POP * h->elem);
+    h->aux[c] = dev_alloc(h, ps * N_AUX * h->celem);
+    if (!h->pop[c] || !h->aux[c]) return bail(PF_ERR_OOM, "state allocation failed");
   }
   h->fields = dev_alloc(h, ps * N_FIELDS * h->celem);
   h->grain = (uint8_t*)dev_alloc(h, ps);
@@ -362,7 +382,8 @@ template <typename S, typename R>
 static pf_status init_spec_t(pf_handle* h, int dom, const pf_init_spec* spec, const double* d_s,
                              const double* d_b) {
   InitArgs<S, R> a{};
-  a.out = reinterpret_cast<S*>(h->state[h->cur]);
+  a.out = reinterpret_cast<S*>(h->pop[h->cur]);
+  a.aout = reinterpret_cast<R*>(h->aux[h->cur]);
   a.fields = fields_ptr<R>(h);
   a.grain = h->grain;
   a.plane_stride = h->plane_stride;
@@ -413,8 +434,10 @@ extern "C" pf_status pf_init_fields(pf_handle* h, int dom, const pf_init_spec* s
   if (!buf) return fail(h, PF_ERR_OOM, "init buffer allocation failed");
   if (ns) PF_CUDA(h, cudaMemcpyAsync(buf, spec->seeds, ns * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   if (nb) PF_CUDA(h, cudaMemcpyAsync(buf + ns, spec->bubbles, nb * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-  st = h->prec == PF_FP64 ? init_spec_t<double, double>(h, dom, spec, buf, buf + ns)
-                          : init_spec_t<float, float>(h, dom, spec, buf, buf + ns);
+  st = dispatch(h, [&](auto s_t, auto r_t) {
+    PF_TYPES(s_t, r_t);
+    return init_spec_t<S, R>(h, dom, spec, buf, buf + ns);
+  });
   cudaError_t e = cudaStreamSynchronize(h->stream);
   dev_free(h, buf);
   if (st != PF_OK) return st;
@@ -425,7 +448,8 @@ extern "C" pf_status pf_init_fields(pf_handle* h, int dom, const pf_init_spec* s
 template <typename S, typename R>
 static pf_status set_fields_t(pf_handle* h, int dom, const double* d_f6, const uint8_t* d_ids) {
   SetFieldsArgs<S, R> a{};
-  a.out = reinterpret_cast<S*>(h->state[h->cur]);
+  a.out = reinterpret_cast<S*>(h->pop[h->cur]);
+  a.aout = reinterpret_cast<R*>(h->aux[h->cur]);
   a.fields = fields_ptr<R>(h);
   a.grain = h->grain;
   a.plane_stride = h->plane_stride;
@@ -476,8 +500,10 @@ extern "C" pf_status pf_set_fields(pf_handle* h, int dom, const double* fields6,
     d_ids = reinterpret_cast<uint8_t*>(buf + 6 * nn);
     PF_CUDA(h, cudaMemcpyAsync(d_ids, ids.data(), nn, cudaMemcpyHostToDevice, h->stream));
   }
-  st = h->prec == PF_FP64 ? set_fields_t<double, double>(h, dom, buf, d_ids)
-                          : set_fields_t<float, float>(h, dom, buf, d_ids);
+  st = dispatch(h, [&](auto s_t, auto r_t) {
+    PF_TYPES(s_t, r_t);
+    return set_fields_t<S, R>(h, dom, buf, d_ids);
+  });
   if (st != PF_OK) return st;
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
   return finish_init(h, dom);
@@ -489,8 +515,10 @@ extern "C" pf_status pf_set_fields(pf_handle* h, int dom, const double* fields6,
 template <typename S, typename R>
 static pf_status step_t(pf_handle* h, bool write_fields) {
   StepArgs<S, R> a{};
-  a.in = reinterpret_cast<const S*>(h->state[h->cur]);
-  a.out = reinterpret_cast<S*>(h->state[h->cur ^ 1]);
+  a.in = reinterpret_cast<const S*>(h->pop[h->cur]);
+  a.out = reinterpret_cast<S*>(h->pop[h->cur ^ 1]);
+  a.ain = reinterpret_cast<const R*>(h->aux[h->cur]);
+  a.aout = reinterpret_cast<R*>(h->aux[h->cur ^ 1]);
   a.plane_stride = h->plane_stride;
   a.grain = h->grain;
   a.grain_cs = h->grain_cs;
@@ -540,8 +568,10 @@ extern "C" pf_status pf_step(pf_handle* h, int n_steps) {
     if (!d) return fail(h, PF_ERR_STATE, "every domain must be initialised before stepping");
   for (int t = 0; t < n_steps; ++t) {
     const bool last = t == n_steps - 1;
-    pf_status st = h->prec == PF_FP64 ? step_t<double, double>(h, last)
-                                      : step_t<float, float>(h, last);
+    pf_status st = dispatch(h, [&](auto s_t, auto r_t) {
+      PF_TYPES(s_t, r_t);
+      return step_t<S, R>(h, last);
+    });
     if (st != PF_OK) return st;
   }
   return PF_OK;
@@ -580,17 +610,19 @@ extern "C" pf_status pf_get_state(pf_handle* h, int dom, double* host_out, size_
     return fail(h, PF_ERR_BAD_ARG, "bad domain or output");
   const DomDesc& dd = h->ddesc[dom];
   const size_t nn = (size_t)dd.nx * dd.ny;
-  if (n < nn * N_PLANES) return fail(h, PF_ERR_BAD_ARG, "output buffer too small");
-  pf_status st = ensure_staging(h, nn * N_PLANES);
+  if (n < nn * N_PHYS) return fail(h, PF_ERR_BAD_ARG, "output buffer too small");
+  pf_status st = ensure_staging(h, nn * N_PHYS);
   if (st != PF_OK) return st;
-  if (h->prec == PF_FP64)
-    PF_CUDA(h, launch_state_to_f64<double>((const double*)h->state[h->cur], h->plane_stride,
-                                           dd.off, (long long)nn, N_PLANES, h->staging, h->stream));
-  else
-    PF_CUDA(h, launch_state_to_f64<float>((const float*)h->state[h->cur], h->plane_stride, dd.off,
-                                          (long long)nn, N_PLANES, h->staging, h->stream));
+  st = dispatch(h, [&](auto s_t, auto r_t) {
+    PF_TYPES(s_t, r_t);
+    PF_CUDA(h, launch_state_to_f64<S, R>((const S*)h->pop[h->cur], (const R*)h->aux[h->cur],
+                                         h->plane_stride, dd.off, (long long)nn, h->staging,
+                                         h->stream));
+    return PF_OK;
+  });
+  if (st != PF_OK) return st;
   h->launches++;
-  PF_CUDA(h, cudaMemcpyAsync(host_out, h->staging, nn * N_PLANES * sizeof(double),
+  PF_CUDA(h, cudaMemcpyAsync(host_out, h->staging, nn * N_PHYS * sizeof(double),
                              cudaMemcpyDeviceToHost, h->stream));
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
   return PF_OK;
@@ -602,17 +634,19 @@ extern "C" pf_status pf_set_state(pf_handle* h, int dom, const double* host_in, 
     return fail(h, PF_ERR_BAD_ARG, "bad domain or input");
   const DomDesc& dd = h->ddesc[dom];
   const size_t nn = (size_t)dd.nx * dd.ny;
-  if (n != nn * N_PLANES) return fail(h, PF_ERR_BAD_ARG, "input must hold 39 planes of nx*ny");
-  pf_status st = ensure_staging(h, nn * N_PLANES);
+  if (n != nn * N_PHYS) return fail(h, PF_ERR_BAD_ARG, "input must hold 39 planes of nx*ny");
+  pf_status st = ensure_staging(h, nn * N_PHYS);
   if (st != PF_OK) return st;
-  PF_CUDA(h, cudaMemcpyAsync(h->staging, host_in, nn * N_PLANES * sizeof(double),
+  PF_CUDA(h, cudaMemcpyAsync(h->staging, host_in, nn * N_PHYS * sizeof(double),
                              cudaMemcpyHostToDevice, h->stream));
-  if (h->prec == PF_FP64)
-    PF_CUDA(h, launch_state_from_f64<double>((double*)h->state[h->cur], h->plane_stride, dd.off,
-                                             (long long)nn, N_PLANES, h->staging, h->stream));
-  else
-    PF_CUDA(h, launch_state_from_f64<float>((float*)h->state[h->cur], h->plane_stride, dd.off,
-                                            (long long)nn, N_PLANES, h->staging, h->stream));
+  st = dispatch(h, [&](auto s_t, auto r_t) {
+    PF_TYPES(s_t, r_t);
+    PF_CUDA(h, launch_state_from_f64<S, R>((S*)h->pop[h->cur], (R*)h->aux[h->cur],
+                                           h->plane_stride, dd.off, (long long)nn, h->staging,
+                                           h->stream));
+    return PF_OK;
+  });
+  if (st != PF_OK) return st;
   h->launches++;
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
   h->inited[dom] = 1;

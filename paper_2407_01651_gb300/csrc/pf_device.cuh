@@ -1,0 +1,107 @@
+// pf_device.cuh -- small device helpers shared by the kernel translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "pf_internal.h"
+#include "pf_model.cuh"
+
+namespace pf {
+
+// Storage codecs.  FP64 / FP32 store populations as they are.  The 16-bit
+// forms store each population as its offset from w_i M_o, with M_o the lagged
+// moment of the site that holds it (phi for h, psi for g, C for s; kept in
+// FP32), so that only the small non-rest part is rounded to 16 bits; the NS
+// populations, which are small already, are stored scaled by 2^12.
+template <typename S>
+struct Codec {
+  static constexpr bool kOffset = false;
+  template <typename R>
+  __device__ __forceinline__ static R dec(S v) { return static_cast<R>(v); }
+  template <typename R>
+  __device__ __forceinline__ static S enc(R v) { return static_cast<S>(v); }
+};
+template <>
+struct Codec<__half> {
+  static constexpr bool kOffset = true;
+  template <typename R>
+  __device__ __forceinline__ static R dec(__half v) { return __half2float(v); }
+  template <typename R>
+  __device__ __forceinline__ static __half enc(R v) { return __float2half_rn(v); }
+};
+template <>
+struct Codec<__nv_bfloat16> {
+  static constexpr bool kOffset = true;
+  template <typename R>
+  __device__ __forceinline__ static R dec(__nv_bfloat16 v) { return __bfloat162float(v); }
+  template <typename R>
+  __device__ __forceinline__ static __nv_bfloat16 enc(R v) { return __float2bfloat16_rn(v); }
+};
+constexpr float kNSScale = 4096.0f;      // NS populations x 2^12 in the 16-bit forms
+constexpr float kNSInvScale = 1.0f / 4096.0f;
+
+
+template <typename R, typename S>
+__device__ __forceinline__ R ld(const S* __restrict__ p, long long i) {
+  return Codec<S>::template dec<R>(__ldg(p + i));
+}
+
+template <typename S, typename R>
+__device__ __forceinline__ void st(S* __restrict__ p, long long i, R v) {
+  p[i] = Codec<S>::template enc<R>(v);
+}
+
+// Weights of the D2Q9 / D2Q5 lattices in the compute type.
+template <typename R>
+__device__ __forceinline__ R w9(int i) {
+  return i == 0 ? R(4.0 / 9.0) : (i < 5 ? R(1.0 / 9.0) : R(1.0 / 36.0));
+}
+template <typename R>
+__device__ __forceinline__ R w5(int i) {
+  return i == 0 ? R(1.0 / 3.0) : R(1.0 / 6.0);
+}
+
+// Physical value <-> stored value of one population.  kind: 0 NS (scaled in
+// the 16-bit forms), 1 offset from w M_o (the caller passes w M_o).
+template <typename S, typename R>
+__device__ __forceinline__ R pop_ns(const S* __restrict__ p, long long i) {
+  if constexpr (Codec<S>::kOffset) return ld<R>(p, i) * R(kNSInvScale);
+  else return ld<R>(p, i);
+}
+template <typename S, typename R>
+__device__ __forceinline__ void st_ns(S* __restrict__ p, long long i, R v) {
+  if constexpr (Codec<S>::kOffset) st(p, i, v * R(kNSScale));
+  else st(p, i, v);
+}
+template <typename S, typename R>
+__device__ __forceinline__ R pop_off(const S* __restrict__ p, long long i, R wm) {
+  if constexpr (Codec<S>::kOffset) return wm + ld<R>(p, i);
+  else return ld<R>(p, i);
+}
+template <typename S, typename R>
+__device__ __forceinline__ void st_off(S* __restrict__ p, long long i, R v, R wm) {
+  if constexpr (Codec<S>::kOffset) st(p, i, v - wm);
+  else st(p, i, v);
+}
+
+// Compensated (Neumaier) accumulation: the zeroth moments phi, psi, C are sums
+// of 5 or 9 populations of similar size; in FP32 plain summation loses up to
+// ~8 ulp(phi), which the W_phi^2-weighted Laplacian in mu_phi then amplifies.
+template <typename R>
+struct CSum {
+  R s = R(0), c = R(0);
+  __device__ __forceinline__ void add(R v) {
+    const R t = s + v;
+    c += (fabs(s) >= fabs(v)) ? ((s - t) + v) : ((v - t) + s);
+    s = t;
+  }
+  __device__ __forceinline__ R value() const { return s + c; }
+};
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+  a %= n;
+  return a < 0 ? a + n : a;
+}
+
+}  // namespace pf

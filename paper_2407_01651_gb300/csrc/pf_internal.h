@@ -21,8 +21,10 @@ constexpr int YM_THREADS = YM_W + 32;  // + one warp whose lanes 0, 1 own the ha
 
 template <typename S, typename R>
 struct StepArgs {
-  const S* __restrict__ in;     // state copy read this step
-  S* __restrict__ out;          // state copy written this step
+  const S* __restrict__ in;     // population planes read this step
+  S* __restrict__ out;          // population planes written this step
+  const R* __restrict__ ain;    // lagged-scalar planes read this step
+  R* __restrict__ aout;         // lagged-scalar planes written this step
   long long plane_stride;       // sites per plane (all domains, padded)
   const uint8_t* __restrict__ grain;    // grain id per site
   const double2* __restrict__ grain_cs; // (cos, sin) of each grain angle
@@ -37,6 +39,7 @@ struct StepArgs {
 template <typename S, typename R>
 struct InitArgs {
   S* out;
+  R* aout;
   R* fields;
   uint8_t* grain;
   long long plane_stride;
@@ -51,6 +54,7 @@ struct InitArgs {
 template <typename S, typename R>
 struct SetFieldsArgs {
   S* out;
+  R* aout;
   R* fields;
   uint8_t* grain;
   long long plane_stride;
@@ -76,11 +80,11 @@ template <typename S, typename R>
 cudaError_t launch_init_spec(const InitArgs<S, R>& a, cudaStream_t st);
 template <typename S, typename R>
 cudaError_t launch_set_fields(const SetFieldsArgs<S, R>& a, cudaStream_t st);
-template <typename S>
-cudaError_t launch_state_to_f64(const S* in, long long ps, long long off, long long n,
-                                int nplanes, double* out, cudaStream_t st);
-template <typename S>
-cudaError_t launch_state_from_f64(S* out, long long ps, long long off, long long n, int nplanes,
+template <typename S, typename R>
+cudaError_t launch_state_to_f64(const S* pin, const R* ain, long long ps, long long off,
+                                long long n, double* out, cudaStream_t st);
+template <typename S, typename R>
+cudaError_t launch_state_from_f64(S* pout, R* aout, long long ps, long long off, long long n,
                                   const double* in, cudaStream_t st);
 template <typename R>
 cudaError_t launch_fields_to_f64(const R* fields, long long ps, long long off, long long n,

@@ -1,463 +1,28 @@
-// pf_kernels.cu -- sm_103a kernels of one coupled lattice Boltzmann step of the
-// gas-liquid-dendrite phase-field model (arXiv 2407.01651):
-//   k_step      fused stream + moments + stencils + sources + four collisions
+// pf_kernels.cu -- sm_103a support kernels of the coupled lattice Boltzmann step
+// of the gas-liquid-dendrite phase-field model (arXiv 2407.01651); the step
+// itself is in pf_step.cu:
 //   k_init_spec initial fields from seeds and bubbles, equilibrium populations
 //   k_set_fields equilibrium populations from given macroscopic fields
 //   k_reduce*   FP64 diagnostics (conservation, centroid, Laplace probe)
 //   k_*_state   raw state to / from FP64
 //
 // Layout: structure of arrays, one plane per population / scalar, x fastest,
-// periodic domains concatenated in every plane.  The step is a pull scheme with
-// two state copies (ping-pong).  One CTA owns a TX x TY tile; it first builds
-// phi, psi and the lagged velocity on the tile plus a one-site halo in shared
-// memory (the stencils of step 3 need them at the 8 neighbours), then each
-// thread streams, collides and stores its own site.
+// periodic domains concatenated in every plane.
 #include "pf_internal.h"
-#include "pf_model.cuh"
+#include "pf_device.cuh"
 
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 
 namespace pf {
 
-template <typename R, typename S>
-__device__ __forceinline__ R ld(const S* __restrict__ p, long long i) {
-  return static_cast<R>(__ldg(p + i));
-}
-
-template <typename S, typename R>
-__device__ __forceinline__ void st(S* __restrict__ p, long long i, R v) {
-  p[i] = static_cast<S>(v);
-}
-
-// Compensated (Neumaier) accumulation: the zeroth moments phi, psi, C are sums
-// of 5 or 9 populations of similar size; in FP32 plain summation loses up to
-// ~8 ulp(phi), which the W_phi^2-weighted Laplacian in mu_phi then amplifies.
-template <typename R>
-struct CSum {
-  R s = R(0), c = R(0);
-  __device__ __forceinline__ void add(R v) {
-    const R t = s + v;
-    c += (fabs(s) >= fabs(v)) ? ((s - t) + v) : ((v - t) + s);
-    s = t;
-  }
-  __device__ __forceinline__ R value() const { return s + c; }
-};
-
-__device__ __forceinline__ int wrapi(int a, int n) {
-  a %= n;
-  return a < 0 ? a + n : a;
-}
-
-// Source sites of the pull for the 9 D2Q9 directions at (x, y):
-// src[i] = (x - cx_i, y - cy_i), periodic.
-struct Src9 {
-  long long s[9];
-};
-
-__device__ __forceinline__ Src9 sources(const DomDesc& d, int x, int y) {
-  const int nx = d.nx, ny = d.ny;
-  const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-  const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-  const long long r0 = d.off + (long long)y * nx, rm = d.off + (long long)ym * nx,
-                  rp = d.off + (long long)yp * nx;
-  Src9 o;
-  o.s[0] = r0 + x; o.s[1] = r0 + xm; o.s[2] = rm + x; o.s[3] = r0 + xp; o.s[4] = rp + x;
-  o.s[5] = rm + xm; o.s[6] = rm + xp; o.s[7] = rp + xp; o.s[8] = rp + xm;
-  return o;
-}
-
-// Streamed CAC populations h and dendrite populations g (with the a_s^2 time
-// stretch g = g_pre + r_src (g_post,src - g_pre)) at (x, y); returns phi, psi
-// (compensated sums) and psi_o = sum g_pre (psi of the previous step).
-template <typename S, typename R>
-__device__ __forceinline__ void pull_hg(const StepArgs<S, R>& a, const Src9& src, R h[9],
-                                        R g[5], R& phi, R& psi, R& psio) {
-  const long long ps = a.plane_stride;
-  CSum<R> sh;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    h[i] = ld<R>(a.in + (P_H + i) * ps, src.s[i]);
-    sh.add(h[i]);
-  }
-  phi = sh.value();
-  CSum<R> sg;
-  R po = R(0);
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const R gold = ld<R>(a.in + (P_GPRE + i) * ps, src.s[0]);
-    const R gpo = ld<R>(a.in + (P_GPOST + i) * ps, src.s[i]);
-    const R rr = ld<R>(a.in + P_RR * ps, src.s[i]);
-    g[i] = gold + (gpo - gold) * rr;
-    sg.add(g[i]);
-    po += gold;
-  }
-  psi = sg.value();
-  psio = po;
-}
-
-// Three rows of a shared-memory field around a site: row y-1, y, y+1.
-template <typename R>
-struct Rows3 {
-  const R* m;
-  const R* c;
-  const R* p;
-};
-
-// Per-site inputs that do not feed the neighbours' stencils: streamed NS and
-// solute populations and the lagged scalars of the site.
-template <typename R>
-struct SiteIn {
-  R f[9], s[5];
-  R phio, Co, Qo;
-  uint8_t gid;
-};
-
-template <typename S, typename R>
-__device__ __forceinline__ void load_site(const StepArgs<S, R>& a, const Src9& src,
-                                          SiteIn<R>& in) {
-  const long long ps = a.plane_stride;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) in.f[i] = ld<R>(a.in + (P_F + i) * ps, src.s[i]);
-#pragma unroll
-  for (int i = 0; i < 5; ++i) in.s[i] = ld<R>(a.in + (P_S + i) * ps, src.s[i]);
-  in.phio = ld<R>(a.in + P_PHIO * ps, src.s[0]);
-  in.Co = ld<R>(a.in + P_CO * ps, src.s[0]);
-  in.Qo = ld<R>(a.in + P_QO * ps, src.s[0]);
-  in.gid = a.grain[src.s[0]];
-}
-
-// Everything after streaming at one site: stencils, interface geometry,
-// forces, sources, the four collisions and the stores.  h, g: streamed
-// populations of the site; `in` holds the rest of its inputs.
-template <typename S, typename R>
-__device__ __forceinline__ void site_update(const StepArgs<S, R>& a, const DomDesc& d,
-                                            const Src9& src, const SiteIn<R>& in,
-                                            const R (&h_in)[9], const R (&g_in)[5], R psio,
-                                            Rows3<R> SP, Rows3<R> SS, Rows3<R> SVX,
-                                            Rows3<R> SVY, int c) {
-  const long long ps = a.plane_stride;
-  const KParams<R>& kp = a.kp;
-  const long long site = src.s[0];
-  R f[9], h[9], g[5], s[5];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    f[i] = in.f[i];
-    h[i] = h_in[i];
-  }
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    s[i] = in.s[i];
-    g[i] = g_in[i];
-  }
-  const R phio = in.phio, Co = in.Co, Qo = in.Qo;
-  const uint8_t gid = in.gid;
-
-  const R phi = SP.c[c], psi = SS.c[c];
-  const R vxo = SVX.c[c], vyo = SVY.c[c];
-  R C;
-  {
-    CSum<R> cs;
-#pragma unroll
-    for (int i = 0; i < 5; ++i) cs.add(s[i]);
-    C = cs.value();
-  }
-
-  // ---- isotropic stencils, on differences from the centre value so that
-  // FP32 keeps the bits of the (small) neighbour differences ----
-  const R w1 = R(1.0 / 9.0), w2 = R(1.0 / 36.0);
-  auto grad = [&](const Rows3<R>& X, R& gx, R& gy) {
-    const R X0 = X.c[c];
-    const R e = X.c[c + 1] - X0, w = X.c[c - 1] - X0, n = X.p[c] - X0, so = X.m[c] - X0;
-    const R ne = X.p[c + 1] - X0, nw = X.p[c - 1] - X0;
-    const R sw = X.m[c - 1] - X0, se = X.m[c + 1] - X0;
-    gx = R(3) * (w1 * (e - w) + w2 * ((ne - sw) + (se - nw)));
-    gy = R(3) * (w1 * (n - so) + w2 * ((ne - sw) + (nw - se)));
-  };
-  R gpx, gpy, gsx, gsy, dvxx, dvxy, dvyx, dvyy;
-  grad(SP, gpx, gpy);
-  grad(SS, gsx, gsy);
-  grad(SVX, dvxx, dvxy);
-  grad(SVY, dvyx, dvyy);
-  R lphi;
-  {
-    const R X0 = SP.c[c];
-    const R ax = ((SP.c[c + 1] - X0) + (SP.c[c - 1] - X0)) + ((SP.p[c] - X0) + (SP.m[c] - X0));
-    const R dg = ((SP.p[c + 1] - X0) + (SP.m[c - 1] - X0)) +
-                 ((SP.p[c - 1] - X0) + (SP.m[c + 1] - X0));
-    lphi = R(6) * (w1 * ax + w2 * dg);
-  }
-
-  // ---- gas-liquid interface, forces ----
-  const R rho = kp.rho_g + phi * kp.drho;
-  const R grx = kp.drho * gpx, gry = kp.drho * gpy;
-  const R igm = R(1) / sqrt(gpx * gpx + gpy * gpy + kp.ge2);
-  const R nfx = gpx * igm, nfy = gpy * igm;
-  const R opsi = R(1) + psi, ophi = R(1) - phi;
-  const R mu = kp.two_bphi * phi * ophi * (R(1) - R(2) * phi) - kp.two_bint * ophi * opsi * opsi -
-               kp.Wphi2 * lphi;
-  const R Fsx = kp.fs_coef * mu * gpx, Fsy = kp.fs_coef * mu * gpy;
-  const R Fby = -(rho - static_cast<R>(d.rho_bar)) * kp.g;
-  const R aphi = kp.kappa * phi * ophi;
-  const R Dx = kp.M_phi * (gpx - aphi * nfx), Dy = kp.M_phi * (gpy - aphi * nfy);
-  const R divD = (phi - phio) + vxo * gpx + vyo * gpy;
-  const R Fmx = kp.drho * (divD * vxo + Dx * dvxx + Dy * dvxy);
-  const R Fmy = kp.drho * (divD * vyo + Dx * dvyx + Dy * dvyy);
-
-  // ---- NS moments, drag, pressure ----
-  const R jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
-  const R jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
-  const R sum_nz = f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
-  const R Fpx = Fsx + Fmx, Fpy = Fsy + Fby + Fmy;
-  const R irho = R(1) / rho;
-  const R vsx = (jx + R(0.5) * Fpx) * irho, vsy = (jy + R(0.5) * Fpy) * irho;
-  const R chi = R(0.5) * opsi;
-  const R vx = (R(1) - chi) * vsx, vy = (R(1) - chi) * vsy;
-  const R Fx = Fpx - R(2) * chi * rho * vsx, Fy = Fpy - R(2) * chi * rho * vsy;
-  const R v2 = vx * vx + vy * vy;
-  // c_s^2/(1-w0) = 3/5; w0/(2 c_s^2) = 2/3
-  const R p = R(0.6) * (sum_nz + R(0.5) * (vx * grx + vy * gry) - R(2.0 / 3.0) * rho * v2);
-
-  // ---- dendrite geometry in the grain frame ----
-  const double2 cs = a.grain_cs[d.grain_off + gid];
-  const R ct = static_cast<R>(cs.x), sn = static_cast<R>(cs.y);
-  const R eps = static_cast<R>(d.eps_s);
-  const R gxr = ct * gsx + sn * gsy, gyr = -sn * gsx + ct * gsy;
-  const R gm2 = gsx * gsx + gsy * gsy;
-  const R smag = sqrt(gm2 + kp.ge2);
-  const R ism = R(1) / smag;
-  const R nxr = -gxr * ism, nyr = -gyr * ism;
-  const R nx2 = nxr * nxr, ny2 = nyr * nyr;
-  const R n2 = nx2 + ny2;
-  const R s4 = nx2 * nx2 + ny2 * ny2;
-  const R as = R(1) + eps * (R(4) * s4 - R(3) * n2 * n2);
-  const R iso = s4 + R(0.75) * n2 * (R(1) - n2);
-  const R pre = R(-16) * eps * as * smag;
-  const R Nxr = pre * nxr * (nx2 - iso), Nyr = pre * nyr * (ny2 - iso);
-  const R Nx = ct * Nxr - sn * Nyr, Ny = sn * Nxr + ct * Nyr;
-  const R as2 = as * as;
-  const R ias2 = R(1) / as2;
-
-  // ---- solute and dendrite sources ----
-  const R omk = R(1) - kp.k;
-  const R A = R(1) + kp.k - omk * psi;
-  const R iA = R(1) / A;
-  const R U = (R(2) * C * iA - R(1)) / omk;
-  const R omp2 = R(1) - psi * psi;
-  const R Q = kp.four_bpsi * psi * omp2 - kp.two_bint * ophi * ophi * opsi -
-              kp.lam * omp2 * omp2 * (kp.theta + kp.Mcinf * U);
-  const R dpsi = psi - psio;
-  const R at = -kp.a_at * kp.W0 * as * (R(1) + omk * U) * dpsi / sqrt(gm2 + kp.gat2);
-  const R qf = R(0.5) * (R(1) - psi);
-  const R jv = kp.D * qf * C * kp.kappa * ophi;
-
-  // ---- collisions ----
-  collide_ns(f, p, rho, vx, vy, Fx, Fy, grx, gry, kp);
-  {
-    const R G1x = (phi * vx - phio * vxo) + R(1.0 / 3.0) * aphi * nfx;
-    const R G1y = (phi * vy - phio * vyo) + R(1.0 / 3.0) * aphi * nfy;
-    collide_cac(h, phi, vx, vy, G1x, G1y, kp);
-  }
-  R gpost[5];
-  {
-    const R Fs = (Q + R(0.5) * (Q - Qo)) * kp.inv_tau0;
-    const R s1 = R(1) / (kp.c_s1 * as2 + R(0.5));
-#pragma unroll
-    for (int i = 0; i < 5; ++i) gpost[i] = g[i];
-    collide_q5(gpost, psi + Fs, s1, R(0), R(0), R(-1.0 / 3.0) * Nx * ias2,
-               R(-1.0 / 3.0) * Ny * ias2);
-  }
-  {
-    const R E = R(2) * omk * kp.D * qf * C * iA * iA;
-    const R jex = C * vx - E * gsx + omk * (at * gsx + jv * nfx);
-    const R jey = C * vy - E * gsy + omk * (at * gsy + jv * nfy);
-    const R DC = R(2) * kp.D * qf * iA;
-    const R sc = R(1) / (R(3) * DC + R(0.5));
-    collide_q5(s, C, sc, jex, jey, C * vx - Co * vxo, C * vy - Co * vyo);
-  }
-
-  // ---- store ----
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    st(a.out + (P_F + i) * ps, site, f[i]);
-    st(a.out + (P_H + i) * ps, site, h[i]);
-  }
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    st(a.out + (P_GPRE + i) * ps, site, g[i]);
-    st(a.out + (P_GPOST + i) * ps, site, gpost[i]);
-    st(a.out + (P_S + i) * ps, site, s[i]);
-  }
-  st(a.out + P_RR * ps, site, ias2);
-  st(a.out + P_PHIO * ps, site, phi);
-  st(a.out + P_CO * ps, site, C);
-  st(a.out + P_VXO * ps, site, vx);
-  st(a.out + P_VYO * ps, site, vy);
-  st(a.out + P_QO * ps, site, Q);
-  if (a.fields) {
-    R* fl = a.fields;
-    fl[FLD_PHI * ps + site] = phi;
-    fl[FLD_PSI * ps + site] = psi;
-    fl[FLD_C * ps + site] = C;
-    fl[FLD_U * ps + site] = U;
-    fl[FLD_P * ps + site] = p;
-    fl[FLD_VX * ps + site] = vx;
-    fl[FLD_VY * ps + site] = vy;
-    fl[FLD_MU * ps + site] = mu;
-  }
-}
-
-// Variant A: 2-D tiles.  The CTA builds phi, psi and the lagged velocity on
-// its TX x TY tile plus a one-site halo in shared memory, then each thread
-// streams, collides and stores its own site.
-template <typename S, typename R>
-__global__ void __launch_bounds__(256) k_step_tile(StepArgs<S, R> a) {
-  extern __shared__ unsigned char smem_raw[];
-  const int TX = blockDim.x, TY = blockDim.y;
-  const int SW = TX + 2, SH = TY + 2;
-  R* sphi = reinterpret_cast<R*>(smem_raw);
-  R* spsi = sphi + SW * SH;
-  R* svx = spsi + SW * SH;
-  R* svy = svx + SW * SH;
-  const int tid = threadIdx.y * TX + threadIdx.x;
-  const int nthr = TX * TY;
-  const long long ps = a.plane_stride;
-
-  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-    const DomDesc d = a.doms[a.tile_dom[tile]];
-    const int lt = tile - d.tile0;
-    const int x0 = (lt % d.tiles_x) * TX, y0 = (lt / d.tiles_x) * TY;
-    const int nx = d.nx, ny = d.ny;
-
-    for (int i = tid; i < SW * SH; i += nthr) {
-      const int gx = wrapi(x0 + (i % SW) - 1, nx), gy = wrapi(y0 + (i / SW) - 1, ny);
-      R h[9], g[5], phi, psi, po;
-      pull_hg(a, sources(d, gx, gy), h, g, phi, psi, po);
-      sphi[i] = phi;
-      spsi[i] = psi;
-      const long long site = d.off + (long long)gy * nx + gx;
-      svx[i] = ld<R>(a.in + P_VXO * ps, site);
-      svy[i] = ld<R>(a.in + P_VYO * ps, site);
-    }
-    __syncthreads();
-
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    if (x < nx && y < ny) {
-      const Src9 src = sources(d, x, y);
-      R h[9], g[5], phi, psi, po;
-      pull_hg(a, src, h, g, phi, psi, po);
-      const int r = threadIdx.y + 1;
-      auto rows = [&](const R* X) { return Rows3<R>{X + (r - 1) * SW, X + r * SW, X + (r + 1) * SW}; };
-      SiteIn<R> in;
-      load_site(a, src, in);
-      site_update(a, d, src, in, h, g, po, rows(sphi), rows(spsi), rows(svx), rows(svy),
-                  threadIdx.x + 1);
-    }
-    __syncthreads();
-  }
-}
-
-// Variant B: column strips marched along y.  Each of the YM_W interior
-// threads owns one column and walks down the rows of its tile (YM_W columns x
-// `chunk` rows); lanes 0 and 1 of one extra warp own the two halo columns.  At
-// row j every thread streams h and g of row j+1 (one-row lookahead kept in
-// registers) and puts phi, psi and the lagged velocity of row j+1 into a
-// 4-slot shared-memory ring; after one barrier the interior threads update row
-// j with the stencils read from slots j-1, j, j+1.  Every population is loaded
-// from memory once (plus 2 halo columns per YM_W).
-template <typename S, typename R>
-__global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 3 : 2) k_step_ymarch(StepArgs<S, R> a) {
-  constexpr int RW = YM_W + 2;
-  __shared__ R ring[4][4][RW];  // [phi, psi, vx_o, vy_o][slot][column]
-  const int t = threadIdx.x;
-  const long long ps = a.plane_stride;
-
-  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-    const DomDesc d = a.doms[a.tile_dom[tile]];
-    const int lt = tile - d.tile0;
-    const int nx = d.nx, ny = d.ny;
-    const int x0 = (lt % d.tiles_x) * YM_W;
-    const int ya = (lt / d.tiles_x) * a.chunk;
-    const int yb = min(ya + a.chunk, ny);
-    const int w = min(YM_W, nx - x0);
-    bool interior = false, active = false;
-    int col = 0, sc = 0;
-    if (t < YM_W) {
-      interior = active = t < w;
-      col = x0 + t;
-      sc = t + 1;
-    } else if (t == YM_W) {
-      active = true;
-      col = x0 == 0 ? nx - 1 : x0 - 1;
-      sc = 0;
-    } else if (t == YM_W + 1) {
-      active = true;
-      col = x0 + w >= nx ? x0 + w - nx : x0 + w;
-      sc = w + 1;
-    }
-
-    R hC[9], gC[5], poC = R(0);
-    // rows ya-1 and ya into the ring (warm-up)
-    for (int k = 0; k < 2; ++k) {
-      const int yy = wrapi(ya - 1 + k, ny);
-      const int slot = (ya - 1 + k) & 3;
-      if (active) {
-        const Src9 src = sources(d, col, yy);
-        R h[9], g[5], phi, psi, po;
-        pull_hg(a, src, h, g, phi, psi, po);
-        ring[0][slot][sc] = phi;
-        ring[1][slot][sc] = psi;
-        ring[2][slot][sc] = ld<R>(a.in + P_VXO * ps, src.s[0]);
-        ring[3][slot][sc] = ld<R>(a.in + P_VYO * ps, src.s[0]);
-        if (k == 1) {
-#pragma unroll
-          for (int i = 0; i < 9; ++i) hC[i] = h[i];
-#pragma unroll
-          for (int i = 0; i < 5; ++i) gC[i] = g[i];
-          poC = po;
-        }
-      }
-    }
-
-    for (int j = ya; j < yb; ++j) {
-      // inputs of row j that no neighbour needs: issued before the barrier so
-      // their latency overlaps the lookahead of row j+1
-      SiteIn<R> in;
-      const Src9 srcj = sources(d, col, j);
-      if (interior) load_site(a, srcj, in);
-      R hL[9], gL[5], poL = R(0);
-      if (active) {
-        const int yn = j + 1 >= ny ? j + 1 - ny : j + 1;
-        const Src9 src = sources(d, col, yn);
-        R phi, psi;
-        pull_hg(a, src, hL, gL, phi, psi, poL);
-        const int slot = (j + 1) & 3;
-        ring[0][slot][sc] = phi;
-        ring[1][slot][sc] = psi;
-        ring[2][slot][sc] = ld<R>(a.in + P_VXO * ps, src.s[0]);
-        ring[3][slot][sc] = ld<R>(a.in + P_VYO * ps, src.s[0]);
-      }
-      __syncthreads();
-      if (interior) {
-        const int m = (j - 1) & 3, c0 = j & 3, pp = (j + 1) & 3;
-        auto rows = [&](int f) { return Rows3<R>{ring[f][m], ring[f][c0], ring[f][pp]}; };
-        site_update(a, d, srcj, in, hC, gC, poC, rows(0), rows(1), rows(2), rows(3), sc);
-      }
-#pragma unroll
-      for (int i = 0; i < 9; ++i) hC[i] = hL[i];
-#pragma unroll
-      for (int i = 0; i < 5; ++i) gC[i] = gL[i];
-      poC = poL;
-    }
-    __syncthreads();
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Initialisation
 // ---------------------------------------------------------------------------
+// Minimum-image offset; fmod(d, L) == d whenever |d| < L, so it is only taken
+// for offsets of a whole period or more.
 __device__ __forceinline__ double min_image(double d, double L) {
-  d = fmod(d, L);
+  if (d <= -L || d >= L) d = fmod(d, L);
   if (d < -0.5 * L) d += L;
   if (d >= 0.5 * L) d -= L;
   return d;
@@ -465,38 +30,40 @@ __device__ __forceinline__ double min_image(double d, double L) {
 
 // Write the equilibrium state and the fields of one site.
 template <typename S, typename R>
-__device__ void write_equilibrium(S* out, R* fields, long long ps, long long site, double phi_d,
-                                  double psi_d, double C_d, double vx_d, double vy_d,
-                                  double p_d, const KParams<R>& kp) {
+__device__ void write_equilibrium(S* out, R* aout, R* fields, long long ps, long long site,
+                                  double phi_d, double psi_d, double C_d, double vx_d,
+                                  double vy_d, double p_d, const KParams<R>& kp) {
   const R phi = static_cast<R>(phi_d), psi = static_cast<R>(psi_d), C = static_cast<R>(C_d);
   const R vx = static_cast<R>(vx_d), vy = static_cast<R>(vy_d), p = static_cast<R>(p_d);
   const R rho = kp.rho_g + phi * kp.drho;
   R f[9];
   feq_ns(p, rho, vx, vy, f);
-  for (int i = 0; i < 9; ++i) st(out + (P_F + i) * ps, site, f[i]);
-  // CAC h_eq = w_i phi (1 + 3 c.v)
-  const R w[9] = {R(4.0 / 9.0), R(1.0 / 9.0), R(1.0 / 9.0), R(1.0 / 9.0), R(1.0 / 9.0),
-                  R(1.0 / 36.0), R(1.0 / 36.0), R(1.0 / 36.0), R(1.0 / 36.0)};
+  // CAC h_eq = w_i phi (1 + 3 c.v); dendrite w_i psi; solute w_i C (1 + 3 c.v)
   const R cu[9] = {R(0), vx, vy, -vx, -vy, vx + vy, -vx + vy, -vx - vy, vx - vy};
-  for (int i = 0; i < 9; ++i) st(out + (P_H + i) * ps, site, w[i] * phi * (R(1) + R(3) * cu[i]));
-  const R w5[5] = {R(1.0 / 3.0), R(1.0 / 6.0), R(1.0 / 6.0), R(1.0 / 6.0), R(1.0 / 6.0)};
-  for (int i = 0; i < 5; ++i) {
-    st(out + (P_GPRE + i) * ps, site, w5[i] * psi);
-    st(out + (P_GPOST + i) * ps, site, w5[i] * psi);
-    st(out + (P_S + i) * ps, site, w5[i] * C + w5[i] * R(3) * C * cu[i]);
+  for (int i = 0; i < 9; ++i) {
+    st_ns<S, R>(out + (P_F + i) * ps, site, f[i]);
+    st_off<S, R>(out + (P_H + i) * ps, site, w9<R>(i) * phi * (R(1) + R(3) * cu[i]),
+                 w9<R>(i) * phi);
   }
-  st(out + P_RR * ps, site, R(1));
+  for (int i = 0; i < 5; ++i) {
+    st_off<S, R>(out + (P_GPRE + i) * ps, site, w5<R>(i) * psi, w5<R>(i) * psi);
+    st_off<S, R>(out + (P_GPOST + i) * ps, site, w5<R>(i) * psi, w5<R>(i) * psi);
+    st_off<S, R>(out + (P_S + i) * ps, site, w5<R>(i) * C * (R(1) + R(3) * cu[i]),
+                 w5<R>(i) * C);
+  }
   const R omk = R(1) - kp.k;
   const R U = (R(2) * C / (R(1) + kp.k - omk * psi) - R(1)) / omk;
   const R omp2 = R(1) - psi * psi;
   const R ophi = R(1) - phi;
   const R Q = kp.four_bpsi * psi * omp2 - kp.two_bint * ophi * ophi * (R(1) + psi) -
               kp.lam * omp2 * omp2 * (kp.theta + kp.Mcinf * U);
-  st(out + P_PHIO * ps, site, phi);
-  st(out + P_CO * ps, site, C);
-  st(out + P_VXO * ps, site, vx);
-  st(out + P_VYO * ps, site, vy);
-  st(out + P_QO * ps, site, Q);
+  aout[A_RR * ps + site] = R(1);
+  aout[A_PHIO * ps + site] = phi;
+  aout[A_CO * ps + site] = C;
+  aout[A_VXO * ps + site] = vx;
+  aout[A_VYO * ps + site] = vy;
+  aout[A_QO * ps + site] = Q;
+  aout[A_PSIO * ps + site] = psi;
   if (fields) {
     fields[FLD_PHI * ps + site] = phi;
     fields[FLD_PSI * ps + site] = psi;
@@ -516,13 +83,18 @@ __global__ void k_init_spec(InitArgs<S, R> a) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(i % d.nx), y = (int)(i / d.nx);
+    // tanh of an argument beyond +-30 is exactly +-1 in FP64, so objects that
+    // far away are not evaluated (identical result, ~100x fewer tanh).
+    const double seed_far = a.R_s + 30.0 * a.W0 / a.sq2bpsi;
     double psi = -1.0, best = 0.0;
     int gid = 0;
     for (int s = 0; s < a.n_seeds; ++s) {
       const double dx = min_image((double)x - a.seeds[3 * s], (double)d.nx);
       const double dy = min_image((double)y - a.seeds[3 * s + 1], (double)d.ny);
       const double r2 = dx * dx + dy * dy;
-      const double v = tanh(a.sq2bpsi * (a.R_s - sqrt(r2)) / a.W0);
+      const double v = r2 > seed_far * seed_far
+                           ? -1.0
+                           : tanh(a.sq2bpsi * (a.R_s - sqrt(r2)) / a.W0);
       if (s == 0 || v > psi) psi = v;
       if (s == 0 || r2 < best) {
         best = r2;
@@ -533,16 +105,19 @@ __global__ void k_init_spec(InitArgs<S, R> a) {
     for (int b = 0; b < a.n_bub; ++b) {
       const double dx = min_image((double)x - a.bubbles[3 * b], (double)d.nx);
       const double dy = min_image((double)y - a.bubbles[3 * b + 1], (double)d.ny);
+      const double r2 = dx * dx + dy * dy;
+      const double far = a.bubbles[3 * b + 2] + 60.0 * a.Wphi / a.sq2bphi;
       const double v =
-          0.5 + 0.5 * tanh(a.sq2bphi * (sqrt(dx * dx + dy * dy) - a.bubbles[3 * b + 2]) /
-                           (2.0 * a.Wphi));
+          r2 > far * far ? 1.0
+                         : 0.5 + 0.5 * tanh(a.sq2bphi * (sqrt(r2) - a.bubbles[3 * b + 2]) /
+                                            (2.0 * a.Wphi));
       if (b == 0 || v < phi) phi = v;
     }
     const double C = phi * (1.0 - (1.0 - a.k) * 0.5 * (1.0 + psi));
     const long long site = d.off + i;
     a.grain[site] = (uint8_t)gid;
-    write_equilibrium<S, R>(a.out, a.fields, a.plane_stride, site, phi, psi, C, 0.0, 0.0, 0.0,
-                            a.kp);
+    write_equilibrium<S, R>(a.out, a.aout, a.fields, a.plane_stride, site, phi, psi, C, 0.0,
+                            0.0, 0.0, a.kp);
   }
 }
 
@@ -554,8 +129,8 @@ __global__ void k_set_fields(SetFieldsArgs<S, R> a) {
        i += (long long)gridDim.x * blockDim.x) {
     const long long site = d.off + i;
     const double* F = a.f6;
-    write_equilibrium<S, R>(a.out, a.fields, a.plane_stride, site, F[i], F[n + i], F[2 * n + i],
-                            F[3 * n + i], F[4 * n + i], F[5 * n + i], a.kp);
+    write_equilibrium<S, R>(a.out, a.aout, a.fields, a.plane_stride, site, F[i], F[n + i],
+                            F[2 * n + i], F[3 * n + i], F[4 * n + i], F[5 * n + i], a.kp);
     a.grain[site] = a.grain_ids ? a.grain_ids[i] : (uint8_t)0;
   }
 }
@@ -563,25 +138,62 @@ __global__ void k_set_fields(SetFieldsArgs<S, R> a) {
 // ---------------------------------------------------------------------------
 // Raw state / fields conversion to and from FP64.
 // ---------------------------------------------------------------------------
-template <typename S>
-__global__ void k_state_to_f64(const S* __restrict__ in, long long ps, long long off,
-                               long long n, int nplanes, double* __restrict__ out) {
-  const long long tot = n * nplanes;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i / n, j = i % n;
-    out[i] = static_cast<double>(in[p * ps + off + j]);
+// Raw state of one site <-> the 39 physical planes (f, h, g_pre, g_post, r,
+// s, phi, C, vx, vy, Q_psi), decoding / encoding the storage form.  In the
+// offset forms a population stored at site x is relative to the lagged
+// moment of x itself.
+template <typename S, typename R>
+__global__ void k_state_to_f64(const S* __restrict__ pin, const R* __restrict__ ain, long long ps,
+                               long long off, long long n, double* __restrict__ out) {
+  constexpr bool offs = Codec<S>::kOffset;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x) {
+    const long long s = off + j;
+    const R phio = ain[A_PHIO * ps + s], Co = ain[A_CO * ps + s];
+    const R psio = offs ? ain[A_PSIO * ps + s] : R(0);
+    for (int i = 0; i < 9; ++i) {
+      out[(0 + i) * n + j] = (double)pop_ns<S, R>(pin + (P_F + i) * ps, s);
+      out[(9 + i) * n + j] = (double)pop_off<S, R>(pin + (P_H + i) * ps, s, w9<R>(i) * phio);
+    }
+    for (int i = 0; i < 5; ++i) {
+      out[(18 + i) * n + j] = (double)pop_off<S, R>(pin + (P_GPRE + i) * ps, s, w5<R>(i) * psio);
+      out[(23 + i) * n + j] = (double)pop_off<S, R>(pin + (P_GPOST + i) * ps, s, w5<R>(i) * psio);
+      out[(29 + i) * n + j] = (double)pop_off<S, R>(pin + (P_S + i) * ps, s, w5<R>(i) * Co);
+    }
+    out[28 * n + j] = (double)ain[A_RR * ps + s];
+    out[34 * n + j] = (double)phio;
+    out[35 * n + j] = (double)Co;
+    out[36 * n + j] = (double)ain[A_VXO * ps + s];
+    out[37 * n + j] = (double)ain[A_VYO * ps + s];
+    out[38 * n + j] = (double)ain[A_QO * ps + s];
   }
 }
 
-template <typename S>
-__global__ void k_state_from_f64(S* __restrict__ out, long long ps, long long off, long long n,
-                                 int nplanes, const double* __restrict__ in) {
-  const long long tot = n * nplanes;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i / n, j = i % n;
-    out[p * ps + off + j] = static_cast<S>(in[i]);
+template <typename S, typename R>
+__global__ void k_state_from_f64(S* __restrict__ pout, R* __restrict__ aout, long long ps,
+                                 long long off, long long n, const double* __restrict__ in) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x) {
+    const long long s = off + j;
+    const R phio = (R)in[34 * n + j], Co = (R)in[35 * n + j];
+    R psio = R(0);  // psi of the last step = sum of g_pre
+    for (int i = 0; i < 5; ++i) psio += (R)in[(18 + i) * n + j];
+    for (int i = 0; i < 9; ++i) {
+      st_ns<S, R>(pout + (P_F + i) * ps, s, (R)in[(0 + i) * n + j]);
+      st_off<S, R>(pout + (P_H + i) * ps, s, (R)in[(9 + i) * n + j], w9<R>(i) * phio);
+    }
+    for (int i = 0; i < 5; ++i) {
+      st_off<S, R>(pout + (P_GPRE + i) * ps, s, (R)in[(18 + i) * n + j], w5<R>(i) * psio);
+      st_off<S, R>(pout + (P_GPOST + i) * ps, s, (R)in[(23 + i) * n + j], w5<R>(i) * psio);
+      st_off<S, R>(pout + (P_S + i) * ps, s, (R)in[(29 + i) * n + j], w5<R>(i) * Co);
+    }
+    aout[A_RR * ps + s] = (R)in[28 * n + j];
+    aout[A_PHIO * ps + s] = phio;
+    aout[A_CO * ps + s] = Co;
+    aout[A_VXO * ps + s] = (R)in[36 * n + j];
+    aout[A_VYO * ps + s] = (R)in[37 * n + j];
+    aout[A_QO * ps + s] = (R)in[38 * n + j];
+    aout[A_PSIO * ps + s] = psio;
   }
 }
 
@@ -673,18 +285,6 @@ __global__ void k_reduce_final(const double* __restrict__ partial, int nblocks,
 // Host-side launchers (explicit instantiations for FP64 and FP32).
 // ---------------------------------------------------------------------------
 template <typename S, typename R>
-cudaError_t launch_step(const StepArgs<S, R>& a, int variant, int tx, int ty, int grid,
-                        cudaStream_t st) {
-  if (variant == STEP_YMARCH) {
-    k_step_ymarch<S, R><<<grid, YM_THREADS, 0, st>>>(a);
-  } else {
-    const size_t smem = 4 * (size_t)(tx + 2) * (ty + 2) * sizeof(R);
-    k_step_tile<S, R><<<grid, dim3(tx, ty), smem, st>>>(a);
-  }
-  return cudaGetLastError();
-}
-
-template <typename S, typename R>
 cudaError_t launch_init_spec(const InitArgs<S, R>& a, cudaStream_t st) {
   const long long n = (long long)a.dom.nx * a.dom.ny;
   const int grid = (int)((n + 255) / 256 < 65535 ? (n + 255) / 256 : 65535);
@@ -700,17 +300,17 @@ cudaError_t launch_set_fields(const SetFieldsArgs<S, R>& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <typename S>
-cudaError_t launch_state_to_f64(const S* in, long long ps, long long off, long long n,
-                                int nplanes, double* out, cudaStream_t st) {
-  k_state_to_f64<S><<<1024, 256, 0, st>>>(in, ps, off, n, nplanes, out);
+template <typename S, typename R>
+cudaError_t launch_state_to_f64(const S* pin, const R* ain, long long ps, long long off,
+                                long long n, double* out, cudaStream_t st) {
+  k_state_to_f64<S, R><<<1024, 256, 0, st>>>(pin, ain, ps, off, n, out);
   return cudaGetLastError();
 }
 
-template <typename S>
-cudaError_t launch_state_from_f64(S* out, long long ps, long long off, long long n, int nplanes,
+template <typename S, typename R>
+cudaError_t launch_state_from_f64(S* pout, R* aout, long long ps, long long off, long long n,
                                   const double* in, cudaStream_t st) {
-  k_state_from_f64<S><<<1024, 256, 0, st>>>(out, ps, off, n, nplanes, in);
+  k_state_from_f64<S, R><<<1024, 256, 0, st>>>(pout, aout, ps, off, n, in);
   return cudaGetLastError();
 }
 
@@ -730,22 +330,18 @@ cudaError_t launch_reduce(const ReduceArgs<R>& a, double* partial, double* out,
 }
 
 #define PF_INST(S, R)                                                                      \
-  template cudaError_t launch_step<S, R>(const StepArgs<S, R>&, int, int, int, int,         \
-                                         cudaStream_t);                                     \
   template cudaError_t launch_init_spec<S, R>(const InitArgs<S, R>&, cudaStream_t);          \
-  template cudaError_t launch_set_fields<S, R>(const SetFieldsArgs<S, R>&, cudaStream_t);
+  template cudaError_t launch_set_fields<S, R>(const SetFieldsArgs<S, R>&, cudaStream_t);    \
+  template cudaError_t launch_state_to_f64<S, R>(const S*, const R*, long long, long long,   \
+                                                 long long, double*, cudaStream_t);          \
+  template cudaError_t launch_state_from_f64<S, R>(S*, R*, long long, long long, long long,  \
+                                                   const double*, cudaStream_t);
 
 PF_INST(double, double)
 PF_INST(float, float)
+PF_INST(__half, float)
+PF_INST(__nv_bfloat16, float)
 
-template cudaError_t launch_state_to_f64<double>(const double*, long long, long long, long long,
-                                                 int, double*, cudaStream_t);
-template cudaError_t launch_state_to_f64<float>(const float*, long long, long long, long long,
-                                                int, double*, cudaStream_t);
-template cudaError_t launch_state_from_f64<double>(double*, long long, long long, long long, int,
-                                                   const double*, cudaStream_t);
-template cudaError_t launch_state_from_f64<float>(float*, long long, long long, long long, int,
-                                                  const double*, cudaStream_t);
 template cudaError_t launch_fields_to_f64<double>(const double*, long long, long long,
                                                   long long, uint32_t, double*, cudaStream_t);
 template cudaError_t launch_fields_to_f64<float>(const float*, long long, long long, long long,

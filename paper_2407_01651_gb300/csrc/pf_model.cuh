@@ -15,23 +15,34 @@
 namespace pf {
 
 // ---------------------------------------------------------------------------
-// State planes.  Each plane holds one value per site of every domain
-// (plane stride = total padded sites); domain d starts at DomDesc::off.
+// State planes.  Each plane holds one value per site of every domain (plane
+// stride = total padded sites); domain d starts at DomDesc::off.  Populations
+// live in one buffer of the storage type, the lagged scalars in another of
+// the compute type.
 // ---------------------------------------------------------------------------
-enum Plane : int {
+enum PopPlane : int {
   P_F = 0,        // NS populations f_0..f_8 (post-collision)
   P_H = 9,        // CAC populations h_0..h_8 (post-collision)
   P_GPRE = 18,    // dendrite populations before collision g_0..g_4
   P_GPOST = 23,   // dendrite populations after collision
-  P_RR = 28,      // 1 / a_s^2 of the last collision
-  P_S = 29,       // solute populations s_0..s_4 (post-collision)
-  P_PHIO = 34,    // phi of the last step
-  P_CO = 35,      // C of the last step
-  P_VXO = 36,     // vx of the last step
-  P_VYO = 37,     // vy of the last step
-  P_QO = 38,      // Q_psi of the last step
-  N_PLANES = 39
+  P_S = 28,       // solute populations s_0..s_4 (post-collision)
+  N_POP = 33
 };
+
+enum AuxPlane : int {
+  A_RR = 0,       // 1 / a_s^2 of the last collision
+  A_PHIO = 1,     // phi of the last step
+  A_CO = 2,       // C of the last step
+  A_VXO = 3,      // vx of the last step
+  A_VYO = 4,      // vy of the last step
+  A_QO = 5,       // Q_psi of the last step
+  A_PSIO = 6,     // psi of the last step (offset storage forms only)
+  N_AUX = 7
+};
+
+// Raw state exchanged with the host (pf_get_state / pf_set_state): 39 planes
+// f[9], h[9], g_pre[5], g_post[5], r, s[5], phi, C, vx, vy, Q_psi.
+constexpr int N_PHYS = 39;
 
 enum Field : int { FLD_PHI, FLD_PSI, FLD_C, FLD_U, FLD_P, FLD_VX, FLD_VY, FLD_MU, N_FIELDS };
 
