@@ -201,6 +201,8 @@ def main() -> None:
     ap.add_argument("--tile-b", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=2000)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -302,6 +304,34 @@ def main() -> None:
                "what": "pf_set_fields from pinned FP64 host fields, pf_step(K), "
                        "pf_get_fields to pinned FP64 host memory; host wall clock"}
 
+    # adjoint / forward cost on the differentiation workload (512^2, 4 seeds,
+    # 8 bubbles, FP32, checkpoint every 100 steps)
+    adj = None
+    if not args.no_adjoint and rank == 0:
+        lay4 = wl.cfg4_layout()
+        n_adj = args.adjoint_steps
+        s4 = pf.Simulation([(lay4.nx, lay4.ny)], lay4.params, "fp32", stream=stream.cuda_stream)
+        s4.init_fields(0, lay4.seeds, lay4.R_s, lay4.bubbles)
+        s4.step(20)
+        s4.sync()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        s4.step(n_adj)
+        e1.record(stream)
+        J, g = s4.adjoint_step(n_adj, 1.0, 1.0, 100)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        t_f = e0.elapsed_time(e1)
+        t_a = e1.elapsed_time(e2)
+        adj = {"workload": f"512x512, 4 seeds, 8 bubbles, FP32, {n_adj} steps, checkpoint every 100",
+               "forward_ms_per_step": t_f / n_adj,
+               "adjoint_call_ms_per_step": t_a / n_adj,
+               "ratio": (t_a - t_f) / t_f,
+               "ratio_def": "(pf_adjoint_step time - forward time) / forward time: the reverse "
+                            "sweep incl. recomputation over the forward",
+               "grad": g.tolist()}
+        s4.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(steps_hint=40, target_s=20.0)
@@ -320,6 +350,7 @@ def main() -> None:
                              "> L2 (no flush)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "step_config": list(sim.step_config()),
+            "adjoint": adj,
             "clocks": clk,
         }
         print(json.dumps(line))

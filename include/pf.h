@@ -194,6 +194,30 @@ pf_status pf_set_state(pf_handle *h, int dom, const double *host_in, size_t n);
  * be NULL.  Synchronises the stream.  Errors: BAD_ARG, CUDA. */
 pf_status pf_reduce(pf_handle *h, int dom, const pf_probe *probe, pf_diag *out);
 
+/* Final-state objective of the discrete adjoint:
+ *   J = w_solid * mean h(psi_T) + w_centroid * y_c(T) / L_y,
+ * with h(psi) = (1+psi)/2 the solid fraction and y_c = sum y (1-phi) /
+ * sum (1-phi) the bubble centroid height (rows).  The reverse sweep stores a
+ * checkpoint every `checkpoint_every` steps and recomputes the steps in
+ * between. */
+typedef struct pf_objective {
+  double w_solid;
+  double w_centroid;
+  int checkpoint_every;
+} pf_objective;
+
+/* Discrete adjoint of the coupled step (reverse mode, hand-written kernels):
+ * advances the handle n_steps from its current state exactly as pf_step would
+ * (the state afterwards is x_T), evaluates J(x_T) and sweeps back, returning
+ * *J_out (may be NULL) and grad_out = dJ/d(eps_s, Omega, sigma) of the whole
+ * discrete trajectory.  When the handle has not stepped since its
+ * initialisation, the Omega-dependence of the initial lagged Q_psi is
+ * included.  Single-domain handles, FP32 or FP64 storage.  Allocates a
+ * workspace of (n_steps/K + K) states plus adjoint planes on first use.
+ * Synchronises the stream.  Errors: BAD_ARG, STATE, OOM, CUDA. */
+pf_status pf_adjoint_step(pf_handle *h, int n_steps, const pf_objective *obj, double *J_out,
+                          double grad_out[3]);
+
 /* Wait for all enqueued work; reports deferred device errors. */
 pf_status pf_sync(pf_handle *h);
 

@@ -1,0 +1,357 @@
+// pf_adjoint.cu -- discrete adjoint of one coupled LB step (reverse mode), for
+// gradients of a final-state objective with respect to the anisotropy
+// strength eps_s, the undercooling Omega and the surface tension sigma.
+//
+// One reverse step maps lambda_{t+1} (the adjoint of the stored state after
+// step t+1) to lambda_t, given the state x_t:
+//   k_adj_local    per site: rebuild the step's inputs at the site from x_t
+//                  (pull, stencils from a shared-memory halo), run the
+//                  hand-written reverse of the site update (pf_local.cuh) and
+//                  store the adjoints of its inputs (43 planes); accumulate
+//                  the parameter adjoints per block.
+//   k_adj_stencil  transpose the isotropic stencils: adjoints of the phi,
+//                  psi and lagged-velocity fields (4 planes).
+//   k_adj_gather   transpose the streaming (a gather from x + c_i) and the
+//                  a_s^2 time stretch of the dendrite lattice: lambda_t.
+// Adjoint planes are in the compute precision.  The FP32 and FP64 storage
+// forms are supported.
+#include "pf_local.cuh"
+#include "pf_pull.cuh"
+
+namespace pf {
+
+namespace {
+
+__device__ constexpr int CX9[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__device__ constexpr int CY9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+template <typename R>
+__device__ __forceinline__ local::Coef<R> make_coef(const KParams<R>& kp, const DomDesc& d,
+                                                    double2 cs) {
+  local::Coef<R> c;
+  c.rho_g = kp.rho_g; c.drho = kp.drho; c.ge2 = kp.ge2; c.gat2 = kp.gat2; c.kappa = kp.kappa;
+  c.fs_coef = kp.fs_coef; c.Wphi2 = kp.Wphi2; c.M_phi = kp.M_phi; c.two_bphi = kp.two_bphi;
+  c.two_bint = kp.two_bint; c.four_bpsi = kp.four_bpsi; c.lam = kp.lam; c.theta = kp.theta;
+  c.Mcinf = kp.Mcinf; c.inv_tau0 = kp.inv_tau0; c.c_s1 = kp.c_s1; c.W0 = kp.W0; c.a_at = kp.a_at;
+  c.k = kp.k; c.D = kp.D; c.g = kp.g; c.s_e = kp.s_e; c.s_eps = kp.s_eps; c.s_q = kp.s_q;
+  c.s_nu = kp.s_nu; c.s_phi = kp.s_phi;
+  c.eps = static_cast<R>(d.eps_s);
+  c.ct = static_cast<R>(cs.x);
+  c.sn = static_cast<R>(cs.y);
+  c.rho_bar = static_cast<R>(d.rho_bar);
+  return c;
+}
+
+__device__ __forceinline__ long long site_at(const DomDesc& d, int x, int y) {
+  x = x < 0 ? x + d.nx : (x >= d.nx ? x - d.nx : x);
+  y = y < 0 ? y + d.ny : (y >= d.ny ? y - d.ny : y);
+  return d.off + (long long)y * d.nx + x;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+template <typename S, typename R>
+__global__ void __launch_bounds__(256) k_adj_local(AdjArgs<S, R> a) {
+  __shared__ R sphi[ADJ_TY + 2][ADJ_TX + 2], spsi[ADJ_TY + 2][ADJ_TX + 2];
+  __shared__ R svx[ADJ_TY + 2][ADJ_TX + 2], svy[ADJ_TY + 2][ADJ_TX + 2];
+  __shared__ R red[3][256];
+  const StepArgs<S, R>& st = a.step;
+  const DomDesc d = a.dom;
+  const long long ps = st.plane_stride;
+  const int tid = threadIdx.y * ADJ_TX + threadIdx.x;
+  const int tiles_x = (d.nx + ADJ_TX - 1) / ADJ_TX;
+  const int ntiles = tiles_x * ((d.ny + ADJ_TY - 1) / ADJ_TY);
+  R pe = R(0), po = R(0), psg = R(0);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int x0 = (tile % tiles_x) * ADJ_TX, y0 = (tile / tiles_x) * ADJ_TY;
+    for (int i = tid; i < (ADJ_TX + 2) * (ADJ_TY + 2); i += ADJ_TX * ADJ_TY) {
+      const int lx = i % (ADJ_TX + 2), ly = i / (ADJ_TX + 2);
+      int gx = x0 + lx - 1, gy = y0 + ly - 1;
+      gx = ((gx % d.nx) + d.nx) % d.nx;
+      gy = ((gy % d.ny) + d.ny) % d.ny;
+      R h[9], g[5], phi, psi, pso;
+      const Src9 src = sources(d, gx, gy);
+      pull_hg(st, src, h, g, phi, psi, pso);
+      sphi[ly][lx] = phi;
+      spsi[ly][lx] = psi;
+      svx[ly][lx] = ld<R>(st.ain + A_VXO * ps, src.s[0]);
+      svy[ly][lx] = ld<R>(st.ain + A_VYO * ps, src.s[0]);
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x < d.nx && y < d.ny) {
+      const Src9 src = sources(d, x, y);
+      local::In<R> in;
+      R phi, psi;
+      pull_hg(st, src, in.h, in.g, phi, psi, in.psio);
+      SiteIn<R> si;
+      load_site(st, src, si);
+      for (int i = 0; i < 9; ++i) in.f[i] = si.f[i];
+      for (int i = 0; i < 5; ++i) in.s[i] = si.s[i];
+      in.phio = si.phio;
+      in.Co = si.Co;
+      in.Qo = si.Qo;
+      const int cx = threadIdx.x + 1, cy = threadIdx.y + 1;
+      in.vxo = svx[cy][cx];
+      in.vyo = svy[cy][cx];
+      const R w1 = R(1.0 / 9.0), w2 = R(1.0 / 36.0);
+      auto grad = [&](R (*X)[ADJ_TX + 2], R& gx, R& gy) {
+        const R X0 = X[cy][cx];
+        const R e = X[cy][cx + 1] - X0, w = X[cy][cx - 1] - X0;
+        const R n = X[cy + 1][cx] - X0, so = X[cy - 1][cx] - X0;
+        const R ne = X[cy + 1][cx + 1] - X0, nw = X[cy + 1][cx - 1] - X0;
+        const R sw = X[cy - 1][cx - 1] - X0, se = X[cy - 1][cx + 1] - X0;
+        gx = R(3) * (w1 * (e - w) + w2 * ((ne - sw) + (se - nw)));
+        gy = R(3) * (w1 * (n - so) + w2 * ((ne - sw) + (nw - se)));
+      };
+      grad(sphi, in.gpx, in.gpy);
+      grad(spsi, in.gsx, in.gsy);
+      grad(svx, in.dvxx, in.dvxy);
+      grad(svy, in.dvyx, in.dvyy);
+      {
+        const R X0 = sphi[cy][cx];
+        const R ax = ((sphi[cy][cx + 1] - X0) + (sphi[cy][cx - 1] - X0)) +
+                     ((sphi[cy + 1][cx] - X0) + (sphi[cy - 1][cx] - X0));
+        const R dg = ((sphi[cy + 1][cx + 1] - X0) + (sphi[cy - 1][cx - 1] - X0)) +
+                     ((sphi[cy + 1][cx - 1] - X0) + (sphi[cy - 1][cx + 1] - X0));
+        in.lphi = R(6) * (w1 * ax + w2 * dg);
+      }
+      const local::Coef<R> c = make_coef(st.kp, d, st.grain_cs[d.grain_off + si.gid]);
+      // output adjoints of the site (39 physical planes)
+      const long long site = src.s[0];
+      const R* L = a.lam_in;
+      local::Out<R> ao;
+      for (int i = 0; i < 9; ++i) {
+        ao.f[i] = L[(0 + i) * ps + site];
+        ao.h[i] = L[(9 + i) * ps + site];
+      }
+      for (int i = 0; i < 5; ++i) {
+        ao.gpre[i] = L[(18 + i) * ps + site];
+        ao.gpost[i] = L[(23 + i) * ps + site];
+        ao.s[i] = L[(29 + i) * ps + site];
+      }
+      ao.rr = L[28 * ps + site];
+      ao.phi = L[34 * ps + site];
+      ao.C = L[35 * ps + site];
+      ao.vx = L[36 * ps + site];
+      ao.vy = L[37 * ps + site];
+      ao.Q = L[38 * ps + site];
+      ao.U = ao.p = ao.mu = R(0);
+      local::In<R> ai;
+      local::ParGrad<R> pg{R(0), R(0), R(0)};
+      local::reverse(in, c, static_cast<R>(a.dfs_dsigma), ao, ai, pg);
+      pe += pg.eps;
+      po += pg.Omega;
+      psg += pg.sigma;
+      R* A = a.ai;
+      for (int i = 0; i < 9; ++i) {
+        A[(AI_F + i) * ps + site] = ai.f[i];
+        A[(AI_H + i) * ps + site] = ai.h[i];
+      }
+      for (int i = 0; i < 5; ++i) {
+        A[(AI_G + i) * ps + site] = ai.g[i];
+        A[(AI_S + i) * ps + site] = ai.s[i];
+      }
+      A[AI_PSIO * ps + site] = ai.psio;
+      A[AI_GPX * ps + site] = ai.gpx;
+      A[AI_GPY * ps + site] = ai.gpy;
+      A[AI_LPHI * ps + site] = ai.lphi;
+      A[AI_GSX * ps + site] = ai.gsx;
+      A[AI_GSY * ps + site] = ai.gsy;
+      A[AI_DVXX * ps + site] = ai.dvxx;
+      A[AI_DVXY * ps + site] = ai.dvxy;
+      A[AI_DVYX * ps + site] = ai.dvyx;
+      A[AI_DVYY * ps + site] = ai.dvyy;
+      A[AI_PHIO * ps + site] = ai.phio;
+      A[AI_CO * ps + site] = ai.Co;
+      A[AI_QO * ps + site] = ai.Qo;
+      A[AI_VXO * ps + site] = ai.vxo;
+      A[AI_VYO * ps + site] = ai.vyo;
+    }
+    __syncthreads();
+  }
+  // block sum of the parameter adjoints, accumulated into this block's record
+  red[0][tid] = pe;
+  red[1][tid] = po;
+  red[2][tid] = psg;
+  __syncthreads();
+  for (int half = 128; half > 0; half >>= 1) {
+    if (tid < half)
+      for (int q = 0; q < 3; ++q) red[q][tid] += red[q][tid + half];
+    __syncthreads();
+  }
+  if (tid < 3) a.partial[blockIdx.x * 3 + tid] += static_cast<double>(red[tid][0]);
+}
+
+// Stencil transposes.  grad X(z) = 3 sum_j w_j c_j X(z + c_j) and
+// lap X(z) = 6 sum_{j>0} w_j (X(z + c_j) - X(z)) give
+//   adj X(x) += sum_j 3 w_j c_j . adj grad(x - c_j)
+//             + sum_{j>0} 6 w_j adj lap(x - c_j) - 6 (1 - w_0) adj lap(x).
+template <typename R>
+__global__ void k_adj_stencil(const R* __restrict__ ai, R* __restrict__ as, DomDesc d,
+                              long long ps) {
+  const long long n = (long long)d.nx * d.ny;
+  const R w[9] = {R(4.0 / 9.0), R(1.0 / 9.0), R(1.0 / 9.0), R(1.0 / 9.0), R(1.0 / 9.0),
+                  R(1.0 / 36.0), R(1.0 / 36.0), R(1.0 / 36.0), R(1.0 / 36.0)};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % d.nx), y = (int)(i / d.nx);
+    const long long site = d.off + i;
+    R aphi = R(-6) * (R(1) - w[0]) * ai[AI_LPHI * ps + site];
+    R apsi = R(0), avx = ai[AI_VXO * ps + site], avy = ai[AI_VYO * ps + site];
+    for (int j = 1; j < 9; ++j) {
+      const long long z = site_at(d, x - CX9[j], y - CY9[j]);
+      const R wx = R(3) * w[j] * R(CX9[j]), wy = R(3) * w[j] * R(CY9[j]);
+      aphi += wx * ai[AI_GPX * ps + z] + wy * ai[AI_GPY * ps + z] +
+              R(6) * w[j] * ai[AI_LPHI * ps + z];
+      apsi += wx * ai[AI_GSX * ps + z] + wy * ai[AI_GSY * ps + z];
+      avx += wx * ai[AI_DVXX * ps + z] + wy * ai[AI_DVXY * ps + z];
+      avy += wx * ai[AI_DVYX * ps + z] + wy * ai[AI_DVYY * ps + z];
+    }
+    as[0 * ps + site] = aphi;
+    as[1 * ps + site] = apsi;
+    as[2 * ps + site] = avx;
+    as[3 * ps + site] = avy;
+  }
+}
+
+// Streaming and time-stretch transposes: lambda_t.
+// g_i(x) = g_pre,i(x) + r(x - c_i) [g_post,i(x - c_i) - g_pre,i(x)] and
+// psi_o(x) = sum_i g_pre,i(x).
+template <typename S, typename R>
+__global__ void k_adj_gather(AdjArgs<S, R> a) {
+  const DomDesc d = a.dom;
+  const long long ps = a.step.plane_stride;
+  const long long n = (long long)d.nx * d.ny;
+  const R* A = a.ai;
+  const R* AS = a.as;
+  const S* P = a.step.in;
+  const R* X = a.step.ain;
+  R* L = a.lam_out;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % d.nx), y = (int)(i / d.nx);
+    const long long site = d.off + i;
+    for (int q = 0; q < 9; ++q) {
+      const long long t = site_at(d, x + CX9[q], y + CY9[q]);
+      L[(0 + q) * ps + site] = A[(AI_F + q) * ps + t];
+      L[(9 + q) * ps + site] = A[(AI_H + q) * ps + t] + AS[0 * ps + t];
+    }
+    const R rr_own = X[A_RR * ps + site];
+    R lrr = R(0);
+    const R apsio = A[AI_PSIO * ps + site];
+    for (int q = 0; q < 5; ++q) {
+      const long long t = site_at(d, x + CX9[q], y + CY9[q]);   // destination of q
+      const long long s = site_at(d, x - CX9[q], y - CY9[q]);   // source of q
+      L[(29 + q) * ps + site] = A[(AI_S + q) * ps + t];
+      const R ag_own = A[(AI_G + q) * ps + site] + AS[1 * ps + site];
+      const R ag_dst = A[(AI_G + q) * ps + t] + AS[1 * ps + t];
+      const R rr_src = X[A_RR * ps + s];
+      L[(18 + q) * ps + site] = ag_own * (R(1) - rr_src) + apsio;
+      L[(23 + q) * ps + site] = ag_dst * rr_own;
+      const R gq_own = ld<R>(P + (P_GPOST + q) * ps, site);
+      const R gp_dst = ld<R>(P + (P_GPRE + q) * ps, t);
+      lrr += ag_dst * (gq_own - gp_dst);
+    }
+    L[28 * ps + site] = lrr;
+    L[34 * ps + site] = A[AI_PHIO * ps + site];
+    L[35 * ps + site] = A[AI_CO * ps + site];
+    L[36 * ps + site] = AS[2 * ps + site];
+    L[37 * ps + site] = AS[3 * ps + site];
+    L[38 * ps + site] = A[AI_QO * ps + site];
+  }
+}
+
+// Adjoint of the final-state objective
+//   J = w_s mean h(psi_T) + w_c y_c(T) / L_y,  y_c = sum y (1 - phi) / sum (1 - phi),
+// with psi_T = sum g_pre and phi_T the stored lagged phi of x_T.
+template <typename R>
+__global__ void k_adj_objective(R* __restrict__ L, DomDesc d, long long ps, double w_s,
+                                double w_c, double yc, double gas) {
+  const long long n = (long long)d.nx * d.ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long site = d.off + i;
+    const double y = (double)(i / d.nx);
+    for (int q = 0; q < N_PHYS; ++q) L[q * ps + site] = R(0);
+    for (int q = 0; q < 5; ++q) L[(18 + q) * ps + site] = static_cast<R>(0.5 * w_s / (double)n);
+    L[34 * ps + site] = static_cast<R>(w_c * (yc - y) / (gas * (double)d.ny));
+  }
+}
+
+// Initial-condition term of d J / d Omega: the initial lagged Q_psi is
+// Q(phi0, psi0, U0), whose Omega-derivative is lambda' (1-psi0^2)^2 (1 + (1-k) U0)
+// (d theta_sys / d Omega = -1, d M c_inf / d Omega = -(1-k)).
+template <typename S, typename R>
+__global__ void k_adj_omega_init(const R* __restrict__ L, const S* __restrict__ P,
+                                 const R* __restrict__ X, DomDesc d, long long ps, double lam,
+                                 double k, double* __restrict__ partial) {
+  __shared__ double red[256];
+  const long long n = (long long)d.nx * d.ny;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long site = d.off + i;
+    double psi = 0.0;
+    for (int q = 0; q < 5; ++q) psi += (double)ld<R>(P + (P_GPRE + q) * ps, site);
+    const double C = (double)X[A_CO * ps + site];
+    const double U = (2.0 * C / (1.0 + k - (1.0 - k) * psi) - 1.0) / (1.0 - k);
+    const double om = 1.0 - psi * psi;
+    acc += (double)L[38 * ps + site] * lam * om * om * (1.0 + (1.0 - k) * U);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int half = blockDim.x / 2; half > 0; half >>= 1) {
+    if ((int)threadIdx.x < half) red[threadIdx.x] += red[threadIdx.x + half];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// ---------------------------------------------------------------------------
+template <typename S, typename R>
+cudaError_t launch_adjoint_step(const AdjArgs<S, R>& a, int grid, cudaStream_t st) {
+  k_adj_local<S, R><<<grid, dim3(ADJ_TX, ADJ_TY), 0, st>>>(a);
+  const long long n = (long long)a.dom.nx * a.dom.ny;
+  const int g2 = (int)std::min<long long>((n + 255) / 256, 4096);
+  k_adj_stencil<R><<<g2, 256, 0, st>>>(a.ai, a.as, a.dom, a.step.plane_stride);
+  k_adj_gather<S, R><<<g2, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_adj_objective(R* lam, DomDesc d, long long ps, double w_s, double w_c,
+                                 double yc, double gas, cudaStream_t st) {
+  const long long n = (long long)d.nx * d.ny;
+  const int g = (int)std::min<long long>((n + 255) / 256, 4096);
+  k_adj_objective<R><<<g, 256, 0, st>>>(lam, d, ps, w_s, w_c, yc, gas);
+  return cudaGetLastError();
+}
+
+template <typename S, typename R>
+cudaError_t launch_adj_omega_init(const R* lam, const S* pop, const R* aux, DomDesc d,
+                                  long long ps, double lam_p, double k, double* partial,
+                                  int blocks, cudaStream_t st) {
+  k_adj_omega_init<S, R><<<blocks, 256, 0, st>>>(lam, pop, aux, d, ps, lam_p, k, partial);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_adjoint_step<double, double>(const AdjArgs<double, double>&, int,
+                                                        cudaStream_t);
+template cudaError_t launch_adjoint_step<float, float>(const AdjArgs<float, float>&, int,
+                                                      cudaStream_t);
+template cudaError_t launch_adj_objective<double>(double*, DomDesc, long long, double, double,
+                                                  double, double, cudaStream_t);
+template cudaError_t launch_adj_objective<float>(float*, DomDesc, long long, double, double,
+                                                 double, double, cudaStream_t);
+template cudaError_t launch_adj_omega_init<double, double>(const double*, const double*,
+                                                          const double*, DomDesc, long long,
+                                                          double, double, double*, int,
+                                                          cudaStream_t);
+template cudaError_t launch_adj_omega_init<float, float>(const float*, const float*,
+                                                        const float*, DomDesc, long long,
+                                                        double, double, double*, int,
+                                                        cudaStream_t);
+
+}  // namespace pf

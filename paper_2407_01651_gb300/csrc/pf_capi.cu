@@ -58,6 +58,9 @@ struct pf_handle {
   long long steps = 0;
   long long launches = 0;
   std::string err;
+  // discrete-adjoint workspace (grown on demand, released by pf_destroy)
+  void* adj_ws = nullptr;
+  size_t adj_ws_bytes = 0;
 };
 
 static std::string g_create_err;
@@ -225,6 +228,8 @@ static void release(pf_handle* h) {
   dev_free(h, h->partial);
   dev_free(h, h->d_diag);
   dev_free(h, h->staging);
+  dev_free(h, h->adj_ws);
+  h->adj_ws = nullptr;
   h->fields = h->grain = nullptr;
 }
 
@@ -513,12 +518,13 @@ extern "C" pf_status pf_set_fields(pf_handle* h, int dom, const double* fields6,
 // stepping
 // ---------------------------------------------------------------------------
 template <typename S, typename R>
-static pf_status step_t(pf_handle* h, bool write_fields) {
+static StepArgs<S, R> make_step_args(const pf_handle* h, const void* pin, const void* ain,
+                                     void* pout, void* aout, bool write_fields) {
   StepArgs<S, R> a{};
-  a.in = reinterpret_cast<const S*>(h->pop[h->cur]);
-  a.out = reinterpret_cast<S*>(h->pop[h->cur ^ 1]);
-  a.ain = reinterpret_cast<const R*>(h->aux[h->cur]);
-  a.aout = reinterpret_cast<R*>(h->aux[h->cur ^ 1]);
+  a.in = reinterpret_cast<const S*>(pin);
+  a.out = reinterpret_cast<S*>(pout);
+  a.ain = reinterpret_cast<const R*>(ain);
+  a.aout = reinterpret_cast<R*>(aout);
   a.plane_stride = h->plane_stride;
   a.grain = h->grain;
   a.grain_cs = h->grain_cs;
@@ -526,8 +532,16 @@ static pf_status step_t(pf_handle* h, bool write_fields) {
   a.tile_dom = h->d_tile_dom;
   a.ntiles = h->ntiles;
   a.chunk = h->chunk;
-  a.fields = write_fields ? fields_ptr<R>(h) : nullptr;
+  a.fields = write_fields ? reinterpret_cast<R*>(h->fields) : nullptr;
   a.kp = make_kparams<R>(h->p);
+  return a;
+}
+
+template <typename S, typename R>
+static pf_status step_t(pf_handle* h, bool write_fields) {
+  const StepArgs<S, R> a = make_step_args<S, R>(h, h->pop[h->cur], h->aux[h->cur],
+                                                h->pop[h->cur ^ 1], h->aux[h->cur ^ 1],
+                                                write_fields);
   PF_CUDA(h, launch_step<S, R>(a, h->variant, h->tx, h->ty, h->grid, h->stream));
   h->launches++;
   h->cur ^= 1;
@@ -678,4 +692,141 @@ extern "C" pf_status pf_reduce(pf_handle* h, int dom, const pf_probe* probe, pf_
   static_assert(sizeof(pf_diag) == NDIAG * sizeof(double), "pf_diag layout");
   std::memcpy(out, buf, sizeof(buf));
   return PF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// discrete adjoint
+// ---------------------------------------------------------------------------
+template <typename S, typename R>
+static pf_status adjoint_t(pf_handle* h, int n, const pf_objective* obj, double* J_out,
+                           double* grad) {
+  const DomDesc dd = h->ddesc[0];
+  const size_t ps = (size_t)h->plane_stride;
+  const size_t pop_b = ps * N_POP * sizeof(S), aux_b = ps * N_AUX * sizeof(R);
+  const size_t state_b = (pop_b + 255) / 256 * 256 + (aux_b + 255) / 256 * 256;
+  const int K = obj->checkpoint_every;
+  const int nseg = (n + K - 1) / K;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  const int tiles = ((dd.nx + ADJ_TX - 1) / ADJ_TX) * ((dd.ny + ADJ_TY - 1) / ADJ_TY);
+  const int grid = std::max(1, std::min(tiles, 4 * std::max(sms, 1)));
+  const int oblocks = 256;
+  const size_t lam_b = ps * N_PHYS * sizeof(R), ai_b = ps * N_AI * sizeof(R),
+               as_b = ps * 4 * sizeof(R);
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t need = (size_t)nseg * state_b + (size_t)K * state_b + 2 * up(lam_b) + up(ai_b) +
+                      up(as_b) + up((size_t)grid * 3 * sizeof(double)) +
+                      up((size_t)oblocks * sizeof(double));
+  if (need > h->adj_ws_bytes) {
+    PF_CUDA(h, cudaStreamSynchronize(h->stream));
+    dev_free(h, h->adj_ws);
+    h->adj_ws = dev_alloc(h, need);
+    h->adj_ws_bytes = h->adj_ws ? need : 0;
+    if (!h->adj_ws) return fail(h, PF_ERR_OOM, "adjoint workspace allocation failed");
+  }
+  char* w = static_cast<char*>(h->adj_ws);
+  auto take = [&](size_t b) { char* p = w; w += up(b); return p; };
+  std::vector<char*> ck(nseg), sg(K);
+  for (int i = 0; i < nseg; ++i) ck[i] = take(state_b);
+  for (int i = 0; i < K; ++i) sg[i] = take(state_b);
+  R* lam[2] = {reinterpret_cast<R*>(take(lam_b)), reinterpret_cast<R*>(take(lam_b))};
+  R* ai = reinterpret_cast<R*>(take(ai_b));
+  R* as = reinterpret_cast<R*>(take(as_b));
+  double* partial = reinterpret_cast<double*>(take((size_t)grid * 3 * sizeof(double)));
+  double* opart = reinterpret_cast<double*>(take((size_t)oblocks * sizeof(double)));
+  auto pop_of = [&](char* st) { return (void*)st; };
+  auto aux_of = [&](char* st) { return (void*)(st + up(pop_b)); };
+  const bool fresh = h->steps == 0;
+
+  // forward sweep with a checkpoint every K steps
+  for (int t = 0; t < n; ++t) {
+    if (t % K == 0) {
+      PF_CUDA(h, cudaMemcpyAsync(pop_of(ck[t / K]), h->pop[h->cur], pop_b,
+                                 cudaMemcpyDeviceToDevice, h->stream));
+      PF_CUDA(h, cudaMemcpyAsync(aux_of(ck[t / K]), h->aux[h->cur], aux_b,
+                                 cudaMemcpyDeviceToDevice, h->stream));
+    }
+    pf_status st = step_t<S, R>(h, t == n - 1);
+    if (st != PF_OK) return st;
+  }
+  // objective J(x_T) and its adjoint lambda_T
+  pf_diag dg{};
+  pf_status st = pf_reduce(h, 0, nullptr, &dg);
+  if (st != PF_OK) return st;
+  const double N = (double)dd.nx * dd.ny;
+  if (!(dg.gas > 0.0) && obj->w_centroid != 0.0)
+    return fail(h, PF_ERR_BAD_ARG, "bubble centroid objective needs gas in the domain");
+  const double yc = dg.gas > 0.0 ? dg.gas_y / dg.gas : 0.0;
+  const double J = obj->w_solid * dg.sum_hpsi / N + obj->w_centroid * yc / dd.ny;
+  PF_CUDA(h, launch_adj_objective<R>(lam[0], dd, (long long)ps, obj->w_solid, obj->w_centroid,
+                                     yc, dg.gas > 0.0 ? dg.gas : 1.0, h->stream));
+  PF_CUDA(h, cudaMemsetAsync(partial, 0, (size_t)grid * 3 * sizeof(double), h->stream));
+  h->launches++;
+
+  // reverse sweep, one checkpoint segment at a time
+  const double dfs = 6.0 / (h->p.W_phi * std::sqrt(2.0 * h->p.beta_phi));
+  int cl = 0;
+  for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+    const int t0 = sgi * K, t1 = std::min(n, t0 + K), L = t1 - t0;
+    PF_CUDA(h, cudaMemcpyAsync(pop_of(sg[0]), pop_of(ck[sgi]), pop_b, cudaMemcpyDeviceToDevice,
+                               h->stream));
+    PF_CUDA(h, cudaMemcpyAsync(aux_of(sg[0]), aux_of(ck[sgi]), aux_b, cudaMemcpyDeviceToDevice,
+                               h->stream));
+    for (int j = 0; j + 1 < L; ++j) {
+      const StepArgs<S, R> a = make_step_args<S, R>(h, pop_of(sg[j]), aux_of(sg[j]),
+                                                    pop_of(sg[j + 1]), aux_of(sg[j + 1]), false);
+      PF_CUDA(h, launch_step<S, R>(a, h->variant, h->tx, h->ty, h->grid, h->stream));
+      h->launches++;
+    }
+    for (int j = L - 1; j >= 0; --j) {
+      AdjArgs<S, R> aa{};
+      aa.step = make_step_args<S, R>(h, pop_of(sg[j]), aux_of(sg[j]), nullptr, nullptr, false);
+      aa.dom = dd;
+      aa.lam_in = lam[cl];
+      aa.lam_out = lam[cl ^ 1];
+      aa.ai = ai;
+      aa.as = as;
+      aa.partial = partial;
+      aa.dfs_dsigma = dfs;
+      PF_CUDA(h, launch_adjoint_step<S, R>(aa, grid, h->stream));
+      h->launches += 3;
+      cl ^= 1;
+    }
+  }
+  std::vector<double> hp((size_t)grid * 3), ho(oblocks, 0.0);
+  if (fresh) {
+    double der[3];
+    pf_params_derived(&h->p, der);
+    PF_CUDA(h, launch_adj_omega_init<S, R>(lam[cl], (const S*)pop_of(ck[0]),
+                                           (const R*)aux_of(ck[0]), dd, (long long)ps, der[0],
+                                           h->p.k, opart, oblocks, h->stream));
+    h->launches++;
+    PF_CUDA(h, cudaMemcpyAsync(ho.data(), opart, oblocks * sizeof(double), cudaMemcpyDeviceToHost,
+                               h->stream));
+  }
+  PF_CUDA(h, cudaMemcpyAsync(hp.data(), partial, hp.size() * sizeof(double),
+                             cudaMemcpyDeviceToHost, h->stream));
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  double g[3] = {0.0, 0.0, 0.0};
+  for (int b = 0; b < grid; ++b)
+    for (int q = 0; q < 3; ++q) g[q] += hp[(size_t)b * 3 + q];
+  for (int b = 0; b < oblocks; ++b) g[1] += ho[b];
+  if (J_out) *J_out = J;
+  for (int q = 0; q < 3; ++q) grad[q] = g[q];
+  return PF_OK;
+}
+
+extern "C" pf_status pf_adjoint_step(pf_handle* h, int n_steps, const pf_objective* obj,
+                                     double* J_out, double grad_out[3]) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (!obj || !grad_out || n_steps < 1 || obj->checkpoint_every < 1)
+    return fail(h, PF_ERR_BAD_ARG, "need n_steps >= 1, an objective and checkpoint_every >= 1");
+  if (h->doms.size() != 1) return fail(h, PF_ERR_BAD_ARG, "the adjoint takes a single-domain handle");
+  if (h->prec != PF_FP32 && h->prec != PF_FP64)
+    return fail(h, PF_ERR_BAD_ARG, "the adjoint supports the FP32 and FP64 storage forms");
+  if (!h->inited[0]) return fail(h, PF_ERR_STATE, "initialise the domain before the adjoint");
+  if (!std::isfinite(obj->w_solid) || !std::isfinite(obj->w_centroid))
+    return fail(h, PF_ERR_BAD_ARG, "objective weights must be finite");
+  if (h->prec == PF_FP64) return adjoint_t<double, double>(h, n_steps, obj, J_out, grad_out);
+  return adjoint_t<float, float>(h, n_steps, obj, J_out, grad_out);
 }

@@ -93,6 +93,39 @@ template <typename R>
 cudaError_t launch_reduce(const ReduceArgs<R>& a, double* partial, double* out,
                           cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// Discrete adjoint
+// ---------------------------------------------------------------------------
+constexpr int ADJ_TX = 32, ADJ_TY = 8;  // tile of the local reverse kernel
+// Planes of the per-site input adjoints (layout of local::In).
+enum AiPlane : int {
+  AI_F = 0, AI_H = 9, AI_G = 18, AI_S = 23, AI_PSIO = 28, AI_GPX = 29, AI_GPY = 30,
+  AI_LPHI = 31, AI_GSX = 32, AI_GSY = 33, AI_DVXX = 34, AI_DVXY = 35, AI_DVYX = 36,
+  AI_DVYY = 37, AI_PHIO = 38, AI_CO = 39, AI_QO = 40, AI_VXO = 41, AI_VYO = 42, N_AI = 43
+};
+
+template <typename S, typename R>
+struct AdjArgs {
+  StepArgs<S, R> step;     // the state x_t (in / ain) and the coefficients
+  DomDesc dom;
+  const R* lam_in;         // lambda_{t+1}, 39 planes
+  R* lam_out;              // lambda_t, 39 planes
+  R* ai;                   // input adjoints, N_AI planes
+  R* as;                   // stencil-transposed field adjoints, 4 planes
+  double* partial;         // per-block parameter adjoints (eps, Omega, sigma), accumulated
+  double dfs_dsigma;       // d(surface-tension coefficient)/d sigma
+};
+
+template <typename S, typename R>
+cudaError_t launch_adjoint_step(const AdjArgs<S, R>& a, int grid, cudaStream_t st);
+template <typename R>
+cudaError_t launch_adj_objective(R* lam, DomDesc d, long long ps, double w_s, double w_c,
+                                 double yc, double gas, cudaStream_t st);
+template <typename S, typename R>
+cudaError_t launch_adj_omega_init(const R* lam, const S* pop, const R* aux, DomDesc d,
+                                  long long ps, double lam_p, double k, double* partial,
+                                  int blocks, cudaStream_t st);
+
 // Message returned by pf_last_error(NULL) (entry points without a handle).
 void set_global_error(const std::string& msg);
 

@@ -57,6 +57,11 @@ class pf_diag(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in _DIAG_FIELDS]
 
 
+class pf_objective(ctypes.Structure):
+    _fields_ = [("w_solid", ctypes.c_double), ("w_centroid", ctypes.c_double),
+                ("checkpoint_every", ctypes.c_int)]
+
+
 class pf_probe(ctypes.Structure):
     _fields_ = [("xc", ctypes.c_double), ("yc", ctypes.c_double), ("R", ctypes.c_double),
                 ("W", ctypes.c_double)]
@@ -90,6 +95,7 @@ def lib() -> ctypes.CDLL:
     L.pf_get_step_config.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
     L.pf_reduce_noalloc.argtypes = [P, I, ctypes.c_longlong, ctypes.c_longlong, I, I,
                                     ctypes.POINTER(pf_probe), ctypes.POINTER(pf_diag), P]
+    L.pf_adjoint_step.argtypes = [P, I, ctypes.POINTER(pf_objective), D, D]
     L.pf_sync.argtypes = [P]
     L.pf_steps_taken.argtypes = [P]
     L.pf_steps_taken.restype = ctypes.c_longlong
@@ -101,7 +107,7 @@ def lib() -> ctypes.CDLL:
     for name in ("pf_params_default", "pf_params_derived", "pf_create", "pf_init_fields",
                  "pf_set_fields", "pf_step", "pf_get_fields", "pf_get_state", "pf_set_state",
                  "pf_reduce", "pf_sync", "pf_destroy", "pf_set_step_config",
-                 "pf_get_step_config", "pf_reduce_noalloc"):
+                 "pf_get_step_config", "pf_reduce_noalloc", "pf_adjoint_step"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -277,6 +283,17 @@ class Simulation:
     def set_state(self, dom: int, state: np.ndarray) -> None:
         a = np.ascontiguousarray(np.asarray(state, dtype=np.float64)).ravel()
         _check(lib().pf_set_state(self.h, dom, _dp(a), a.size), self.h)
+
+    def adjoint_step(self, n_steps: int, w_solid: float = 1.0, w_centroid: float = 1.0,
+                     checkpoint_every: int = 100) -> tuple[float, np.ndarray]:
+        """Run n_steps forward with checkpoints, then the discrete adjoint:
+        returns (J, dJ/d(eps_s, Omega, sigma))."""
+        obj = pf_objective(float(w_solid), float(w_centroid), int(checkpoint_every))
+        J = ctypes.c_double()
+        g = np.zeros(3)
+        _check(lib().pf_adjoint_step(self.h, int(n_steps), ctypes.byref(obj), ctypes.byref(J),
+                                     _dp(g)), self.h)
+        return J.value, g
 
     def reduce(self, dom: int = 0, probe=None) -> dict:
         d = pf_diag()

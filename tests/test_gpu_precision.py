@@ -57,6 +57,12 @@ def test_offset_storage_against_oracle(precision):
     assert abs(d["sum_C"] / d0["sum_C"] - 1) < 1e-5
 
 
+# The raw FP64 state has no psi_o plane: restoring re-encodes the dendrite
+# offsets relative to sum g_pre instead of the stored lagged psi, which
+# re-rounds them once at the storage precision.
+ROUNDTRIP = {"fp16": (1e-5, 1e-4), "bf16": (1e-4, 1e-3)}
+
+
 @pytest.mark.parametrize("precision", ["fp16", "bf16"])
 def test_offset_state_checkpoint_roundtrip(precision):
     lay = wl.random_layout(64, 48, 2, 1, rng_seed=9, R_max=8)
@@ -67,9 +73,10 @@ def test_offset_state_checkpoint_roundtrip(precision):
     b = pf.Simulation([(lay.nx, lay.ny)], lay.params, precision)
     b.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
     b.set_state(0, ck)
-    assert rel(b.get_state(), ck) < 1e-6
+    tol_state, tol_fields = ROUNDTRIP[precision]
+    assert rel(b.get_state(), ck) < tol_state
     a.step(5)
     b.step(5)
     fa, fb = a.fields(), b.fields()
     for k in ("phi", "psi", "C", "U"):
-        assert rel(fb[k], fa[k]) < 1e-5, k
+        assert rel(fb[k], fa[k]) < tol_fields, k
