@@ -188,6 +188,95 @@ def run_reference(args) -> None:
     print(json.dumps(line))
 
 
+def _time_steps(torch, sim, stream, n):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sim.sync()
+    e0.record(stream)
+    sim.step(n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_ensemble(args) -> None:
+    """96 independent domains of uneven size (32 each of 256^2, 512x384,
+    1024x512; 1-4 seeds, 1-6 bubbles, eps_s ~ U[0.02, 0.07]) in one handle:
+    one launch per domain per step vs one batched launch per step vs the
+    autotuned batched launch replayed as CUDA graphs."""
+    import torch
+
+    from paper_2407_01651_gb300 import pf
+    from paper_2407_01651_gb300 import workload as wl
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    lays = wl.cfg5_layouts()
+    stream = torch.cuda.current_stream()
+    sim = pf.Simulation([(l.nx, l.ny, l.params["eps_s"]) for l in lays], wl.BASE_PARAMS, "fp32",
+                        stream=stream.cuda_stream)
+    for d, l in enumerate(lays):
+        sim.init_fields(d, l.seeds, l.R_s, l.bubbles)
+    sites = sum(l.nx * l.ny for l in lays)
+    res = {}
+    sim.set_launch(1, 0, 0)
+    sim.step(args.warmup)
+    ms = _time_steps(torch, sim, stream, args.steps)
+    res["sequential_per_domain"] = sites * args.steps / ms / 1e3
+    sim.set_launch(0, 0, 0)
+    sim.step(args.warmup)
+    ms = _time_steps(torch, sim, stream, args.steps)
+    res["batched_one_launch"] = sites * args.steps / ms / 1e3
+    cfg = sim.autotune(10)
+    sim.set_launch(0, cfg[3], 64)
+    sim.step(args.warmup)
+    launches0 = sim.launches
+    ms = _time_steps(torch, sim, stream, args.steps)
+    res["batched_autotuned_graph"] = sites * args.steps / ms / 1e3
+    print(json.dumps({
+        "metric": "ensemble aggregate MLUPS (96 uneven domains)", "value": res["batched_autotuned_graph"],
+        "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "96 domains: 32 x 256^2, 32 x 512x384, 32 x 1024x512, seed 5",
+                   "sites": sites, "autotuned": list(cfg), "graph_steps": 64},
+        "modes": res, "speedup_vs_sequential": res["batched_autotuned_graph"] /
+        res["sequential_per_domain"], "gpu_launches": sim.launches - launches0}))
+    sim.close()
+
+
+def run_precision(args) -> None:
+    """8192 x 4096 seeded like the 128^2 case (one seed, one bubble), FP32 vs
+    FP16- and BF16-offset storage."""
+    import torch
+
+    from paper_2407_01651_gb300 import pf
+    from paper_2407_01651_gb300 import workload as wl
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    lay = wl.single_seed_bubble(8192, 4096, rng_seed=1)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for prec in ("fp32", "fp16", "bf16"):
+        sim = pf.Simulation([(lay.nx, lay.ny)], lay.params, prec, stream=stream.cuda_stream)
+        sim.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
+        sim.step(args.warmup)
+        ms = _time_steps(torch, sim, stream, args.steps)
+        bpl = BYTES_PER_LU[prec]
+        out[prec] = {"mlups": lay.nx * lay.ny * args.steps / ms / 1e3,
+                     "ms_per_step": ms / args.steps,
+                     "algorithmic_gbs": bpl * lay.nx * lay.ny * args.steps / ms / 1e6,
+                     "bytes_per_lu": bpl}
+        sim.close()
+        torch.cuda.empty_cache()
+    print(json.dumps({
+        "metric": "precision-form MLUPS at 8192x4096", "value": out["fp16"]["mlups"],
+        "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f16-storage/f32", "data": "synthetic",
+        "config": {"workload": "8192x4096, one seed + one R=16 bubble (seed 1)"},
+        "forms": out, "speedup_fp16_vs_fp32": out["fp16"]["mlups"] / out["fp32"]["mlups"],
+        "speedup_bf16_vs_fp32": out["bf16"]["mlups"] / out["fp32"]["mlups"]}))
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -199,6 +288,9 @@ def main() -> None:
     ap.add_argument("--variant", type=int, default=None, help="step kernel traversal")
     ap.add_argument("--chunk", type=int, default=None, help="rows per y-march tile / tile a")
     ap.add_argument("--tile-b", type=int, default=0)
+    ap.add_argument("--workload", default="lattice", choices=("lattice", "ensemble", "precision"),
+                    help="lattice: the 4096^2 headline; ensemble: 96 uneven domains; "
+                         "precision: 8192x4096 in FP32 / FP16 / BF16 storage")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -209,6 +301,12 @@ def main() -> None:
 
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "ensemble":
+        run_ensemble(args)
+        return
+    if args.workload == "precision":
+        run_precision(args)
         return
 
     import numpy as np

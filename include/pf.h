@@ -55,7 +55,9 @@ typedef enum {
  *  beta_phi, beta_psi, beta_inter   double-well / interaction heights
  *                 (Eq. eq-douWell, eq-f3Inter); the paper uses 1/4, 1/4, 3/4
  *  W0, tau0       dendrite interface width and relaxation time (Eq. eq-AnACE)
- *  eps_s          fourfold anisotropy strength (anisotropy function, Sec. 3.3)
+ *  eps_s          fourfold anisotropy strength (anisotropy function, Sec. 3.3),
+ *                 in [0, 0.25); above 1/15 the interface stiffness is negative
+ *                 along <11> (corners form)
  *  k              partition coefficient
  *  D              solute diffusivity in the liquid
  *  Omega          solutal undercooling; theta_sys and M c_inf follow from it
@@ -73,7 +75,8 @@ typedef struct pf_params {
   double grad_eps, grad_eps_at, s_e, s_eps;
 } pf_params;
 
-/* One periodic domain of an ensemble.  eps_s < 0 uses pf_params.eps_s. */
+/* One periodic domain of an ensemble.  eps_s < 0 uses pf_params.eps_s;
+ * otherwise it must be below 0.25. */
 typedef struct pf_domain {
   int nx, ny;
   double eps_s;
@@ -175,6 +178,24 @@ pf_status pf_step(pf_handle *h, int n_steps);
  * tiles of a rows (b ignored; the default, a = 48).  Synchronises the stream
  * and rebuilds the tile table.  Errors: BAD_ARG. */
 pf_status pf_set_step_config(pf_handle *h, int variant, int a, int b);
+
+/* How a step is launched over an ensemble of domains:
+ *  per_domain = 0: one launch whose tile list spans every domain (default);
+ *               1: one launch per domain, one after the other.
+ *  persistent = 1: the grid is the device's resident CTAs of the step kernel,
+ *               each looping over tiles; 0: one CTA per tile (default).
+ *  graph_steps > 0 (even): pf_step replays CUDA graphs of graph_steps steps
+ *               (captured on an internal stream on first use, replayed on the
+ *               handle's stream); 0 launches step by step (default).
+ * Synchronises the stream.  Errors: BAD_ARG. */
+pf_status pf_set_launch(pf_handle *h, int per_domain, int persistent, int graph_steps);
+
+/* Autotuner: times every step traversal and tile height (and persistent or
+ * not) on the handle's own domains for trial_steps steps each, starting every
+ * candidate from a snapshot of the current state, restores that state and
+ * keeps the fastest configuration.  out (may be NULL): variant, a, b,
+ * persistent.  Errors: BAD_ARG, STATE, OOM, CUDA. */
+pf_status pf_autotune(pf_handle *h, int trial_steps, int out[4]);
 
 /* Current traversal: out[0] variant, out[1] a, out[2] b. */
 pf_status pf_get_step_config(const pf_handle *h, int out[3]);

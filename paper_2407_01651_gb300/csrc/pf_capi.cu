@@ -43,6 +43,13 @@ struct pf_handle {
   int chunk = 48;           // rows per tile of the y-march variant (tuned at 4096^2)
   int ntiles = 0;
   int grid = 0;
+  int launch_mode = 0;      // 0: one launch over all domains; 1: one launch per domain
+  int persistent = 0;       // 1: grid = resident CTAs, each loops over tiles
+  int sms = 0;
+  // CUDA-graph replay of the stepping: one executable graph per buffer parity
+  int graph_steps = 0;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  cudaStream_t cap_stream = nullptr;
   void* pop[2] = {nullptr, nullptr};   // population planes, storage type
   void* aux[2] = {nullptr, nullptr};   // lagged-scalar planes, compute type
   int cur = 0;
@@ -167,8 +174,10 @@ static pf_status check_params(const pf_params* p) {
       !finite_pos(p->s_eps) || p->s_e >= 2.0 || p->s_eps >= 2.0)
     return fail(nullptr, PF_ERR_BAD_ARG, "a parameter is non-finite or out of range");
   if (!(p->k > 0.0 && p->k < 1.0)) return fail(nullptr, PF_ERR_BAD_ARG, "k must be in (0, 1)");
-  if (!(p->eps_s >= 0.0 && p->eps_s < 1.0 / 15.0))
-    return fail(nullptr, PF_ERR_BAD_ARG, "eps_s must be in [0, 1/15)");
+  // a_s >= 1 - eps > 0 needs eps < 1; beyond 1/15 the interface stiffness
+  // a_s + a_s'' turns negative along the <11> directions (sharp corners)
+  if (!(p->eps_s >= 0.0 && p->eps_s < 0.25))
+    return fail(nullptr, PF_ERR_BAD_ARG, "eps_s must be in [0, 0.25)");
   if (1.0 - (1.0 - p->k) * p->Omega == 0.0)
     return fail(nullptr, PF_ERR_BAD_ARG, "1 - (1-k) Omega must be non-zero");
   return PF_OK;
@@ -230,6 +239,9 @@ static void release(pf_handle* h) {
   dev_free(h, h->staging);
   dev_free(h, h->adj_ws);
   h->adj_ws = nullptr;
+  for (auto& g : h->gexec)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  if (h->cap_stream) { cudaStreamDestroy(h->cap_stream); h->cap_stream = nullptr; }
   h->fields = h->grain = nullptr;
 }
 
@@ -254,10 +266,10 @@ static pf_status upload_tables(pf_handle* h) {
   PF_CUDA(h, cudaMemcpyAsync(h->d_doms, h->ddesc.data(), h->ddesc.size() * sizeof(DomDesc),
                              cudaMemcpyHostToDevice, h->stream));
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  for (auto& g : h->gexec)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
   h->grid = h->ntiles;  // one CTA per tile; the kernel also accepts fewer (grid-stride)
-  (void)sms;
   return PF_OK;
 }
 
@@ -274,8 +286,8 @@ extern "C" pf_status pf_create(const pf_params* p, const pf_domain* doms, int n_
   for (int d = 0; d < n_doms; ++d) {
     if (doms[d].nx < 4 || doms[d].ny < 4 || doms[d].nx > (1 << 16) || doms[d].ny > (1 << 16))
       return fail(nullptr, PF_ERR_BAD_ARG, "domain sizes must be in [4, 65536]");
-    if (doms[d].eps_s >= 1.0 / 15.0 || !std::isfinite(doms[d].eps_s))
-      return fail(nullptr, PF_ERR_BAD_ARG, "domain eps_s must be < 1/15");
+    if (doms[d].eps_s >= 0.25 || !std::isfinite(doms[d].eps_s))
+      return fail(nullptr, PF_ERR_BAD_ARG, "domain eps_s must be < 0.25");
   }
   if (alloc && (!alloc->alloc || !alloc->free))
     return fail(nullptr, PF_ERR_BAD_ARG, "allocator needs alloc and free");
@@ -537,15 +549,87 @@ static StepArgs<S, R> make_step_args(const pf_handle* h, const void* pin, const 
   return a;
 }
 
+// Launch the step over every domain: one launch over the whole tile list, or
+// one launch per domain; the grid is one CTA per tile, or the resident CTAs
+// of the device looping over the tiles (persistent).
 template <typename S, typename R>
-static pf_status step_t(pf_handle* h, bool write_fields) {
+static pf_status launch_all(pf_handle* h, StepArgs<S, R> a, cudaStream_t stream) {
+  const int cap = h->persistent
+                      ? std::max(1, h->sms) * step_blocks_per_sm<S, R>(h->variant, h->tx, h->ty)
+                      : 1 << 30;
+  if (h->launch_mode == 0) {
+    a.tile_base = 0;
+    a.ntiles = h->ntiles;
+    PF_CUDA(h, launch_step<S, R>(a, h->variant, h->tx, h->ty, std::min(h->ntiles, cap), stream));
+    h->launches++;
+  } else {
+    for (size_t d = 0; d < h->ddesc.size(); ++d) {
+      const int t0 = h->ddesc[d].tile0;
+      const int t1 = d + 1 < h->ddesc.size() ? h->ddesc[d + 1].tile0 : h->ntiles;
+      a.tile_base = t0;
+      a.ntiles = t1;
+      PF_CUDA(h, launch_step<S, R>(a, h->variant, h->tx, h->ty, std::min(t1 - t0, cap), stream));
+      h->launches++;
+    }
+  }
+  return PF_OK;
+}
+
+template <typename S, typename R>
+static pf_status step_t(pf_handle* h, bool write_fields, cudaStream_t stream = nullptr) {
   const StepArgs<S, R> a = make_step_args<S, R>(h, h->pop[h->cur], h->aux[h->cur],
                                                 h->pop[h->cur ^ 1], h->aux[h->cur ^ 1],
                                                 write_fields);
-  PF_CUDA(h, launch_step<S, R>(a, h->variant, h->tx, h->ty, h->grid, h->stream));
-  h->launches++;
+  pf_status st = launch_all<S, R>(h, a, stream ? stream : h->stream);
+  if (st != PF_OK) return st;
   h->cur ^= 1;
   h->steps++;
+  return PF_OK;
+}
+
+// Executable graph of graph_steps steps (no field output) starting from the
+// current buffer parity; captured on an internal stream, replayed on the
+// handle's stream.  graph_steps is even, so the parity is unchanged.
+template <typename S, typename R>
+static pf_status ensure_graph(pf_handle* h) {
+  const int par = h->cur;
+  if (h->gexec[par]) return PF_OK;
+  if (!h->cap_stream) PF_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  const long long steps0 = h->steps, launches0 = h->launches;
+  PF_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  pf_status st = PF_OK;
+  for (int t = 0; t < h->graph_steps && st == PF_OK; ++t) st = step_t<S, R>(h, false, h->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+  h->cur = par;
+  h->steps = steps0;
+  h->launches = launches0;
+  if (st != PF_OK) { if (g) cudaGraphDestroy(g); return st; }
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&h->gexec[par], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { h->gexec[par] = nullptr; return cuda_fail(h, e, "cudaGraphInstantiate"); }
+  return PF_OK;
+}
+
+template <typename S, typename R>
+static pf_status step_n(pf_handle* h, int n_steps) {
+  int done = 0;
+  if (h->graph_steps > 0) {
+    const int launches_per_step = h->launch_mode == 0 ? 1 : (int)h->ddesc.size();
+    while (n_steps - 1 - done >= h->graph_steps) {
+      pf_status st = ensure_graph<S, R>(h);
+      if (st != PF_OK) return st;
+      PF_CUDA(h, cudaGraphLaunch(h->gexec[h->cur], h->stream));
+      done += h->graph_steps;
+      h->steps += h->graph_steps;
+      h->launches += (long long)h->graph_steps * launches_per_step;
+    }
+  }
+  for (; done < n_steps; ++done) {
+    pf_status st = step_t<S, R>(h, done == n_steps - 1);
+    if (st != PF_OK) return st;
+  }
   return PF_OK;
 }
 
@@ -567,6 +651,99 @@ extern "C" pf_status pf_set_step_config(pf_handle* h, int variant, int a, int b)
   return upload_tables(h);
 }
 
+extern "C" pf_status pf_set_launch(pf_handle* h, int per_domain, int persistent,
+                                   int graph_steps) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (per_domain < 0 || per_domain > 1 || persistent < 0 || persistent > 1 || graph_steps < 0 ||
+      (graph_steps % 2) != 0 || graph_steps > 4096)
+    return fail(h, PF_ERR_BAD_ARG, "per_domain, persistent in {0,1}; graph_steps even in [0, 4096]");
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->launch_mode = per_domain;
+  h->persistent = persistent;
+  h->graph_steps = graph_steps;
+  for (auto& g : h->gexec)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  return PF_OK;
+}
+
+template <typename S, typename R>
+static pf_status autotune_t(pf_handle* h, int trial_steps, int out[4]) {
+  const size_t ps = (size_t)h->plane_stride;
+  const size_t pop_b = ps * N_POP * sizeof(S), aux_b = ps * N_AUX * sizeof(R);
+  void* snap_p = dev_alloc(h, pop_b);
+  void* snap_a = dev_alloc(h, aux_b);
+  if (!snap_p || !snap_a) {
+    dev_free(h, snap_p);
+    dev_free(h, snap_a);
+    return fail(h, PF_ERR_OOM, "autotune snapshot allocation failed");
+  }
+  const int cur0 = h->cur;
+  const long long steps0 = h->steps, launches0 = h->launches;
+  PF_CUDA(h, cudaMemcpyAsync(snap_p, h->pop[cur0], pop_b, cudaMemcpyDeviceToDevice, h->stream));
+  PF_CUDA(h, cudaMemcpyAsync(snap_a, h->aux[cur0], aux_b, cudaMemcpyDeviceToDevice, h->stream));
+  struct Cand { int variant, a, b, persistent; };
+  std::vector<Cand> cands;
+  for (int ch : {8, 16, 24, 32, 48, 64, 96})
+    for (int pers : {0, 1}) cands.push_back({STEP_YMARCH, ch, 0, pers});
+  cands.push_back({STEP_TILE, 32, 8, 0});
+  cands.push_back({STEP_TILE, 64, 4, 0});
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  Cand bc = cands[0];
+  pf_status st = PF_OK;
+  for (const Cand& c : cands) {
+    h->variant = c.variant;
+    if (c.variant == STEP_YMARCH) h->chunk = c.a; else { h->tx = c.a; h->ty = c.b; }
+    h->persistent = c.persistent;
+    st = upload_tables(h);
+    if (st != PF_OK) break;
+    for (int t = 0; t < 2 && st == PF_OK; ++t) st = step_t<S, R>(h, false);
+    cudaEventRecord(e0, h->stream);
+    for (int t = 0; t < trial_steps && st == PF_OK; ++t) st = step_t<S, R>(h, false);
+    cudaEventRecord(e1, h->stream);
+    if (st != PF_OK) break;
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; bc = c; }
+    // every candidate starts from the same state
+    h->cur = cur0;
+    cudaMemcpyAsync(h->pop[cur0], snap_p, pop_b, cudaMemcpyDeviceToDevice, h->stream);
+    cudaMemcpyAsync(h->aux[cur0], snap_a, aux_b, cudaMemcpyDeviceToDevice, h->stream);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(h->stream);
+  dev_free(h, snap_p);
+  dev_free(h, snap_a);
+  h->cur = cur0;
+  h->steps = steps0;
+  h->launches = launches0;
+  if (st != PF_OK) return st;
+  h->variant = bc.variant;
+  if (bc.variant == STEP_YMARCH) h->chunk = bc.a; else { h->tx = bc.a; h->ty = bc.b; }
+  h->persistent = bc.persistent;
+  st = upload_tables(h);
+  if (st != PF_OK) return st;
+  if (out) { out[0] = bc.variant; out[1] = bc.a; out[2] = bc.b; out[3] = bc.persistent; }
+  return PF_OK;
+}
+
+extern "C" pf_status pf_autotune(pf_handle* h, int trial_steps, int out[4]) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (trial_steps < 1 || trial_steps > 10000)
+    return fail(h, PF_ERR_BAD_ARG, "trial_steps must be in [1, 10000]");
+  for (int d : h->inited)
+    if (!d) return fail(h, PF_ERR_STATE, "initialise every domain before autotuning");
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  return dispatch(h, [&](auto s_t, auto r_t) {
+    PF_TYPES(s_t, r_t);
+    return autotune_t<S, R>(h, trial_steps, out);
+  });
+}
+
 extern "C" pf_status pf_get_step_config(const pf_handle* h, int out[3]) {
   if (!h || !out) return PF_ERR_BAD_ARG;
   out[0] = h->variant;
@@ -580,15 +757,10 @@ extern "C" pf_status pf_step(pf_handle* h, int n_steps) {
   if (n_steps < 0) return fail(h, PF_ERR_BAD_ARG, "n_steps must be >= 0");
   for (int d : h->inited)
     if (!d) return fail(h, PF_ERR_STATE, "every domain must be initialised before stepping");
-  for (int t = 0; t < n_steps; ++t) {
-    const bool last = t == n_steps - 1;
-    pf_status st = dispatch(h, [&](auto s_t, auto r_t) {
-      PF_TYPES(s_t, r_t);
-      return step_t<S, R>(h, last);
-    });
-    if (st != PF_OK) return st;
-  }
-  return PF_OK;
+  return dispatch(h, [&](auto s_t, auto r_t) {
+    PF_TYPES(s_t, r_t);
+    return step_n<S, R>(h, n_steps);
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -775,8 +947,8 @@ static pf_status adjoint_t(pf_handle* h, int n, const pf_objective* obj, double*
     for (int j = 0; j + 1 < L; ++j) {
       const StepArgs<S, R> a = make_step_args<S, R>(h, pop_of(sg[j]), aux_of(sg[j]),
                                                     pop_of(sg[j + 1]), aux_of(sg[j + 1]), false);
-      PF_CUDA(h, launch_step<S, R>(a, h->variant, h->tx, h->ty, h->grid, h->stream));
-      h->launches++;
+      pf_status sl = launch_all<S, R>(h, a, h->stream);
+      if (sl != PF_OK) return sl;
     }
     for (int j = L - 1; j >= 0; --j) {
       AdjArgs<S, R> aa{};

@@ -30,7 +30,8 @@ struct StepArgs {
   const double2* __restrict__ grain_cs; // (cos, sin) of each grain angle
   const DomDesc* __restrict__ doms;
   const int* __restrict__ tile_dom;     // domain of each tile
-  int ntiles;
+  int tile_base;                // first tile of this launch
+  int ntiles;                   // one past the last tile of this launch
   int chunk;                    // rows per y-march tile
   R* fields;                    // 8 field planes, or nullptr
   KParams<R> kp;
@@ -76,6 +77,9 @@ struct ReduceArgs {
 template <typename S, typename R>
 cudaError_t launch_step(const StepArgs<S, R>& a, int variant, int tx, int ty, int grid,
                         cudaStream_t st);
+// Resident CTAs per SM of the step kernel (for persistent grids).
+template <typename S, typename R>
+int step_blocks_per_sm(int variant, int tx, int ty);
 template <typename S, typename R>
 cudaError_t launch_init_spec(const InitArgs<S, R>& a, cudaStream_t st);
 template <typename S, typename R>

@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(256) k_step_tile(StepArgs<S, R> a) {
   const int nthr = TX * TY;
   const long long ps = a.plane_stride;
 
-  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+  for (int tile = a.tile_base + blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     const DomDesc d = a.doms[a.tile_dom[tile]];
     const int lt = tile - d.tile0;
     const int x0 = (lt % d.tiles_x) * TX, y0 = (lt / d.tiles_x) * TY;
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 3 : 2) k_step_yma
   const int t = threadIdx.x;
   const long long ps = a.plane_stride;
 
-  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+  for (int tile = a.tile_base + blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     const DomDesc d = a.doms[a.tile_dom[tile]];
     const int lt = tile - d.tile0;
     const int nx = d.nx, ny = d.ny;
@@ -349,6 +349,22 @@ cudaError_t launch_step(const StepArgs<S, R>& a, int variant, int tx, int ty, in
   }
   return cudaGetLastError();
 }
+
+template <typename S, typename R>
+int step_blocks_per_sm(int variant, int tx, int ty) {
+  int n = 0;
+  if (variant == STEP_YMARCH)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_ymarch<S, R>, YM_THREADS, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_tile<S, R>, tx * ty,
+                                                  4 * (size_t)(tx + 2) * (ty + 2) * sizeof(R));
+  return n > 0 ? n : 1;
+}
+
+template int step_blocks_per_sm<double, double>(int, int, int);
+template int step_blocks_per_sm<float, float>(int, int, int);
+template int step_blocks_per_sm<__half, float>(int, int, int);
+template int step_blocks_per_sm<__nv_bfloat16, float>(int, int, int);
 
 template cudaError_t launch_step<double, double>(const StepArgs<double, double>&, int, int, int,
                                                 int, cudaStream_t);

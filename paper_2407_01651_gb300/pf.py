@@ -96,6 +96,8 @@ def lib() -> ctypes.CDLL:
     L.pf_reduce_noalloc.argtypes = [P, I, ctypes.c_longlong, ctypes.c_longlong, I, I,
                                     ctypes.POINTER(pf_probe), ctypes.POINTER(pf_diag), P]
     L.pf_adjoint_step.argtypes = [P, I, ctypes.POINTER(pf_objective), D, D]
+    L.pf_set_launch.argtypes = [P, I, I, I]
+    L.pf_autotune.argtypes = [P, I, ctypes.POINTER(ctypes.c_int)]
     L.pf_sync.argtypes = [P]
     L.pf_steps_taken.argtypes = [P]
     L.pf_steps_taken.restype = ctypes.c_longlong
@@ -107,7 +109,8 @@ def lib() -> ctypes.CDLL:
     for name in ("pf_params_default", "pf_params_derived", "pf_create", "pf_init_fields",
                  "pf_set_fields", "pf_step", "pf_get_fields", "pf_get_state", "pf_set_state",
                  "pf_reduce", "pf_sync", "pf_destroy", "pf_set_step_config",
-                 "pf_get_step_config", "pf_reduce_noalloc", "pf_adjoint_step"):
+                 "pf_get_step_config", "pf_reduce_noalloc", "pf_adjoint_step",
+                 "pf_set_launch", "pf_autotune"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -244,6 +247,17 @@ class Simulation:
     def set_step_config(self, variant: int, a: int, b: int = 0) -> None:
         """variant 0: 2-D tiles a x b; variant 1: y-march strips, a rows per tile."""
         _check(lib().pf_set_step_config(self.h, int(variant), int(a), int(b)), self.h)
+
+    def set_launch(self, per_domain: bool = False, persistent: bool = False,
+                   graph_steps: int = 0) -> None:
+        _check(lib().pf_set_launch(self.h, int(per_domain), int(persistent), int(graph_steps)),
+               self.h)
+
+    def autotune(self, trial_steps: int = 20) -> tuple[int, int, int, int]:
+        """Pick the fastest step traversal for these domains (state unchanged)."""
+        out = (ctypes.c_int * 4)()
+        _check(lib().pf_autotune(self.h, int(trial_steps), out), self.h)
+        return tuple(out)
 
     def step_config(self) -> tuple[int, int, int]:
         out = (ctypes.c_int * 3)()

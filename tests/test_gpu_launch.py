@@ -1,0 +1,87 @@
+"""Launch machinery of the step: one launch over all domains vs one per
+domain, persistent grids, CUDA-graph replay, and the autotuner.  The
+arithmetic per site is the same in every mode, so results are bitwise equal
+(same traversal) or agree to rounding (different traversal)."""
+import numpy as np
+import pytest
+
+from paper_2407_01651_gb300 import pf
+from paper_2407_01651_gb300 import workload as wl
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ("phi", "psi", "C", "U", "p", "vx", "vy", "mu")
+
+
+def ensemble(n=5, seed=3):
+    lays = []
+    for i in range(n):
+        nx, ny = [(64, 48), (96, 96), (40, 72), (128, 64), (33, 45)][i % 5]
+        lay = wl.random_layout(nx, ny, 1 + i % 2, 1 + i % 3, rng_seed=seed + i, R_min=4,
+                               R_max=6)
+        lay.params = dict(lay.params, eps_s=0.02 + 0.01 * i)
+        lays.append(lay)
+    return lays
+
+
+def make(lays, precision="fp32"):
+    sim = pf.Simulation([(l.nx, l.ny, l.params["eps_s"]) for l in lays], wl.BASE_PARAMS,
+                        precision)
+    for d, l in enumerate(lays):
+        sim.init_fields(d, l.seeds, l.R_s, l.bubbles)
+    return sim
+
+
+def fields_all(sim, n):
+    return [sim.fields(d) for d in range(n)]
+
+
+def test_launch_modes_and_graphs_are_bitwise_identical():
+    lays = ensemble()
+    ref = make(lays)
+    ref.step(21)
+    fr = fields_all(ref, len(lays))
+    for per_domain, persistent, graph in ((1, 0, 0), (0, 1, 0), (0, 0, 8), (1, 1, 4), (0, 1, 2)):
+        sim = make(lays)
+        sim.set_launch(per_domain, persistent, graph)
+        sim.step(10)
+        sim.step(11)      # second call starts from the other buffer parity
+        assert sim.steps == 21
+        fs = fields_all(sim, len(lays))
+        for d in range(len(lays)):
+            for k in NAMES:
+                assert np.array_equal(fs[d][k], fr[d][k]), (per_domain, persistent, graph, d, k)
+
+
+def test_graph_replay_counts_launches():
+    lays = ensemble(3)
+    sim = make(lays)
+    sim.set_launch(0, 0, 8)
+    l0 = sim.launches
+    sim.step(17)
+    sim.sync()
+    assert sim.launches - l0 == 17
+
+
+def test_autotune_restores_the_state_and_keeps_a_valid_config():
+    lays = ensemble()
+    a = make(lays)
+    cfg = a.autotune(3)
+    assert a.steps == 0
+    b = make(lays)
+    b.set_step_config(cfg[0], cfg[1], cfg[2])
+    b.set_launch(0, cfg[3], 0)
+    a.step(9)
+    b.step(9)
+    fa, fb = fields_all(a, len(lays)), fields_all(b, len(lays))
+    for d in range(len(lays)):
+        for k in NAMES:
+            assert np.array_equal(fa[d][k], fb[d][k]), (cfg, d, k)
+
+
+def test_set_launch_rejects_bad_arguments():
+    sim = make(ensemble(2))
+    for args in ((2, 0, 0), (0, 2, 0), (0, 0, 3), (0, 0, -2)):
+        with pytest.raises(pf.PFError) as e:
+            sim.set_launch(*args)
+        assert e.value.code == pf.PF_ERR_BAD_ARG
