@@ -88,7 +88,9 @@ class ClockSampler:
                 idx = parts[gpu_index]
         self.idx = idx
 
-    def start(self):
+    def start(self, wait_s: float = 10.0):
+        """Start sampling and wait for the first sample, so that nvidia-smi's
+        own start-up (NVML initialisation) happens before the timed region."""
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
@@ -98,6 +100,17 @@ class ClockSampler:
                  "-lms", "200", "-i", self.idx], stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < wait_s:
+            if self.proc.poll() is not None:
+                break
+            try:
+                if os.path.getsize(self.path) > 0:
+                    break
+            except OSError:
+                pass
+            time.sleep(0.05)
 
     def stop(self):
         if self.proc is None:
@@ -294,6 +307,7 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -340,7 +354,8 @@ def main() -> None:
     sim.sync()
 
     clocks = ClockSampler(local)
-    clocks.start()
+    if not args.no_clocks:
+        clocks.start()
     barrier()
     torch.cuda.synchronize()
     launches0 = sim.launches

@@ -155,6 +155,7 @@ static KParams<R> make_kparams(const pf_params& p) {
   k.k = (R)p.k;
   k.D = (R)p.D;
   k.g = (R)p.g;
+  k.inv_omk = (R)(1.0 / (1.0 - p.k));
   k.s_e = (R)p.s_e;
   k.s_eps = (R)p.s_eps;
   k.s_q = (R)(8.0 * (2.0 - s_nu) / (8.0 - s_nu));
@@ -320,6 +321,12 @@ extern "C" pf_status pf_create(const pf_params* p, const pf_domain* doms, int n_
   }
   h->plane_stride = off;
   const size_t ps = (size_t)off;
+  // the step kernel addresses every buffer with 32-bit element offsets
+  if ((unsigned long long)ps * std::max<int>(N_POP, std::max<int>(N_AUX, N_FIELDS)) >= (1ull << 32)) {
+    g_create_err = "too many sites for one handle (at most ~130 million)";
+    delete h;
+    return PF_ERR_BAD_ARG;
+  }
 
   auto bail = [&](pf_status code, const char* msg) {
     g_create_err = msg;

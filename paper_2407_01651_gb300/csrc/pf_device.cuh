@@ -42,15 +42,22 @@ constexpr float kNSScale = 4096.0f;      // NS populations x 2^12 in the 16-bit 
 constexpr float kNSInvScale = 1.0f / 4096.0f;
 
 
-template <typename R, typename S>
-__device__ __forceinline__ R ld(const S* __restrict__ p, long long i) {
+template <typename R, typename S, typename I>
+__device__ __forceinline__ R ld(const S* __restrict__ p, I i) {
   return Codec<S>::template dec<R>(__ldg(p + i));
 }
 
-template <typename S, typename R>
-__device__ __forceinline__ void st(S* __restrict__ p, long long i, R v) {
+template <typename S, typename R, typename I>
+__device__ __forceinline__ void st(S* __restrict__ p, I i, R v) {
   p[i] = Codec<S>::template enc<R>(v);
 }
+
+// Reciprocal and reciprocal square root: IEEE in FP64; in FP32 the hardware
+// approximations (relative error a few 1e-7), far inside the FP32 tolerance.
+__device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double frsqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float frsqrt(float x) { return rsqrtf(x); }
 
 // Weights of the D2Q9 / D2Q5 lattices in the compute type.
 template <typename R>
@@ -64,23 +71,23 @@ __device__ __forceinline__ R w5(int i) {
 
 // Physical value <-> stored value of one population.  kind: 0 NS (scaled in
 // the 16-bit forms), 1 offset from w M_o (the caller passes w M_o).
-template <typename S, typename R>
-__device__ __forceinline__ R pop_ns(const S* __restrict__ p, long long i) {
+template <typename S, typename R, typename I>
+__device__ __forceinline__ R pop_ns(const S* __restrict__ p, I i) {
   if constexpr (Codec<S>::kOffset) return ld<R>(p, i) * R(kNSInvScale);
   else return ld<R>(p, i);
 }
-template <typename S, typename R>
-__device__ __forceinline__ void st_ns(S* __restrict__ p, long long i, R v) {
+template <typename S, typename R, typename I>
+__device__ __forceinline__ void st_ns(S* __restrict__ p, I i, R v) {
   if constexpr (Codec<S>::kOffset) st(p, i, v * R(kNSScale));
   else st(p, i, v);
 }
-template <typename S, typename R>
-__device__ __forceinline__ R pop_off(const S* __restrict__ p, long long i, R wm) {
+template <typename S, typename R, typename I>
+__device__ __forceinline__ R pop_off(const S* __restrict__ p, I i, R wm) {
   if constexpr (Codec<S>::kOffset) return wm + ld<R>(p, i);
   else return ld<R>(p, i);
 }
-template <typename S, typename R>
-__device__ __forceinline__ void st_off(S* __restrict__ p, long long i, R v, R wm) {
+template <typename S, typename R, typename I>
+__device__ __forceinline__ void st_off(S* __restrict__ p, I i, R v, R wm) {
   if constexpr (Codec<S>::kOffset) st(p, i, v - wm);
   else st(p, i, v);
 }
@@ -91,9 +98,11 @@ __device__ __forceinline__ void st_off(S* __restrict__ p, long long i, R v, R wm
 template <typename R>
 struct CSum {
   R s = R(0), c = R(0);
+  // Fast2Sum: the first term added (the rest population, weight 1/3 or 4/9)
+  // is the largest, so |s| >= |v| holds for the later terms.
   __device__ __forceinline__ void add(R v) {
     const R t = s + v;
-    c += (fabs(s) >= fabs(v)) ? ((s - t) + v) : ((v - t) + s);
+    c += (s - t) + v;
     s = t;
   }
   __device__ __forceinline__ R value() const { return s + c; }

@@ -69,6 +69,7 @@ struct KParams {
   R inv_tau0, c_s1;         // 1/tau0, 3 W0^2 / tau0
   R W0, a_at;               // W0, a(psi) = 1/(2 sqrt2)
   R k, D, g;
+  R inv_omk;                // 1 / (1 - k)
   R s_e, s_eps, s_q, s_nu, s_phi;
 };
 

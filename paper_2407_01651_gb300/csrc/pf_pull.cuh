@@ -11,15 +11,16 @@ namespace pf {
 // Source sites of the pull for the 9 D2Q9 directions at (x, y):
 // src[i] = (x - cx_i, y - cy_i), periodic.
 struct Src9 {
-  long long s[9];
+  unsigned s[9];   // element offsets (a handle holds < 2^32 elements per buffer)
 };
 
 __device__ __forceinline__ Src9 sources(const DomDesc& d, int x, int y) {
   const int nx = d.nx, ny = d.ny;
   const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
   const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-  const long long r0 = d.off + (long long)y * nx, rm = d.off + (long long)ym * nx,
-                  rp = d.off + (long long)yp * nx;
+  const unsigned off = (unsigned)d.off;
+  const unsigned r0 = off + (unsigned)(y * nx), rm = off + (unsigned)(ym * nx),
+                 rp = off + (unsigned)(yp * nx);
   Src9 o;
   o.s[0] = r0 + x; o.s[1] = r0 + xm; o.s[2] = rm + x; o.s[3] = r0 + xp; o.s[4] = rp + x;
   o.s[5] = rm + xm; o.s[6] = rm + xp; o.s[7] = rp + xp; o.s[8] = rp + xm;
@@ -34,25 +35,25 @@ __device__ __forceinline__ Src9 sources(const DomDesc& d, int x, int y) {
 template <typename S, typename R>
 __device__ __forceinline__ void pull_hg(const StepArgs<S, R>& a, const Src9& src, R h[9],
                                         R g[5], R& phi, R& psi, R& psio) {
-  const long long ps = a.plane_stride;
+  const unsigned ps = (unsigned)a.plane_stride;
   constexpr bool off = Codec<S>::kOffset;
   CSum<R> sh;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    const R wm = off ? w9<R>(i) * ld<R>(a.ain + A_PHIO * ps, src.s[i]) : R(0);
-    h[i] = pop_off<S, R>(a.in + (P_H + i) * ps, src.s[i], wm);
+    const R wm = off ? w9<R>(i) * ld<R>(a.ain, A_PHIO * ps + src.s[i]) : R(0);
+    h[i] = pop_off<S, R>(a.in, (P_H + i) * ps + src.s[i], wm);
     sh.add(h[i]);
   }
   phi = sh.value();
   CSum<R> sg;
   R po = R(0);
-  const R psio_own = off ? ld<R>(a.ain + A_PSIO * ps, src.s[0]) : R(0);
+  const R psio_own = off ? ld<R>(a.ain, A_PSIO * ps + src.s[0]) : R(0);
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    const R gold = pop_off<S, R>(a.in + (P_GPRE + i) * ps, src.s[0], w5<R>(i) * psio_own);
-    const R wm = off ? w5<R>(i) * ld<R>(a.ain + A_PSIO * ps, src.s[i]) : R(0);
-    const R gpo = pop_off<S, R>(a.in + (P_GPOST + i) * ps, src.s[i], wm);
-    const R rr = ld<R>(a.ain + A_RR * ps, src.s[i]);
+    const R gold = pop_off<S, R>(a.in, (P_GPRE + i) * ps + src.s[0], w5<R>(i) * psio_own);
+    const R wm = off ? w5<R>(i) * ld<R>(a.ain, A_PSIO * ps + src.s[i]) : R(0);
+    const R gpo = pop_off<S, R>(a.in, (P_GPOST + i) * ps + src.s[i], wm);
+    const R rr = ld<R>(a.ain, A_RR * ps + src.s[i]);
     g[i] = gold + (gpo - gold) * rr;
     sg.add(g[i]);
     po += gold;
@@ -81,18 +82,18 @@ struct SiteIn {
 template <typename S, typename R>
 __device__ __forceinline__ void load_site(const StepArgs<S, R>& a, const Src9& src,
                                           SiteIn<R>& in) {
-  const long long ps = a.plane_stride;
+  const unsigned ps = (unsigned)a.plane_stride;
   constexpr bool off = Codec<S>::kOffset;
 #pragma unroll
-  for (int i = 0; i < 9; ++i) in.f[i] = pop_ns<S, R>(a.in + (P_F + i) * ps, src.s[i]);
+  for (int i = 0; i < 9; ++i) in.f[i] = pop_ns<S, R>(a.in, (P_F + i) * ps + src.s[i]);
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    const R wm = off ? w5<R>(i) * ld<R>(a.ain + A_CO * ps, src.s[i]) : R(0);
-    in.s[i] = pop_off<S, R>(a.in + (P_S + i) * ps, src.s[i], wm);
+    const R wm = off ? w5<R>(i) * ld<R>(a.ain, A_CO * ps + src.s[i]) : R(0);
+    in.s[i] = pop_off<S, R>(a.in, (P_S + i) * ps + src.s[i], wm);
   }
-  in.phio = ld<R>(a.ain + A_PHIO * ps, src.s[0]);
-  in.Co = ld<R>(a.ain + A_CO * ps, src.s[0]);
-  in.Qo = ld<R>(a.ain + A_QO * ps, src.s[0]);
+  in.phio = ld<R>(a.ain, A_PHIO * ps + src.s[0]);
+  in.Co = ld<R>(a.ain, A_CO * ps + src.s[0]);
+  in.Qo = ld<R>(a.ain, A_QO * ps + src.s[0]);
   in.gid = a.grain[src.s[0]];
 }
 

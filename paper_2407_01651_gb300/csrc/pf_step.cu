@@ -20,9 +20,9 @@ __device__ __forceinline__ void site_update(const StepArgs<S, R>& a, const DomDe
                                             const R (&h_in)[9], const R (&g_in)[5], R psio,
                                             Rows3<R> SP, Rows3<R> SS, Rows3<R> SVX,
                                             Rows3<R> SVY, int c) {
-  const long long ps = a.plane_stride;
+  const unsigned ps = (unsigned)a.plane_stride;
   const KParams<R>& kp = a.kp;
-  const long long site = src.s[0];
+  const unsigned site = src.s[0];
   R f[9], h[9], g[5], s[5];
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
@@ -75,7 +75,7 @@ __device__ __forceinline__ void site_update(const StepArgs<S, R>& a, const DomDe
   // ---- gas-liquid interface, forces ----
   const R rho = kp.rho_g + phi * kp.drho;
   const R grx = kp.drho * gpx, gry = kp.drho * gpy;
-  const R igm = R(1) / sqrt(gpx * gpx + gpy * gpy + kp.ge2);
+  const R igm = frsqrt(gpx * gpx + gpy * gpy + kp.ge2);
   const R nfx = gpx * igm, nfy = gpy * igm;
   const R opsi = R(1) + psi, ophi = R(1) - phi;
   const R mu = kp.two_bphi * phi * ophi * (R(1) - R(2) * phi) - kp.two_bint * ophi * opsi * opsi -
@@ -93,7 +93,7 @@ __device__ __forceinline__ void site_update(const StepArgs<S, R>& a, const DomDe
   const R jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
   const R sum_nz = f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
   const R Fpx = Fsx + Fmx, Fpy = Fsy + Fby + Fmy;
-  const R irho = R(1) / rho;
+  const R irho = frcp(rho);
   const R vsx = (jx + R(0.5) * Fpx) * irho, vsy = (jy + R(0.5) * Fpy) * irho;
   const R chi = R(0.5) * opsi;
   const R vx = (R(1) - chi) * vsx, vy = (R(1) - chi) * vsy;
@@ -108,8 +108,8 @@ __device__ __forceinline__ void site_update(const StepArgs<S, R>& a, const DomDe
   const R eps = static_cast<R>(d.eps_s);
   const R gxr = ct * gsx + sn * gsy, gyr = -sn * gsx + ct * gsy;
   const R gm2 = gsx * gsx + gsy * gsy;
-  const R smag = sqrt(gm2 + kp.ge2);
-  const R ism = R(1) / smag;
+  const R ism = frsqrt(gm2 + kp.ge2);
+  const R smag = (gm2 + kp.ge2) * ism;
   const R nxr = -gxr * ism, nyr = -gyr * ism;
   const R nx2 = nxr * nxr, ny2 = nyr * nyr;
   const R n2 = nx2 + ny2;
@@ -120,18 +120,18 @@ __device__ __forceinline__ void site_update(const StepArgs<S, R>& a, const DomDe
   const R Nxr = pre * nxr * (nx2 - iso), Nyr = pre * nyr * (ny2 - iso);
   const R Nx = ct * Nxr - sn * Nyr, Ny = sn * Nxr + ct * Nyr;
   const R as2 = as * as;
-  const R ias2 = R(1) / as2;
+  const R ias2 = frcp(as2);
 
   // ---- solute and dendrite sources ----
   const R omk = R(1) - kp.k;
   const R A = R(1) + kp.k - omk * psi;
-  const R iA = R(1) / A;
-  const R U = (R(2) * C * iA - R(1)) / omk;
+  const R iA = frcp(A);
+  const R U = (R(2) * C * iA - R(1)) * kp.inv_omk;
   const R omp2 = R(1) - psi * psi;
   const R Q = kp.four_bpsi * psi * omp2 - kp.two_bint * ophi * ophi * opsi -
               kp.lam * omp2 * omp2 * (kp.theta + kp.Mcinf * U);
   const R dpsi = psi - psio;
-  const R at = -kp.a_at * kp.W0 * as * (R(1) + omk * U) * dpsi / sqrt(gm2 + kp.gat2);
+  const R at = -kp.a_at * kp.W0 * as * (R(1) + omk * U) * dpsi * frsqrt(gm2 + kp.gat2);
   const R qf = R(0.5) * (R(1) - psi);
   const R jv = kp.D * qf * C * kp.kappa * ophi;
 
@@ -145,7 +145,7 @@ __device__ __forceinline__ void site_update(const StepArgs<S, R>& a, const DomDe
   R gpost[5];
   {
     const R Fs = (Q + R(0.5) * (Q - Qo)) * kp.inv_tau0;
-    const R s1 = R(1) / (kp.c_s1 * as2 + R(0.5));
+    const R s1 = frcp(kp.c_s1 * as2 + R(0.5));
 #pragma unroll
     for (int i = 0; i < 5; ++i) gpost[i] = g[i];
     collide_q5(gpost, psi + Fs, s1, R(0), R(0), R(-1.0 / 3.0) * Nx * ias2,
@@ -156,21 +156,21 @@ __device__ __forceinline__ void site_update(const StepArgs<S, R>& a, const DomDe
     const R jex = C * vx - E * gsx + omk * (at * gsx + jv * nfx);
     const R jey = C * vy - E * gsy + omk * (at * gsy + jv * nfy);
     const R DC = R(2) * kp.D * qf * iA;
-    const R sc = R(1) / (R(3) * DC + R(0.5));
+    const R sc = frcp(R(3) * DC + R(0.5));
     collide_q5(s, C, sc, jex, jey, C * vx - Co * vxo, C * vy - Co * vyo);
   }
 
   // ---- store ----
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    st_ns<S, R>(a.out + (P_F + i) * ps, site, f[i]);
-    st_off<S, R>(a.out + (P_H + i) * ps, site, h[i], w9<R>(i) * phi);
+    st_ns<S, R>(a.out, (P_F + i) * ps + site, f[i]);
+    st_off<S, R>(a.out, (P_H + i) * ps + site, h[i], w9<R>(i) * phi);
   }
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    st_off<S, R>(a.out + (P_GPRE + i) * ps, site, g[i], w5<R>(i) * psi);
-    st_off<S, R>(a.out + (P_GPOST + i) * ps, site, gpost[i], w5<R>(i) * psi);
-    st_off<S, R>(a.out + (P_S + i) * ps, site, s[i], w5<R>(i) * C);
+    st_off<S, R>(a.out, (P_GPRE + i) * ps + site, g[i], w5<R>(i) * psi);
+    st_off<S, R>(a.out, (P_GPOST + i) * ps + site, gpost[i], w5<R>(i) * psi);
+    st_off<S, R>(a.out, (P_S + i) * ps + site, s[i], w5<R>(i) * C);
   }
   a.aout[A_RR * ps + site] = ias2;
   a.aout[A_PHIO * ps + site] = phi;
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(256) k_step_tile(StepArgs<S, R> a) {
   R* svy = svx + SW * SH;
   const int tid = threadIdx.y * TX + threadIdx.x;
   const int nthr = TX * TY;
-  const long long ps = a.plane_stride;
+  const unsigned ps = (unsigned)a.plane_stride;
 
   for (int tile = a.tile_base + blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     const DomDesc d = a.doms[a.tile_dom[tile]];
@@ -220,9 +220,9 @@ __global__ void __launch_bounds__(256) k_step_tile(StepArgs<S, R> a) {
       pull_hg(a, sources(d, gx, gy), h, g, phi, psi, po);
       sphi[i] = phi;
       spsi[i] = psi;
-      const long long site = d.off + (long long)gy * nx + gx;
-      svx[i] = ld<R>(a.ain + A_VXO * ps, site);
-      svy[i] = ld<R>(a.ain + A_VYO * ps, site);
+      const unsigned site = (unsigned)d.off + (unsigned)(gy * nx + gx);
+      svx[i] = ld<R>(a.ain, A_VXO * ps + site);
+      svy[i] = ld<R>(a.ain, A_VYO * ps + site);
     }
     __syncthreads();
 
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 3 : 2) k_step_yma
   constexpr int RW = YM_W + 2;
   __shared__ R ring[4][4][RW];  // [phi, psi, vx_o, vy_o][slot][column]
   const int t = threadIdx.x;
-  const long long ps = a.plane_stride;
+  const unsigned ps = (unsigned)a.plane_stride;
 
   for (int tile = a.tile_base + blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     const DomDesc d = a.doms[a.tile_dom[tile]];
@@ -292,8 +292,8 @@ __global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 3 : 2) k_step_yma
         pull_hg(a, src, h, g, phi, psi, po);
         ring[0][slot][sc] = phi;
         ring[1][slot][sc] = psi;
-        ring[2][slot][sc] = ld<R>(a.ain + A_VXO * ps, src.s[0]);
-        ring[3][slot][sc] = ld<R>(a.ain + A_VYO * ps, src.s[0]);
+        ring[2][slot][sc] = ld<R>(a.ain, A_VXO * ps + src.s[0]);
+        ring[3][slot][sc] = ld<R>(a.ain, A_VYO * ps + src.s[0]);
         if (k == 1) {
 #pragma unroll
           for (int i = 0; i < 9; ++i) hC[i] = h[i];
@@ -319,8 +319,8 @@ __global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 3 : 2) k_step_yma
         const int slot = (j + 1) & 3;
         ring[0][slot][sc] = phi;
         ring[1][slot][sc] = psi;
-        ring[2][slot][sc] = ld<R>(a.ain + A_VXO * ps, src.s[0]);
-        ring[3][slot][sc] = ld<R>(a.ain + A_VYO * ps, src.s[0]);
+        ring[2][slot][sc] = ld<R>(a.ain, A_VXO * ps + src.s[0]);
+        ring[3][slot][sc] = ld<R>(a.ain, A_VYO * ps + src.s[0]);
       }
       __syncthreads();
       if (interior) {
