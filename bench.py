@@ -38,7 +38,8 @@ BYTES_PER_LU = {"fp32": 39 * 4 * 2 + 1, "fp64": 39 * 8 * 2 + 1,
 DTYPE = {"fp32": "f32", "fp64": "f64", "fp16": "f16-storage/f32", "bf16": "bf16-storage/f32"}
 KERNEL_SOURCES = ("paper_2407_01651_gb300/csrc/pf_step.cu",
                   "paper_2407_01651_gb300/csrc/pf_device.cuh",
-                  "paper_2407_01651_gb300/csrc/pf_model.cuh")
+                  "paper_2407_01651_gb300/csrc/pf_model.cuh",
+                  "paper_2407_01651_gb300/csrc/pf_pull.cuh")
 
 
 def kernel_hash() -> str:
