@@ -112,22 +112,22 @@ def random_layout(nx: int, ny: int, n_seeds: int, n_bubbles: int, rng_seed: int,
     return Layout(nx, ny, seeds=seeds, bubbles=bubbles)
 
 
-def cfg1_layout() -> Layout:
+def seed_bubble_128() -> Layout:
     """128 x 128, one centred seed, one R=16 bubble at a seed-drawn offset."""
     return single_seed_bubble(128, 128, rng_seed=1)
 
 
-def cfg2_layout(nx: int = 4096, ny: int = 4096) -> Layout:
+def growth_lattice(nx: int = 4096, ny: int = 4096) -> Layout:
     """4096 x 4096, 64 seeds, 128 non-overlapping bubbles, R in [8, 40]."""
     return random_layout(nx, ny, 64, 128, rng_seed=2)
 
 
-def cfg4_layout(n: int = 512, rng_seed: int = 4) -> Layout:
+def growth_512(n: int = 512, rng_seed: int = 4) -> Layout:
     """512 x 512 (or n x n), 4 seeds and 8 bubbles."""
     return random_layout(n, n, 4, 8, rng_seed=rng_seed, R_max=min(40.0, n / 8))
 
 
-def cfg5_layouts(rng_seed: int = 5) -> list[Layout]:
+def ensemble_96(rng_seed: int = 5) -> list[Layout]:
     """96 uneven domains: 32 each of 256x256, 512x384, 1024x512; per-domain
     seeds, 1..6 bubbles and eps_s uniform in [0.02, 0.07]."""
     rng = SplitMix64(rng_seed)

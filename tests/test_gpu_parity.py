@@ -102,7 +102,7 @@ def test_few_steps_with_rotated_grains_and_gravity(precision, tol):
 def test_fp64_thousand_steps_128(tmp_path):
     """The 128^2 workload: same-step compare every 100 steps over 1000 steps,
     and conservation of gas and solute to 1e-10 in the FP64 reductions."""
-    lay = wl.cfg1_layout()
+    lay = wl.seed_bubble_128()
     o, sim = pair(lay, "fp64")
     d0 = sim.reduce(0)
     worst = {}
@@ -122,7 +122,7 @@ def test_fp64_thousand_steps_128(tmp_path):
 
 def test_fp32_error_against_fp64_oracle_over_steps():
     """FP32 per-step error stays at 1e-5; over 100 steps it stays bounded."""
-    lay = wl.cfg1_layout()
+    lay = wl.seed_bubble_128()
     o, sim = pair(lay, "fp32")
     o.step(1)
     sim.step(1)
@@ -137,7 +137,7 @@ def test_fp32_per_step_error_on_a_developed_state():
     follows the oracle to 1e-9 over 1000 steps, test above) advances the 128^2
     workload 500 steps; its state rounded to FP32 takes one FP32 step and is
     compared with one more FP64 step."""
-    lay = wl.cfg1_layout()
+    lay = wl.seed_bubble_128()
     a = pf.Simulation([(lay.nx, lay.ny)], lay.params, "fp64")
     a.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
     a.step(500)
@@ -313,7 +313,7 @@ def test_full_size_4096_sampled_against_oracle_windows():
     """The 4096^2 FP32 workload in the launch configuration the benchmark
     times: after 2 steps, sites sampled near seeds and bubbles match oracle
     windows (global coordinates, full-lattice rho_bar computed by the oracle)."""
-    lay = wl.cfg2_layout()
+    lay = wl.growth_lattice()
     sim = pf.Simulation([(lay.nx, lay.ny)], lay.params, "fp32")
     sim.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
     T = 2

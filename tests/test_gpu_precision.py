@@ -28,7 +28,7 @@ def rel(a, b):
 def test_offset_storage_starts_exact(precision):
     """At the initial equilibrium every offset is zero, so the 16-bit state
     decodes to the FP32 state exactly."""
-    lay = wl.cfg1_layout()
+    lay = wl.seed_bubble_128()
     a = pf.Simulation([(lay.nx, lay.ny)], lay.params, "fp32")
     b = pf.Simulation([(lay.nx, lay.ny)], lay.params, precision)
     for s in (a, b):
@@ -52,7 +52,7 @@ def test_offset_storage_against_oracle(precision):
     bad = {k: v for k, v in errs.items() if v > BOUND_100[precision][k]}
     assert not bad, (bad, errs)
     d = sim.reduce(0)
-    # gas and solute totals drift only by the FP32 arithmetic (see DESIGN)
+    # gas and solute totals drift only by the FP32 arithmetic of the step
     assert abs(d["sum_phi"] / d0["sum_phi"] - 1) < 1e-5
     assert abs(d["sum_C"] / d0["sum_C"] - 1) < 1e-5
 
