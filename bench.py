@@ -39,7 +39,9 @@ DTYPE = {"fp32": "f32", "fp64": "f64", "fp16": "f16-storage/f32", "bf16": "bf16-
 KERNEL_SOURCES = ("paper_2407_01651_gb300/csrc/pf_step.cu",
                   "paper_2407_01651_gb300/csrc/pf_device.cuh",
                   "paper_2407_01651_gb300/csrc/pf_model.cuh",
-                  "paper_2407_01651_gb300/csrc/pf_pull.cuh")
+                  "paper_2407_01651_gb300/csrc/pf_pull.cuh",
+                  "paper_2407_01651_gb300/csrc/pf_site.cuh",
+                  "paper_2407_01651_gb300/csrc/pf_step_staged.cu")
 
 
 def kernel_hash() -> str:

@@ -15,7 +15,7 @@ constexpr int REDUCE_BLOCKS = 1024;  // blocks of the first reduction pass
 constexpr int MAX_GRAINS = 256;      // grain ids are uint8
 
 // Step kernel variants (same arithmetic, different traversal).
-enum StepVariant : int { STEP_TILE = 0, STEP_YMARCH = 1 };
+enum StepVariant : int { STEP_TILE = 0, STEP_YMARCH = 1, STEP_STAGED = 2 };
 constexpr int YM_W = 128;            // interior columns of a y-march strip
 constexpr int YM_THREADS = YM_W + 32;  // + one warp whose lanes 0, 1 own the halo columns
 
@@ -34,6 +34,7 @@ struct StepArgs {
   int ntiles;                   // one past the last tile of this launch
   int chunk;                    // rows per y-march tile
   R* fields;                    // 8 field planes, or nullptr
+  unsigned int* err;            // device error bits (1: a staged copy timed out), or nullptr
   KParams<R> kp;
 };
 
@@ -77,6 +78,17 @@ struct ReduceArgs {
 template <typename S, typename R>
 cudaError_t launch_step(const StepArgs<S, R>& a, int variant, int tx, int ty, int grid,
                         cudaStream_t st);
+// Staged variant (bulk copies of the input rows into shared memory): launch,
+// dynamic shared memory, the x granularity it needs (nx a multiple of it), and
+// resident CTAs per SM.
+template <typename S, typename R>
+cudaError_t launch_step_staged(const StepArgs<S, R>& a, int grid, cudaStream_t st);
+template <typename S, typename R>
+int staged_smem_bytes();
+template <typename S, typename R>
+int staged_halo_columns();
+template <typename S, typename R>
+int staged_blocks_per_sm();
 // Resident CTAs per SM of the step kernel (for persistent grids).
 template <typename S, typename R>
 int step_blocks_per_sm(int variant, int tx, int ty);

@@ -245,7 +245,10 @@ class Simulation:
         _check(lib().pf_step(self.h, int(n)), self.h)
 
     def set_step_config(self, variant: int, a: int, b: int = 0) -> None:
-        """variant 0: 2-D tiles a x b; variant 1: y-march strips, a rows per tile."""
+        """variant 0: 2-D tiles a x b; variant 1: y-march strips, a rows per tile;
+        variant 2: y-march strips with the input rows staged in shared memory by
+        bulk copies, a rows per tile (needs nx a multiple of 16 bytes of storage
+        in every domain)."""
         _check(lib().pf_set_step_config(self.h, int(variant), int(a), int(b)), self.h)
 
     def set_launch(self, per_domain: bool = False, persistent: bool = False,

@@ -343,3 +343,72 @@ def test_full_size_4096_sampled_against_oracle_windows():
         r, g = np.concatenate(ref[k]), np.concatenate(got[k])
         err = rel(g, r, FLOOR[k])
         assert err <= 1e-5 * EARLY_FLOW_FACTOR.get(k, 1.0), (k, err)
+
+
+# ---------------------------------------------------------------------------
+# Staged traversal (bulk copies of the input rows into shared memory)
+# ---------------------------------------------------------------------------
+def staged_layout():
+    # 136 x 52: two strips, the second 8 columns wide; nx is a multiple of
+    # 16 bytes of storage in every precision
+    return wl.random_layout(136, 52, 2, 2, rng_seed=23, R_max=10)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+@pytest.mark.parametrize("chunk", [1, 3, 16, 128])
+def test_staged_traversal_matches_oracle(precision, tol, chunk):
+    lay = staged_layout()
+    o, sim = pair(lay, precision)
+    sim.set_step_config(2, chunk)
+    assert sim.step_config()[:2] == (2, chunk)
+    o.step(3)
+    sim.step(3)
+    compare_fields(o, sim, tol, early=True)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16", "bf16"])
+def test_staged_equals_ymarch(precision):
+    """Same per-site arithmetic, inputs from shared memory instead of global
+    loads: the staged and the plain y-march traversals give the same state."""
+    lay = wl.random_layout(256, 96, 3, 3, rng_seed=29, R_max=12)
+    sims = []
+    for variant in (1, 2):
+        s = pf.Simulation([(lay.nx, lay.ny)], lay.params, precision)
+        s.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
+        s.set_step_config(variant, 24)
+        s.step(40)
+        sims.append(s)
+    fa, fb = sims[0].fields(), sims[1].fields()
+    for k in FIELDS:
+        scale = max(np.abs(fa[k]).max(), FLOOR[k])
+        assert np.abs(fa[k] - fb[k]).max() <= 1e-6 * scale, k
+
+
+def test_staged_small_and_multi_domain():
+    """Smallest eligible widths (one strip narrower than the 128 columns, x
+    halos wrapping onto the same strip), short domains, several domains in
+    one launch, FP64 against the oracle."""
+    lays = [wl.Layout(8, 4, seeds=[(4.0, 2.0, 0.3)], bubbles=[]),
+            wl.Layout(16, 9, seeds=[(8.0, 4.0, 0.1)], bubbles=[]),
+            wl.random_layout(264, 40, 1, 1, rng_seed=31, R_min=4, R_max=6)]
+    sim = pf.Simulation([(l.nx, l.ny) for l in lays], wl.BASE_PARAMS, "fp64")
+    for d, l in enumerate(lays):
+        sim.init_fields(d, l.seeds, l.R_s, l.bubbles)
+    sim.set_step_config(2, 5)
+    sim.step(3)
+    for d, l in enumerate(lays):
+        o = oracle.Oracle(l.nx, l.ny, wl.BASE_PARAMS)
+        o.init_spec(l.seeds, l.R_s, l.bubbles)
+        o.step(3)
+        compare_fields(o, sim, 1e-11, dom=d)
+
+
+def test_staged_rejects_ineligible_widths():
+    lay = small_layout()   # nx = 70: not a multiple of 4 FP32 sites
+    sim = pf.Simulation([(lay.nx, lay.ny)], lay.params, "fp32")
+    with pytest.raises(pf.PFError) as e:
+        sim.set_step_config(2, 16)
+    assert e.value.code == pf.PF_ERR_BAD_ARG
+    sim16 = pf.Simulation([(20, 16)], lay.params, "fp16")   # 20 % 8 != 0
+    with pytest.raises(pf.PFError):
+        sim16.set_step_config(2, 16)
