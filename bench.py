@@ -41,6 +41,7 @@ KERNEL_SOURCES = ("paper_2407_01651_gb300/csrc/pf_step.cu",
                   "paper_2407_01651_gb300/csrc/pf_model.cuh",
                   "paper_2407_01651_gb300/csrc/pf_pull.cuh",
                   "paper_2407_01651_gb300/csrc/pf_site.cuh",
+                  "paper_2407_01651_gb300/csrc/pf_v2.cuh",
                   "paper_2407_01651_gb300/csrc/pf_step_staged.cu")
 
 

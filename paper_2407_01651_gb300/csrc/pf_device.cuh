@@ -59,6 +59,17 @@ __device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double frsqrt(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float frsqrt(float x) { return rsqrtf(x); }
 
+// Plane k of a plane-major buffer: a warp-uniform base pointer, so that one
+// per-thread element offset serves every plane of a site.
+template <typename T>
+__device__ __forceinline__ const T* plane(const T* p, int k, unsigned ps) {
+  return p + (size_t)k * ps;
+}
+template <typename T>
+__device__ __forceinline__ T* plane(T* p, int k, unsigned ps) {
+  return p + (size_t)k * ps;
+}
+
 // Weights of the D2Q9 / D2Q5 lattices in the compute type.
 template <typename R>
 __device__ __forceinline__ R w9(int i) {

@@ -12,6 +12,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "pf_v2.cuh"
+
 namespace pf {
 
 // ---------------------------------------------------------------------------
@@ -96,57 +98,39 @@ __device__ __forceinline__ void feq_ns(R p, R rho, R vx, R vy, R f[9]) {
 }
 
 // ---------------------------------------------------------------------------
-// D2Q9 moment transforms (Lallemand-Luo order rho, e, eps, jx, qx, jy, qy,
-// pxx, pxy) and the inverse via M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12,
-// 1/6, 1/12, 1/4, 1/4).
+// Collisions.  Moments follow the Lallemand-Luo order (rho, e, eps, jx, qx,
+// jy, qy, pxx, pxy); the back-transform is M^-1 = M^T diag(1/9, 1/36, 1/36,
+// 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).  Both transforms are written on the
+// opposite-direction pairs (f1, f2) / (f3, f4) and (f5, f6) / (f7, f8) and on
+// (x, y) pairs of moments, so that the FP32 build issues paired instructions.
 // ---------------------------------------------------------------------------
-template <typename R>
-__device__ __forceinline__ void m9_from_f(const R f[9], R m[9]) {
-  const R a14 = f[1] + f[2] + f[3] + f[4];
-  const R a58 = f[5] + f[6] + f[7] + f[8];
-  m[0] = f[0] + a14 + a58;
-  m[1] = R(-4) * f[0] - a14 + R(2) * a58;
-  m[2] = R(4) * f[0] - R(2) * a14 + a58;
-  const R dx = f[5] - f[6] - f[7] + f[8];
-  const R dy = f[5] + f[6] - f[7] - f[8];
-  m[3] = f[1] - f[3] + dx;
-  m[4] = R(-2) * (f[1] - f[3]) + dx;
-  m[5] = f[2] - f[4] + dy;
-  m[6] = R(-2) * (f[2] - f[4]) + dy;
-  m[7] = f[1] - f[2] + f[3] - f[4];
-  m[8] = f[5] - f[6] + f[7] - f[8];
-}
 
+// Populations f1..f8 from the moments, given as the scalars of the rest/energy
+// group (m0/9, m1/36, m2/36 folded into axis, diag, f0), the flux pairs
+// DF = (m3, m5)/6 and EG = (m4, m6)/12, and h = m7/4, k = m8/4.
 template <typename R>
-__device__ __forceinline__ void f_from_m9(const R m[9], R f[9]) {
-  const R a = m[0] * R(1.0 / 9.0), b = m[1] * R(1.0 / 36.0), c = m[2] * R(1.0 / 36.0);
-  const R d = m[3] * R(1.0 / 6.0), e = m[4] * R(1.0 / 12.0);
-  const R fy = m[5] * R(1.0 / 6.0), gy = m[6] * R(1.0 / 12.0);
-  const R h = m[7] * R(0.25), k = m[8] * R(0.25);
-  const R axis = a - b - R(2) * c;
-  const R diag = a + R(2) * b + c;
-  f[0] = a - R(4) * b + R(4) * c;
-  f[1] = axis + d - R(2) * e + h;
-  f[2] = axis + fy - R(2) * gy - h;
-  f[3] = axis - d + R(2) * e + h;
-  f[4] = axis - fy + R(2) * gy - h;
-  f[5] = diag + d + e + fy + gy + k;
-  f[6] = diag - d - e + fy + gy - k;
-  f[7] = diag - d - e - fy - gy + k;
-  f[8] = diag + d + e - fy - gy - k;
+__device__ __forceinline__ void f_from_moments(R axis, R diag, V2<R> DF, V2<R> EG, R h, R k,
+                                               R f[9]) {
+  const V2<R> Q = fma(R(-2), EG, DF);            // (d - 2e, fy - 2gy)
+  const V2<R> A = vec2(axis + h, axis - h);
+  const V2<R> f12 = A + Q, f34 = A - Q;
+  const V2<R> S = DF + EG;                       // (d + e, fy + gy)
+  const R P = S.x + k, N = S.x - k;
+  const V2<R> f56 = splat(diag + S.y) + vec2(P, -P);
+  const V2<R> f78 = splat(diag - S.y) + vec2(-N, N);
+  f[1] = f12.x; f[2] = f12.y; f[3] = f34.x; f[4] = f34.y;
+  f[5] = f56.x; f[6] = f56.y; f[7] = f78.x; f[8] = f78.y;
 }
 
 // D2Q5 post-collision populations from (m0, jx, jy) with the energy moment at
 // -(2/3) m0 and the anisotropic moment at 0 (their equilibria, rate 1):
 // s_0 = m0/3, s_{1,3} = m0/6 +- jx/2, s_{2,4} = m0/6 +- jy/2.
 template <typename R>
-__device__ __forceinline__ void q5_from_m(R m0, R jx, R jy, R s[5]) {
-  const R a = m0 * R(1.0 / 6.0);
+__device__ __forceinline__ void q5_from_m(R m0, V2<R> J, R s[5]) {
+  const V2<R> a = splat(m0 * R(1.0 / 6.0));
+  const V2<R> s12 = fma(R(0.5), J, a), s34 = fma(R(-0.5), J, a);
   s[0] = m0 * R(1.0 / 3.0);
-  s[1] = a + R(0.5) * jx;
-  s[3] = a - R(0.5) * jx;
-  s[2] = a + R(0.5) * jy;
-  s[4] = a - R(0.5) * jy;
+  s[1] = s12.x; s[2] = s12.y; s[3] = s34.x; s[4] = s34.y;
 }
 
 // NS collision, D2Q9 MRT with forcing through (I - S/2):
@@ -154,63 +138,71 @@ __device__ __forceinline__ void q5_from_m(R m0, R jx, R jy, R s[5]) {
 // m_eq = (0, 6p + 3 rho v^2, -9p - 3 rho v^2, rho vx, -rho vx, rho vy, -rho vy,
 //         rho (vx^2 - vy^2), rho vx vy),
 // M G  = (v.g, 0, -v.g, Fx, -Fx, Fy, -Fy, 2/3 (vx gx - vy gy), 1/3 (vx gy + vy gx))
-// with G_i = w_i [c_i.F/cs2 + (c_i.v)(c_i.g)/cs2], g = grad rho.
+// with G_i = w_i [c_i.F/cs2 + (c_i.v)(c_i.g)/cs2], g = grad rho.  The
+// conserved moments come out as m*_0 = v.g/2 and m*_{3,5} = rho v + F/2.
 template <typename R>
-__device__ __forceinline__ void collide_ns(R f[9], R p, R rho, R vx, R vy, R Fx, R Fy,
-                                           R gx, R gy, const KParams<R>& kp) {
-  R m[9];
-  m9_from_f(f, m);
-  const R v2 = vx * vx + vy * vy;
-  const R vg = vx * gx + vy * gy;
-  const R rv2 = rho * v2;
-  R ms[9];
-  ms[0] = R(0.5) * vg;
-  ms[1] = m[1] - kp.s_e * (m[1] - (R(6) * p + R(3) * rv2));
-  ms[2] = m[2] - kp.s_eps * (m[2] - (R(-9) * p - R(3) * rv2)) - (R(1) - R(0.5) * kp.s_eps) * vg;
-  ms[3] = rho * vx + R(0.5) * Fx;
-  ms[4] = m[4] - kp.s_q * (m[4] + rho * vx) - (R(1) - R(0.5) * kp.s_q) * Fx;
-  ms[5] = rho * vy + R(0.5) * Fy;
-  ms[6] = m[6] - kp.s_q * (m[6] + rho * vy) - (R(1) - R(0.5) * kp.s_q) * Fy;
+__device__ __forceinline__ void collide_ns(R f[9], R p, R rho, V2<R> v, V2<R> F, V2<R> g,
+                                           const KParams<R>& kp) {
+  const V2<R> A = vec2(f[1], f[2]), B = vec2(f[3], f[4]), C = vec2(f[5], f[6]), D = vec2(f[7], f[8]);
+  const V2<R> S = A + B, Dl = A - B, T = C + D, U = C - D;
+  const R a14 = S.x + S.y, a58 = T.x + T.y;
+  const R m1 = R(-4) * f[0] - a14 + R(2) * a58;
+  const R m2 = R(4) * f[0] - R(2) * a14 + a58;
+  const V2<R> dxy = vec2(U.x - U.y, U.x + U.y);
+  const V2<R> m46 = fma(R(-2), Dl, dxy);
+  const V2<R> m78 = vec2(S.x - S.y, T.x - T.y);
+
+  const V2<R> vv = v * v;
+  const R v2s = vv.x + vv.y;
+  const V2<R> vgp = v * g;
+  const R vg = vgp.x + vgp.y;
+  const R rv2 = rho * v2s;
+  const R ms0 = R(0.5) * vg;
+  const R ms1 = m1 - kp.s_e * (m1 - (R(6) * p + R(3) * rv2));
+  const R ms2 = m2 - kp.s_eps * (m2 - (R(-9) * p - R(3) * rv2)) - (R(1) - R(0.5) * kp.s_eps) * vg;
+  const V2<R> rv = rho * v;
+  const V2<R> ms35 = fma(R(0.5), F, rv);
+  const V2<R> ms46 =
+      fma(splat(-kp.s_q), m46 + rv, m46) - (R(1) - R(0.5) * kp.s_q) * F;
   const R hn = R(1) - R(0.5) * kp.s_nu;
-  ms[7] = m[7] - kp.s_nu * (m[7] - rho * (vx * vx - vy * vy)) +
-          hn * R(2.0 / 3.0) * (vx * gx - vy * gy);
-  ms[8] = m[8] - kp.s_nu * (m[8] - rho * vx * vy) + hn * R(1.0 / 3.0) * (vx * gy + vy * gx);
-  f_from_m9(ms, f);
+  const V2<R> eq78 = vec2(rho * (vv.x - vv.y), rho * v.x * v.y);
+  const V2<R> fr78 = vec2(R(2.0 / 3.0) * (vgp.x - vgp.y), R(1.0 / 3.0) * (v.x * g.y + v.y * g.x));
+  const V2<R> ms78 = fma(splat(hn), fr78, fma(splat(-kp.s_nu), m78 - eq78, m78));
+
+  const R a = ms0 * R(1.0 / 9.0), b = ms1 * R(1.0 / 36.0), c = ms2 * R(1.0 / 36.0);
+  f[0] = a - R(4) * b + R(4) * c;
+  f_from_moments(a - b - R(2) * c, a + R(2) * b + c, R(1.0 / 6.0) * ms35,
+                 R(1.0 / 12.0) * ms46, R(0.25) * ms78.x, R(0.25) * ms78.y, f);
 }
 
 // CAC collision, D2Q9: h_eq = w_i phi (1 + 3 c.v), G_i = 3 w_i c.G1.  Flux
 // moments relax with s_phi, all others with 1:
-// m* = (phi, -2 phi, phi, j*x, -phi vx - G1x/2, j*y, -phi vy - G1y/2, 0, 0).
+// m* = (phi, -2 phi, phi, j*x, -phi vx - G1x/2, j*y, -phi vy - G1y/2, 0, 0),
+// whose back-transform has axis = phi/9, diag = phi/36, h_0 = 4 phi/9.
 template <typename R>
-__device__ __forceinline__ void collide_cac(R h[9], R phi, R vx, R vy, R G1x, R G1y,
+__device__ __forceinline__ void collide_cac(R h[9], R phi, V2<R> v, V2<R> G1,
                                             const KParams<R>& kp) {
-  const R jx = h[1] - h[3] + h[5] - h[6] - h[7] + h[8];
-  const R jy = h[2] - h[4] + h[5] + h[6] - h[7] - h[8];
+  const V2<R> Dl = vec2(h[1], h[2]) - vec2(h[3], h[4]);
+  const V2<R> U = vec2(h[5], h[6]) - vec2(h[7], h[8]);
+  const V2<R> J = Dl + vec2(U.x - U.y, U.x + U.y);
   const R hs = R(1) - R(0.5) * kp.s_phi;
-  R ms[9];
-  ms[0] = phi;
-  ms[1] = R(-2) * phi;
-  ms[2] = phi;
-  ms[3] = jx - kp.s_phi * (jx - phi * vx) + hs * G1x;
-  ms[4] = -phi * vx - R(0.5) * G1x;
-  ms[5] = jy - kp.s_phi * (jy - phi * vy) + hs * G1y;
-  ms[6] = -phi * vy - R(0.5) * G1y;
-  ms[7] = R(0);
-  ms[8] = R(0);
-  f_from_m9(ms, h);
+  const V2<R> pv = phi * v;
+  const V2<R> JS = fma(splat(hs), G1, fma(splat(-kp.s_phi), J - pv, J));
+  const V2<R> q46 = fma(R(-0.5), G1, splat(R(0)) - pv);   // (-phi vx - G1x/2, ...)
+  h[0] = phi * R(4.0 / 9.0);
+  f_from_moments(phi * R(1.0 / 9.0), phi * R(1.0 / 36.0), R(1.0 / 6.0) * JS,
+                 R(1.0 / 12.0) * q46, R(0), R(0), h);
 }
 
 // D2Q5 collision with conserved zeroth moment m0 (after the direct source),
 // flux moments j relaxing with rate s towards jeq plus (1 - s/2) Gj, and the
 // other moments at their equilibria.
 template <typename R>
-__device__ __forceinline__ void collide_q5(R q[5], R m0, R s, R jeqx, R jeqy, R Gx, R Gy) {
-  const R jx = q[1] - q[3];
-  const R jy = q[2] - q[4];
+__device__ __forceinline__ void collide_q5(R q[5], R m0, R s, V2<R> Jeq, V2<R> G) {
+  const V2<R> J = vec2(q[1], q[2]) - vec2(q[3], q[4]);
   const R hs = R(1) - R(0.5) * s;
-  const R jsx = jx - s * (jx - jeqx) + hs * Gx;
-  const R jsy = jy - s * (jy - jeqy) + hs * Gy;
-  q5_from_m(m0, jsx, jsy, q);
+  const V2<R> JS = fma(splat(hs), G, fma(splat(-s), J - Jeq, J));
+  q5_from_m(m0, JS, q);
 }
 
 }  // namespace pf

@@ -146,11 +146,11 @@ __device__ __forceinline__ void issue_row(const StepArgs<S, R>& a, const DomDesc
   const unsigned row = (unsigned)d.off + (unsigned)(gy * d.nx);
   if (q < G::NPS) {
     copy_plane_row<S>(smem_u32(slot + q * G::PWS * sizeof(S)),
-                      a.in + (unsigned)pop_plane(q) * ps + row, x0, w, d.nx, G::HS, bar);
+                      plane(a.in, pop_plane(q), ps) + row, x0, w, d.nx, G::HS, bar);
   } else {
     const int u = q - G::NPS;
     copy_plane_row<R>(smem_u32(slot + G::POP_BYTES + u * G::PWR * sizeof(R)),
-                      a.ain + (unsigned)aux_plane(u) * ps + row, x0, w, d.nx, G::HR, bar);
+                      plane(a.ain, aux_plane(u), ps) + row, x0, w, d.nx, G::HR, bar);
   }
 }
 
@@ -209,19 +209,19 @@ template <typename S, typename R>
 __device__ __forceinline__ void load_own_hg(const StepArgs<S, R>& a, unsigned site, OwnHG<S, R>& o) {
   const unsigned ps = (unsigned)a.plane_stride;
 #pragma unroll
-  for (int i = 0; i < 5; ++i) o.gpre[i] = __ldg(a.in + (P_GPRE + i) * ps + site);
-  o.vxo = __ldg(a.ain + A_VXO * ps + site);
-  o.vyo = __ldg(a.ain + A_VYO * ps + site);
+  for (int i = 0; i < 5; ++i) o.gpre[i] = __ldg(plane(a.in, P_GPRE + i, ps) + site);
+  o.vxo = __ldg(plane(a.ain, A_VXO, ps) + site);
+  o.vyo = __ldg(plane(a.ain, A_VYO, ps) + site);
 }
 template <typename S, typename R>
 __device__ __forceinline__ void load_own_site(const StepArgs<S, R>& a, unsigned site,
                                               OwnSite<S, R>& o) {
   const unsigned ps = (unsigned)a.plane_stride;
   if constexpr (!Codec<S>::kOffset) {
-    o.phio = __ldg(a.ain + A_PHIO * ps + site);
-    o.Co = __ldg(a.ain + A_CO * ps + site);
+    o.phio = __ldg(plane(a.ain, A_PHIO, ps) + site);
+    o.Co = __ldg(plane(a.ain, A_CO, ps) + site);
   }
-  o.Qo = __ldg(a.ain + A_QO * ps + site);
+  o.Qo = __ldg(plane(a.ain, A_QO, ps) + site);
   o.gid = __ldg(a.grain + site);
 }
 
