@@ -41,7 +41,7 @@ struct pf_handle {
   size_t celem = 4;         // bytes per compute value
   int variant = STEP_YMARCH;  // step kernel traversal
   int tx = 32, ty = 8;      // tile of the 2-D variant
-  int chunk = 48;           // rows per tile of the y-march variant (tuned at 4096^2)
+  int chunk = 32;           // rows per tile of the y-march variants (tuned at 4096^2)
   int ntiles = 0;
   int grid = 0;
   int launch_mode = 0;      // 0: one launch over all domains; 1: one launch per domain
@@ -367,7 +367,10 @@ extern "C" pf_status pf_create(const pf_params* p, const pf_domain* doms, int n_
     return bail(PF_ERR_CUDA, "grain table upload failed");
   // default traversal: the staged y-march for the 16-bit storage forms
   // (measured faster at 4096^2), the plain y-march otherwise
-  if ((prec == PF_FP16_OFFSET || prec == PF_BF16_OFFSET) && staged_ok(h)) h->variant = STEP_STAGED;
+  if ((prec == PF_FP16_OFFSET || prec == PF_BF16_OFFSET) && staged_ok(h)) {
+    h->variant = STEP_STAGED;
+    h->chunk = 48;
+  }
   if (upload_tables(h) != PF_OK) return bail(PF_ERR_CUDA, h->err.c_str());
   *out = h;
   return PF_OK;

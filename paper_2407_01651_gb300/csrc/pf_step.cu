@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256) k_step_tile(StepArgs<S, R> a) {
 // j with the stencils read from slots j-1, j, j+1.  Every population is loaded
 // from memory once (plus 2 halo columns per YM_W).
 template <typename S, typename R>
-__global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 3 : 2) k_step_ymarch(StepArgs<S, R> a) {
+__global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 4 : 2) k_step_ymarch(StepArgs<S, R> a) {
   constexpr int RW = YM_W + 2;
   __shared__ R ring[4][4][RW];  // [phi, psi, vx_o, vy_o][slot][column]
   const int t = threadIdx.x;
