@@ -42,17 +42,11 @@ __device__ __forceinline__ local::Coef<R> make_coef(const KParams<R>& kp, const 
   return c;
 }
 
-__device__ __forceinline__ long long site_at(const DomDesc& d, int x, int y) {
-  x = x < 0 ? x + d.nx : (x >= d.nx ? x - d.nx : x);
-  y = y < 0 ? y + d.ny : (y >= d.ny ? y - d.ny : y);
-  return d.off + (long long)y * d.nx + x;
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
 template <typename S, typename R>
-__global__ void __launch_bounds__(256) k_adj_local(AdjArgs<S, R> a) {
+__global__ void __launch_bounds__(256, 2) k_adj_local(AdjArgs<S, R> a) {
   __shared__ R sphi[ADJ_TY + 2][ADJ_TX + 2], spsi[ADJ_TY + 2][ADJ_TX + 2];
   __shared__ R svx[ADJ_TY + 2][ADJ_TX + 2], svy[ADJ_TY + 2][ADJ_TX + 2];
   __shared__ R red[3][256];
@@ -189,77 +183,84 @@ __global__ void __launch_bounds__(256) k_adj_local(AdjArgs<S, R> a) {
 //   adj X(x) += sum_j 3 w_j c_j . adj grad(x - c_j)
 //             + sum_{j>0} 6 w_j adj lap(x - c_j) - 6 (1 - w_0) adj lap(x).
 template <typename R>
-__global__ void k_adj_stencil(const R* __restrict__ ai, R* __restrict__ as, DomDesc d,
-                              long long ps) {
-  const long long n = (long long)d.nx * d.ny;
+__global__ void __launch_bounds__(256) k_adj_stencil(const R* __restrict__ ai, R* __restrict__ as,
+                                                     DomDesc d, long long ps_) {
+  const unsigned ps = (unsigned)ps_;
   const R w[9] = {R(4.0 / 9.0), R(1.0 / 9.0), R(1.0 / 9.0), R(1.0 / 9.0), R(1.0 / 9.0),
                   R(1.0 / 36.0), R(1.0 / 36.0), R(1.0 / 36.0), R(1.0 / 36.0)};
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(i % d.nx), y = (int)(i / d.nx);
-    const long long site = d.off + i;
-    R aphi = R(-6) * (R(1) - w[0]) * ai[AI_LPHI * ps + site];
-    R apsi = R(0), avx = ai[AI_VXO * ps + site], avy = ai[AI_VYO * ps + site];
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= d.nx) return;
+  for (int y = blockIdx.y; y < d.ny; y += gridDim.y) {
+    const Src9 src = sources(d, x, y);   // src.s[j] = x - c_j
+    const unsigned site = src.s[0];
+    R aphi = R(-6) * (R(1) - w[0]) * plane(ai, AI_LPHI, ps)[site];
+    R apsi = R(0), avx = plane(ai, AI_VXO, ps)[site], avy = plane(ai, AI_VYO, ps)[site];
+#pragma unroll
     for (int j = 1; j < 9; ++j) {
-      const long long z = site_at(d, x - CX9[j], y - CY9[j]);
+      const unsigned z = src.s[j];
       const R wx = R(3) * w[j] * R(CX9[j]), wy = R(3) * w[j] * R(CY9[j]);
-      aphi += wx * ai[AI_GPX * ps + z] + wy * ai[AI_GPY * ps + z] +
-              R(6) * w[j] * ai[AI_LPHI * ps + z];
-      apsi += wx * ai[AI_GSX * ps + z] + wy * ai[AI_GSY * ps + z];
-      avx += wx * ai[AI_DVXX * ps + z] + wy * ai[AI_DVXY * ps + z];
-      avy += wx * ai[AI_DVYX * ps + z] + wy * ai[AI_DVYY * ps + z];
+      aphi += wx * plane(ai, AI_GPX, ps)[z] + wy * plane(ai, AI_GPY, ps)[z] +
+              R(6) * w[j] * plane(ai, AI_LPHI, ps)[z];
+      apsi += wx * plane(ai, AI_GSX, ps)[z] + wy * plane(ai, AI_GSY, ps)[z];
+      avx += wx * plane(ai, AI_DVXX, ps)[z] + wy * plane(ai, AI_DVXY, ps)[z];
+      avy += wx * plane(ai, AI_DVYX, ps)[z] + wy * plane(ai, AI_DVYY, ps)[z];
     }
-    as[0 * ps + site] = aphi;
-    as[1 * ps + site] = apsi;
-    as[2 * ps + site] = avx;
-    as[3 * ps + site] = avy;
+    plane(as, 0, ps)[site] = aphi;
+    plane(as, 1, ps)[site] = apsi;
+    plane(as, 2, ps)[site] = avx;
+    plane(as, 3, ps)[site] = avy;
   }
 }
 
 // Streaming and time-stretch transposes: lambda_t.
 // g_i(x) = g_pre,i(x) + r(x - c_i) [g_post,i(x - c_i) - g_pre,i(x)] and
-// psi_o(x) = sum_i g_pre,i(x).
+// psi_o(x) = sum_i g_pre,i(x).  The population of direction q leaving x lands
+// on x + c_q, the source x - c_{opp(q)} of the pull with the opposite direction.
 template <typename S, typename R>
-__global__ void k_adj_gather(AdjArgs<S, R> a) {
+__global__ void __launch_bounds__(256) k_adj_gather(AdjArgs<S, R> a) {
   const DomDesc d = a.dom;
-  const long long ps = a.step.plane_stride;
-  const long long n = (long long)d.nx * d.ny;
+  const unsigned ps = (unsigned)a.step.plane_stride;
   const R* A = a.ai;
   const R* AS = a.as;
   const S* P = a.step.in;
   const R* X = a.step.ain;
   R* L = a.lam_out;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(i % d.nx), y = (int)(i / d.nx);
-    const long long site = d.off + i;
+  constexpr int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= d.nx) return;
+  for (int y = blockIdx.y; y < d.ny; y += gridDim.y) {
+    const Src9 src = sources(d, x, y);
+    const unsigned site = src.s[0];
+#pragma unroll
     for (int q = 0; q < 9; ++q) {
-      const long long t = site_at(d, x + CX9[q], y + CY9[q]);
-      L[(0 + q) * ps + site] = A[(AI_F + q) * ps + t];
-      L[(9 + q) * ps + site] = A[(AI_H + q) * ps + t] + AS[0 * ps + t];
+      const unsigned t = src.s[OPP[q]];   // x + c_q
+      plane(L, 0 + q, ps)[site] = plane(A, AI_F + q, ps)[t];
+      plane(L, 9 + q, ps)[site] = plane(A, AI_H + q, ps)[t] + plane(AS, 0, ps)[t];
     }
-    const R rr_own = X[A_RR * ps + site];
+    const R rr_own = plane(X, A_RR, ps)[site];
     R lrr = R(0);
-    const R apsio = A[AI_PSIO * ps + site];
+    const R apsio = plane(A, AI_PSIO, ps)[site];
+    const R as1 = plane(AS, 1, ps)[site];
+#pragma unroll
     for (int q = 0; q < 5; ++q) {
-      const long long t = site_at(d, x + CX9[q], y + CY9[q]);   // destination of q
-      const long long s = site_at(d, x - CX9[q], y - CY9[q]);   // source of q
-      L[(29 + q) * ps + site] = A[(AI_S + q) * ps + t];
-      const R ag_own = A[(AI_G + q) * ps + site] + AS[1 * ps + site];
-      const R ag_dst = A[(AI_G + q) * ps + t] + AS[1 * ps + t];
-      const R rr_src = X[A_RR * ps + s];
-      L[(18 + q) * ps + site] = ag_own * (R(1) - rr_src) + apsio;
-      L[(23 + q) * ps + site] = ag_dst * rr_own;
-      const R gq_own = ld<R>(P + (P_GPOST + q) * ps, site);
-      const R gp_dst = ld<R>(P + (P_GPRE + q) * ps, t);
+      const unsigned t = src.s[OPP[q]];   // destination of q
+      const unsigned sq = src.s[q];       // source of q
+      plane(L, 29 + q, ps)[site] = plane(A, AI_S + q, ps)[t];
+      const R ag_own = plane(A, AI_G + q, ps)[site] + as1;
+      const R ag_dst = plane(A, AI_G + q, ps)[t] + plane(AS, 1, ps)[t];
+      const R rr_src = plane(X, A_RR, ps)[sq];
+      plane(L, 18 + q, ps)[site] = ag_own * (R(1) - rr_src) + apsio;
+      plane(L, 23 + q, ps)[site] = ag_dst * rr_own;
+      const R gq_own = ld<R>(plane(P, P_GPOST + q, ps), site);
+      const R gp_dst = ld<R>(plane(P, P_GPRE + q, ps), t);
       lrr += ag_dst * (gq_own - gp_dst);
     }
-    L[28 * ps + site] = lrr;
-    L[34 * ps + site] = A[AI_PHIO * ps + site];
-    L[35 * ps + site] = A[AI_CO * ps + site];
-    L[36 * ps + site] = AS[2 * ps + site];
-    L[37 * ps + site] = AS[3 * ps + site];
-    L[38 * ps + site] = A[AI_QO * ps + site];
+    plane(L, 28, ps)[site] = lrr;
+    plane(L, 34, ps)[site] = plane(A, AI_PHIO, ps)[site];
+    plane(L, 35, ps)[site] = plane(A, AI_CO, ps)[site];
+    plane(L, 36, ps)[site] = plane(AS, 2, ps)[site];
+    plane(L, 37, ps)[site] = plane(AS, 3, ps)[site];
+    plane(L, 38, ps)[site] = plane(A, AI_QO, ps)[site];
   }
 }
 
@@ -313,8 +314,7 @@ __global__ void k_adj_omega_init(const R* __restrict__ L, const S* __restrict__ 
 template <typename S, typename R>
 cudaError_t launch_adjoint_step(const AdjArgs<S, R>& a, int grid, cudaStream_t st) {
   k_adj_local<S, R><<<grid, dim3(ADJ_TX, ADJ_TY), 0, st>>>(a);
-  const long long n = (long long)a.dom.nx * a.dom.ny;
-  const int g2 = (int)std::min<long long>((n + 255) / 256, 4096);
+  const dim3 g2((a.dom.nx + 255) / 256, std::min(a.dom.ny, 65535));
   k_adj_stencil<R><<<g2, 256, 0, st>>>(a.ai, a.as, a.dom, a.step.plane_stride);
   k_adj_gather<S, R><<<g2, 256, 0, st>>>(a);
   return cudaGetLastError();
