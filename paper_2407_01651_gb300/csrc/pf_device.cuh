@@ -13,10 +13,14 @@ namespace pf {
 // forms store each population as its offset from w_i M_o, with M_o the lagged
 // moment of the site that holds it (phi for h, psi for g, C for s; kept in
 // FP32), so that only the small non-rest part is rounded to 16 bits; the NS
-// populations, which are small already, are stored scaled by 2^12.
+// populations, which are small already, are stored scaled by 2^12.  FP16
+// also scales the offsets by 2^14 (exact): its narrow exponent range would
+// otherwise put the tiny offsets of a quiet bulk among the subnormals, where
+// every site rounds them the same way and the conserved totals drift.
 template <typename S>
 struct Codec {
   static constexpr bool kOffset = false;
+  static constexpr float kOffScale = 1.0f;
   template <typename R>
   __device__ __forceinline__ static R dec(S v) { return static_cast<R>(v); }
   template <typename R>
@@ -25,6 +29,7 @@ struct Codec {
 template <>
 struct Codec<__half> {
   static constexpr bool kOffset = true;
+  static constexpr float kOffScale = 16384.0f;
   template <typename R>
   __device__ __forceinline__ static R dec(__half v) { return __half2float(v); }
   template <typename R>
@@ -33,6 +38,7 @@ struct Codec<__half> {
 template <>
 struct Codec<__nv_bfloat16> {
   static constexpr bool kOffset = true;
+  static constexpr float kOffScale = 1.0f;
   template <typename R>
   __device__ __forceinline__ static R dec(__nv_bfloat16 v) { return __bfloat162float(v); }
   template <typename R>
@@ -92,15 +98,27 @@ __device__ __forceinline__ void st_ns(S* __restrict__ p, I i, R v) {
   if constexpr (Codec<S>::kOffset) st(p, i, v * R(kNSScale));
   else st(p, i, v);
 }
+// Offset-stored value <-> population (wm = w_i M_o; unused by FP64/FP32).
+template <typename S, typename R>
+__device__ __forceinline__ R dec_off(S v, R wm) {
+  const R raw = Codec<S>::template dec<R>(v);
+  if constexpr (!Codec<S>::kOffset) return raw;
+  else if constexpr (Codec<S>::kOffScale == 1.0f) return wm + raw;
+  else return raw * R(1.0f / Codec<S>::kOffScale) + wm;
+}
+template <typename S, typename R>
+__device__ __forceinline__ S enc_off(R v, R wm) {
+  if constexpr (!Codec<S>::kOffset) return Codec<S>::template enc<R>(v);
+  else if constexpr (Codec<S>::kOffScale == 1.0f) return Codec<S>::template enc<R>(v - wm);
+  else return Codec<S>::template enc<R>((v - wm) * R(Codec<S>::kOffScale));
+}
 template <typename S, typename R, typename I>
 __device__ __forceinline__ R pop_off(const S* __restrict__ p, I i, R wm) {
-  if constexpr (Codec<S>::kOffset) return wm + ld<R>(p, i);
-  else return ld<R>(p, i);
+  return dec_off<S, R>(__ldg(p + i), wm);
 }
 template <typename S, typename R, typename I>
 __device__ __forceinline__ void st_off(S* __restrict__ p, I i, R v, R wm) {
-  if constexpr (Codec<S>::kOffset) st(p, i, v - wm);
-  else st(p, i, v);
+  p[i] = enc_off<S, R>(v, wm);
 }
 
 // Compensated (Neumaier) accumulation: the zeroth moments phi, psi, C are sums

@@ -125,11 +125,16 @@ __device__ __forceinline__ void f_from_moments(R axis, R diag, V2<R> DF, V2<R> E
 // D2Q5 post-collision populations from (m0, jx, jy) with the energy moment at
 // -(2/3) m0 and the anisotropic moment at 0 (their equilibria, rate 1):
 // s_0 = m0/3, s_{1,3} = m0/6 +- jx/2, s_{2,4} = m0/6 +- jy/2.
+// s_0 is formed as m0 - 4 (m0/6): by Sterbenz's lemma that difference is
+// exact, so sum_i s_i = m0 up to the unbiased rounding of the +-j/2 terms.
+// (Rounding m0 * fl(1/3) and m0 * fl(1/6) separately would bias every site's
+// sum the same way, a drift of ~0.5 ulp per step in a conserved total.)
 template <typename R>
 __device__ __forceinline__ void q5_from_m(R m0, V2<R> J, R s[5]) {
-  const V2<R> a = splat(m0 * R(1.0 / 6.0));
+  const R a0 = m0 * R(1.0 / 6.0);
+  const V2<R> a = splat(a0);
   const V2<R> s12 = fma(R(0.5), J, a), s34 = fma(R(-0.5), J, a);
-  s[0] = m0 * R(1.0 / 3.0);
+  s[0] = m0 - R(4) * a0;
   s[1] = s12.x; s[2] = s12.y; s[3] = s34.x; s[4] = s34.y;
 }
 
@@ -178,7 +183,12 @@ __device__ __forceinline__ void collide_ns(R f[9], R p, R rho, V2<R> v, V2<R> F,
 // CAC collision, D2Q9: h_eq = w_i phi (1 + 3 c.v), G_i = 3 w_i c.G1.  Flux
 // moments relax with s_phi, all others with 1:
 // m* = (phi, -2 phi, phi, j*x, -phi vx - G1x/2, j*y, -phi vy - G1y/2, 0, 0),
-// whose back-transform has axis = phi/9, diag = phi/36, h_0 = 4 phi/9.
+// whose back-transform has axis = phi/9, diag = phi/36, h_0 = 4 phi/9.  The
+// rest population is formed as h_0 = phi - 4 t with t = fl(axis + diag), an
+// exact difference (Sterbenz), and the diagonal base is shifted by the exact
+// rounding error of t (Fast2Sum), so that h_0 + 4 axis + 4 diag = phi holds
+// exactly.  Otherwise a uniform bulk, where every site rounds the same value
+// the same way, would lose a fixed fraction of phi at every step.
 template <typename R>
 __device__ __forceinline__ void collide_cac(R h[9], R phi, V2<R> v, V2<R> G1,
                                             const KParams<R>& kp) {
@@ -189,9 +199,11 @@ __device__ __forceinline__ void collide_cac(R h[9], R phi, V2<R> v, V2<R> G1,
   const V2<R> pv = phi * v;
   const V2<R> JS = fma(splat(hs), G1, fma(splat(-kp.s_phi), J - pv, J));
   const V2<R> q46 = fma(R(-0.5), G1, splat(R(0)) - pv);   // (-phi vx - G1x/2, ...)
-  h[0] = phi * R(4.0 / 9.0);
-  f_from_moments(phi * R(1.0 / 9.0), phi * R(1.0 / 36.0), R(1.0 / 6.0) * JS,
-                 R(1.0 / 12.0) * q46, R(0), R(0), h);
+  const R axis = phi * R(1.0 / 9.0), diag = phi * R(1.0 / 36.0);
+  const R t = axis + diag;
+  const R e = diag - (t - axis);   // axis + diag - t, exact (|axis| >= |diag|)
+  h[0] = phi - R(4) * t;
+  f_from_moments(axis, diag - e, R(1.0 / 6.0) * JS, R(1.0 / 12.0) * q46, R(0), R(0), h);
 }
 
 // D2Q5 collision with conserved zeroth moment m0 (after the direct source),

@@ -237,8 +237,7 @@ __device__ __forceinline__ void stream_hg(const SlotView<S, R> (&rows)[3], int d
   for (int i = 0; i < 9; ++i) {
     const SlotView<S, R>& r = rows[src_row(i)];
     const int sx = dx + src_dx(i);
-    const R raw = dec<S, R>(r.p(9 + i, sx));
-    h[i] = off ? w9<R>(i) * r.x(U_PHIO, sx) + raw : raw;
+    h[i] = dec_off<S, R>(r.p(9 + i, sx), off ? w9<R>(i) * r.x(U_PHIO, sx) : R(0));
     sh.add(h[i]);
   }
   phi = sh.value();
@@ -249,9 +248,8 @@ __device__ __forceinline__ void stream_hg(const SlotView<S, R> (&rows)[3], int d
   for (int i = 0; i < 5; ++i) {
     const SlotView<S, R>& r = rows[src_row(i)];
     const int sx = dx + src_dx(i);
-    const R gold = off ? w5<R>(i) * psio_own + dec<S, R>(own.gpre[i]) : dec<S, R>(own.gpre[i]);
-    const R raw = dec<S, R>(r.p(18 + i, sx));
-    const R gpo = off ? w5<R>(i) * r.x(U_PSIO, sx) + raw : raw;
+    const R gold = dec_off<S, R>(own.gpre[i], w5<R>(i) * psio_own);
+    const R gpo = dec_off<S, R>(r.p(18 + i, sx), off ? w5<R>(i) * r.x(U_PSIO, sx) : R(0));
     const R rr = r.x(U_RR, sx);
     g[i] = gold + (gpo - gold) * rr;
     sg.add(g[i]);
@@ -272,8 +270,7 @@ __device__ __forceinline__ void site_inputs(const SlotView<S, R> (&rows)[3], int
   for (int i = 0; i < 5; ++i) {
     const SlotView<S, R>& r = rows[src_row(i)];
     const int sx = dx + src_dx(i);
-    const R raw = dec<S, R>(r.p(23 + i, sx));
-    in.s[i] = off ? w5<R>(i) * r.x(U_CO, sx) + raw : raw;
+    in.s[i] = dec_off<S, R>(r.p(23 + i, sx), off ? w5<R>(i) * r.x(U_CO, sx) : R(0));
   }
   if constexpr (off) {
     in.phio = rows[1].x(U_PHIO, dx);

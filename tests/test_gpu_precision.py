@@ -1,7 +1,8 @@
 """Reduced-precision storage forms (FP16 / BF16 offsets from the local rest
-equilibrium w_i M_o, NS populations scaled by 2^12; FP32 arithmetic) against
-the FP64 oracle.  Bounds are ~3x the errors measured on the 256^2 workload
-(100 steps: FP16 phi 8e-6, psi 2.3e-5, v 6e-3; BF16 about 10x FP16)."""
+equilibrium w_i M_o, NS populations scaled by 2^12, FP16 offsets by 2^14;
+FP32 arithmetic) and the FP32 form against the FP64 oracle.  Bounds are ~3x
+the errors measured on the 256^2 workload (100 steps: FP16 phi 7e-6, psi
+2.5e-5, v 8e-3; BF16 about 10x FP16; FP32 below 1e-6 on phi, psi, C)."""
 import numpy as np
 import pytest
 
@@ -37,24 +38,70 @@ def test_offset_storage_starts_exact(precision):
     assert np.array_equal(sa, sb)
 
 
-@pytest.mark.parametrize("precision", ["fp16", "bf16"])
-def test_offset_storage_against_oracle(precision):
+# Per-field bounds against the FP64 oracle on the 256^2 one-seed/one-bubble
+# workload after 100 and 1000 steps: about 3x the errors measured on a GB300.
+BOUNDS = {
+    100: {
+        "fp32": {"phi": 3e-6, "psi": 3e-6, "C": 3e-6, "U": 3e-6, "p": 1e-5, "vx": 2e-4, "vy": 1e-4,
+                 "mu": 1e-4},
+        "fp16": BOUND_100["fp16"],
+        "bf16": BOUND_100["bf16"],
+    },
+    1000: {
+        "fp32": {"phi": 3e-6, "psi": 3e-6, "C": 3e-6, "U": 1e-5, "p": 3e-5, "vx": 3e-4, "vy": 3e-4,
+                 "mu": 3e-5},
+        "fp16": {"phi": 4e-5, "psi": 1e-4, "C": 1e-4, "U": 2e-4, "p": 2e-3, "vx": 6e-3,
+                 "vy": 6e-3, "mu": 1e-3},
+        "bf16": {"phi": 6e-4, "psi": 2e-3, "C": 1e-3, "U": 2e-3, "p": 3e-2, "vx": 5e-2,
+                 "vy": 5e-2, "mu": 6e-3},
+    },
+}
+
+
+@pytest.fixture(scope="module")
+def oracle_256():
+    """Oracle fields of the 256^2 workload after 1, 100 and 1000 steps."""
     lay = wl.single_seed_bubble(256, 256, rng_seed=1)
     o = oracle.Oracle(lay.nx, lay.ny, lay.params)
     o.init_spec(lay.seeds, lay.R_s, lay.bubbles)
+    out, done = {}, 0
+    for T in (1, 100, 1000):
+        o.step(T - done)
+        done = T
+        out[T] = o.fields()
+    return lay, out
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
+def test_storage_forms_against_oracle_1_100_1000_steps(precision, oracle_256):
+    lay, fo = oracle_256
     sim = pf.Simulation([(lay.nx, lay.ny)], lay.params, precision)
     sim.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
     d0 = sim.reduce(0)
-    o.step(100)
-    sim.step(100)
-    fo, fg = o.fields(), sim.fields()
-    errs = {k: rel(fg[k], fo[k]) for k in FIELDS}
-    bad = {k: v for k, v in errs.items() if v > BOUND_100[precision][k]}
-    assert not bad, (bad, errs)
+    ref = pf.Simulation([(lay.nx, lay.ny)], lay.params, "fp32")
+    ref.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
+    done = 0
+    for T in (1, 100, 1000):
+        sim.step(T - done)
+        if T == 1:
+            ref.step(1)
+        done = T
+        fg = sim.fields()
+        errs = {k: rel(fg[k], fo[T][k]) for k in FIELDS}
+        if T == 1:
+            # the initial state encodes exactly, and the first step's fields
+            # come out of the FP32 arithmetic before any 16-bit rounding
+            fr = ref.fields()
+            for k in FIELDS:
+                assert rel(fg[k], fr[k]) <= 1e-6, (k, rel(fg[k], fr[k]))
+            continue
+        bad = {k: v for k, v in errs.items() if v > BOUNDS[T][precision][k]}
+        assert not bad, (T, bad, errs)
+    # gas and solute totals: no systematic drift (measured ~1e-7 after 1000
+    # steps; a biased rounding of the rest populations gave 3e-5)
     d = sim.reduce(0)
-    # gas and solute totals drift only by the FP32 arithmetic of the step
-    assert abs(d["sum_phi"] / d0["sum_phi"] - 1) < 1e-5
-    assert abs(d["sum_C"] / d0["sum_C"] - 1) < 1e-5
+    assert abs(d["sum_phi"] / d0["sum_phi"] - 1) < 1e-6
+    assert abs(d["sum_C"] / d0["sum_C"] - 1) < 1e-6
 
 
 # The raw FP64 state has no psi_o plane: restoring re-encodes the dendrite
