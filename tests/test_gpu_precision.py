@@ -127,3 +127,43 @@ def test_offset_state_checkpoint_roundtrip(precision):
     fa, fb = a.fields(), b.fields()
     for k in ("phi", "psi", "C", "U"):
         assert rel(fb[k], fa[k]) < tol_fields, k
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_full_size_8192x4096_sampled_against_oracle_windows(precision):
+    """The 8192 x 4096 storage-form workload in the launch configuration the
+    benchmark times (staged traversal): after 10 steps, windows around the
+    seed and the bubble match oracle windows in global coordinates (the
+    oracle's full-lattice rho_bar), within the 100-step bounds."""
+    lay = wl.single_seed_bubble(8192, 4096, rng_seed=1)
+    sim = pf.Simulation([(lay.nx, lay.ny)], lay.params, precision)
+    sim.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
+    assert sim.step_config()[0] == 2
+    T = 10
+    sim.step(T)
+    names = ("phi", "psi", "C", "vx", "vy")
+    fg = sim.fields(0, names)
+    W, M = 64, 2 * T                      # window and trusted margin (2 sites per step)
+    probe = oracle.Oracle(4, 4, lay.params, window=(lay.nx, lay.ny, 0, 0))
+    rho_bar = lay.params["rho_g"] + probe.mean_phi_global(lay.bubbles) * (
+        lay.params["rho_l"] - lay.params["rho_g"])
+    sx, sy, _ = lay.seeds[0]
+    bx, by, bR = lay.bubbles[0]
+    centers = [(int(sx) + 6, int(sy)), (int(bx + bR), int(by)), (int(bx), int(by - bR))]
+    ref, got = {k: [] for k in names}, {k: [] for k in names}
+    for cx, cy in centers:
+        x0, y0 = cx - W // 2, cy - W // 2
+        o = oracle.Oracle(W, W, lay.params, window=(lay.nx, lay.ny, x0, y0))
+        o.set_rho_bar(rho_bar)
+        o.init_spec(lay.seeds, lay.R_s, lay.bubbles)
+        o.step(T)
+        fo = o.fields(names)
+        ys = (np.arange(M, W - M) + y0) % lay.ny
+        xs = (np.arange(M, W - M) + x0) % lay.nx
+        for k in names:
+            ref[k].append(fo[k][M:W - M, M:W - M])
+            got[k].append(fg[k][np.ix_(ys, xs)])
+    for k in names:
+        r, g = np.concatenate(ref[k]), np.concatenate(got[k])
+        err = rel(g, r)
+        assert err <= BOUND_100[precision][k], (k, err)
