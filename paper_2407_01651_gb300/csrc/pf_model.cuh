@@ -108,16 +108,16 @@ __device__ __forceinline__ void feq_ns(R p, R rho, R vx, R vy, R f[9]) {
 // Populations f1..f8 from the moments, given as the scalars of the rest/energy
 // group (m0/9, m1/36, m2/36 folded into axis, diag, f0), the flux pairs
 // DF = (m3, m5)/6 and EG = (m4, m6)/12, and h = m7/4, k = m8/4.
-template <typename R>
-__device__ __forceinline__ void f_from_moments(R axis, R diag, V2<R> DF, V2<R> EG, R h, R k,
-                                               R f[9]) {
-  const V2<R> Q = fma(R(-2), EG, DF);            // (d - 2e, fy - 2gy)
-  const V2<R> A = vec2(axis + h, axis - h);
-  const V2<R> f12 = A + Q, f34 = A - Q;
-  const V2<R> S = DF + EG;                       // (d + e, fy + gy)
-  const R P = S.x + k, N = S.x - k;
-  const V2<R> f56 = splat(diag + S.y) + vec2(P, -P);
-  const V2<R> f78 = splat(diag - S.y) + vec2(-N, N);
+template <typename T>
+__device__ __forceinline__ void f_from_moments(T axis, T diag, V2<T> DF, V2<T> EG, T h, T k,
+                                               T f[9]) {
+  const V2<T> Q = fma(T(-2), EG, DF);            // (d - 2e, fy - 2gy)
+  const V2<T> A = vec2(axis + h, axis - h);
+  const V2<T> f12 = A + Q, f34 = A - Q;
+  const V2<T> S = DF + EG;                       // (d + e, fy + gy)
+  const T P = S.x + k, N = S.x - k;
+  const V2<T> f56 = splat(diag + S.y) + vec2(P, -P);
+  const V2<T> f78 = splat(diag - S.y) + vec2(-N, N);
   f[1] = f12.x; f[2] = f12.y; f[3] = f34.x; f[4] = f34.y;
   f[5] = f56.x; f[6] = f56.y; f[7] = f78.x; f[8] = f78.y;
 }
@@ -129,12 +129,12 @@ __device__ __forceinline__ void f_from_moments(R axis, R diag, V2<R> DF, V2<R> E
 // exact, so sum_i s_i = m0 up to the unbiased rounding of the +-j/2 terms.
 // (Rounding m0 * fl(1/3) and m0 * fl(1/6) separately would bias every site's
 // sum the same way, a drift of ~0.5 ulp per step in a conserved total.)
-template <typename R>
-__device__ __forceinline__ void q5_from_m(R m0, V2<R> J, R s[5]) {
-  const R a0 = m0 * R(1.0 / 6.0);
-  const V2<R> a = splat(a0);
-  const V2<R> s12 = fma(R(0.5), J, a), s34 = fma(R(-0.5), J, a);
-  s[0] = m0 - R(4) * a0;
+template <typename T>
+__device__ __forceinline__ void q5_from_m(T m0, V2<T> J, T s[5]) {
+  const T a0 = m0 * T(1.0 / 6.0);
+  const V2<T> a = splat(a0);
+  const V2<T> s12 = fma(T(0.5), J, a), s34 = fma(T(-0.5), J, a);
+  s[0] = m0 - T(4) * a0;
   s[1] = s12.x; s[2] = s12.y; s[3] = s34.x; s[4] = s34.y;
 }
 
@@ -145,39 +145,40 @@ __device__ __forceinline__ void q5_from_m(R m0, V2<R> J, R s[5]) {
 // M G  = (v.g, 0, -v.g, Fx, -Fx, Fy, -Fy, 2/3 (vx gx - vy gy), 1/3 (vx gy + vy gx))
 // with G_i = w_i [c_i.F/cs2 + (c_i.v)(c_i.g)/cs2], g = grad rho.  The
 // conserved moments come out as m*_0 = v.g/2 and m*_{3,5} = rho v + F/2.
-template <typename R>
-__device__ __forceinline__ void collide_ns(R f[9], R p, R rho, V2<R> v, V2<R> F, V2<R> g,
+template <typename T, typename R>
+__device__ __forceinline__ void collide_ns(T f[9], T p, T rho, V2<T> v, V2<T> F, V2<T> g,
                                            const KParams<R>& kp) {
-  const V2<R> A = vec2(f[1], f[2]), B = vec2(f[3], f[4]), C = vec2(f[5], f[6]), D = vec2(f[7], f[8]);
-  const V2<R> S = A + B, Dl = A - B, T = C + D, U = C - D;
-  const R a14 = S.x + S.y, a58 = T.x + T.y;
-  const R m1 = R(-4) * f[0] - a14 + R(2) * a58;
-  const R m2 = R(4) * f[0] - R(2) * a14 + a58;
-  const V2<R> dxy = vec2(U.x - U.y, U.x + U.y);
-  const V2<R> m46 = fma(R(-2), Dl, dxy);
-  const V2<R> m78 = vec2(S.x - S.y, T.x - T.y);
+  const V2<T> A = vec2(f[1], f[2]), B = vec2(f[3], f[4]), C = vec2(f[5], f[6]),
+              D = vec2(f[7], f[8]);
+  const V2<T> S = A + B, Dl = A - B, Tt = C + D, U = C - D;
+  const T a14 = S.x + S.y, a58 = Tt.x + Tt.y;
+  const T m1 = T(-4) * f[0] - a14 + T(2) * a58;
+  const T m2 = T(4) * f[0] - T(2) * a14 + a58;
+  const V2<T> dxy = vec2(U.x - U.y, U.x + U.y);
+  const V2<T> m46 = fma(T(-2), Dl, dxy);
+  const V2<T> m78 = vec2(S.x - S.y, Tt.x - Tt.y);
 
-  const V2<R> vv = v * v;
-  const R v2s = vv.x + vv.y;
-  const V2<R> vgp = v * g;
-  const R vg = vgp.x + vgp.y;
-  const R rv2 = rho * v2s;
-  const R ms0 = R(0.5) * vg;
-  const R ms1 = m1 - kp.s_e * (m1 - (R(6) * p + R(3) * rv2));
-  const R ms2 = m2 - kp.s_eps * (m2 - (R(-9) * p - R(3) * rv2)) - (R(1) - R(0.5) * kp.s_eps) * vg;
-  const V2<R> rv = rho * v;
-  const V2<R> ms35 = fma(R(0.5), F, rv);
-  const V2<R> ms46 =
-      fma(splat(-kp.s_q), m46 + rv, m46) - (R(1) - R(0.5) * kp.s_q) * F;
+  const V2<T> vv = v * v;
+  const T v2s = vv.x + vv.y;
+  const V2<T> vgp = v * g;
+  const T vg = vgp.x + vgp.y;
+  const T rv2 = rho * v2s;
+  const T ms0 = T(0.5) * vg;
+  const T ms1 = m1 - T(kp.s_e) * (m1 - (T(6) * p + T(3) * rv2));
+  const T ms2 = m2 - T(kp.s_eps) * (m2 - (T(-9) * p - T(3) * rv2)) -
+                T(R(1) - R(0.5) * kp.s_eps) * vg;
+  const V2<T> rv = rho * v;
+  const V2<T> ms35 = fma(T(0.5), F, rv);
+  const V2<T> ms46 = fma(splat(T(-kp.s_q)), m46 + rv, m46) - (R(1) - R(0.5) * kp.s_q) * F;
   const R hn = R(1) - R(0.5) * kp.s_nu;
-  const V2<R> eq78 = vec2(rho * (vv.x - vv.y), rho * v.x * v.y);
-  const V2<R> fr78 = vec2(R(2.0 / 3.0) * (vgp.x - vgp.y), R(1.0 / 3.0) * (v.x * g.y + v.y * g.x));
-  const V2<R> ms78 = fma(splat(hn), fr78, fma(splat(-kp.s_nu), m78 - eq78, m78));
+  const V2<T> eq78 = vec2(rho * (vv.x - vv.y), rho * v.x * v.y);
+  const V2<T> fr78 = vec2(T(2.0 / 3.0) * (vgp.x - vgp.y), T(1.0 / 3.0) * (v.x * g.y + v.y * g.x));
+  const V2<T> ms78 = fma(splat(T(hn)), fr78, fma(splat(T(-kp.s_nu)), m78 - eq78, m78));
 
-  const R a = ms0 * R(1.0 / 9.0), b = ms1 * R(1.0 / 36.0), c = ms2 * R(1.0 / 36.0);
-  f[0] = a - R(4) * b + R(4) * c;
-  f_from_moments(a - b - R(2) * c, a + R(2) * b + c, R(1.0 / 6.0) * ms35,
-                 R(1.0 / 12.0) * ms46, R(0.25) * ms78.x, R(0.25) * ms78.y, f);
+  const T a = ms0 * T(1.0 / 9.0), b = ms1 * T(1.0 / 36.0), c = ms2 * T(1.0 / 36.0);
+  f[0] = a - T(4) * b + T(4) * c;
+  f_from_moments(a - b - T(2) * c, a + T(2) * b + c, T(1.0 / 6.0) * ms35,
+                 T(1.0 / 12.0) * ms46, T(0.25) * ms78.x, T(0.25) * ms78.y, f);
 }
 
 // CAC collision, D2Q9: h_eq = w_i phi (1 + 3 c.v), G_i = 3 w_i c.G1.  Flux
@@ -189,31 +190,31 @@ __device__ __forceinline__ void collide_ns(R f[9], R p, R rho, V2<R> v, V2<R> F,
 // rounding error of t (Fast2Sum), so that h_0 + 4 axis + 4 diag = phi holds
 // exactly.  Otherwise a uniform bulk, where every site rounds the same value
 // the same way, would lose a fixed fraction of phi at every step.
-template <typename R>
-__device__ __forceinline__ void collide_cac(R h[9], R phi, V2<R> v, V2<R> G1,
+template <typename T, typename R>
+__device__ __forceinline__ void collide_cac(T h[9], T phi, V2<T> v, V2<T> G1,
                                             const KParams<R>& kp) {
-  const V2<R> Dl = vec2(h[1], h[2]) - vec2(h[3], h[4]);
-  const V2<R> U = vec2(h[5], h[6]) - vec2(h[7], h[8]);
-  const V2<R> J = Dl + vec2(U.x - U.y, U.x + U.y);
+  const V2<T> Dl = vec2(h[1], h[2]) - vec2(h[3], h[4]);
+  const V2<T> U = vec2(h[5], h[6]) - vec2(h[7], h[8]);
+  const V2<T> J = Dl + vec2(U.x - U.y, U.x + U.y);
   const R hs = R(1) - R(0.5) * kp.s_phi;
-  const V2<R> pv = phi * v;
-  const V2<R> JS = fma(splat(hs), G1, fma(splat(-kp.s_phi), J - pv, J));
-  const V2<R> q46 = fma(R(-0.5), G1, splat(R(0)) - pv);   // (-phi vx - G1x/2, ...)
-  const R axis = phi * R(1.0 / 9.0), diag = phi * R(1.0 / 36.0);
-  const R t = axis + diag;
-  const R e = diag - (t - axis);   // axis + diag - t, exact (|axis| >= |diag|)
-  h[0] = phi - R(4) * t;
-  f_from_moments(axis, diag - e, R(1.0 / 6.0) * JS, R(1.0 / 12.0) * q46, R(0), R(0), h);
+  const V2<T> pv = phi * v;
+  const V2<T> JS = fma(splat(T(hs)), G1, fma(splat(T(-kp.s_phi)), J - pv, J));
+  const V2<T> q46 = fma(T(-0.5), G1, splat(T(0)) - pv);   // (-phi vx - G1x/2, ...)
+  const T axis = phi * T(1.0 / 9.0), diag = phi * T(1.0 / 36.0);
+  const T t = axis + diag;
+  const T e = diag - (t - axis);   // axis + diag - t, exact (|axis| >= |diag|)
+  h[0] = phi - T(4) * t;
+  f_from_moments(axis, diag - e, T(1.0 / 6.0) * JS, T(1.0 / 12.0) * q46, T(0), T(0), h);
 }
 
 // D2Q5 collision with conserved zeroth moment m0 (after the direct source),
 // flux moments j relaxing with rate s towards jeq plus (1 - s/2) Gj, and the
 // other moments at their equilibria.
-template <typename R>
-__device__ __forceinline__ void collide_q5(R q[5], R m0, R s, V2<R> Jeq, V2<R> G) {
-  const V2<R> J = vec2(q[1], q[2]) - vec2(q[3], q[4]);
-  const R hs = R(1) - R(0.5) * s;
-  const V2<R> JS = fma(splat(hs), G, fma(splat(-s), J - Jeq, J));
+template <typename T>
+__device__ __forceinline__ void collide_q5(T q[5], T m0, T s, V2<T> Jeq, V2<T> G) {
+  const V2<T> J = vec2(q[1], q[2]) - vec2(q[3], q[4]);
+  const T hs = T(1) - T(0.5) * s;
+  const V2<T> JS = fma(splat(hs), G, fma(splat(-s), J - Jeq, J));
   q5_from_m(m0, JS, q);
 }
 

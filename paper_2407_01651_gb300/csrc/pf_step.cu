@@ -163,6 +163,7 @@ template <typename S, typename R>
 cudaError_t launch_step(const StepArgs<S, R>& a, int variant, int tx, int ty, int grid,
                         cudaStream_t st) {
   if (variant == STEP_STAGED) return launch_step_staged<S, R>(a, grid, st);
+
   if (variant == STEP_YMARCH) {
     k_step_ymarch<S, R><<<grid, YM_THREADS, 0, st>>>(a);
   } else {
@@ -176,6 +177,7 @@ template <typename S, typename R>
 int step_blocks_per_sm(int variant, int tx, int ty) {
   int n = 0;
   if (variant == STEP_STAGED) return staged_blocks_per_sm<S, R>();
+
   if (variant == STEP_YMARCH)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_ymarch<S, R>, YM_THREADS, 0);
   else

@@ -11,12 +11,19 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace pf {
 
 template <typename R>
 struct V2 {
   R x, y;
 };
+
+// Scalar fused multiply-add under the name the pair code uses (the lane types
+// add their own overloads).
+__device__ __forceinline__ float fma(float a, float b, float c) { return ::fmaf(a, b, c); }
+__device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
 
 template <typename R>
 __device__ __forceinline__ V2<R> vec2(R x, R y) {
@@ -42,7 +49,7 @@ __device__ __forceinline__ V2<R> operator*(V2<R> a, V2<R> b) {
 // a * b + c, fused
 template <typename R>
 __device__ __forceinline__ V2<R> fma(V2<R> a, V2<R> b, V2<R> c) {
-  return {::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y)};
+  return {fma(a.x, b.x, c.x), fma(a.y, b.y, c.y)};
 }
 
 #if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
@@ -67,14 +74,19 @@ __device__ __forceinline__ V2<float> fma(V2<float> a, V2<float> b, V2<float> c) 
 }
 #endif
 
-// scalar-times-pair helpers
-template <typename R>
-__device__ __forceinline__ V2<R> operator*(R s, V2<R> a) {
-  return splat(s) * a;
+template <typename U>
+struct is_v2 : std::false_type {};
+template <typename T>
+struct is_v2<V2<T>> : std::true_type {};
+
+// scalar-times-pair helpers (the scalar is converted to the lane type)
+template <typename T, typename U, typename = std::enable_if_t<!is_v2<U>::value>>
+__device__ __forceinline__ V2<T> operator*(U s, V2<T> a) {
+  return splat(T(s)) * a;
 }
-template <typename R>
-__device__ __forceinline__ V2<R> fma(R s, V2<R> b, V2<R> c) {
-  return fma(splat(s), b, c);
+template <typename T, typename U, typename = std::enable_if_t<!is_v2<U>::value>>
+__device__ __forceinline__ V2<T> fma(U s, V2<T> b, V2<T> c) {
+  return fma(splat(T(s)), b, c);
 }
 
 }  // namespace pf
