@@ -175,8 +175,12 @@ pf_status pf_step(pf_handle *h, int n_steps);
 /* Traversal of the step kernel (same arithmetic, results identical to
  * rounding order): variant 0 = 2-D tiles of a x b sites (a a multiple of 32,
  * a*b <= 256); variant 1 = column strips of 128 sites marched along y in
- * tiles of a rows (b ignored; the default, a = 48).  Synchronises the stream
- * and rebuilds the tile table.  Errors: BAD_ARG. */
+ * tiles of a rows (b ignored; the default for FP32/FP64, a = 32); variant 2 =
+ * the same strips with their input rows staged in shared memory by bulk
+ * copies (b ignored; the default for FP16/BF16 storage, a = 48; needs every
+ * domain's nx to be a multiple of 16 bytes of storage: 4 FP32, 8 FP16/BF16,
+ * 2 FP64 sites).  Synchronises the stream and rebuilds the tile table.
+ * Errors: BAD_ARG. */
 pf_status pf_set_step_config(pf_handle *h, int variant, int a, int b);
 
 /* How a step is launched over an ensemble of domains:
@@ -239,8 +243,20 @@ typedef struct pf_objective {
 pf_status pf_adjoint_step(pf_handle *h, int n_steps, const pf_objective *obj, double *J_out,
                           double grad_out[3]);
 
-/* Wait for all enqueued work; reports deferred device errors. */
+/* Wait for all enqueued work; reports deferred device errors: CUDA, or
+ * TIMEOUT when a bulk copy of the staged step kernel did not arrive within
+ * its bounded wait (the state is then invalid until pf_init_fields,
+ * pf_set_fields or pf_set_state, which clear the condition). */
 pf_status pf_sync(pf_handle *h);
+
+/* Testing only: fault injection for the bounded waits of the staged step
+ * kernel (the paper has no counterpart).  on = 1 makes variant 2 skip its
+ * bulk copies; each wait then gives up after about one second, the kernel
+ * drains and returns, and the next synchronising call reports
+ * PF_ERR_TIMEOUT.  No copy is left in flight and the GPU stays usable.
+ * on = 0 restores normal copies.  Destroys captured step graphs.
+ * Errors: BAD_ARG. */
+pf_status pf_test_drop_staged_copies(pf_handle *h, int on);
 
 /* Number of steps taken since the last initialisation. */
 long long pf_steps_taken(const pf_handle *h);

@@ -62,6 +62,7 @@ struct pf_handle {
   double* partial = nullptr;
   double* d_diag = nullptr;
   unsigned int* d_err = nullptr;  // device error bits written by the step kernels
+  int drop_copies = 0;            // testing only (pf_test_drop_staged_copies)
   double* staging = nullptr;    // FP64 device staging (largest domain x 39 planes)
   size_t staging_elems = 0;
   long long steps = 0;
@@ -403,6 +404,22 @@ static pf_status check_device_error(pf_handle* h) {
   return PF_OK;
 }
 
+// A re-initialised state is valid again: clear the device error bits.
+static pf_status clear_device_error(pf_handle* h) {
+  PF_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(unsigned int), h->stream));
+  return PF_OK;
+}
+
+extern "C" pf_status pf_test_drop_staged_copies(pf_handle* h, int on) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (on != 0 && on != 1) return fail(h, PF_ERR_BAD_ARG, "on must be 0 or 1");
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->drop_copies = on;
+  for (auto& g : h->gexec)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  return PF_OK;
+}
+
 extern "C" pf_status pf_sync(pf_handle* h) {
   if (!h) return PF_ERR_BAD_ARG;
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -478,7 +495,9 @@ extern "C" pf_status pf_init_fields(pf_handle* h, int dom, const pf_init_spec* s
     if (!std::isfinite(spec->bubbles[i])) return fail(h, PF_ERR_BAD_ARG, "non-finite bubble");
   std::vector<double> angles;
   for (int s = 0; s < spec->n_seeds; ++s) angles.push_back(spec->seeds[3 * s + 2]);
-  pf_status st = upload_grain_table(h, dom, angles);
+  pf_status st = clear_device_error(h);
+  if (st != PF_OK) return st;
+  st = upload_grain_table(h, dom, angles);
   if (st != PF_OK) return st;
   const size_t ns = 3 * (size_t)spec->n_seeds, nb = 3 * (size_t)spec->n_bubbles;
   double* buf = (double*)dev_alloc(h, (ns + nb + 1) * sizeof(double));
@@ -540,7 +559,9 @@ extern "C" pf_status pf_set_fields(pf_handle* h, int dom, const double* fields6,
       ids[i] = (uint8_t)it->second;
     }
   }
-  pf_status st = upload_grain_table(h, dom, angles);
+  pf_status st = clear_device_error(h);
+  if (st != PF_OK) return st;
+  st = upload_grain_table(h, dom, angles);
   if (st != PF_OK) return st;
   st = ensure_staging(h, 7 * nn);  // 6 x n doubles + n grain ids
   if (st != PF_OK) return st;
@@ -580,6 +601,7 @@ static StepArgs<S, R> make_step_args(const pf_handle* h, const void* pin, const 
   a.chunk = h->chunk;
   a.fields = write_fields ? reinterpret_cast<R*>(h->fields) : nullptr;
   a.err = h->d_err;
+  a.drop_copies = h->drop_copies;
   a.kp = make_kparams<R>(h->p);
   return a;
 }
@@ -883,7 +905,9 @@ extern "C" pf_status pf_set_state(pf_handle* h, int dom, const double* host_in, 
   const DomDesc& dd = h->ddesc[dom];
   const size_t nn = (size_t)dd.nx * dd.ny;
   if (n != nn * N_PHYS) return fail(h, PF_ERR_BAD_ARG, "input must hold 39 planes of nx*ny");
-  pf_status st = ensure_staging(h, nn * N_PHYS);
+  pf_status st = clear_device_error(h);
+  if (st != PF_OK) return st;
+  st = ensure_staging(h, nn * N_PHYS);
   if (st != PF_OK) return st;
   PF_CUDA(h, cudaMemcpyAsync(h->staging, host_in, nn * N_PHYS * sizeof(double),
                              cudaMemcpyHostToDevice, h->stream));

@@ -35,6 +35,7 @@ struct StepArgs {
   int chunk;                    // rows per y-march tile
   R* fields;                    // 8 field planes, or nullptr
   unsigned int* err;            // device error bits (1: a staged copy timed out), or nullptr
+  int drop_copies;              // testing only: the staged kernel skips its bulk copies
   KParams<R> kp;
 };
 

@@ -99,6 +99,7 @@ def lib() -> ctypes.CDLL:
     L.pf_set_launch.argtypes = [P, I, I, I]
     L.pf_autotune.argtypes = [P, I, ctypes.POINTER(ctypes.c_int)]
     L.pf_sync.argtypes = [P]
+    L.pf_test_drop_staged_copies.argtypes = [P, I]
     L.pf_steps_taken.argtypes = [P]
     L.pf_steps_taken.restype = ctypes.c_longlong
     L.pf_launch_count.argtypes = [P]
@@ -266,6 +267,12 @@ class Simulation:
         out = (ctypes.c_int * 3)()
         _check(lib().pf_get_step_config(self.h, out), self.h)
         return tuple(out)
+
+    def test_drop_staged_copies(self, on: bool) -> None:
+        """Testing only: make the staged step kernel skip its bulk copies, so
+        that its bounded waits time out and the next synchronising call
+        raises PFError(PF_ERR_TIMEOUT)."""
+        _check(lib().pf_test_drop_staged_copies(self.h, int(bool(on))), self.h)
 
     def sync(self) -> None:
         _check(lib().pf_sync(self.h), self.h)

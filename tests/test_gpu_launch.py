@@ -85,3 +85,30 @@ def test_set_launch_rejects_bad_arguments():
         with pytest.raises(pf.PFError) as e:
             sim.set_launch(*args)
         assert e.value.code == pf.PF_ERR_BAD_ARG
+
+
+def test_staged_copy_timeout_is_reported_and_recoverable():
+    """Failure detection of the staged kernel's bounded waits: with its bulk
+    copies dropped (host-side injection) every wait gives up after about a
+    second, the kernel drains and returns, and the host reads PF_ERR_TIMEOUT.
+    The GPU stays usable: re-initialising clears the condition and the same
+    handle then steps to the same state as a fresh one."""
+    lay = wl.random_layout(256, 48, 1, 1, rng_seed=7, R_min=4, R_max=6)
+    sim = pf.Simulation([(lay.nx, lay.ny)], lay.params, "fp16")
+    sim.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
+    assert sim.step_config()[0] == 2
+    sim.test_drop_staged_copies(True)
+    sim.step(1)
+    with pytest.raises(pf.PFError) as e:
+        sim.sync()
+    assert e.value.code == pf.PF_ERR_TIMEOUT
+    sim.test_drop_staged_copies(False)
+    sim.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
+    sim.step(3)
+    sim.sync()
+    ref = pf.Simulation([(lay.nx, lay.ny)], lay.params, "fp16")
+    ref.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
+    ref.step(3)
+    fa, fb = sim.fields(), ref.fields()
+    for k in NAMES:
+        assert np.array_equal(fa[k], fb[k]), k
