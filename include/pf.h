@@ -147,10 +147,12 @@ pf_status pf_params_default(pf_params *out);
  * out[1] M c_inf, out[2] theta_sys (Eq. eq-Tsys). */
 pf_status pf_params_derived(const pf_params *p, double out[3]);
 
-/* Create a handle for n_doms periodic domains (n_doms >= 1, each nx, ny >= 4).
- * cuda_stream: a cudaStream_t (NULL = legacy default stream).  alloc may be
- * NULL (cudaMalloc).  Allocates two copies of the 39-plane state, the field
- * planes and reduction scratch.  Errors: BAD_ARG, OOM, CUDA. */
+/* Create a handle for n_doms periodic domains (n_doms >= 1, each nx, ny in
+ * [4, 65536]; fewer than 2^32 sites in all, each domain padded to a multiple
+ * of 64).  cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * alloc may be NULL (cudaMalloc).  Allocates two copies of the 39-plane state
+ * (about 2 x 160 B per site in FP32), the field planes and reduction scratch.
+ * Errors: BAD_ARG, OOM, CUDA. */
 pf_status pf_create(const pf_params *p, const pf_domain *doms, int n_doms,
                     pf_precision prec, void *cuda_stream, const pf_allocator *alloc,
                     pf_handle **out);

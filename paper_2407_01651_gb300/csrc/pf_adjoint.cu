@@ -45,7 +45,7 @@ __device__ __forceinline__ local::Coef<R> make_coef(const KParams<R>& kp, const 
 }  // namespace
 
 // ---------------------------------------------------------------------------
-template <typename S, typename R>
+template <typename S, typename R, bool BIG>
 __global__ void __launch_bounds__(256, 2) k_adj_local(AdjArgs<S, R> a) {
   __shared__ R sphi[ADJ_TY + 2][ADJ_TX + 2], spsi[ADJ_TY + 2][ADJ_TX + 2];
   __shared__ R svx[ADJ_TY + 2][ADJ_TX + 2], svy[ADJ_TY + 2][ADJ_TX + 2];
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_local(AdjArgs<S, R> a) {
       gy = ((gy % d.ny) + d.ny) % d.ny;
       R h[9], g[5], phi, psi, pso;
       const Src9 src = sources(d, gx, gy);
-      pull_hg(st, src, h, g, phi, psi, pso);
+      pull_hg<S, R, BIG>(st, src, h, g, phi, psi, pso);
       sphi[ly][lx] = phi;
       spsi[ly][lx] = psi;
       svx[ly][lx] = ld<R>(st.ain + A_VXO * ps, src.s[0]);
@@ -78,9 +78,9 @@ __global__ void __launch_bounds__(256, 2) k_adj_local(AdjArgs<S, R> a) {
       const Src9 src = sources(d, x, y);
       local::In<R> in;
       R phi, psi;
-      pull_hg(st, src, in.h, in.g, phi, psi, in.psio);
+      pull_hg<S, R, BIG>(st, src, in.h, in.g, phi, psi, in.psio);
       SiteIn<R> si;
-      load_site(st, src, si);
+      load_site<S, R, BIG>(st, src, si);
       for (int i = 0; i < 9; ++i) in.f[i] = si.f[i];
       for (int i = 0; i < 5; ++i) in.s[i] = si.s[i];
       in.phio = si.phio;
@@ -313,7 +313,10 @@ __global__ void k_adj_omega_init(const R* __restrict__ L, const S* __restrict__ 
 // ---------------------------------------------------------------------------
 template <typename S, typename R>
 cudaError_t launch_adjoint_step(const AdjArgs<S, R>& a, int grid, cudaStream_t st) {
-  k_adj_local<S, R><<<grid, dim3(ADJ_TX, ADJ_TY), 0, st>>>(a);
+  if ((unsigned long long)a.step.plane_stride * N_POP >= (1ull << 32))
+    k_adj_local<S, R, true><<<grid, dim3(ADJ_TX, ADJ_TY), 0, st>>>(a);
+  else
+    k_adj_local<S, R, false><<<grid, dim3(ADJ_TX, ADJ_TY), 0, st>>>(a);
   const dim3 g2((a.dom.nx + 255) / 256, std::min(a.dom.ny, 65535));
   k_adj_stencil<R><<<g2, 256, 0, st>>>(a.ai, a.as, a.dom, a.step.plane_stride);
   k_adj_gather<S, R><<<g2, 256, 0, st>>>(a);

@@ -329,9 +329,10 @@ extern "C" pf_status pf_create(const pf_params* p, const pf_domain* doms, int n_
   }
   h->plane_stride = off;
   const size_t ps = (size_t)off;
-  // the step kernel addresses every buffer with 32-bit element offsets
-  if ((unsigned long long)ps * std::max<int>(N_POP, std::max<int>(N_AUX, N_FIELDS)) >= (1ull << 32)) {
-    g_create_err = "too many sites for one handle (at most ~130 million)";
+  // site indices are 32-bit (handles with more than 2^32 buffer elements
+  // switch the step kernels to 64-bit plane bases)
+  if ((unsigned long long)ps >= (1ull << 32)) {
+    g_create_err = "too many sites for one handle (at most 2^32 including padding)";
     delete h;
     return PF_ERR_BAD_ARG;
   }
@@ -612,7 +613,7 @@ static StepArgs<S, R> make_step_args(const pf_handle* h, const void* pin, const 
 template <typename S, typename R>
 static pf_status launch_all(pf_handle* h, StepArgs<S, R> a, cudaStream_t stream) {
   const int cap = h->persistent
-                      ? std::max(1, h->sms) * step_blocks_per_sm<S, R>(h->variant, h->tx, h->ty)
+                      ? std::max(1, h->sms) * step_blocks_per_sm<S, R>(h->variant, h->tx, h->ty, h->plane_stride)
                       : 1 << 30;
   if (h->launch_mode == 0) {
     a.tile_base = 0;

@@ -92,7 +92,7 @@ template <typename S, typename R>
 int staged_blocks_per_sm();
 // Resident CTAs per SM of the step kernel (for persistent grids).
 template <typename S, typename R>
-int step_blocks_per_sm(int variant, int tx, int ty);
+int step_blocks_per_sm(int variant, int tx, int ty, long long plane_stride);
 template <typename S, typename R>
 cudaError_t launch_init_spec(const InitArgs<S, R>& a, cudaStream_t st);
 template <typename S, typename R>

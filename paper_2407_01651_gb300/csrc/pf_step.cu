@@ -16,7 +16,7 @@ namespace pf {
 // Variant A: 2-D tiles.  The CTA builds phi, psi and the lagged velocity on
 // its TX x TY tile plus a one-site halo in shared memory, then each thread
 // streams, collides and stores its own site.
-template <typename S, typename R>
+template <typename S, typename R, bool BIG>
 __global__ void __launch_bounds__(256) k_step_tile(StepArgs<S, R> a) {
   extern __shared__ unsigned char smem_raw[];
   const int TX = blockDim.x, TY = blockDim.y;
@@ -38,12 +38,12 @@ __global__ void __launch_bounds__(256) k_step_tile(StepArgs<S, R> a) {
     for (int i = tid; i < SW * SH; i += nthr) {
       const int gx = wrapi(x0 + (i % SW) - 1, nx), gy = wrapi(y0 + (i / SW) - 1, ny);
       R h[9], g[5], phi, psi, po;
-      pull_hg(a, sources(d, gx, gy), h, g, phi, psi, po);
+      pull_hg<S, R, BIG>(a, sources(d, gx, gy), h, g, phi, psi, po);
       sphi[i] = phi;
       spsi[i] = psi;
-      const unsigned site = (unsigned)d.off + (unsigned)(gy * nx + gx);
-      svx[i] = ld<R>(a.ain, A_VXO * ps + site);
-      svy[i] = ld<R>(a.ain, A_VYO * ps + site);
+      const unsigned site = (unsigned)d.off + (unsigned)gy * (unsigned)nx + (unsigned)gx;
+      svx[i] = ld<R>(pbase<BIG>(a.ain, A_VXO, ps), pidx<BIG>(A_VXO, ps, site));
+      svy[i] = ld<R>(pbase<BIG>(a.ain, A_VYO, ps), pidx<BIG>(A_VYO, ps, site));
     }
     __syncthreads();
 
@@ -51,11 +51,11 @@ __global__ void __launch_bounds__(256) k_step_tile(StepArgs<S, R> a) {
     if (x < nx && y < ny) {
       const Src9 src = sources(d, x, y);
       R h[9], g[5], phi, psi, po;
-      pull_hg(a, src, h, g, phi, psi, po);
+      pull_hg<S, R, BIG>(a, src, h, g, phi, psi, po);
       const int r = threadIdx.y + 1;
       auto rows = [&](const R* X) { return Rows3<R>{X + (r - 1) * SW, X + r * SW, X + (r + 1) * SW}; };
       SiteIn<R> in;
-      load_site(a, src, in);
+      load_site<S, R, BIG>(a, src, in);
       site_update(a, d, src, in, h, g, po, rows(sphi), rows(spsi), rows(svx), rows(svy),
                   threadIdx.x + 1);
     }
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256) k_step_tile(StepArgs<S, R> a) {
 // 4-slot shared-memory ring; after one barrier the interior threads update row
 // j with the stencils read from slots j-1, j, j+1.  Every population is loaded
 // from memory once (plus 2 halo columns per YM_W).
-template <typename S, typename R>
+template <typename S, typename R, bool BIG>
 __global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 4 : 2) k_step_ymarch(StepArgs<S, R> a) {
   constexpr int RW = YM_W + 2;
   __shared__ R ring[4][4][RW];  // [phi, psi, vx_o, vy_o][slot][column]
@@ -110,11 +110,11 @@ __global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 4 : 2) k_step_yma
       if (active) {
         const Src9 src = sources(d, col, yy);
         R h[9], g[5], phi, psi, po;
-        pull_hg(a, src, h, g, phi, psi, po);
+        pull_hg<S, R, BIG>(a, src, h, g, phi, psi, po);
         ring[0][slot][sc] = phi;
         ring[1][slot][sc] = psi;
-        ring[2][slot][sc] = ld<R>(a.ain, A_VXO * ps + src.s[0]);
-        ring[3][slot][sc] = ld<R>(a.ain, A_VYO * ps + src.s[0]);
+        ring[2][slot][sc] = ld<R>(pbase<BIG>(a.ain, A_VXO, ps), pidx<BIG>(A_VXO, ps, src.s[0]));
+        ring[3][slot][sc] = ld<R>(pbase<BIG>(a.ain, A_VYO, ps), pidx<BIG>(A_VYO, ps, src.s[0]));
         if (k == 1) {
 #pragma unroll
           for (int i = 0; i < 9; ++i) hC[i] = h[i];
@@ -130,18 +130,18 @@ __global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 4 : 2) k_step_yma
       // their latency overlaps the lookahead of row j+1
       SiteIn<R> in;
       const Src9 srcj = sources(d, col, j);
-      if (interior) load_site(a, srcj, in);
+      if (interior) load_site<S, R, BIG>(a, srcj, in);
       R hL[9], gL[5], poL = R(0);
       if (active) {
         const int yn = j + 1 >= ny ? j + 1 - ny : j + 1;
         const Src9 src = sources(d, col, yn);
         R phi, psi;
-        pull_hg(a, src, hL, gL, phi, psi, poL);
+        pull_hg<S, R, BIG>(a, src, hL, gL, phi, psi, poL);
         const int slot = (j + 1) & 3;
         ring[0][slot][sc] = phi;
         ring[1][slot][sc] = psi;
-        ring[2][slot][sc] = ld<R>(a.ain, A_VXO * ps + src.s[0]);
-        ring[3][slot][sc] = ld<R>(a.ain, A_VYO * ps + src.s[0]);
+        ring[2][slot][sc] = ld<R>(pbase<BIG>(a.ain, A_VXO, ps), pidx<BIG>(A_VXO, ps, src.s[0]));
+        ring[3][slot][sc] = ld<R>(pbase<BIG>(a.ain, A_VYO, ps), pidx<BIG>(A_VYO, ps, src.s[0]));
       }
       __syncthreads();
       if (interior) {
@@ -159,37 +159,54 @@ __global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 4 : 2) k_step_yma
   }
 }
 
+// Buffers of more than 2^32 elements (plane stride x 33 population planes)
+// take the 64-bit plane-base addressing of the pull helpers.
+inline bool big_handle(long long plane_stride) {
+  return (unsigned long long)plane_stride * N_POP >= (1ull << 32);
+}
+
+template <typename S, typename R, bool BIG>
+static void launch_traversal(const StepArgs<S, R>& a, int variant, int tx, int ty, int grid,
+                             cudaStream_t st) {
+  if (variant == STEP_YMARCH) {
+    k_step_ymarch<S, R, BIG><<<grid, YM_THREADS, 0, st>>>(a);
+  } else {
+    const size_t smem = 4 * (size_t)(tx + 2) * (ty + 2) * sizeof(R);
+    k_step_tile<S, R, BIG><<<grid, dim3(tx, ty), smem, st>>>(a);
+  }
+}
+
 template <typename S, typename R>
 cudaError_t launch_step(const StepArgs<S, R>& a, int variant, int tx, int ty, int grid,
                         cudaStream_t st) {
   if (variant == STEP_STAGED) return launch_step_staged<S, R>(a, grid, st);
-
-  if (variant == STEP_YMARCH) {
-    k_step_ymarch<S, R><<<grid, YM_THREADS, 0, st>>>(a);
-  } else {
-    const size_t smem = 4 * (size_t)(tx + 2) * (ty + 2) * sizeof(R);
-    k_step_tile<S, R><<<grid, dim3(tx, ty), smem, st>>>(a);
-  }
+  if (big_handle(a.plane_stride)) launch_traversal<S, R, true>(a, variant, tx, ty, grid, st);
+  else launch_traversal<S, R, false>(a, variant, tx, ty, grid, st);
   return cudaGetLastError();
 }
 
-template <typename S, typename R>
-int step_blocks_per_sm(int variant, int tx, int ty) {
+template <typename S, typename R, bool BIG>
+static int traversal_blocks_per_sm(int variant, int tx, int ty) {
   int n = 0;
-  if (variant == STEP_STAGED) return staged_blocks_per_sm<S, R>();
-
   if (variant == STEP_YMARCH)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_ymarch<S, R>, YM_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_ymarch<S, R, BIG>, YM_THREADS, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_tile<S, R>, tx * ty,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_tile<S, R, BIG>, tx * ty,
                                                   4 * (size_t)(tx + 2) * (ty + 2) * sizeof(R));
   return n > 0 ? n : 1;
 }
 
-template int step_blocks_per_sm<double, double>(int, int, int);
-template int step_blocks_per_sm<float, float>(int, int, int);
-template int step_blocks_per_sm<__half, float>(int, int, int);
-template int step_blocks_per_sm<__nv_bfloat16, float>(int, int, int);
+template <typename S, typename R>
+int step_blocks_per_sm(int variant, int tx, int ty, long long plane_stride) {
+  if (variant == STEP_STAGED) return staged_blocks_per_sm<S, R>();
+  return big_handle(plane_stride) ? traversal_blocks_per_sm<S, R, true>(variant, tx, ty)
+                                  : traversal_blocks_per_sm<S, R, false>(variant, tx, ty);
+}
+
+template int step_blocks_per_sm<double, double>(int, int, int, long long);
+template int step_blocks_per_sm<float, float>(int, int, int, long long);
+template int step_blocks_per_sm<__half, float>(int, int, int, long long);
+template int step_blocks_per_sm<__nv_bfloat16, float>(int, int, int, long long);
 
 template cudaError_t launch_step<double, double>(const StepArgs<double, double>&, int, int, int,
                                                 int, cudaStream_t);

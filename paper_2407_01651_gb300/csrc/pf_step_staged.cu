@@ -144,7 +144,7 @@ __device__ __forceinline__ void issue_row(const StepArgs<S, R>& a, const DomDesc
   if (q >= G::NPS + G::NAS) return;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   const unsigned ps = (unsigned)a.plane_stride;
-  const unsigned row = (unsigned)d.off + (unsigned)(gy * d.nx);
+  const unsigned row = (unsigned)d.off + (unsigned)gy * (unsigned)d.nx;
   if (q < G::NPS) {
     copy_plane_row<S>(smem_u32(slot + q * G::PWS * sizeof(S)),
                       plane(a.in, pop_plane(q), ps) + row, x0, w, d.nx, G::HS, bar);
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(YM_THREADS, Stage<S, R>::MIN_BLOCKS)
     }
     const int sc = dx + 1;   // ring column
     auto site_of = [&](int row) {
-      return (unsigned)d.off + (unsigned)(wrapi(row, ny) * nx + col);
+      return (unsigned)d.off + (unsigned)wrapi(row, ny) * (unsigned)nx + (unsigned)col;
     };
     auto slot_of = [&](int row) { return (row - k0) % G::NSLOT; };
     auto wait_row = [&](int row) {

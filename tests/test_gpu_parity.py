@@ -412,3 +412,47 @@ def test_staged_rejects_ineligible_widths():
     sim16 = pf.Simulation([(20, 16)], lay.params, "fp16")   # 20 % 8 != 0
     with pytest.raises(pf.PFError):
         sim16.set_step_config(2, 16)
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_handle_beyond_2e32_buffer_elements(variant):
+    """A 11264 x 11584 lattice (130.5 million sites): its population buffer
+    holds more than 2^32 elements, so the y-march takes 64-bit plane bases
+    (the staged kernel always does).  After 2 steps, windows around seeds and
+    bubbles match oracle windows in global coordinates."""
+    nx, ny = 11264, 11584
+    assert nx * ny * 33 >= 2 ** 32
+    lay = wl.random_layout(nx, ny, 8, 16, rng_seed=37)
+    sim = pf.Simulation([(nx, ny)], lay.params, "fp32")
+    sim.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
+    sim.set_step_config(variant, 32)
+    T = 2
+    sim.step(T)
+    names = ("phi", "psi", "C", "vx", "vy", "p")
+    fg = sim.fields(0, names)
+    sim.close()                              # ~46 GB of device memory
+    W, M = 24, 2 * T
+    probe = oracle.Oracle(4, 4, lay.params, window=(nx, ny, 0, 0))
+    rho_bar = lay.params["rho_g"] + probe.mean_phi_global(lay.bubbles) * (
+        lay.params["rho_l"] - lay.params["rho_g"])
+    centers = [(int(s[0]) + 5, int(s[1])) for s in lay.seeds[:3]]
+    centers += [(int(b[0] + b[2]), int(b[1])) for b in lay.bubbles[:3]]
+    centers += [(nx - 3, ny - 3)]            # the last rows and columns (and their wrap)
+    ref, got = {k: [] for k in names}, {k: [] for k in names}
+    for cx, cy in centers:
+        x0, y0 = cx - W // 2, cy - W // 2
+        o = oracle.Oracle(W, W, lay.params, window=(nx, ny, x0, y0))
+        o.set_rho_bar(rho_bar)
+        o.init_spec(lay.seeds, lay.R_s, lay.bubbles)
+        o.step(T)
+        fo = o.fields(names)
+        ys = (np.arange(M, W - M) + y0) % ny
+        xs = (np.arange(M, W - M) + x0) % nx
+        for k in names:
+            ref[k].append(fo[k][M:W - M, M:W - M])
+            got[k].append(fg[k][np.ix_(ys, xs)])
+    del fg
+    for k in names:
+        r, g = np.concatenate(ref[k]), np.concatenate(got[k])
+        err = rel(g, r, FLOOR[k])
+        assert err <= 1e-5 * EARLY_FLOW_FACTOR.get(k, 1.0), (k, err)
