@@ -148,6 +148,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def workload_config(size: int, precision: str) -> dict:
+    """The lattice workload both arms measure (growth_lattice at size^2)."""
+    return {"workload": f"{size}x{size} periodic lattice, 64 seeds (R=6, theta~U[0,pi/2)), "
+                        "128 bubbles (R~U[8,40]), seed 2",
+            "lattice": [size, size], "precision": precision}
+
+
 def cpu_oracle_sample(steps_hint: int, target_s: float, side: int | None = None) -> dict:
     """Time the FP64 oracle (test infrastructure, run as a child process) on a
     window of the 4096^2 workload; all host cores."""
@@ -194,10 +201,11 @@ def run_reference(args) -> None:
     line = {
         "impl": "reference", "metric": METRIC, "value": base["value"], "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": 4096 * 4096 / (base["value"] * 1e3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "4096x4096 periodic lattice, 64 seeds, 128 bubbles (window sample)",
-                   "precision": "fp64-cpu"},
+        "config": dict(workload_config(4096, "fp64"),
+                       sample="bounded window of the lattice, see cpu_baseline"),
         "cpu_baseline": base,
         "e2e": {"value": base["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -486,12 +494,10 @@ def main() -> None:
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[args.precision], "data": "synthetic",
-            "config": {"workload": f"{lay.nx}x{lay.ny} periodic lattice, 64 seeds (R=6, "
-                                   "theta~U[0,pi/2)), 128 bubbles (R~U[8,40]), seed 2",
-                       "lattice": [lay.nx, lay.ny], "precision": args.precision,
-                       "parallelism": f"replicas x{world}",
-                       "l2": f"inputs {(bpl - 1) * sites / 1e9:.1f} GB read+written per step "
-                             "> L2 (no flush)"},
+            "config": dict(workload_config(lay.nx, args.precision),
+                           parallelism=f"replicas x{world}",
+                           l2=f"inputs {(bpl - 1) * sites / 1e9:.1f} GB read+written per step "
+                              "> L2 (no flush)"),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "step_config": list(sim.step_config()),
             "adjoint": adj,
