@@ -389,6 +389,7 @@ def main() -> None:
     if args.variant is not None:
         sim.set_step_config(args.variant, args.chunk or 64, args.tile_b)
     sites = lay.nx * lay.ny
+    d_init = sim.reduce(0)
     sim.step(args.warmup)
     sim.sync()
 
@@ -415,6 +416,10 @@ def main() -> None:
     d = sim.reduce(0)
     if d["nonfinite"]:
         raise SystemExit(f"non-finite fields after the timed run: {d['nonfinite']}")
+    conservation = {"steps": args.warmup + args.steps,
+                    "sum_phi_rel_drift": d["sum_phi"] / d_init["sum_phi"] - 1.0,
+                    "sum_C_rel_drift": d["sum_C"] / d_init["sum_C"] - 1.0,
+                    "reductions": "FP64 on the GPU"}
 
     ms_per_step = ms_max / args.steps
     value = world * sites * args.steps / (ms_max / 1e3) / 1e6
@@ -501,6 +506,7 @@ def main() -> None:
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "step_config": list(sim.step_config()),
             "adjoint": adj,
+            "conservation": conservation,
             "clocks": clk,
         }
         print(json.dumps(line))

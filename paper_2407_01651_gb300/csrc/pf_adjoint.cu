@@ -220,47 +220,72 @@ template <typename S, typename R>
 __global__ void __launch_bounds__(256) k_adj_gather(AdjArgs<S, R> a) {
   const DomDesc d = a.dom;
   const unsigned ps = (unsigned)a.step.plane_stride;
-  const R* A = a.ai;
-  const R* AS = a.as;
-  const S* P = a.step.in;
-  const R* X = a.step.ain;
-  R* L = a.lam_out;
+  const R* __restrict__ A = a.ai;
+  const R* __restrict__ AS = a.as;
+  const S* __restrict__ P = a.step.in;
+  const R* __restrict__ X = a.step.ain;
+  R* __restrict__ L = a.lam_out;
   constexpr int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= d.nx) return;
   for (int y = blockIdx.y; y < d.ny; y += gridDim.y) {
     const Src9 src = sources(d, x, y);
     const unsigned site = src.s[0];
+    // every input of the site first (independent loads), then the stores
+    R lf[9], lh[9], ls[5], lgpre[5], lgpost[5];
+    const R as0_dst[9] = {__ldg(plane(AS, 0, ps) + src.s[OPP[0]]),
+                          __ldg(plane(AS, 0, ps) + src.s[OPP[1]]),
+                          __ldg(plane(AS, 0, ps) + src.s[OPP[2]]),
+                          __ldg(plane(AS, 0, ps) + src.s[OPP[3]]),
+                          __ldg(plane(AS, 0, ps) + src.s[OPP[4]]),
+                          __ldg(plane(AS, 0, ps) + src.s[OPP[5]]),
+                          __ldg(plane(AS, 0, ps) + src.s[OPP[6]]),
+                          __ldg(plane(AS, 0, ps) + src.s[OPP[7]]),
+                          __ldg(plane(AS, 0, ps) + src.s[OPP[8]])};
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
       const unsigned t = src.s[OPP[q]];   // x + c_q
-      plane(L, 0 + q, ps)[site] = plane(A, AI_F + q, ps)[t];
-      plane(L, 9 + q, ps)[site] = plane(A, AI_H + q, ps)[t] + plane(AS, 0, ps)[t];
+      lf[q] = __ldg(plane(A, AI_F + q, ps) + t);
+      lh[q] = __ldg(plane(A, AI_H + q, ps) + t) + as0_dst[q];
     }
-    const R rr_own = plane(X, A_RR, ps)[site];
+    const R rr_own = __ldg(plane(X, A_RR, ps) + site);
+    const R apsio = __ldg(plane(A, AI_PSIO, ps) + site);
+    const R as1 = __ldg(plane(AS, 1, ps) + site);
     R lrr = R(0);
-    const R apsio = plane(A, AI_PSIO, ps)[site];
-    const R as1 = plane(AS, 1, ps)[site];
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
       const unsigned t = src.s[OPP[q]];   // destination of q
       const unsigned sq = src.s[q];       // source of q
-      plane(L, 29 + q, ps)[site] = plane(A, AI_S + q, ps)[t];
-      const R ag_own = plane(A, AI_G + q, ps)[site] + as1;
-      const R ag_dst = plane(A, AI_G + q, ps)[t] + plane(AS, 1, ps)[t];
-      const R rr_src = plane(X, A_RR, ps)[sq];
-      plane(L, 18 + q, ps)[site] = ag_own * (R(1) - rr_src) + apsio;
-      plane(L, 23 + q, ps)[site] = ag_dst * rr_own;
+      ls[q] = __ldg(plane(A, AI_S + q, ps) + t);
+      const R ag_own = __ldg(plane(A, AI_G + q, ps) + site) + as1;
+      const R ag_dst = __ldg(plane(A, AI_G + q, ps) + t) + __ldg(plane(AS, 1, ps) + t);
+      const R rr_src = __ldg(plane(X, A_RR, ps) + sq);
+      lgpre[q] = ag_own * (R(1) - rr_src) + apsio;
+      lgpost[q] = ag_dst * rr_own;
       const R gq_own = ld<R>(plane(P, P_GPOST + q, ps), site);
       const R gp_dst = ld<R>(plane(P, P_GPRE + q, ps), t);
       lrr += ag_dst * (gq_own - gp_dst);
     }
+    const R l34 = __ldg(plane(A, AI_PHIO, ps) + site), l35 = __ldg(plane(A, AI_CO, ps) + site);
+    const R l36 = __ldg(plane(AS, 2, ps) + site), l37 = __ldg(plane(AS, 3, ps) + site);
+    const R l38 = __ldg(plane(A, AI_QO, ps) + site);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      plane(L, 0 + q, ps)[site] = lf[q];
+      plane(L, 9 + q, ps)[site] = lh[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      plane(L, 18 + q, ps)[site] = lgpre[q];
+      plane(L, 23 + q, ps)[site] = lgpost[q];
+      plane(L, 29 + q, ps)[site] = ls[q];
+    }
     plane(L, 28, ps)[site] = lrr;
-    plane(L, 34, ps)[site] = plane(A, AI_PHIO, ps)[site];
-    plane(L, 35, ps)[site] = plane(A, AI_CO, ps)[site];
-    plane(L, 36, ps)[site] = plane(AS, 2, ps)[site];
-    plane(L, 37, ps)[site] = plane(AS, 3, ps)[site];
-    plane(L, 38, ps)[site] = plane(A, AI_QO, ps)[site];
+    plane(L, 34, ps)[site] = l34;
+    plane(L, 35, ps)[site] = l35;
+    plane(L, 36, ps)[site] = l36;
+    plane(L, 37, ps)[site] = l37;
+    plane(L, 38, ps)[site] = l38;
   }
 }
 
