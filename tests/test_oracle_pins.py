@@ -508,3 +508,32 @@ def test_complex_step_matches_finite_difference():
             js.append(od.objective()[0])
         fd = (js[0] - js[1]) / (2 * h)
         assert math.isclose(dj, fd, rel_tol=1e-4, abs_tol=1e-9), (name, dj, fd)
+
+
+def test_diagnostics_and_objective_against_their_definitions():
+    """The FP64 diagnostics (S12: totals, gas centroid, Laplace probe means,
+    max |v|) and the final-state objective J = mean h(psi) + y_c / L_y
+    (readings R16, R17) recomputed with numpy from the oracle's own fields."""
+    lay = wl.random_layout(64, 48, 2, 2, rng_seed=13, R_min=4, R_max=8)
+    o = oracle.Oracle(lay.nx, lay.ny, dict(lay.params, g=1e-5))
+    o.init_spec(lay.seeds, lay.R_s, lay.bubbles)
+    o.step(15)
+    f = o.fields(("phi", "psi", "C", "p", "vx", "vy"))
+    phi, psi, C, p = f["phi"], f["psi"], f["C"], f["p"]
+    y, x = np.mgrid[0:lay.ny, 0:lay.nx].astype(float)
+    xc, yc, R, W = lay.bubbles[0][0], lay.bubbles[0][1], lay.bubbles[0][2], 4.0
+
+    def mi(d, L):
+        return (d + 0.5 * L) % L - 0.5 * L
+
+    r = np.hypot(mi(x - xc, lay.nx), mi(y - yc, lay.ny))
+    inside, outside = r < R - 2 * W, r > R + 4 * W
+    ref = {"sum_phi": phi.sum(), "sum_C": C.sum(), "sum_hpsi": (0.5 * (1 + psi)).sum(),
+           "gas": (1 - phi).sum(), "gas_x": (x * (1 - phi)).sum(), "gas_y": (y * (1 - phi)).sum(),
+           "p_in_sum": p[inside].sum(), "p_in_n": inside.sum(), "p_out_sum": p[outside].sum(),
+           "p_out_n": outside.sum(), "max_v": np.hypot(f["vx"], f["vy"]).max(), "nonfinite": 0}
+    d = o.diag((xc, yc, R, W))
+    for k, v in ref.items():
+        assert math.isclose(d[k], float(v), rel_tol=1e-12, abs_tol=1e-15), (k, d[k], v)
+    J = (0.5 * (1 + psi)).mean() + ((y * (1 - phi)).sum() / (1 - phi).sum()) / lay.ny
+    assert math.isclose(o.objective()[0], J, rel_tol=1e-13)
