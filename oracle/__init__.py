@@ -27,11 +27,14 @@ _BUILD = os.path.join(_HERE, "_build")
 PARAM_NAMES = (
     "rho_l", "rho_g", "nu", "sigma", "W_phi", "M_phi", "beta_phi", "beta_psi",
     "beta_inter", "W0", "tau0", "eps_s", "k", "D", "Omega", "g", "grad_eps",
-    "s_e", "s_eps", "grad_eps_at",
+    "s_e", "s_eps", "grad_eps_at", "thermal", "Le", "latent", "theta0", "cp",
 )
+# Defaults of the temperature-coupling parameters: isothermal closure
+# (Eq. eq-Tsys), so a parameter dict without them runs the isothermal model.
+THERMAL_DEFAULTS = dict(thermal=0.0, Le=1.0, latent=1.0, theta0=-0.55, cp=10.0)
 # Field order of or_get_fields.
-FIELDS = ("phi", "psi", "C", "U", "p", "vx", "vy", "mu")
-N_STATE_PLANES = 39
+FIELDS = ("phi", "psi", "C", "U", "p", "vx", "vy", "mu", "theta")
+N_STATE_PLANES = 39          # isothermal; thermal mode adds e[5] and H_o
 
 _lock = threading.Lock()
 _libs: dict[str, ctypes.CDLL] = {}
@@ -70,7 +73,7 @@ def _lib(tag: str) -> ctypes.CDLL:
         lib.or_set_rho_bar.argtypes = [P, ctypes.c_double]
         lib.or_get_rho_bar.restype = ctypes.c_double
         lib.or_get_rho_bar.argtypes = [P]
-        lib.or_init_from_fields.argtypes = [P, D, D, D, D, D, D]
+        lib.or_init_from_fields.argtypes = [P, D, D, D, D, D, D, D]
         lib.or_set_orientation.argtypes = [P, D, ctypes.c_int]
         lib.or_fields_from_spec.argtypes = [P, D, ctypes.c_int, ctypes.c_double, D,
                                             ctypes.c_int, D, D, D]
@@ -98,6 +101,11 @@ def _lib(tag: str) -> ctypes.CDLL:
         lib.or_mean_phi_global.argtypes = [P, D, ctypes.c_int]
         lib.or_get_steps.restype = ctypes.c_long
         lib.or_get_steps.argtypes = [P]
+        lib.or_state_planes.restype = ctypes.c_int
+        lib.or_state_planes.argtypes = [P]
+        lib.or_teq_th.argtypes = [ctypes.c_double] * 4 + [D]
+        lib.or_thermal_coefs.argtypes = [P, ctypes.c_double, D]
+        lib.or_thermal_totals.argtypes = [P, D]
         _libs[tag] = lib
         return lib
 
@@ -126,7 +134,8 @@ class Oracle:
         self.h = self.lib.or_new(self.nx, self.ny)
         if not self.h:
             raise MemoryError("oracle allocation failed")
-        pv = _f64([float(params[k]) for k in PARAM_NAMES])
+        pv = _f64([float(params[k] if k in params else THERMAL_DEFAULTS[k])
+                   for k in PARAM_NAMES])
         self.lib.or_set_params(self.h, _dp(pv))
         self._pv = pv
         if window is not None:
@@ -178,8 +187,9 @@ class Oracle:
         s = np.ascontiguousarray(_f64(seeds).reshape(-1, 3))
         self.lib.or_set_orientation(self.h, _dp(s), len(s))
 
-    def init_fields(self, phi, psi, C, vx=None, vy=None, p=None) -> None:
-        arrs = [_f64(a).ravel() if a is not None else None for a in (phi, psi, C, vx, vy, p)]
+    def init_fields(self, phi, psi, C, vx=None, vy=None, p=None, theta=None) -> None:
+        arrs = [_f64(a).ravel() if a is not None else None
+                for a in (phi, psi, C, vx, vy, p, theta)]
         self._keep = arrs
         self.lib.or_init_from_fields(self.h, *[_dp(a) for a in arrs])
 
@@ -200,9 +210,22 @@ class Oracle:
         return {nm: out[i] for i, nm in enumerate(sel)}
 
     def state(self) -> np.ndarray:
-        out = np.empty(N_STATE_PLANES * self.nx * self.ny)
+        npl = self.lib.or_state_planes(self.h)
+        out = np.empty(npl * self.nx * self.ny)
         self.lib.or_get_state(self.h, _dp(out))
-        return out.reshape(N_STATE_PLANES, self.ny, self.nx)
+        return out.reshape(npl, self.ny, self.nx)
+
+    def thermal_coefs(self, U: float) -> dict[str, float]:
+        """F(U), k_T and the temperature flux rate s_th."""
+        out = np.zeros(3)
+        self.lib.or_thermal_coefs(self.h, float(U), _dp(out))
+        return dict(zip(("F", "kT", "s_th"), out.tolist()))
+
+    def thermal_totals(self) -> dict[str, float]:
+        """Sum of the temperature populations (total rho H), sum theta, sum psi."""
+        out = np.zeros(3)
+        self.lib.or_thermal_totals(self.h, _dp(out))
+        return dict(zip(("sum_e", "sum_theta", "sum_psi"), out.tolist()))
 
     def diag(self, probe=(0.0, 0.0, 0.0, 0.0)) -> dict[str, float]:
         out = np.zeros(12)
@@ -258,6 +281,12 @@ def heq_cac(phi, vx, vy):
 def seq_sol(C, jx, jy):
     out = np.zeros(5)
     _lib("d").or_seq_sol(float(C), float(jx), float(jy), _dp(out))
+    return out
+
+
+def teq_th(rhoH, theta, jx, jy):
+    out = np.zeros(5)
+    _lib("d").or_teq_th(float(rhoH), float(theta), float(jx), float(jy), _dp(out))
     return out
 
 

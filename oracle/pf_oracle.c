@@ -107,7 +107,13 @@ static void build_inverse(void) {
 enum {
   P_RHO_L, P_RHO_G, P_NU, P_SIGMA, P_W_PHI, P_M_PHI, P_BETA_PHI, P_BETA_PSI,
   P_BETA_INTER, P_W0, P_TAU0, P_EPS_S, P_K, P_D, P_OMEGA, P_G, P_GRAD_EPS,
-  P_S_E, P_S_EPS, P_GRAD_EPS_AT, NPAR
+  P_S_E, P_S_EPS, P_GRAD_EPS_AT,
+  /* temperature coupling (Section 2.1 and Appendix B): P_THERMAL = 0 keeps the
+   * isothermal closure theta = theta_sys, F(U) = 1 (Eq. eq-Tsys); 1 solves the
+   * temperature equation with Lewis number Le = alpha / D, latent-heat factor
+   * c_p^s / c_p, uniform initial temperature theta0 and lattice heat capacity
+   * c_p (reading R28). */
+  P_THERMAL, P_LE, P_LATENT, P_THETA0, P_CP, NPAR
 };
 
 typedef struct {
@@ -120,18 +126,21 @@ typedef struct {
   /* state after the last step: post-collision populations + lagged values */
   real_t *f[9], *h[9], *gpre[5], *gpost[5], *rr, *s[5];
   real_t *phi_o, *C_o, *vx_o, *vy_o, *Q_o;
+  real_t *e[5], *H_o;       /* temperature populations and lagged H (thermal mode) */
   double *cth, *sth;        /* grain orientation per site (reading R10) */
-  /* macroscopic fields of the last step: phi, psi, C, U, p, vx, vy, mu_phi */
-  real_t *fld[8];
+  /* macroscopic fields of the last step: phi, psi, C, U, p, vx, vy, mu_phi, theta */
+  real_t *fld[9];
   /* scratch for the streaming pass */
   real_t *fS[9], *hS[9], *gS[5], *sS[5], *phiS, *psiS, *CS, *psiOld;
+  real_t *eS[5], *US;
   /* next-state buffers */
   real_t *nf[9], *nh[9], *ngpre[5], *ngpost[5], *nrr, *ns[5];
   real_t *nphi_o, *nC_o, *nvx_o, *nvy_o, *nQ_o;
+  real_t *ne[5], *nH_o;
   real_t *block;
 } ostate;
 
-enum { F_PHI, F_PSI, F_C, F_U, F_P, F_VX, F_VY, F_MU };
+enum { F_PHI, F_PSI, F_C, F_U, F_P, F_VX, F_VY, F_MU, F_THETA, NFLD };
 
 /* Derived coefficients of the isothermal closure and the thin-interface map. */
 typedef struct {
@@ -141,6 +150,8 @@ typedef struct {
   real_t kappa;    /* sqrt(2 beta_phi) / W_phi                                   */
   real_t fs_coef;  /* 6 sigma / ((phi_l-phi_g)^3 W_phi sqrt(2 beta_phi))          */
   real_t s_nu, s_q, s_phi;
+  real_t kT;       /* thermal conductivity k_T = Le D rho_l c_p                   */
+  real_t s_th;     /* k_T = (1/s_th - 1/2) c_s^2 (Appendix B, temperature)       */
 } derived_t;
 
 static derived_t derive(const ostate *st) {
@@ -159,6 +170,10 @@ static derived_t derive(const ostate *st) {
   d.s_q = 8.0 * (2.0 - d.s_nu) / (8.0 - d.s_nu);   /* reading R7 */
   /* CAC mobility M_phi = (1/s - 1/2) c_s^2. */
   d.s_phi = 1.0 / (p[P_M_PHI] / CS2 + 0.5);
+  /* Temperature (reading R28): Le = alpha / D (Section 2.1) with alpha =
+   * k_T / (rho_l c_p) the liquid's diffusivity and k_T uniform. */
+  d.kT = p[P_LE] * p[P_D] * p[P_RHO_L] * p[P_CP];
+  d.s_th = 1.0 / (d.kT / CS2 + 0.5);
   return d;
 }
 
@@ -175,8 +190,9 @@ ostate *or_new(int nx, int ny) {
   st->nx = nx; st->ny = ny; st->n = nx * ny;
   st->NX = nx; st->NY = ny; st->x0 = 0; st->y0 = 0;
   size_t n = (size_t)st->n;
-  /* 2 state copies + 8 fields + streaming scratch (28 pops + 4 moments) */
-  size_t nplanes = 2 * NPLANES + 8 + 28 + 4;
+  /* 2 state copies (+ 6 temperature planes each) + 9 fields + streaming
+   * scratch (28 pops + 4 moments, + 5 temperature pops + U) */
+  size_t nplanes = 2 * (NPLANES + 6) + 9 + 28 + 4 + 6;
   st->block = (real_t *)calloc(nplanes * n, sizeof(real_t));
   st->cth = (double *)calloc(n, sizeof(double));
   st->sth = (double *)calloc(n, sizeof(double));
@@ -193,6 +209,8 @@ ostate *or_new(int nx, int ny) {
   TAKE(st->rr);
   for (int i = 0; i < 5; ++i) TAKE(st->s[i]);
   TAKE(st->phi_o); TAKE(st->C_o); TAKE(st->vx_o); TAKE(st->vy_o); TAKE(st->Q_o);
+  for (int i = 0; i < 5; ++i) TAKE(st->e[i]);
+  TAKE(st->H_o);
   for (int i = 0; i < 9; ++i) TAKE(st->nf[i]);
   for (int i = 0; i < 9; ++i) TAKE(st->nh[i]);
   for (int i = 0; i < 5; ++i) TAKE(st->ngpre[i]);
@@ -200,12 +218,16 @@ ostate *or_new(int nx, int ny) {
   TAKE(st->nrr);
   for (int i = 0; i < 5; ++i) TAKE(st->ns[i]);
   TAKE(st->nphi_o); TAKE(st->nC_o); TAKE(st->nvx_o); TAKE(st->nvy_o); TAKE(st->nQ_o);
-  for (int i = 0; i < 8; ++i) TAKE(st->fld[i]);
+  for (int i = 0; i < 5; ++i) TAKE(st->ne[i]);
+  TAKE(st->nH_o);
+  for (int i = 0; i < NFLD; ++i) TAKE(st->fld[i]);
   for (int i = 0; i < 9; ++i) TAKE(st->fS[i]);
   for (int i = 0; i < 9; ++i) TAKE(st->hS[i]);
   for (int i = 0; i < 5; ++i) TAKE(st->gS[i]);
   for (int i = 0; i < 5; ++i) TAKE(st->sS[i]);
   TAKE(st->phiS); TAKE(st->psiS); TAKE(st->CS); TAKE(st->psiOld);
+  for (int i = 0; i < 5; ++i) TAKE(st->eS[i]);
+  TAKE(st->US);
 #undef TAKE
   for (size_t i = 0; i < n; ++i) st->cth[i] = 1.0;
   return st;
@@ -256,15 +278,28 @@ static real_t supersat(const ostate *st, real_t C, real_t psi) {
 /* Q_psi = -[f2' + d_psi f3 + lambda p'(psi) (theta + M c_inf U)], Appendix B,
  * with f2 = beta_psi (1-psi^2)^2, f3 = beta_inter (1-phi)^2 (1+psi)^2
  * (Eq. eq-douWell, eq-f3Inter) and lambda p' = lambda' (1-psi^2)^2. */
-static real_t q_psi(const ostate *st, const derived_t *d, real_t phi, real_t psi,
-                    real_t U) {
+static real_t q_psi_at(const ostate *st, const derived_t *d, real_t phi, real_t psi,
+                       real_t U, real_t theta) {
   const real_t *p = st->par;
   real_t one_m = 1.0 - psi * psi;
   real_t f2p = -4.0 * p[P_BETA_PSI] * psi * one_m;
   real_t f3p = 2.0 * p[P_BETA_INTER] * (1.0 - phi) * (1.0 - phi) * (1.0 + psi);
-  real_t drive = d->lam * one_m * one_m * (d->theta + d->Mcinf * U);
+  real_t drive = d->lam * one_m * one_m * (theta + d->Mcinf * U);
   return -(f2p + f3p + drive);
 }
+
+/* Isothermal form: theta = theta_sys everywhere (Eq. eq-Tsys). */
+static real_t q_psi(const ostate *st, const derived_t *d, real_t phi, real_t psi,
+                    real_t U) {
+  return q_psi_at(st, d, phi, psi, U, d->theta);
+}
+
+/* F(U) = 1/Le + M c_inf [1 + (1-k) U] (Section 2.1, thin-interface limit). */
+static real_t f_of_u(const ostate *st, const derived_t *d, real_t U) {
+  return 1.0 / st->par[P_LE] + d->Mcinf * (1.0 + (1.0 - st->par[P_K]) * U);
+}
+
+static int thermal_on(const ostate *st) { return RE_(st->par[P_THERMAL]) != 0.0; }
 
 /* Anisotropy of the solid-liquid interface for a grain rotated by theta
  * (reading R10).  g = grad psi, n_psi = -g/|g|_reg (Section 2.1, regularised
@@ -322,6 +357,16 @@ static void heq_cac(real_t phi, real_t vx, real_t vy, real_t out[9]) {
 static void seq_sol(real_t C, real_t jx, real_t jy, real_t out[5]) {
   for (int i = 0; i < 5; ++i)
     out[i] = W5[i] * C + W5[i] * (CX[i] * jx + CY[i] * jy) / CS2;
+}
+
+/* Temperature equilibrium (Appendix B) for the variable H = c_p theta -
+ * c_p^s h(psi):  g_0^eq = rho H + (w_0 - 1) theta,
+ *                g_i^eq = w_i theta + w_i c_i . (rho H v) / c_s^2  (i != 0),
+ * so that sum g^eq = rho H, sum c g^eq = rho H v, sum c c g^eq = c_s^2 theta I. */
+static void teq_th(real_t rhoH, real_t theta, real_t jx, real_t jy, real_t out[5]) {
+  for (int i = 0; i < 5; ++i)
+    out[i] = W5[i] * theta + W5[i] * (CX[i] * jx + CY[i] * jy) / CS2;
+  out[0] = rhoH + (W5[0] - 1.0) * theta;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -382,10 +427,13 @@ static double min_image(double d, double L) {
 /* Set every population to its equilibrium for given macroscopic fields, the
  * lagged values equal to the current ones (first-step time derivatives are
  * zero) and the dendrite time-stretch factor 1/a_s^2 = 1.  Reading R20 of the
- * initial state.  Arrays: phi, psi, C, vx, vy, p (host, n each). */
+ * initial state.  Arrays: phi, psi, C, vx, vy, p, theta (host, n each; vx, vy,
+ * p and theta may be NULL: zero velocity and pressure, theta0).  In thermal
+ * mode the lagged dendrite source starts at its pointwise part Q_psi / F(U)
+ * (reading R29). */
 void or_init_from_fields(ostate *st, const double *phi, const double *psi,
                          const double *C, const double *vx, const double *vy,
-                         const double *p) {
+                         const double *p, const double *theta) {
   derived_t d = derive(st);
   const real_t *par = st->par;
   double sphi = 0;
@@ -407,7 +455,22 @@ void or_init_from_fields(ostate *st, const double *phi, const double *psi,
     for (int i = 0; i < 5; ++i) st->s[i][idx] = t5[i];
     st->phi_o[idx] = ph; st->C_o[idx] = c;
     st->vx_o[idx] = ux; st->vy_o[idx] = uy;
-    st->Q_o[idx] = q_psi(st, &d, ph, ps, U);
+    if (thermal_on(st)) {
+      /* H = c_p theta - c_p^s h(psi) = c_p [theta - (c_p^s/c_p) h(psi)],
+       * h = (1+psi)/2 (Appendix B) */
+      real_t th = theta ? theta[idx] : par[P_THETA0];
+      real_t H = par[P_CP] * (th - par[P_LATENT] * 0.5 * (1.0 + ps));
+      teq_th(rho * H, th, rho * H * ux, rho * H * uy, t5);
+      for (int i = 0; i < 5; ++i) st->e[i][idx] = t5[i];
+      st->H_o[idx] = H;
+      st->Q_o[idx] = q_psi_at(st, &d, ph, ps, U, th) / f_of_u(st, &d, U);
+      st->fld[F_THETA][idx] = th;
+    } else {
+      for (int i = 0; i < 5; ++i) st->e[i][idx] = 0.0;
+      st->H_o[idx] = 0.0;
+      st->Q_o[idx] = q_psi(st, &d, ph, ps, U);
+      st->fld[F_THETA][idx] = d.theta;
+    }
     st->fld[F_PHI][idx] = ph; st->fld[F_PSI][idx] = ps; st->fld[F_C][idx] = c;
     st->fld[F_U][idx] = U; st->fld[F_P][idx] = pp;
     st->fld[F_VX][idx] = ux; st->fld[F_VY][idx] = uy; st->fld[F_MU][idx] = 0.0;
@@ -508,7 +571,7 @@ int or_init_spec(ostate *st, const double *seeds, int n_seeds, double R_s,
   or_set_orientation(st, seeds, n_seeds);
   or_fields_from_spec(st, seeds, n_seeds, R_s, bubbles, n_bub, buf, buf + n,
                       buf + 2 * n);
-  or_init_from_fields(st, buf, buf + n, buf + 2 * n, NULL, NULL, NULL);
+  or_init_from_fields(st, buf, buf + n, buf + 2 * n, NULL, NULL, NULL, NULL);
   free(buf);
   return 0;
 }
@@ -549,6 +612,13 @@ static void pass_stream(ostate *st) {
       st->psiS[idx] = psi;
       st->CS[idx] = C;
       st->psiOld[idx] = psio;
+      /* temperature populations (thermal mode): plain pull, and the
+       * supersaturation field whose gradient enters grad F(U) */
+      for (int i = 0; i < 5; ++i) {
+        int src = wrap(y - CY[i], ny) * nx + wrap(x - CX[i], nx);
+        st->eS[i][idx] = st->e[i][src];
+      }
+      st->US[idx] = supersat(st, C, psi);
     }
 }
 
@@ -582,6 +652,7 @@ static void pass_collide(ostate *st) {
   const real_t rl = par[P_RHO_L], rg = par[P_RHO_G];
   const real_t eps = par[P_EPS_S], k = par[P_K];
   const real_t ge2 = par[P_GRAD_EPS] * par[P_GRAD_EPS];
+  const int thermal = thermal_on(st);
 #pragma omp parallel for schedule(static)
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
@@ -645,7 +716,14 @@ static void pass_collide(ostate *st) {
 
       /* --- solute --- */
       const real_t U = supersat(st, C, psi);
-      const real_t Q = q_psi(st, &d, phi, psi, U);
+      /* --- temperature (thermal mode, Appendix B): rho H = sum_i g_i and
+       * theta = H / c_p + (c_p^s / c_p) h(psi), h = (1+psi)/2 --- */
+      real_t rhoH = 0.0, theta = d.theta;
+      if (thermal) {
+        for (int i = 0; i < 5; ++i) rhoH += st->eS[i][idx];
+        theta = rhoH / (rho * par[P_CP]) + par[P_LATENT] * 0.5 * (1.0 + psi);
+      }
+      const real_t Q = thermal ? q_psi_at(st, &d, phi, psi, U, theta) : q_psi(st, &d, phi, psi, U);
       const real_t Wpsi = par[P_W0] * as;                /* reading R11 */
       const real_t dpsi = psi - psio;                    /* reading R4 */
       /* antitrapping direction grad psi / |grad psi| with its own, larger
@@ -684,18 +762,34 @@ static void pass_collide(ostate *st) {
         collide9(hh, heq, S, G, out);
         for (int i = 0; i < 9; ++i) st->nh[i][idx] = out[i];
       }
-      /* --- dendrite collision: D2Q5 MRT of Appendix B with F == 1 --- */
+      /* --- dendrite collision: D2Q5 MRT of Appendix B.  Isothermal: F == 1
+       * (reading R8).  Thermal: the source of the rewritten equation,
+       *   tau0 F_psi = Q_psi / F + W0^2 / F^2 grad F . (a_s^2 grad psi + N),
+       * with grad F = M c_inf (1-k) grad U, and the rate from
+       *   W0^2 a_s^2 / (tau0 F) = (1/s1 - 1/2) cs2. --- */
+      real_t Qeff = Q;
       {
         real_t gg[5], geq[5], G[5], Fd[5], out[5];
+        real_t Fu = 1.0;
+        if (thermal) {
+          Fu = f_of_u(st, &d, U);
+          real_t gux, guy;
+          grad9(st->US, nx, ny, x, y, &gux, &guy);
+          const real_t Xx = as2 * gsx + Nx, Xy = as2 * gsy + Ny;
+          const real_t dFx = d.Mcinf * (1.0 - k) * gux, dFy = d.Mcinf * (1.0 - k) * guy;
+          Qeff = Q / Fu + par[P_W0] * par[P_W0] / (Fu * Fu) * (dFx * Xx + dFy * Xy);
+        }
         for (int i = 0; i < 5; ++i) {
           gg[i] = st->gS[i][idx];
           geq[i] = W5[i] * psi;
           G[i] = -W5[i] * (CX[i] * Nx + CY[i] * Ny) / as2;
           /* dt F + dt^2/2 dF/dt with a backward difference (reading R4) */
-          Fd[i] = W5[i] * Q / par[P_TAU0] + 0.5 * W5[i] * (Q - Qo) / par[P_TAU0];
+          Fd[i] = W5[i] * Qeff / par[P_TAU0] + 0.5 * W5[i] * (Qeff - Qo) / par[P_TAU0];
         }
-        /* W0^2 a_s^2 / tau0 = (1/s1 - 1/2) cs2 */
-        const real_t s1 = 1.0 / (par[P_W0] * par[P_W0] * as2 / (par[P_TAU0] * CS2) + 0.5);
+        /* W0^2 a_s^2 / (tau0 F) = (1/s1 - 1/2) cs2 */
+        const real_t s1 = thermal
+            ? 1.0 / (par[P_W0] * par[P_W0] * as2 / (par[P_TAU0] * Fu * CS2) + 0.5)
+            : 1.0 / (par[P_W0] * par[P_W0] * as2 / (par[P_TAU0] * CS2) + 0.5);
         const real_t S[5] = {1, s1, s1, 1, 1};
         collide5(gg, geq, S, G, Fd, out);
         for (int i = 0; i < 5; ++i) {
@@ -727,11 +821,31 @@ static void pass_collide(ostate *st) {
         collide5(ss, seq, S, G, Fd, out);
         for (int i = 0; i < 5; ++i) st->ns[i][idx] = out[i];
       }
+      /* --- temperature collision (thermal mode): D2Q5 MRT of Appendix B,
+       * equilibrium teq_th with rho H v, G_i = w_i c_i . d_t(rho H v) / cs2 with
+       * a backward difference (reading R4), k_T = (1/s - 1/2) cs2 --- */
+      if (thermal) {
+        real_t ee[5], teq[5], G[5], Fd[5] = {0, 0, 0, 0, 0}, out[5];
+        const real_t rho_o = rg + phio * (rl - rg);
+        const real_t jx = rhoH * vx, jy = rhoH * vy;
+        teq_th(rhoH, theta, jx, jy, teq);
+        const real_t Gx = jx - rho_o * st->H_o[idx] * vxo;
+        const real_t Gy = jy - rho_o * st->H_o[idx] * vyo;
+        for (int i = 0; i < 5; ++i) {
+          ee[i] = st->eS[i][idx];
+          G[i] = W5[i] * (CX[i] * Gx + CY[i] * Gy) / CS2;
+        }
+        const real_t S[5] = {1, d.s_th, d.s_th, 1, 1};
+        collide5(ee, teq, S, G, Fd, out);
+        for (int i = 0; i < 5; ++i) st->ne[i][idx] = out[i];
+        st->nH_o[idx] = rhoH / rho;
+      }
+      st->fld[F_THETA][idx] = theta;
       st->nphi_o[idx] = phi;
       st->nC_o[idx] = C;
       st->nvx_o[idx] = vx;
       st->nvy_o[idx] = vy;
-      st->nQ_o[idx] = Q;
+      st->nQ_o[idx] = Qeff;
       st->fld[F_PHI][idx] = phi; st->fld[F_PSI][idx] = psi; st->fld[F_C][idx] = C;
       st->fld[F_U][idx] = U; st->fld[F_P][idx] = p;
       st->fld[F_VX][idx] = vx; st->fld[F_VY][idx] = vy; st->fld[F_MU][idx] = mu;
@@ -748,6 +862,10 @@ static void swap_state(ostate *st) {
   SW(st->rr, st->nrr);
   SW(st->phi_o, st->nphi_o); SW(st->C_o, st->nC_o);
   SW(st->vx_o, st->nvx_o); SW(st->vy_o, st->nvy_o); SW(st->Q_o, st->nQ_o);
+  if (thermal_on(st)) {
+    for (int i = 0; i < 5; ++i) SW(st->e[i], st->ne[i]);
+    SW(st->H_o, st->nH_o);
+  }
 #undef SW
 }
 
@@ -765,10 +883,10 @@ void or_step(ostate *st, int n_steps) {
 /* ------------------------------------------------------------------------ */
 
 /* Fields of the last step (real part), field-major: out[f * n + idx] for the
- * fields selected by mask bits (phi, psi, C, U, p, vx, vy, mu_phi). */
+ * fields selected by mask bits (phi, psi, C, U, p, vx, vy, mu_phi, theta). */
 void or_get_fields(const ostate *st, unsigned mask, double *out) {
   int o = 0;
-  for (int fi = 0; fi < 8; ++fi)
+  for (int fi = 0; fi < NFLD; ++fi)
     if (mask & (1u << fi)) {
       for (int idx = 0; idx < st->n; ++idx) out[(size_t)o * st->n + idx] = RE_(st->fld[fi][idx]);
       ++o;
@@ -778,7 +896,7 @@ void or_get_fields(const ostate *st, unsigned mask, double *out) {
 /* Imaginary parts (complex build; zeros otherwise). */
 void or_get_fields_im(const ostate *st, unsigned mask, double *out) {
   int o = 0;
-  for (int fi = 0; fi < 8; ++fi)
+  for (int fi = 0; fi < NFLD; ++fi)
     if (mask & (1u << fi)) {
       for (int idx = 0; idx < st->n; ++idx) out[(size_t)o * st->n + idx] = IM_(st->fld[fi][idx]);
       ++o;
@@ -786,9 +904,12 @@ void or_get_fields_im(const ostate *st, unsigned mask, double *out) {
 }
 
 /* Raw state, 39 planes in the documented order:
- * f[9], h[9], gpre[5], gpost[5], rr, s[5], phi_o, C_o, vx_o, vy_o, Q_o. */
+ * f[9], h[9], gpre[5], gpost[5], rr, s[5], phi_o, C_o, vx_o, vy_o, Q_o,
+ * then in thermal mode 6 more: e[5] (temperature populations), H_o. */
+int or_state_planes(const ostate *st) { return thermal_on(st) ? 45 : 39; }
+
 void or_get_state(const ostate *st, double *out) {
-  const real_t *planes[39];
+  const real_t *planes[45];
   int q = 0;
   for (int i = 0; i < 9; ++i) planes[q++] = st->f[i];
   for (int i = 0; i < 9; ++i) planes[q++] = st->h[i];
@@ -798,7 +919,11 @@ void or_get_state(const ostate *st, double *out) {
   for (int i = 0; i < 5; ++i) planes[q++] = st->s[i];
   planes[q++] = st->phi_o; planes[q++] = st->C_o;
   planes[q++] = st->vx_o; planes[q++] = st->vy_o; planes[q++] = st->Q_o;
-  for (int p = 0; p < 39; ++p)
+  if (thermal_on(st)) {
+    for (int i = 0; i < 5; ++i) planes[q++] = st->e[i];
+    planes[q++] = st->H_o;
+  }
+  for (int p = 0; p < q; ++p)
     for (int idx = 0; idx < st->n; ++idx) out[(size_t)p * st->n + idx] = RE_(planes[p][idx]);
 }
 
@@ -917,4 +1042,41 @@ void or_pointwise(const ostate *st, double phi, double psi, double C, double *ou
   real_t U = supersat(st, C, psi);
   out[0] = RE_(U);
   out[1] = RE_(q_psi(st, &d, phi, psi, U));
+}
+
+/* Temperature equilibrium of Appendix B (for the pin tests). */
+void or_teq_th(double rhoH, double theta, double jx, double jy, double *out) {
+  real_t o[5];
+  teq_th(rhoH, theta, jx, jy, o);
+  for (int i = 0; i < 5; ++i) out[i] = RE_(o[i]);
+}
+
+/* F(U) of Section 2.1 and the thermal rate s_th (for the pin tests). */
+void or_thermal_coefs(const ostate *st, double U, double *out) {
+  derived_t d = derive(st);
+  out[0] = RE_(f_of_u(st, &d, U));
+  out[1] = RE_(d.kT);
+  out[2] = RE_(d.s_th);
+}
+
+/* Totals of the thermal state: out[0] = sum over sites and directions of the
+ * temperature populations (the total of rho H, conserved by the collision and
+ * the streaming), out[1] = sum theta, out[2] = sum psi. */
+static void neumaier_add(double *s, double *c, double v) {
+  double t = *s + v;
+  if (fabs(*s) >= fabs(v)) *c += (*s - t) + v;
+  else *c += (v - t) + *s;
+  *s = t;
+}
+
+void or_thermal_totals(const ostate *st, double *out) {
+  /* compensated (Neumaier) sums, so that the totals carry no summation-order
+   * error at the 1e-12 level of the conservation checks */
+  double s[3] = {0, 0, 0}, c[3] = {0, 0, 0};
+  for (int idx = 0; idx < st->n; ++idx) {
+    for (int i = 0; i < 5; ++i) neumaier_add(&s[0], &c[0], RE_(st->e[i][idx]));
+    neumaier_add(&s[1], &c[1], RE_(st->fld[F_THETA][idx]));
+    neumaier_add(&s[2], &c[2], RE_(st->fld[F_PSI][idx]));
+  }
+  for (int k = 0; k < 3; ++k) out[k] = s[k] + c[k];
 }
