@@ -36,6 +36,8 @@ METRIC = "coupled-step MLUPS at 4096² and % of HBM roofline; adjoint/forward ti
 BYTES_PER_LU = {"fp32": 39 * 4 * 2 + 1, "fp64": 39 * 8 * 2 + 1,
                 "fp16": (33 * 2 + 7 * 4) * 2 + 1, "bf16": (33 * 2 + 7 * 4) * 2 + 1}
 DTYPE = {"fp32": "f32", "fp64": "f64", "fp16": "f16-storage/f32", "bf16": "bf16-storage/f32"}
+# Thermal mode adds 5 temperature populations and the lagged H: 45 planes.
+BYTES_PER_LU_THERMAL = {"fp32": 45 * 4 * 2 + 1, "fp64": 45 * 8 * 2 + 1}
 KERNEL_SOURCES = ("paper_2407_01651_gb300/csrc/pf_step.cu",
                   "paper_2407_01651_gb300/csrc/pf_device.cuh",
                   "paper_2407_01651_gb300/csrc/pf_model.cuh",
@@ -329,6 +331,65 @@ def run_precision(args) -> None:
         "speedup_bf16_vs_fp32": out["bf16"]["mlups"] / out["fp32"]["mlups"]}))
 
 
+def run_thermal(args) -> None:
+    """The 4096^2 lattice with the temperature lattice on (Section 4 of the
+    paper: Le = 50, c_p^s / c_p = 1, theta0 = -Omega): MLUPS and the HBM
+    roofline at 361 B/LU (FP32), the FP64 drift of the conserved totals, and
+    the isothermal step timed in the same process for the cost ratio."""
+    import torch
+
+    from paper_2407_01651_gb300 import pf
+    from paper_2407_01651_gb300 import workload as wl
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    prec = args.precision if args.precision in BYTES_PER_LU_THERMAL else "fp32"
+    lay = wl.growth_lattice(args.size, args.size)
+    par = dict(lay.params, **wl.THERMAL_PARAMS)
+    stream = torch.cuda.current_stream()
+    sites = lay.nx * lay.ny
+    res = {}
+    for mode, p_, bpl in (("thermal", par, BYTES_PER_LU_THERMAL[prec]),
+                          ("isothermal", lay.params, BYTES_PER_LU[prec])):
+        sim = pf.Simulation([(lay.nx, lay.ny)], p_, prec, stream=stream.cuda_stream)
+        sim.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
+        d0 = sim.reduce(0)
+        t0 = sim.reduce_thermal(0) if mode == "thermal" else None
+        sim.step(args.warmup)
+        launches0 = sim.launches
+        ms = _time_steps(torch, sim, stream, args.steps)
+        launches = sim.launches - launches0
+        d = sim.reduce(0)
+        if d["nonfinite"]:
+            raise SystemExit(f"{mode}: non-finite fields after the timed run")
+        r = {"mlups": sites * args.steps / ms / 1e3, "ms_per_step": ms / args.steps,
+             "bytes_per_lu": bpl, "algorithmic_gbs": bpl * sites * args.steps / ms / 1e6,
+             "gpu_launches": launches,
+             "sum_phi_rel_drift": d["sum_phi"] / d0["sum_phi"] - 1.0,
+             "sum_C_rel_drift": d["sum_C"] / d0["sum_C"] - 1.0}
+        if t0 is not None:
+            t = sim.reduce_thermal(0)
+            r["sum_rhoH_rel_drift"] = t["sum_e"] / t0["sum_e"] - 1.0
+            r["mean_theta"] = t["sum_theta"] / sites
+        res[mode] = r
+        sim.close()
+        torch.cuda.empty_cache()
+    peak, peak_kind = measured_peaks()
+    th = res["thermal"]
+    print(json.dumps({
+        "metric": "thermal coupled-step MLUPS at 4096² and % of HBM roofline",
+        "value": th["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": th["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
+        "config": dict(workload_config(lay.nx, prec), thermal=wl.THERMAL_PARAMS),
+        "roofline": {"bound": "hbm", "achieved": th["algorithmic_gbs"], "peak": peak,
+                     "unit": "GB/s", "frac": th["algorithmic_gbs"] / peak,
+                     "traffic": None, "peak_kind": peak_kind,
+                     "bytes_per_lu": th["bytes_per_lu"],
+                     "kernel": "k_step_ymarch<thermal> (one launch per step)"},
+        "modes": res, "thermal_cost_vs_isothermal": res["isothermal"]["mlups"] / th["mlups"],
+        "gpu_launches": th["gpu_launches"]}))
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -340,9 +401,11 @@ def main() -> None:
     ap.add_argument("--variant", type=int, default=None, help="step kernel traversal")
     ap.add_argument("--chunk", type=int, default=None, help="rows per y-march tile / tile a")
     ap.add_argument("--tile-b", type=int, default=0)
-    ap.add_argument("--workload", default="lattice", choices=("lattice", "ensemble", "precision"),
+    ap.add_argument("--workload", default="lattice",
+                    choices=("lattice", "ensemble", "precision", "thermal"),
                     help="lattice: the 4096^2 headline; ensemble: 96 uneven domains; "
-                         "precision: 8192x4096 in FP32 / FP16 / BF16 storage")
+                         "precision: 8192x4096 in FP32 / FP16 / BF16 storage; "
+                         "thermal: the 4096^2 lattice with the temperature lattice on")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -360,6 +423,9 @@ def main() -> None:
         return
     if args.workload == "precision":
         run_precision(args)
+        return
+    if args.workload == "thermal":
+        run_thermal(args)
         return
 
     import numpy as np

@@ -67,12 +67,27 @@ typedef enum {
  *  grad_eps_at    regularisation of |grad psi| in the antitrapping direction
  *  s_e, s_eps     free MRT rates of the NS energy moments (default 1)
  * lambda' = 15 lambda / 16 is derived as D tau0 / (a2' W0^2), a2' = 47/75
- * (thin-interface limit, Appendix A). */
+ * (thin-interface limit, Appendix A).
+ * Temperature coupling (Section 2.1, Appendix B), used when thermal = 1:
+ *  Le             Lewis number alpha / D; alpha = k_T / (rho_l c_p) is the
+ *                 melt's thermal diffusivity, F(U) = 1/Le + M c_inf [1 + (1-k) U]
+ *  latent         c_p^s / c_p: theta = H / c_p + latent h(psi)
+ *  theta0         uniform initial temperature (pf_set_temperature sets a field)
+ *  cp             lattice heat capacity c_p (a numerical constant: the equation
+ *                 depends on k_T / c_p only); rho_g * cp >= 2/3 is required
+ *                 for the rest population rho H + (w_0 - 1) theta to keep the
+ *                 scheme stable in the gas
+ *  thermal        0: isothermal closure theta = theta_sys, F = 1 (Eq. eq-Tsys);
+ *                 1: temperature lattice (FP32 / FP64 storage, y-march
+ *                 traversal; no adjoint)
+ *  reserved       must be 0 */
 typedef struct pf_params {
   double rho_l, rho_g, nu, sigma, W_phi, M_phi;
   double beta_phi, beta_psi, beta_inter;
   double W0, tau0, eps_s, k, D, Omega, g;
   double grad_eps, grad_eps_at, s_e, s_eps;
+  double Le, latent, theta0, cp;
+  int thermal, reserved;
 } pf_params;
 
 /* One periodic domain of an ensemble.  eps_s < 0 uses pf_params.eps_s;
@@ -126,7 +141,8 @@ enum {
   PF_FIELD_P = 1u << 4,    /* pressure p                                    */
   PF_FIELD_VX = 1u << 5,
   PF_FIELD_VY = 1u << 6,
-  PF_FIELD_MU = 1u << 7    /* chemical potential mu_phi (0 before a step)   */
+  PF_FIELD_MU = 1u << 7,   /* chemical potential mu_phi (0 before a step)   */
+  PF_FIELD_THETA = 1u << 8 /* temperature theta (theta_sys when isothermal) */
 };
 
 /* Number of FP64 planes of the raw state (pf_get_state / pf_set_state):
@@ -134,6 +150,9 @@ enum {
  * r = 1/a_s^2, s[5] (solute, post-collision), phi, C, vx, vy, Q_psi of the
  * last step. */
 #define PF_STATE_PLANES 39
+/* Thermal mode: 6 more planes, e[5] (temperature populations, post-collision)
+ * and H of the last step; pf_state_planes() gives the count of a handle. */
+#define PF_STATE_PLANES_THERMAL 45
 
 typedef struct pf_handle pf_handle;
 
@@ -211,8 +230,8 @@ pf_status pf_get_step_config(const pf_handle *h, int out[3]);
  * host_out in doubles.  Synchronises the stream. */
 pf_status pf_get_fields(pf_handle *h, int dom, uint32_t mask, double *host_out, size_t n);
 
-/* Raw state of domain dom (PF_STATE_PLANES planes, FP64) to / from the host:
- * checkpoint and restart.  Synchronise the stream. */
+/* Raw state of domain dom (pf_state_planes(h) planes, FP64) to / from the
+ * host: checkpoint and restart.  Synchronise the stream. */
 pf_status pf_get_state(pf_handle *h, int dom, double *host_out, size_t n);
 pf_status pf_set_state(pf_handle *h, int dom, const double *host_in, size_t n);
 
@@ -293,6 +312,26 @@ long long pf_launch_count(const pf_handle *h);
 pf_status pf_reduce_noalloc(const void *fields, int fields_fp64, long long plane_stride,
                             long long offset, int nx, int ny, const pf_probe *probe,
                             pf_diag *out, void *cuda_stream);
+
+/* Planes of the raw state of the handle: PF_STATE_PLANES, or
+ * PF_STATE_PLANES_THERMAL in thermal mode; -1 for NULL. */
+int pf_state_planes(const pf_handle *h);
+
+/* Thermal mode: set the temperature field theta (host, FP64, n = nx*ny) of
+ * domain dom after pf_init_fields / pf_set_fields and before the first step.
+ * The temperature populations are set to the equilibrium of Appendix B,
+ * g^eq(rho H, theta, rho H v) with H = c_p [theta - (c_p^s/c_p) h(psi)] and phi,
+ * psi, U, v of the initialisation; the lagged H and the lagged dendrite source
+ * Q_psi(theta) / F(U) follow.  Synchronises the stream.  Errors: BAD_ARG (not
+ * thermal, bad sizes, non-finite values), STATE (not initialised, or already
+ * stepped), CUDA. */
+pf_status pf_set_temperature(pf_handle *h, int dom, const double *theta, size_t n);
+
+/* Thermal mode: FP64 totals of domain dom.  out[0] = sum over sites of the
+ * five temperature populations (the total of rho H, conserved by the
+ * temperature equation of Appendix B on a periodic domain), out[1] = sum theta,
+ * out[2] = sum psi.  Synchronises the stream.  Errors: BAD_ARG, CUDA. */
+pf_status pf_reduce_thermal(pf_handle *h, int dom, double out[3]);
 
 /* Release every resource of the handle (NULL is ignored). */
 pf_status pf_destroy(pf_handle *h);

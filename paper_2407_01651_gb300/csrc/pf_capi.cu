@@ -1,8 +1,9 @@
 // pf_capi.cu -- implementation of the C ABI declared in include/pf.h.
 //
 // A handle owns, for all of its domains together:
-//   - two copies of the 39-plane state (ping-pong of the pull scheme),
-//   - 8 field planes in compute precision (written by the last step of each
+//   - two copies of the 39-plane state (45 in thermal mode; ping-pong of the
+//     pull scheme),
+//   - 9 field planes in compute precision (written by the last step of each
 //     pf_step call and by the initialisation),
 //   - a uint8 grain id per site and a (cos, sin) table per domain,
 //   - the domain and tile tables of the step kernel,
@@ -39,6 +40,10 @@ struct pf_handle {
   long long plane_stride = 0;
   size_t elem = 4;          // bytes per stored value
   size_t celem = 4;         // bytes per compute value
+  int thermal = 0;          // temperature lattice and finite-Le F(U)
+  int n_pop = N_POP;        // population planes per state copy
+  int n_aux = N_AUX;        // lagged-scalar planes per state copy
+  int n_phys = N_PHYS;      // planes of the raw FP64 state
   int variant = STEP_YMARCH;  // step kernel traversal
   int tx = 32, ty = 8;      // tile of the 2-D variant
   int chunk = 32;           // rows per tile of the y-march variants (tuned at 4096^2)
@@ -166,6 +171,17 @@ static KParams<R> make_kparams(const pf_params& p) {
   k.s_q = (R)(8.0 * (2.0 - s_nu) / (8.0 - s_nu));
   k.s_nu = (R)s_nu;
   k.s_phi = (R)(1.0 / (3.0 * p.M_phi + 0.5));
+  // temperature coupling: alpha = k_T / (rho_l c_p) = Le D, k_T = (1/s - 1/2) / 3
+  if (p.thermal) {
+    const double kT = p.Le * p.D * p.rho_l * p.cp;
+    k.th_cp = (R)p.cp;
+    k.th_icp = (R)(1.0 / p.cp);
+    k.th_lh = (R)(0.5 * p.latent);
+    k.th_s = (R)(1.0 / (3.0 * kT + 0.5));
+    k.th_iLe = (R)(1.0 / p.Le);
+    k.th_dF = (R)(der[1] * (1.0 - p.k));
+    k.W0sq = (R)(p.W0 * p.W0);
+  }
   return k;
 }
 
@@ -186,6 +202,18 @@ static pf_status check_params(const pf_params* p) {
     return fail(nullptr, PF_ERR_BAD_ARG, "eps_s must be in [0, 0.25)");
   if (1.0 - (1.0 - p->k) * p->Omega == 0.0)
     return fail(nullptr, PF_ERR_BAD_ARG, "1 - (1-k) Omega must be non-zero");
+  if (p->thermal != 0 && p->thermal != 1)
+    return fail(nullptr, PF_ERR_BAD_ARG, "thermal must be 0 or 1");
+  if (p->reserved != 0) return fail(nullptr, PF_ERR_BAD_ARG, "reserved must be 0");
+  if (p->thermal) {
+    if (!finite_pos(p->Le) || !finite_pos(p->cp) || !std::isfinite(p->latent) ||
+        !std::isfinite(p->theta0))
+      return fail(nullptr, PF_ERR_BAD_ARG, "thermal mode needs Le > 0, cp > 0, finite latent, theta0");
+    // the rest population rho H + (w_0 - 1) theta keeps the update of theta a
+    // positive average only for rho c_p >= 1 - w_0 = 2/3 (gas included)
+    if (p->rho_g * p->cp < 2.0 / 3.0)
+      return fail(nullptr, PF_ERR_BAD_ARG, "thermal mode needs rho_g * cp >= 2/3 (stability)");
+  }
   return PF_OK;
 }
 
@@ -214,6 +242,7 @@ extern "C" pf_status pf_params_default(pf_params* out) {
   p.beta_phi = 0.25; p.beta_psi = 0.25; p.beta_inter = 0.75;
   p.W0 = 4.0; p.tau0 = 320.0; p.eps_s = 0.05; p.k = 0.15; p.D = 0.1; p.Omega = 0.55;
   p.g = 1e-6; p.grad_eps = 1e-3; p.grad_eps_at = 1e-2; p.s_e = 1.0; p.s_eps = 1.0;
+  p.Le = 1.0; p.latent = 1.0; p.theta0 = -0.55; p.cp = 10.0; p.thermal = 0;
   *out = p;
   return PF_OK;
 }
@@ -300,6 +329,8 @@ extern "C" pf_status pf_create(const pf_params* p, const pf_domain* doms, int n_
   }
   if (alloc && (!alloc->alloc || !alloc->free))
     return fail(nullptr, PF_ERR_BAD_ARG, "allocator needs alloc and free");
+  if (p->thermal && prec != PF_FP32 && prec != PF_FP64)
+    return fail(nullptr, PF_ERR_BAD_ARG, "thermal mode needs FP32 or FP64 storage");
 
   pf_handle* h = new (std::nothrow) pf_handle();
   if (!h) return fail(nullptr, PF_ERR_OOM, "host allocation failed");
@@ -310,6 +341,10 @@ extern "C" pf_status pf_create(const pf_params* p, const pf_domain* doms, int n_
   cudaGetDevice(&h->device);
   h->elem = prec == PF_FP64 ? 8 : (prec == PF_FP32 ? 4 : 2);
   h->celem = prec == PF_FP64 ? 8 : 4;
+  h->thermal = p->thermal;
+  h->n_pop = p->thermal ? N_POP_TH : N_POP;
+  h->n_aux = p->thermal ? N_AUX_TH : N_AUX;
+  h->n_phys = p->thermal ? N_PHYS_TH : N_PHYS;
   h->doms.assign(doms, doms + n_doms);
   h->inited.assign(n_doms, 0);
   long long off = 0;
@@ -344,8 +379,8 @@ extern "C" pf_status pf_create(const pf_params* p, const pf_domain* doms, int n_
     return code;
   };
   for (int c = 0; c < 2; ++c) {
-    h->pop[c] = dev_alloc(h, ps * N_POP * h->elem);
-    h->aux[c] = dev_alloc(h, ps * N_AUX * h->celem);
+    h->pop[c] = dev_alloc(h, ps * h->n_pop * h->elem);
+    h->aux[c] = dev_alloc(h, ps * h->n_aux * h->celem);
     if (!h->pop[c] || !h->aux[c]) return bail(PF_ERR_OOM, "state allocation failed");
   }
   h->fields = dev_alloc(h, ps * N_FIELDS * h->celem);
@@ -468,6 +503,8 @@ static pf_status init_spec_t(pf_handle* h, int dom, const pf_init_spec* spec, co
   a.sq2bphi = std::sqrt(2.0 * h->p.beta_phi);
   a.k = h->p.k;
   a.kp = make_kparams<R>(h->p);
+  a.thermal = h->thermal;
+  a.theta0 = h->p.theta0;
   PF_CUDA(h, launch_init_spec<S, R>(a, h->stream));
   h->launches++;
   return PF_OK;
@@ -528,6 +565,8 @@ static pf_status set_fields_t(pf_handle* h, int dom, const double* d_f6, const u
   a.f6 = d_f6;
   a.grain_ids = d_ids;
   a.kp = make_kparams<R>(h->p);
+  a.thermal = h->thermal;
+  a.theta0 = h->p.theta0;
   PF_CUDA(h, launch_set_fields<S, R>(a, h->stream));
   h->launches++;
   return PF_OK;
@@ -603,6 +642,7 @@ static StepArgs<S, R> make_step_args(const pf_handle* h, const void* pin, const 
   a.fields = write_fields ? reinterpret_cast<R*>(h->fields) : nullptr;
   a.err = h->d_err;
   a.drop_copies = h->drop_copies;
+  a.thermal = h->thermal;
   a.kp = make_kparams<R>(h->p);
   return a;
 }
@@ -613,7 +653,9 @@ static StepArgs<S, R> make_step_args(const pf_handle* h, const void* pin, const 
 template <typename S, typename R>
 static pf_status launch_all(pf_handle* h, StepArgs<S, R> a, cudaStream_t stream) {
   const int cap = h->persistent
-                      ? std::max(1, h->sms) * step_blocks_per_sm<S, R>(h->variant, h->tx, h->ty, h->plane_stride)
+                      ? std::max(1, h->sms) * step_blocks_per_sm<S, R>(h->variant, h->tx, h->ty,
+                                                                       h->plane_stride,
+                                                                       h->thermal != 0)
                       : 1 << 30;
   if (h->launch_mode == 0) {
     a.tile_base = 0;
@@ -713,6 +755,8 @@ static bool staged_ok(const pf_handle* h) {
 
 extern "C" pf_status pf_set_step_config(pf_handle* h, int variant, int a, int b) {
   if (!h) return PF_ERR_BAD_ARG;
+  if (h->thermal && variant != STEP_YMARCH)
+    return fail(h, PF_ERR_BAD_ARG, "thermal mode runs the y-march traversal (variant 1) only");
   if (variant == STEP_TILE) {
     if (a < 1 || b < 1 || a * b > 256 || a % 32 != 0)
       return fail(h, PF_ERR_BAD_ARG, "tile variant needs tx a multiple of 32 and tx*ty <= 256");
@@ -751,7 +795,7 @@ extern "C" pf_status pf_set_launch(pf_handle* h, int per_domain, int persistent,
 template <typename S, typename R>
 static pf_status autotune_t(pf_handle* h, int trial_steps, int out[4]) {
   const size_t ps = (size_t)h->plane_stride;
-  const size_t pop_b = ps * N_POP * sizeof(S), aux_b = ps * N_AUX * sizeof(R);
+  const size_t pop_b = ps * h->n_pop * sizeof(S), aux_b = ps * h->n_aux * sizeof(R);
   void* snap_p = dev_alloc(h, pop_b);
   void* snap_a = dev_alloc(h, aux_b);
   if (!snap_p || !snap_a) {
@@ -767,11 +811,13 @@ static pf_status autotune_t(pf_handle* h, int trial_steps, int out[4]) {
   std::vector<Cand> cands;
   for (int ch : {8, 16, 24, 32, 48, 64, 96})
     for (int pers : {0, 1}) cands.push_back({STEP_YMARCH, ch, 0, pers});
-  if (staged_ok_t<S, R>(h))
-    for (int ch : {16, 32, 48, 64, 96, 128})
-      for (int pers : {0, 1}) cands.push_back({STEP_STAGED, ch, 0, pers});
-  cands.push_back({STEP_TILE, 32, 8, 0});
-  cands.push_back({STEP_TILE, 64, 4, 0});
+  if (!h->thermal) {
+    if (staged_ok_t<S, R>(h))
+      for (int ch : {16, 32, 48, 64, 96, 128})
+        for (int pers : {0, 1}) cands.push_back({STEP_STAGED, ch, 0, pers});
+    cands.push_back({STEP_TILE, 32, 8, 0});
+    cands.push_back({STEP_TILE, 64, 4, 0});
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -854,7 +900,7 @@ extern "C" pf_status pf_step(pf_handle* h, int n_steps) {
 extern "C" pf_status pf_get_fields(pf_handle* h, int dom, uint32_t mask, double* host_out,
                                    size_t n) {
   if (!h) return PF_ERR_BAD_ARG;
-  if (dom < 0 || dom >= (int)h->doms.size() || !host_out || (mask & ~0xFFu) || !mask)
+  if (dom < 0 || dom >= (int)h->doms.size() || !host_out || (mask & ~0x1FFu) || !mask)
     return fail(h, PF_ERR_BAD_ARG, "bad domain, mask or output");
   const DomDesc& dd = h->ddesc[dom];
   const size_t nn = (size_t)dd.nx * dd.ny;
@@ -881,19 +927,20 @@ extern "C" pf_status pf_get_state(pf_handle* h, int dom, double* host_out, size_
     return fail(h, PF_ERR_BAD_ARG, "bad domain or output");
   const DomDesc& dd = h->ddesc[dom];
   const size_t nn = (size_t)dd.nx * dd.ny;
-  if (n < nn * N_PHYS) return fail(h, PF_ERR_BAD_ARG, "output buffer too small");
-  pf_status st = ensure_staging(h, nn * N_PHYS);
+  const size_t np = (size_t)h->n_phys;
+  if (n < nn * np) return fail(h, PF_ERR_BAD_ARG, "output buffer too small");
+  pf_status st = ensure_staging(h, nn * np);
   if (st != PF_OK) return st;
   st = dispatch(h, [&](auto s_t, auto r_t) {
     PF_TYPES(s_t, r_t);
     PF_CUDA(h, launch_state_to_f64<S, R>((const S*)h->pop[h->cur], (const R*)h->aux[h->cur],
                                          h->plane_stride, dd.off, (long long)nn, h->staging,
-                                         h->stream));
+                                         h->thermal, h->stream));
     return PF_OK;
   });
   if (st != PF_OK) return st;
   h->launches++;
-  PF_CUDA(h, cudaMemcpyAsync(host_out, h->staging, nn * N_PHYS * sizeof(double),
+  PF_CUDA(h, cudaMemcpyAsync(host_out, h->staging, nn * np * sizeof(double),
                              cudaMemcpyDeviceToHost, h->stream));
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
   return check_device_error(h);
@@ -905,18 +952,20 @@ extern "C" pf_status pf_set_state(pf_handle* h, int dom, const double* host_in, 
     return fail(h, PF_ERR_BAD_ARG, "bad domain or input");
   const DomDesc& dd = h->ddesc[dom];
   const size_t nn = (size_t)dd.nx * dd.ny;
-  if (n != nn * N_PHYS) return fail(h, PF_ERR_BAD_ARG, "input must hold 39 planes of nx*ny");
+  const size_t np = (size_t)h->n_phys;
+  if (n != nn * np)
+    return fail(h, PF_ERR_BAD_ARG, "input must hold pf_state_planes(h) planes of nx*ny");
   pf_status st = clear_device_error(h);
   if (st != PF_OK) return st;
-  st = ensure_staging(h, nn * N_PHYS);
+  st = ensure_staging(h, nn * np);
   if (st != PF_OK) return st;
-  PF_CUDA(h, cudaMemcpyAsync(h->staging, host_in, nn * N_PHYS * sizeof(double),
+  PF_CUDA(h, cudaMemcpyAsync(h->staging, host_in, nn * np * sizeof(double),
                              cudaMemcpyHostToDevice, h->stream));
   st = dispatch(h, [&](auto s_t, auto r_t) {
     PF_TYPES(s_t, r_t);
     PF_CUDA(h, launch_state_from_f64<S, R>((S*)h->pop[h->cur], (R*)h->aux[h->cur],
                                            h->plane_stride, dd.off, (long long)nn, h->staging,
-                                           h->stream));
+                                           h->thermal, h->stream));
     return PF_OK;
   });
   if (st != PF_OK) return st;
@@ -950,6 +999,61 @@ extern "C" pf_status pf_reduce(pf_handle* h, int dom, const pf_probe* probe, pf_
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
   static_assert(sizeof(pf_diag) == NDIAG * sizeof(double), "pf_diag layout");
   std::memcpy(out, buf, sizeof(buf));
+  return check_device_error(h);
+}
+
+// ---------------------------------------------------------------------------
+// thermal mode
+// ---------------------------------------------------------------------------
+extern "C" int pf_state_planes(const pf_handle* h) { return h ? h->n_phys : -1; }
+
+extern "C" pf_status pf_set_temperature(pf_handle* h, int dom, const double* theta, size_t n) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (!h->thermal) return fail(h, PF_ERR_BAD_ARG, "the handle is not in thermal mode");
+  if (dom < 0 || dom >= (int)h->doms.size() || !theta)
+    return fail(h, PF_ERR_BAD_ARG, "bad domain index or NULL theta");
+  if (!h->inited[dom]) return fail(h, PF_ERR_STATE, "initialise the domain first");
+  if (h->steps != 0) return fail(h, PF_ERR_STATE, "set the temperature before the first step");
+  const DomDesc& dd = h->ddesc[dom];
+  const size_t nn = (size_t)dd.nx * dd.ny;
+  if (n != nn) return fail(h, PF_ERR_BAD_ARG, "n must equal nx*ny of the domain");
+  for (size_t i = 0; i < nn; ++i)
+    if (!std::isfinite(theta[i])) return fail(h, PF_ERR_BAD_ARG, "non-finite temperature");
+  pf_status st = ensure_staging(h, nn);
+  if (st != PF_OK) return st;
+  PF_CUDA(h, cudaMemcpyAsync(h->staging, theta, nn * sizeof(double), cudaMemcpyHostToDevice,
+                             h->stream));
+  st = dispatch(h, [&](auto s_t, auto r_t) {
+    PF_TYPES(s_t, r_t);
+    PF_CUDA(h, launch_set_temperature<S, R>((S*)h->pop[h->cur], (R*)h->aux[h->cur],
+                                            fields_ptr<R>(h), h->plane_stride, dd, h->staging,
+                                            make_kparams<R>(h->p), h->stream));
+    return PF_OK;
+  });
+  if (st != PF_OK) return st;
+  h->launches++;
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PF_OK;
+}
+
+extern "C" pf_status pf_reduce_thermal(pf_handle* h, int dom, double out[3]) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (!h->thermal) return fail(h, PF_ERR_BAD_ARG, "the handle is not in thermal mode");
+  if (dom < 0 || dom >= (int)h->doms.size() || !out)
+    return fail(h, PF_ERR_BAD_ARG, "bad domain or output");
+  const DomDesc& dd = h->ddesc[dom];
+  pf_status st = dispatch(h, [&](auto s_t, auto r_t) {
+    PF_TYPES(s_t, r_t);
+    PF_CUDA(h, launch_reduce_thermal<S, R>((const S*)h->pop[h->cur], fields_ptr<R>(h),
+                                           h->plane_stride, dd, h->partial, h->d_diag,
+                                           h->stream));
+    return PF_OK;
+  });
+  if (st != PF_OK) return st;
+  h->launches += 2;
+  PF_CUDA(h, cudaMemcpyAsync(out, h->d_diag, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                             h->stream));
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
   return check_device_error(h);
 }
 
@@ -1083,6 +1187,8 @@ extern "C" pf_status pf_adjoint_step(pf_handle* h, int n_steps, const pf_objecti
   if (h->doms.size() != 1) return fail(h, PF_ERR_BAD_ARG, "the adjoint takes a single-domain handle");
   if (h->prec != PF_FP32 && h->prec != PF_FP64)
     return fail(h, PF_ERR_BAD_ARG, "the adjoint supports the FP32 and FP64 storage forms");
+  if (h->thermal)
+    return fail(h, PF_ERR_BAD_ARG, "the adjoint covers the isothermal model (thermal = 0) only");
   if (!h->inited[0]) return fail(h, PF_ERR_STATE, "initialise the domain before the adjoint");
   if (!std::isfinite(obj->w_solid) || !std::isfinite(obj->w_centroid))
     return fail(h, PF_ERR_BAD_ARG, "objective weights must be finite");

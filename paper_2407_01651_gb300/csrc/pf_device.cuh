@@ -120,6 +120,20 @@ template <typename S, typename R, typename I>
 __device__ __forceinline__ void st_off(S* __restrict__ p, I i, R v, R wm) {
   p[i] = enc_off<S, R>(v, wm);
 }
+// Same value as st_off(p, i, v, w * M), with the weight w a compile-time
+// lattice weight: in FP16 the scale folds into one FMA per population,
+// v * 2^14 - (w * 2^14) * M, and (w * 2^14) * M is shared by every population
+// of the same weight class.  Scaling by a power of two commutes with rounding,
+// so the stored bits equal those of (v - w M) * 2^14.
+template <typename S, typename R, typename I>
+__device__ __forceinline__ void st_off_w(S* __restrict__ p, I i, R v, R w, R M) {
+  if constexpr (Codec<S>::kOffset && Codec<S>::kOffScale != 1.0f) {
+    constexpr R sc = R(Codec<S>::kOffScale);
+    p[i] = Codec<S>::template enc<R>(fma(v, sc, -((w * sc) * M)));
+  } else {
+    p[i] = enc_off<S, R>(v, w * M);
+  }
+}
 
 // Compensated (Neumaier) accumulation: the zeroth moments phi, psi, C are sums
 // of 5 or 9 populations of similar size; in FP32 plain summation loses up to

@@ -36,6 +36,7 @@ struct StepArgs {
   R* fields;                    // 8 field planes, or nullptr
   unsigned int* err;            // device error bits (1: a staged copy timed out), or nullptr
   int drop_copies;              // testing only: the staged kernel skips its bulk copies
+  int thermal;                  // 1: temperature lattice and finite-Le F(U) (FP32 / FP64)
   KParams<R> kp;
 };
 
@@ -52,6 +53,8 @@ struct InitArgs {
   int n_seeds, n_bub;
   double R_s, W0, Wphi, sq2bpsi, sq2bphi, k;
   KParams<R> kp;
+  int thermal;           // also initialise the temperature lattice at theta0
+  double theta0;
 };
 
 template <typename S, typename R>
@@ -65,6 +68,8 @@ struct SetFieldsArgs {
   const double* f6;          // device, 6 x n
   const uint8_t* grain_ids;  // device, n, or nullptr
   KParams<R> kp;
+  int thermal;               // also initialise the temperature lattice at theta0
+  double theta0;
 };
 
 template <typename R>
@@ -92,17 +97,25 @@ template <typename S, typename R>
 int staged_blocks_per_sm();
 // Resident CTAs per SM of the step kernel (for persistent grids).
 template <typename S, typename R>
-int step_blocks_per_sm(int variant, int tx, int ty, long long plane_stride);
+int step_blocks_per_sm(int variant, int tx, int ty, long long plane_stride, bool thermal);
 template <typename S, typename R>
 cudaError_t launch_init_spec(const InitArgs<S, R>& a, cudaStream_t st);
 template <typename S, typename R>
 cudaError_t launch_set_fields(const SetFieldsArgs<S, R>& a, cudaStream_t st);
 template <typename S, typename R>
 cudaError_t launch_state_to_f64(const S* pin, const R* ain, long long ps, long long off,
-                                long long n, double* out, cudaStream_t st);
+                                long long n, double* out, int thermal, cudaStream_t st);
 template <typename S, typename R>
 cudaError_t launch_state_from_f64(S* pout, R* aout, long long ps, long long off, long long n,
-                                  const double* in, cudaStream_t st);
+                                  const double* in, int thermal, cudaStream_t st);
+// Thermal mode: temperature lattice at equilibrium for a theta field (device,
+// n of the domain), and the FP64 totals (sum e, sum theta, sum psi).
+template <typename S, typename R>
+cudaError_t launch_set_temperature(S* out, R* aout, R* fields, long long ps, const DomDesc& d,
+                                   const double* theta, const KParams<R>& kp, cudaStream_t st);
+template <typename S, typename R>
+cudaError_t launch_reduce_thermal(const S* pop, const R* fields, long long ps, const DomDesc& d,
+                                  double* partial, double* out, cudaStream_t st);
 template <typename R>
 cudaError_t launch_fields_to_f64(const R* fields, long long ps, long long off, long long n,
                                  uint32_t mask, double* out, cudaStream_t st);

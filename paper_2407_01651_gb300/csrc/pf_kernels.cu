@@ -28,11 +28,36 @@ __device__ __forceinline__ double min_image(double d, double L) {
   return d;
 }
 
+// Temperature lattice of one site at equilibrium (thermal mode): H =
+// c_p [theta - (c_p^s/c_p) h(psi)], e = g^eq(rho H, theta, rho H v) of
+// Appendix B (with the axis base rounded as in collide_th), lagged H = H and
+// the lagged dendrite source at its pointwise part Q_psi(theta) / F(U).
+template <typename S, typename R>
+__device__ void write_thermal(S* out, R* aout, R* fields, long long ps, long long site, R phi,
+                              R psi, R U, R vx, R vy, R theta, const KParams<R>& kp) {
+  const R rho = kp.rho_g + phi * kp.drho;
+  const R H = kp.th_cp * (theta - kp.th_lh * (R(1) + psi));
+  const R m0 = rho * H;
+  const R b = round_to_multiple(theta * R(1.0 / 6.0), quantum_quarter_ulp(m0));
+  const R jx = m0 * vx, jy = m0 * vy;
+  const R e[5] = {m0 - R(4) * b, b + R(0.5) * jx, b + R(0.5) * jy, b - R(0.5) * jx,
+                  b - R(0.5) * jy};
+  for (int i = 0; i < 5; ++i) st<S, R>(out + (P_E + i) * ps, site, e[i]);
+  aout[A_HO * ps + site] = H;
+  const R omp2 = R(1) - psi * psi, ophi = R(1) - phi;
+  const R Q = kp.four_bpsi * psi * omp2 - kp.two_bint * ophi * ophi * (R(1) + psi) -
+              kp.lam * omp2 * omp2 * (theta + kp.Mcinf * U);
+  const R F = kp.th_iLe + kp.Mcinf * (R(1) + (R(1) - kp.k) * U);
+  aout[A_QO * ps + site] = Q / F;
+  if (fields) fields[FLD_THETA * ps + site] = theta;
+}
+
 // Write the equilibrium state and the fields of one site.
 template <typename S, typename R>
 __device__ void write_equilibrium(S* out, R* aout, R* fields, long long ps, long long site,
                                   double phi_d, double psi_d, double C_d, double vx_d,
-                                  double vy_d, double p_d, const KParams<R>& kp) {
+                                  double vy_d, double p_d, const KParams<R>& kp, int thermal,
+                                  double theta_d) {
   const R phi = static_cast<R>(phi_d), psi = static_cast<R>(psi_d), C = static_cast<R>(C_d);
   const R vx = static_cast<R>(vx_d), vy = static_cast<R>(vy_d), p = static_cast<R>(p_d);
   const R rho = kp.rho_g + phi * kp.drho;
@@ -73,7 +98,10 @@ __device__ void write_equilibrium(S* out, R* aout, R* fields, long long ps, long
     fields[FLD_VX * ps + site] = vx;
     fields[FLD_VY * ps + site] = vy;
     fields[FLD_MU * ps + site] = R(0);
+    fields[FLD_THETA * ps + site] = kp.theta;
   }
+  if (thermal) write_thermal<S, R>(out, aout, fields, ps, site, phi, psi, U, vx, vy,
+                                   static_cast<R>(theta_d), kp);
 }
 
 template <typename S, typename R>
@@ -117,7 +145,7 @@ __global__ void k_init_spec(InitArgs<S, R> a) {
     const long long site = d.off + i;
     a.grain[site] = (uint8_t)gid;
     write_equilibrium<S, R>(a.out, a.aout, a.fields, a.plane_stride, site, phi, psi, C, 0.0,
-                            0.0, 0.0, a.kp);
+                            0.0, 0.0, a.kp, a.thermal, a.theta0);
   }
 }
 
@@ -130,8 +158,26 @@ __global__ void k_set_fields(SetFieldsArgs<S, R> a) {
     const long long site = d.off + i;
     const double* F = a.f6;
     write_equilibrium<S, R>(a.out, a.aout, a.fields, a.plane_stride, site, F[i], F[n + i],
-                            F[2 * n + i], F[3 * n + i], F[4 * n + i], F[5 * n + i], a.kp);
+                            F[2 * n + i], F[3 * n + i], F[4 * n + i], F[5 * n + i], a.kp,
+                            a.thermal, a.theta0);
     a.grain[site] = a.grain_ids ? a.grain_ids[i] : (uint8_t)0;
+  }
+}
+
+// Thermal mode: the temperature lattice of a domain at equilibrium for a given
+// theta field, with phi, psi, U and v taken from the field planes (the state
+// written by the last initialisation).
+template <typename S, typename R>
+__global__ void k_set_temperature(S* out, R* aout, R* fields, long long ps, DomDesc d,
+                                  const double* __restrict__ theta, KParams<R> kp) {
+  const long long n = (long long)d.nx * d.ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long site = d.off + i;
+    write_thermal<S, R>(out, aout, fields, ps, site, fields[FLD_PHI * ps + site],
+                        fields[FLD_PSI * ps + site], fields[FLD_U * ps + site],
+                        fields[FLD_VX * ps + site], fields[FLD_VY * ps + site],
+                        static_cast<R>(theta[i]), kp);
   }
 }
 
@@ -142,9 +188,11 @@ __global__ void k_set_fields(SetFieldsArgs<S, R> a) {
 // s, phi, C, vx, vy, Q_psi), decoding / encoding the storage form.  In the
 // offset forms a population stored at site x is relative to the lagged
 // moment of x itself.
+// Thermal mode adds planes 39..43 (e_0..e_4) and 44 (H of the last step).
 template <typename S, typename R>
 __global__ void k_state_to_f64(const S* __restrict__ pin, const R* __restrict__ ain, long long ps,
-                               long long off, long long n, double* __restrict__ out) {
+                               long long off, long long n, double* __restrict__ out,
+                               int thermal) {
   constexpr bool offs = Codec<S>::kOffset;
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
        j += (long long)gridDim.x * blockDim.x) {
@@ -166,12 +214,17 @@ __global__ void k_state_to_f64(const S* __restrict__ pin, const R* __restrict__ 
     out[36 * n + j] = (double)ain[A_VXO * ps + s];
     out[37 * n + j] = (double)ain[A_VYO * ps + s];
     out[38 * n + j] = (double)ain[A_QO * ps + s];
+    if (thermal) {
+      for (int i = 0; i < 5; ++i) out[(39 + i) * n + j] = (double)ld<R>(pin + (P_E + i) * ps, s);
+      out[44 * n + j] = (double)ain[A_HO * ps + s];
+    }
   }
 }
 
 template <typename S, typename R>
 __global__ void k_state_from_f64(S* __restrict__ pout, R* __restrict__ aout, long long ps,
-                                 long long off, long long n, const double* __restrict__ in) {
+                                 long long off, long long n, const double* __restrict__ in,
+                                 int thermal) {
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
        j += (long long)gridDim.x * blockDim.x) {
     const long long s = off + j;
@@ -194,6 +247,10 @@ __global__ void k_state_from_f64(S* __restrict__ pout, R* __restrict__ aout, lon
     aout[A_VYO * ps + s] = (R)in[37 * n + j];
     aout[A_QO * ps + s] = (R)in[38 * n + j];
     aout[A_PSIO * ps + s] = psio;
+    if (thermal) {
+      for (int i = 0; i < 5; ++i) st<S, R>(pout + (P_E + i) * ps, s, (R)in[(39 + i) * n + j]);
+      aout[A_HO * ps + s] = (R)in[44 * n + j];
+    }
   }
 }
 
@@ -269,6 +326,43 @@ __global__ void k_reduce_partial(ReduceArgs<R> a, double* __restrict__ partial) 
     for (int q = 0; q < NDIAG; ++q) partial[blockIdx.x * NDIAG + q] = sh[q][0];
 }
 
+// Thermal totals (FP64): sum over sites of the five temperature populations
+// (the total of rho H), sum theta, sum psi; fixed-order partials as above.
+template <typename S, typename R>
+__global__ void k_reduce_thermal_partial(const S* __restrict__ pop, const R* __restrict__ fields,
+                                         long long ps, DomDesc d, double* __restrict__ partial) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  const long long n = (long long)d.nx * d.ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long site = d.off + i;
+    double se = 0.0;
+    for (int q = 0; q < 5; ++q) se += (double)ld<R>(pop + (P_E + q) * ps, site);
+    acc[0] += se;
+    acc[1] += (double)fields[FLD_THETA * ps + site];
+    acc[2] += (double)fields[FLD_PSI * ps + site];
+  }
+  __shared__ double sh[3][256];
+  for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int stride = blockDim.x / 2; stride > 0; stride >>= 1) {
+    if ((int)threadIdx.x < stride)
+      for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + stride];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) partial[blockIdx.x * 3 + q] = sh[q][0];
+}
+
+__global__ void k_reduce_thermal_final(const double* __restrict__ partial, int nblocks,
+                                       double* __restrict__ out) {
+  const int q = threadIdx.x;
+  if (q >= 3) return;
+  double acc = 0.0;
+  for (int b = 0; b < nblocks; ++b) acc += partial[b * 3 + q];
+  out[q] = acc;
+}
+
 __global__ void k_reduce_final(const double* __restrict__ partial, int nblocks,
                                double* __restrict__ out) {
   const int q = threadIdx.x;
@@ -302,15 +396,32 @@ cudaError_t launch_set_fields(const SetFieldsArgs<S, R>& a, cudaStream_t st) {
 
 template <typename S, typename R>
 cudaError_t launch_state_to_f64(const S* pin, const R* ain, long long ps, long long off,
-                                long long n, double* out, cudaStream_t st) {
-  k_state_to_f64<S, R><<<1024, 256, 0, st>>>(pin, ain, ps, off, n, out);
+                                long long n, double* out, int thermal, cudaStream_t st) {
+  k_state_to_f64<S, R><<<1024, 256, 0, st>>>(pin, ain, ps, off, n, out, thermal);
   return cudaGetLastError();
 }
 
 template <typename S, typename R>
 cudaError_t launch_state_from_f64(S* pout, R* aout, long long ps, long long off, long long n,
-                                  const double* in, cudaStream_t st) {
-  k_state_from_f64<S, R><<<1024, 256, 0, st>>>(pout, aout, ps, off, n, in);
+                                  const double* in, int thermal, cudaStream_t st) {
+  k_state_from_f64<S, R><<<1024, 256, 0, st>>>(pout, aout, ps, off, n, in, thermal);
+  return cudaGetLastError();
+}
+
+template <typename S, typename R>
+cudaError_t launch_set_temperature(S* out, R* aout, R* fields, long long ps, const DomDesc& d,
+                                   const double* theta, const KParams<R>& kp, cudaStream_t st) {
+  const long long n = (long long)d.nx * d.ny;
+  const int grid = (int)((n + 255) / 256 < 65535 ? (n + 255) / 256 : 65535);
+  k_set_temperature<S, R><<<grid, 256, 0, st>>>(out, aout, fields, ps, d, theta, kp);
+  return cudaGetLastError();
+}
+
+template <typename S, typename R>
+cudaError_t launch_reduce_thermal(const S* pop, const R* fields, long long ps, const DomDesc& d,
+                                  double* partial, double* out, cudaStream_t st) {
+  k_reduce_thermal_partial<S, R><<<REDUCE_BLOCKS, 256, 0, st>>>(pop, fields, ps, d, partial);
+  k_reduce_thermal_final<<<1, 32, 0, st>>>(partial, REDUCE_BLOCKS, out);
   return cudaGetLastError();
 }
 
@@ -333,9 +444,15 @@ cudaError_t launch_reduce(const ReduceArgs<R>& a, double* partial, double* out,
   template cudaError_t launch_init_spec<S, R>(const InitArgs<S, R>&, cudaStream_t);          \
   template cudaError_t launch_set_fields<S, R>(const SetFieldsArgs<S, R>&, cudaStream_t);    \
   template cudaError_t launch_state_to_f64<S, R>(const S*, const R*, long long, long long,   \
-                                                 long long, double*, cudaStream_t);          \
+                                                 long long, double*, int, cudaStream_t);     \
   template cudaError_t launch_state_from_f64<S, R>(S*, R*, long long, long long, long long,  \
-                                                   const double*, cudaStream_t);
+                                                   const double*, int, cudaStream_t);        \
+  template cudaError_t launch_set_temperature<S, R>(S*, R*, R*, long long, const DomDesc&,   \
+                                                    const double*, const KParams<R>&,        \
+                                                    cudaStream_t);                           \
+  template cudaError_t launch_reduce_thermal<S, R>(const S*, const R*, long long,            \
+                                                   const DomDesc&, double*, double*,         \
+                                                   cudaStream_t);
 
 PF_INST(double, double)
 PF_INST(float, float)

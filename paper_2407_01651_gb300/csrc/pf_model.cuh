@@ -28,7 +28,9 @@ enum PopPlane : int {
   P_GPRE = 18,    // dendrite populations before collision g_0..g_4
   P_GPOST = 23,   // dendrite populations after collision
   P_S = 28,       // solute populations s_0..s_4 (post-collision)
-  N_POP = 33
+  N_POP = 33,
+  P_E = 33,       // temperature populations e_0..e_4 (post-collision; thermal mode)
+  N_POP_TH = 38
 };
 
 enum AuxPlane : int {
@@ -39,14 +41,18 @@ enum AuxPlane : int {
   A_VYO = 4,      // vy of the last step
   A_QO = 5,       // Q_psi of the last step
   A_PSIO = 6,     // psi of the last step (offset storage forms only)
-  N_AUX = 7
+  N_AUX = 7,
+  A_HO = 7,       // H = c_p theta - c_p^s h(psi) of the last step (thermal mode)
+  N_AUX_TH = 8
 };
 
 // Raw state exchanged with the host (pf_get_state / pf_set_state): 39 planes
 // f[9], h[9], g_pre[5], g_post[5], r, s[5], phi, C, vx, vy, Q_psi.
 constexpr int N_PHYS = 39;
+// Thermal mode: + e[5], H_o.
+constexpr int N_PHYS_TH = 45;
 
-enum Field : int { FLD_PHI, FLD_PSI, FLD_C, FLD_U, FLD_P, FLD_VX, FLD_VY, FLD_MU, N_FIELDS };
+enum Field : int { FLD_PHI, FLD_PSI, FLD_C, FLD_U, FLD_P, FLD_VX, FLD_VY, FLD_MU, FLD_THETA, N_FIELDS };
 
 struct DomDesc {
   long long off;      // first site of the domain in every plane
@@ -73,6 +79,13 @@ struct KParams {
   R k, D, g;
   R inv_omk;                // 1 / (1 - k)
   R s_e, s_eps, s_q, s_nu, s_phi;
+  // temperature coupling (thermal mode)
+  R th_cp, th_icp;          // c_p, 1 / c_p
+  R th_lh;                  // (c_p^s / c_p) / 2: theta = H / c_p + th_lh (1 + psi)
+  R th_s;                   // flux rate of the temperature lattice, k_T = (1/s - 1/2) c_s^2
+  R th_iLe;                 // 1 / Le
+  R th_dF;                  // M c_inf (1 - k): grad F = th_dF grad U
+  R W0sq;                   // W0^2
 };
 
 // ---------------------------------------------------------------------------
@@ -216,6 +229,47 @@ __device__ __forceinline__ void collide_q5(T q[5], T m0, T s, V2<T> Jeq, V2<T> G
   const T hs = T(1) - T(0.5) * s;
   const V2<T> JS = fma(splat(hs), G, fma(splat(-s), J - Jeq, J));
   q5_from_m(m0, JS, q);
+}
+
+// Temperature collision, D2Q5 (Appendix B): g_0^eq = rho H + (w_0 - 1) theta,
+// g_i^eq = w_i theta + w_i c_i.(rho H v)/c_s^2, G_i = w_i c_i.dJ/c_s^2 with
+// dJ = d_t(rho H v); flux moments relax with s, the others with 1.  In moment
+// space the energy moment is at -4 m0 + (10/3) theta and the anisotropic one
+// at 0, whose back-transform is e_0 = m0 - (2/3) theta, e_{1,3} = theta/6 +- j*x/2,
+// e_{2,4} = theta/6 +- j*y/2.  m0 = rho H is conserved as it came in.  The
+// base theta/6 of the axis populations is rounded to a multiple of ulp(m0)/4,
+// which makes m0 - 4 (theta/6) exact in the common case: a uniform region
+// would otherwise round every site's e_0 the same way and drift the conserved
+// total of rho H by a fixed fraction per step.
+template <typename T>
+__device__ __forceinline__ T quantum_quarter_ulp(T m) {
+  if constexpr (sizeof(T) == 4) {
+    const unsigned e = __float_as_uint(m) & 0x7f800000u;   // 2^E of m, E >= -126
+    // 2^(E - 25) = ulp(m) / 4 for a normal m; a tiny m gets the smallest normal
+    return e > (25u << 23) ? __uint_as_float(e - (25u << 23)) : __uint_as_float(1u << 23);
+  } else {
+    const unsigned long long e =
+        (unsigned long long)__double_as_longlong(m) & 0x7ff0000000000000ull;
+    return e > (54ull << 52) ? __longlong_as_double((long long)(e - (54ull << 52)))
+                             : __longlong_as_double(1ll << 52);
+  }
+}
+template <typename T>
+__device__ __forceinline__ T round_to_multiple(T v, T q) {
+  // q is a power of two, so 1/q and both products are exact
+  if constexpr (sizeof(T) == 4) return rintf(v * __frcp_rn(q)) * q;
+  else return rint(v * __drcp_rn(q)) * q;
+}
+template <typename T>
+__device__ __forceinline__ void collide_th(T e[5], T m0, T theta, T s, V2<T> Jeq, V2<T> G) {
+  const V2<T> J = vec2(e[1], e[2]) - vec2(e[3], e[4]);
+  const T hs = T(1) - T(0.5) * s;
+  const V2<T> JS = fma(splat(hs), G, fma(splat(-s), J - Jeq, J));
+  const T b = round_to_multiple(theta * T(1.0 / 6.0), quantum_quarter_ulp(m0));
+  const V2<T> a = splat(b);
+  const V2<T> e12 = fma(T(0.5), JS, a), e34 = fma(T(-0.5), JS, a);
+  e[0] = m0 - T(4) * b;
+  e[1] = e12.x; e[2] = e12.y; e[3] = e34.x; e[4] = e34.y;
 }
 
 }  // namespace pf

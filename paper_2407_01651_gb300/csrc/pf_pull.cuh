@@ -93,9 +93,10 @@ struct SiteIn {
   R f[9], s[5];
   R phio, Co, Qo;
   uint8_t gid;
+  R e[5], Ho;     // thermal mode: streamed temperature populations, lagged H
 };
 
-template <typename S, typename R, bool BIG = false>
+template <typename S, typename R, bool BIG = false, bool TH = false>
 __device__ __forceinline__ void load_site(const StepArgs<S, R>& a, const Src9& src,
                                           SiteIn<R>& in) {
   const unsigned ps = (unsigned)a.plane_stride;
@@ -111,6 +112,28 @@ __device__ __forceinline__ void load_site(const StepArgs<S, R>& a, const Src9& s
   in.Co = ld<R>(pbase<BIG>(a.ain, A_CO, ps), pidx<BIG>(A_CO, ps, src.s[0]));
   in.Qo = ld<R>(pbase<BIG>(a.ain, A_QO, ps), pidx<BIG>(A_QO, ps, src.s[0]));
   in.gid = a.grain[src.s[0]];
+  if constexpr (TH) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+      in.e[i] = ld<R>(pbase<BIG>(a.in, P_E + i, ps), pidx<BIG>(P_E + i, ps, src.s[i]));
+    in.Ho = ld<R>(pbase<BIG>(a.ain, A_HO, ps), pidx<BIG>(A_HO, ps, src.s[0]));
+  }
+}
+
+// Supersaturation U of a site from its streamed solute populations (thermal
+// mode: U on the stencil neighbourhood feeds grad F), with the arithmetic of
+// the site update's own C and U.
+template <typename S, typename R, bool BIG = false>
+__device__ __forceinline__ R pull_U(const StepArgs<S, R>& a, const Src9& src, R psi) {
+  const unsigned ps = (unsigned)a.plane_stride;
+  CSum<R> cs;
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+    cs.add(ld<R>(pbase<BIG>(a.in, P_S + i, ps), pidx<BIG>(P_S + i, ps, src.s[i])));
+  const R C = cs.value();
+  const R omk = R(1) - a.kp.k;
+  const R A = (R(1) + a.kp.k) - omk * psi;
+  return (R(2) * C * frcp(A) - R(1)) * a.kp.inv_omk;
 }
 
 }  // namespace pf

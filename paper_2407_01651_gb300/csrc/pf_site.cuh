@@ -29,6 +29,19 @@ struct SiteOut {
   T ias2, phi, psi, C, U, p, vx, vy, Q, mu;
 };
 
+// Temperature coupling (thermal mode): inputs and outputs of a site.
+template <typename T>
+struct ThermIn {
+  T e[5];     // streamed temperature populations
+  T Ho;       // H of the previous step
+  Nb9<T> U;   // supersaturation on the 3 x 3 neighbourhood (for grad F)
+};
+template <typename T>
+struct ThermOut {
+  T e[5];     // post-collision temperature populations
+  T H, theta;
+};
+
 // Everything after streaming at one site:
 //   f, h, g, s   streamed populations (g after the a_s^2 time stretch)
 //   psio         psi of the previous step
@@ -36,12 +49,19 @@ struct SiteOut {
 //   P, S, VX, VY phi, psi and the lagged velocity on the 3 x 3 neighbourhood
 //   ct, sn       grain rotation; eps anisotropy strength; rho_bar mean density
 // g is stored unchanged as the next g_pre; everything else goes to `o`.
-template <typename T, typename R>
+// TH (thermal mode, Section 2.1 and Appendix B): theta comes from the
+// temperature lattice (ti, to) instead of theta_sys, and the dendrite lattice
+// takes F(U) = 1/Le + M c_inf [1 + (1-k) U] in its rate and the source
+//   Q_eff = Q / F + W0^2 / F^2 grad F . (a_s^2 grad psi + N),
+// stored as the lagged source (o.Q) in place of Q.
+template <typename T, typename R, bool TH = false>
 __device__ __forceinline__ void site_math(const KParams<R>& kp, T rho_bar, T eps, T ct, T sn,
                                           const T (&f_in)[9], const T (&h_in)[9],
                                           const T (&g)[5], const T (&s_in)[5], T psio, T phio,
                                           T Co, T Qo, const Nb9<T>& P, const Nb9<T>& S,
-                                          const Nb9<T>& VX, const Nb9<T>& VY, SiteOut<T>& o) {
+                                          const Nb9<T>& VX, const Nb9<T>& VY, SiteOut<T>& o,
+                                          const ThermIn<T>* ti = nullptr,
+                                          ThermOut<T>* to = nullptr) {
   T* f = o.f;
   T* h = o.h;
   T* s = o.s;
@@ -157,8 +177,18 @@ __device__ __forceinline__ void site_math(const KParams<R>& kp, T rho_bar, T eps
   const T iA = frcp(A);
   const T U = (T(2) * C * iA - T(1)) * T(kp.inv_omk);
   const T omp2 = T(1) - psi * psi;
+  // temperature: rho H = sum of the streamed e (rest population first, the
+  // largest), theta = H / c_p + (c_p^s / c_p) h(psi)
+  T rhoH = T(0), theta = T(kp.theta);
+  if constexpr (TH) {
+    CSum<T> es;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) es.add(ti->e[i]);
+    rhoH = es.value();
+    theta = fma(rhoH * irho, T(kp.th_icp), T(kp.th_lh) * opsi);
+  }
   const T Q = T(kp.four_bpsi) * psi * omp2 - T(kp.two_bint) * ophi * ophi * opsi -
-              T(kp.lam) * omp2 * omp2 * (T(kp.theta) + T(kp.Mcinf) * U);
+              T(kp.lam) * omp2 * omp2 * (theta + T(kp.Mcinf) * U);
   const T dpsi = psi - psio;
   const T at = T(-kp.a_at * kp.W0) * as * (T(1) + omk * U) * dpsi * frsqrt(gm2 + T(kp.gat2));
   const T qf = T(0.5) * (T(1) - psi);
@@ -167,9 +197,31 @@ __device__ __forceinline__ void site_math(const KParams<R>& kp, T rho_bar, T eps
   // ---- collisions ----
   collide_ns(f, p, rho, v, F, gr, kp);
   collide_cac(h, phi, v, fma(T(1.0 / 3.0) * aphi, nf, fma(phi, v, (-phio) * vo)), kp);
+  T Qs = Q;        // source stored as the lagged value
   {
-    const T Fs = (Q + T(0.5) * (Q - Qo)) * T(kp.inv_tau0);
-    const T s1 = frcp(T(kp.c_s1) * as2 + T(0.5));
+    T s1;
+    if constexpr (TH) {
+      const T iF = frcp(T(kp.th_iLe) + T(kp.Mcinf) * (T(1) + omk * U));
+      V2<T> gu;
+      {
+        const Nb9<T>& X = ti->U;
+        const V2<T> X0 = splat(X.v[1][1]);
+        const V2<T> en = vec2(X.v[1][2], X.v[2][1]) - X0;
+        const V2<T> ws = vec2(X.v[1][0], X.v[0][1]) - X0;
+        const V2<T> nen = vec2(X.v[2][2], X.v[2][0]) - X0;
+        const V2<T> sws = vec2(X.v[0][0], X.v[0][2]) - X0;
+        const V2<T> dd = nen - sws;
+        const V2<T> cr = vec2(dd.x - dd.y, dd.x + dd.y);
+        gu = T(3) * fma(splat(w1), en - ws, w2 * cr);   // grad U
+      }
+      const V2<T> Xv = fma(splat(as2), gs, vec2(Nx, Ny));   // a_s^2 grad psi + N
+      const V2<T> gX = gu * Xv;
+      Qs = fma(T(kp.W0sq) * T(kp.th_dF) * iF * iF, gX.x + gX.y, Q * iF);
+      s1 = frcp(T(kp.c_s1) * as2 * iF + T(0.5));
+    } else {
+      s1 = frcp(T(kp.c_s1) * as2 + T(0.5));
+    }
+    const T Fs = (Qs + T(0.5) * (Qs - Qo)) * T(kp.inv_tau0);
 #pragma unroll
     for (int i = 0; i < 5; ++i) o.gpost[i] = g[i];
     collide_q5(o.gpost, psi + Fs, s1, vec2(T(0), T(0)), (T(-1.0 / 3.0) * ias2) * vec2(Nx, Ny));
@@ -181,6 +233,17 @@ __device__ __forceinline__ void site_math(const KParams<R>& kp, T rho_bar, T eps
     const T sc = frcp(T(3) * DC + T(0.5));
     collide_q5(s, C, sc, jeq, fma(C, v, (-Co) * vo));
   }
+  if constexpr (TH) {
+    // d_t(rho H v) with rho_o H_o v_o of the previous step (backward difference)
+    const T rho_o = T(kp.rho_g) + phio * T(kp.drho);
+    const V2<T> jH = rhoH * v;
+    const V2<T> dJ = fma(-(rho_o * ti->Ho), vo, jH);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) to->e[i] = ti->e[i];
+    collide_th(to->e, rhoH, theta, T(kp.th_s), jH, dJ);
+    to->H = rhoH * irho;
+    to->theta = theta;
+  }
   o.ias2 = ias2;
   o.phi = phi;
   o.psi = psi;
@@ -189,18 +252,19 @@ __device__ __forceinline__ void site_math(const KParams<R>& kp, T rho_bar, T eps
   o.p = p;
   o.vx = v.x;
   o.vy = v.y;
-  o.Q = Q;
+  o.Q = Qs;
   o.mu = mu;
 }
 
 // One site: gather the stencil values from the traversal's shared-memory rows,
 // run site_math and store the new state and (if requested) the fields.
-template <typename S, typename R>
+// TH: thermal mode, with SU the supersaturation rows and in.e / in.Ho loaded.
+template <typename S, typename R, bool TH = false>
 __device__ __forceinline__ void site_update(const StepArgs<S, R>& a, const DomDesc& d,
                                             const Src9& src, const SiteIn<R>& in,
                                             const R (&h_in)[9], const R (&g_in)[5], R psio,
                                             Rows3<R> SP, Rows3<R> SS, Rows3<R> SVX,
-                                            Rows3<R> SVY, int c) {
+                                            Rows3<R> SVY, int c, Rows3<R> SU = Rows3<R>{}) {
   const unsigned ps = (unsigned)a.plane_stride;
   const unsigned site = src.s[0];
   auto nb = [&](const Rows3<R>& X) {
@@ -215,22 +279,30 @@ __device__ __forceinline__ void site_update(const StepArgs<S, R>& a, const DomDe
   };
   const double2 cs = a.grain_cs[d.grain_off + in.gid];
   SiteOut<R> o;
-  site_math<R, R>(a.kp, static_cast<R>(d.rho_bar), static_cast<R>(d.eps_s),
-                  static_cast<R>(cs.x), static_cast<R>(cs.y), in.f, h_in, g_in, in.s, psio,
-                  in.phio, in.Co, in.Qo, nb(SP), nb(SS), nb(SVX), nb(SVY), o);
+  ThermIn<R> ti;
+  ThermOut<R> to;
+  if constexpr (TH) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) ti.e[i] = in.e[i];
+    ti.Ho = in.Ho;
+    ti.U = nb(SU);
+  }
+  site_math<R, R, TH>(a.kp, static_cast<R>(d.rho_bar), static_cast<R>(d.eps_s),
+                      static_cast<R>(cs.x), static_cast<R>(cs.y), in.f, h_in, g_in, in.s, psio,
+                      in.phio, in.Co, in.Qo, nb(SP), nb(SS), nb(SVX), nb(SVY), o, &ti, &to);
 
   // ---- store ----
   const R phi = o.phi, psi = o.psi, C = o.C;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     st_ns<S, R>(plane(a.out, P_F + i, ps), site, o.f[i]);
-    st_off<S, R>(plane(a.out, P_H + i, ps), site, o.h[i], w9<R>(i) * phi);
+    st_off_w<S, R>(plane(a.out, P_H + i, ps), site, o.h[i], w9<R>(i), phi);
   }
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    st_off<S, R>(plane(a.out, P_GPRE + i, ps), site, g_in[i], w5<R>(i) * psi);
-    st_off<S, R>(plane(a.out, P_GPOST + i, ps), site, o.gpost[i], w5<R>(i) * psi);
-    st_off<S, R>(plane(a.out, P_S + i, ps), site, o.s[i], w5<R>(i) * C);
+    st_off_w<S, R>(plane(a.out, P_GPRE + i, ps), site, g_in[i], w5<R>(i), psi);
+    st_off_w<S, R>(plane(a.out, P_GPOST + i, ps), site, o.gpost[i], w5<R>(i), psi);
+    st_off_w<S, R>(plane(a.out, P_S + i, ps), site, o.s[i], w5<R>(i), C);
   }
   plane(a.aout, A_RR, ps)[site] = o.ias2;
   plane(a.aout, A_PHIO, ps)[site] = phi;
@@ -239,6 +311,11 @@ __device__ __forceinline__ void site_update(const StepArgs<S, R>& a, const DomDe
   plane(a.aout, A_VYO, ps)[site] = o.vy;
   plane(a.aout, A_QO, ps)[site] = o.Q;
   if constexpr (Codec<S>::kOffset) plane(a.aout, A_PSIO, ps)[site] = psi;
+  if constexpr (TH) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) st<S, R>(plane(a.out, P_E + i, ps), site, to.e[i]);
+    plane(a.aout, A_HO, ps)[site] = to.H;
+  }
   if (a.fields) {
     R* fl = a.fields;
     plane(fl, FLD_PHI, ps)[site] = phi;
@@ -249,6 +326,7 @@ __device__ __forceinline__ void site_update(const StepArgs<S, R>& a, const DomDe
     plane(fl, FLD_VX, ps)[site] = o.vx;
     plane(fl, FLD_VY, ps)[site] = o.vy;
     plane(fl, FLD_MU, ps)[site] = o.mu;
+    if constexpr (TH) plane(fl, FLD_THETA, ps)[site] = to.theta;
   }
 }
 

@@ -70,11 +70,15 @@ __global__ void __launch_bounds__(256) k_step_tile(StepArgs<S, R> a) {
 // registers) and puts phi, psi and the lagged velocity of row j+1 into a
 // 4-slot shared-memory ring; after one barrier the interior threads update row
 // j with the stencils read from slots j-1, j, j+1.  Every population is loaded
-// from memory once (plus 2 halo columns per YM_W).
-template <typename S, typename R, bool BIG>
-__global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 4 : 2) k_step_ymarch(StepArgs<S, R> a) {
+// from memory once (plus 2 halo columns per YM_W).  TH (thermal mode) adds the
+// supersaturation U of row j+1 to the ring (for grad F) and the temperature
+// lattice to the site update; it runs 3 CTAs per SM.
+template <typename S, typename R, bool BIG, bool TH = false>
+__global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? (TH ? 3 : 4) : 2)
+    k_step_ymarch(StepArgs<S, R> a) {
   constexpr int RW = YM_W + 2;
-  __shared__ R ring[4][4][RW];  // [phi, psi, vx_o, vy_o][slot][column]
+  constexpr int NF = TH ? 5 : 4;
+  __shared__ R ring[NF][4][RW];  // [phi, psi, vx_o, vy_o (, U)][slot][column]
   const int t = threadIdx.x;
   const unsigned ps = (unsigned)a.plane_stride;
 
@@ -115,6 +119,7 @@ __global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 4 : 2) k_step_yma
         ring[1][slot][sc] = psi;
         ring[2][slot][sc] = ld<R>(pbase<BIG>(a.ain, A_VXO, ps), pidx<BIG>(A_VXO, ps, src.s[0]));
         ring[3][slot][sc] = ld<R>(pbase<BIG>(a.ain, A_VYO, ps), pidx<BIG>(A_VYO, ps, src.s[0]));
+        if constexpr (TH) ring[NF - 1][slot][sc] = pull_U<S, R, BIG>(a, src, psi);
         if (k == 1) {
 #pragma unroll
           for (int i = 0; i < 9; ++i) hC[i] = h[i];
@@ -130,7 +135,7 @@ __global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 4 : 2) k_step_yma
       // their latency overlaps the lookahead of row j+1
       SiteIn<R> in;
       const Src9 srcj = sources(d, col, j);
-      if (interior) load_site<S, R, BIG>(a, srcj, in);
+      if (interior) load_site<S, R, BIG, TH>(a, srcj, in);
       R hL[9], gL[5], poL = R(0);
       if (active) {
         const int yn = j + 1 >= ny ? j + 1 - ny : j + 1;
@@ -142,12 +147,14 @@ __global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 4 : 2) k_step_yma
         ring[1][slot][sc] = psi;
         ring[2][slot][sc] = ld<R>(pbase<BIG>(a.ain, A_VXO, ps), pidx<BIG>(A_VXO, ps, src.s[0]));
         ring[3][slot][sc] = ld<R>(pbase<BIG>(a.ain, A_VYO, ps), pidx<BIG>(A_VYO, ps, src.s[0]));
+        if constexpr (TH) ring[NF - 1][slot][sc] = pull_U<S, R, BIG>(a, src, psi);
       }
       __syncthreads();
       if (interior) {
         const int m = (j - 1) & 3, c0 = j & 3, pp = (j + 1) & 3;
         auto rows = [&](int f) { return Rows3<R>{ring[f][m], ring[f][c0], ring[f][pp]}; };
-        site_update(a, d, srcj, in, hC, gC, poC, rows(0), rows(1), rows(2), rows(3), sc);
+        site_update<S, R, TH>(a, d, srcj, in, hC, gC, poC, rows(0), rows(1), rows(2), rows(3),
+                              sc, rows(NF - 1));
       }
 #pragma unroll
       for (int i = 0; i < 9; ++i) hC[i] = hL[i];
@@ -161,14 +168,20 @@ __global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 4 : 2) k_step_yma
 
 // Buffers of more than 2^32 elements (plane stride x 33 population planes)
 // take the 64-bit plane-base addressing of the pull helpers.
-inline bool big_handle(long long plane_stride) {
-  return (unsigned long long)plane_stride * N_POP >= (1ull << 32);
+inline bool big_handle(long long plane_stride, bool thermal) {
+  return (unsigned long long)plane_stride * (thermal ? N_POP_TH : N_POP) >= (1ull << 32);
 }
 
 template <typename S, typename R, bool BIG>
 static void launch_traversal(const StepArgs<S, R>& a, int variant, int tx, int ty, int grid,
                              cudaStream_t st) {
   if (variant == STEP_YMARCH) {
+    if constexpr (sizeof(S) == sizeof(R)) {
+      if (a.thermal) {
+        k_step_ymarch<S, R, BIG, true><<<grid, YM_THREADS, 0, st>>>(a);
+        return;
+      }
+    }
     k_step_ymarch<S, R, BIG><<<grid, YM_THREADS, 0, st>>>(a);
   } else {
     const size_t smem = 4 * (size_t)(tx + 2) * (ty + 2) * sizeof(R);
@@ -180,15 +193,20 @@ template <typename S, typename R>
 cudaError_t launch_step(const StepArgs<S, R>& a, int variant, int tx, int ty, int grid,
                         cudaStream_t st) {
   if (variant == STEP_STAGED) return launch_step_staged<S, R>(a, grid, st);
-  if (big_handle(a.plane_stride)) launch_traversal<S, R, true>(a, variant, tx, ty, grid, st);
+  if (big_handle(a.plane_stride, a.thermal != 0))
+    launch_traversal<S, R, true>(a, variant, tx, ty, grid, st);
   else launch_traversal<S, R, false>(a, variant, tx, ty, grid, st);
   return cudaGetLastError();
 }
 
 template <typename S, typename R, bool BIG>
-static int traversal_blocks_per_sm(int variant, int tx, int ty) {
+static int traversal_blocks_per_sm(int variant, int tx, int ty, bool thermal) {
   int n = 0;
-  if (variant == STEP_YMARCH)
+  if (variant == STEP_YMARCH && thermal) {
+    if constexpr (sizeof(S) == sizeof(R))
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_ymarch<S, R, BIG, true>,
+                                                    YM_THREADS, 0);
+  } else if (variant == STEP_YMARCH)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_ymarch<S, R, BIG>, YM_THREADS, 0);
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_tile<S, R, BIG>, tx * ty,
@@ -197,16 +215,17 @@ static int traversal_blocks_per_sm(int variant, int tx, int ty) {
 }
 
 template <typename S, typename R>
-int step_blocks_per_sm(int variant, int tx, int ty, long long plane_stride) {
+int step_blocks_per_sm(int variant, int tx, int ty, long long plane_stride, bool thermal) {
   if (variant == STEP_STAGED) return staged_blocks_per_sm<S, R>();
-  return big_handle(plane_stride) ? traversal_blocks_per_sm<S, R, true>(variant, tx, ty)
-                                  : traversal_blocks_per_sm<S, R, false>(variant, tx, ty);
+  return big_handle(plane_stride, thermal)
+             ? traversal_blocks_per_sm<S, R, true>(variant, tx, ty, thermal)
+             : traversal_blocks_per_sm<S, R, false>(variant, tx, ty, thermal);
 }
 
-template int step_blocks_per_sm<double, double>(int, int, int, long long);
-template int step_blocks_per_sm<float, float>(int, int, int, long long);
-template int step_blocks_per_sm<__half, float>(int, int, int, long long);
-template int step_blocks_per_sm<__nv_bfloat16, float>(int, int, int, long long);
+template int step_blocks_per_sm<double, double>(int, int, int, long long, bool);
+template int step_blocks_per_sm<float, float>(int, int, int, long long, bool);
+template int step_blocks_per_sm<__half, float>(int, int, int, long long, bool);
+template int step_blocks_per_sm<__nv_bfloat16, float>(int, int, int, long long, bool);
 
 template cudaError_t launch_step<double, double>(const StepArgs<double, double>&, int, int, int,
                                                 int, cudaStream_t);

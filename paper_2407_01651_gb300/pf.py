@@ -19,16 +19,18 @@ PF_OK, PF_ERR_BAD_ARG, PF_ERR_OOM, PF_ERR_CUDA, PF_ERR_TIMEOUT, PF_ERR_NAN, PF_E
     0, -1, -2, -3, -4, -5, -6)
 PF_FP64, PF_FP32, PF_FP16_OFFSET, PF_BF16_OFFSET = 0, 1, 2, 3
 PRECISIONS = {"fp64": PF_FP64, "fp32": PF_FP32, "fp16": PF_FP16_OFFSET, "bf16": PF_BF16_OFFSET}
-FIELDS = ("phi", "psi", "C", "U", "p", "vx", "vy", "mu")
-STATE_PLANES = 39
+FIELDS = ("phi", "psi", "C", "U", "p", "vx", "vy", "mu", "theta")
+STATE_PLANES = 39            # PF_STATE_PLANES; thermal handles have 45
 
 _PARAM_FIELDS = ("rho_l", "rho_g", "nu", "sigma", "W_phi", "M_phi", "beta_phi", "beta_psi",
                  "beta_inter", "W0", "tau0", "eps_s", "k", "D", "Omega", "g", "grad_eps",
-                 "grad_eps_at", "s_e", "s_eps")
+                 "grad_eps_at", "s_e", "s_eps", "Le", "latent", "theta0", "cp")
+_PARAM_INTS = ("thermal", "reserved")
 
 
 class pf_params(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_double) for n in _PARAM_FIELDS]
+    _fields_ = ([(n, ctypes.c_double) for n in _PARAM_FIELDS] +
+                [(n, ctypes.c_int) for n in _PARAM_INTS])
 
 
 class pf_domain(ctypes.Structure):
@@ -107,11 +109,15 @@ def lib() -> ctypes.CDLL:
     L.pf_destroy.argtypes = [P]
     L.pf_last_error.argtypes = [P]
     L.pf_last_error.restype = ctypes.c_char_p
+    L.pf_state_planes.argtypes = [P]
+    L.pf_state_planes.restype = ctypes.c_int
+    L.pf_set_temperature.argtypes = [P, I, D, S]
+    L.pf_reduce_thermal.argtypes = [P, I, D]
     for name in ("pf_params_default", "pf_params_derived", "pf_create", "pf_init_fields",
                  "pf_set_fields", "pf_step", "pf_get_fields", "pf_get_state", "pf_set_state",
                  "pf_reduce", "pf_sync", "pf_destroy", "pf_set_step_config",
                  "pf_get_step_config", "pf_reduce_noalloc", "pf_adjoint_step",
-                 "pf_set_launch", "pf_autotune"):
+                 "pf_set_launch", "pf_autotune", "pf_set_temperature", "pf_reduce_thermal"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -139,6 +145,8 @@ def params_from_dict(d: dict | None = None) -> pf_params:
     for k, v in (d or {}).items():
         if k in _PARAM_FIELDS:
             setattr(p, k, float(v))
+        elif k in _PARAM_INTS:
+            setattr(p, k, int(v))
     return p
 
 
@@ -298,11 +306,29 @@ class Simulation:
         out = out[: len(sel) * nx * ny].reshape(len(sel), ny, nx)
         return {nm: out[i] for i, nm in enumerate(sel)}
 
+    @property
+    def state_planes(self) -> int:
+        return lib().pf_state_planes(self.h)
+
     def get_state(self, dom: int = 0) -> np.ndarray:
         nx, ny = self.domains[dom]
-        out = np.empty(STATE_PLANES * nx * ny)
+        npl = self.state_planes
+        out = np.empty(npl * nx * ny)
         _check(lib().pf_get_state(self.h, dom, _dp(out), out.size), self.h)
-        return out.reshape(STATE_PLANES, ny, nx)
+        return out.reshape(npl, ny, nx)
+
+    def set_temperature(self, dom: int, theta) -> None:
+        """Thermal mode: temperature field theta ([ny][nx]) before the first step."""
+        nx, ny = self.domains[dom]
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(theta, dtype=np.float64), (ny, nx)))
+        _check(lib().pf_set_temperature(self.h, dom, _dp(a), nx * ny), self.h)
+
+    def reduce_thermal(self, dom: int = 0) -> dict:
+        """Thermal mode: FP64 sum of the temperature populations (total rho H),
+        sum theta and sum psi."""
+        out = np.zeros(3)
+        _check(lib().pf_reduce_thermal(self.h, dom, _dp(out)), self.h)
+        return dict(zip(("sum_e", "sum_theta", "sum_psi"), out.tolist()))
 
     def set_state(self, dom: int, state: np.ndarray) -> None:
         a = np.ascontiguousarray(np.asarray(state, dtype=np.float64)).ravel()

@@ -25,7 +25,12 @@ BASE_PARAMS = dict(
     beta_phi=0.25, beta_psi=0.25, beta_inter=0.75, W0=4.0, tau0=320.0,
     eps_s=0.05, k=0.15, D=0.1, Omega=0.55, g=1e-6, grad_eps=1e-3,
     grad_eps_at=1e-2, s_e=1.0, s_eps=1.0,
+    # temperature coupling off: the isothermal closure theta = theta_sys, F = 1
+    thermal=0, Le=1.0, latent=1.0, theta0=-0.55, cp=10.0,
 )
+# Thermosolutal variant (Section 4 of the paper: Le = 50, c_p^s / c_p = 1,
+# initial temperature -Omega); c_p is the lattice heat capacity.
+THERMAL_PARAMS = dict(thermal=1, Le=50.0, latent=1.0, theta0=-0.55, cp=10.0)
 SEED_RADIUS = 6.0
 
 

@@ -58,3 +58,22 @@ def test_defaults_match_the_workload_parameters(libpf):
     p = pf.params_from_dict({})
     for k, v in workload.BASE_PARAMS.items():
         assert getattr(p, k) == v, k
+
+
+def test_thermal_parameters_are_checked_before_any_device_work(libpf):
+    """Thermal mode: rho_g c_p below 2/3 (unstable rest population), non-positive
+    Le, or 16-bit storage are rejected by pf_create before it touches a GPU."""
+    from paper_2407_01651_gb300 import pf
+    doms = (pf.pf_domain * 1)(pf.pf_domain(16, 16, -1.0))
+    h = ctypes.c_void_p()
+    L = pf.lib()
+    for over, prec in ((dict(thermal=1, cp=1.0), pf.PF_FP32),
+                       (dict(thermal=1, Le=0.0), pf.PF_FP32),
+                       (dict(thermal=2), pf.PF_FP32),
+                       (dict(thermal=1), pf.PF_FP16_OFFSET),
+                       (dict(thermal=1), pf.PF_BF16_OFFSET)):
+        p = pf.params_from_dict(over)
+        code = L.pf_create(ctypes.byref(p), doms, 1, prec, None, None, ctypes.byref(h))
+        assert code == pf.PF_ERR_BAD_ARG, over
+        assert L.pf_last_error(None)
+    assert L.pf_state_planes(None) == -1
