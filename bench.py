@@ -383,7 +383,8 @@ def run_thermal(args) -> None:
         "config": dict(workload_config(lay.nx, prec), thermal=wl.THERMAL_PARAMS),
         "roofline": {"bound": "hbm", "achieved": th["algorithmic_gbs"], "peak": peak,
                      "unit": "GB/s", "frac": th["algorithmic_gbs"] / peak,
-                     "traffic": None, "peak_kind": peak_kind,
+                     "traffic": recorded_traffic(f"thermal_{prec}", args.size),
+                     "peak_kind": peak_kind,
                      "bytes_per_lu": th["bytes_per_lu"],
                      "kernel": "k_step_ymarch<thermal> (one launch per step)"},
         "modes": res, "thermal_cost_vs_isothermal": res["isothermal"]["mlups"] / th["mlups"],
