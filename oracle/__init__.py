@@ -101,6 +101,7 @@ def _lib(tag: str) -> ctypes.CDLL:
         lib.or_mean_phi_global.argtypes = [P, D, ctypes.c_int]
         lib.or_get_steps.restype = ctypes.c_long
         lib.or_get_steps.argtypes = [P]
+        lib.or_set_bc.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.or_state_planes.restype = ctypes.c_int
         lib.or_state_planes.argtypes = [P]
         lib.or_teq_th.argtypes = [ctypes.c_double] * 4 + [D]
@@ -152,6 +153,12 @@ class Oracle:
     # -- set-up --------------------------------------------------------------
     def perturb(self, name: str, h: float) -> None:
         self.lib.or_perturb_param(self.h, PARAM_NAMES.index(name), float(h))
+
+    def set_bc(self, xm: int, xp: int, ym: int, yp: int) -> None:
+        """Boundary types of the sides x-, x+, y-, y+: 0 periodic, 1 symmetric,
+        2 wall (half-way bounce-back), 3 far field (wall for the flow and phi,
+        Dirichlet psi = -1, C = 1, theta = theta0).  Set before initialising."""
+        self.lib.or_set_bc(self.h, int(xm), int(xp), int(ym), int(yp))
 
     def set_rho_bar(self, rho_bar: float) -> None:
         self.lib.or_set_rho_bar(self.h, float(rho_bar))

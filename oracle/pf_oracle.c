@@ -116,9 +116,14 @@ enum {
   P_THERMAL, P_LE, P_LATENT, P_THETA0, P_CP, NPAR
 };
 
+/* Boundary type of each side (reading R31): x- (left), x+ (right), y- (bottom),
+ * y+ (top), all at the half-way position between the last site and its ghost. */
+enum { BC_PERIODIC = 0, BC_SYMMETRIC = 1, BC_WALL = 2, BC_FARFIELD = 3 };
+
 typedef struct {
   int nx, ny, n;
   int NX, NY, x0, y0;       /* placement of this lattice in a periodic NX x NY one */
+  int bc[4];                /* boundary types: x-, x+, y-, y+ */
   real_t par[NPAR];
   real_t rho_bar;           /* domain-mean density (reading R13) */
   int rho_bar_fixed;
@@ -424,6 +429,16 @@ static double min_image(double d, double L) {
   return d;
 }
 
+/* Signed offset along an axis: the minimum image on a periodic axis, the
+ * plain difference otherwise. */
+static double axis_offset(double d, double L, int periodic) {
+  return periodic ? min_image(d, L) : d;
+}
+
+void or_set_bc(ostate *st, int xm, int xp, int ym, int yp) {
+  st->bc[0] = xm; st->bc[1] = xp; st->bc[2] = ym; st->bc[3] = yp;
+}
+
 /* Set every population to its equilibrium for given macroscopic fields, the
  * lagged values equal to the current ones (first-step time derivatives are
  * zero) and the dendrite time-stretch factor 1/a_s^2 = 1.  Reading R20 of the
@@ -489,8 +504,8 @@ void or_set_orientation(ostate *st, const double *seeds, int n_seeds) {
       int idx = y * st->nx + x;
       double th = 0.0, best = 0.0;
       for (int s = 0; s < n_seeds; ++s) {
-        double dx = min_image((st->x0 + x) - seeds[3 * s], st->NX);
-        double dy = min_image((st->y0 + y) - seeds[3 * s + 1], st->NY);
+        double dx = axis_offset((st->x0 + x) - seeds[3 * s], st->NX, st->bc[0] == BC_PERIODIC);
+        double dy = axis_offset((st->y0 + y) - seeds[3 * s + 1], st->NY, st->bc[2] == BC_PERIODIC);
         double r2 = dx * dx + dy * dy;
         if (s == 0 || r2 < best) { best = r2; th = seeds[3 * s + 2]; }
       }
@@ -517,15 +532,15 @@ void or_fields_from_spec(const ostate *st, const double *seeds, int n_seeds,
       int idx = y * st->nx + x;
       double ps = -1.0;
       for (int s = 0; s < n_seeds; ++s) {
-        double dx = min_image((st->x0 + x) - seeds[3 * s], st->NX);
-        double dy = min_image((st->y0 + y) - seeds[3 * s + 1], st->NY);
+        double dx = axis_offset((st->x0 + x) - seeds[3 * s], st->NX, st->bc[0] == BC_PERIODIC);
+        double dy = axis_offset((st->y0 + y) - seeds[3 * s + 1], st->NY, st->bc[2] == BC_PERIODIC);
         double v = tanh(sqrt(2.0 * bpsi) * (R_s - sqrt(dx * dx + dy * dy)) / W0);
         if (s == 0 || v > ps) ps = v;
       }
       double ph = 1.0;
       for (int b = 0; b < n_bub; ++b) {
-        double dx = min_image((st->x0 + x) - bubbles[3 * b], st->NX);
-        double dy = min_image((st->y0 + y) - bubbles[3 * b + 1], st->NY);
+        double dx = axis_offset((st->x0 + x) - bubbles[3 * b], st->NX, st->bc[0] == BC_PERIODIC);
+        double dy = axis_offset((st->y0 + y) - bubbles[3 * b + 1], st->NY, st->bc[2] == BC_PERIODIC);
         double v = 0.5 + 0.5 * tanh(sqrt(2.0 * bphi) *
                                     (sqrt(dx * dx + dy * dy) - bubbles[3 * b + 2]) /
                                     (2.0 * Wphi));
@@ -548,8 +563,8 @@ double or_mean_phi_global(const ostate *st, const double *bubbles, int n_bub) {
     for (int x = 0; x < st->NX; ++x) {
       double ph = 1.0;
       for (int b = 0; b < n_bub; ++b) {
-        double dx = min_image(x - bubbles[3 * b], st->NX);
-        double dy = min_image(y - bubbles[3 * b + 1], st->NY);
+        double dx = axis_offset(x - bubbles[3 * b], st->NX, st->bc[0] == BC_PERIODIC);
+        double dy = axis_offset(y - bubbles[3 * b + 1], st->NY, st->bc[2] == BC_PERIODIC);
         double v = 0.5 + 0.5 * tanh(sqrt(2.0 * bphi) *
                                     (sqrt(dx * dx + dy * dy) - bubbles[3 * b + 2]) /
                                     (2.0 * Wphi));
@@ -581,6 +596,88 @@ int or_init_spec(ostate *st, const double *seeds, int n_seeds, double R_s,
 /* ------------------------------------------------------------------------ */
 static inline int wrap(int a, int n) { a %= n; return a < 0 ? a + n : a; }
 
+/* Direction maps of D2Q9 (and of its D2Q5 subset 0..4): opposite, and the
+ * reflections that flip c_x or c_y. */
+static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+static const int MIRX[9] = {0, 3, 2, 1, 4, 6, 5, 8, 7};
+static const int MIRY[9] = {0, 1, 4, 3, 2, 8, 7, 6, 5};
+
+/* Far-field values of the Dirichlet sides (Section 4: psi = psi_l, C = 1,
+ * theta = -Omega, here theta0), and U of that state (0). */
+static const double PSI_FAR = -1.0, C_FAR = 1.0;
+
+/* Source of the population of direction i pulled by site (x, y) (reading
+ * R31).  Periodic sides wrap; a symmetric side reflects the source site about
+ * the half-way plane and the direction with it; a wall or far-field side
+ * returns the site's own post-collision population of the opposite direction
+ * (half-way bounce-back), which the far-field side turns into an
+ * anti-bounce-back on the lattices with a Dirichlet value.  Returns 0 (plain
+ * or reflected source), 1 (wall) or 2 (far field); *src and *q give the site
+ * and the direction to read. */
+static int pull_src(const ostate *st, int x, int y, int i, int *src, int *q) {
+  const int nx = st->nx, ny = st->ny;
+  int sx = x - CX[i], sy = y - CY[i], qi = i, bounce = 0;
+  if (sx < 0 || sx >= nx) {
+    const int t = st->bc[sx < 0 ? 0 : 1];
+    if (t == BC_PERIODIC) sx = wrap(sx, nx);
+    else if (t == BC_SYMMETRIC) { sx = sx < 0 ? -1 - sx : 2 * nx - 1 - sx; qi = MIRX[qi]; }
+    else bounce = t == BC_WALL ? (bounce > 1 ? bounce : 1) : 2;
+  }
+  if (sy < 0 || sy >= ny) {
+    const int t = st->bc[sy < 0 ? 2 : 3];
+    if (t == BC_PERIODIC) sy = wrap(sy, ny);
+    else if (t == BC_SYMMETRIC) { sy = sy < 0 ? -1 - sy : 2 * ny - 1 - sy; qi = MIRY[qi]; }
+    else bounce = t == BC_WALL ? (bounce > 1 ? bounce : 1) : 2;
+  }
+  if (bounce) { *src = y * nx + x; *q = OPP[i]; return bounce; }
+  *src = sy * nx + sx;
+  *q = qi;
+  return 0;
+}
+
+/* Kinds of field read on the stencil neighbourhood, for the ghost values. */
+enum { GK_NOFLUX, GK_PSI, GK_U, GK_VX, GK_VY };
+
+/* Ghost value across one non-periodic side of type t on axis a (0: x, 1: y)
+ * from the value v at the mirror site (reading R31): zero normal gradient for
+ * phi, and for psi and U except at a far-field side, where the ghost is the
+ * linear extrapolation 2 X_far - v through the boundary value; the velocity
+ * flips its normal component at a symmetric side and both components at a
+ * wall or far-field side (no slip). */
+static real_t ghost_map(int t, int axis, int kind, real_t v) {
+  if (kind == GK_VX || kind == GK_VY) {
+    const int normal = (kind == GK_VX) == (axis == 0);
+    if (t == BC_SYMMETRIC) return normal ? -v : v;
+    return -v;
+  }
+  if (t == BC_FARFIELD) {
+    if (kind == GK_PSI) return 2.0 * PSI_FAR - v;
+    if (kind == GK_U) return -v;                 /* U = 0 at psi = -1, C = 1 */
+  }
+  return v;
+}
+
+/* X at (x, y), one site beyond the lattice at most: periodic sides wrap, the
+ * others read the mirror site and map the value (y side first, then x). */
+static real_t field_at(const ostate *st, const real_t *X, int x, int y, int kind) {
+  const int nx = st->nx, ny = st->ny;
+  int tx = -1, ty = -1;
+  if (x < 0 || x >= nx) {
+    const int t = st->bc[x < 0 ? 0 : 1];
+    if (t == BC_PERIODIC) x = wrap(x, nx);
+    else { tx = t; x = x < 0 ? -1 - x : 2 * nx - 1 - x; }
+  }
+  if (y < 0 || y >= ny) {
+    const int t = st->bc[y < 0 ? 2 : 3];
+    if (t == BC_PERIODIC) y = wrap(y, ny);
+    else { ty = t; y = y < 0 ? -1 - y : 2 * ny - 1 - y; }
+  }
+  real_t v = X[y * nx + x];
+  if (ty >= 0) v = ghost_map(ty, 1, kind, v);
+  if (tx >= 0) v = ghost_map(tx, 0, kind, v);
+  return v;
+}
+
 /* Pass 1: streaming (Eq. of the unified LBE, pull form) and zeroth moments.
  * NS, CAC and solute: f_i(x, t+1) = f*_i(x - c_i, t).
  * Dendrite, with the time stretch a_n = a_s^2 of Appendix B realised as
@@ -593,18 +690,22 @@ static void pass_stream(ostate *st) {
     for (int x = 0; x < nx; ++x) {
       int idx = y * nx + x;
       real_t phi = 0, psi = 0, C = 0, psio = 0;
+      int src, q;
       for (int i = 0; i < 9; ++i) {
-        int src = wrap(y - CY[i], ny) * nx + wrap(x - CX[i], nx);
-        st->fS[i][idx] = st->f[i][src];
-        st->hS[i][idx] = st->h[i][src];
+        pull_src(st, x, y, i, &src, &q);     /* NS and CAC: bounce-back at walls */
+        st->fS[i][idx] = st->f[q][src];
+        st->hS[i][idx] = st->h[q][src];
         phi += st->hS[i][idx];
       }
       for (int i = 0; i < 5; ++i) {
-        int src = wrap(y - CY[i], ny) * nx + wrap(x - CX[i], nx);
-        st->sS[i][idx] = st->s[i][src];
+        const int mode = pull_src(st, x, y, i, &src, &q);
+        /* anti-bounce-back to the far-field values: -f*_opp + 2 w_i X_far */
+        st->sS[i][idx] = mode == 2 ? -st->s[q][src] + 2.0 * W5[i] * C_FAR : st->s[q][src];
         C += st->sS[i][idx];
         real_t gold = st->gpre[i][idx];
-        st->gS[i][idx] = gold + (st->gpost[i][src] - gold) * st->rr[src];
+        const real_t gsrc = mode == 2 ? -st->gpost[q][src] + 2.0 * W5[i] * PSI_FAR
+                                      : st->gpost[q][src];
+        st->gS[i][idx] = gold + (gsrc - gold) * st->rr[src];
         psi += st->gS[i][idx];
         psio += gold;
       }
@@ -615,8 +716,9 @@ static void pass_stream(ostate *st) {
       /* temperature populations (thermal mode): plain pull, and the
        * supersaturation field whose gradient enters grad F(U) */
       for (int i = 0; i < 5; ++i) {
-        int src = wrap(y - CY[i], ny) * nx + wrap(x - CX[i], nx);
-        st->eS[i][idx] = st->e[i][src];
+        const int mode = pull_src(st, x, y, i, &src, &q);
+        st->eS[i][idx] = mode == 2 ? -st->e[q][src] + 2.0 * W5[i] * st->par[P_THETA0]
+                                   : st->e[q][src];
       }
       st->US[idx] = supersat(st, C, psi);
     }
@@ -625,11 +727,11 @@ static void pass_stream(ostate *st) {
 /* Isotropic 9-point gradient and Laplacian (reading R5):
  *   grad X = (1/cs2) sum_i w_i c_i X(x + c_i)
  *   lap  X = (2/cs2) sum_i w_i [X(x + c_i) - X(x)]                       */
-static void grad9(const real_t *X, int nx, int ny, int x, int y, real_t *gx,
+static void grad9(const ostate *st, const real_t *X, int kind, int x, int y, real_t *gx,
                   real_t *gy) {
   real_t ax = 0, ay = 0;
   for (int i = 1; i < 9; ++i) {
-    real_t v = X[wrap(y + CY[i], ny) * nx + wrap(x + CX[i], nx)];
+    real_t v = field_at(st, X, x + CX[i], y + CY[i], kind);
     ax += W9[i] * CX[i] * v;
     ay += W9[i] * CY[i] * v;
   }
@@ -637,10 +739,10 @@ static void grad9(const real_t *X, int nx, int ny, int x, int y, real_t *gx,
   *gy = ay / CS2;
 }
 
-static real_t lap9(const real_t *X, int nx, int ny, int x, int y) {
-  real_t c = X[y * nx + x], a = 0;
+static real_t lap9(const ostate *st, const real_t *X, int kind, int x, int y) {
+  real_t c = X[y * st->nx + x], a = 0;
   for (int i = 1; i < 9; ++i)
-    a += W9[i] * (X[wrap(y + CY[i], ny) * nx + wrap(x + CX[i], nx)] - c);
+    a += W9[i] * (field_at(st, X, x + CX[i], y + CY[i], kind) - c);
   return 2.0 * a / CS2;
 }
 
@@ -664,11 +766,11 @@ static void pass_collide(ostate *st) {
 
       /* --- stencils --- */
       real_t gpx, gpy, gsx, gsy, dvxx, dvxy, dvyx, dvyy;
-      grad9(st->phiS, nx, ny, x, y, &gpx, &gpy);
-      real_t lphi = lap9(st->phiS, nx, ny, x, y);
-      grad9(st->psiS, nx, ny, x, y, &gsx, &gsy);
-      grad9(st->vx_o, nx, ny, x, y, &dvxx, &dvxy);  /* d_x vx, d_y vx */
-      grad9(st->vy_o, nx, ny, x, y, &dvyx, &dvyy);  /* d_x vy, d_y vy */
+      grad9(st, st->phiS, GK_NOFLUX, x, y, &gpx, &gpy);
+      real_t lphi = lap9(st, st->phiS, GK_NOFLUX, x, y);
+      grad9(st, st->psiS, GK_PSI, x, y, &gsx, &gsy);
+      grad9(st, st->vx_o, GK_VX, x, y, &dvxx, &dvxy);  /* d_x vx, d_y vx */
+      grad9(st, st->vy_o, GK_VY, x, y, &dvyx, &dvyy);  /* d_x vy, d_y vy */
 
       /* --- gas-liquid interface --- */
       const real_t rho = rg + phi * (rl - rg);
@@ -774,7 +876,7 @@ static void pass_collide(ostate *st) {
         if (thermal) {
           Fu = f_of_u(st, &d, U);
           real_t gux, guy;
-          grad9(st->US, nx, ny, x, y, &gux, &guy);
+          grad9(st, st->US, GK_U, x, y, &gux, &guy);
           const real_t Xx = as2 * gsx + Nx, Xy = as2 * gsy + Ny;
           const real_t dFx = d.Mcinf * (1.0 - k) * gux, dFy = d.Mcinf * (1.0 - k) * guy;
           Qeff = Q / Fu + par[P_W0] * par[P_W0] / (Fu * Fu) * (dFx * Xx + dFy * Xy);
@@ -1022,9 +1124,12 @@ void or_stencil(const double *X, int nx, int ny, int x, int y, double *out) {
   real_t *tmp = (real_t *)malloc((size_t)nx * ny * sizeof(real_t));
   if (!tmp) return;
   for (int i = 0; i < nx * ny; ++i) tmp[i] = X[i];
+  ostate per;                       /* a periodic lattice of the array's size */
+  memset(&per, 0, sizeof(per));
+  per.nx = nx; per.ny = ny; per.n = nx * ny;
   real_t gx, gy;
-  grad9(tmp, nx, ny, x, y, &gx, &gy);
-  out[0] = RE_(gx); out[1] = RE_(gy); out[2] = RE_(lap9(tmp, nx, ny, x, y));
+  grad9(&per, tmp, GK_NOFLUX, x, y, &gx, &gy);
+  out[0] = RE_(gx); out[1] = RE_(gy); out[2] = RE_(lap9(&per, tmp, GK_NOFLUX, x, y));
   free(tmp);
 }
 

@@ -1,0 +1,129 @@
+"""Pins of the oracle's boundary conditions (Section 3, model parameters:
+half-way bounce-back for no-slip and no-flux walls, the symmetric scheme for
+symmetry planes; Section 4: far-field Dirichlet values psi = psi_l, C = 1,
+theta = -Omega), as read in reading R31.
+
+Each test checks the oracle against something other than its own formulas:
+the closed-form decay of a shear wave between no-slip walls, the exact
+equivalence of a symmetric side with the mirrored half of a periodic lattice
+twice as large, conservation in a closed box, and the Fourier-series solution
+of diffusion between a no-flux wall and a Dirichlet side.
+"""
+import math
+
+import numpy as np
+
+import oracle
+from paper_2407_01651_gb300 import workload as wl
+
+PERIODIC, SYMMETRIC, WALL, FARFIELD = 0, 1, 2, 3
+
+
+def test_shear_wave_between_walls_decays_at_the_viscous_rate():
+    """v_x = U sin(pi (y + 1/2) / H) between half-way bounce-back walls at
+    y = -1/2 and y = H - 1/2 decays as exp(-nu (pi/H)^2 t) with its shape kept:
+    the walls sit exactly half-way and carry no slip."""
+    nx, ny, U0 = 4, 32, 1e-3
+    p = dict(wl.BASE_PARAMS, g=0.0)
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    mode = np.sin(math.pi * (y + 0.5) / ny)
+    one = np.ones_like(x)
+    o = oracle.Oracle(nx, ny, p)
+    o.set_bc(PERIODIC, PERIODIC, WALL, WALL)
+    o.init_fields(one, -one, one, U0 * mode, 0 * one, 0 * one)
+    for T in (600, 1500):
+        o.step(T - o.steps)
+        f = o.fields(("vx", "vy"))
+        amp = (f["vx"] * mode).sum() / (mode * mode).sum()
+        assert math.isclose(amp / U0, math.exp(-p["nu"] * (math.pi / ny) ** 2 * T), rel_tol=1e-3)
+        assert np.abs(f["vx"] - amp * mode).max() < 1e-4 * U0
+        assert np.abs(f["vy"]).max() < 1e-5 * U0
+
+
+def _mirror_equivalence(axis, thermal, T=60):
+    nx, ny = 40, 48
+    p = dict(wl.BASE_PARAMS, g=(1e-5 if axis == 0 else 0.0))
+    if thermal:
+        p.update(wl.THERMAL_PARAMS, Le=2.0)
+    a = oracle.Oracle(nx, ny, p)
+    a.set_bc(*((SYMMETRIC, SYMMETRIC, PERIODIC, PERIODIC) if axis == 0
+               else (PERIODIC, PERIODIC, SYMMETRIC, SYMMETRIC)))
+    a.init_spec([(12.3, 20.7, 0.0)], 6.0, [(28.4, 30.2, 9.0)])
+    f0 = a.fields(("phi", "psi", "C"))
+    if axis == 0:
+        NX, NY = 2 * nx, ny
+        mir = lambda f: np.concatenate([f, f[:, ::-1]], axis=1)      # noqa: E731
+        half = lambda f: f[:, :nx]                                     # noqa: E731
+    else:
+        NX, NY = nx, 2 * ny
+        mir = lambda f: np.concatenate([f, f[::-1, :]], axis=0)      # noqa: E731
+        half = lambda f: f[:ny, :]                                     # noqa: E731
+    b = oracle.Oracle(NX, NY, p)
+    b.set_rho_bar(a.rho_bar)
+    b.init_fields(mir(f0["phi"]), mir(f0["psi"]), mir(f0["C"]))
+    a.step(T)
+    b.step(T)
+    fa, fb = a.fields(), b.fields()
+    for k in fa:
+        scale = max(np.abs(half(fb[k])).max(), 1e-30)
+        assert np.abs(fa[k] - half(fb[k])).max() <= 1e-12 * scale, (axis, k)
+    assert fa["psi"].max() > 0.5 and np.abs(fa["vx"]).max() > 0.0
+
+
+def test_symmetric_sides_equal_the_mirrored_periodic_lattice():
+    """A lattice with symmetric planes on two opposite sides evolves exactly
+    like one half of the periodic lattice of twice its size whose initial
+    fields are mirrored (the symmetric scheme reflects populations and the
+    normal velocity), with a seed, a bubble, flow and gravity along the
+    planes, in the isothermal and thermal models."""
+    _mirror_equivalence(0, False)
+    _mirror_equivalence(1, False)
+    _mirror_equivalence(0, True)
+
+
+def test_closed_box_conserves_gas_solute_and_enthalpy():
+    """Half-way bounce-back on all four sides returns every population to its
+    site: sum phi, sum C and sum rho H stay constant with bubbles rising and a
+    dendrite growing."""
+    lay = wl.random_layout(56, 64, 2, 2, rng_seed=9, R_max=9)
+    p = dict(lay.params, g=1e-5, **dict(wl.THERMAL_PARAMS, Le=2.0))
+    o = oracle.Oracle(lay.nx, lay.ny, p)
+    o.set_bc(WALL, WALL, WALL, WALL)
+    o.init_spec(lay.seeds, lay.R_s, lay.bubbles)
+    d0, t0 = o.diag(), o.thermal_totals()
+    o.step(200)
+    d, t = o.diag(), o.thermal_totals()
+    assert d["nonfinite"] == 0 and d["max_v"] > 0
+    assert abs(d["sum_phi"] / d0["sum_phi"] - 1) < 1e-12
+    assert abs(d["sum_C"] / d0["sum_C"] - 1) < 1e-12
+    assert abs(t["sum_e"] / t0["sum_e"] - 1) < 1e-12
+
+
+def _series(v0, vfar, D, t, L, yw):
+    """Diffusion on [0, L] with zero flux at 0, u(L) = vfar, u(0, .) = v0."""
+    u = np.full_like(yw, vfar)
+    for n in range(400):
+        k = (n + 0.5) * math.pi / L
+        u += (v0 - vfar) * 2 * (-1) ** n / ((n + 0.5) * math.pi) * np.cos(k * yw) * math.exp(
+            -D * k * k * t)
+    return u
+
+
+def test_far_field_dirichlet_against_the_diffusion_series():
+    """A melt column between a no-flux wall (y = -1/2) and a far-field side
+    (y = H - 1/2) with C = 1 and theta = -Omega there: from uniform C = 0.5 and
+    theta = -0.3 both relax like the series solution of the diffusion
+    equation (D for C, alpha = Le D for theta); psi stays at psi_l."""
+    nx, ny = 4, 40
+    p = dict(wl.BASE_PARAMS, g=0.0, **dict(wl.THERMAL_PARAMS, Le=1.0, theta0=-0.55))
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    one = np.ones_like(x)
+    o = oracle.Oracle(nx, ny, p)
+    o.set_bc(PERIODIC, PERIODIC, WALL, FARFIELD)
+    o.init_fields(one, -one, 0.5 * one, theta=-0.3 * one)
+    o.step(1000)
+    f = o.fields(("C", "theta", "psi"))
+    yw = y[:, 0] + 0.5
+    assert np.abs(f["C"] - _series(0.5, 1.0, p["D"], 1000, ny, yw)[:, None]).max() < 2e-4
+    assert np.abs(f["theta"] - _series(-0.3, -0.55, p["D"], 1000, ny, yw)[:, None]).max() < 2e-3
+    assert np.abs(f["psi"] + 1).max() < 1e-14
