@@ -331,6 +331,61 @@ def run_precision(args) -> None:
         "speedup_bf16_vs_fp32": out["bf16"]["mlups"] / out["fp32"]["mlups"]}))
 
 
+def run_bounded(args) -> None:
+    """The 4096^2 lattice in the boundary arrangement of the paper's Section 4
+    (symmetric sides in x, a no-flux wall at the bottom, the far field psi_l,
+    C = 1, theta = -Omega at the top) with the temperature lattice on: MLUPS
+    and roofline of the boundary-aware y-march, against the periodic thermal
+    step in the same process."""
+    import torch
+
+    from paper_2407_01651_gb300 import pf
+    from paper_2407_01651_gb300 import workload as wl
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    lay = wl.growth_lattice(args.size, args.size)
+    par = dict(lay.params, **wl.THERMAL_PARAMS)
+    stream = torch.cuda.current_stream()
+    sites = lay.nx * lay.ny
+    bpl = BYTES_PER_LU_THERMAL["fp32"]
+    res = {}
+    for mode, bc in (("bounded", (pf.BC_SYMMETRIC, pf.BC_SYMMETRIC, pf.BC_WALL, pf.BC_FARFIELD)),
+                     ("periodic", None)):
+        sim = pf.Simulation([(lay.nx, lay.ny)], par, "fp32", stream=stream.cuda_stream)
+        if bc:
+            sim.set_boundaries(0, *bc)
+        sim.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
+        d0, t0 = sim.reduce(0), sim.reduce_thermal(0)
+        sim.step(args.warmup)
+        launches0 = sim.launches
+        ms = _time_steps(torch, sim, stream, args.steps)
+        launches = sim.launches - launches0
+        d, t = sim.reduce(0), sim.reduce_thermal(0)
+        if d["nonfinite"]:
+            raise SystemExit(f"{mode}: non-finite fields after the timed run")
+        res[mode] = {"mlups": sites * args.steps / ms / 1e3, "ms_per_step": ms / args.steps,
+                     "algorithmic_gbs": bpl * sites * args.steps / ms / 1e6,
+                     "gpu_launches": launches,
+                     "sum_phi_rel_drift": d["sum_phi"] / d0["sum_phi"] - 1.0,
+                     "mean_theta": t["sum_theta"] / sites}
+        sim.close()
+        torch.cuda.empty_cache()
+    peak, peak_kind = measured_peaks()
+    b = res["bounded"]
+    print(json.dumps({
+        "metric": "bounded thermal coupled-step MLUPS at 4096² and % of HBM roofline",
+        "value": b["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(workload_config(lay.nx, "fp32"), thermal=wl.THERMAL_PARAMS,
+                       boundaries="x: symmetric | y-: wall | y+: far field"),
+        "roofline": {"bound": "hbm", "achieved": b["algorithmic_gbs"], "peak": peak,
+                     "unit": "GB/s", "frac": b["algorithmic_gbs"] / peak, "traffic": None,
+                     "peak_kind": peak_kind, "bytes_per_lu": bpl,
+                     "kernel": "k_step_ymarch_bc<thermal> (one launch per step)"},
+        "modes": res, "gpu_launches": b["gpu_launches"]}))
+
+
 def run_thermal(args) -> None:
     """The 4096^2 lattice with the temperature lattice on (Section 4 of the
     paper: Le = 50, c_p^s / c_p = 1, theta0 = -Omega): MLUPS and the HBM
@@ -403,10 +458,11 @@ def main() -> None:
     ap.add_argument("--chunk", type=int, default=None, help="rows per y-march tile / tile a")
     ap.add_argument("--tile-b", type=int, default=0)
     ap.add_argument("--workload", default="lattice",
-                    choices=("lattice", "ensemble", "precision", "thermal"),
+                    choices=("lattice", "ensemble", "precision", "thermal", "bounded"),
                     help="lattice: the 4096^2 headline; ensemble: 96 uneven domains; "
                          "precision: 8192x4096 in FP32 / FP16 / BF16 storage; "
-                         "thermal: the 4096^2 lattice with the temperature lattice on")
+                         "thermal: the 4096^2 lattice with the temperature lattice on; "
+                         "bounded: the same with the paper's Section-4 boundaries")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -427,6 +483,9 @@ def main() -> None:
         return
     if args.workload == "thermal":
         run_thermal(args)
+        return
+    if args.workload == "bounded":
+        run_bounded(args)
         return
 
     import numpy as np

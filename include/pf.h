@@ -313,6 +313,27 @@ pf_status pf_reduce_noalloc(const void *fields, int fields_fp64, long long plane
                             long long offset, int nx, int ny, const pf_probe *probe,
                             pf_diag *out, void *cuda_stream);
 
+/* Boundary types of a domain side (Section 3: half-way bounce-back for no-slip
+ * walls and no-flux scalars, the symmetric scheme for symmetry planes;
+ * Section 4: far-field Dirichlet values).  Every side sits half-way between
+ * the last site and its ghost. */
+enum {
+  PF_BC_PERIODIC = 0,   /* wraps to the opposite side (which must be periodic too)   */
+  PF_BC_SYMMETRIC = 1,  /* mirror plane: populations reflected, normal velocity flipped */
+  PF_BC_WALL = 2,       /* half-way bounce-back on every lattice: no slip, no flux     */
+  PF_BC_FARFIELD = 3    /* bounce-back for the flow and phi; Dirichlet psi = -1, C = 1,
+                           theta = theta0 by anti-bounce-back                         */
+};
+
+/* Boundary types of domain dom's sides, bc = {x-, x+, y-, y+}, before
+ * pf_init_fields / pf_set_fields of that domain (seeds and bubbles then use
+ * plain distances along non-periodic axes).  Non-periodic sides need FP32 or
+ * FP64 storage and the y-march traversal (selected here); the adjoint takes
+ * periodic domains only.  Synchronises the stream.  Errors: BAD_ARG (type out
+ * of range, unpaired periodic side, 16-bit storage), STATE (domain already
+ * initialised), CUDA. */
+pf_status pf_set_boundaries(pf_handle *h, int dom, const int bc[4]);
+
 /* Planes of the raw state of the handle: PF_STATE_PLANES, or
  * PF_STATE_PLANES_THERMAL in thermal mode; -1 for NULL. */
 int pf_state_planes(const pf_handle *h);

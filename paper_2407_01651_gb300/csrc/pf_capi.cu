@@ -44,6 +44,7 @@ struct pf_handle {
   int n_pop = N_POP;        // population planes per state copy
   int n_aux = N_AUX;        // lagged-scalar planes per state copy
   int n_phys = N_PHYS;      // planes of the raw FP64 state
+  int any_bc = 0;           // some domain has a non-periodic side
   int variant = STEP_YMARCH;  // step kernel traversal
   int tx = 32, ty = 8;      // tile of the 2-D variant
   int chunk = 32;           // rows per tile of the y-march variants (tuned at 4096^2)
@@ -181,6 +182,7 @@ static KParams<R> make_kparams(const pf_params& p) {
     k.th_iLe = (R)(1.0 / p.Le);
     k.th_dF = (R)(der[1] * (1.0 - p.k));
     k.W0sq = (R)(p.W0 * p.W0);
+    k.th_far = (R)p.theta0;
   }
   return k;
 }
@@ -643,6 +645,7 @@ static StepArgs<S, R> make_step_args(const pf_handle* h, const void* pin, const 
   a.err = h->d_err;
   a.drop_copies = h->drop_copies;
   a.thermal = h->thermal;
+  a.bc = h->any_bc;
   a.kp = make_kparams<R>(h->p);
   return a;
 }
@@ -655,7 +658,8 @@ static pf_status launch_all(pf_handle* h, StepArgs<S, R> a, cudaStream_t stream)
   const int cap = h->persistent
                       ? std::max(1, h->sms) * step_blocks_per_sm<S, R>(h->variant, h->tx, h->ty,
                                                                        h->plane_stride,
-                                                                       h->thermal != 0)
+                                                                       h->thermal != 0,
+                                                                       h->any_bc != 0)
                       : 1 << 30;
   if (h->launch_mode == 0) {
     a.tile_base = 0;
@@ -757,6 +761,9 @@ extern "C" pf_status pf_set_step_config(pf_handle* h, int variant, int a, int b)
   if (!h) return PF_ERR_BAD_ARG;
   if (h->thermal && variant != STEP_YMARCH)
     return fail(h, PF_ERR_BAD_ARG, "thermal mode runs the y-march traversal (variant 1) only");
+  if (h->any_bc && variant != STEP_YMARCH)
+    return fail(h, PF_ERR_BAD_ARG,
+                "domains with non-periodic sides run the y-march traversal (variant 1) only");
   if (variant == STEP_TILE) {
     if (a < 1 || b < 1 || a * b > 256 || a % 32 != 0)
       return fail(h, PF_ERR_BAD_ARG, "tile variant needs tx a multiple of 32 and tx*ty <= 256");
@@ -811,7 +818,7 @@ static pf_status autotune_t(pf_handle* h, int trial_steps, int out[4]) {
   std::vector<Cand> cands;
   for (int ch : {8, 16, 24, 32, 48, 64, 96})
     for (int pers : {0, 1}) cands.push_back({STEP_YMARCH, ch, 0, pers});
-  if (!h->thermal) {
+  if (!h->thermal && !h->any_bc) {
     if (staged_ok_t<S, R>(h))
       for (int ch : {16, 32, 48, 64, 96, 128})
         for (int pers : {0, 1}) cands.push_back({STEP_STAGED, ch, 0, pers});
@@ -1003,6 +1010,38 @@ extern "C" pf_status pf_reduce(pf_handle* h, int dom, const pf_probe* probe, pf_
 }
 
 // ---------------------------------------------------------------------------
+// boundaries
+// ---------------------------------------------------------------------------
+extern "C" pf_status pf_set_boundaries(pf_handle* h, int dom, const int bc[4]) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (dom < 0 || dom >= (int)h->doms.size() || !bc)
+    return fail(h, PF_ERR_BAD_ARG, "bad domain index or NULL bc");
+  for (int k = 0; k < 4; ++k)
+    if (bc[k] < PF_BC_PERIODIC || bc[k] > PF_BC_FARFIELD)
+      return fail(h, PF_ERR_BAD_ARG, "boundary types are 0 (periodic) .. 3 (far field)");
+  if ((bc[0] == PF_BC_PERIODIC) != (bc[1] == PF_BC_PERIODIC) ||
+      (bc[2] == PF_BC_PERIODIC) != (bc[3] == PF_BC_PERIODIC))
+    return fail(h, PF_ERR_BAD_ARG, "a periodic side needs a periodic opposite side");
+  const bool open = bc[0] || bc[1] || bc[2] || bc[3];
+  if (open && h->prec != PF_FP32 && h->prec != PF_FP64)
+    return fail(h, PF_ERR_BAD_ARG, "non-periodic sides need FP32 or FP64 storage");
+  if (h->inited[dom])
+    return fail(h, PF_ERR_STATE, "set the boundaries before initialising the domain");
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (int k = 0; k < 4; ++k) h->ddesc[dom].bc[k] = (unsigned char)bc[k];
+  h->any_bc = 0;
+  for (const DomDesc& d : h->ddesc)
+    if (d.bc[0] || d.bc[1] || d.bc[2] || d.bc[3]) h->any_bc = 1;
+  if (h->any_bc && h->variant != STEP_YMARCH) {
+    h->variant = STEP_YMARCH;
+    h->chunk = 32;
+  }
+  for (auto& g : h->gexec)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  return upload_tables(h);
+}
+
+// ---------------------------------------------------------------------------
 // thermal mode
 // ---------------------------------------------------------------------------
 extern "C" int pf_state_planes(const pf_handle* h) { return h ? h->n_phys : -1; }
@@ -1189,6 +1228,8 @@ extern "C" pf_status pf_adjoint_step(pf_handle* h, int n_steps, const pf_objecti
     return fail(h, PF_ERR_BAD_ARG, "the adjoint supports the FP32 and FP64 storage forms");
   if (h->thermal)
     return fail(h, PF_ERR_BAD_ARG, "the adjoint covers the isothermal model (thermal = 0) only");
+  if (h->any_bc)
+    return fail(h, PF_ERR_BAD_ARG, "the adjoint covers periodic domains only");
   if (!h->inited[0]) return fail(h, PF_ERR_STATE, "initialise the domain before the adjoint");
   if (!std::isfinite(obj->w_solid) || !std::isfinite(obj->w_centroid))
     return fail(h, PF_ERR_BAD_ARG, "objective weights must be finite");

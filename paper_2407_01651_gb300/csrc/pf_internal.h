@@ -37,6 +37,7 @@ struct StepArgs {
   unsigned int* err;            // device error bits (1: a staged copy timed out), or nullptr
   int drop_copies;              // testing only: the staged kernel skips its bulk copies
   int thermal;                  // 1: temperature lattice and finite-Le F(U) (FP32 / FP64)
+  int bc;                       // 1: some domain has a non-periodic side (y-march only)
   KParams<R> kp;
 };
 
@@ -89,6 +90,11 @@ cudaError_t launch_step(const StepArgs<S, R>& a, int variant, int tx, int ty, in
 // resident CTAs per SM.
 template <typename S, typename R>
 cudaError_t launch_step_staged(const StepArgs<S, R>& a, int grid, cudaStream_t st);
+// y-march for handles with non-periodic domain sides (FP32 / FP64 storage).
+template <typename S, typename R>
+cudaError_t launch_ymarch_bc(const StepArgs<S, R>& a, bool big, int grid, cudaStream_t st);
+template <typename S, typename R>
+int ymarch_bc_blocks_per_sm(bool big, bool thermal);
 template <typename S, typename R>
 int staged_smem_bytes();
 template <typename S, typename R>
@@ -97,7 +103,8 @@ template <typename S, typename R>
 int staged_blocks_per_sm();
 // Resident CTAs per SM of the step kernel (for persistent grids).
 template <typename S, typename R>
-int step_blocks_per_sm(int variant, int tx, int ty, long long plane_stride, bool thermal);
+int step_blocks_per_sm(int variant, int tx, int ty, long long plane_stride, bool thermal,
+                       bool bc);
 template <typename S, typename R>
 cudaError_t launch_init_spec(const InitArgs<S, R>& a, cudaStream_t st);
 template <typename S, typename R>

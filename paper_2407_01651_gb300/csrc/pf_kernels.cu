@@ -52,6 +52,11 @@ __device__ void write_thermal(S* out, R* aout, R* fields, long long ps, long lon
   if (fields) fields[FLD_THETA * ps + site] = theta;
 }
 
+// Offset along an axis: minimum image on a periodic axis, plain otherwise.
+__device__ __forceinline__ double axis_offset(double d, double L, bool periodic) {
+  return periodic ? min_image(d, L) : d;
+}
+
 // Write the equilibrium state and the fields of one site.
 template <typename S, typename R>
 __device__ void write_equilibrium(S* out, R* aout, R* fields, long long ps, long long site,
@@ -117,8 +122,8 @@ __global__ void k_init_spec(InitArgs<S, R> a) {
     double psi = -1.0, best = 0.0;
     int gid = 0;
     for (int s = 0; s < a.n_seeds; ++s) {
-      const double dx = min_image((double)x - a.seeds[3 * s], (double)d.nx);
-      const double dy = min_image((double)y - a.seeds[3 * s + 1], (double)d.ny);
+      const double dx = axis_offset((double)x - a.seeds[3 * s], (double)d.nx, d.bc[0] == 0);
+      const double dy = axis_offset((double)y - a.seeds[3 * s + 1], (double)d.ny, d.bc[2] == 0);
       const double r2 = dx * dx + dy * dy;
       const double v = r2 > seed_far * seed_far
                            ? -1.0
@@ -131,8 +136,8 @@ __global__ void k_init_spec(InitArgs<S, R> a) {
     }
     double phi = 1.0;
     for (int b = 0; b < a.n_bub; ++b) {
-      const double dx = min_image((double)x - a.bubbles[3 * b], (double)d.nx);
-      const double dy = min_image((double)y - a.bubbles[3 * b + 1], (double)d.ny);
+      const double dx = axis_offset((double)x - a.bubbles[3 * b], (double)d.nx, d.bc[0] == 0);
+      const double dy = axis_offset((double)y - a.bubbles[3 * b + 1], (double)d.ny, d.bc[2] == 0);
       const double r2 = dx * dx + dy * dy;
       const double far = a.bubbles[3 * b + 2] + 60.0 * a.Wphi / a.sq2bphi;
       const double v =

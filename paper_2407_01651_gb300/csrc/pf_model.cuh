@@ -54,12 +54,19 @@ constexpr int N_PHYS_TH = 45;
 
 enum Field : int { FLD_PHI, FLD_PSI, FLD_C, FLD_U, FLD_P, FLD_VX, FLD_VY, FLD_MU, FLD_THETA, N_FIELDS };
 
+// Boundary type of a domain side, placed half-way between the last site and
+// its ghost: periodic; symmetric plane (populations and the normal velocity
+// mirrored); wall (half-way bounce-back: no slip, no flux); far field (wall
+// for the flow and phi, Dirichlet psi = -1, C = 1, theta = theta0 by
+// anti-bounce-back).
+enum BoundaryType : int { BC_PERIODIC = 0, BC_SYMMETRIC = 1, BC_WALL = 2, BC_FARFIELD = 3 };
+
 struct DomDesc {
   long long off;      // first site of the domain in every plane
   int nx, ny;
   int tiles_x, tile0; // tiling of the step kernel
   int grain_off;      // first entry of the domain in the grain table
-  int pad;
+  unsigned char bc[4];  // side types x-, x+, y-, y+ (BoundaryType; 0 = periodic)
   double eps_s;       // anisotropy strength of this domain
   double rho_bar;     // domain-mean density (buoyancy reference)
 };
@@ -86,6 +93,7 @@ struct KParams {
   R th_iLe;                 // 1 / Le
   R th_dF;                  // M c_inf (1 - k): grad F = th_dF grad U
   R W0sq;                   // W0^2
+  R th_far;                 // theta at a far-field side (theta0)
 };
 
 // ---------------------------------------------------------------------------

@@ -193,6 +193,8 @@ template <typename S, typename R>
 cudaError_t launch_step(const StepArgs<S, R>& a, int variant, int tx, int ty, int grid,
                         cudaStream_t st) {
   if (variant == STEP_STAGED) return launch_step_staged<S, R>(a, grid, st);
+  if (variant == STEP_YMARCH && a.bc)
+    return launch_ymarch_bc<S, R>(a, big_handle(a.plane_stride, a.thermal != 0), grid, st);
   if (big_handle(a.plane_stride, a.thermal != 0))
     launch_traversal<S, R, true>(a, variant, tx, ty, grid, st);
   else launch_traversal<S, R, false>(a, variant, tx, ty, grid, st);
@@ -215,17 +217,20 @@ static int traversal_blocks_per_sm(int variant, int tx, int ty, bool thermal) {
 }
 
 template <typename S, typename R>
-int step_blocks_per_sm(int variant, int tx, int ty, long long plane_stride, bool thermal) {
+int step_blocks_per_sm(int variant, int tx, int ty, long long plane_stride, bool thermal,
+                       bool bc) {
   if (variant == STEP_STAGED) return staged_blocks_per_sm<S, R>();
+  if (variant == STEP_YMARCH && bc)
+    return ymarch_bc_blocks_per_sm<S, R>(big_handle(plane_stride, thermal), thermal);
   return big_handle(plane_stride, thermal)
              ? traversal_blocks_per_sm<S, R, true>(variant, tx, ty, thermal)
              : traversal_blocks_per_sm<S, R, false>(variant, tx, ty, thermal);
 }
 
-template int step_blocks_per_sm<double, double>(int, int, int, long long, bool);
-template int step_blocks_per_sm<float, float>(int, int, int, long long, bool);
-template int step_blocks_per_sm<__half, float>(int, int, int, long long, bool);
-template int step_blocks_per_sm<__nv_bfloat16, float>(int, int, int, long long, bool);
+template int step_blocks_per_sm<double, double>(int, int, int, long long, bool, bool);
+template int step_blocks_per_sm<float, float>(int, int, int, long long, bool, bool);
+template int step_blocks_per_sm<__half, float>(int, int, int, long long, bool, bool);
+template int step_blocks_per_sm<__nv_bfloat16, float>(int, int, int, long long, bool, bool);
 
 template cudaError_t launch_step<double, double>(const StepArgs<double, double>&, int, int, int,
                                                 int, cudaStream_t);

@@ -1,0 +1,331 @@
+// pf_step_bc.cu -- the y-march step kernel for domains with non-periodic
+// sides (arXiv 2407.01651, Section 3: half-way bounce-back for no-slip walls
+// and no-flux scalars, the symmetric scheme for symmetry planes; Section 4:
+// far-field Dirichlet values psi = psi_l, C = 1, theta = -Omega).
+//
+// Same traversal and per-site arithmetic as k_step_ymarch (pf_step.cu); what
+// differs is where values come from at a non-periodic side:
+//   - pull streaming: a symmetric side reflects the source site and the
+//     direction; a wall returns the site's own post-collision population of
+//     the opposite direction; a far-field side does the same for NS and CAC
+//     and an anti-bounce-back -f*_opp + 2 w_i X_far for psi, C and theta; a
+//     diagonal source beyond both a reflecting and a bouncing side bounces;
+//   - stencils: ghost rows and columns of the shared-memory ring hold the
+//     mirror site's values mapped per side (phi, psi, U unchanged, or
+//     2 X_far - X for psi and U at a far-field side; the velocity's normal
+//     component flipped at a symmetric side, both components at a wall or far
+//     field; corners: the y side's map, then the x side's).
+// Sites away from a non-periodic side take the periodic pulls of pf_pull.cuh.
+// FP32 and FP64 storage only.
+#include "pf_site.cuh"
+
+namespace pf {
+
+namespace {
+
+__device__ __forceinline__ constexpr int cx9(int i) {
+  return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__device__ __forceinline__ constexpr int cy9(int i) {
+  return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__device__ __forceinline__ constexpr int opp9(int i) {
+  return i == 0 ? 0 : (i <= 4 ? (i + 1) % 4 + 1 : (i + 1) % 4 + 5);
+}
+// reflections that flip c_x / c_y
+__device__ __forceinline__ int mirx9(int i) {
+  switch (i) {
+    case 1: return 3; case 3: return 1; case 5: return 6; case 6: return 5;
+    case 7: return 8; case 8: return 7; default: return i;
+  }
+}
+__device__ __forceinline__ int miry9(int i) {
+  switch (i) {
+    case 2: return 4; case 4: return 2; case 5: return 8; case 8: return 5;
+    case 6: return 7; case 7: return 6; default: return i;
+  }
+}
+
+__device__ __forceinline__ unsigned site_at(const DomDesc& d, int x, int y) {
+  return (unsigned)d.off + (unsigned)y * (unsigned)d.nx + (unsigned)x;
+}
+
+// Source of the population of direction i pulled by (x, y): site, direction
+// to read and mode (0 plain or reflected, 1 wall bounce, 2 far-field bounce).
+struct PullSrc {
+  unsigned site;
+  int q, mode;
+};
+__device__ __forceinline__ PullSrc pull_src(const DomDesc& d, int x, int y, int i) {
+  const int nx = d.nx, ny = d.ny;
+  int sx = x - cx9(i), sy = y - cy9(i), q = i, bounce = 0;
+  if (sx < 0 || sx >= nx) {
+    const int t = d.bc[sx < 0 ? 0 : 1];
+    if (t == BC_PERIODIC) sx += sx < 0 ? nx : -nx;
+    else if (t == BC_SYMMETRIC) { sx = sx < 0 ? -1 - sx : 2 * nx - 1 - sx; q = mirx9(q); }
+    else bounce = t == BC_WALL ? 1 : 2;
+  }
+  if (sy < 0 || sy >= ny) {
+    const int t = d.bc[sy < 0 ? 2 : 3];
+    if (t == BC_PERIODIC) sy += sy < 0 ? ny : -ny;
+    else if (t == BC_SYMMETRIC) { sy = sy < 0 ? -1 - sy : 2 * ny - 1 - sy; q = miry9(q); }
+    else bounce = (t == BC_WALL && bounce < 2) ? 1 : 2;
+  }
+  if (bounce) return {site_at(d, x, y), opp9(i), bounce};
+  return {site_at(d, sx, sy), q, 0};
+}
+
+// A pull source of (x, y) lies beyond a non-periodic side.
+__device__ __forceinline__ bool near_side(const DomDesc& d, int x, int y) {
+  return (x == 0 && d.bc[0]) || (x == d.nx - 1 && d.bc[1]) || (y == 0 && d.bc[2]) ||
+         (y == d.ny - 1 && d.bc[3]);
+}
+
+// Ring fields: 0 phi, 1 psi, 2 vx_o, 3 vy_o, 4 U.  Ghost value across one side
+// of type t on axis (0: x, 1: y) from the mirror site's value v.
+template <typename R>
+__device__ __forceinline__ R ghost_map(int t, int axis, int field, R v) {
+  if (field == 2 || field == 3) {
+    const bool normal = (field == 2) == (axis == 0);
+    if (t == BC_SYMMETRIC) return normal ? -v : v;
+    return -v;
+  }
+  if (t == BC_FARFIELD) {
+    if (field == 1) return R(-2) - v;   // 2 psi_far - psi, psi_far = -1
+    if (field == 4) return -v;          // 2 U_far - U, U_far = 0
+  }
+  return v;
+}
+
+template <typename S, typename R, bool BIG>
+__device__ __forceinline__ void pull_hg_b(const StepArgs<S, R>& a, const DomDesc& d, int x,
+                                          int y, R h[9], R g[5], R& phi, R& psi, R& psio) {
+  const unsigned ps = (unsigned)a.plane_stride;
+  const unsigned own = site_at(d, x, y);
+  CSum<R> sh;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const PullSrc p = pull_src(d, x, y, i);
+    h[i] = ld<R>(pbase<BIG>(a.in, P_H + p.q, ps), pidx<BIG>(P_H + p.q, ps, p.site));
+    sh.add(h[i]);
+  }
+  phi = sh.value();
+  CSum<R> sg;
+  R po = R(0);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const PullSrc p = pull_src(d, x, y, i);
+    const R gold = ld<R>(pbase<BIG>(a.in, P_GPRE + i, ps), pidx<BIG>(P_GPRE + i, ps, own));
+    R gpo = ld<R>(pbase<BIG>(a.in, P_GPOST + p.q, ps), pidx<BIG>(P_GPOST + p.q, ps, p.site));
+    if (p.mode == 2) gpo = -gpo + R(2) * w5<R>(i) * R(-1);
+    const R rr = ld<R>(pbase<BIG>(a.ain, A_RR, ps), pidx<BIG>(A_RR, ps, p.site));
+    g[i] = gold + (gpo - gold) * rr;
+    sg.add(g[i]);
+    po += gold;
+  }
+  psi = sg.value();
+  psio = po;
+}
+
+template <typename S, typename R, bool BIG, bool TH>
+__device__ __forceinline__ void load_site_b(const StepArgs<S, R>& a, const DomDesc& d, int x,
+                                            int y, SiteIn<R>& in) {
+  const unsigned ps = (unsigned)a.plane_stride;
+  const unsigned own = site_at(d, x, y);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const PullSrc p = pull_src(d, x, y, i);
+    in.f[i] = ld<R>(pbase<BIG>(a.in, P_F + p.q, ps), pidx<BIG>(P_F + p.q, ps, p.site));
+  }
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const PullSrc p = pull_src(d, x, y, i);
+    R v = ld<R>(pbase<BIG>(a.in, P_S + p.q, ps), pidx<BIG>(P_S + p.q, ps, p.site));
+    if (p.mode == 2) v = -v + R(2) * w5<R>(i) * R(1);          // C_far = 1
+    in.s[i] = v;
+    if constexpr (TH) {
+      R e = ld<R>(pbase<BIG>(a.in, P_E + p.q, ps), pidx<BIG>(P_E + p.q, ps, p.site));
+      if (p.mode == 2) e = -e + R(2) * w5<R>(i) * a.kp.th_far;
+      in.e[i] = e;
+    }
+  }
+  in.phio = ld<R>(pbase<BIG>(a.ain, A_PHIO, ps), pidx<BIG>(A_PHIO, ps, own));
+  in.Co = ld<R>(pbase<BIG>(a.ain, A_CO, ps), pidx<BIG>(A_CO, ps, own));
+  in.Qo = ld<R>(pbase<BIG>(a.ain, A_QO, ps), pidx<BIG>(A_QO, ps, own));
+  in.gid = a.grain[own];
+  if constexpr (TH) in.Ho = ld<R>(pbase<BIG>(a.ain, A_HO, ps), pidx<BIG>(A_HO, ps, own));
+}
+
+template <typename S, typename R, bool BIG>
+__device__ __forceinline__ R pull_U_b(const StepArgs<S, R>& a, const DomDesc& d, int x, int y,
+                                      R psi) {
+  const unsigned ps = (unsigned)a.plane_stride;
+  CSum<R> cs;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const PullSrc p = pull_src(d, x, y, i);
+    R v = ld<R>(pbase<BIG>(a.in, P_S + p.q, ps), pidx<BIG>(P_S + p.q, ps, p.site));
+    if (p.mode == 2) v = -v + R(2) * w5<R>(i) * R(1);
+    cs.add(v);
+  }
+  const R C = cs.value();
+  const R omk = R(1) - a.kp.k;
+  const R A = (R(1) + a.kp.k) - omk * psi;
+  return (R(2) * C * frcp(A) - R(1)) * a.kp.inv_omk;
+}
+
+}  // namespace
+
+template <typename S, typename R, bool BIG, bool TH>
+__global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 3 : 2)
+    k_step_ymarch_bc(StepArgs<S, R> a) {
+  constexpr int RW = YM_W + 2;
+  constexpr int NF = TH ? 5 : 4;
+  __shared__ R ring[NF][4][RW];
+  const int t = threadIdx.x;
+  const unsigned ps = (unsigned)a.plane_stride;
+
+  for (int tile = a.tile_base + blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const DomDesc d = a.doms[a.tile_dom[tile]];
+    const int lt = tile - d.tile0;
+    const int nx = d.nx, ny = d.ny;
+    const int x0 = (lt % d.tiles_x) * YM_W;
+    const int ya = (lt / d.tiles_x) * a.chunk;
+    const int yb = min(ya + a.chunk, ny);
+    const int w = min(YM_W, nx - x0);
+    bool interior = false, active = false;
+    int col = 0, sc = 0, tx = -1;   // column of the values, ring column, x ghost side type
+    if (t < YM_W) {
+      interior = active = t < w;
+      col = x0 + t;
+      sc = t + 1;
+    } else if (t == YM_W) {
+      active = true;
+      sc = 0;
+      if (x0 == 0 && d.bc[0]) { col = 0; tx = d.bc[0]; }
+      else col = x0 == 0 ? nx - 1 : x0 - 1;
+    } else if (t == YM_W + 1) {
+      active = true;
+      sc = w + 1;
+      if (x0 + w >= nx && d.bc[1]) { col = nx - 1; tx = d.bc[1]; }
+      else col = x0 + w >= nx ? x0 + w - nx : x0 + w;
+    }
+
+    // ring values of row yr (ya-1 .. yb, possibly a ghost row) and the
+    // streamed h, g of the site (col, row) they were computed at
+    auto fill = [&](int yr, R (&h)[9], R (&g)[5], R& po) {
+      int ey = yr, ty = -1;
+      if (yr < 0) {
+        if (d.bc[2]) { ey = 0; ty = d.bc[2]; } else ey = yr + ny;
+      } else if (yr >= ny) {
+        if (d.bc[3]) { ey = ny - 1; ty = d.bc[3]; } else ey = yr - ny;
+      }
+      R v[NF];
+      const bool near = near_side(d, col, ey);
+      if (near) pull_hg_b<S, R, BIG>(a, d, col, ey, h, g, v[0], v[1], po);
+      else pull_hg<S, R, BIG>(a, sources(d, col, ey), h, g, v[0], v[1], po);
+      const unsigned s0 = site_at(d, col, ey);
+      v[2] = ld<R>(pbase<BIG>(a.ain, A_VXO, ps), pidx<BIG>(A_VXO, ps, s0));
+      v[3] = ld<R>(pbase<BIG>(a.ain, A_VYO, ps), pidx<BIG>(A_VYO, ps, s0));
+      if constexpr (TH)
+        v[4] = near ? pull_U_b<S, R, BIG>(a, d, col, ey, v[1])
+                    : pull_U<S, R, BIG>(a, sources(d, col, ey), v[1]);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        R u = v[f];
+        if (ty >= 0) u = ghost_map<R>(ty, 1, f, u);
+        if (tx >= 0) u = ghost_map<R>(tx, 0, f, u);
+        ring[f][yr & 3][sc] = u;
+      }
+    };
+
+    R hC[9], gC[5], poC = R(0);
+    for (int k = 0; k < 2; ++k) {
+      if (active) {
+        R h[9], g[5], po;
+        fill(ya - 1 + k, h, g, po);
+        if (k == 1) {
+#pragma unroll
+          for (int i = 0; i < 9; ++i) hC[i] = h[i];
+#pragma unroll
+          for (int i = 0; i < 5; ++i) gC[i] = g[i];
+          poC = po;
+        }
+      }
+    }
+
+    for (int j = ya; j < yb; ++j) {
+      SiteIn<R> in;
+      Src9 srcj;
+      if (interior) {
+        if (near_side(d, col, j)) {
+          load_site_b<S, R, BIG, TH>(a, d, col, j, in);
+          srcj.s[0] = site_at(d, col, j);
+        } else {
+          srcj = sources(d, col, j);
+          load_site<S, R, BIG, TH>(a, srcj, in);
+        }
+      }
+      R hL[9], gL[5], poL = R(0);
+      if (active) fill(j + 1, hL, gL, poL);
+      __syncthreads();
+      if (interior) {
+        const int m = (j - 1) & 3, c0 = j & 3, pp = (j + 1) & 3;
+        auto rows = [&](int f) { return Rows3<R>{ring[f][m], ring[f][c0], ring[f][pp]}; };
+        site_update<S, R, TH>(a, d, srcj, in, hC, gC, poC, rows(0), rows(1), rows(2), rows(3),
+                              sc, rows(NF - 1));
+      }
+#pragma unroll
+      for (int i = 0; i < 9; ++i) hC[i] = hL[i];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) gC[i] = gL[i];
+      poC = poL;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename S, typename R>
+cudaError_t launch_ymarch_bc(const StepArgs<S, R>& a, bool big, int grid, cudaStream_t st) {
+  if constexpr (sizeof(S) == sizeof(R)) {
+    if (big) {
+      if (a.thermal) k_step_ymarch_bc<S, R, true, true><<<grid, YM_THREADS, 0, st>>>(a);
+      else k_step_ymarch_bc<S, R, true, false><<<grid, YM_THREADS, 0, st>>>(a);
+    } else {
+      if (a.thermal) k_step_ymarch_bc<S, R, false, true><<<grid, YM_THREADS, 0, st>>>(a);
+      else k_step_ymarch_bc<S, R, false, false><<<grid, YM_THREADS, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+  } else {
+    return cudaErrorInvalidValue;   // boundaries need FP32 or FP64 storage (checked on the host)
+  }
+}
+
+template <typename S, typename R>
+int ymarch_bc_blocks_per_sm(bool big, bool thermal) {
+  int n = 0;
+  if constexpr (sizeof(S) == sizeof(R)) {
+    if (big) {
+      if (thermal)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_ymarch_bc<S, R, true, true>, YM_THREADS, 0);
+      else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_ymarch_bc<S, R, true, false>, YM_THREADS, 0);
+    } else {
+      if (thermal)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_ymarch_bc<S, R, false, true>, YM_THREADS, 0);
+      else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_ymarch_bc<S, R, false, false>, YM_THREADS, 0);
+    }
+  }
+  return n > 0 ? n : 1;
+}
+
+#define PF_BC_INST(S, R)                                                                  \
+  template cudaError_t launch_ymarch_bc<S, R>(const StepArgs<S, R>&, bool, int, cudaStream_t); \
+  template int ymarch_bc_blocks_per_sm<S, R>(bool, bool);
+PF_BC_INST(double, double)
+PF_BC_INST(float, float)
+PF_BC_INST(__half, float)
+PF_BC_INST(__nv_bfloat16, float)
+
+}  // namespace pf

@@ -19,6 +19,7 @@ PF_OK, PF_ERR_BAD_ARG, PF_ERR_OOM, PF_ERR_CUDA, PF_ERR_TIMEOUT, PF_ERR_NAN, PF_E
     0, -1, -2, -3, -4, -5, -6)
 PF_FP64, PF_FP32, PF_FP16_OFFSET, PF_BF16_OFFSET = 0, 1, 2, 3
 PRECISIONS = {"fp64": PF_FP64, "fp32": PF_FP32, "fp16": PF_FP16_OFFSET, "bf16": PF_BF16_OFFSET}
+BC_PERIODIC, BC_SYMMETRIC, BC_WALL, BC_FARFIELD = 0, 1, 2, 3
 FIELDS = ("phi", "psi", "C", "U", "p", "vx", "vy", "mu", "theta")
 STATE_PLANES = 39            # PF_STATE_PLANES; thermal handles have 45
 
@@ -113,11 +114,13 @@ def lib() -> ctypes.CDLL:
     L.pf_state_planes.restype = ctypes.c_int
     L.pf_set_temperature.argtypes = [P, I, D, S]
     L.pf_reduce_thermal.argtypes = [P, I, D]
+    L.pf_set_boundaries.argtypes = [P, I, ctypes.POINTER(ctypes.c_int)]
     for name in ("pf_params_default", "pf_params_derived", "pf_create", "pf_init_fields",
                  "pf_set_fields", "pf_step", "pf_get_fields", "pf_get_state", "pf_set_state",
                  "pf_reduce", "pf_sync", "pf_destroy", "pf_set_step_config",
                  "pf_get_step_config", "pf_reduce_noalloc", "pf_adjoint_step",
-                 "pf_set_launch", "pf_autotune", "pf_set_temperature", "pf_reduce_thermal"):
+                 "pf_set_launch", "pf_autotune", "pf_set_temperature", "pf_reduce_thermal",
+                 "pf_set_boundaries"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -233,6 +236,12 @@ class Simulation:
         self.close()
 
     # -- initialisation --------------------------------------------------------
+    def set_boundaries(self, dom: int, xm: int, xp: int, ym: int, yp: int) -> None:
+        """Side types x-, x+, y-, y+ of a domain before its initialisation:
+        BC_PERIODIC, BC_SYMMETRIC, BC_WALL or BC_FARFIELD."""
+        bc = (ctypes.c_int * 4)(int(xm), int(xp), int(ym), int(yp))
+        _check(lib().pf_set_boundaries(self.h, int(dom), bc), self.h)
+
     def init_fields(self, dom: int, seeds, R_s: float, bubbles) -> None:
         s = np.ascontiguousarray(np.asarray(seeds, dtype=np.float64).reshape(-1, 3))
         b = np.ascontiguousarray(np.asarray(bubbles, dtype=np.float64).reshape(-1, 3))
