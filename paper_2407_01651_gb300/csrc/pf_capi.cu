@@ -45,6 +45,18 @@ struct pf_handle {
   int n_aux = N_AUX;        // lagged-scalar planes per state copy
   int n_phys = N_PHYS;      // planes of the raw FP64 state
   int any_bc = 0;           // some domain has a non-periodic side
+  // With non-periodic sides (y-march): tiles touching such a side ("edge"
+  // tiles) run the boundary-aware kernel, the others the periodic one.  Tiles
+  // are ordered [plain tiles of every domain][edge tiles of every domain]; each
+  // run of consecutive tiles of one domain has its own descriptor in d_runs,
+  // whose tile0 maps the launch index back to the tile of the domain.
+  DomDesc* d_runs = nullptr;
+  int n_plain = 0;
+  std::vector<int> plain0, plain1, edge0, edge1;   // per-domain tile ranges
+  // the edge tiles run on a side stream, forked from and joined to the step's
+  // stream by events, so that they fill the SMs beside the plain tiles
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   int variant = STEP_YMARCH;  // step kernel traversal
   int tx = 32, ty = 8;      // tile of the 2-D variant
   int chunk = 32;           // rows per tile of the y-march variants (tuned at 4096^2)
@@ -270,6 +282,8 @@ static void release(pf_handle* h) {
   dev_free(h, h->grain);
   dev_free(h, h->grain_cs);
   dev_free(h, h->d_doms);
+  dev_free(h, h->d_runs);
+  h->d_runs = nullptr;
   dev_free(h, h->d_tile_dom);
   dev_free(h, h->partial);
   dev_free(h, h->d_diag);
@@ -281,23 +295,64 @@ static void release(pf_handle* h) {
   for (auto& g : h->gexec)
     if (g) { cudaGraphExecDestroy(g); g = nullptr; }
   if (h->cap_stream) { cudaStreamDestroy(h->cap_stream); h->cap_stream = nullptr; }
+  if (h->side) { cudaStreamDestroy(h->side); h->side = nullptr; }
+  if (h->fork_ev) { cudaEventDestroy(h->fork_ev); h->fork_ev = nullptr; }
+  if (h->join_ev) { cudaEventDestroy(h->join_ev); h->join_ev = nullptr; }
   h->fields = h->grain = nullptr;
 }
 
 static pf_status upload_tables(pf_handle* h) {
   // tiles of every domain, in domain order
   std::vector<int> tile_dom;
+  std::vector<int> tiles_y(h->ddesc.size());
   for (size_t d = 0; d < h->ddesc.size(); ++d) {
     DomDesc& dd = h->ddesc[d];
     const bool strip = h->variant == STEP_YMARCH || h->variant == STEP_STAGED;
     const int tw = strip ? YM_W : h->tx;
     const int th = strip ? h->chunk : h->ty;
     dd.tiles_x = (dd.nx + tw - 1) / tw;
-    const int tiles_y = (dd.ny + th - 1) / th;
+    tiles_y[d] = (dd.ny + th - 1) / th;
     dd.tile0 = (int)tile_dom.size();
-    for (int t = 0; t < dd.tiles_x * tiles_y; ++t) tile_dom.push_back((int)d);
+    for (int t = 0; t < dd.tiles_x * tiles_y[d]; ++t) tile_dom.push_back((int)d);
   }
   h->ntiles = (int)tile_dom.size();
+  if (h->any_bc) {
+    // plain tiles first, then edge tiles, in runs with their own descriptors
+    const size_t nd = h->ddesc.size();
+    std::vector<DomDesc> runs;
+    std::vector<int> order;
+    h->plain0.assign(nd, 0); h->plain1.assign(nd, 0);
+    h->edge0.assign(nd, 0); h->edge1.assign(nd, 0);
+    for (int pass = 0; pass < 2; ++pass) {
+      for (size_t d = 0; d < nd; ++d) {
+        const DomDesc& dd = h->ddesc[d];
+        const int tx = dd.tiles_x, ty = tiles_y[d];
+        (pass ? h->edge0 : h->plain0)[d] = (int)order.size();
+        int prev = -2;
+        for (int lt = 0; lt < tx * ty; ++lt) {
+          const int sx = lt % tx, cy = lt / tx;
+          const bool edge = (sx == 0 && dd.bc[0]) || (sx == tx - 1 && dd.bc[1]) ||
+                            (cy == 0 && dd.bc[2]) || (cy == ty - 1 && dd.bc[3]);
+          if (edge != (pass == 1)) continue;
+          if (lt != prev + 1) {
+            DomDesc r = dd;
+            r.tile0 = (int)order.size() - lt;
+            runs.push_back(r);
+          }
+          order.push_back((int)runs.size() - 1);
+          prev = lt;
+        }
+        (pass ? h->edge1 : h->plain1)[d] = (int)order.size();
+      }
+      if (pass == 0) h->n_plain = (int)order.size();
+    }
+    tile_dom.swap(order);
+    dev_free(h, h->d_runs);
+    h->d_runs = (DomDesc*)dev_alloc(h, runs.size() * sizeof(DomDesc));
+    if (!h->d_runs) return fail(h, PF_ERR_OOM, "tile table allocation failed");
+    PF_CUDA(h, cudaMemcpyAsync(h->d_runs, runs.data(), runs.size() * sizeof(DomDesc),
+                               cudaMemcpyHostToDevice, h->stream));
+  }
   dev_free(h, h->d_tile_dom);
   h->d_tile_dom = (int*)dev_alloc(h, tile_dom.size() * sizeof(int));
   if (!h->d_tile_dom) return fail(h, PF_ERR_OOM, "tile table allocation failed");
@@ -476,6 +531,10 @@ static pf_status finish_init(pf_handle* h, int dom) {
   DomDesc& dd = h->ddesc[dom];
   const double n = (double)dd.nx * dd.ny;
   dd.rho_bar = h->p.rho_g + (dg.sum_phi / n) * (h->p.rho_l - h->p.rho_g);
+  if (h->any_bc) {
+    pf_status st2 = upload_tables(h);   // the run descriptors carry rho_bar too
+    if (st2 != PF_OK) return st2;
+  }
   PF_CUDA(h, cudaMemcpyAsync(h->d_doms + dom, &dd, sizeof(DomDesc), cudaMemcpyHostToDevice,
                              h->stream));
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -637,7 +696,7 @@ static StepArgs<S, R> make_step_args(const pf_handle* h, const void* pin, const 
   a.plane_stride = h->plane_stride;
   a.grain = h->grain;
   a.grain_cs = h->grain_cs;
-  a.doms = h->d_doms;
+  a.doms = h->any_bc ? h->d_runs : h->d_doms;
   a.tile_dom = h->d_tile_dom;
   a.ntiles = h->ntiles;
   a.chunk = h->chunk;
@@ -655,28 +714,69 @@ static StepArgs<S, R> make_step_args(const pf_handle* h, const void* pin, const 
 // of the device looping over the tiles (persistent).
 template <typename S, typename R>
 static pf_status launch_all(pf_handle* h, StepArgs<S, R> a, cudaStream_t stream) {
-  const int cap = h->persistent
-                      ? std::max(1, h->sms) * step_blocks_per_sm<S, R>(h->variant, h->tx, h->ty,
-                                                                       h->plane_stride,
-                                                                       h->thermal != 0,
-                                                                       h->any_bc != 0)
-                      : 1 << 30;
-  if (h->launch_mode == 0) {
-    a.tile_base = 0;
-    a.ntiles = h->ntiles;
-    PF_CUDA(h, launch_step<S, R>(a, h->variant, h->tx, h->ty, std::min(h->ntiles, cap), stream));
+  auto cap_of = [&](bool bc) {
+    return h->persistent ? std::max(1, h->sms) *
+                               step_blocks_per_sm<S, R>(h->variant, h->tx, h->ty,
+                                                        h->plane_stride, h->thermal != 0, bc)
+                         : 1 << 30;
+  };
+  // one launch over tiles [t0, t1) of the periodic (bc = 0) or boundary-aware kernel
+  auto go = [&](int t0, int t1, int bc, cudaStream_t sx) -> pf_status {
+    if (t1 <= t0) return PF_OK;
+    a.tile_base = t0;
+    a.ntiles = t1;
+    a.bc = bc;
+    PF_CUDA(h, launch_step<S, R>(a, h->variant, h->tx, h->ty, std::min(t1 - t0, cap_of(bc != 0)),
+                                 sx));
     h->launches++;
-  } else {
-    for (size_t d = 0; d < h->ddesc.size(); ++d) {
-      const int t0 = h->ddesc[d].tile0;
-      const int t1 = d + 1 < h->ddesc.size() ? h->ddesc[d + 1].tile0 : h->ntiles;
-      a.tile_base = t0;
-      a.ntiles = t1;
-      PF_CUDA(h, launch_step<S, R>(a, h->variant, h->tx, h->ty, std::min(t1 - t0, cap), stream));
-      h->launches++;
+    return PF_OK;
+  };
+  auto go1 = [&](int t0, int t1, int bc) { return go(t0, t1, bc, stream); };
+  pf_status st = PF_OK;
+  if (h->any_bc) {
+    // plain tiles: the periodic kernel; edge tiles: the boundary-aware one, on
+    // the side stream (both read the same state and write disjoint sites)
+    if (h->launch_mode == 0) {
+      if (h->ntiles > h->n_plain && h->n_plain > 0) {
+        if (!h->side) {
+          PF_CUDA(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+          PF_CUDA(h, cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+          PF_CUDA(h, cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming));
+        }
+        PF_CUDA(h, cudaEventRecord(h->fork_ev, stream));
+        PF_CUDA(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
+        if ((st = go(h->n_plain, h->ntiles, 1, h->side)) != PF_OK) return st;
+        if ((st = go1(0, h->n_plain, 0)) != PF_OK) return st;
+        PF_CUDA(h, cudaEventRecord(h->join_ev, h->side));
+        PF_CUDA(h, cudaStreamWaitEvent(stream, h->join_ev, 0));
+        return PF_OK;
+      }
+      if ((st = go1(0, h->n_plain, 0)) != PF_OK) return st;
+      return go1(h->n_plain, h->ntiles, 1);
     }
+    for (size_t d = 0; d < h->ddesc.size(); ++d) {
+      if ((st = go1(h->plain0[d], h->plain1[d], 0)) != PF_OK) return st;
+      if ((st = go1(h->edge0[d], h->edge1[d], 1)) != PF_OK) return st;
+    }
+    return PF_OK;
+  }
+  if (h->launch_mode == 0) return go1(0, h->ntiles, 0);
+  for (size_t d = 0; d < h->ddesc.size(); ++d) {
+    const int t0 = h->ddesc[d].tile0;
+    const int t1 = d + 1 < h->ddesc.size() ? h->ddesc[d + 1].tile0 : h->ntiles;
+    if ((st = go1(t0, t1, 0)) != PF_OK) return st;
   }
   return PF_OK;
+}
+
+// Kernel launches of one step (the graph replay counts them without launching).
+static int launches_per_step(const pf_handle* h) {
+  if (!h->any_bc) return h->launch_mode == 0 ? 1 : (int)h->ddesc.size();
+  int n = 0;
+  if (h->launch_mode == 0) return (h->n_plain > 0) + (h->ntiles > h->n_plain);
+  for (size_t d = 0; d < h->ddesc.size(); ++d)
+    n += (h->plain1[d] > h->plain0[d]) + (h->edge1[d] > h->edge0[d]);
+  return n;
 }
 
 template <typename S, typename R>
@@ -720,14 +820,14 @@ template <typename S, typename R>
 static pf_status step_n(pf_handle* h, int n_steps) {
   int done = 0;
   if (h->graph_steps > 0) {
-    const int launches_per_step = h->launch_mode == 0 ? 1 : (int)h->ddesc.size();
+    const int per_step = launches_per_step(h);
     while (n_steps - 1 - done >= h->graph_steps) {
       pf_status st = ensure_graph<S, R>(h);
       if (st != PF_OK) return st;
       PF_CUDA(h, cudaGraphLaunch(h->gexec[h->cur], h->stream));
       done += h->graph_steps;
       h->steps += h->graph_steps;
-      h->launches += (long long)h->graph_steps * launches_per_step;
+      h->launches += (long long)h->graph_steps * per_step;
     }
   }
   for (; done < n_steps; ++done) {
