@@ -27,11 +27,12 @@ _BUILD = os.path.join(_HERE, "_build")
 PARAM_NAMES = (
     "rho_l", "rho_g", "nu", "sigma", "W_phi", "M_phi", "beta_phi", "beta_psi",
     "beta_inter", "W0", "tau0", "eps_s", "k", "D", "Omega", "g", "grad_eps",
-    "s_e", "s_eps", "grad_eps_at", "thermal", "Le", "latent", "theta0", "cp",
+    "s_e", "s_eps", "grad_eps_at", "thermal", "Le", "latent", "theta0", "cp", "vin_x", "vin_y",
 )
 # Defaults of the temperature-coupling parameters: isothermal closure
 # (Eq. eq-Tsys), so a parameter dict without them runs the isothermal model.
-THERMAL_DEFAULTS = dict(thermal=0.0, Le=1.0, latent=1.0, theta0=-0.55, cp=10.0)
+THERMAL_DEFAULTS = dict(thermal=0.0, Le=1.0, latent=1.0, theta0=-0.55, cp=10.0, vin_x=0.0,
+                        vin_y=0.0)
 # Field order of or_get_fields.
 FIELDS = ("phi", "psi", "C", "U", "p", "vx", "vy", "mu", "theta")
 N_STATE_PLANES = 39          # isothermal; thermal mode adds e[5] and H_o
@@ -157,7 +158,9 @@ class Oracle:
     def set_bc(self, xm: int, xp: int, ym: int, yp: int) -> None:
         """Boundary types of the sides x-, x+, y-, y+: 0 periodic, 1 symmetric,
         2 wall (half-way bounce-back), 3 far field (wall for the flow and phi,
-        Dirichlet psi = -1, C = 1, theta = theta0).  Set before initialising."""
+        Dirichlet psi = -1, C = 1, theta = theta0), 4 inlet (velocity
+        (vin_x, vin_y), liquid phi = 1, far-field scalars), 5 outlet (zero
+        gradient).  Set before initialising."""
         self.lib.or_set_bc(self.h, int(xm), int(xp), int(ym), int(yp))
 
     def set_rho_bar(self, rho_bar: float) -> None:

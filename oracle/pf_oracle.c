@@ -113,12 +113,15 @@ enum {
    * temperature equation with Lewis number Le = alpha / D, latent-heat factor
    * c_p^s / c_p, uniform initial temperature theta0 and lattice heat capacity
    * c_p (reading R28). */
-  P_THERMAL, P_LE, P_LATENT, P_THETA0, P_CP, NPAR
+  P_THERMAL, P_LE, P_LATENT, P_THETA0, P_CP,
+  /* velocity at an inlet side (reading R32) */
+  P_VIN_X, P_VIN_Y, NPAR
 };
 
 /* Boundary type of each side (reading R31): x- (left), x+ (right), y- (bottom),
  * y+ (top), all at the half-way position between the last site and its ghost. */
-enum { BC_PERIODIC = 0, BC_SYMMETRIC = 1, BC_WALL = 2, BC_FARFIELD = 3 };
+enum { BC_PERIODIC = 0, BC_SYMMETRIC = 1, BC_WALL = 2, BC_FARFIELD = 3, BC_INLET = 4,
+       BC_OUTLET = 5 };
 
 typedef struct {
   int nx, ny, n;
@@ -606,53 +609,68 @@ static const int MIRY[9] = {0, 1, 4, 3, 2, 8, 7, 6, 5};
  * theta = -Omega, here theta0), and U of that state (0). */
 static const double PSI_FAR = -1.0, C_FAR = 1.0;
 
-/* Source of the population of direction i pulled by site (x, y) (reading
- * R31).  Periodic sides wrap; a symmetric side reflects the source site about
- * the half-way plane and the direction with it; a wall or far-field side
- * returns the site's own post-collision population of the opposite direction
- * (half-way bounce-back), which the far-field side turns into an
- * anti-bounce-back on the lattices with a Dirichlet value.  Returns 0 (plain
- * or reflected source), 1 (wall) or 2 (far field); *src and *q give the site
- * and the direction to read. */
+/* Source of the population of direction i pulled by site (x, y) (readings
+ * R31, R32).  Periodic sides wrap; a symmetric side reflects the source site
+ * about the half-way plane and the direction with it; an outlet clamps the
+ * source to the last site (zero gradient; the NS lattice instead takes a
+ * pressure anti-bounce-back, applied by the caller); a wall, far-field or
+ * inlet side returns the site's own post-collision population of the opposite
+ * direction (half-way bounce-back), which the far-field side turns into an
+ * anti-bounce-back on the lattices with a Dirichlet value and the inlet into a
+ * moving-wall bounce-back for the flow and anti-bounce-backs for the scalars.
+ * Returns 0 (plain or reflected source), 1 (wall), 2 (far field), 3 (inlet)
+ * or 4 (outlet, clamped source), a bounce winning over the rest where two
+ * sides are crossed; *src and *q give the site and the direction to read. */
+static int bounce_rank(int t) {
+  return t == BC_WALL ? 1 : (t == BC_FARFIELD ? 2 : (t == BC_INLET ? 3 : 0));
+}
+
 static int pull_src(const ostate *st, int x, int y, int i, int *src, int *q) {
   const int nx = st->nx, ny = st->ny;
-  int sx = x - CX[i], sy = y - CY[i], qi = i, bounce = 0;
+  int sx = x - CX[i], sy = y - CY[i], qi = i, bounce = 0, outlet = 0;
   if (sx < 0 || sx >= nx) {
     const int t = st->bc[sx < 0 ? 0 : 1];
     if (t == BC_PERIODIC) sx = wrap(sx, nx);
     else if (t == BC_SYMMETRIC) { sx = sx < 0 ? -1 - sx : 2 * nx - 1 - sx; qi = MIRX[qi]; }
-    else bounce = t == BC_WALL ? (bounce > 1 ? bounce : 1) : 2;
+    else if (t == BC_OUTLET) { sx = sx < 0 ? 0 : nx - 1; outlet = 1; }
+    else if (bounce_rank(t) > bounce) bounce = bounce_rank(t);
   }
   if (sy < 0 || sy >= ny) {
     const int t = st->bc[sy < 0 ? 2 : 3];
     if (t == BC_PERIODIC) sy = wrap(sy, ny);
     else if (t == BC_SYMMETRIC) { sy = sy < 0 ? -1 - sy : 2 * ny - 1 - sy; qi = MIRY[qi]; }
-    else bounce = t == BC_WALL ? (bounce > 1 ? bounce : 1) : 2;
+    else if (t == BC_OUTLET) { sy = sy < 0 ? 0 : ny - 1; outlet = 1; }
+    else if (bounce_rank(t) > bounce) bounce = bounce_rank(t);
   }
   if (bounce) { *src = y * nx + x; *q = OPP[i]; return bounce; }
   *src = sy * nx + sx;
   *q = qi;
-  return 0;
+  return outlet ? 4 : 0;
 }
 
 /* Kinds of field read on the stencil neighbourhood, for the ghost values. */
 enum { GK_NOFLUX, GK_PSI, GK_U, GK_VX, GK_VY };
 
 /* Ghost value across one non-periodic side of type t on axis a (0: x, 1: y)
- * from the value v at the mirror site (reading R31): zero normal gradient for
- * phi, and for psi and U except at a far-field side, where the ghost is the
- * linear extrapolation 2 X_far - v through the boundary value; the velocity
- * flips its normal component at a symmetric side and both components at a
- * wall or far-field side (no slip). */
-static real_t ghost_map(int t, int axis, int kind, real_t v) {
+ * from the value v at the mirror site (readings R31, R32): zero normal
+ * gradient for phi, and for psi and U except at a far-field side or an inlet,
+ * where the ghost is the linear extrapolation 2 X_far - v through the boundary
+ * value (phi_far = 1 at an inlet); the velocity flips its normal component at
+ * a symmetric side and both components at a wall or far-field side (no slip),
+ * and is extrapolated through the inlet velocity; an outlet copies every
+ * value (zero gradient). */
+static real_t ghost_map(const ostate *st, int t, int axis, int kind, real_t v) {
+  if (t == BC_OUTLET) return v;
   if (kind == GK_VX || kind == GK_VY) {
     const int normal = (kind == GK_VX) == (axis == 0);
     if (t == BC_SYMMETRIC) return normal ? -v : v;
+    if (t == BC_INLET) return 2.0 * st->par[kind == GK_VX ? P_VIN_X : P_VIN_Y] - v;
     return -v;
   }
-  if (t == BC_FARFIELD) {
+  if (t == BC_FARFIELD || t == BC_INLET) {
     if (kind == GK_PSI) return 2.0 * PSI_FAR - v;
     if (kind == GK_U) return -v;                 /* U = 0 at psi = -1, C = 1 */
+    if (kind == GK_NOFLUX && t == BC_INLET) return 2.0 * 1.0 - v;   /* liquid inflow */
   }
   return v;
 }
@@ -673,8 +691,8 @@ static real_t field_at(const ostate *st, const real_t *X, int x, int y, int kind
     else { ty = t; y = y < 0 ? -1 - y : 2 * ny - 1 - y; }
   }
   real_t v = X[y * nx + x];
-  if (ty >= 0) v = ghost_map(ty, 1, kind, v);
-  if (tx >= 0) v = ghost_map(tx, 0, kind, v);
+  if (ty >= 0) v = ghost_map(st, ty, 1, kind, v);
+  if (tx >= 0) v = ghost_map(st, tx, 0, kind, v);
   return v;
 }
 
@@ -692,18 +710,37 @@ static void pass_stream(ostate *st) {
       real_t phi = 0, psi = 0, C = 0, psio = 0;
       int src, q;
       for (int i = 0; i < 9; ++i) {
-        pull_src(st, x, y, i, &src, &q);     /* NS and CAC: bounce-back at walls */
-        st->fS[i][idx] = st->f[q][src];
-        st->hS[i][idx] = st->h[q][src];
+        const int mode = pull_src(st, x, y, i, &src, &q);
+        /* NS and CAC: bounce-back at walls and far-field sides; at an inlet the
+         * moving-wall bounce-back f*_opp + 2 rho_l w_i c_i.u_in / cs2 and the
+         * anti-bounce-back to phi = 1 (reading R32) */
+        if (mode == 3) {
+          const real_t cu = CX[i] * st->par[P_VIN_X] + CY[i] * st->par[P_VIN_Y];
+          st->fS[i][idx] = st->f[q][src] + 2.0 * st->par[P_RHO_L] * W9[i] * cu / CS2;
+          st->hS[i][idx] = -st->h[q][src] + 2.0 * W9[i] * 1.0;
+        } else if (mode == 4) {
+          /* pressure outlet p = 0: anti-bounce-back of the site's own opposite
+           * population plus twice the even part of the equilibrium at p = 0,
+           * with the site's velocity and density of the last step */
+          const real_t ux = st->vx_o[idx], uy = st->vy_o[idx];
+          const real_t rho_o = st->par[P_RHO_G] + st->phi_o[idx] * (st->par[P_RHO_L] - st->par[P_RHO_G]);
+          const real_t cu = CX[i] * ux + CY[i] * uy;
+          st->fS[i][idx] = -st->f[OPP[i]][idx] +
+                           2.0 * rho_o * W9[i] * (cu * cu / (2.0 * CS2 * CS2) - (ux * ux + uy * uy) / (2.0 * CS2));
+          st->hS[i][idx] = st->h[q][src];
+        } else {
+          st->fS[i][idx] = st->f[q][src];
+          st->hS[i][idx] = st->h[q][src];
+        }
         phi += st->hS[i][idx];
       }
       for (int i = 0; i < 5; ++i) {
         const int mode = pull_src(st, x, y, i, &src, &q);
         /* anti-bounce-back to the far-field values: -f*_opp + 2 w_i X_far */
-        st->sS[i][idx] = mode == 2 ? -st->s[q][src] + 2.0 * W5[i] * C_FAR : st->s[q][src];
+        st->sS[i][idx] = (mode == 2 || mode == 3) ? -st->s[q][src] + 2.0 * W5[i] * C_FAR : st->s[q][src];
         C += st->sS[i][idx];
         real_t gold = st->gpre[i][idx];
-        const real_t gsrc = mode == 2 ? -st->gpost[q][src] + 2.0 * W5[i] * PSI_FAR
+        const real_t gsrc = (mode == 2 || mode == 3) ? -st->gpost[q][src] + 2.0 * W5[i] * PSI_FAR
                                       : st->gpost[q][src];
         st->gS[i][idx] = gold + (gsrc - gold) * st->rr[src];
         psi += st->gS[i][idx];
@@ -717,7 +754,7 @@ static void pass_stream(ostate *st) {
        * supersaturation field whose gradient enters grad F(U) */
       for (int i = 0; i < 5; ++i) {
         const int mode = pull_src(st, x, y, i, &src, &q);
-        st->eS[i][idx] = mode == 2 ? -st->e[q][src] + 2.0 * W5[i] * st->par[P_THETA0]
+        st->eS[i][idx] = (mode == 2 || mode == 3) ? -st->e[q][src] + 2.0 * W5[i] * st->par[P_THETA0]
                                    : st->e[q][src];
       }
       st->US[idx] = supersat(st, C, psi);

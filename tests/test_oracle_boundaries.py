@@ -127,3 +127,75 @@ def test_far_field_dirichlet_against_the_diffusion_series():
     assert np.abs(f["C"] - _series(0.5, 1.0, p["D"], 1000, ny, yw)[:, None]).max() < 2e-4
     assert np.abs(f["theta"] - _series(-0.3, -0.55, p["D"], 1000, ny, yw)[:, None]).max() < 2e-3
     assert np.abs(f["psi"] + 1).max() < 1e-14
+
+
+INLET, OUTLET = 4, 5
+
+
+def test_plug_flow_through_inlet_and_outlet_is_exact():
+    """A uniform liquid inflow through a channel with symmetric sides is an
+    exact steady state of the inlet (moving-wall bounce-back at u_in) and the
+    pressure outlet (p = 0): velocity, pressure and the scalars stay uniform."""
+    nx, ny, vin = 8, 40, 0.01
+    p = dict(wl.BASE_PARAMS, g=0.0, vin_y=vin)
+    one = np.ones((ny, nx))
+    o = oracle.Oracle(nx, ny, p)
+    o.set_bc(SYMMETRIC, SYMMETRIC, INLET, OUTLET)
+    o.init_fields(one, -one, one, 0 * one, vin * one, 0 * one)
+    o.step(400)
+    f = o.fields(("vx", "vy", "p", "phi", "C", "psi"))
+    assert np.abs(f["vy"] / vin - 1).max() < 1e-12
+    assert np.abs(f["vx"]).max() < 1e-15 and np.abs(f["p"]).max() < 1e-14
+    for k, v in (("phi", 1.0), ("C", 1.0), ("psi", -1.0)):
+        assert np.abs(f[k] - v).max() < 1e-14, k
+
+
+def test_inflow_between_walls_develops_the_poiseuille_profile():
+    """Inflow at u_in between two no-slip walls (width W) relaxes downstream to
+    the plane Poiseuille profile 6 u_in xi (1 - xi), xi = (x + 1/2) / W, and
+    the volume flux W u_in is the same through every row."""
+    W, L, vin = 16, 96, 0.01
+    p = dict(wl.BASE_PARAMS, g=0.0, vin_y=vin)
+    one = np.ones((L, W))
+    o = oracle.Oracle(W, L, p)
+    o.set_bc(WALL, WALL, INLET, OUTLET)
+    o.init_fields(one, -one, one, 0 * one, 0 * one, 0 * one)
+    o.step(6000)
+    f = o.fields(("vx", "vy"))
+    xi = (np.arange(W) + 0.5) / W
+    assert np.abs(f["vy"][L - 20] - 6 * vin * xi * (1 - xi)).max() < 5e-3 * 1.5 * vin
+    flux = f["vy"].sum(axis=1) / (W * vin)
+    assert np.abs(flux - 1).max() < 1e-3
+    assert np.abs(f["vx"][L - 20]).max() < 1e-3 * vin
+
+
+def _forced_convection(vin, T=2500):
+    nx, ny = 64, 128
+    p = dict(wl.BASE_PARAMS, g=0.0, vin_y=vin)
+    cx, cy = -0.5, ny / 2          # seed centred on the symmetry plane x = -1/2
+    o = oracle.Oracle(nx, ny, p)
+    o.set_bc(SYMMETRIC, SYMMETRIC, INLET, OUTLET)
+    phi, psi, C = o.fields_from_spec([(cx, cy, 0.0)], 6.0, [])
+    o.set_orientation([(cx, cy, 0.0)])
+    o.init_fields(phi, psi, C, 0 * phi, vin * (1 - 0.5 * (1 + psi)), 0 * phi)
+    o.step(T)
+    f = o.fields(("psi",))["psi"]
+
+    def arm(arr, start, step):        # distance to the psi = 0 crossing
+        i = start
+        while 0 <= i + step < len(arr) and arr[i + step] > 0:
+            i += step
+        a, b = arr[i], arr[i + step]
+        return abs(i - start) + a / (a - b)
+    col, row = f[:, 0], f[int(cy), :]
+    return arm(col, int(cy), -1), arm(col, int(cy), +1), arm(row, 0, +1)
+
+
+def test_forced_convection_favours_the_upstream_arm():
+    """Section 3.3 (dendritic growth with an inlet velocity): the arm growing
+    against the flow is longer than the normal and the downstream arms.  The
+    same growth without inflow is symmetric between up and down."""
+    up, down, normal = _forced_convection(0.025)
+    assert up > down + 0.3 and up > normal + 0.5
+    up0, down0, normal0 = _forced_convection(0.0)
+    assert abs(up0 - down0) < 0.05
