@@ -80,6 +80,7 @@ typedef enum {
  *  thermal        0: isothermal closure theta = theta_sys, F = 1 (Eq. eq-Tsys);
  *                 1: temperature lattice (FP32 / FP64 storage, y-march
  *                 traversal; no adjoint)
+ *  vin_x, vin_y   velocity at an inlet side (PF_BC_INLET)
  *  reserved       must be 0 */
 typedef struct pf_params {
   double rho_l, rho_g, nu, sigma, W_phi, M_phi;
@@ -87,6 +88,7 @@ typedef struct pf_params {
   double W0, tau0, eps_s, k, D, Omega, g;
   double grad_eps, grad_eps_at, s_e, s_eps;
   double Le, latent, theta0, cp;
+  double vin_x, vin_y;
   int thermal, reserved;
 } pf_params;
 
@@ -321,8 +323,12 @@ enum {
   PF_BC_PERIODIC = 0,   /* wraps to the opposite side (which must be periodic too)   */
   PF_BC_SYMMETRIC = 1,  /* mirror plane: populations reflected, normal velocity flipped */
   PF_BC_WALL = 2,       /* half-way bounce-back on every lattice: no slip, no flux     */
-  PF_BC_FARFIELD = 3    /* bounce-back for the flow and phi; Dirichlet psi = -1, C = 1,
+  PF_BC_FARFIELD = 3,   /* bounce-back for the flow and phi; Dirichlet psi = -1, C = 1,
                            theta = theta0 by anti-bounce-back                         */
+  PF_BC_INLET = 4,      /* velocity (vin_x, vin_y) by moving-wall bounce-back; liquid
+                           phi = 1 and the far-field psi, C, theta by anti-bounce-back */
+  PF_BC_OUTLET = 5      /* pressure p = 0 for the flow (anti-bounce-back); zero gradient
+                           for phi, psi, C, theta                                       */
 };
 
 /* Boundary types of domain dom's sides, bc = {x-, x+, y-, y+}, before

@@ -184,6 +184,8 @@ static KParams<R> make_kparams(const pf_params& p) {
   k.s_q = (R)(8.0 * (2.0 - s_nu) / (8.0 - s_nu));
   k.s_nu = (R)s_nu;
   k.s_phi = (R)(1.0 / (3.0 * p.M_phi + 0.5));
+  k.vin_x = (R)p.vin_x;
+  k.vin_y = (R)p.vin_y;
   // temperature coupling: alpha = k_T / (rho_l c_p) = Le D, k_T = (1/s - 1/2) / 3
   if (p.thermal) {
     const double kT = p.Le * p.D * p.rho_l * p.cp;
@@ -207,7 +209,8 @@ static pf_status check_params(const pf_params* p) {
       !finite_pos(p->beta_psi) || !std::isfinite(p->beta_inter) || !std::isfinite(p->sigma) ||
       !std::isfinite(p->g) || !std::isfinite(p->Omega) || !std::isfinite(p->eps_s) ||
       !finite_pos(p->grad_eps) || !finite_pos(p->grad_eps_at) || !finite_pos(p->s_e) ||
-      !finite_pos(p->s_eps) || p->s_e >= 2.0 || p->s_eps >= 2.0)
+      !finite_pos(p->s_eps) || p->s_e >= 2.0 || p->s_eps >= 2.0 || !std::isfinite(p->vin_x) ||
+      !std::isfinite(p->vin_y))
     return fail(nullptr, PF_ERR_BAD_ARG, "a parameter is non-finite or out of range");
   if (!(p->k > 0.0 && p->k < 1.0)) return fail(nullptr, PF_ERR_BAD_ARG, "k must be in (0, 1)");
   // a_s >= 1 - eps > 0 needs eps < 1; beyond 1/15 the interface stiffness
@@ -1117,8 +1120,8 @@ extern "C" pf_status pf_set_boundaries(pf_handle* h, int dom, const int bc[4]) {
   if (dom < 0 || dom >= (int)h->doms.size() || !bc)
     return fail(h, PF_ERR_BAD_ARG, "bad domain index or NULL bc");
   for (int k = 0; k < 4; ++k)
-    if (bc[k] < PF_BC_PERIODIC || bc[k] > PF_BC_FARFIELD)
-      return fail(h, PF_ERR_BAD_ARG, "boundary types are 0 (periodic) .. 3 (far field)");
+    if (bc[k] < PF_BC_PERIODIC || bc[k] > PF_BC_OUTLET)
+      return fail(h, PF_ERR_BAD_ARG, "boundary types are 0 (periodic) .. 5 (outlet)");
   if ((bc[0] == PF_BC_PERIODIC) != (bc[1] == PF_BC_PERIODIC) ||
       (bc[2] == PF_BC_PERIODIC) != (bc[3] == PF_BC_PERIODIC))
     return fail(h, PF_ERR_BAD_ARG, "a periodic side needs a periodic opposite side");

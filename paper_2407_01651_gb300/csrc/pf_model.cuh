@@ -59,7 +59,11 @@ enum Field : int { FLD_PHI, FLD_PSI, FLD_C, FLD_U, FLD_P, FLD_VX, FLD_VY, FLD_MU
 // mirrored); wall (half-way bounce-back: no slip, no flux); far field (wall
 // for the flow and phi, Dirichlet psi = -1, C = 1, theta = theta0 by
 // anti-bounce-back).
-enum BoundaryType : int { BC_PERIODIC = 0, BC_SYMMETRIC = 1, BC_WALL = 2, BC_FARFIELD = 3 };
+// Inlet: velocity u_in by moving-wall bounce-back, liquid phi = 1 and the far
+// field for psi, C, theta; outlet: pressure p = 0 for the flow, zero gradient
+// for the rest.
+enum BoundaryType : int { BC_PERIODIC = 0, BC_SYMMETRIC = 1, BC_WALL = 2, BC_FARFIELD = 3,
+                          BC_INLET = 4, BC_OUTLET = 5 };
 
 struct DomDesc {
   long long off;      // first site of the domain in every plane
@@ -94,6 +98,7 @@ struct KParams {
   R th_dF;                  // M c_inf (1 - k): grad F = th_dF grad U
   R W0sq;                   // W0^2
   R th_far;                 // theta at a far-field side (theta0)
+  R vin_x, vin_y;           // velocity at an inlet side
 };
 
 // ---------------------------------------------------------------------------

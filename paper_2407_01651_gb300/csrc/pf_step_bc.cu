@@ -8,13 +8,17 @@
 //   - pull streaming: a symmetric side reflects the source site and the
 //     direction; a wall returns the site's own post-collision population of
 //     the opposite direction; a far-field side does the same for NS and CAC
-//     and an anti-bounce-back -f*_opp + 2 w_i X_far for psi, C and theta; a
-//     diagonal source beyond both a reflecting and a bouncing side bounces;
+//     and an anti-bounce-back -f*_opp + 2 w_i X_far for psi, C and theta; an
+//     inlet adds the moving-wall term 2 rho_l w_i c_i.u_in / c_s^2 for NS and
+//     anti-bounces CAC to phi = 1; an outlet anti-bounces NS to p = 0 and
+//     clamps the other lattices' source to the last site; a bounce wins where
+//     two sides are crossed, then the clamp, then the reflection;
 //   - stencils: ghost rows and columns of the shared-memory ring hold the
 //     mirror site's values mapped per side (phi, psi, U unchanged, or
-//     2 X_far - X for psi and U at a far-field side; the velocity's normal
-//     component flipped at a symmetric side, both components at a wall or far
-//     field; corners: the y side's map, then the x side's).
+//     2 X_far - X for psi and U at a far-field side or inlet, 2 - phi at an
+//     inlet; the velocity's normal component flipped at a symmetric side, both
+//     components at a wall or far field, 2 u_in - v at an inlet; everything
+//     copied at an outlet; corners: the y side's map, then the x side's).
 // Sites away from a non-periodic side take the periodic pulls of pf_pull.cuh.
 // FP32 and FP64 storage only.
 #include "pf_site.cuh"
@@ -51,28 +55,34 @@ __device__ __forceinline__ unsigned site_at(const DomDesc& d, int x, int y) {
 }
 
 // Source of the population of direction i pulled by (x, y): site, direction
-// to read and mode (0 plain or reflected, 1 wall bounce, 2 far-field bounce).
+// to read and mode (0 plain or reflected, 1 wall bounce, 2 far-field bounce,
+// 3 inlet bounce, 4 outlet: source clamped to the last site).
 struct PullSrc {
   unsigned site;
   int q, mode;
 };
+__device__ __forceinline__ int bounce_rank(int t) {
+  return t == BC_WALL ? 1 : (t == BC_FARFIELD ? 2 : (t == BC_INLET ? 3 : 0));
+}
 __device__ __forceinline__ PullSrc pull_src(const DomDesc& d, int x, int y, int i) {
   const int nx = d.nx, ny = d.ny;
-  int sx = x - cx9(i), sy = y - cy9(i), q = i, bounce = 0;
+  int sx = x - cx9(i), sy = y - cy9(i), q = i, bounce = 0, outlet = 0;
   if (sx < 0 || sx >= nx) {
     const int t = d.bc[sx < 0 ? 0 : 1];
     if (t == BC_PERIODIC) sx += sx < 0 ? nx : -nx;
     else if (t == BC_SYMMETRIC) { sx = sx < 0 ? -1 - sx : 2 * nx - 1 - sx; q = mirx9(q); }
-    else bounce = t == BC_WALL ? 1 : 2;
+    else if (t == BC_OUTLET) { sx = sx < 0 ? 0 : nx - 1; outlet = 1; }
+    else bounce = bounce_rank(t);
   }
   if (sy < 0 || sy >= ny) {
     const int t = d.bc[sy < 0 ? 2 : 3];
     if (t == BC_PERIODIC) sy += sy < 0 ? ny : -ny;
     else if (t == BC_SYMMETRIC) { sy = sy < 0 ? -1 - sy : 2 * ny - 1 - sy; q = miry9(q); }
-    else bounce = (t == BC_WALL && bounce < 2) ? 1 : 2;
+    else if (t == BC_OUTLET) { sy = sy < 0 ? 0 : ny - 1; outlet = 1; }
+    else bounce = max(bounce, bounce_rank(t));
   }
   if (bounce) return {site_at(d, x, y), opp9(i), bounce};
-  return {site_at(d, sx, sy), q, 0};
+  return {site_at(d, sx, sy), q, outlet ? 4 : 0};
 }
 
 // A pull source of (x, y) lies beyond a non-periodic side.
@@ -84,15 +94,18 @@ __device__ __forceinline__ bool near_side(const DomDesc& d, int x, int y) {
 // Ring fields: 0 phi, 1 psi, 2 vx_o, 3 vy_o, 4 U.  Ghost value across one side
 // of type t on axis (0: x, 1: y) from the mirror site's value v.
 template <typename R>
-__device__ __forceinline__ R ghost_map(int t, int axis, int field, R v) {
+__device__ __forceinline__ R ghost_map(const KParams<R>& kp, int t, int axis, int field, R v) {
+  if (t == BC_OUTLET) return v;
   if (field == 2 || field == 3) {
     const bool normal = (field == 2) == (axis == 0);
     if (t == BC_SYMMETRIC) return normal ? -v : v;
+    if (t == BC_INLET) return R(2) * (field == 2 ? kp.vin_x : kp.vin_y) - v;
     return -v;
   }
-  if (t == BC_FARFIELD) {
+  if (t == BC_FARFIELD || t == BC_INLET) {
     if (field == 1) return R(-2) - v;   // 2 psi_far - psi, psi_far = -1
     if (field == 4) return -v;          // 2 U_far - U, U_far = 0
+    if (field == 0 && t == BC_INLET) return R(2) - v;   // liquid inflow, phi = 1
   }
   return v;
 }
@@ -106,7 +119,9 @@ __device__ __forceinline__ void pull_hg_b(const StepArgs<S, R>& a, const DomDesc
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     const PullSrc p = pull_src(d, x, y, i);
-    h[i] = ld<R>(pbase<BIG>(a.in, P_H + p.q, ps), pidx<BIG>(P_H + p.q, ps, p.site));
+    R v = ld<R>(pbase<BIG>(a.in, P_H + p.q, ps), pidx<BIG>(P_H + p.q, ps, p.site));
+    if (p.mode == 3) v = -v + R(2) * w9<R>(i) * R(1);   // inlet: phi = 1
+    h[i] = v;
     sh.add(h[i]);
   }
   phi = sh.value();
@@ -117,7 +132,7 @@ __device__ __forceinline__ void pull_hg_b(const StepArgs<S, R>& a, const DomDesc
     const PullSrc p = pull_src(d, x, y, i);
     const R gold = ld<R>(pbase<BIG>(a.in, P_GPRE + i, ps), pidx<BIG>(P_GPRE + i, ps, own));
     R gpo = ld<R>(pbase<BIG>(a.in, P_GPOST + p.q, ps), pidx<BIG>(P_GPOST + p.q, ps, p.site));
-    if (p.mode == 2) gpo = -gpo + R(2) * w5<R>(i) * R(-1);
+    if (p.mode == 2 || p.mode == 3) gpo = -gpo + R(2) * w5<R>(i) * R(-1);
     const R rr = ld<R>(pbase<BIG>(a.ain, A_RR, ps), pidx<BIG>(A_RR, ps, p.site));
     g[i] = gold + (gpo - gold) * rr;
     sg.add(g[i]);
@@ -132,24 +147,38 @@ __device__ __forceinline__ void load_site_b(const StepArgs<S, R>& a, const DomDe
                                             int y, SiteIn<R>& in) {
   const unsigned ps = (unsigned)a.plane_stride;
   const unsigned own = site_at(d, x, y);
+  in.phio = ld<R>(pbase<BIG>(a.ain, A_PHIO, ps), pidx<BIG>(A_PHIO, ps, own));
+  const R vxo = ld<R>(pbase<BIG>(a.ain, A_VXO, ps), pidx<BIG>(A_VXO, ps, own));
+  const R vyo = ld<R>(pbase<BIG>(a.ain, A_VYO, ps), pidx<BIG>(A_VYO, ps, own));
+  const R rho_o = a.kp.rho_g + in.phio * a.kp.drho;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     const PullSrc p = pull_src(d, x, y, i);
-    in.f[i] = ld<R>(pbase<BIG>(a.in, P_F + p.q, ps), pidx<BIG>(P_F + p.q, ps, p.site));
+    if (p.mode == 4) {
+      // pressure outlet p = 0: -f*_opp(own) + 2 rho_o w_i [(c.v_o)^2 / (2 cs^4) - v_o^2 / (2 cs^2)]
+      const R fo = ld<R>(pbase<BIG>(a.in, P_F + opp9(i), ps), pidx<BIG>(P_F + opp9(i), ps, own));
+      const R cu = R(cx9(i)) * vxo + R(cy9(i)) * vyo;
+      in.f[i] = -fo + R(2) * rho_o * w9<R>(i) * (R(4.5) * cu * cu - R(1.5) * (vxo * vxo + vyo * vyo));
+    } else {
+      R v = ld<R>(pbase<BIG>(a.in, P_F + p.q, ps), pidx<BIG>(P_F + p.q, ps, p.site));
+      if (p.mode == 3)   // inlet: moving-wall bounce-back
+        v += R(2) * (a.kp.rho_g + a.kp.drho) * w9<R>(i) * R(3) *
+             (R(cx9(i)) * a.kp.vin_x + R(cy9(i)) * a.kp.vin_y);
+      in.f[i] = v;
+    }
   }
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
     const PullSrc p = pull_src(d, x, y, i);
     R v = ld<R>(pbase<BIG>(a.in, P_S + p.q, ps), pidx<BIG>(P_S + p.q, ps, p.site));
-    if (p.mode == 2) v = -v + R(2) * w5<R>(i) * R(1);          // C_far = 1
+    if (p.mode == 2 || p.mode == 3) v = -v + R(2) * w5<R>(i) * R(1);   // C_far = 1
     in.s[i] = v;
     if constexpr (TH) {
       R e = ld<R>(pbase<BIG>(a.in, P_E + p.q, ps), pidx<BIG>(P_E + p.q, ps, p.site));
-      if (p.mode == 2) e = -e + R(2) * w5<R>(i) * a.kp.th_far;
+      if (p.mode == 2 || p.mode == 3) e = -e + R(2) * w5<R>(i) * a.kp.th_far;
       in.e[i] = e;
     }
   }
-  in.phio = ld<R>(pbase<BIG>(a.ain, A_PHIO, ps), pidx<BIG>(A_PHIO, ps, own));
   in.Co = ld<R>(pbase<BIG>(a.ain, A_CO, ps), pidx<BIG>(A_CO, ps, own));
   in.Qo = ld<R>(pbase<BIG>(a.ain, A_QO, ps), pidx<BIG>(A_QO, ps, own));
   in.gid = a.grain[own];
@@ -165,7 +194,7 @@ __device__ __forceinline__ R pull_U_b(const StepArgs<S, R>& a, const DomDesc& d,
   for (int i = 0; i < 5; ++i) {
     const PullSrc p = pull_src(d, x, y, i);
     R v = ld<R>(pbase<BIG>(a.in, P_S + p.q, ps), pidx<BIG>(P_S + p.q, ps, p.site));
-    if (p.mode == 2) v = -v + R(2) * w5<R>(i) * R(1);
+    if (p.mode == 2 || p.mode == 3) v = -v + R(2) * w5<R>(i) * R(1);
     cs.add(v);
   }
   const R C = cs.value();
@@ -233,8 +262,8 @@ __global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 3 : 2)
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         R u = v[f];
-        if (ty >= 0) u = ghost_map<R>(ty, 1, f, u);
-        if (tx >= 0) u = ghost_map<R>(tx, 0, f, u);
+        if (ty >= 0) u = ghost_map<R>(a.kp, ty, 1, f, u);
+        if (tx >= 0) u = ghost_map<R>(a.kp, tx, 0, f, u);
         ring[f][yr & 3][sc] = u;
       }
     };

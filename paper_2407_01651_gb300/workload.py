@@ -27,6 +27,8 @@ BASE_PARAMS = dict(
     grad_eps_at=1e-2, s_e=1.0, s_eps=1.0,
     # temperature coupling off: the isothermal closure theta = theta_sys, F = 1
     thermal=0, Le=1.0, latent=1.0, theta0=-0.55, cp=10.0,
+    # velocity at an inlet side (forced convection)
+    vin_x=0.0, vin_y=0.0,
 )
 # Thermosolutal variant (Section 4 of the paper: Le = 50, c_p^s / c_p = 1,
 # initial temperature -Omega); c_p is the lattice heat capacity.

@@ -14,6 +14,7 @@ from paper_2407_01651_gb300 import workload as wl
 pytestmark = pytest.mark.gpu
 
 P, S, W, F = pf.BC_PERIODIC, pf.BC_SYMMETRIC, pf.BC_WALL, pf.BC_FARFIELD
+I, O = pf.BC_INLET, pf.BC_OUTLET
 FIELDS = ("phi", "psi", "C", "U", "p", "vx", "vy", "mu", "theta")
 FLOOR = {"phi": 1e-9, "psi": 1e-9, "C": 1e-9, "U": 1e-9, "p": 1e-12, "vx": 1e-10,
          "vy": 1e-10, "mu": 1e-3, "theta": 1e-9}
@@ -143,7 +144,7 @@ def test_boundary_configuration_errors():
         sim.set_boundaries(0, P, W, P, P)             # unpaired periodic side
     assert e.value.code == pf.PF_ERR_BAD_ARG
     with pytest.raises(pf.PFError):
-        sim.set_boundaries(0, 4, 4, P, P)             # unknown type
+        sim.set_boundaries(0, 6, 6, P, P)             # unknown type
     sim.set_boundaries(0, S, S, W, F)
     for variant in (0, 2):
         with pytest.raises(pf.PFError):
@@ -157,3 +158,58 @@ def test_boundary_configuration_errors():
     s16 = pf.Simulation([(32, 32)], lay.params, "fp16")
     with pytest.raises(pf.PFError):
         s16.set_boundaries(0, W, W, W, W)
+
+
+@pytest.mark.parametrize("bc,vin", [((S, S, I, O), (0.0, 0.01)), ((W, W, I, O), (0.0, 0.02)),
+                                    ((I, O, S, W), (0.015, 0.0)), ((O, I, P, P), (-0.01, 0.0))])
+def test_inlet_outlet_match_oracle(bc, vin):
+    """Inlet (moving-wall bounce-back at u_in) and pressure outlet (reading R32)
+    in several arrangements, with seeds and bubbles, FP64 over 6 steps and
+    FP32 for one."""
+    lay = layout()
+    par = dict(lay.params, g=1e-5, vin_x=vin[0], vin_y=vin[1])
+    o, sim = pair(lay, bc, "fp64", par)
+    for _ in range(6):
+        o.step(1)
+        sim.step(1)
+        compare(o, sim, 1e-11, early=True)
+    o32, s32 = pair(lay, bc, "fp32", par)
+    o32.step(1)
+    s32.step(1)
+    compare(o32, s32, 1e-5, early=True)
+
+
+def test_inlet_outlet_thermal_matches_oracle():
+    lay = layout()
+    par = {**lay.params, **wl.THERMAL_PARAMS, "Le": 2.0, "g": 0.0, "vin_y": 0.0125}
+    o, sim = pair(lay, (S, S, I, O), "fp64", par)
+    o.step(30)
+    sim.step(30)
+    compare(o, sim, 1e-10)
+
+
+def test_forced_convection_upstream_arm_on_the_gpu():
+    """Section 3.3 at a larger size on the CUDA path (FP32): a seed on the
+    symmetry plane in a melt flowing in from the bottom grows its upstream arm
+    longer than its downstream and normal arms."""
+    nx, ny, vin = 128, 256, 0.0125
+    par = dict(wl.BASE_PARAMS, g=0.0, vin_y=vin)
+    cx, cy = -0.5, ny / 2
+    o = oracle.Oracle(nx, ny, par)
+    o.set_bc(S, S, I, O)
+    phi, psi, C = o.fields_from_spec([(cx, cy, 0.0)], 6.0, [])
+    sim = pf.Simulation([(nx, ny)], par, "fp32")
+    sim.set_boundaries(0, S, S, I, O)
+    sim.set_fields(0, phi, psi, C, 0 * phi, vin * (1 - 0.5 * (1 + psi)), 0 * phi)
+    sim.step(6000)
+    f = sim.fields(0, ("psi",))["psi"]
+
+    def arm(arr, start, step):
+        i = start
+        while 0 <= i + step < len(arr) and arr[i + step] > 0:
+            i += step
+        a, b = arr[i], arr[i + step]
+        return abs(i - start) + a / (a - b)
+    up, down = arm(f[:, 0], int(cy), -1), arm(f[:, 0], int(cy), +1)
+    normal = arm(f[int(cy), :], 0, +1)
+    assert up > down + 0.5 and up > normal + 0.5, (up, down, normal)
