@@ -41,18 +41,21 @@ _lock = threading.Lock()
 _libs: dict[str, ctypes.CDLL] = {}
 
 
+_SRC3 = os.path.join(_HERE, "pf_oracle3d.c")
+
+
 def build(force: bool = False) -> None:
-    """Compile both oracle builds with gcc (no fast-math, no FMA contraction,
-    OpenMP over lattice rows)."""
+    """Compile both oracle builds and the 3-D oracle with gcc (no fast-math,
+    no FMA contraction, OpenMP over lattice rows)."""
     os.makedirs(_BUILD, exist_ok=True)
-    for tag, extra in (("d", []), ("z", ["-DPF_ORACLE_Z"])):
+    for tag, extra, src in (("d", [], _SRC), ("z", ["-DPF_ORACLE_Z"], _SRC), ("3d", [], _SRC3)):
         out = os.path.join(_BUILD, f"liboracle_{tag}.so")
         if (not force and os.path.exists(out)
-                and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+                and os.path.getmtime(out) >= os.path.getmtime(src)):
             continue
         tmp = out + f".tmp{os.getpid()}"
         cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fopenmp",
-               "-ffp-contract=off", *extra, _SRC, "-o", tmp, "-lm"]
+               "-ffp-contract=off", *extra, src, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, out)
 
@@ -320,4 +323,97 @@ def stencil(X, x, y):
     ny, nx = X.shape
     out = np.zeros(3)
     _lib("d").or_stencil(_dp(X), nx, ny, int(x), int(y), _dp(out))
+    return out
+
+
+# -- the three-dimensional dendrite oracle (pf_oracle3d.c) ---------------------
+PARAM_NAMES_3D = ("beta_psi", "W0", "tau0", "eps_s", "k", "D", "Omega", "grad_eps",
+                  "grad_eps_at")
+_lib3 = None
+
+
+def _l3() -> ctypes.CDLL:
+    global _lib3
+    with _lock:
+        if _lib3 is None:
+            build()
+            lib = ctypes.CDLL(os.path.join(_BUILD, "liboracle_3d.so"))
+            P, D, I = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+            lib.or3_new.restype = P
+            lib.or3_new.argtypes = [I, I, I]
+            lib.or3_free.argtypes = [P]
+            lib.or3_set_params.argtypes = [P, D]
+            lib.or3_init.argtypes = [P, D, I, ctypes.c_double]
+            lib.or3_init_fields.argtypes = [P, D, D]
+            lib.or3_step.argtypes = [P, I]
+            lib.or3_fields.argtypes = [P, D]
+            lib.or3_state.argtypes = [P, D]
+            lib.or3_aniso.argtypes = [D, ctypes.c_double, ctypes.c_double, D]
+            lib.or3_collide7.argtypes = [D] * 6
+            lib.or3_grad.argtypes = [D, I, I, I, I, I, I, D]
+            _lib3 = lib
+    return _lib3
+
+
+class Oracle3D:
+    """Periodic nx x ny x nz lattice of the 3-D dendrite model (psi and C on
+    D3Q7, no gas, no flow).  Arrays are [z][y][x]."""
+
+    def __init__(self, nx: int, ny: int, nz: int, params: dict):
+        self.lib = _l3()
+        self.shape = (int(nz), int(ny), int(nx))
+        self.h = self.lib.or3_new(int(nx), int(ny), int(nz))
+        if not self.h:
+            raise MemoryError("oracle allocation failed")
+        pv = _f64([float(params[k]) for k in PARAM_NAMES_3D])
+        self.lib.or3_set_params(self.h, _dp(pv))
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.lib.or3_free(h)
+            self.h = None
+
+    def init_spec(self, seeds, R_s: float) -> None:
+        s = np.ascontiguousarray(_f64(seeds).reshape(-1, 3))
+        self.lib.or3_init(self.h, _dp(s), len(s), float(R_s))
+
+    def init_fields(self, psi, C) -> None:
+        self._keep = [_f64(psi).ravel(), _f64(C).ravel()]
+        self.lib.or3_init_fields(self.h, *[_dp(a) for a in self._keep])
+
+    def step(self, n: int = 1) -> None:
+        self.lib.or3_step(self.h, int(n))
+
+    def fields(self) -> dict:
+        out = np.empty(3 * int(np.prod(self.shape)))
+        self.lib.or3_fields(self.h, _dp(out))
+        out = out.reshape((3,) + self.shape)
+        return {"psi": out[0], "C": out[1], "U": out[2]}
+
+    def state(self) -> np.ndarray:
+        out = np.empty(23 * int(np.prod(self.shape)))
+        self.lib.or3_state(self.h, _dp(out))
+        return out.reshape((23,) + self.shape)
+
+
+def aniso3(g, eps, geps=1e-3):
+    out = np.zeros(5)
+    gg = _f64(g)
+    _l3().or3_aniso(_dp(gg), float(eps), float(geps), _dp(out))
+    return out
+
+
+def collide7(f, feq, S, G, Fd):
+    args = [_f64(a) for a in (f, feq, S, G, Fd)]
+    out = np.zeros(7)
+    _l3().or3_collide7(*[_dp(a) for a in args], _dp(out))
+    return out
+
+
+def grad3(X, x, y, z):
+    X = _f64(X)
+    nz, ny, nx = X.shape
+    out = np.zeros(3)
+    _l3().or3_grad(_dp(X), nx, ny, nz, int(x), int(y), int(z), _dp(out))
     return out
