@@ -360,6 +360,49 @@ pf_status pf_set_temperature(pf_handle *h, int dom, const double *theta, size_t 
  * out[2] = sum psi.  Synchronises the stream.  Errors: BAD_ARG, CUDA. */
 pf_status pf_reduce_thermal(pf_handle *h, int dom, double out[3]);
 
+/* ------------------------------------------------------------------------
+ * Three-dimensional dendrite step (Section 2.1 with the anisotropy summed over
+ * three axes): psi (anisotropic Allen-Cahn with the a_s^2 time stretch of
+ * Appendix B) and C (solute with antitrapping) on D3Q7 lattices (w0 = 1/4,
+ * wi = 1/8, c_s^2 = 1/4) in a periodic melt without gas or flow, one grain
+ * orientation aligned with the lattice.  Arrays are [z][y][x], x fastest.
+ * Uses rho and flow parameters of pf_params not at all; thermal must be 0.
+ * ------------------------------------------------------------------------ */
+typedef struct pf3_handle pf3_handle;
+
+/* Raw FP64 state planes of pf3_get_state: g_pre[7], g_post[7], r = 1/a_s^2,
+ * s[7], Q_psi of the last step. */
+#define PF3_STATE_PLANES 23
+
+/* Handle of an nx x ny x nz lattice (each in [4, 4096]), FP32 or FP64
+ * storage, on cuda_stream; allocates two state copies (23 planes each) and
+ * 3 field planes.  Errors: BAD_ARG, OOM. */
+pf_status pf3_create(const pf_params *p, int nx, int ny, int nz, pf_precision prec,
+                     void *cuda_stream, pf3_handle **out);
+/* Spherical seeds n x (x, y, z) of radius R_s: psi = max tanh(sqrt(2 beta_psi)
+ * (R_s - r) / W0), C = 1 - (1-k) h(psi), populations at equilibrium.
+ * Synchronises.  Errors: BAD_ARG, OOM, CUDA. */
+pf_status pf3_init_seeds(pf3_handle *h, const double *seeds, int n_seeds, double R_s);
+/* Initial psi and C fields (host, n = nx*ny*nz each).  Synchronises. */
+pf_status pf3_set_fields(pf3_handle *h, const double *psi, const double *C, size_t n);
+/* Planes per tile of the z-march (default 16). */
+pf_status pf3_set_chunk(pf3_handle *h, int chunk);
+/* Advance n_steps (enqueued; errors of the launch are reported).
+ * Errors: BAD_ARG, STATE, CUDA. */
+pf_status pf3_step(pf3_handle *h, int n_steps);
+/* psi, C, U of the last step (3 planes of n).  Synchronises. */
+pf_status pf3_get_fields(pf3_handle *h, double *out, size_t n);
+/* Raw state (PF3_STATE_PLANES planes of n).  Synchronises. */
+pf_status pf3_get_state(pf3_handle *h, double *out, size_t n);
+/* FP64 totals: out[0] = sum C (conserved), out[1] = sum h(psi).  Synchronises. */
+pf_status pf3_reduce(pf3_handle *h, double out[2]);
+/* Kernel launches of the handle; -1 for NULL. */
+long long pf3_launch_count(const pf3_handle *h);
+/* Last error of the handle, or of the last failed pf3_create for NULL. */
+const char *pf3_last_error(const pf3_handle *h);
+/* Release the handle (NULL is ignored). */
+pf_status pf3_destroy(pf3_handle *h);
+
 /* Release every resource of the handle (NULL is ignored). */
 pf_status pf_destroy(pf_handle *h);
 

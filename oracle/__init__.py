@@ -351,6 +351,7 @@ def _l3() -> ctypes.CDLL:
             lib.or3_aniso.argtypes = [D, ctypes.c_double, ctypes.c_double, D]
             lib.or3_collide7.argtypes = [D] * 6
             lib.or3_grad.argtypes = [D, I, I, I, I, I, I, D]
+            lib.or3_set_window.argtypes = [P, I, I, I, I, I, I]
             _lib3 = lib
     return _lib3
 
@@ -359,7 +360,7 @@ class Oracle3D:
     """Periodic nx x ny x nz lattice of the 3-D dendrite model (psi and C on
     D3Q7, no gas, no flow).  Arrays are [z][y][x]."""
 
-    def __init__(self, nx: int, ny: int, nz: int, params: dict):
+    def __init__(self, nx: int, ny: int, nz: int, params: dict, window=None):
         self.lib = _l3()
         self.shape = (int(nz), int(ny), int(nx))
         self.h = self.lib.or3_new(int(nx), int(ny), int(nz))
@@ -367,6 +368,8 @@ class Oracle3D:
             raise MemoryError("oracle allocation failed")
         pv = _f64([float(params[k]) for k in PARAM_NAMES_3D])
         self.lib.or3_set_params(self.h, _dp(pv))
+        if window is not None:           # (NX, NY, NZ, x0, y0, z0)
+            self.lib.or3_set_window(self.h, *[int(v) for v in window])
 
     def __del__(self):
         h = getattr(self, "h", None)

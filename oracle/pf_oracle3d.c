@@ -75,6 +75,7 @@ enum { Q_BETA_PSI, Q_W0, Q_TAU0, Q_EPS_S, Q_K, Q_D, Q_OMEGA, Q_GRAD_EPS, Q_GRAD_
 
 typedef struct {
   int nx, ny, nz, n;
+  int NX, NY, NZ, x0, y0, z0;  /* placement of this lattice in a periodic NX x NY x NZ one */
   double par[NPAR3];
   long steps;
   real *gpre[7], *gpost[7], *rr, *s[7], *Q_o;      /* state */
@@ -96,6 +97,7 @@ o3state *or3_new(int nx, int ny, int nz) {
   o3state *st = (o3state *)calloc(1, sizeof(o3state));
   if (!st) return NULL;
   st->nx = nx; st->ny = ny; st->nz = nz; st->n = nx * ny * nz;
+  st->NX = nx; st->NY = ny; st->NZ = nz;
   const size_t n = (size_t)st->n, planes = 2 * (7 + 7 + 1 + 7 + 1) + 3 + 14 + 3;
   st->block = (real *)calloc(planes * n, sizeof(real));
   if (!st->block) { free(st); return NULL; }
@@ -116,6 +118,14 @@ void or3_free(o3state *st) {
   if (!st) return;
   free(st->block);
   free(st);
+}
+
+/* A window of a larger periodic lattice: the initial seeds are placed with
+ * global coordinates and minimum images in NX x NY x NZ; the window itself
+ * stays periodic, so only sites far enough from its faces follow the large
+ * lattice (two sites per step). */
+void or3_set_window(o3state *st, int NX, int NY, int NZ, int x0, int y0, int z0) {
+  st->NX = NX; st->NY = NY; st->NZ = NZ; st->x0 = x0; st->y0 = y0; st->z0 = z0;
 }
 
 void or3_set_params(o3state *st, const double *p) {
@@ -197,8 +207,9 @@ void or3_init(o3state *st, const double *seeds, int n_seeds, double R_s) {
         const int id = (z * st->ny + y) * st->nx + x;
         double psi = -1.0;
         for (int s = 0; s < n_seeds; ++s) {
-          double d[3] = {x - seeds[3 * s], y - seeds[3 * s + 1], z - seeds[3 * s + 2]};
-          const double L[3] = {st->nx, st->ny, st->nz};
+          double d[3] = {st->x0 + x - seeds[3 * s], st->y0 + y - seeds[3 * s + 1],
+                         st->z0 + z - seeds[3 * s + 2]};
+          const double L[3] = {st->NX, st->NY, st->NZ};
           double r2 = 0;
           for (int a = 0; a < 3; ++a) {
             d[a] = fmod(d[a], L[a]);

@@ -1,0 +1,636 @@
+// pf_step3d.cu -- the three-dimensional dendrite step of arXiv 2407.01651
+// (Section 2.1 with the anisotropy summed over three axes; the anisotropic
+// Allen-Cahn equation with the a_s^2 time stretch of Appendix B and the
+// solute equation with antitrapping) on D3Q7 lattices, in a melt without gas
+// or flow, and the C ABI of its handle (pf3_* in include/pf.h).
+//
+// Kernel: k_step3d, a z-march.  A CTA owns a 32 x 8 column tile and walks
+// `chunk` planes along z; 256 threads own the interior columns and 84 more
+// the halo ring of the tile.  At plane k every thread pulls g of plane k+1 at
+// its column (the a_s^2-stretched streaming) and writes psi into a 4-slot
+// shared-memory ring; after one barrier the interior threads update plane k
+// with the 18-neighbour gradient read from slots k-1, k, k+1.  D3Q7 weights
+// w0 = 1/4, wi = 1/8, c_s^2 = 1/4; gradient with D3Q19 weights (1/18 faces,
+// 1/36 edges).  Layout: one plane per population, [z][y][x], x fastest.
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pf.h"
+#include "pf_device.cuh"
+
+namespace pf {
+namespace d3 {
+
+constexpr int TX = 32, TY = 8;                    // interior tile
+constexpr int HX = TX + 2, HY = TY + 2;           // tile with its halo ring
+constexpr int NIN = TX * TY;                      // 256 interior threads
+constexpr int NHALO = HX * HY - NIN;              // 84 halo threads
+constexpr int THREADS = 352;                      // 11 warps (340 used)
+// planes: g_pre 0..6, g_post 7..13, s 14..20 (storage type); r, Q_o (compute type)
+constexpr int G_PRE = 0, G_POST = 7, S_POP = 14, NPOP3 = 21;
+constexpr int A3_RR = 0, A3_QO = 1, NAUX3 = 2;
+constexpr int NSTATE3 = 23;                       // raw FP64 state planes
+
+__device__ __forceinline__ constexpr int cx7(int i) { return i == 1 ? 1 : (i == 2 ? -1 : 0); }
+__device__ __forceinline__ constexpr int cy7(int i) { return i == 3 ? 1 : (i == 4 ? -1 : 0); }
+__device__ __forceinline__ constexpr int cz7(int i) { return i == 5 ? 1 : (i == 6 ? -1 : 0); }
+template <typename R>
+__device__ __forceinline__ R w7(int i) { return i == 0 ? R(0.25) : R(0.125); }
+
+template <typename R>
+struct Coef3 {
+  R eps, ge2, gat2, four_bpsi, lam, theta, Mcinf, inv_tau0, c4W0sq_tau0, k, inv_omk, D, aW0;
+};
+
+template <typename S, typename R>
+struct Args3 {
+  const S* in;
+  S* out;
+  const R* ain;
+  R* aout;
+  R* fields;            // psi, C, U planes, or nullptr
+  unsigned long long ps;
+  int nx, ny, nz, chunk;
+  int tiles_x, tiles_y, tiles_z;
+  Coef3<R> c;
+};
+
+template <typename T>
+__device__ __forceinline__ const T* pl(const T* p, int k, unsigned long long ps) { return p + (size_t)k * ps; }
+template <typename T>
+__device__ __forceinline__ T* pl(T* p, int k, unsigned long long ps) { return p + (size_t)k * ps; }
+
+// one step across a periodic boundary (z), and a full modulo (tile columns,
+// which may lie up to a tile beyond a small domain)
+__device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+__device__ __forceinline__ int wrapm(int a, int n) { a %= n; return a < 0 ? a + n : a; }
+
+// Streamed g at (x, y, z) (time stretch g = g_pre + r_src (g_post,src - g_pre))
+// and psi, psi_o (compensated sums).
+template <typename S, typename R>
+__device__ __forceinline__ void stream_g(const Args3<S, R>& a, int x, int y, int z, R g[7],
+                                         R& psi, R& psio) {
+  const unsigned long long own = ((unsigned long long)z * a.ny + y) * a.nx + x;
+  CSum<R> sg;
+  R po = R(0);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    const unsigned long long src =
+        ((unsigned long long)wrap1(z - cz7(i), a.nz) * a.ny + wrap1(y - cy7(i), a.ny)) * a.nx +
+        wrap1(x - cx7(i), a.nx);   // x, y in range: one step wraps
+    const R gold = ld<R>(pl(a.in, G_PRE + i, a.ps), own);
+    const R gpo = ld<R>(pl(a.in, G_POST + i, a.ps), src);
+    const R rr = ld<R>(pl(a.ain, A3_RR, a.ps), src);
+    g[i] = gold + (gpo - gold) * rr;
+    sg.add(g[i]);
+    po += gold;
+  }
+  psi = sg.value();
+  psio = po;
+}
+
+template <typename S, typename R>
+__global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R> a) {
+  __shared__ R ring[4][HY][HX];
+  const int t = threadIdx.x;
+  // column of this thread within the halo tile
+  int hx = 0, hy = 0;
+  const bool interior = t < NIN;
+  if (interior) {
+    hx = 1 + t % TX;
+    hy = 1 + t / TX;
+  } else if (t < NIN + NHALO) {
+    const int h = t - NIN;            // halo ring: bottom row, top row, left, right
+    if (h < HX) { hx = h; hy = 0; }
+    else if (h < 2 * HX) { hx = h - HX; hy = HY - 1; }
+    else if (h < 2 * HX + TY) { hx = 0; hy = 1 + h - 2 * HX; }
+    else { hx = HX - 1; hy = 1 + h - 2 * HX - TY; }
+  }
+  const bool active = t < NIN + NHALO;
+  const int ntiles = a.tiles_x * a.tiles_y * a.tiles_z;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int tx = tile % a.tiles_x, ty = (tile / a.tiles_x) % a.tiles_y;
+    const int tz = tile / (a.tiles_x * a.tiles_y);
+    const int za = tz * a.chunk, zb = min(za + a.chunk, a.nz);
+    const int x = wrapm(tx * TX + hx - 1, a.nx), y = wrapm(ty * TY + hy - 1, a.ny);
+    const bool mine = interior && tx * TX + hx - 1 < a.nx && ty * TY + hy - 1 < a.ny;
+    R gC[7], gL[7], poC = R(0), poL = R(0);
+    // ring planes za-1 and za
+    for (int k = 0; k < 2; ++k) {
+      if (active) {
+        const int z = wrap1(za - 1 + k, a.nz);
+        R g[7], psi, po;
+        stream_g(a, x, y, z, g, psi, po);
+        ring[(za - 1 + k) & 3][hy][hx] = psi;
+        if (k == 1) {
+#pragma unroll
+          for (int i = 0; i < 7; ++i) gC[i] = g[i];
+          poC = po;
+        }
+      }
+    }
+    for (int z = za; z < zb; ++z) {
+      // own inputs of plane z: streamed solute populations and the lagged source
+      R sv[7], Qo = R(0);
+      const unsigned long long site = ((unsigned long long)z * a.ny + y) * a.nx + x;
+      if (mine) {
+#pragma unroll
+        for (int i = 0; i < 7; ++i) {
+          const unsigned long long src =
+              ((unsigned long long)wrap1(z - cz7(i), a.nz) * a.ny + wrap1(y - cy7(i), a.ny)) *
+                  a.nx + wrap1(x - cx7(i), a.nx);
+          sv[i] = ld<R>(pl(a.in, S_POP + i, a.ps), src);
+        }
+        Qo = ld<R>(pl(a.ain, A3_QO, a.ps), site);
+      }
+      if (active) {
+        R psi;
+        stream_g(a, x, y, wrap1(z + 1, a.nz), gL, psi, poL);
+        ring[(z + 1) & 3][hy][hx] = psi;
+      }
+      __syncthreads();
+      if (mine) {
+        const Coef3<R>& c = a.c;
+        const R (*Pm)[HX] = ring[(z - 1) & 3];
+        const R (*P0)[HX] = ring[z & 3];
+        const R (*Pp)[HX] = ring[(z + 1) & 3];
+        const R psi = P0[hy][hx];
+        // gradient: 3 sum w c (X - X0) over faces (1/18) and edges (1/36)
+        const R X0 = psi;
+        auto d = [&](const R (*Pl)[HX], int dx, int dy) { return Pl[hy + dy][hx + dx] - X0; };
+        const R w1 = R(1.0 / 18.0), w2 = R(1.0 / 36.0);
+        R gx = w1 * (d(P0, 1, 0) - d(P0, -1, 0)) +
+               w2 * ((d(P0, 1, 1) - d(P0, -1, 1)) + (d(P0, 1, -1) - d(P0, -1, -1)) +
+                     (d(Pp, 1, 0) - d(Pp, -1, 0)) + (d(Pm, 1, 0) - d(Pm, -1, 0)));
+        R gy = w1 * (d(P0, 0, 1) - d(P0, 0, -1)) +
+               w2 * ((d(P0, 1, 1) - d(P0, 1, -1)) + (d(P0, -1, 1) - d(P0, -1, -1)) +
+                     (d(Pp, 0, 1) - d(Pp, 0, -1)) + (d(Pm, 0, 1) - d(Pm, 0, -1)));
+        R gz = w1 * (d(Pp, 0, 0) - d(Pm, 0, 0)) +
+               w2 * ((d(Pp, 1, 0) - d(Pm, 1, 0)) + (d(Pp, -1, 0) - d(Pm, -1, 0)) +
+                     (d(Pp, 0, 1) - d(Pm, 0, 1)) + (d(Pp, 0, -1) - d(Pm, 0, -1)));
+        gx *= R(3); gy *= R(3); gz *= R(3);
+        // anisotropy (three axes), regularised normal
+        const R gm2 = gx * gx + gy * gy + gz * gz;
+        const R im = frsqrt(gm2 + c.ge2);
+        const R m = (gm2 + c.ge2) * im;
+        const R n0 = -gx * im, n1 = -gy * im, n2v = -gz * im;
+        const R q0 = n0 * n0, q1 = n1 * n1, q2 = n2v * n2v;
+        const R n2 = q0 + q1 + q2, s4 = q0 * q0 + q1 * q1 + q2 * q2;
+        const R as = R(1) + c.eps * (R(4) * s4 - R(3) * n2 * n2);
+        const R iso = s4 + R(0.75) * n2 * (R(1) - n2);
+        const R pre = R(-16) * c.eps * as * m;
+        const R Nx = pre * n0 * (q0 - iso), Ny = pre * n1 * (q1 - iso), Nz = pre * n2v * (q2 - iso);
+        const R as2 = as * as, ias2 = frcp(as2);
+        // moments, sources
+        CSum<R> cs;
+#pragma unroll
+        for (int i = 0; i < 7; ++i) cs.add(sv[i]);
+        const R C = cs.value();
+        const R omk = R(1) - c.k;
+        const R A = (R(1) + c.k) - omk * psi;
+        const R iA = frcp(A);
+        const R U = (R(2) * C * iA - R(1)) * c.inv_omk;
+        const R omp2 = R(1) - psi * psi;
+        const R Q = c.four_bpsi * psi * omp2 - c.lam * omp2 * omp2 * (c.theta + c.Mcinf * U);
+        const R at = -c.aW0 * as * (R(1) + omk * U) * (psi - poC) * frsqrt(gm2 + c.gat2);
+        // psi: D3Q7, m0 = psi + (Q + (Q - Q_o)/2) / tau0, flux rate s1 from
+        // W0^2 a_s^2 / tau0 = (1/s1 - 1/2) c_s^2, forcing flux -c_s^2 N / a_s^2
+        {
+          const R m0 = psi + (Q + R(0.5) * (Q - Qo)) * c.inv_tau0;
+          const R s1 = frcp(c.c4W0sq_tau0 * as2 + R(0.5));
+          const R hs = R(1) - R(0.5) * s1;
+          const R Jx = gC[1] - gC[2], Jy = gC[3] - gC[4], Jz = gC[5] - gC[6];
+          const R gq = R(-0.25) * ias2;
+          const R Sx = fma(hs, gq * Nx, Jx - s1 * Jx), Sy = fma(hs, gq * Ny, Jy - s1 * Jy),
+                  Sz = fma(hs, gq * Nz, Jz - s1 * Jz);
+          const R b = m0 * R(0.125);
+          R go[7];
+          go[0] = m0 - R(6) * b;
+          go[1] = fma(R(0.5), Sx, b); go[2] = fma(R(-0.5), Sx, b);
+          go[3] = fma(R(0.5), Sy, b); go[4] = fma(R(-0.5), Sy, b);
+          go[5] = fma(R(0.5), Sz, b); go[6] = fma(R(-0.5), Sz, b);
+#pragma unroll
+          for (int i = 0; i < 7; ++i) {
+            st<S, R>(pl(a.out, G_PRE + i, a.ps), site, gC[i]);
+            st<S, R>(pl(a.out, G_POST + i, a.ps), site, go[i]);
+          }
+          pl(a.aout, A3_RR, a.ps)[site] = ias2;
+          pl(a.aout, A3_QO, a.ps)[site] = Q;
+        }
+        // solute: D3Q7, Jeq = -E grad psi + (1-k) J_at, rate from
+        // D_C = 2 D q / A = (1/s - 1/2) c_s^2
+        {
+          const R qf = R(0.5) * (R(1) - psi);
+          const R E = R(2) * omk * c.D * qf * C * iA * iA;
+          const R DC = R(2) * c.D * qf * iA;
+          const R sc = frcp(R(4) * DC + R(0.5));
+          const R coef = omk * at - E;
+          const R Ex = coef * gx, Ey = coef * gy, Ez = coef * gz;
+          const R Jx = sv[1] - sv[2], Jy = sv[3] - sv[4], Jz = sv[5] - sv[6];
+          const R Sx = Jx - sc * (Jx - Ex), Sy = Jy - sc * (Jy - Ey), Sz = Jz - sc * (Jz - Ez);
+          const R b = C * R(0.125);
+          R so[7];
+          so[0] = C - R(6) * b;
+          so[1] = fma(R(0.5), Sx, b); so[2] = fma(R(-0.5), Sx, b);
+          so[3] = fma(R(0.5), Sy, b); so[4] = fma(R(-0.5), Sy, b);
+          so[5] = fma(R(0.5), Sz, b); so[6] = fma(R(-0.5), Sz, b);
+#pragma unroll
+          for (int i = 0; i < 7; ++i) st<S, R>(pl(a.out, S_POP + i, a.ps), site, so[i]);
+        }
+        if (a.fields) {
+          pl(a.fields, 0, a.ps)[site] = psi;
+          pl(a.fields, 1, a.ps)[site] = C;
+          pl(a.fields, 2, a.ps)[site] = U;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 7; ++i) gC[i] = gL[i];
+      poC = poL;
+    }
+    __syncthreads();
+  }
+}
+
+// Equilibrium state of a site from psi and C (populations w psi / w C, r = 1,
+// lagged source Q_psi), fields written.
+template <typename S, typename R>
+__device__ void write_eq3(const Args3<S, R>& a, unsigned long long site, R psi, R C) {
+  const Coef3<R>& c = a.c;
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    st<S, R>(pl(a.out, G_PRE + i, a.ps), site, w7<R>(i) * psi);
+    st<S, R>(pl(a.out, G_POST + i, a.ps), site, w7<R>(i) * psi);
+    st<S, R>(pl(a.out, S_POP + i, a.ps), site, w7<R>(i) * C);
+  }
+  const R omk = R(1) - c.k;
+  const R U = (R(2) * C / ((R(1) + c.k) - omk * psi) - R(1)) * c.inv_omk;
+  const R omp2 = R(1) - psi * psi;
+  pl(a.aout, A3_RR, a.ps)[site] = R(1);
+  pl(a.aout, A3_QO, a.ps)[site] = c.four_bpsi * psi * omp2 - c.lam * omp2 * omp2 * (c.theta + c.Mcinf * U);
+  pl(a.fields, 0, a.ps)[site] = psi;
+  pl(a.fields, 1, a.ps)[site] = C;
+  pl(a.fields, 2, a.ps)[site] = U;
+}
+
+__device__ __forceinline__ double min_image1(double d, double L) {
+  if (d <= -L || d >= L) d = fmod(d, L);
+  if (d < -0.5 * L) d += L;
+  if (d >= 0.5 * L) d -= L;
+  return d;
+}
+
+template <typename S, typename R>
+__global__ void k_init3(Args3<S, R> a, const double* seeds, int n_seeds, double R_s, double sq2b,
+                        double W0, double k) {
+  const unsigned long long n = (unsigned long long)a.nx * a.ny * a.nz;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % a.nx), y = (int)((i / a.nx) % a.ny), z = (int)(i / ((unsigned long long)a.nx * a.ny));
+    double psi = -1.0;
+    const double far = R_s + 30.0 * W0 / sq2b;
+    for (int s = 0; s < n_seeds; ++s) {
+      const double dx = min_image1(x - seeds[3 * s], a.nx), dy = min_image1(y - seeds[3 * s + 1], a.ny);
+      const double dz = min_image1(z - seeds[3 * s + 2], a.nz);
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      const double v = r2 > far * far ? -1.0 : tanh(sq2b * (R_s - sqrt(r2)) / W0);
+      if (s == 0 || v > psi) psi = v;
+    }
+    const double C = 1.0 - (1.0 - k) * 0.5 * (1.0 + psi);
+    write_eq3<S, R>(a, i, (R)psi, (R)C);
+  }
+}
+
+template <typename S, typename R>
+__global__ void k_set3(Args3<S, R> a, const double* psi, const double* C) {
+  const unsigned long long n = (unsigned long long)a.nx * a.ny * a.nz;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x)
+    write_eq3<S, R>(a, i, (R)psi[i], (R)C[i]);
+}
+
+template <typename S, typename R>
+__global__ void k_state3(const S* pin, const R* ain, unsigned long long ps, unsigned long long n,
+                         double* out) {
+  for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < n;
+       j += (unsigned long long)gridDim.x * blockDim.x) {
+    for (int i = 0; i < 7; ++i) {
+      out[(0 + i) * n + j] = (double)ld<R>(pl(pin, G_PRE + i, ps), j);
+      out[(7 + i) * n + j] = (double)ld<R>(pl(pin, G_POST + i, ps), j);
+      out[(15 + i) * n + j] = (double)ld<R>(pl(pin, S_POP + i, ps), j);
+    }
+    out[14 * n + j] = (double)ain[A3_RR * ps + j];
+    out[22 * n + j] = (double)ain[A3_QO * ps + j];
+  }
+}
+
+template <typename R>
+__global__ void k_fields3(const R* f, unsigned long long ps, unsigned long long n, double* out) {
+  for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < 3 * n;
+       j += (unsigned long long)gridDim.x * blockDim.x)
+    out[j] = (double)f[(j / n) * ps + j % n];
+}
+
+// FP64 totals: sum C, sum h(psi) = sum (1 + psi) / 2; fixed-order partials.
+template <typename R>
+__global__ void k_reduce3(const R* f, unsigned long long ps, unsigned long long n, double* part) {
+  double a0 = 0.0, a1 = 0.0;
+  for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < n;
+       j += (unsigned long long)gridDim.x * blockDim.x) {
+    a1 += 0.5 * (1.0 + (double)f[j]);
+    a0 += (double)f[ps + j];
+  }
+  __shared__ double sh[2][256];
+  sh[0][threadIdx.x] = a0;
+  sh[1][threadIdx.x] = a1;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + s];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { part[2 * blockIdx.x] = sh[0][0]; part[2 * blockIdx.x + 1] = sh[1][0]; }
+}
+__global__ void k_reduce3_final(const double* part, int nb, double* out) {
+  if (threadIdx.x >= 2) return;
+  double acc = 0.0;
+  for (int b = 0; b < nb; ++b) acc += part[2 * b + threadIdx.x];
+  out[threadIdx.x] = acc;
+}
+
+}  // namespace d3
+}  // namespace pf
+
+using namespace pf;
+using namespace pf::d3;
+
+struct pf3_handle {
+  pf_params p{};
+  pf_precision prec = PF_FP32;
+  cudaStream_t stream = nullptr;
+  int nx = 0, ny = 0, nz = 0, chunk = 16;
+  unsigned long long n = 0;
+  size_t elem = 4, celem = 4;
+  void* pop[2] = {nullptr, nullptr};
+  void* aux[2] = {nullptr, nullptr};
+  void* fields = nullptr;
+  double* scratch = nullptr;      // FP64 staging and reduction partials
+  size_t scratch_elems = 0;
+  int cur = 0, inited = 0;
+  long long steps = 0, launches = 0;
+  std::string err;
+};
+
+static std::string g3_err;
+
+static pf_status fail3(pf3_handle* h, pf_status code, const std::string& m) {
+  if (h) h->err = m; else g3_err = m;
+  return code;
+}
+#define PF3_CUDA(h, ...)                                                                \
+  do {                                                                                  \
+    cudaError_t e_ = (__VA_ARGS__);                                                     \
+    if (e_ != cudaSuccess) return fail3((h), PF_ERR_CUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename R>
+static Coef3<R> coef3(const pf_params& p) {
+  Coef3<R> c{};
+  double der[3];
+  pf_params_derived(&p, der);
+  c.eps = (R)p.eps_s;
+  c.ge2 = (R)(p.grad_eps * p.grad_eps);
+  c.gat2 = (R)(p.grad_eps_at * p.grad_eps_at);
+  c.four_bpsi = (R)(4.0 * p.beta_psi);
+  c.lam = (R)der[0];
+  c.Mcinf = (R)der[1];
+  c.theta = (R)der[2];
+  c.inv_tau0 = (R)(1.0 / p.tau0);
+  c.c4W0sq_tau0 = (R)(4.0 * p.W0 * p.W0 / p.tau0);   // W0^2 / (tau0 c_s^2), c_s^2 = 1/4
+  c.k = (R)p.k;
+  c.inv_omk = (R)(1.0 / (1.0 - p.k));
+  c.D = (R)p.D;
+  c.aW0 = (R)(p.W0 / (2.0 * std::sqrt(2.0)));
+  return c;
+}
+
+template <typename S, typename R>
+static Args3<S, R> args3(const pf3_handle* h, bool fields) {
+  Args3<S, R> a{};
+  a.in = (const S*)h->pop[h->cur];
+  a.out = (S*)h->pop[h->cur ^ 1];
+  a.ain = (const R*)h->aux[h->cur];
+  a.aout = (R*)h->aux[h->cur ^ 1];
+  a.fields = fields ? (R*)h->fields : nullptr;
+  a.ps = h->n;
+  a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.chunk = h->chunk;
+  a.tiles_x = (h->nx + TX - 1) / TX;
+  a.tiles_y = (h->ny + TY - 1) / TY;
+  a.tiles_z = (h->nz + h->chunk - 1) / h->chunk;
+  a.c = coef3<R>(h->p);
+  return a;
+}
+
+static pf_status ensure_scratch3(pf3_handle* h, size_t elems) {
+  if (elems <= h->scratch_elems) return PF_OK;
+  cudaStreamSynchronize(h->stream);
+  cudaFree(h->scratch);
+  h->scratch = nullptr;
+  h->scratch_elems = 0;
+  if (cudaMalloc(&h->scratch, elems * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail3(h, PF_ERR_OOM, "staging allocation failed");
+  }
+  h->scratch_elems = elems;
+  return PF_OK;
+}
+
+template <typename F>
+static pf_status dispatch3(const pf3_handle* h, F&& f) {
+  if (h->prec == PF_FP64) return f(double{}, double{});
+  return f(float{}, float{});
+}
+
+extern "C" pf_status pf3_create(const pf_params* p, int nx, int ny, int nz, pf_precision prec,
+                                void* cuda_stream, pf3_handle** out) {
+  if (!out || !p) return fail3(nullptr, PF_ERR_BAD_ARG, "NULL argument");
+  *out = nullptr;
+  if (prec != PF_FP32 && prec != PF_FP64)
+    return fail3(nullptr, PF_ERR_BAD_ARG, "the 3-D step takes FP32 or FP64 storage");
+  if (nx < 4 || ny < 4 || nz < 4 || nx > 4096 || ny > 4096 || nz > 4096)
+    return fail3(nullptr, PF_ERR_BAD_ARG, "sizes must be in [4, 4096]");
+  if (!(p->W0 > 0) || !(p->tau0 > 0) || !(p->D > 0) || !(p->k > 0 && p->k < 1) ||
+      !(p->eps_s >= 0 && p->eps_s < 0.25) || !(p->grad_eps > 0) || !(p->grad_eps_at > 0) ||
+      1.0 - (1.0 - p->k) * p->Omega == 0.0)
+    return fail3(nullptr, PF_ERR_BAD_ARG, "a parameter is out of range");
+  const unsigned long long n = (unsigned long long)nx * ny * nz;
+  pf3_handle* h = new (std::nothrow) pf3_handle();
+  if (!h) return fail3(nullptr, PF_ERR_OOM, "host allocation failed");
+  h->p = *p; h->prec = prec; h->stream = (cudaStream_t)cuda_stream;
+  h->nx = nx; h->ny = ny; h->nz = nz; h->n = n;
+  h->elem = h->celem = prec == PF_FP64 ? 8 : 4;
+  bool ok = true;
+  for (int c = 0; c < 2; ++c) {
+    ok = ok && cudaMalloc(&h->pop[c], n * NPOP3 * h->elem) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->aux[c], n * NAUX3 * h->celem) == cudaSuccess;
+  }
+  ok = ok && cudaMalloc(&h->fields, n * 3 * h->celem) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    pf3_destroy(h);
+    return fail3(nullptr, PF_ERR_OOM, "device allocation failed");
+  }
+  *out = h;
+  return PF_OK;
+}
+
+extern "C" pf_status pf3_destroy(pf3_handle* h) {
+  if (!h) return PF_OK;
+  cudaStreamSynchronize(h->stream);
+  for (int c = 0; c < 2; ++c) { cudaFree(h->pop[c]); cudaFree(h->aux[c]); }
+  cudaFree(h->fields);
+  cudaFree(h->scratch);
+  const cudaError_t e = cudaGetLastError();
+  delete h;
+  return e == cudaSuccess ? PF_OK : PF_ERR_CUDA;
+}
+
+extern "C" const char* pf3_last_error(const pf3_handle* h) { return h ? h->err.c_str() : g3_err.c_str(); }
+extern "C" long long pf3_launch_count(const pf3_handle* h) { return h ? h->launches : -1; }
+
+extern "C" pf_status pf3_init_seeds(pf3_handle* h, const double* seeds, int n_seeds, double R_s) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (n_seeds < 0 || (n_seeds > 0 && !seeds) || !std::isfinite(R_s))
+    return fail3(h, PF_ERR_BAD_ARG, "bad seeds");
+  pf_status st = ensure_scratch3(h, 3 * (size_t)n_seeds + 1);
+  if (st != PF_OK) return st;
+  if (n_seeds)
+    PF3_CUDA(h, cudaMemcpyAsync(h->scratch, seeds, 3 * (size_t)n_seeds * sizeof(double),
+                                cudaMemcpyHostToDevice, h->stream));
+  h->cur = 0;
+  st = dispatch3(h, [&](auto s_t, auto r_t) {
+    using S = decltype(s_t);
+    using R = decltype(r_t);
+    Args3<S, R> a = args3<S, R>(h, true);
+    a.out = (S*)h->pop[0];
+    a.aout = (R*)h->aux[0];
+    k_init3<S, R><<<1024, 256, 0, h->stream>>>(a, h->scratch, n_seeds, R_s,
+                                                std::sqrt(2.0 * h->p.beta_psi), h->p.W0, h->p.k);
+    PF3_CUDA(h, cudaGetLastError());
+    return PF_OK;
+  });
+  if (st != PF_OK) return st;
+  h->launches++;
+  PF3_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->inited = 1;
+  h->steps = 0;
+  return PF_OK;
+}
+
+extern "C" pf_status pf3_set_fields(pf3_handle* h, const double* psi, const double* C, size_t n) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (!psi || !C || n != h->n) return fail3(h, PF_ERR_BAD_ARG, "need psi and C of nx*ny*nz");
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(psi[i]) || !std::isfinite(C[i])) return fail3(h, PF_ERR_BAD_ARG, "non-finite field");
+  pf_status st = ensure_scratch3(h, 2 * n);
+  if (st != PF_OK) return st;
+  PF3_CUDA(h, cudaMemcpyAsync(h->scratch, psi, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  PF3_CUDA(h, cudaMemcpyAsync(h->scratch + n, C, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  h->cur = 0;
+  st = dispatch3(h, [&](auto s_t, auto r_t) {
+    using S = decltype(s_t);
+    using R = decltype(r_t);
+    Args3<S, R> a = args3<S, R>(h, true);
+    a.out = (S*)h->pop[0];
+    a.aout = (R*)h->aux[0];
+    k_set3<S, R><<<1024, 256, 0, h->stream>>>(a, h->scratch, h->scratch + n);
+    PF3_CUDA(h, cudaGetLastError());
+    return PF_OK;
+  });
+  if (st != PF_OK) return st;
+  h->launches++;
+  PF3_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->inited = 1;
+  h->steps = 0;
+  return PF_OK;
+}
+
+extern "C" pf_status pf3_set_chunk(pf3_handle* h, int chunk) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (chunk < 1 || chunk > 4096) return fail3(h, PF_ERR_BAD_ARG, "chunk must be in [1, 4096]");
+  h->chunk = chunk;
+  return PF_OK;
+}
+
+extern "C" pf_status pf3_step(pf3_handle* h, int n_steps) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (n_steps < 0) return fail3(h, PF_ERR_BAD_ARG, "n_steps must be >= 0");
+  if (!h->inited) return fail3(h, PF_ERR_STATE, "initialise before stepping");
+  return dispatch3(h, [&](auto s_t, auto r_t) {
+    using S = decltype(s_t);
+    using R = decltype(r_t);
+    for (int t = 0; t < n_steps; ++t) {
+      const Args3<S, R> a = args3<S, R>(h, t == n_steps - 1);
+      const int tiles = a.tiles_x * a.tiles_y * a.tiles_z;
+      k_step3d<S, R><<<tiles, THREADS, 0, h->stream>>>(a);
+      PF3_CUDA(h, cudaGetLastError());
+      h->cur ^= 1;
+      h->steps++;
+      h->launches++;
+    }
+    return PF_OK;
+  });
+}
+
+extern "C" pf_status pf3_get_fields(pf3_handle* h, double* out, size_t n) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (!out || n < 3 * h->n) return fail3(h, PF_ERR_BAD_ARG, "output must hold 3 planes");
+  pf_status st = ensure_scratch3(h, 3 * h->n);
+  if (st != PF_OK) return st;
+  if (h->prec == PF_FP64) k_fields3<double><<<1024, 256, 0, h->stream>>>((const double*)h->fields, h->n, h->n, h->scratch);
+  else k_fields3<float><<<1024, 256, 0, h->stream>>>((const float*)h->fields, h->n, h->n, h->scratch);
+  PF3_CUDA(h, cudaGetLastError());
+  h->launches++;
+  PF3_CUDA(h, cudaMemcpyAsync(out, h->scratch, 3 * h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  PF3_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PF_OK;
+}
+
+extern "C" pf_status pf3_get_state(pf3_handle* h, double* out, size_t n) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (!out || n < NSTATE3 * h->n) return fail3(h, PF_ERR_BAD_ARG, "output must hold 23 planes");
+  pf_status st = ensure_scratch3(h, NSTATE3 * h->n);
+  if (st != PF_OK) return st;
+  st = dispatch3(h, [&](auto s_t, auto r_t) {
+    using S = decltype(s_t);
+    using R = decltype(r_t);
+    k_state3<S, R><<<1024, 256, 0, h->stream>>>((const S*)h->pop[h->cur], (const R*)h->aux[h->cur],
+                                                 h->n, h->n, h->scratch);
+    PF3_CUDA(h, cudaGetLastError());
+    return PF_OK;
+  });
+  if (st != PF_OK) return st;
+  h->launches++;
+  PF3_CUDA(h, cudaMemcpyAsync(out, h->scratch, NSTATE3 * h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  PF3_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PF_OK;
+}
+
+extern "C" pf_status pf3_reduce(pf3_handle* h, double out[2]) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (!out) return fail3(h, PF_ERR_BAD_ARG, "NULL output");
+  const int nb = 1024;
+  pf_status st = ensure_scratch3(h, 2 * nb + 2);
+  if (st != PF_OK) return st;
+  if (h->prec == PF_FP64) k_reduce3<double><<<nb, 256, 0, h->stream>>>((const double*)h->fields, h->n, h->n, h->scratch);
+  else k_reduce3<float><<<nb, 256, 0, h->stream>>>((const float*)h->fields, h->n, h->n, h->scratch);
+  k_reduce3_final<<<1, 32, 0, h->stream>>>(h->scratch, nb, h->scratch + 2 * nb);
+  PF3_CUDA(h, cudaGetLastError());
+  h->launches += 2;
+  PF3_CUDA(h, cudaMemcpyAsync(out, h->scratch + 2 * nb, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  PF3_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PF_OK;
+}

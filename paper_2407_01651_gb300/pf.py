@@ -115,12 +115,27 @@ def lib() -> ctypes.CDLL:
     L.pf_set_temperature.argtypes = [P, I, D, S]
     L.pf_reduce_thermal.argtypes = [P, I, D]
     L.pf_set_boundaries.argtypes = [P, I, ctypes.POINTER(ctypes.c_int)]
+    L.pf3_create.argtypes = [ctypes.POINTER(pf_params), I, I, I, I, P, ctypes.POINTER(P)]
+    L.pf3_init_seeds.argtypes = [P, D, I, ctypes.c_double]
+    L.pf3_set_fields.argtypes = [P, D, D, S]
+    L.pf3_set_chunk.argtypes = [P, I]
+    L.pf3_step.argtypes = [P, I]
+    L.pf3_get_fields.argtypes = [P, D, S]
+    L.pf3_get_state.argtypes = [P, D, S]
+    L.pf3_reduce.argtypes = [P, D]
+    L.pf3_launch_count.argtypes = [P]
+    L.pf3_launch_count.restype = ctypes.c_longlong
+    L.pf3_last_error.argtypes = [P]
+    L.pf3_last_error.restype = ctypes.c_char_p
+    L.pf3_destroy.argtypes = [P]
     for name in ("pf_params_default", "pf_params_derived", "pf_create", "pf_init_fields",
                  "pf_set_fields", "pf_step", "pf_get_fields", "pf_get_state", "pf_set_state",
                  "pf_reduce", "pf_sync", "pf_destroy", "pf_set_step_config",
                  "pf_get_step_config", "pf_reduce_noalloc", "pf_adjoint_step",
                  "pf_set_launch", "pf_autotune", "pf_set_temperature", "pf_reduce_thermal",
-                 "pf_set_boundaries"):
+                 "pf_set_boundaries", "pf3_create", "pf3_init_seeds", "pf3_set_fields",
+                 "pf3_set_chunk", "pf3_step", "pf3_get_fields", "pf3_get_state", "pf3_reduce",
+                 "pf3_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -360,3 +375,79 @@ class Simulation:
         _check(lib().pf_reduce(self.h, dom, ctypes.byref(pr) if pr else None, ctypes.byref(d)),
                self.h)
         return {k: getattr(d, k) for k in _DIAG_FIELDS}
+
+
+PF3_STATE_PLANES = 23
+
+
+def _check3(code: int, handle=None) -> None:
+    if code != PF_OK:
+        raise PFError(code, lib().pf3_last_error(handle).decode(errors="replace"))
+
+
+class Simulation3D:
+    """Handle of the 3-D dendrite step (psi and C on D3Q7, periodic
+    nx x ny x nz, no gas or flow); arrays are [z][y][x]."""
+
+    def __init__(self, shape, params: dict | None = None, precision: str = "fp32", stream=None):
+        nx, ny, nz = (int(v) for v in shape)
+        self.shape = (nz, ny, nx)
+        self.params = params_from_dict(params)
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                stream = 0
+        h = ctypes.c_void_p()
+        _check3(lib().pf3_create(ctypes.byref(self.params), nx, ny, nz, PRECISIONS[precision],
+                                 ctypes.c_void_p(stream), ctypes.byref(h)))
+        self.h = h
+        self.n = nx * ny * nz
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            code = lib().pf3_destroy(self.h)
+            self.h = None
+            _check3(code)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_seeds(self, seeds, R_s: float) -> None:
+        s = np.ascontiguousarray(np.asarray(seeds, dtype=np.float64).reshape(-1, 3))
+        _check3(lib().pf3_init_seeds(self.h, _dp(s), len(s), float(R_s)), self.h)
+
+    def set_fields(self, psi, C) -> None:
+        a = np.ascontiguousarray(np.asarray(psi, dtype=np.float64).reshape(self.shape))
+        b = np.ascontiguousarray(np.asarray(C, dtype=np.float64).reshape(self.shape))
+        _check3(lib().pf3_set_fields(self.h, _dp(a), _dp(b), self.n), self.h)
+
+    def set_chunk(self, chunk: int) -> None:
+        _check3(lib().pf3_set_chunk(self.h, int(chunk)), self.h)
+
+    def step(self, n: int = 1) -> None:
+        _check3(lib().pf3_step(self.h, int(n)), self.h)
+
+    def fields(self) -> dict:
+        out = np.empty(3 * self.n)
+        _check3(lib().pf3_get_fields(self.h, _dp(out), out.size), self.h)
+        out = out.reshape((3,) + self.shape)
+        return {"psi": out[0], "C": out[1], "U": out[2]}
+
+    def get_state(self) -> np.ndarray:
+        out = np.empty(PF3_STATE_PLANES * self.n)
+        _check3(lib().pf3_get_state(self.h, _dp(out), out.size), self.h)
+        return out.reshape((PF3_STATE_PLANES,) + self.shape)
+
+    def reduce(self) -> dict:
+        out = np.zeros(2)
+        _check3(lib().pf3_reduce(self.h, _dp(out)), self.h)
+        return {"sum_C": out[0], "sum_hpsi": out[1]}
+
+    @property
+    def launches(self) -> int:
+        return lib().pf3_launch_count(self.h)

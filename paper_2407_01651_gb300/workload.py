@@ -149,3 +149,11 @@ def ensemble_96(rng_seed: int = 5) -> list[Layout]:
             lay.params = dict(BASE_PARAMS, eps_s=eps)
             out.append(lay)
     return out
+
+
+def growth_3d(n: int = 256, n_seeds: int = 64, rng_seed: int = 4, R_s: float = 8.0):
+    """A periodic n^3 melt with n_seeds spherical seeds (radius R_s) at
+    uniform positions, for the 3-D dendrite step; returns (seeds, R_s)."""
+    rng = SplitMix64(rng_seed)
+    seeds = [(n * rng.uniform(), n * rng.uniform(), n * rng.uniform()) for _ in range(n_seeds)]
+    return seeds, R_s

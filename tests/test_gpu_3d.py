@@ -1,0 +1,132 @@
+"""The 3-D dendrite step (psi and C on D3Q7, reading R33) of the CUDA path
+against the FP64 3-D oracle, through the C ABI.  Tolerances as for the 2-D
+step: FP64 within 1e-11 relative per field over a few steps (1e-9 over
+hundreds), FP32 within 1e-5 per step."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_01651_gb300 import pf
+from paper_2407_01651_gb300 import workload as wl
+
+pytestmark = pytest.mark.gpu
+
+P3 = {k: wl.BASE_PARAMS[k] for k in oracle.PARAM_NAMES_3D}
+# Without gas, U starts at exactly 0 (C = 1 - (1-k) h(psi)) and grows slowly
+# from solute rejection: its scale is that of the supersaturation the
+# undercooling sets, O(Omega) = O(0.1), not its tiny early maximum (FP32
+# computes 2C/A - 1 from C rounded to ~6e-8).
+FLOOR = {"psi": 1e-9, "C": 1e-9, "U": 0.1}
+
+
+def rel(a, b, floor):
+    return np.abs(a - b).max() / max(np.abs(b).max(), floor)
+
+
+def pair(shape, seeds, R_s, precision, params=P3):
+    nx, ny, nz = shape
+    o = oracle.Oracle3D(nx, ny, nz, params)
+    o.init_spec(seeds, R_s)
+    sim = pf.Simulation3D(shape, dict(wl.BASE_PARAMS, **params), precision)
+    sim.init_seeds(seeds, R_s)
+    return o, sim
+
+
+def compare(o, sim, tol):
+    fo, fg = o.fields(), sim.fields()
+    errs = {k: rel(fg[k], fo[k], FLOOR[k]) for k in fo}
+    assert all(v <= tol for v in errs.values()), errs
+    return errs
+
+
+RAGGED = (40, 19, 13)          # two column tiles in x (one ragged), three in y, chunks in z
+SEEDS = [(10.3, 9.1, 6.2), (33.0, 4.0, 11.5)]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_3d_initial_state(precision, tol):
+    o, sim = pair(RAGGED, SEEDS, 5.0, precision)
+    compare(o, sim, tol)
+    so, sg = o.state(), sim.get_state()
+    for p in range(pf.PF3_STATE_PLANES):
+        assert rel(sg[p], so[p], 1e-12) <= max(tol, 1e-15), p
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+def test_3d_steps_match_oracle(precision, tol):
+    o, sim = pair(RAGGED, SEEDS, 5.0, precision)
+    sim.set_chunk(5)
+    for _ in range(3):
+        o.step(1)
+        sim.step(1)
+        compare(o, sim, tol)
+    so, sg = o.state(), sim.get_state()
+    for p in range(pf.PF3_STATE_PLANES):
+        assert rel(sg[p], so[p], 1e-12) <= tol * 10, p
+
+
+def test_3d_fp64_many_steps_symmetry_and_conservation():
+    """A centred seed over 150 steps: within 1e-9 of the oracle, with the
+    symmetry of the cube and sum C conserved to 1e-12 in FP64."""
+    n = 28
+    o, sim = pair((n, n, n), [(n / 2, n / 2, n / 2)], 8.0, "fp64")
+    c0 = sim.reduce()["sum_C"]
+    o.step(150)
+    sim.step(150)
+    compare(o, sim, 1e-9)
+    psi = sim.fields()["psi"]
+    for t in (psi.transpose(0, 2, 1), psi.transpose(2, 1, 0),
+              np.roll(np.flip(psi, axis=2), 1, axis=2)):
+        assert np.abs(psi - t).max() < 1e-12
+    assert abs(sim.reduce()["sum_C"] / c0 - 1) <= 1e-12
+
+
+def test_3d_fp32_drift_and_bounded_error():
+    n = 32
+    o, sim = pair((n, n, n), [(10.0, 12.0, 16.0), (24.0, 20.0, 8.0)], 7.0, "fp32")
+    c0 = sim.reduce()["sum_C"]
+    o.step(200)
+    sim.step(200)
+    compare(o, sim, 1e-3)
+    assert abs(sim.reduce()["sum_C"] / c0 - 1) <= 1e-6
+
+
+def test_3d_full_size_windows():
+    """The 256^3 workload (64 seeds) in the benchmark's launch configuration:
+    after 2 steps, 24^3 windows around seeds and across the periodic corner
+    match oracle windows placed in global coordinates."""
+    n = 256
+    seeds, R_s = wl.growth_3d(n)
+    sim = pf.Simulation3D((n, n, n), wl.BASE_PARAMS, "fp32")
+    sim.init_seeds(seeds, R_s)
+    T = 2
+    sim.step(T)
+    fg = sim.fields()
+    sim.close()
+    W, M = 24, 2 * T
+    centres = [(int(s[0]) + 7, int(s[1]), int(s[2])) for s in seeds[:3]] + [(n - 2, n - 2, n - 2)]
+    ref, got = {k: [] for k in fg}, {k: [] for k in fg}
+    for cx, cy, cz in centres:
+        x0, y0, z0 = cx - W // 2, cy - W // 2, cz - W // 2
+        o = oracle.Oracle3D(W, W, W, P3, window=(n, n, n, x0, y0, z0))
+        o.init_spec(seeds, R_s)
+        o.step(T)
+        fo = o.fields()
+        idx = [(np.arange(M, W - M) + c0) % n for c0 in (z0, y0, x0)]
+        for k in fo:
+            ref[k].append(fo[k][M:W - M, M:W - M, M:W - M].ravel())
+            got[k].append(fg[k][np.ix_(*idx)].ravel())
+    for k in fg:
+        err = rel(np.concatenate(got[k]), np.concatenate(ref[k]), FLOOR[k])
+        assert err <= 1e-5, (k, err)
+
+
+def test_3d_configuration_errors():
+    with pytest.raises(pf.PFError):
+        pf.Simulation3D((3, 8, 8), wl.BASE_PARAMS, "fp32")
+    with pytest.raises(pf.PFError):
+        pf.Simulation3D((8, 8, 8), wl.BASE_PARAMS, "fp16")
+    sim = pf.Simulation3D((8, 8, 8), wl.BASE_PARAMS, "fp32")
+    with pytest.raises(pf.PFError) as e:
+        sim.step(1)                        # not initialised
+    assert e.value.code == pf.PF_ERR_STATE
