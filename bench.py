@@ -388,7 +388,7 @@ def run_bounded(args) -> None:
 
 def run_3d(args) -> None:
     """The 3-D dendrite step (psi and C on D3Q7, no gas or flow) on a periodic
-    256^3 melt with 64 seeds: MLUPS and the HBM roofline at 185 B/LU (FP32: 23
+    256^3 melt with 64 seeds: MLUPS and the HBM roofline at 184 B/LU (FP32: 23
     planes read and written, g_pre[7], g_post[7], r, s[7], Q_psi)."""
     import torch
 
