@@ -192,6 +192,54 @@ print(json.dumps(dict(side=side, steps={steps_hint}, seconds=dt)))
                       f"OpenMP over rows"}
 
 
+def cpu_oracle_variant(kind: str, steps: int = 0) -> dict:
+    """Time the FP64 oracle (a child process, all host cores) on a bounded
+    sample of a variant workload: 'thermal' (a 768^2 window of the thermal
+    4096^2 lattice), 'bounded' (a 768^2 lattice of the same recipe with the
+    Section-4 sides, thermal), '3d' (a 96^3 melt with 8 seeds)."""
+    cores = os.cpu_count() or 1
+    steps = steps or {"thermal": 60, "bounded": 60, "3d": 120}[kind]   # about 10 s of CPU work
+    code = f"""
+import json, sys, time
+sys.path.insert(0, {ROOT!r})
+import oracle
+from paper_2407_01651_gb300 import workload as wl
+kind = {kind!r}
+if kind == "3d":
+    n = 96
+    seeds, R_s = wl.growth_3d(n, 8)
+    p = {{k: wl.BASE_PARAMS[k] for k in oracle.PARAM_NAMES_3D}}
+    o = oracle.Oracle3D(n, n, n, p)
+    o.init_spec(seeds, R_s)
+    sites, what = n ** 3, f"{{n}}^3 melt with 8 seeds (3-D oracle)"
+else:
+    lay = wl.growth_lattice()
+    par = dict(lay.params, **wl.THERMAL_PARAMS)
+    s = 768
+    if kind == "thermal":
+        o = oracle.Oracle(s, s, par, window=(lay.nx, lay.ny, 1024, 1024))
+        what = f"{{s}}x{{s}} window of the thermal 4096^2 layout"
+    else:
+        lay = wl.random_layout(s, s, 3, 6, rng_seed=2)
+        o = oracle.Oracle(s, s, par)
+        o.set_bc(1, 1, 2, 3)
+        what = f"{{s}}x{{s}} lattice, 3 seeds, 6 bubbles, Section-4 sides, thermal"
+    o.init_spec(lay.seeds, lay.R_s, lay.bubbles)
+    sites = s * s
+o.step(1)
+t = time.perf_counter(); o.step({steps}); dt = time.perf_counter() - t
+print(json.dumps(dict(sites=sites, steps={steps}, seconds=dt, what=what)))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS=str(cores))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         check=True)
+    rec = json.loads(out.stdout.strip().splitlines()[-1])
+    return {"value": rec["sites"] * rec["steps"] / rec["seconds"] / 1e6, "unit": "MLUPS",
+            "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle, {rec['what']}, {rec['steps']} steps in "
+                      f"{rec['seconds']:.1f} s, OpenMP over rows"}
+
+
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -383,7 +431,8 @@ def run_bounded(args) -> None:
                      "unit": "GB/s", "frac": b["algorithmic_gbs"] / peak, "traffic": None,
                      "peak_kind": peak_kind, "bytes_per_lu": bpl,
                      "kernel": "k_step_ymarch_bc<thermal> (one launch per step)"},
-        "modes": res, "gpu_launches": b["gpu_launches"]}))
+        "modes": res, "gpu_launches": b["gpu_launches"],
+        "cpu_baseline": None if args.no_cpu_baseline else cpu_oracle_variant("bounded")}))
 
 
 def run_3d(args) -> None:
@@ -432,7 +481,8 @@ def run_3d(args) -> None:
                      "bytes_per_lu": bpl, "kernel": "k_step3d (one launch per step)"},
         "sum_C_rel_drift": d["sum_C"] / d0["sum_C"] - 1.0,
         "solid_fraction": d["sum_hpsi"] / sites,
-        "gpu_launches": sim.launches - l0}))
+        "gpu_launches": sim.launches - l0,
+        "cpu_baseline": None if args.no_cpu_baseline else cpu_oracle_variant("3d")}))
     sim.close()
 
 
@@ -493,6 +543,7 @@ def run_thermal(args) -> None:
                      "bytes_per_lu": th["bytes_per_lu"],
                      "kernel": "k_step_ymarch<thermal> (one launch per step)"},
         "modes": res, "thermal_cost_vs_isothermal": res["isothermal"]["mlups"] / th["mlups"],
+        "cpu_baseline": None if args.no_cpu_baseline else cpu_oracle_variant("thermal"),
         "gpu_launches": th["gpu_launches"]}))
 
 
