@@ -328,7 +328,7 @@ def stencil(X, x, y):
 
 # -- the three-dimensional dendrite oracle (pf_oracle3d.c) ---------------------
 PARAM_NAMES_3D = ("beta_psi", "W0", "tau0", "eps_s", "k", "D", "Omega", "grad_eps",
-                  "grad_eps_at")
+                  "grad_eps_at", "thermal", "Le", "latent", "theta0", "cp", "rho_l")
 _lib3 = None
 
 
@@ -352,6 +352,10 @@ def _l3() -> ctypes.CDLL:
             lib.or3_collide7.argtypes = [D] * 6
             lib.or3_grad.argtypes = [D, I, I, I, I, I, I, D]
             lib.or3_set_window.argtypes = [P, I, I, I, I, I, I]
+            lib.or3_init_fields.argtypes = [P, D, D, D]
+            lib.or3_state_planes.restype = I
+            lib.or3_state_planes.argtypes = [P]
+            lib.or3_thermal_totals.argtypes = [P, D]
             _lib3 = lib
     return _lib3
 
@@ -366,7 +370,8 @@ class Oracle3D:
         self.h = self.lib.or3_new(int(nx), int(ny), int(nz))
         if not self.h:
             raise MemoryError("oracle allocation failed")
-        pv = _f64([float(params[k]) for k in PARAM_NAMES_3D])
+        dflt = dict(THERMAL_DEFAULTS, rho_l=1.0)
+        pv = _f64([float(params[k] if k in params else dflt[k]) for k in PARAM_NAMES_3D])
         self.lib.or3_set_params(self.h, _dp(pv))
         if window is not None:           # (NX, NY, NZ, x0, y0, z0)
             self.lib.or3_set_window(self.h, *[int(v) for v in window])
@@ -381,23 +386,30 @@ class Oracle3D:
         s = np.ascontiguousarray(_f64(seeds).reshape(-1, 3))
         self.lib.or3_init(self.h, _dp(s), len(s), float(R_s))
 
-    def init_fields(self, psi, C) -> None:
-        self._keep = [_f64(psi).ravel(), _f64(C).ravel()]
+    def init_fields(self, psi, C, theta=None) -> None:
+        self._keep = [_f64(psi).ravel(), _f64(C).ravel(),
+                      None if theta is None else _f64(theta).ravel()]
         self.lib.or3_init_fields(self.h, *[_dp(a) for a in self._keep])
 
     def step(self, n: int = 1) -> None:
         self.lib.or3_step(self.h, int(n))
 
     def fields(self) -> dict:
-        out = np.empty(3 * int(np.prod(self.shape)))
+        out = np.empty(4 * int(np.prod(self.shape)))
         self.lib.or3_fields(self.h, _dp(out))
-        out = out.reshape((3,) + self.shape)
-        return {"psi": out[0], "C": out[1], "U": out[2]}
+        out = out.reshape((4,) + self.shape)
+        return {"psi": out[0], "C": out[1], "U": out[2], "theta": out[3]}
 
     def state(self) -> np.ndarray:
-        out = np.empty(23 * int(np.prod(self.shape)))
+        npl = self.lib.or3_state_planes(self.h)
+        out = np.empty(npl * int(np.prod(self.shape)))
         self.lib.or3_state(self.h, _dp(out))
-        return out.reshape((23,) + self.shape)
+        return out.reshape((npl,) + self.shape)
+
+    def thermal_totals(self) -> dict:
+        out = np.zeros(2)
+        self.lib.or3_thermal_totals(self.h, _dp(out))
+        return {"sum_e": out[0], "sum_theta": out[1]}
 
 
 def aniso3(g, eps, geps=1e-3):

@@ -71,7 +71,9 @@ static void build_n18(void) {
 
 /* Parameters (same symbols as the 2-D oracle). */
 enum { Q_BETA_PSI, Q_W0, Q_TAU0, Q_EPS_S, Q_K, Q_D, Q_OMEGA, Q_GRAD_EPS, Q_GRAD_EPS_AT,
-       NPAR3 };
+       /* temperature coupling (as in 2-D, readings R28-R30): thermal 0/1, Le,
+        * latent = c_p^s/c_p, theta0, c_p; rho = rho_l (no gas) */
+       Q_THERMAL, Q_LE, Q_LATENT, Q_THETA0, Q_CP, Q_RHO_L, NPAR3 };
 
 typedef struct {
   int nx, ny, nz, n;
@@ -81,7 +83,8 @@ typedef struct {
   real *gpre[7], *gpost[7], *rr, *s[7], *Q_o;      /* state */
   real *ngpre[7], *ngpost[7], *nrr, *ns[7], *nQ_o; /* next state */
   real *psiS, *CS, *psiOld, *gS[7], *sS[7];        /* streaming scratch */
-  real *fld[3];                                     /* psi, C, U of the last step */
+  real *e[7], *ne[7], *eS[7], *US;                  /* temperature populations (thermal) */
+  real *fld[4];                                     /* psi, C, U, theta of the last step */
   real *block;
 } o3state;
 
@@ -98,7 +101,7 @@ o3state *or3_new(int nx, int ny, int nz) {
   if (!st) return NULL;
   st->nx = nx; st->ny = ny; st->nz = nz; st->n = nx * ny * nz;
   st->NX = nx; st->NY = ny; st->NZ = nz;
-  const size_t n = (size_t)st->n, planes = 2 * (7 + 7 + 1 + 7 + 1) + 3 + 14 + 3;
+  const size_t n = (size_t)st->n, planes = 2 * (7 + 7 + 1 + 7 + 1) + 3 + 14 + 4 + 22;
   st->block = (real *)calloc(planes * n, sizeof(real));
   if (!st->block) { free(st); return NULL; }
   real *q = st->block;
@@ -109,7 +112,9 @@ o3state *or3_new(int nx, int ny, int nz) {
   TAKE(st->nrr); TAKE(st->nQ_o);
   TAKE(st->psiS); TAKE(st->CS); TAKE(st->psiOld);
   for (int i = 0; i < 7; ++i) { TAKE(st->gS[i]); TAKE(st->sS[i]); }
-  for (int f = 0; f < 3; ++f) TAKE(st->fld[f]);
+  for (int i = 0; i < 7; ++i) { TAKE(st->e[i]); TAKE(st->ne[i]); TAKE(st->eS[i]); }
+  TAKE(st->US);
+  for (int f = 0; f < 4; ++f) TAKE(st->fld[f]);
 #undef TAKE
   return st;
 }
@@ -145,12 +150,47 @@ static double supersat3(const o3state *st, double C, double psi) {
   return (2.0 * C / (1.0 + k - (1.0 - k) * psi) - 1.0) / (1.0 - k);
 }
 
-/* Q_psi with phi = 1 (no interaction with gas) */
-static double qpsi3(const o3state *st, double psi, double U) {
+/* Q_psi with phi = 1 (no interaction with gas), at temperature theta */
+static double qpsi3_at(const o3state *st, double psi, double U, double theta) {
   double lam, Mc, th;
   derived3(st, &lam, &Mc, &th);
   const double om = 1.0 - psi * psi;
-  return 4.0 * st->par[Q_BETA_PSI] * psi * om - lam * om * om * (th + Mc * U);
+  return 4.0 * st->par[Q_BETA_PSI] * psi * om - lam * om * om * (theta + Mc * U);
+}
+
+/* isothermal: theta = theta_sys (Eq. eq-Tsys) */
+static double qpsi3(const o3state *st, double psi, double U) {
+  double lam, Mc, th;
+  derived3(st, &lam, &Mc, &th);
+  return qpsi3_at(st, psi, U, th);
+}
+
+static int thermal3(const o3state *st) { return st->par[Q_THERMAL] != 0.0; }
+
+/* F(U) = 1/Le + M c_inf [1 + (1-k) U] (Section 2.1) */
+static double f_of_u3(const o3state *st, double U) {
+  double lam, Mc, th;
+  derived3(st, &lam, &Mc, &th);
+  return 1.0 / st->par[Q_LE] + Mc * (1.0 + (1.0 - st->par[Q_K]) * U);
+}
+
+/* Temperature equilibrium on D3Q7 at rest (no flow): e_0 = rho H + (w_0 - 1)
+ * theta, e_i = w_i theta (Appendix B). */
+static void teq3(double rhoH, double theta, real out[7]) {
+  for (int i = 0; i < 7; ++i) out[i] = W7[i] * theta;
+  out[0] = rhoH + (W7[0] - 1.0) * theta;
+}
+
+/* thermal initial populations and lagged source at theta */
+static void init_thermal_site(o3state *st, int id, double psi, double C, double theta) {
+  const double *p = st->par;
+  const double H = p[Q_CP] * (theta - p[Q_LATENT] * 0.5 * (1.0 + psi));
+  real t[7];
+  teq3(p[Q_RHO_L] * H, theta, t);
+  for (int i = 0; i < 7; ++i) st->e[i][id] = t[i];
+  const double U = supersat3(st, C, psi);
+  st->Q_o[id] = qpsi3_at(st, psi, U, theta) / f_of_u3(st, U);
+  st->fld[3][id] = theta;
 }
 
 /* Anisotropy in 3-D (Section 2.1, sum over alpha = 1..3), the same regularised
@@ -229,12 +269,17 @@ void or3_init(o3state *st, const double *seeds, int n_seeds, double R_s) {
         const double U = supersat3(st, C, psi);
         st->Q_o[id] = qpsi3(st, psi, U);
         st->fld[0][id] = psi; st->fld[1][id] = C; st->fld[2][id] = U;
+        double lam, Mc, th;
+        derived3(st, &lam, &Mc, &th);
+        st->fld[3][id] = th;
+        if (thermal3(st)) init_thermal_site(st, id, psi, C, p[Q_THETA0]);
       }
   st->steps = 0;
 }
 
-/* Initial state from given psi and C fields (n each). */
-void or3_init_fields(o3state *st, const double *psi, const double *C) {
+/* Initial state from given psi and C fields (n each) and, in thermal mode,
+ * theta (NULL: theta0). */
+void or3_init_fields(o3state *st, const double *psi, const double *C, const double *theta) {
   for (int id = 0; id < st->n; ++id) {
     for (int i = 0; i < 7; ++i) {
       st->gpre[i][id] = st->gpost[i][id] = W7[i] * psi[id];
@@ -244,6 +289,11 @@ void or3_init_fields(o3state *st, const double *psi, const double *C) {
     const double U = supersat3(st, C[id], psi[id]);
     st->Q_o[id] = qpsi3(st, psi[id], U);
     st->fld[0][id] = psi[id]; st->fld[1][id] = C[id]; st->fld[2][id] = U;
+    double lam, Mc, th;
+    derived3(st, &lam, &Mc, &th);
+    st->fld[3][id] = th;
+    if (thermal3(st))
+      init_thermal_site(st, id, psi[id], C[id], theta ? theta[id] : st->par[Q_THETA0]);
   }
   st->steps = 0;
 }
@@ -269,6 +319,10 @@ static void step3(o3state *st) {
           C += st->sS[i][id];
         }
         st->psiS[id] = psi; st->psiOld[id] = psio; st->CS[id] = C;
+        st->US[id] = supersat3(st, C, psi);
+        if (thermal3(st))
+          for (int i = 0; i < 7; ++i)
+            st->eS[i][id] = st->e[i][idx3(st, x - C7[i][0], y - C7[i][1], z - C7[i][2])];
       }
   /* pass 2: gradient, anisotropy, sources, collisions */
 #pragma omp parallel for schedule(static)
@@ -287,7 +341,33 @@ static void step3(o3state *st) {
         aniso3(g, eps, p[Q_GRAD_EPS], &as, N, &gm);
         const double as2 = as * as;
         const double U = supersat3(st, C, psi);
-        const double Q = qpsi3(st, psi, U);
+        /* temperature (thermal mode): rho H = sum e, theta = H / c_p + L h(psi) */
+        const int th_on = thermal3(st);
+        double rhoH = 0.0, theta = 0.0, Fu = 1.0, Qeff;
+        if (th_on) {
+          for (int i = 0; i < 7; ++i) rhoH += st->eS[i][id];
+          theta = rhoH / (p[Q_RHO_L] * p[Q_CP]) + p[Q_LATENT] * 0.5 * (1.0 + psi);
+        }
+        const double Q = th_on ? qpsi3_at(st, psi, U, theta) : qpsi3(st, psi, U);
+        Qeff = Q;
+        if (th_on) {
+          /* rewritten dendrite equation of Appendix B: source Q/F + W0^2/F^2
+           * grad F . (a_s^2 grad psi + N), grad F = M c_inf (1-k) grad U */
+          double lam, Mc, thsys;
+          derived3(st, &lam, &Mc, &thsys);
+          double gu[3] = {0, 0, 0};
+          for (int q = 0; q < 18; ++q) {
+            const real v = st->US[idx3(st, x + N18[q][0], y + N18[q][1], z + N18[q][2])];
+            for (int a2 = 0; a2 < 3; ++a2) gu[a2] += WN18[q] * N18[q][a2] * v;
+          }
+          double dot = 0;
+          for (int a2 = 0; a2 < 3; ++a2) {
+            gu[a2] /= (1.0 / 3.0);
+            dot += Mc * (1.0 - k) * gu[a2] * (as2 * g[a2] + N[a2]);
+          }
+          Fu = f_of_u3(st, U);
+          Qeff = Q / Fu + W0 * W0 / (Fu * Fu) * dot;
+        }
         /* antitrapping with the direction's own regularisation (reading R6b) */
         const double at = -(1.0 / (2.0 * sqrt(2.0))) * W0 * as * (1.0 + (1.0 - k) * U) *
                           (psi - psio) /
@@ -300,9 +380,10 @@ static void step3(o3state *st) {
             gg[i] = st->gS[i][id];
             geq[i] = W7[i] * psi;
             G[i] = -W7[i] * (C7[i][0] * N[0] + C7[i][1] * N[1] + C7[i][2] * N[2]) / as2;
-            Fd[i] = W7[i] * Q / tau0 + 0.5 * W7[i] * (Q - st->Q_o[id]) / tau0;
+            Fd[i] = W7[i] * Qeff / tau0 + 0.5 * W7[i] * (Qeff - st->Q_o[id]) / tau0;
           }
-          const double s1 = 1.0 / (W0 * W0 * as2 / (tau0 * CS2_7) + 0.5);
+          const double s1 = th_on ? 1.0 / (W0 * W0 * as2 / (tau0 * Fu * CS2_7) + 0.5)
+                                  : 1.0 / (W0 * W0 * as2 / (tau0 * CS2_7) + 0.5);
           const real S[7] = {1, s1, s1, s1, 1, 1, 1};
           collide7(gg, geq, S, G, Fd, out);
           for (int i = 0; i < 7; ++i) { st->ngpost[i][id] = out[i]; st->ngpre[i][id] = gg[i]; }
@@ -328,13 +409,28 @@ static void step3(o3state *st) {
           collide7(ss, seq, S, G, Fd, out);
           for (int i = 0; i < 7; ++i) st->ns[i][id] = out[i];
         }
-        st->nQ_o[id] = Q;
+        /* temperature collision (D3Q7, no flow): flux rate from
+         * k_T = Le D rho_l c_p = (1/s - 1/2) c_s^2, other moments at 1 */
+        if (th_on) {
+          real ee[7], teq[7], G0[7] = {0, 0, 0, 0, 0, 0, 0}, out[7];
+          teq3(rhoH, theta, teq);
+          for (int i = 0; i < 7; ++i) ee[i] = st->eS[i][id];
+          const double kT = p[Q_LE] * p[Q_D] * p[Q_RHO_L] * p[Q_CP];
+          const double sth = 1.0 / (kT / CS2_7 + 0.5);
+          const real S[7] = {1, sth, sth, sth, 1, 1, 1};
+          collide7(ee, teq, S, G0, G0, out);
+          for (int i = 0; i < 7; ++i) st->ne[i][id] = out[i];
+          st->fld[3][id] = theta;
+        }
+        st->nQ_o[id] = Qeff;
         st->fld[0][id] = psi; st->fld[1][id] = C; st->fld[2][id] = U;
       }
   real *t;
 #define SW(a, b) do { t = (a); (a) = (b); (b) = t; } while (0)
   for (int i = 0; i < 7; ++i) { SW(st->gpre[i], st->ngpre[i]); SW(st->gpost[i], st->ngpost[i]); SW(st->s[i], st->ns[i]); }
   SW(st->rr, st->nrr); SW(st->Q_o, st->nQ_o);
+  if (thermal3(st))
+    for (int i = 0; i < 7; ++i) SW(st->e[i], st->ne[i]);
 #undef SW
   st->steps++;
 }
@@ -343,21 +439,42 @@ void or3_step(o3state *st, int n) {
   for (int t = 0; t < n; ++t) step3(st);
 }
 
-/* Fields psi, C, U of the last step, field-major (3 x n). */
+/* Fields psi, C, U, theta of the last step, field-major (4 x n). */
 void or3_fields(const o3state *st, double *out) {
-  for (int f = 0; f < 3; ++f) memcpy(out + (size_t)f * st->n, st->fld[f], st->n * sizeof(double));
+  for (int f = 0; f < 4; ++f) memcpy(out + (size_t)f * st->n, st->fld[f], st->n * sizeof(double));
 }
 
-/* Raw state: g_pre[7], g_post[7], r, s[7], Q_o (23 planes). */
+/* Sum over sites of the temperature populations (total rho H) and of theta,
+ * compensated (Neumaier). */
+void or3_thermal_totals(const o3state *st, double *out) {
+  double s[2] = {0, 0}, c[2] = {0, 0};
+  for (int id = 0; id < st->n; ++id)
+    for (int k2 = 0; k2 < 8; ++k2) {
+      const double v = k2 < 7 ? st->e[k2][id] : st->fld[3][id];
+      const int j = k2 < 7 ? 0 : 1;
+      const double t = s[j] + v;
+      c[j] += fabs(s[j]) >= fabs(v) ? (s[j] - t) + v : (v - t) + s[j];
+      s[j] = t;
+    }
+  out[0] = s[0] + c[0];
+  out[1] = s[1] + c[1];
+}
+
+/* Raw state: g_pre[7], g_post[7], r, s[7], Q_o (23 planes), then in thermal
+ * mode e[7] (30 planes). */
+int or3_state_planes(const o3state *st) { return thermal3(st) ? 30 : 23; }
+
 void or3_state(const o3state *st, double *out) {
-  const real *pl[23];
+  const real *pl[30];
   int q = 0;
   for (int i = 0; i < 7; ++i) pl[q++] = st->gpre[i];
   for (int i = 0; i < 7; ++i) pl[q++] = st->gpost[i];
   pl[q++] = st->rr;
   for (int i = 0; i < 7; ++i) pl[q++] = st->s[i];
   pl[q++] = st->Q_o;
-  for (int p = 0; p < 23; ++p) memcpy(out + (size_t)p * st->n, pl[p], st->n * sizeof(double));
+  if (thermal3(st))
+    for (int i = 0; i < 7; ++i) pl[q++] = st->e[i];
+  for (int p = 0; p < q; ++p) memcpy(out + (size_t)p * st->n, pl[p], st->n * sizeof(double));
 }
 
 /* Pointwise pieces for the pin tests. */

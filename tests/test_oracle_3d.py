@@ -143,3 +143,76 @@ def test_flat_fronts_have_the_3d_anisotropic_widths():
     assert math.isclose(w110, math.sqrt(2) * W0 * (1 - eps), rel_tol=0.02)
     assert math.isclose(w100 / w110, (1 + eps) / (1 - eps), rel_tol=0.02)
     assert not math.isclose(w100 / w110, 1.0, rel_tol=0.05)    # anisotropy is there
+
+
+# ---------------------------------------------------------------------------
+# temperature coupling in 3-D (thermal mode: D3Q7 temperature lattice, F(U)
+# and the grad F source of Appendix B; readings R28-R30, R33)
+# ---------------------------------------------------------------------------
+T3 = dict(P3, thermal=1, Le=2.0, latent=1.0, theta0=-0.55, cp=10.0, rho_l=1.0)
+
+
+def test_3d_enthalpy_conserved_and_latent_heat_balance():
+    """sum rho H is constant, and the mean temperature rises by (c_p^s/c_p)/2
+    times the rise of the mean psi while a seed solidifies (Eq. eq-tem2)."""
+    n = 28
+    for latent in (1.0, 0.5):
+        o = oracle.Oracle3D(n, n, n, dict(T3, latent=latent))
+        o.init_spec([(n / 2, n / 2, n / 2)], 8.0)
+        t0, f0 = o.thermal_totals(), o.fields()
+        o.step(150)
+        t1, f1 = o.thermal_totals(), o.fields()
+        assert abs(t1["sum_e"] / t0["sum_e"] - 1) < 1e-13
+        dpsi = (f1["psi"].sum() - f0["psi"].sum()) / n ** 3
+        dth = (t1["sum_theta"] - t0["sum_theta"]) / n ** 3
+        assert dpsi > 0.05 and math.isclose(dth, 0.5 * latent * dpsi, rel_tol=1e-9)
+
+
+def test_3d_heat_gaussian_variance():
+    """In the liquid the temperature diffuses with alpha = Le D: a 3-D
+    Gaussian's variance grows 2 alpha per step per axis."""
+    m, Le = 56, 1.5
+    z, y, x = np.mgrid[0:m, 0:m, 0:m].astype(float)
+    th = -0.5 + 0.1 * np.exp(-((x - 28) ** 2 + (y - 28) ** 2 + (z - 28) ** 2) / 18.0)
+    o = oracle.Oracle3D(m, m, m, dict(T3, Le=Le, theta0=-0.5))
+    o.init_fields(-np.ones_like(th), np.ones_like(th), th)
+    var = []
+    for T in (40, 100):
+        o.step(T - (0 if T == 40 else 40))
+        w = o.fields()["theta"] + 0.5
+        var.append([((q - 28) ** 2 * w).sum() / w.sum() for q in (x, y, z)])
+    for a in range(3):
+        assert math.isclose((var[1][a] - var[0][a]) / 60.0, 2 * Le * T3["D"], rel_tol=3e-3)
+
+
+def test_3d_gradF_source_matches_the_original_equation():
+    """The planar problem of the 2-D grad F pin on a 192 x 4 x 4 lattice: the
+    3-D scheme (D3Q7) follows the finite-difference solution of the original
+    equations far better than that solution differs from the one without the
+    grad F source."""
+    from test_oracle_thermal import _fd_1d
+    nx, W0 = 192, 8.0
+    base = dict(beta_psi=0.25, W0=W0, tau0=2 * W0 ** 2 / 0.1, eps_s=0.0, k=0.15, D=0.1,
+                Omega=0.55, grad_eps=1e-3, grad_eps_at=1e-2, thermal=1, Le=50.0, latent=1.0,
+                theta0=-0.3, cp=10.0, rho_l=1.0)
+    k = base["k"]
+    x = np.arange(nx, dtype=float)
+    psi0 = np.tanh(math.sqrt(0.5) * (nx / 6 - np.abs(x - nx / 2)) / W0)
+    U0 = 0.5 * np.sin(4 * math.pi * x / nx)
+    C0 = 0.5 * (1 + k - (1 - k) * psi0) * (1 + (1 - k) * U0)
+    th0 = np.full(nx, base["theta0"])
+    T = 1200
+    o = oracle.Oracle3D(nx, 4, 4, base)
+    tile = lambda a: np.tile(a, (4, 4, 1))          # noqa: E731  [z][y][x]
+    o.init_fields(tile(psi0), tile(C0), tile(th0))
+    o.step(T)
+    f = o.fields()
+    for a in ("psi", "C", "theta"):
+        assert np.abs(f[a] - f[a][0, 0]).max() < 1e-13          # planar
+    psi_fd, C_fd, th_fd = _fd_1d(base, psi0, C0, th0, T, 0.05, 1.0)
+    psi_no, _, _ = _fd_1d(base, psi0, C0, th0, T, 0.05, 0.0)
+    effect = np.abs(psi_fd - psi_no).max()
+    assert effect > 0.03
+    assert np.abs(f["psi"][0, 0] - psi_fd).max() < 0.15 * effect
+    assert np.abs(f["C"][0, 0] - C_fd).max() < 0.01
+    assert np.abs(f["theta"][0, 0] - th_fd).max() < 0.01
