@@ -196,22 +196,26 @@ def cpu_oracle_variant(kind: str, steps: int = 0) -> dict:
     """Time the FP64 oracle (a child process, all host cores) on a bounded
     sample of a variant workload: 'thermal' (a 768^2 window of the thermal
     4096^2 lattice), 'bounded' (a 768^2 lattice of the same recipe with the
-    Section-4 sides, thermal), '3d' (a 96^3 melt with 8 seeds)."""
+    Section-4 sides, thermal), '3d' (a 96^3 melt with 8 seeds), '3d_thermal'
+    (the same with the temperature lattice)."""
     cores = os.cpu_count() or 1
-    steps = steps or {"thermal": 60, "bounded": 60, "3d": 120}[kind]   # about 10 s of CPU work
+    steps = steps or {"thermal": 60, "bounded": 60, "3d": 120, "3d_thermal": 300}[kind]  # ~10 s CPU
     code = f"""
 import json, sys, time
 sys.path.insert(0, {ROOT!r})
 import oracle
 from paper_2407_01651_gb300 import workload as wl
 kind = {kind!r}
-if kind == "3d":
+if kind in ("3d", "3d_thermal"):
     n = 96
     seeds, R_s = wl.growth_3d(n, 8)
     p = {{k: wl.BASE_PARAMS[k] for k in oracle.PARAM_NAMES_3D}}
+    if kind == "3d_thermal":
+        p.update(wl.THERMAL_PARAMS)
     o = oracle.Oracle3D(n, n, n, p)
     o.init_spec(seeds, R_s)
-    sites, what = n ** 3, f"{{n}}^3 melt with 8 seeds (3-D oracle)"
+    sites = n ** 3
+    what = f"{{n}}^3 melt with 8 seeds (3-D oracle{{', thermal' if p['thermal'] else ''}})"
 else:
     lay = wl.growth_lattice()
     par = dict(lay.params, **wl.THERMAL_PARAMS)
@@ -438,7 +442,8 @@ def run_bounded(args) -> None:
 def run_3d(args) -> None:
     """The 3-D dendrite step (psi and C on D3Q7, no gas or flow) on a periodic
     256^3 melt with 64 seeds: MLUPS and the HBM roofline at 184 B/LU (FP32: 23
-    planes read and written, g_pre[7], g_post[7], r, s[7], Q_psi)."""
+    planes read and written, g_pre[7], g_post[7], r, s[7], Q_psi); with the
+    temperature lattice ('3d_thermal') 240 B/LU (30 planes, e[7] added)."""
     import torch
 
     from paper_2407_01651_gb300 import pf
@@ -449,11 +454,14 @@ def run_3d(args) -> None:
     seeds, R_s = wl.growth_3d(n)
     stream = torch.cuda.current_stream()
     prec = args.precision if args.precision in ("fp32", "fp64") else "fp32"
-    sim = pf.Simulation3D((n, n, n), wl.BASE_PARAMS, prec, stream=stream.cuda_stream)
+    thermal = args.workload == "3d_thermal"
+    params = dict(wl.BASE_PARAMS, **wl.THERMAL_PARAMS) if thermal else wl.BASE_PARAMS
+    sim = pf.Simulation3D((n, n, n), params, prec, stream=stream.cuda_stream)
     sim.init_seeds(seeds, R_s)
     if args.chunk:
         sim.set_chunk(args.chunk)
     d0 = sim.reduce()
+    t0 = sim.reduce_thermal() if thermal else None
     sim.step(args.warmup)
     l0 = sim.launches
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -465,24 +473,33 @@ def run_3d(args) -> None:
     ms = e0.elapsed_time(e1)
     d = sim.reduce()
     sites = n ** 3
-    bpl = 23 * 2 * (4 if prec == "fp32" else 8)
+    planes = 30 if thermal else 23
+    bpl = planes * 2 * (4 if prec == "fp32" else 8)
     gbs = bpl * sites * args.steps / ms / 1e6
     peak, peak_kind = measured_peaks()
+    extra = {}
+    if thermal:
+        t1 = sim.reduce_thermal()
+        extra = {"sum_rhoH_rel_drift": t1["sum_e"] / t0["sum_e"] - 1.0,
+                 "mean_theta": t1["sum_theta"] / sites}
     print(json.dumps({
-        "metric": "3-D dendrite-step MLUPS at 256³ and % of HBM roofline",
+        "metric": ("3-D thermal dendrite-step" if thermal else "3-D dendrite-step") +
+                  " MLUPS at 256³ and % of HBM roofline",
         "value": sites * args.steps / ms / 1e3, "unit": "MLUPS", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPE[prec], "data": "synthetic",
-        "config": {"workload": f"{n}^3 periodic melt, 64 seeds (R=8) at uniform positions, seed 4",
+        "config": {"workload": f"{n}^3 periodic melt, 64 seeds (R=8) at uniform positions, seed 4"
+                               + (", temperature lattice (Le 50, theta0 -0.55)" if thermal else ""),
                    "lattice": [n, n, n], "precision": prec},
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                      "frac": gbs / peak, "traffic": None, "peak_kind": peak_kind,
                      "bytes_per_lu": bpl, "kernel": "k_step3d (one launch per step)"},
         "sum_C_rel_drift": d["sum_C"] / d0["sum_C"] - 1.0,
-        "solid_fraction": d["sum_hpsi"] / sites,
+        "solid_fraction": d["sum_hpsi"] / sites, **extra,
         "gpu_launches": sim.launches - l0,
-        "cpu_baseline": None if args.no_cpu_baseline else cpu_oracle_variant("3d")}))
+        "cpu_baseline": None if args.no_cpu_baseline else
+        cpu_oracle_variant("3d_thermal" if thermal else "3d")}))
     sim.close()
 
 
@@ -559,12 +576,14 @@ def main() -> None:
     ap.add_argument("--chunk", type=int, default=None, help="rows per y-march tile / tile a")
     ap.add_argument("--tile-b", type=int, default=0)
     ap.add_argument("--workload", default="lattice",
-                    choices=("lattice", "ensemble", "precision", "thermal", "bounded", "3d"),
+                    choices=("lattice", "ensemble", "precision", "thermal", "bounded", "3d",
+                             "3d_thermal"),
                     help="lattice: the 4096^2 headline; ensemble: 96 uneven domains; "
                          "precision: 8192x4096 in FP32 / FP16 / BF16 storage; "
                          "thermal: the 4096^2 lattice with the temperature lattice on; "
                          "bounded: the same with the paper's Section-4 boundaries; "
-                         "3d: the 3-D dendrite step on a 256^3 melt")
+                         "3d: the 3-D dendrite step on a 256^3 melt; "
+                         "3d_thermal: the same with the temperature lattice")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -589,7 +608,7 @@ def main() -> None:
     if args.workload == "bounded":
         run_bounded(args)
         return
-    if args.workload == "3d":
+    if args.workload in ("3d", "3d_thermal"):
         run_3d(args)
         return
 

@@ -366,36 +366,60 @@ pf_status pf_reduce_thermal(pf_handle *h, int dom, double out[3]);
  * Appendix B) and C (solute with antitrapping) on D3Q7 lattices (w0 = 1/4,
  * wi = 1/8, c_s^2 = 1/4) in a periodic melt without gas or flow, one grain
  * orientation aligned with the lattice.  Arrays are [z][y][x], x fastest.
- * Uses rho and flow parameters of pf_params not at all; thermal must be 0.
+ * Uses the gas and flow parameters of pf_params not at all.  With thermal = 1
+ * a D3Q7 temperature lattice (Appendix B at rest: e_0 = rho H - (3/4) theta,
+ * e_i = theta/8, k_T = Le D rho_l c_p) is coupled as in 2-D: theta = H / c_p +
+ * latent h(psi) enters Q_psi, F(U) = 1/Le + M c_inf [1 + (1-k) U] scales the
+ * relaxation of psi, and the source gains W0^2/F^2 grad F . (a_s^2 grad psi +
+ * N); Le, latent, theta0, cp and rho_l are read (rho_l cp >= 3/4).
  * ------------------------------------------------------------------------ */
 typedef struct pf3_handle pf3_handle;
 
 /* Raw FP64 state planes of pf3_get_state: g_pre[7], g_post[7], r = 1/a_s^2,
- * s[7], Q_psi of the last step. */
+ * s[7], Q_psi of the last step (Q_psi / F + the grad F term in thermal mode),
+ * then in thermal mode the temperature populations e[7]. */
 #define PF3_STATE_PLANES 23
+#define PF3_STATE_PLANES_THERMAL 30
 
 /* Handle of an nx x ny x nz lattice (each in [4, 4096]), FP32 or FP64
- * storage, on cuda_stream; allocates two state copies (23 planes each) and
- * 3 field planes.  Errors: BAD_ARG, OOM. */
+ * storage, on cuda_stream; allocates two state copies (23 planes each, 30 in
+ * thermal mode) and 3 field planes (4 in thermal mode).  Errors: BAD_ARG, OOM. */
 pf_status pf3_create(const pf_params *p, int nx, int ny, int nz, pf_precision prec,
                      void *cuda_stream, pf3_handle **out);
 /* Spherical seeds n x (x, y, z) of radius R_s: psi = max tanh(sqrt(2 beta_psi)
- * (R_s - r) / W0), C = 1 - (1-k) h(psi), populations at equilibrium.
+ * (R_s - r) / W0), C = 1 - (1-k) h(psi), populations at equilibrium (thermal
+ * mode: temperature populations at rest at theta0, lagged source Q_psi / F).
  * Synchronises.  Errors: BAD_ARG, OOM, CUDA. */
 pf_status pf3_init_seeds(pf3_handle *h, const double *seeds, int n_seeds, double R_s);
 /* Initial psi and C fields (host, n = nx*ny*nz each).  Synchronises. */
 pf_status pf3_set_fields(pf3_handle *h, const double *psi, const double *C, size_t n);
+/* Thermal mode: temperature field theta (host, FP64, n = nx*ny*nz) of the
+ * initial state, after pf3_init_seeds / pf3_set_fields and before the first
+ * step: temperature populations at rest for rho H = rho_l c_p (theta - latent
+ * h(psi)), lagged source Q_psi(theta) / F(U).  Synchronises.  Errors: BAD_ARG
+ * (not thermal, size, non-finite), STATE (not initialised or already stepped),
+ * OOM, CUDA. */
+pf_status pf3_set_temperature(pf3_handle *h, const double *theta, size_t n);
 /* Planes per tile of the z-march (default 16). */
 pf_status pf3_set_chunk(pf3_handle *h, int chunk);
 /* Advance n_steps (enqueued; errors of the launch are reported).
  * Errors: BAD_ARG, STATE, CUDA. */
 pf_status pf3_step(pf3_handle *h, int n_steps);
-/* psi, C, U of the last step (3 planes of n).  Synchronises. */
+/* psi, C, U (and theta in thermal mode) of the last step: pf3_field_planes
+ * planes of n.  Synchronises.  Errors: BAD_ARG (out too small), OOM, CUDA. */
 pf_status pf3_get_fields(pf3_handle *h, double *out, size_t n);
-/* Raw state (PF3_STATE_PLANES planes of n).  Synchronises. */
+/* Raw state (pf3_state_planes planes of n).  Synchronises. */
 pf_status pf3_get_state(pf3_handle *h, double *out, size_t n);
 /* FP64 totals: out[0] = sum C (conserved), out[1] = sum h(psi).  Synchronises. */
 pf_status pf3_reduce(pf3_handle *h, double out[2]);
+/* Thermal mode: FP64 totals out[0] = sum of the seven temperature populations
+ * (rho H, conserved on the periodic cube), out[1] = sum theta, out[2] = sum
+ * psi.  Synchronises.  Errors: BAD_ARG (NULL, not thermal), OOM, CUDA. */
+pf_status pf3_reduce_thermal(pf3_handle *h, double out[3]);
+/* Field planes (3, or 4 in thermal mode) and raw state planes (23 or 30) of
+ * the handle; -1 for NULL. */
+int pf3_field_planes(const pf3_handle *h);
+int pf3_state_planes(const pf3_handle *h);
 /* Kernel launches of the handle; -1 for NULL. */
 long long pf3_launch_count(const pf3_handle *h);
 /* Last error of the handle, or of the last failed pf3_create for NULL. */

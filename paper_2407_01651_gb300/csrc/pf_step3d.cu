@@ -28,10 +28,11 @@ constexpr int HX = TX + 2, HY = TY + 2;           // tile with its halo ring
 constexpr int NIN = TX * TY;                      // 256 interior threads
 constexpr int NHALO = HX * HY - NIN;              // 84 halo threads
 constexpr int THREADS = 352;                      // 11 warps (340 used)
-// planes: g_pre 0..6, g_post 7..13, s 14..20 (storage type); r, Q_o (compute type)
-constexpr int G_PRE = 0, G_POST = 7, S_POP = 14, NPOP3 = 21;
+// planes: g_pre 0..6, g_post 7..13, s 14..20, thermal e 21..27 (storage
+// type); r, Q_o (compute type)
+constexpr int G_PRE = 0, G_POST = 7, S_POP = 14, E_POP = 21, NPOP3 = 21, NPOP3_TH = 28;
 constexpr int A3_RR = 0, A3_QO = 1, NAUX3 = 2;
-constexpr int NSTATE3 = 23;                       // raw FP64 state planes
+constexpr int NSTATE3 = 23, NSTATE3_TH = 30;      // raw FP64 state planes
 
 __device__ __forceinline__ constexpr int cx7(int i) { return i == 1 ? 1 : (i == 2 ? -1 : 0); }
 __device__ __forceinline__ constexpr int cy7(int i) { return i == 3 ? 1 : (i == 4 ? -1 : 0); }
@@ -42,6 +43,8 @@ __device__ __forceinline__ R w7(int i) { return i == 0 ? R(0.25) : R(0.125); }
 template <typename R>
 struct Coef3 {
   R eps, ge2, gat2, four_bpsi, lam, theta, Mcinf, inv_tau0, c4W0sq_tau0, k, inv_omk, D, aW0;
+  // thermal mode: rho_l c_p and its inverse, latent / 2, 1/Le, W0^2, 1 - s_T
+  R rcp, irc, halfL, iLe, W0sq, omsth;
 };
 
 template <typename S, typename R>
@@ -50,7 +53,7 @@ struct Args3 {
   S* out;
   const R* ain;
   R* aout;
-  R* fields;            // psi, C, U planes, or nullptr
+  R* fields;            // psi, C, U (and theta) planes, or nullptr
   unsigned long long ps;
   int nx, ny, nz, chunk;
   int tiles_x, tiles_y, tiles_z;
@@ -67,6 +70,12 @@ __device__ __forceinline__ T* pl(T* p, int k, unsigned long long ps) { return p 
 __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 __device__ __forceinline__ int wrapm(int a, int n) { a %= n; return a < 0 ? a + n : a; }
 
+template <typename S, typename R>
+__device__ __forceinline__ unsigned long long src7(const Args3<S, R>& a, int x, int y, int z, int i) {
+  return ((unsigned long long)wrap1(z - cz7(i), a.nz) * a.ny + wrap1(y - cy7(i), a.ny)) * a.nx +
+         wrap1(x - cx7(i), a.nx);   // x, y in range: one step wraps
+}
+
 // Streamed g at (x, y, z) (time stretch g = g_pre + r_src (g_post,src - g_pre))
 // and psi, psi_o (compensated sums).
 template <typename S, typename R>
@@ -77,9 +86,7 @@ __device__ __forceinline__ void stream_g(const Args3<S, R>& a, int x, int y, int
   R po = R(0);
 #pragma unroll
   for (int i = 0; i < 7; ++i) {
-    const unsigned long long src =
-        ((unsigned long long)wrap1(z - cz7(i), a.nz) * a.ny + wrap1(y - cy7(i), a.ny)) * a.nx +
-        wrap1(x - cx7(i), a.nx);   // x, y in range: one step wraps
+    const unsigned long long src = src7(a, x, y, z, i);
     const R gold = ld<R>(pl(a.in, G_PRE + i, a.ps), own);
     const R gpo = ld<R>(pl(a.in, G_POST + i, a.ps), src);
     const R rr = ld<R>(pl(a.ain, A3_RR, a.ps), src);
@@ -91,9 +98,56 @@ __device__ __forceinline__ void stream_g(const Args3<S, R>& a, int x, int y, int
   psio = po;
 }
 
+// Streamed populations of one D3Q7 lattice (plane base P) at (x, y, z).
 template <typename S, typename R>
+__device__ __forceinline__ void stream7(const Args3<S, R>& a, int P, int x, int y, int z, R f[7]) {
+#pragma unroll
+  for (int i = 0; i < 7; ++i) f[i] = ld<R>(pl(a.in, P + i, a.ps), src7(a, x, y, z, i));
+}
+
+template <typename R>
+__device__ __forceinline__ R sum7(const R f[7]) {
+  CSum<R> cs;
+#pragma unroll
+  for (int i = 0; i < 7; ++i) cs.add(f[i]);
+  return cs.value();
+}
+
+// U = (2C/A - 1)/(1-k), A = 1+k - (1-k) psi (Eq. eq-u with phi = 1)
+template <typename R>
+__device__ __forceinline__ R supersat3(const Coef3<R>& c, R C, R psi) {
+  const R A = (R(1) + c.k) - (R(1) - c.k) * psi;
+  return (R(2) * C * frcp(A) - R(1)) * c.inv_omk;
+}
+
+// 3 sum_q w_q c_q (X(x + c_q) - X(x)) over the 6 face (w = 1/18) and 12 edge
+// (w = 1/36) neighbours of the ring column (hy, hx): the isotropic gradient.
+template <typename R>
+__device__ __forceinline__ void grad18(const R (*Pm)[HX], const R (*P0)[HX], const R (*Pp)[HX],
+                                       int hy, int hx, R& gx, R& gy, R& gz) {
+  const R X0 = P0[hy][hx];
+  auto d = [&](const R (*Pl)[HX], int dx, int dy) { return Pl[hy + dy][hx + dx] - X0; };
+  const R w1 = R(1.0 / 18.0), w2 = R(1.0 / 36.0);
+  gx = w1 * (d(P0, 1, 0) - d(P0, -1, 0)) +
+       w2 * ((d(P0, 1, 1) - d(P0, -1, 1)) + (d(P0, 1, -1) - d(P0, -1, -1)) +
+             (d(Pp, 1, 0) - d(Pp, -1, 0)) + (d(Pm, 1, 0) - d(Pm, -1, 0)));
+  gy = w1 * (d(P0, 0, 1) - d(P0, 0, -1)) +
+       w2 * ((d(P0, 1, 1) - d(P0, 1, -1)) + (d(P0, -1, 1) - d(P0, -1, -1)) +
+             (d(Pp, 0, 1) - d(Pp, 0, -1)) + (d(Pm, 0, 1) - d(Pm, 0, -1)));
+  gz = w1 * (d(Pp, 0, 0) - d(Pm, 0, 0)) +
+       w2 * ((d(Pp, 1, 0) - d(Pm, 1, 0)) + (d(Pp, -1, 0) - d(Pm, -1, 0)) +
+             (d(Pp, 0, 1) - d(Pm, 0, 1)) + (d(Pp, 0, -1) - d(Pm, 0, -1)));
+  gx *= R(3); gy *= R(3); gz *= R(3);
+}
+
+// TH: the temperature lattice of Appendix B on D3Q7 (rho H conserved, theta =
+// H / c_p + (c_p^s/c_p) h(psi)), F(U) = 1/Le + M c_inf [1 + (1-k) U] in the
+// relaxation of psi, and the source Q / F + W0^2 / F^2 grad F . (a_s^2 grad psi
+// + N) with grad F = M c_inf (1-k) grad U; U is kept in a second ring.
+template <typename S, typename R, bool TH>
 __global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R> a) {
   __shared__ R ring[4][HY][HX];
+  __shared__ R uring[TH ? 4 : 1][HY][HX];
   const int t = threadIdx.x;
   // column of this thread within the halo tile
   int hx = 0, hy = 0;
@@ -117,6 +171,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R> a) {
     const int x = wrapm(tx * TX + hx - 1, a.nx), y = wrapm(ty * TY + hy - 1, a.ny);
     const bool mine = interior && tx * TX + hx - 1 < a.nx && ty * TY + hy - 1 < a.ny;
     R gC[7], gL[7], poC = R(0), poL = R(0);
+    R sC[7], sL[7], CC = R(0), CL = R(0);   // TH: streamed s and C carried a plane ahead
     // ring planes za-1 and za
     for (int k = 0; k < 2; ++k) {
       if (active) {
@@ -124,6 +179,17 @@ __global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R> a) {
         R g[7], psi, po;
         stream_g(a, x, y, z, g, psi, po);
         ring[(za - 1 + k) & 3][hy][hx] = psi;
+        if constexpr (TH) {
+          R sv[7];
+          stream7(a, S_POP, x, y, z, sv);
+          const R C = sum7(sv);
+          uring[(za - 1 + k) & 3][hy][hx] = supersat3(a.c, C, psi);
+          if (k == 1) {
+#pragma unroll
+            for (int i = 0; i < 7; ++i) sC[i] = sv[i];
+            CC = C;
+          }
+        }
         if (k == 1) {
 #pragma unroll
           for (int i = 0; i < 7; ++i) gC[i] = g[i];
@@ -132,45 +198,37 @@ __global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R> a) {
       }
     }
     for (int z = za; z < zb; ++z) {
-      // own inputs of plane z: streamed solute populations and the lagged source
-      R sv[7], Qo = R(0);
+      // own inputs of plane z: streamed solute (and temperature) populations
+      // and the lagged source
+      R sv[7], ev[7], Qo = R(0);
       const unsigned long long site = ((unsigned long long)z * a.ny + y) * a.nx + x;
       if (mine) {
+        if constexpr (TH) {
 #pragma unroll
-        for (int i = 0; i < 7; ++i) {
-          const unsigned long long src =
-              ((unsigned long long)wrap1(z - cz7(i), a.nz) * a.ny + wrap1(y - cy7(i), a.ny)) *
-                  a.nx + wrap1(x - cx7(i), a.nx);
-          sv[i] = ld<R>(pl(a.in, S_POP + i, a.ps), src);
+          for (int i = 0; i < 7; ++i) sv[i] = sC[i];
+          stream7(a, E_POP, x, y, z, ev);
+        } else {
+          stream7(a, S_POP, x, y, z, sv);
         }
         Qo = ld<R>(pl(a.ain, A3_QO, a.ps), site);
       }
       if (active) {
         R psi;
-        stream_g(a, x, y, wrap1(z + 1, a.nz), gL, psi, poL);
+        const int zn = wrap1(z + 1, a.nz);
+        stream_g(a, x, y, zn, gL, psi, poL);
         ring[(z + 1) & 3][hy][hx] = psi;
+        if constexpr (TH) {
+          stream7(a, S_POP, x, y, zn, sL);
+          CL = sum7(sL);
+          uring[(z + 1) & 3][hy][hx] = supersat3(a.c, CL, psi);
+        }
       }
       __syncthreads();
       if (mine) {
         const Coef3<R>& c = a.c;
-        const R (*Pm)[HX] = ring[(z - 1) & 3];
-        const R (*P0)[HX] = ring[z & 3];
-        const R (*Pp)[HX] = ring[(z + 1) & 3];
-        const R psi = P0[hy][hx];
-        // gradient: 3 sum w c (X - X0) over faces (1/18) and edges (1/36)
-        const R X0 = psi;
-        auto d = [&](const R (*Pl)[HX], int dx, int dy) { return Pl[hy + dy][hx + dx] - X0; };
-        const R w1 = R(1.0 / 18.0), w2 = R(1.0 / 36.0);
-        R gx = w1 * (d(P0, 1, 0) - d(P0, -1, 0)) +
-               w2 * ((d(P0, 1, 1) - d(P0, -1, 1)) + (d(P0, 1, -1) - d(P0, -1, -1)) +
-                     (d(Pp, 1, 0) - d(Pp, -1, 0)) + (d(Pm, 1, 0) - d(Pm, -1, 0)));
-        R gy = w1 * (d(P0, 0, 1) - d(P0, 0, -1)) +
-               w2 * ((d(P0, 1, 1) - d(P0, 1, -1)) + (d(P0, -1, 1) - d(P0, -1, -1)) +
-                     (d(Pp, 0, 1) - d(Pp, 0, -1)) + (d(Pm, 0, 1) - d(Pm, 0, -1)));
-        R gz = w1 * (d(Pp, 0, 0) - d(Pm, 0, 0)) +
-               w2 * ((d(Pp, 1, 0) - d(Pm, 1, 0)) + (d(Pp, -1, 0) - d(Pm, -1, 0)) +
-                     (d(Pp, 0, 1) - d(Pm, 0, 1)) + (d(Pp, 0, -1) - d(Pm, 0, -1)));
-        gx *= R(3); gy *= R(3); gz *= R(3);
+        const R psi = ring[z & 3][hy][hx];
+        R gx, gy, gz;
+        grad18<R>(ring[(z - 1) & 3], ring[z & 3], ring[(z + 1) & 3], hy, hx, gx, gy, gz);
         // anisotropy (three axes), regularised normal
         const R gm2 = gx * gx + gy * gy + gz * gz;
         const R im = frsqrt(gm2 + c.ge2);
@@ -184,22 +242,33 @@ __global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R> a) {
         const R Nx = pre * n0 * (q0 - iso), Ny = pre * n1 * (q1 - iso), Nz = pre * n2v * (q2 - iso);
         const R as2 = as * as, ias2 = frcp(as2);
         // moments, sources
-        CSum<R> cs;
-#pragma unroll
-        for (int i = 0; i < 7; ++i) cs.add(sv[i]);
-        const R C = cs.value();
+        const R C = TH ? CC : sum7(sv);
         const R omk = R(1) - c.k;
         const R A = (R(1) + c.k) - omk * psi;
         const R iA = frcp(A);
         const R U = (R(2) * C * iA - R(1)) * c.inv_omk;
         const R omp2 = R(1) - psi * psi;
-        const R Q = c.four_bpsi * psi * omp2 - c.lam * omp2 * omp2 * (c.theta + c.Mcinf * U);
+        R theta = c.theta, m0e = R(0), iF = R(1);
+        if constexpr (TH) {
+          m0e = sum7(ev);
+          theta = m0e * c.irc + c.halfL * (R(1) + psi);
+        }
+        const R Q = c.four_bpsi * psi * omp2 - c.lam * omp2 * omp2 * (theta + c.Mcinf * U);
+        R Qeff = Q;
+        if constexpr (TH) {
+          R ux, uy, uz;
+          grad18<R>(uring[(z - 1) & 3], uring[z & 3], uring[(z + 1) & 3], hy, hx, ux, uy, uz);
+          iF = frcp(c.iLe + c.Mcinf * (R(1) + omk * U));
+          const R dot = c.Mcinf * omk *
+                        (ux * (as2 * gx + Nx) + uy * (as2 * gy + Ny) + uz * (as2 * gz + Nz));
+          Qeff = Q * iF + c.W0sq * iF * iF * dot;
+        }
         const R at = -c.aW0 * as * (R(1) + omk * U) * (psi - poC) * frsqrt(gm2 + c.gat2);
         // psi: D3Q7, m0 = psi + (Q + (Q - Q_o)/2) / tau0, flux rate s1 from
-        // W0^2 a_s^2 / tau0 = (1/s1 - 1/2) c_s^2, forcing flux -c_s^2 N / a_s^2
+        // W0^2 a_s^2 / (tau0 F) = (1/s1 - 1/2) c_s^2, forcing flux -c_s^2 N / a_s^2
         {
-          const R m0 = psi + (Q + R(0.5) * (Q - Qo)) * c.inv_tau0;
-          const R s1 = frcp(c.c4W0sq_tau0 * as2 + R(0.5));
+          const R m0 = psi + (Qeff + R(0.5) * (Qeff - Qo)) * c.inv_tau0;
+          const R s1 = frcp(c.c4W0sq_tau0 * as2 * iF + R(0.5));
           const R hs = R(1) - R(0.5) * s1;
           const R Jx = gC[1] - gC[2], Jy = gC[3] - gC[4], Jz = gC[5] - gC[6];
           const R gq = R(-0.25) * ias2;
@@ -217,7 +286,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R> a) {
             st<S, R>(pl(a.out, G_POST + i, a.ps), site, go[i]);
           }
           pl(a.aout, A3_RR, a.ps)[site] = ias2;
-          pl(a.aout, A3_QO, a.ps)[site] = Q;
+          pl(a.aout, A3_QO, a.ps)[site] = Qeff;
         }
         // solute: D3Q7, Jeq = -E grad psi + (1-k) J_at, rate from
         // D_C = 2 D q / A = (1/s - 1/2) c_s^2
@@ -239,24 +308,64 @@ __global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R> a) {
 #pragma unroll
           for (int i = 0; i < 7; ++i) st<S, R>(pl(a.out, S_POP + i, a.ps), site, so[i]);
         }
+        // temperature (TH): at rest the equilibrium is e_0 = rho H - (3/4) theta,
+        // e_i = theta / 8; the flux relaxes to 0 at s_T from k_T = (1/s_T - 1/2)
+        // c_s^2, every other moment to its equilibrium.  theta/8 is rounded to
+        // a multiple of ulp(rho H)/2 so that rho H - 6 (theta/8) is exact in the
+        // common case and a uniform region keeps sum rho H to the last bit.
+        if constexpr (TH) {
+          const R b = round_to_multiple(theta * R(0.125), R(2) * quantum_quarter_ulp(m0e));
+          const R Sx = c.omsth * (ev[1] - ev[2]), Sy = c.omsth * (ev[3] - ev[4]),
+                  Sz = c.omsth * (ev[5] - ev[6]);
+          R eo[7];
+          eo[0] = fma(R(-6), b, m0e);
+          eo[1] = fma(R(0.5), Sx, b); eo[2] = fma(R(-0.5), Sx, b);
+          eo[3] = fma(R(0.5), Sy, b); eo[4] = fma(R(-0.5), Sy, b);
+          eo[5] = fma(R(0.5), Sz, b); eo[6] = fma(R(-0.5), Sz, b);
+#pragma unroll
+          for (int i = 0; i < 7; ++i) st<S, R>(pl(a.out, E_POP + i, a.ps), site, eo[i]);
+        }
         if (a.fields) {
           pl(a.fields, 0, a.ps)[site] = psi;
           pl(a.fields, 1, a.ps)[site] = C;
           pl(a.fields, 2, a.ps)[site] = U;
+          if constexpr (TH) pl(a.fields, 3, a.ps)[site] = theta;
         }
       }
 #pragma unroll
       for (int i = 0; i < 7; ++i) gC[i] = gL[i];
       poC = poL;
+      if constexpr (TH) {
+#pragma unroll
+        for (int i = 0; i < 7; ++i) sC[i] = sL[i];
+        CC = CL;
+      }
     }
     __syncthreads();
   }
 }
 
-// Equilibrium state of a site from psi and C (populations w psi / w C, r = 1,
-// lagged source Q_psi), fields written.
+// Temperature populations at rest (Appendix B) for theta: rho H = rho_l c_p
+// (theta - (c_p^s/c_p) h(psi)), e_0 = rho H - (3/4) theta, e_i = theta / 8;
+// the lagged source becomes Q_psi(theta) / F(U); theta is written to the fields.
 template <typename S, typename R>
-__device__ void write_eq3(const Args3<S, R>& a, unsigned long long site, R psi, R C) {
+__device__ void write_th3(const Args3<S, R>& a, unsigned long long site, R psi, R C, R theta) {
+  const Coef3<R>& c = a.c;
+  const R m0 = c.rcp * (theta - c.halfL * (R(1) + psi));
+#pragma unroll
+  for (int i = 1; i < 7; ++i) st<S, R>(pl(a.out, E_POP + i, a.ps), site, R(0.125) * theta);
+  st<S, R>(pl(a.out, E_POP, a.ps), site, m0 - R(0.75) * theta);
+  const R U = supersat3(c, C, psi);
+  const R omp2 = R(1) - psi * psi;
+  const R Q = c.four_bpsi * psi * omp2 - c.lam * omp2 * omp2 * (theta + c.Mcinf * U);
+  pl(a.aout, A3_QO, a.ps)[site] = Q / (c.iLe + c.Mcinf * (R(1) + (R(1) - c.k) * U));
+  pl(a.fields, 3, a.ps)[site] = theta;
+}
+
+// Equilibrium state of a site from psi and C (populations w psi / w C, r = 1,
+// lagged source Q_psi), fields written; TH: temperature populations at theta.
+template <typename S, typename R, bool TH>
+__device__ void write_eq3(const Args3<S, R>& a, unsigned long long site, R psi, R C, R theta) {
   const Coef3<R>& c = a.c;
 #pragma unroll
   for (int i = 0; i < 7; ++i) {
@@ -272,6 +381,7 @@ __device__ void write_eq3(const Args3<S, R>& a, unsigned long long site, R psi, 
   pl(a.fields, 0, a.ps)[site] = psi;
   pl(a.fields, 1, a.ps)[site] = C;
   pl(a.fields, 2, a.ps)[site] = U;
+  if constexpr (TH) write_th3(a, site, psi, C, theta);
 }
 
 __device__ __forceinline__ double min_image1(double d, double L) {
@@ -281,9 +391,9 @@ __device__ __forceinline__ double min_image1(double d, double L) {
   return d;
 }
 
-template <typename S, typename R>
+template <typename S, typename R, bool TH>
 __global__ void k_init3(Args3<S, R> a, const double* seeds, int n_seeds, double R_s, double sq2b,
-                        double W0, double k) {
+                        double W0, double k, double theta0) {
   const unsigned long long n = (unsigned long long)a.nx * a.ny * a.nz;
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
        i += (unsigned long long)gridDim.x * blockDim.x) {
@@ -298,21 +408,30 @@ __global__ void k_init3(Args3<S, R> a, const double* seeds, int n_seeds, double 
       if (s == 0 || v > psi) psi = v;
     }
     const double C = 1.0 - (1.0 - k) * 0.5 * (1.0 + psi);
-    write_eq3<S, R>(a, i, (R)psi, (R)C);
+    write_eq3<S, R, TH>(a, i, (R)psi, (R)C, (R)theta0);
   }
 }
 
-template <typename S, typename R>
-__global__ void k_set3(Args3<S, R> a, const double* psi, const double* C) {
+template <typename S, typename R, bool TH>
+__global__ void k_set3(Args3<S, R> a, const double* psi, const double* C, double theta0) {
   const unsigned long long n = (unsigned long long)a.nx * a.ny * a.nz;
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
        i += (unsigned long long)gridDim.x * blockDim.x)
-    write_eq3<S, R>(a, i, (R)psi[i], (R)C[i]);
+    write_eq3<S, R, TH>(a, i, (R)psi[i], (R)C[i], (R)theta0);
+}
+
+// Temperature field of the initial state (psi and C from the field planes).
+template <typename S, typename R>
+__global__ void k_settemp3(Args3<S, R> a, const double* theta) {
+  const unsigned long long n = (unsigned long long)a.nx * a.ny * a.nz;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x)
+    write_th3(a, i, pl(a.fields, 0, a.ps)[i], pl(a.fields, 1, a.ps)[i], (R)theta[i]);
 }
 
 template <typename S, typename R>
 __global__ void k_state3(const S* pin, const R* ain, unsigned long long ps, unsigned long long n,
-                         double* out) {
+                         int thermal, double* out) {
   for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < n;
        j += (unsigned long long)gridDim.x * blockDim.x) {
     for (int i = 0; i < 7; ++i) {
@@ -322,12 +441,15 @@ __global__ void k_state3(const S* pin, const R* ain, unsigned long long ps, unsi
     }
     out[14 * n + j] = (double)ain[A3_RR * ps + j];
     out[22 * n + j] = (double)ain[A3_QO * ps + j];
+    if (thermal)
+      for (int i = 0; i < 7; ++i) out[(23 + i) * n + j] = (double)ld<R>(pl(pin, E_POP + i, ps), j);
   }
 }
 
 template <typename R>
-__global__ void k_fields3(const R* f, unsigned long long ps, unsigned long long n, double* out) {
-  for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < 3 * n;
+__global__ void k_fields3(const R* f, unsigned long long ps, unsigned long long n, int planes,
+                          double* out) {
+  for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < planes * n;
        j += (unsigned long long)gridDim.x * blockDim.x)
     out[j] = (double)f[(j / n) * ps + j % n];
 }
@@ -354,11 +476,37 @@ __global__ void k_reduce3(const R* f, unsigned long long ps, unsigned long long 
   }
   if (threadIdx.x == 0) { part[2 * blockIdx.x] = sh[0][0]; part[2 * blockIdx.x + 1] = sh[1][0]; }
 }
-__global__ void k_reduce3_final(const double* part, int nb, double* out) {
-  if (threadIdx.x >= 2) return;
+__global__ void k_reduce3_final(const double* part, int nb, int k, double* out) {
+  if ((int)threadIdx.x >= k) return;
   double acc = 0.0;
-  for (int b = 0; b < nb; ++b) acc += part[2 * b + threadIdx.x];
+  for (int b = 0; b < nb; ++b) acc += part[k * b + threadIdx.x];
   out[threadIdx.x] = acc;
+}
+
+// Thermal totals: sum of the seven temperature populations (rho H), sum theta,
+// sum psi; fixed-order partials.
+template <typename S, typename R>
+__global__ void k_reduce3_th(const S* pin, const R* f, unsigned long long ps, unsigned long long n,
+                             double* part) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < n;
+       j += (unsigned long long)gridDim.x * blockDim.x) {
+    for (int i = 0; i < 7; ++i) a0 += (double)ld<R>(pl(pin, E_POP + i, ps), j);
+    a1 += (double)f[3 * ps + j];
+    a2 += (double)f[j];
+  }
+  __shared__ double sh[3][256];
+  sh[0][threadIdx.x] = a0;
+  sh[1][threadIdx.x] = a1;
+  sh[2][threadIdx.x] = a2;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) part[3 * blockIdx.x + q] = sh[q][0];
 }
 
 }  // namespace d3
@@ -372,6 +520,7 @@ struct pf3_handle {
   pf_precision prec = PF_FP32;
   cudaStream_t stream = nullptr;
   int nx = 0, ny = 0, nz = 0, chunk = 16;
+  int thermal = 0, npop = NPOP3, nfields = 3, nstate = NSTATE3;
   unsigned long long n = 0;
   size_t elem = 4, celem = 4;
   void* pop[2] = {nullptr, nullptr};
@@ -414,6 +563,16 @@ static Coef3<R> coef3(const pf_params& p) {
   c.inv_omk = (R)(1.0 / (1.0 - p.k));
   c.D = (R)p.D;
   c.aW0 = (R)(p.W0 / (2.0 * std::sqrt(2.0)));
+  if (p.thermal) {
+    const double rcp = p.rho_l * p.cp;
+    const double kT = p.Le * p.D * rcp;                 // k_T = alpha rho_l c_p, alpha = Le D
+    c.rcp = (R)rcp;
+    c.irc = (R)(1.0 / rcp);
+    c.halfL = (R)(0.5 * p.latent);
+    c.iLe = (R)(1.0 / p.Le);
+    c.W0sq = (R)(p.W0 * p.W0);
+    c.omsth = (R)(1.0 - 1.0 / (4.0 * kT + 0.5));       // 1 - s_T, c_s^2 = 1/4
+  }
   return c;
 }
 
@@ -466,18 +625,31 @@ extern "C" pf_status pf3_create(const pf_params* p, int nx, int ny, int nz, pf_p
       !(p->eps_s >= 0 && p->eps_s < 0.25) || !(p->grad_eps > 0) || !(p->grad_eps_at > 0) ||
       1.0 - (1.0 - p->k) * p->Omega == 0.0)
     return fail3(nullptr, PF_ERR_BAD_ARG, "a parameter is out of range");
+  if (p->thermal != 0 && p->thermal != 1) return fail3(nullptr, PF_ERR_BAD_ARG, "thermal must be 0 or 1");
+  if (p->thermal) {
+    auto pos = [](double v) { return std::isfinite(v) && v > 0; };
+    if (!pos(p->Le) || !pos(p->cp) || !pos(p->rho_l) || !std::isfinite(p->latent) ||
+        !std::isfinite(p->theta0))
+      return fail3(nullptr, PF_ERR_BAD_ARG, "thermal mode needs Le, cp, rho_l > 0, finite latent, theta0");
+    if (p->rho_l * p->cp < 0.75)
+      return fail3(nullptr, PF_ERR_BAD_ARG, "thermal mode needs rho_l * cp >= 3/4 (stability)");
+  }
   const unsigned long long n = (unsigned long long)nx * ny * nz;
   pf3_handle* h = new (std::nothrow) pf3_handle();
   if (!h) return fail3(nullptr, PF_ERR_OOM, "host allocation failed");
   h->p = *p; h->prec = prec; h->stream = (cudaStream_t)cuda_stream;
   h->nx = nx; h->ny = ny; h->nz = nz; h->n = n;
+  h->thermal = p->thermal;
+  h->npop = p->thermal ? NPOP3_TH : NPOP3;
+  h->nfields = p->thermal ? 4 : 3;
+  h->nstate = p->thermal ? NSTATE3_TH : NSTATE3;
   h->elem = h->celem = prec == PF_FP64 ? 8 : 4;
   bool ok = true;
   for (int c = 0; c < 2; ++c) {
-    ok = ok && cudaMalloc(&h->pop[c], n * NPOP3 * h->elem) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->pop[c], n * h->npop * h->elem) == cudaSuccess;
     ok = ok && cudaMalloc(&h->aux[c], n * NAUX3 * h->celem) == cudaSuccess;
   }
-  ok = ok && cudaMalloc(&h->fields, n * 3 * h->celem) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->fields, n * h->nfields * h->celem) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     pf3_destroy(h);
@@ -500,6 +672,8 @@ extern "C" pf_status pf3_destroy(pf3_handle* h) {
 
 extern "C" const char* pf3_last_error(const pf3_handle* h) { return h ? h->err.c_str() : g3_err.c_str(); }
 extern "C" long long pf3_launch_count(const pf3_handle* h) { return h ? h->launches : -1; }
+extern "C" int pf3_state_planes(const pf3_handle* h) { return h ? h->nstate : -1; }
+extern "C" int pf3_field_planes(const pf3_handle* h) { return h ? h->nfields : -1; }
 
 extern "C" pf_status pf3_init_seeds(pf3_handle* h, const double* seeds, int n_seeds, double R_s) {
   if (!h) return PF_ERR_BAD_ARG;
@@ -517,8 +691,13 @@ extern "C" pf_status pf3_init_seeds(pf3_handle* h, const double* seeds, int n_se
     Args3<S, R> a = args3<S, R>(h, true);
     a.out = (S*)h->pop[0];
     a.aout = (R*)h->aux[0];
-    k_init3<S, R><<<1024, 256, 0, h->stream>>>(a, h->scratch, n_seeds, R_s,
-                                                std::sqrt(2.0 * h->p.beta_psi), h->p.W0, h->p.k);
+    const double sq2b = std::sqrt(2.0 * h->p.beta_psi);
+    if (h->thermal)
+      k_init3<S, R, true><<<1024, 256, 0, h->stream>>>(a, h->scratch, n_seeds, R_s, sq2b, h->p.W0,
+                                                       h->p.k, h->p.theta0);
+    else
+      k_init3<S, R, false><<<1024, 256, 0, h->stream>>>(a, h->scratch, n_seeds, R_s, sq2b, h->p.W0,
+                                                        h->p.k, 0.0);
     PF3_CUDA(h, cudaGetLastError());
     return PF_OK;
   });
@@ -546,7 +725,10 @@ extern "C" pf_status pf3_set_fields(pf3_handle* h, const double* psi, const doub
     Args3<S, R> a = args3<S, R>(h, true);
     a.out = (S*)h->pop[0];
     a.aout = (R*)h->aux[0];
-    k_set3<S, R><<<1024, 256, 0, h->stream>>>(a, h->scratch, h->scratch + n);
+    if (h->thermal)
+      k_set3<S, R, true><<<1024, 256, 0, h->stream>>>(a, h->scratch, h->scratch + n, h->p.theta0);
+    else
+      k_set3<S, R, false><<<1024, 256, 0, h->stream>>>(a, h->scratch, h->scratch + n, 0.0);
     PF3_CUDA(h, cudaGetLastError());
     return PF_OK;
   });
@@ -555,6 +737,33 @@ extern "C" pf_status pf3_set_fields(pf3_handle* h, const double* psi, const doub
   PF3_CUDA(h, cudaStreamSynchronize(h->stream));
   h->inited = 1;
   h->steps = 0;
+  return PF_OK;
+}
+
+extern "C" pf_status pf3_set_temperature(pf3_handle* h, const double* theta, size_t n) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (!h->thermal) return fail3(h, PF_ERR_BAD_ARG, "the handle is not in thermal mode");
+  if (!theta || n != h->n) return fail3(h, PF_ERR_BAD_ARG, "need theta of nx*ny*nz");
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(theta[i])) return fail3(h, PF_ERR_BAD_ARG, "non-finite theta");
+  if (!h->inited || h->steps != 0)
+    return fail3(h, PF_ERR_STATE, "set the temperature after initialisation, before stepping");
+  pf_status st = ensure_scratch3(h, n);
+  if (st != PF_OK) return st;
+  PF3_CUDA(h, cudaMemcpyAsync(h->scratch, theta, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  st = dispatch3(h, [&](auto s_t, auto r_t) {
+    using S = decltype(s_t);
+    using R = decltype(r_t);
+    Args3<S, R> a = args3<S, R>(h, true);
+    a.out = (S*)h->pop[0];
+    a.aout = (R*)h->aux[0];
+    k_settemp3<S, R><<<1024, 256, 0, h->stream>>>(a, h->scratch);
+    PF3_CUDA(h, cudaGetLastError());
+    return PF_OK;
+  });
+  if (st != PF_OK) return st;
+  h->launches++;
+  PF3_CUDA(h, cudaStreamSynchronize(h->stream));
   return PF_OK;
 }
 
@@ -575,7 +784,8 @@ extern "C" pf_status pf3_step(pf3_handle* h, int n_steps) {
     for (int t = 0; t < n_steps; ++t) {
       const Args3<S, R> a = args3<S, R>(h, t == n_steps - 1);
       const int tiles = a.tiles_x * a.tiles_y * a.tiles_z;
-      k_step3d<S, R><<<tiles, THREADS, 0, h->stream>>>(a);
+      if (h->thermal) k_step3d<S, R, true><<<tiles, THREADS, 0, h->stream>>>(a);
+      else k_step3d<S, R, false><<<tiles, THREADS, 0, h->stream>>>(a);
       PF3_CUDA(h, cudaGetLastError());
       h->cur ^= 1;
       h->steps++;
@@ -587,34 +797,38 @@ extern "C" pf_status pf3_step(pf3_handle* h, int n_steps) {
 
 extern "C" pf_status pf3_get_fields(pf3_handle* h, double* out, size_t n) {
   if (!h) return PF_ERR_BAD_ARG;
-  if (!out || n < 3 * h->n) return fail3(h, PF_ERR_BAD_ARG, "output must hold 3 planes");
-  pf_status st = ensure_scratch3(h, 3 * h->n);
+  const size_t need = (size_t)h->nfields * h->n;
+  if (!out || n < need) return fail3(h, PF_ERR_BAD_ARG, "output must hold pf3_field_planes planes");
+  pf_status st = ensure_scratch3(h, need);
   if (st != PF_OK) return st;
-  if (h->prec == PF_FP64) k_fields3<double><<<1024, 256, 0, h->stream>>>((const double*)h->fields, h->n, h->n, h->scratch);
-  else k_fields3<float><<<1024, 256, 0, h->stream>>>((const float*)h->fields, h->n, h->n, h->scratch);
+  if (h->prec == PF_FP64)
+    k_fields3<double><<<1024, 256, 0, h->stream>>>((const double*)h->fields, h->n, h->n, h->nfields, h->scratch);
+  else
+    k_fields3<float><<<1024, 256, 0, h->stream>>>((const float*)h->fields, h->n, h->n, h->nfields, h->scratch);
   PF3_CUDA(h, cudaGetLastError());
   h->launches++;
-  PF3_CUDA(h, cudaMemcpyAsync(out, h->scratch, 3 * h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  PF3_CUDA(h, cudaMemcpyAsync(out, h->scratch, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   PF3_CUDA(h, cudaStreamSynchronize(h->stream));
   return PF_OK;
 }
 
 extern "C" pf_status pf3_get_state(pf3_handle* h, double* out, size_t n) {
   if (!h) return PF_ERR_BAD_ARG;
-  if (!out || n < NSTATE3 * h->n) return fail3(h, PF_ERR_BAD_ARG, "output must hold 23 planes");
-  pf_status st = ensure_scratch3(h, NSTATE3 * h->n);
+  const size_t need = (size_t)h->nstate * h->n;
+  if (!out || n < need) return fail3(h, PF_ERR_BAD_ARG, "output must hold pf3_state_planes planes");
+  pf_status st = ensure_scratch3(h, need);
   if (st != PF_OK) return st;
   st = dispatch3(h, [&](auto s_t, auto r_t) {
     using S = decltype(s_t);
     using R = decltype(r_t);
     k_state3<S, R><<<1024, 256, 0, h->stream>>>((const S*)h->pop[h->cur], (const R*)h->aux[h->cur],
-                                                 h->n, h->n, h->scratch);
+                                                 h->n, h->n, h->thermal, h->scratch);
     PF3_CUDA(h, cudaGetLastError());
     return PF_OK;
   });
   if (st != PF_OK) return st;
   h->launches++;
-  PF3_CUDA(h, cudaMemcpyAsync(out, h->scratch, NSTATE3 * h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  PF3_CUDA(h, cudaMemcpyAsync(out, h->scratch, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   PF3_CUDA(h, cudaStreamSynchronize(h->stream));
   return PF_OK;
 }
@@ -627,10 +841,33 @@ extern "C" pf_status pf3_reduce(pf3_handle* h, double out[2]) {
   if (st != PF_OK) return st;
   if (h->prec == PF_FP64) k_reduce3<double><<<nb, 256, 0, h->stream>>>((const double*)h->fields, h->n, h->n, h->scratch);
   else k_reduce3<float><<<nb, 256, 0, h->stream>>>((const float*)h->fields, h->n, h->n, h->scratch);
-  k_reduce3_final<<<1, 32, 0, h->stream>>>(h->scratch, nb, h->scratch + 2 * nb);
+  k_reduce3_final<<<1, 32, 0, h->stream>>>(h->scratch, nb, 2, h->scratch + 2 * nb);
   PF3_CUDA(h, cudaGetLastError());
   h->launches += 2;
   PF3_CUDA(h, cudaMemcpyAsync(out, h->scratch + 2 * nb, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  PF3_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PF_OK;
+}
+
+extern "C" pf_status pf3_reduce_thermal(pf3_handle* h, double out[3]) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (!out) return fail3(h, PF_ERR_BAD_ARG, "NULL output");
+  if (!h->thermal) return fail3(h, PF_ERR_BAD_ARG, "the handle is not in thermal mode");
+  const int nb = 1024;
+  pf_status st = ensure_scratch3(h, 3 * nb + 3);
+  if (st != PF_OK) return st;
+  st = dispatch3(h, [&](auto s_t, auto r_t) {
+    using S = decltype(s_t);
+    using R = decltype(r_t);
+    k_reduce3_th<S, R><<<nb, 256, 0, h->stream>>>((const S*)h->pop[h->cur], (const R*)h->fields,
+                                                   h->n, h->n, h->scratch);
+    k_reduce3_final<<<1, 32, 0, h->stream>>>(h->scratch, nb, 3, h->scratch + 3 * nb);
+    PF3_CUDA(h, cudaGetLastError());
+    return PF_OK;
+  });
+  if (st != PF_OK) return st;
+  h->launches += 2;
+  PF3_CUDA(h, cudaMemcpyAsync(out, h->scratch + 3 * nb, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   PF3_CUDA(h, cudaStreamSynchronize(h->stream));
   return PF_OK;
 }

@@ -123,6 +123,10 @@ def lib() -> ctypes.CDLL:
     L.pf3_get_fields.argtypes = [P, D, S]
     L.pf3_get_state.argtypes = [P, D, S]
     L.pf3_reduce.argtypes = [P, D]
+    L.pf3_set_temperature.argtypes = [P, D, S]
+    L.pf3_reduce_thermal.argtypes = [P, D]
+    L.pf3_field_planes.argtypes = [P]
+    L.pf3_state_planes.argtypes = [P]
     L.pf3_launch_count.argtypes = [P]
     L.pf3_launch_count.restype = ctypes.c_longlong
     L.pf3_last_error.argtypes = [P]
@@ -135,7 +139,7 @@ def lib() -> ctypes.CDLL:
                  "pf_set_launch", "pf_autotune", "pf_set_temperature", "pf_reduce_thermal",
                  "pf_set_boundaries", "pf3_create", "pf3_init_seeds", "pf3_set_fields",
                  "pf3_set_chunk", "pf3_step", "pf3_get_fields", "pf3_get_state", "pf3_reduce",
-                 "pf3_destroy"):
+                 "pf3_destroy", "pf3_set_temperature", "pf3_reduce_thermal"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -378,6 +382,7 @@ class Simulation:
 
 
 PF3_STATE_PLANES = 23
+PF3_STATE_PLANES_THERMAL = 30
 
 
 def _check3(code: int, handle=None) -> None:
@@ -426,6 +431,11 @@ class Simulation3D:
         b = np.ascontiguousarray(np.asarray(C, dtype=np.float64).reshape(self.shape))
         _check3(lib().pf3_set_fields(self.h, _dp(a), _dp(b), self.n), self.h)
 
+    def set_temperature(self, theta) -> None:
+        """Thermal mode: temperature field of the initial state ([z][y][x])."""
+        a = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(self.shape))
+        _check3(lib().pf3_set_temperature(self.h, _dp(a), self.n), self.h)
+
     def set_chunk(self, chunk: int) -> None:
         _check3(lib().pf3_set_chunk(self.h, int(chunk)), self.h)
 
@@ -433,20 +443,28 @@ class Simulation3D:
         _check3(lib().pf3_step(self.h, int(n)), self.h)
 
     def fields(self) -> dict:
-        out = np.empty(3 * self.n)
+        k = lib().pf3_field_planes(self.h)
+        out = np.empty(k * self.n)
         _check3(lib().pf3_get_fields(self.h, _dp(out), out.size), self.h)
-        out = out.reshape((3,) + self.shape)
-        return {"psi": out[0], "C": out[1], "U": out[2]}
+        out = out.reshape((k,) + self.shape)
+        return dict(zip(("psi", "C", "U", "theta"), out))
 
     def get_state(self) -> np.ndarray:
-        out = np.empty(PF3_STATE_PLANES * self.n)
+        k = lib().pf3_state_planes(self.h)
+        out = np.empty(k * self.n)
         _check3(lib().pf3_get_state(self.h, _dp(out), out.size), self.h)
-        return out.reshape((PF3_STATE_PLANES,) + self.shape)
+        return out.reshape((k,) + self.shape)
 
     def reduce(self) -> dict:
         out = np.zeros(2)
         _check3(lib().pf3_reduce(self.h, _dp(out)), self.h)
         return {"sum_C": out[0], "sum_hpsi": out[1]}
+
+    def reduce_thermal(self) -> dict:
+        """Thermal mode: FP64 sums of rho H (the seven populations), theta, psi."""
+        out = np.zeros(3)
+        _check3(lib().pf3_reduce_thermal(self.h, _dp(out)), self.h)
+        return {"sum_e": out[0], "sum_theta": out[1], "sum_psi": out[2]}
 
     @property
     def launches(self) -> int:

@@ -34,7 +34,7 @@ def pair(shape, seeds, R_s, precision, params=P3):
 
 def compare(o, sim, tol):
     fo, fg = o.fields(), sim.fields()
-    errs = {k: rel(fg[k], fo[k], FLOOR[k]) for k in fo}
+    errs = {k: rel(fg[k], fo[k], FLOOR[k]) for k in fg}      # the oracle adds theta
     assert all(v <= tol for v in errs.values()), errs
     return errs
 
@@ -113,7 +113,7 @@ def test_3d_full_size_windows():
         o.step(T)
         fo = o.fields()
         idx = [(np.arange(M, W - M) + c0) % n for c0 in (z0, y0, x0)]
-        for k in fo:
+        for k in fg:
             ref[k].append(fo[k][M:W - M, M:W - M, M:W - M].ravel())
             got[k].append(fg[k][np.ix_(*idx)].ravel())
     for k in fg:
@@ -129,4 +129,139 @@ def test_3d_configuration_errors():
     sim = pf.Simulation3D((8, 8, 8), wl.BASE_PARAMS, "fp32")
     with pytest.raises(pf.PFError) as e:
         sim.step(1)                        # not initialised
+    assert e.value.code == pf.PF_ERR_STATE
+
+
+# ---------------------------------------------------------------------------
+# thermal mode: D3Q7 temperature lattice, F(U) and the grad F source
+# ---------------------------------------------------------------------------
+T3 = dict(P3, thermal=1, Le=2.0, latent=1.0, theta0=-0.55, cp=10.0, rho_l=1.0)
+FLOOR_T = dict(FLOOR, theta=1e-9)
+
+
+def compare_t(o, sim, tol):
+    fo, fg = o.fields(), sim.fields()
+    assert set(fg) == set(fo) == {"psi", "C", "U", "theta"}
+    errs = {k: rel(fg[k], fo[k], FLOOR_T[k]) for k in fo}
+    assert all(v <= tol for v in errs.values()), errs
+    return errs
+
+
+def theta_field(shape):
+    """A smooth non-uniform temperature: a gradient along x and a bump."""
+    nx, ny, nz = shape
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:nx].astype(float)
+    return -0.55 + 0.05 * np.sin(2 * np.pi * x / nx) + \
+        0.08 * np.exp(-((x - nx / 3) ** 2 + (y - ny / 2) ** 2 + (z - nz / 2) ** 2) / 20.0)
+
+
+def pair_t(shape, seeds, R_s, precision, theta=None, params=T3):
+    o, sim = pair(shape, seeds, R_s, precision, params)
+    if theta is not None:
+        o.init_fields(o.fields()["psi"], o.fields()["C"], theta)
+        sim.set_temperature(theta)
+    return o, sim
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_3d_thermal_initial_state(precision, tol):
+    o, sim = pair_t(RAGGED, SEEDS, 5.0, precision, theta_field(RAGGED))
+    compare_t(o, sim, tol)
+    so, sg = o.state(), sim.get_state()
+    assert sg.shape[0] == pf.PF3_STATE_PLANES_THERMAL == so.shape[0]
+    for p in range(pf.PF3_STATE_PLANES_THERMAL):
+        assert rel(sg[p], so[p], 1e-12) <= max(tol, 1e-15), p
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+def test_3d_thermal_steps_match_oracle(precision, tol):
+    o, sim = pair_t(RAGGED, SEEDS, 5.0, precision, theta_field(RAGGED))
+    sim.set_chunk(5)
+    for _ in range(3):
+        o.step(1)
+        sim.step(1)
+        compare_t(o, sim, tol)
+    so, sg = o.state(), sim.get_state()
+    for p in range(pf.PF3_STATE_PLANES_THERMAL):
+        assert rel(sg[p], so[p], 1e-12) <= tol * 10, p
+
+
+def test_3d_thermal_fp64_many_steps_conservation_and_latent_heat():
+    """A centred seed over 150 steps in FP64: within 1e-9 of the oracle, the
+    cube's symmetry, sum rho H constant to 1e-13 and the mean theta rising by
+    (latent/2) x the mean psi rise."""
+    n = 28
+    o, sim = pair_t((n, n, n), [(n / 2, n / 2, n / 2)], 8.0, "fp64")
+    t0 = sim.reduce_thermal()
+    o.step(150)
+    sim.step(150)
+    compare_t(o, sim, 1e-9)
+    psi = sim.fields()["psi"]
+    for t in (psi.transpose(0, 2, 1), psi.transpose(2, 1, 0)):
+        assert np.abs(psi - t).max() < 1e-12
+    t1 = sim.reduce_thermal()
+    assert abs(t1["sum_e"] / t0["sum_e"] - 1) < 1e-13
+    dpsi, dth = t1["sum_psi"] - t0["sum_psi"], t1["sum_theta"] - t0["sum_theta"]
+    assert dpsi > 0.05 * n ** 3 and abs(dth / (0.5 * dpsi) - 1) < 1e-9
+
+
+def test_3d_thermal_fp32_drift_and_bounded_error():
+    n = 32
+    shape = (n, n, n)
+    o, sim = pair_t(shape, [(10.0, 12.0, 16.0), (24.0, 20.0, 8.0)], 7.0, "fp32", theta_field(shape))
+    t0, c0 = sim.reduce_thermal(), sim.reduce()["sum_C"]
+    o.step(200)
+    sim.step(200)
+    compare_t(o, sim, 1e-3)
+    assert abs(sim.reduce_thermal()["sum_e"] / t0["sum_e"] - 1) <= 1e-6
+    assert abs(sim.reduce()["sum_C"] / c0 - 1) <= 1e-6
+
+
+def test_3d_thermal_full_size_windows():
+    """The 256^3 thermal workload (64 seeds, theta0 everywhere, Le 50) in the
+    benchmark's launch configuration: after 2 steps, 24^3 windows match
+    oracle windows placed in global coordinates."""
+    n = 256
+    seeds, R_s = wl.growth_3d(n)
+    sim = pf.Simulation3D((n, n, n), dict(wl.BASE_PARAMS, **wl.THERMAL_PARAMS), "fp32")
+    sim.init_seeds(seeds, R_s)
+    T = 2
+    sim.step(T)
+    fg = sim.fields()
+    sim.close()
+    W, M = 24, 2 * T
+    centres = [(int(s[0]) + 7, int(s[1]), int(s[2])) for s in seeds[:2]] + [(n - 2, n - 2, n - 2)]
+    ref, got = {k: [] for k in fg}, {k: [] for k in fg}
+    for cx, cy, cz in centres:
+        x0, y0, z0 = cx - W // 2, cy - W // 2, cz - W // 2
+        o = oracle.Oracle3D(W, W, W, dict(T3, **wl.THERMAL_PARAMS), window=(n, n, n, x0, y0, z0))
+        o.init_spec(seeds, R_s)
+        o.step(T)
+        fo = o.fields()
+        idx = [(np.arange(M, W - M) + c0) % n for c0 in (z0, y0, x0)]
+        for k in fg:
+            ref[k].append(fo[k][M:W - M, M:W - M, M:W - M].ravel())
+            got[k].append(fg[k][np.ix_(*idx)].ravel())
+    for k in fg:
+        err = rel(np.concatenate(got[k]), np.concatenate(ref[k]), FLOOR_T[k])
+        assert err <= 1e-5, (k, err)
+
+
+def test_3d_thermal_configuration_errors():
+    with pytest.raises(pf.PFError):
+        pf.Simulation3D((8, 8, 8), dict(wl.BASE_PARAMS, **dict(T3, cp=0.5)), "fp32")
+    iso = pf.Simulation3D((8, 8, 8), wl.BASE_PARAMS, "fp32")
+    iso.init_seeds([(4, 4, 4)], 2.0)
+    with pytest.raises(pf.PFError):
+        iso.set_temperature(np.zeros((8, 8, 8)))          # not thermal
+    with pytest.raises(pf.PFError):
+        iso.reduce_thermal()
+    sim = pf.Simulation3D((8, 8, 8), dict(wl.BASE_PARAMS, **T3), "fp32")
+    with pytest.raises(pf.PFError) as e:
+        sim.set_temperature(np.zeros((8, 8, 8)))          # not initialised
+    assert e.value.code == pf.PF_ERR_STATE
+    sim.init_seeds([(4, 4, 4)], 2.0)
+    sim.step(1)
+    with pytest.raises(pf.PFError) as e:
+        sim.set_temperature(np.zeros((8, 8, 8)))          # already stepped
     assert e.value.code == pf.PF_ERR_STATE
