@@ -432,3 +432,136 @@ def grad3(X, x, y, z):
     out = np.zeros(3)
     _l3().or3_grad(_dp(X), nx, ny, nz, int(x), int(y), int(z), _dp(out))
     return out
+
+
+# -- the three-dimensional two-phase oracle (pf_oracle3d.c, or3f_*) ----------
+PARAM_NAMES_3F = ("rho_l", "rho_g", "nu", "sigma", "W_phi", "M_phi", "beta_phi", "beta_psi",
+                  "beta_inter", "W0", "tau0", "eps_s", "k", "D", "Omega", "g", "grad_eps",
+                  "grad_eps_at", "s_e", "s_eps")
+FIELDS_3F = ("phi", "psi", "C", "U", "p", "vx", "vy", "vz", "mu")
+_lib3f = None
+
+
+def _l3f() -> ctypes.CDLL:
+    global _lib3f
+    lib = _l3()                          # takes the module lock itself
+    with _lock:
+        if _lib3f is None:
+            P, D, I = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+            lib.or3f_new.restype = P
+            lib.or3f_new.argtypes = [I, I, I]
+            lib.or3f_free.argtypes = [P]
+            lib.or3f_set_params.argtypes = [P, D]
+            lib.or3f_set_window.argtypes = [P, I, I, I, I, I, I]
+            lib.or3f_set_rho_bar.argtypes = [P, ctypes.c_double]
+            lib.or3f_get_rho_bar.argtypes = [P]
+            lib.or3f_get_rho_bar.restype = ctypes.c_double
+            lib.or3f_init_fields.argtypes = [P, D, D, D, D, D, D, D]
+            lib.or3f_fields_from_spec.argtypes = [P, D, I, ctypes.c_double, D, I, D, D, D]
+            lib.or3f_mean_phi_global.argtypes = [P, D, I]
+            lib.or3f_mean_phi_global.restype = ctypes.c_double
+            lib.or3f_init_spec.argtypes = [P, D, I, ctypes.c_double, D, I]
+            lib.or3f_step.argtypes = [P, I]
+            lib.or3f_fields.argtypes = [P, D]
+            lib.or3f_state.argtypes = [P, D]
+            lib.or3f_totals.argtypes = [P, D]
+            lib.or3f_basis.argtypes = [D, D, ctypes.POINTER(ctypes.c_int)]
+            lib.or3f_collide19.argtypes = [D] * 5
+            lib.or3f_feq.argtypes = [ctypes.c_double, ctypes.c_double, D, D]
+            _lib3f = lib
+    return _lib3f
+
+
+class Oracle3F:
+    """Periodic nx x ny x nz lattice of the 3-D two-phase step: NS and CAC on
+    D3Q19, psi and C on D3Q7, coupled as in 2-D.  Arrays are [z][y][x]; seeds
+    are (x, y, z), bubbles (x, y, z, R)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, params: dict, window=None):
+        self.lib = _l3f()
+        self.shape = (int(nz), int(ny), int(nx))
+        self.h = self.lib.or3f_new(int(nx), int(ny), int(nz))
+        if not self.h:
+            raise MemoryError("oracle allocation failed")
+        dflt = {"s_e": 1.0, "s_eps": 1.0}
+        pv = _f64([float(params[k] if k in params else dflt[k]) for k in PARAM_NAMES_3F])
+        self.lib.or3f_set_params(self.h, _dp(pv))
+        if window is not None:           # (NX, NY, NZ, x0, y0, z0)
+            self.lib.or3f_set_window(self.h, *[int(v) for v in window])
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.lib.or3f_free(h)
+            self.h = None
+
+    def set_rho_bar(self, rho_bar: float) -> None:
+        self.lib.or3f_set_rho_bar(self.h, float(rho_bar))
+
+    @property
+    def rho_bar(self) -> float:
+        return self.lib.or3f_get_rho_bar(self.h)
+
+    def fields_from_spec(self, seeds, R_s, bubbles):
+        s = np.ascontiguousarray(_f64(seeds).reshape(-1, 3))
+        b = np.ascontiguousarray(_f64(bubbles).reshape(-1, 4))
+        n = int(np.prod(self.shape))
+        out = np.empty(3 * n)
+        self.lib.or3f_fields_from_spec(self.h, _dp(s), len(s), float(R_s), _dp(b), len(b),
+                                       _dp(out[:n]), _dp(out[n:2 * n]), _dp(out[2 * n:]))
+        out = out.reshape((3,) + self.shape)
+        return {"phi": out[0], "psi": out[1], "C": out[2]}
+
+    def mean_phi_global(self, bubbles) -> float:
+        b = np.ascontiguousarray(_f64(bubbles).reshape(-1, 4))
+        return self.lib.or3f_mean_phi_global(self.h, _dp(b), len(b))
+
+    def init_spec(self, seeds, R_s: float, bubbles) -> None:
+        s = np.ascontiguousarray(_f64(seeds).reshape(-1, 3))
+        b = np.ascontiguousarray(_f64(bubbles).reshape(-1, 4))
+        self.lib.or3f_init_spec(self.h, _dp(s), len(s), float(R_s), _dp(b), len(b))
+
+    def init_fields(self, phi, psi, C, vx=None, vy=None, vz=None, p=None) -> None:
+        self._keep = [None if a is None else _f64(a).ravel() for a in (phi, psi, C, vx, vy, vz, p)]
+        self.lib.or3f_init_fields(self.h, *[_dp(a) for a in self._keep])
+
+    def step(self, n: int = 1) -> None:
+        self.lib.or3f_step(self.h, int(n))
+
+    def fields(self) -> dict:
+        k = len(FIELDS_3F)
+        out = np.empty(k * int(np.prod(self.shape)))
+        self.lib.or3f_fields(self.h, _dp(out))
+        return dict(zip(FIELDS_3F, out.reshape((k,) + self.shape)))
+
+    def state(self) -> np.ndarray:
+        out = np.empty(66 * int(np.prod(self.shape)))
+        self.lib.or3f_state(self.h, _dp(out))
+        return out.reshape((66,) + self.shape)
+
+    def totals(self) -> dict:
+        out = np.zeros(5)
+        self.lib.or3f_totals(self.h, _dp(out))
+        return {"sum_phi": out[0], "sum_C": out[1], "j": out[2:5].copy()}
+
+
+def basis19():
+    """(M, w, c) of the D3Q19 lattice: moment rows, weights, velocities."""
+    M, W = np.zeros((19, 19)), np.zeros(19)
+    C = np.zeros(57, dtype=np.int32)
+    _l3f().or3f_basis(_dp(M), _dp(W), C.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    return M, W, C.reshape(19, 3)
+
+
+def collide19(f, feq, S, G):
+    args = [_f64(a) for a in (f, feq, S, G)]
+    out = np.zeros(19)
+    _l3f().or3f_collide19(*[_dp(a) for a in args], _dp(out))
+    return out
+
+
+def feq19(p, rho, v):
+    out = np.zeros(19)
+    vv = _f64(v)
+    _l3f().or3f_feq(float(p), float(rho), _dp(vv), _dp(out))
+    return out

@@ -503,3 +503,581 @@ void or3_grad(const double *X, int nx, int ny, int nz, int x, int y, int z, doub
   }
   for (int a = 0; a < 3; ++a) out[a] = 3.0 * g[a];
 }
+
+/* ======================================================================== */
+/* Three-dimensional two-phase step (reading R34): the coupled step of the   */
+/* 2-D oracle written for d = 3.  Incompressible Navier-Stokes and the       */
+/* conservative Allen-Cahn equation on D3Q19 lattices (w0 = 1/3, faces 1/18, */
+/* edges 1/36, c_s^2 = 1/3) with the MRT of d'Humieres et al. (2002) in the  */
+/* role of the paper's M0 (the paper gives the D2Q9 one only); psi and C on  */
+/* the D3Q7 lattices above, coupled to the flow and the gas as in 2-D.       */
+/* Periodic cube, one grain orientation aligned with the lattice.            */
+/* ======================================================================== */
+
+/* D3Q19: rest, six faces, twelve edges; opposite directions in pairs
+ * (2j-1, 2j). */
+static const int C19[19][3] = {
+    {0, 0, 0},   {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},  {0, -1, 0},  {0, 0, 1},  {0, 0, -1},
+    {1, 1, 0},   {-1, -1, 0}, {1, -1, 0},  {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1},
+    {1, 0, -1},  {-1, 0, 1},  {0, 1, 1},   {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+static double W19[19];
+static const double CS2_19 = 1.0 / 3.0;
+/* Moment basis: rho, e, eps, jx, qx, jy, qy, jz, qz, 3pxx, 3pixx, pww, piww,
+ * pxy, pyz, pxz, mx, my, mz, as polynomials of c; mutually orthogonal rows,
+ * so M^-1 = M^T diag(1 / |row|^2). */
+static double M19[19][19], M19I[19][19];
+static int m19_built = 0;
+
+static void build_m19(void) {
+  if (m19_built) return;
+  for (int j = 0; j < 19; ++j) {
+    const double x = C19[j][0], y = C19[j][1], z = C19[j][2];
+    const double c2 = x * x + y * y + z * z;
+    W19[j] = c2 == 0 ? 1.0 / 3.0 : (c2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+    const double r[19] = {1.0,
+                          19 * c2 - 30,
+                          (21 * c2 * c2 - 53 * c2 + 24) / 2,
+                          x, (5 * c2 - 9) * x,
+                          y, (5 * c2 - 9) * y,
+                          z, (5 * c2 - 9) * z,
+                          3 * x * x - c2, (3 * c2 - 5) * (3 * x * x - c2),
+                          y * y - z * z, (3 * c2 - 5) * (y * y - z * z),
+                          x * y, y * z, x * z,
+                          (y * y - z * z) * x, (z * z - x * x) * y, (x * x - y * y) * z};
+    for (int k = 0; k < 19; ++k) M19[k][j] = r[k];
+  }
+  for (int k = 0; k < 19; ++k) {
+    double n2 = 0;
+    for (int j = 0; j < 19; ++j) n2 += M19[k][j] * M19[k][j];
+    for (int j = 0; j < 19; ++j) M19I[j][k] = M19[k][j] / n2;
+  }
+  m19_built = 1;
+}
+
+/* m* = m - S (m - m_eq) + (I - S/2) M G, f* = M^-1 m* (Appendix B's operator). */
+static void collide19(const real f[19], const real feq[19], const real S[19], const real G[19],
+                      real out[19]) {
+  real ms[19];
+  for (int k = 0; k < 19; ++k) {
+    real a = 0, b = 0, c = 0;
+    for (int j = 0; j < 19; ++j) {
+      a += M19[k][j] * f[j];
+      b += M19[k][j] * feq[j];
+      c += M19[k][j] * G[j];
+    }
+    ms[k] = a - S[k] * (a - b) + (1.0 - 0.5 * S[k]) * c;
+  }
+  for (int j = 0; j < 19; ++j) {
+    real o = 0;
+    for (int k = 0; k < 19; ++k) o += M19I[j][k] * ms[k];
+    out[j] = o;
+  }
+}
+
+/* Parameters of the two-phase step (the 2-D symbols). */
+enum { F3_RHO_L, F3_RHO_G, F3_NU, F3_SIGMA, F3_W_PHI, F3_M_PHI, F3_BETA_PHI, F3_BETA_PSI,
+       F3_BETA_INTER, F3_W0, F3_TAU0, F3_EPS_S, F3_K, F3_D, F3_OMEGA, F3_G, F3_GRAD_EPS,
+       F3_GRAD_EPS_AT, F3_S_E, F3_S_EPS, NPAR3F };
+
+enum { G3_PHI, G3_PSI, G3_C, G3_U, G3_P, G3_VX, G3_VY, G3_VZ, G3_MU, NFLD3F };
+
+typedef struct {
+  int nx, ny, nz, n;
+  int NX, NY, NZ, x0, y0, z0;
+  double par[NPAR3F];
+  double rho_bar;
+  int rho_bar_fixed;
+  long steps;
+  /* state */
+  real *f[19], *h[19], *gpre[7], *gpost[7], *rr, *s[7], *Q_o, *phi_o, *C_o, *v_o[3];
+  /* next state */
+  real *nf[19], *nh[19], *ngpre[7], *ngpost[7], *nrr, *ns[7], *nQ_o, *nphi_o, *nC_o, *nv_o[3];
+  /* streaming scratch */
+  real *fS[19], *hS[19], *gS[7], *sS[7], *phiS, *psiS, *CS, *psiOld;
+  real *fld[NFLD3F];
+  real *block;
+} o3fstate;
+
+static double derivedf(const o3fstate *st, double *lam, double *Mc, double *th) {
+  const double *p = st->par;
+  *lam = p[F3_D] * p[F3_TAU0] / ((47.0 / 75.0) * p[F3_W0] * p[F3_W0]);
+  *Mc = 1.0 - (1.0 - p[F3_K]) * p[F3_OMEGA];
+  *th = -*Mc * p[F3_OMEGA] / (1.0 - (1.0 - p[F3_K]) * p[F3_OMEGA]);
+  return *lam;
+}
+
+o3fstate *or3f_new(int nx, int ny, int nz) {
+  build_m7();
+  build_n18();
+  build_m19();
+  if (nx < 1 || ny < 1 || nz < 1) return NULL;
+  o3fstate *st = (o3fstate *)calloc(1, sizeof(o3fstate));
+  if (!st) return NULL;
+  st->nx = nx; st->ny = ny; st->nz = nz; st->n = nx * ny * nz;
+  st->NX = nx; st->NY = ny; st->NZ = nz;
+  const size_t n = (size_t)st->n;
+  const size_t planes = 2 * (19 + 19 + 7 + 7 + 1 + 7 + 1 + 1 + 1 + 3) + (19 + 19 + 7 + 7 + 4) + NFLD3F;
+  st->block = (real *)calloc(planes * n, sizeof(real));
+  if (!st->block) { free(st); return NULL; }
+  real *q = st->block;
+#define TAKE(p) do { (p) = q; q += n; } while (0)
+  for (int i = 0; i < 19; ++i) { TAKE(st->f[i]); TAKE(st->h[i]); TAKE(st->nf[i]); TAKE(st->nh[i]); }
+  for (int i = 0; i < 7; ++i) {
+    TAKE(st->gpre[i]); TAKE(st->gpost[i]); TAKE(st->s[i]);
+    TAKE(st->ngpre[i]); TAKE(st->ngpost[i]); TAKE(st->ns[i]);
+  }
+  TAKE(st->rr); TAKE(st->Q_o); TAKE(st->phi_o); TAKE(st->C_o);
+  TAKE(st->nrr); TAKE(st->nQ_o); TAKE(st->nphi_o); TAKE(st->nC_o);
+  for (int a = 0; a < 3; ++a) { TAKE(st->v_o[a]); TAKE(st->nv_o[a]); }
+  for (int i = 0; i < 19; ++i) { TAKE(st->fS[i]); TAKE(st->hS[i]); }
+  for (int i = 0; i < 7; ++i) { TAKE(st->gS[i]); TAKE(st->sS[i]); }
+  TAKE(st->phiS); TAKE(st->psiS); TAKE(st->CS); TAKE(st->psiOld);
+  for (int f = 0; f < NFLD3F; ++f) TAKE(st->fld[f]);
+#undef TAKE
+  return st;
+}
+
+void or3f_free(o3fstate *st) {
+  if (!st) return;
+  free(st->block);
+  free(st);
+}
+
+void or3f_set_params(o3fstate *st, const double *p) {
+  for (int i = 0; i < NPAR3F; ++i) st->par[i] = p[i];
+}
+
+void or3f_set_window(o3fstate *st, int NX, int NY, int NZ, int x0, int y0, int z0) {
+  st->NX = NX; st->NY = NY; st->NZ = NZ; st->x0 = x0; st->y0 = y0; st->z0 = z0;
+}
+
+/* Fix the buoyancy reference density (reading R13) instead of taking it from
+ * the initial phi of this lattice (a window of a larger one). */
+void or3f_set_rho_bar(o3fstate *st, double rho_bar) { st->rho_bar = rho_bar; st->rho_bar_fixed = 1; }
+double or3f_get_rho_bar(const o3fstate *st) { return st->rho_bar; }
+
+static inline int idx3f(const o3fstate *st, int x, int y, int z) {
+  return (wrap3(z, st->nz) * st->ny + wrap3(y, st->ny)) * st->nx + wrap3(x, st->nx);
+}
+
+static double supersatf(const o3fstate *st, double C, double psi) {
+  const double k = st->par[F3_K];
+  return (2.0 * C / (1.0 + k - (1.0 - k) * psi) - 1.0) / (1.0 - k);
+}
+
+/* Q_psi = -[f2' + d_psi f3 + lambda' (1-psi^2)^2 (theta_sys + M c_inf U)] with
+ * f3 = beta_inter (1-phi)^2 (1+psi)^2 (Appendix B, Eq. eq-f3Inter) */
+static double qpsif(const o3fstate *st, double phi, double psi, double U) {
+  const double *p = st->par;
+  double lam, Mc, th;
+  derivedf(st, &lam, &Mc, &th);
+  const double om = 1.0 - psi * psi;
+  return 4.0 * p[F3_BETA_PSI] * psi * om - 2.0 * p[F3_BETA_INTER] * (1.0 - phi) * (1.0 - phi) * (1.0 + psi) -
+         lam * om * om * (th + Mc * U);
+}
+
+/* Pressure-based incompressible equilibrium on D3Q19: w p / c_s^2 off the
+ * rest direction, -(1 - w0) p / c_s^2 on it, plus rho w [c.v/c_s^2 +
+ * (c.v)^2/(2 c_s^4) - v^2/(2 c_s^2)] (reading R1 in 3-D). */
+static void feq19(double p, double rho, const double v[3], real out[19]) {
+  const double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  for (int i = 0; i < 19; ++i) {
+    const double cu = C19[i][0] * v[0] + C19[i][1] * v[1] + C19[i][2] * v[2];
+    out[i] = W19[i] * p / CS2_19 +
+             rho * W19[i] * (cu / CS2_19 + cu * cu / (2 * CS2_19 * CS2_19) - v2 / (2 * CS2_19));
+    if (i == 0) out[i] -= p / CS2_19;
+  }
+}
+
+/* CAC equilibrium w phi (1 + c.v / c_s^2) */
+static void heq19(double phi, const double v[3], real out[19]) {
+  for (int i = 0; i < 19; ++i)
+    out[i] = W19[i] * phi * (1.0 + (C19[i][0] * v[0] + C19[i][1] * v[1] + C19[i][2] * v[2]) / CS2_19);
+}
+
+/* Initial state from fields (n each; v and p may be NULL: rest, p = 0):
+ * populations at equilibrium, lagged values equal to the current ones,
+ * r = 1 (reading R20 in 3-D). */
+void or3f_init_fields(o3fstate *st, const double *phi, const double *psi, const double *C,
+                      const double *vx, const double *vy, const double *vz, const double *p) {
+  const double *par = st->par;
+  double sphi = 0.0;
+  for (int id = 0; id < st->n; ++id) {
+    const double ph = phi[id], ps = psi[id], c = C[id];
+    const double v[3] = {vx ? vx[id] : 0.0, vy ? vy[id] : 0.0, vz ? vz[id] : 0.0};
+    const double pp = p ? p[id] : 0.0;
+    const double rho = par[F3_RHO_G] + ph * (par[F3_RHO_L] - par[F3_RHO_G]);
+    real t[19];
+    feq19(pp, rho, v, t);
+    for (int i = 0; i < 19; ++i) st->f[i][id] = t[i];
+    heq19(ph, v, t);
+    for (int i = 0; i < 19; ++i) st->h[i][id] = t[i];
+    for (int i = 0; i < 7; ++i) {
+      st->gpre[i][id] = st->gpost[i][id] = W7[i] * ps;
+      st->s[i][id] = W7[i] * c + W7[i] * c * (C7[i][0] * v[0] + C7[i][1] * v[1] + C7[i][2] * v[2]) / CS2_7;
+    }
+    st->rr[id] = 1.0;
+    const double U = supersatf(st, c, ps);
+    st->Q_o[id] = qpsif(st, ph, ps, U);
+    st->phi_o[id] = ph; st->C_o[id] = c;
+    for (int a = 0; a < 3; ++a) st->v_o[a][id] = v[a];
+    st->fld[G3_PHI][id] = ph; st->fld[G3_PSI][id] = ps; st->fld[G3_C][id] = c;
+    st->fld[G3_U][id] = U; st->fld[G3_P][id] = pp;
+    st->fld[G3_VX][id] = v[0]; st->fld[G3_VY][id] = v[1]; st->fld[G3_VZ][id] = v[2];
+    st->fld[G3_MU][id] = 0.0;
+    sphi += ph;
+  }
+  if (!st->rho_bar_fixed)
+    st->rho_bar = par[F3_RHO_G] + (sphi / st->n) * (par[F3_RHO_L] - par[F3_RHO_G]);
+  st->steps = 0;
+}
+
+/* Signed minimum-image offset on a periodic axis of length L */
+static double min_image3(double d, double L) {
+  d = fmod(d, L);
+  if (d < -0.5 * L) d += L;
+  if (d >= 0.5 * L) d -= L;
+  return d;
+}
+
+/* Initial fields from spherical seeds (x, y, z) of radius R_s and bubbles
+ * (x, y, z, R_b) (readings R9, R21 in 3-D): psi = max tanh(sqrt(2 beta_psi)
+ * (R_s - r)/W0), phi = min [1/2 + 1/2 tanh(sqrt(2 beta_phi) (r - R_b)/(2 W_phi))],
+ * C = phi [1 - (1-k) h(psi)]. */
+void or3f_fields_from_spec(const o3fstate *st, const double *seeds, int n_seeds, double R_s,
+                           const double *bubbles, int n_bub, double *phi, double *psi, double *C) {
+  const double *p = st->par;
+  const double sb = sqrt(2.0 * p[F3_BETA_PSI]), sp = sqrt(2.0 * p[F3_BETA_PHI]);
+  for (int z = 0; z < st->nz; ++z)
+    for (int y = 0; y < st->ny; ++y)
+      for (int x = 0; x < st->nx; ++x) {
+        const int id = (z * st->ny + y) * st->nx + x;
+        const double X[3] = {st->x0 + x, st->y0 + y, st->z0 + z}, L[3] = {st->NX, st->NY, st->NZ};
+        double ps = -1.0, ph = 1.0;
+        for (int s = 0; s < n_seeds; ++s) {
+          double r2 = 0;
+          for (int a = 0; a < 3; ++a) {
+            const double d = min_image3(X[a] - seeds[3 * s + a], L[a]);
+            r2 += d * d;
+          }
+          const double v = tanh(sb * (R_s - sqrt(r2)) / p[F3_W0]);
+          if (s == 0 || v > ps) ps = v;
+        }
+        for (int b = 0; b < n_bub; ++b) {
+          double r2 = 0;
+          for (int a = 0; a < 3; ++a) {
+            const double d = min_image3(X[a] - bubbles[4 * b + a], L[a]);
+            r2 += d * d;
+          }
+          const double v = 0.5 + 0.5 * tanh(sp * (sqrt(r2) - bubbles[4 * b + 3]) / (2.0 * p[F3_W_PHI]));
+          if (b == 0 || v < ph) ph = v;
+        }
+        phi[id] = ph;
+        psi[id] = ps;
+        C[id] = ph * (1.0 - (1.0 - p[F3_K]) * 0.5 * (1.0 + ps));
+      }
+}
+
+/* mean phi of the spec over the whole NX x NY x NZ lattice */
+double or3f_mean_phi_global(const o3fstate *st, const double *bubbles, int n_bub) {
+  const double sp = sqrt(2.0 * st->par[F3_BETA_PHI]);
+  double total = 0.0;
+#pragma omp parallel for reduction(+ : total) schedule(static)
+  for (int z = 0; z < st->NZ; ++z)
+    for (int y = 0; y < st->NY; ++y)
+      for (int x = 0; x < st->NX; ++x) {
+        const double X[3] = {x, y, z}, L[3] = {st->NX, st->NY, st->NZ};
+        double ph = 1.0;
+        for (int b = 0; b < n_bub; ++b) {
+          double r2 = 0;
+          for (int a = 0; a < 3; ++a) {
+            const double d = min_image3(X[a] - bubbles[4 * b + a], L[a]);
+            r2 += d * d;
+          }
+          const double v = 0.5 + 0.5 * tanh(sp * (sqrt(r2) - bubbles[4 * b + 3]) / (2.0 * st->par[F3_W_PHI]));
+          if (b == 0 || v < ph) ph = v;
+        }
+        total += ph;
+      }
+  return total / ((double)st->NX * st->NY * st->NZ);
+}
+
+int or3f_init_spec(o3fstate *st, const double *seeds, int n_seeds, double R_s,
+                   const double *bubbles, int n_bub) {
+  const size_t n = (size_t)st->n;
+  double *buf = (double *)malloc(3 * n * sizeof(double));
+  if (!buf) return -1;
+  or3f_fields_from_spec(st, seeds, n_seeds, R_s, bubbles, n_bub, buf, buf + n, buf + 2 * n);
+  or3f_init_fields(st, buf, buf + n, buf + 2 * n, NULL, NULL, NULL, NULL);
+  free(buf);
+  return 0;
+}
+
+/* isotropic gradient and Laplacian with the D3Q19 weights (reading R5 in 3-D):
+ * grad X = (1/c_s^2) sum w c X(x+c), lap X = (2/c_s^2) sum w [X(x+c) - X(x)] */
+static void grad19(const o3fstate *st, const real *X, int x, int y, int z, double g[3]) {
+  g[0] = g[1] = g[2] = 0.0;
+  for (int i = 1; i < 19; ++i) {
+    const double v = X[idx3f(st, x + C19[i][0], y + C19[i][1], z + C19[i][2])];
+    for (int a = 0; a < 3; ++a) g[a] += W19[i] * C19[i][a] * v;
+  }
+  for (int a = 0; a < 3; ++a) g[a] /= CS2_19;
+}
+static double lap19(const o3fstate *st, const real *X, int x, int y, int z) {
+  const double c = X[idx3f(st, x, y, z)];
+  double a = 0.0;
+  for (int i = 1; i < 19; ++i) a += W19[i] * (X[idx3f(st, x + C19[i][0], y + C19[i][1], z + C19[i][2])] - c);
+  return 2.0 * a / CS2_19;
+}
+
+static void step3f(o3fstate *st) {
+  const int nx = st->nx, ny = st->ny, nz = st->nz;
+  const double *p = st->par;
+  /* pass 1: pull streaming of f, h, s and of g with the time stretch (R3) */
+#pragma omp parallel for schedule(static)
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const int id = (z * ny + y) * nx + x;
+        real phi = 0, psi = 0, psio = 0, C = 0;
+        for (int i = 0; i < 19; ++i) {
+          const int src = idx3f(st, x - C19[i][0], y - C19[i][1], z - C19[i][2]);
+          st->fS[i][id] = st->f[i][src];
+          st->hS[i][id] = st->h[i][src];
+          phi += st->hS[i][id];
+        }
+        for (int i = 0; i < 7; ++i) {
+          const int src = idx3f(st, x - C7[i][0], y - C7[i][1], z - C7[i][2]);
+          const real gold = st->gpre[i][id];
+          st->gS[i][id] = gold + (st->gpost[i][src] - gold) * st->rr[src];
+          st->sS[i][id] = st->s[i][src];
+          psi += st->gS[i][id];
+          psio += gold;
+          C += st->sS[i][id];
+        }
+        st->phiS[id] = phi; st->psiS[id] = psi; st->psiOld[id] = psio; st->CS[id] = C;
+      }
+  double lam, Mc, thsys;
+  derivedf(st, &lam, &Mc, &thsys);
+  const double rl = p[F3_RHO_L], rg = p[F3_RHO_G], k = p[F3_K], W0 = p[F3_W0], tau0 = p[F3_TAU0];
+  const double kappa = sqrt(2.0 * p[F3_BETA_PHI]) / p[F3_W_PHI];
+  /* F_s = 6 sigma / (W_phi sqrt(2 beta_phi)) mu grad phi (Section 2.2, phi_l - phi_g = 1) */
+  const double fs_coef = 6.0 * p[F3_SIGMA] / (p[F3_W_PHI] * sqrt(2.0 * p[F3_BETA_PHI]));
+  const double s_nu = 1.0 / (p[F3_NU] / CS2_19 + 0.5);
+  const double s_q = 8.0 * (2.0 - s_nu) / (8.0 - s_nu);          /* reading R7 */
+  const double s_phi = 1.0 / (p[F3_M_PHI] / CS2_19 + 0.5);
+  /* pass 2 */
+#pragma omp parallel for schedule(static)
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const int id = (z * ny + y) * nx + x;
+        const double phi = st->phiS[id], psi = st->psiS[id], C = st->CS[id], psio = st->psiOld[id];
+        const double phio = st->phi_o[id], Co = st->C_o[id], Qo = st->Q_o[id];
+        const double vo[3] = {st->v_o[0][id], st->v_o[1][id], st->v_o[2][id]};
+        /* stencils */
+        double gp[3], gs[3], dv[3][3];   /* dv[a][b] = d_b v_o,a */
+        grad19(st, st->phiS, x, y, z, gp);
+        const double lphi = lap19(st, st->phiS, x, y, z);
+        grad19(st, st->psiS, x, y, z, gs);
+        for (int a = 0; a < 3; ++a) grad19(st, st->v_o[a], x, y, z, dv[a]);
+        /* gas-liquid interface */
+        const double rho = rg + phi * (rl - rg);
+        double gr[3], nf[3];
+        const double gm = sqrt(gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2] + p[F3_GRAD_EPS] * p[F3_GRAD_EPS]);
+        for (int a = 0; a < 3; ++a) { gr[a] = (rl - rg) * gp[a]; nf[a] = gp[a] / gm; }
+        const double mu = 2.0 * p[F3_BETA_PHI] * phi * (1.0 - phi) * (1.0 - 2.0 * phi) -
+                          2.0 * p[F3_BETA_INTER] * (1.0 - phi) * (1.0 + psi) * (1.0 + psi) -
+                          p[F3_W_PHI] * p[F3_W_PHI] * lphi;
+        const double aphi = kappa * phi * (1.0 - phi);
+        double Dm[3];
+        for (int a = 0; a < 3; ++a) Dm[a] = p[F3_M_PHI] * (gp[a] - aphi * nf[a]);
+        const double divD = (phi - phio) + vo[0] * gp[0] + vo[1] * gp[1] + vo[2] * gp[2];
+        double Fp[3];
+        for (int a = 0; a < 3; ++a) {
+          const double Fs = fs_coef * mu * gp[a];
+          const double Fb = a == 1 ? -(rho - st->rho_bar) * p[F3_G] : 0.0;   /* reading R13 */
+          const double Fm = (rl - rg) * (divD * vo[a] + Dm[0] * dv[a][0] + Dm[1] * dv[a][1] + Dm[2] * dv[a][2]);
+          Fp[a] = Fs + Fb + Fm;
+        }
+        /* NS moments, drag (reading R2), pressure */
+        real f[19];
+        double j[3] = {0, 0, 0}, sum_nz = 0;
+        for (int i = 0; i < 19; ++i) {
+          f[i] = st->fS[i][id];
+          for (int a = 0; a < 3; ++a) j[a] += C19[i][a] * f[i];
+          if (i) sum_nz += f[i];
+        }
+        const double chi = 0.5 * (1.0 + psi);
+        double vs[3], v[3], F[3];
+        for (int a = 0; a < 3; ++a) {
+          vs[a] = (j[a] + 0.5 * Fp[a]) / rho;
+          v[a] = (1.0 - chi) * vs[a];
+          F[a] = Fp[a] - 2.0 * chi * rho * vs[a];
+        }
+        const double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        const double pr = CS2_19 / (1.0 - W19[0]) *
+                          (sum_nz + 0.5 * (v[0] * gr[0] + v[1] * gr[1] + v[2] * gr[2]) -
+                           W19[0] * rho * v2 / (2.0 * CS2_19));
+        /* dendrite geometry and sources */
+        double as, N[3], gmag;
+        aniso3(gs, p[F3_EPS_S], p[F3_GRAD_EPS], &as, N, &gmag);
+        const double as2 = as * as;
+        const double U = supersatf(st, C, psi);
+        const double Q = qpsif(st, phi, psi, U);
+        const double at = -(1.0 / (2.0 * sqrt(2.0))) * W0 * as * (1.0 + (1.0 - k) * U) * (psi - psio) /
+                          sqrt(gs[0] * gs[0] + gs[1] * gs[1] + gs[2] * gs[2] +
+                               p[F3_GRAD_EPS_AT] * p[F3_GRAD_EPS_AT]);
+        const double qf = 0.5 * (1.0 - psi);
+        const double jv = p[F3_D] * qf * C * kappa * (1.0 - phi);     /* gas-vacuum flux J */
+        /* NS collision: D3Q19 MRT with forcing */
+        {
+          real feq[19], G[19], out[19];
+          feq19(pr, rho, v, feq);
+          for (int i = 0; i < 19; ++i) {
+            const double cF = C19[i][0] * F[0] + C19[i][1] * F[1] + C19[i][2] * F[2];
+            const double cv = C19[i][0] * v[0] + C19[i][1] * v[1] + C19[i][2] * v[2];
+            const double cg = C19[i][0] * gr[0] + C19[i][1] * gr[1] + C19[i][2] * gr[2];
+            G[i] = W19[i] * (cF / CS2_19 + cv * cg / CS2_19);
+          }
+          const real S[19] = {1, p[F3_S_E], p[F3_S_EPS], 1, s_q, 1, s_q, 1, s_q,
+                              s_nu, 1, s_nu, 1, s_nu, s_nu, s_nu, s_q, s_q, s_q};
+          collide19(f, feq, S, G, out);
+          for (int i = 0; i < 19; ++i) st->nf[i][id] = out[i];
+        }
+        /* CAC collision: D3Q19 MRT, fluxes at s_phi from M_phi = (1/s - 1/2) c_s^2 */
+        {
+          real hh[19], heq[19], G[19], out[19];
+          for (int i = 0; i < 19; ++i) hh[i] = st->hS[i][id];
+          heq19(phi, v, heq);
+          double G1[3];
+          for (int a = 0; a < 3; ++a) G1[a] = (phi * v[a] - phio * vo[a]) + CS2_19 * aphi * nf[a];
+          for (int i = 0; i < 19; ++i)
+            G[i] = W19[i] * (C19[i][0] * G1[0] + C19[i][1] * G1[1] + C19[i][2] * G1[2]) / CS2_19;
+          real S[19];
+          for (int kk = 0; kk < 19; ++kk) S[kk] = 1.0;
+          S[3] = S[5] = S[7] = s_phi;
+          collide19(hh, heq, S, G, out);
+          for (int i = 0; i < 19; ++i) st->nh[i][id] = out[i];
+        }
+        /* psi: D3Q7 MRT as in the melt-only step */
+        {
+          real gg[7], geq[7], G[7], Fd[7], out[7];
+          for (int i = 0; i < 7; ++i) {
+            gg[i] = st->gS[i][id];
+            geq[i] = W7[i] * psi;
+            G[i] = -W7[i] * (C7[i][0] * N[0] + C7[i][1] * N[1] + C7[i][2] * N[2]) / as2;
+            Fd[i] = W7[i] * Q / tau0 + 0.5 * W7[i] * (Q - Qo) / tau0;
+          }
+          const double s1 = 1.0 / (W0 * W0 * as2 / (tau0 * CS2_7) + 0.5);
+          const real S[7] = {1, s1, s1, s1, 1, 1, 1};
+          collide7(gg, geq, S, G, Fd, out);
+          for (int i = 0; i < 7; ++i) { st->ngpost[i][id] = out[i]; st->ngpre[i][id] = gg[i]; }
+          st->nrr[id] = 1.0 / as2;
+        }
+        /* solute: D3Q7, C v - E grad psi + (1-k)(J_at + J) in the equilibrium
+         * flux, G = w c . d_t(C v) / c_s^2 (backward difference) */
+        {
+          real ss[7], seq[7], G[7], Fd[7] = {0, 0, 0, 0, 0, 0, 0}, out[7];
+          const double A = 1.0 + k - (1.0 - k) * psi;
+          const double DC = 2.0 * p[F3_D] * qf / A;
+          const double E = 2.0 * (1.0 - k) * p[F3_D] * qf * C / (A * A);
+          double Jq[3], Gq[3];
+          for (int a = 0; a < 3; ++a) {
+            Jq[a] = C * v[a] - E * gs[a] + (1.0 - k) * (at * gs[a] + jv * nf[a]);
+            Gq[a] = C * v[a] - Co * vo[a];
+          }
+          for (int i = 0; i < 7; ++i) {
+            ss[i] = st->sS[i][id];
+            seq[i] = W7[i] * C + W7[i] * (C7[i][0] * Jq[0] + C7[i][1] * Jq[1] + C7[i][2] * Jq[2]) / CS2_7;
+            G[i] = W7[i] * (C7[i][0] * Gq[0] + C7[i][1] * Gq[1] + C7[i][2] * Gq[2]) / CS2_7;
+          }
+          const double sc = 1.0 / (DC / CS2_7 + 0.5);
+          const real S[7] = {1, sc, sc, sc, 1, 1, 1};
+          collide7(ss, seq, S, G, Fd, out);
+          for (int i = 0; i < 7; ++i) st->ns[i][id] = out[i];
+        }
+        st->nQ_o[id] = Q;
+        st->nphi_o[id] = phi;
+        st->nC_o[id] = C;
+        for (int a = 0; a < 3; ++a) st->nv_o[a][id] = v[a];
+        st->fld[G3_PHI][id] = phi; st->fld[G3_PSI][id] = psi; st->fld[G3_C][id] = C;
+        st->fld[G3_U][id] = U; st->fld[G3_P][id] = pr;
+        st->fld[G3_VX][id] = v[0]; st->fld[G3_VY][id] = v[1]; st->fld[G3_VZ][id] = v[2];
+        st->fld[G3_MU][id] = mu;
+      }
+  real *t;
+#define SW(a, b) do { t = (a); (a) = (b); (b) = t; } while (0)
+  for (int i = 0; i < 19; ++i) { SW(st->f[i], st->nf[i]); SW(st->h[i], st->nh[i]); }
+  for (int i = 0; i < 7; ++i) { SW(st->gpre[i], st->ngpre[i]); SW(st->gpost[i], st->ngpost[i]); SW(st->s[i], st->ns[i]); }
+  SW(st->rr, st->nrr); SW(st->Q_o, st->nQ_o); SW(st->phi_o, st->nphi_o); SW(st->C_o, st->nC_o);
+  for (int a = 0; a < 3; ++a) SW(st->v_o[a], st->nv_o[a]);
+#undef SW
+  st->steps++;
+}
+
+void or3f_step(o3fstate *st, int n) {
+  for (int t = 0; t < n; ++t) step3f(st);
+}
+
+int or3f_nfields(void) { return NFLD3F; }
+int or3f_npar(void) { return NPAR3F; }
+
+/* Fields phi, psi, C, U, p, vx, vy, vz, mu_phi of the last step (9 x n). */
+void or3f_fields(const o3fstate *st, double *out) {
+  for (int f = 0; f < NFLD3F; ++f) memcpy(out + (size_t)f * st->n, st->fld[f], st->n * sizeof(double));
+}
+
+/* Raw state, 66 planes: f[19], h[19], g_pre[7], g_post[7], r, s[7], Q_o,
+ * phi_o, C_o, vx_o, vy_o, vz_o. */
+int or3f_state_planes(void) { return 66; }
+void or3f_state(const o3fstate *st, double *out) {
+  const real *pl[66];
+  int q = 0;
+  for (int i = 0; i < 19; ++i) pl[q++] = st->f[i];
+  for (int i = 0; i < 19; ++i) pl[q++] = st->h[i];
+  for (int i = 0; i < 7; ++i) pl[q++] = st->gpre[i];
+  for (int i = 0; i < 7; ++i) pl[q++] = st->gpost[i];
+  pl[q++] = st->rr;
+  for (int i = 0; i < 7; ++i) pl[q++] = st->s[i];
+  pl[q++] = st->Q_o; pl[q++] = st->phi_o; pl[q++] = st->C_o;
+  for (int a = 0; a < 3; ++a) pl[q++] = st->v_o[a];
+  for (int p = 0; p < q; ++p) memcpy(out + (size_t)p * st->n, pl[p], st->n * sizeof(double));
+}
+
+/* Totals (compensated): sum phi, sum C, sum of the NS momentum j = sum c f
+ * (three components) of the current populations. */
+void or3f_totals(const o3fstate *st, double *out) {
+  double s[5] = {0, 0, 0, 0, 0}, c[5] = {0, 0, 0, 0, 0};
+  for (int id = 0; id < st->n; ++id) {
+    double v[5] = {st->fld[G3_PHI][id], st->fld[G3_C][id], 0, 0, 0};
+    for (int i = 0; i < 19; ++i)
+      for (int a = 0; a < 3; ++a) v[2 + a] += C19[i][a] * st->f[i][id];
+    for (int q = 0; q < 5; ++q) {
+      const double t = s[q] + v[q];
+      c[q] += fabs(s[q]) >= fabs(v[q]) ? (s[q] - t) + v[q] : (v[q] - t) + s[q];
+      s[q] = t;
+    }
+  }
+  for (int q = 0; q < 5; ++q) out[q] = s[q] + c[q];
+}
+
+/* Pointwise pieces for the pin tests: the D3Q19 basis and weights, the MRT
+ * collision, the equilibria. */
+void or3f_basis(double *M, double *W, int *C) {
+  build_m19();
+  for (int k = 0; k < 19; ++k)
+    for (int j = 0; j < 19; ++j) M[k * 19 + j] = M19[k][j];
+  for (int j = 0; j < 19; ++j) {
+    W[j] = W19[j];
+    for (int a = 0; a < 3; ++a) C[3 * j + a] = C19[j][a];
+  }
+}
+void or3f_collide19(const double *f, const double *feq, const double *S, const double *G, double *out) {
+  build_m19();
+  collide19(f, feq, S, G, out);
+}
+void or3f_feq(double p, double rho, const double *v, double *out) {
+  build_m19();
+  feq19(p, rho, v, out);
+}

@@ -1,0 +1,203 @@
+"""Pins of the 3-D two-phase oracle (reading R34: NS and CAC on D3Q19 with the
+d'Humieres MRT basis, psi and C on D3Q7, coupled as in 2-D).  Each check is
+fixed by the lattice, a closed form or a reduction, not by the oracle itself:
+lattice isotropy and an orthogonal moment basis, the moments of the
+equilibrium, BGK as the equal-rate special case of the MRT, the viscous decay
+of a shear wave in each orientation, Young-Laplace for a cylinder and a
+sphere, Galilean advection of a gas layer, zero velocity in the solid, a
+rising bubble, and the reduction to the melt-only 3-D step without gas."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_01651_gb300 import workload as wl
+
+P3F = {k: wl.BASE_PARAMS[k] for k in oracle.PARAM_NAMES_3F}
+
+
+def test_d3q19_lattice_and_basis():
+    """Weights and velocities give the isotropic tensors up to fourth order
+    (c_s^2 = 1/3); the 19 moment rows are mutually orthogonal and hold the
+    conserved and hydrodynamic moments (1, c, the traceless and bulk parts of
+    cc)."""
+    M, w, c = oracle.basis19()
+    assert abs(w.sum() - 1) < 1e-15
+    cs2 = 1.0 / 3.0
+    d = np.eye(3)
+    assert np.abs(np.einsum("i,ia->a", w, c)).max() < 1e-15
+    assert np.abs(np.einsum("i,ia,ib->ab", w, c, c) - cs2 * d).max() < 1e-15
+    assert np.abs(np.einsum("i,ia,ib,ic->abc", w, c, c, c)).max() < 1e-15
+    iso4 = cs2 ** 2 * (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d) +
+                       np.einsum("ad,bc->abcd", d, d))
+    assert np.abs(np.einsum("i,ia,ib,ic,id->abcd", w, c, c, c, c) - iso4).max() < 1e-15
+    G = M @ M.T
+    assert np.abs(G - np.diag(np.diag(G))).max() == 0.0
+    assert np.linalg.matrix_rank(M) == 19
+    np.testing.assert_array_equal(M[0], np.ones(19))
+    for a, row in zip(range(3), (3, 5, 7)):
+        np.testing.assert_array_equal(M[row], c[:, a])
+    np.testing.assert_array_equal(M[13], c[:, 0] * c[:, 1])
+    np.testing.assert_array_equal(M[9], 3 * c[:, 0] ** 2 - (c ** 2).sum(1))
+    # pairs (2j-1, 2j) are opposite directions
+    assert all((c[2 * j - 1] == -c[2 * j]).all() for j in range(1, 10))
+
+
+def test_equilibrium_moments_and_bgk_limit():
+    """The pressure-based equilibrium carries p I + rho v v in its second
+    moment and rho v in its first (reading R1); with all rates equal to s the
+    MRT collision is BGK, f - s (f - feq) + (1 - s/2) G."""
+    _, w, c = oracle.basis19()
+    p, rho, v = 0.013, 0.7, np.array([0.02, -0.011, 0.005])
+    feq = oracle.feq19(p, rho, v)
+    assert abs(feq.sum() - rho * 0.0 - (feq[1:].sum() + feq[0])) < 1e-15
+    np.testing.assert_allclose(c.T @ feq, rho * v, atol=1e-16)
+    np.testing.assert_allclose(np.einsum("i,ia,ib->ab", feq, c, c),
+                               p * np.eye(3) + rho * np.outer(v, v), atol=1e-16)
+    rng = np.random.default_rng(5)
+    f, fe, G = rng.normal(size=19), rng.normal(size=19), rng.normal(size=19)
+    for s in (0.6, 1.0, 1.7):
+        out = oracle.collide19(f, fe, np.full(19, s), G)
+        np.testing.assert_allclose(out, f - s * (f - fe) + (1 - s / 2) * G, atol=1e-14)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_shear_wave_decays_at_the_viscous_rate(axis):
+    """A shear wave in pure liquid decays as exp(-nu k^2 t), nu = (1/s_nu -
+    1/2) c_s^2 (reading R23), whichever axis it varies along."""
+    n, A = 16, 1e-3
+    z, y, x = np.mgrid[0:n, 0:n, 0:n].astype(float)
+    v = [np.zeros_like(x) for _ in range(3)]
+    comp = (axis + 1) % 3
+    v[comp] = A * np.sin(2 * np.pi * (x, y, z)[axis] / n)
+    one = np.ones_like(x)
+    o = oracle.Oracle3F(n, n, n, dict(P3F, g=0.0))
+    o.init_fields(one, -one, one, *v)
+    key = "v" + "xyz"[comp]
+    o.step(1)
+    a0 = np.abs(o.fields()[key]).max()
+    o.step(200)
+    a1 = np.abs(o.fields()[key]).max()
+    rate = math.log(a0 / a1) / 200
+    assert math.isclose(rate, P3F["nu"] * (2 * np.pi / n) ** 2, rel_tol=5e-3)
+    for other in set("xyz") - {"xyz"[comp]}:
+        assert np.abs(o.fields()["v" + other]).max() < 1e-6 * A
+
+
+def _laplace(shape, R, T, cylinder):
+    W, sigma = 2.0, 1e-3
+    nx, ny, nz = shape
+    o = oracle.Oracle3F(nx, ny, nz, dict(P3F, g=0.0, sigma=sigma, W_phi=W, nu=0.3))
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:nx].astype(float)
+    if cylinder:        # axis along x
+        r = np.sqrt((y - ny / 2) ** 2 + (z - nz / 2) ** 2)
+    else:
+        r = np.sqrt((x - nx / 2) ** 2 + (y - ny / 2) ** 2 + (z - nz / 2) ** 2)
+    phi = 0.5 + 0.5 * np.tanh(math.sqrt(0.5) / W * (r - R) / 2)
+    o.init_fields(phi, -np.ones_like(phi), phi)
+    o.step(T)
+    f = o.fields()
+    dp = f["p"][r < R - 2 * W].mean() - f["p"][r > R + 2 * W].mean()
+    vmax = max(np.abs(f[k]).max() for k in ("vx", "vy", "vz"))
+    return dp, sigma, vmax
+
+
+def test_laplace_law_cylinder():
+    """Young-Laplace (Eq. eq-laplace) with one curvature: a gas cylinder along
+    x settles to p_in - p_out = sigma / R; the residual parasitic current is
+    below 1e-5 (0.3 % of sigma / mu)."""
+    R = 10.0
+    dp, sigma, vmax = _laplace((2, 64, 64), R, 2000, True)
+    assert math.isclose(dp, sigma / R, rel_tol=0.02)
+    assert vmax < 1e-5
+
+
+def test_laplace_law_sphere():
+    """Young-Laplace with two curvatures: a spherical bubble, p_in - p_out =
+    2 sigma / R; a force that acted along two axes only would give sigma / R."""
+    R = 7.0
+    dp, sigma, _ = _laplace((32, 32, 32), R, 1000, False)
+    assert math.isclose(dp, 2 * sigma / R, rel_tol=0.02)
+
+
+def test_gas_layer_translates_with_uniform_flow():
+    """Galilean check of the CAC advection and the mass-consistent momentum
+    flux (Section 2.2) along z: a flat gas layer in a uniform flow normal to
+    it is carried rigidly at that speed, the flow stays uniform, the solute is
+    carried with it and sum phi, sum C stay constant."""
+    nz, W, V, T = 96, 2.0, 0.01, 400
+    zz = np.arange(nz, dtype=float)
+    phi1 = 0.5 + 0.5 * np.tanh((np.abs(zz - 48.0) - 16.0) / (2 * math.sqrt(2) * W))
+    phi = np.broadcast_to(phi1[:, None, None], (nz, 2, 2)).copy()
+    one = np.ones_like(phi)
+    o = oracle.Oracle3F(2, 2, nz, dict(P3F, g=0.0, sigma=0.0, W_phi=W))
+    o.init_fields(phi, -one, phi, 0 * one, 0 * one, V * one)
+    t0 = o.totals()
+    o.step(T)
+    f, t1 = o.fields(), o.totals()
+    assert np.abs(f["vz"] - V).max() < 0.05 * V
+    assert np.abs(f["vx"]).max() < 1e-15 and np.abs(f["vy"]).max() < 1e-15
+    moved = np.roll(phi1, int(V * T))
+    assert np.abs(f["phi"][:, 0, 0] - moved).max() < 3e-3
+    assert np.abs(f["phi"][:, 0, 0] - phi1).max() > 0.1
+    assert abs(t1["sum_phi"] / t0["sum_phi"] - 1) < 1e-13
+    assert abs(t1["sum_C"] / t0["sum_C"] - 1) < 1e-13
+    # the solute vacancy of the gas layer moves with it
+    dc = 1.0 - f["C"][:, 0, 0]
+    assert abs((zz * dc).sum() / dc.sum() - (48.0 + V * T)) < 0.2
+
+
+def test_solid_has_zero_velocity():
+    """Drag of reading R2: v = (1 - h(psi)) v*, so inside a fully solid cube
+    (psi = 1) the velocity is exactly zero while the melt keeps flowing."""
+    n = 32
+    z, y, x = np.mgrid[0:n, 0:n, 0:n].astype(float)
+    box = lambda a: (abs(x - 16) < a) & (abs(y - 16) < a) & (abs(z - 16) < a)  # noqa: E731
+    psi = np.where(box(8), 1.0, -1.0)
+    one = np.ones_like(x)
+    o = oracle.Oracle3F(n, n, n, dict(P3F, g=0.0))
+    o.init_fields(one, psi, one - 0.85 * (1 + psi) / 2, 0 * one, 0 * one, 1e-3 * one)
+    for _ in range(4):
+        o.step(1)       # the solid moves with the flow it starts in: zero from the first step
+        f = o.fields()
+        assert np.abs(f["psi"][box(3)] - 1.0).max() < 1e-14
+        assert np.abs(f["vz"][box(3)]).max() < 1e-15
+        assert np.abs(f["vz"][~box(12)]).min() > 5e-4
+
+
+def test_bubble_rises_against_gravity():
+    """Buoyancy -(rho - rho_bar) g along -y (reading R13): a bubble in a
+    periodic liquid box rises along +y and stays on its axis."""
+    n, R = 32, 6.0
+    o = oracle.Oracle3F(n, n, n, dict(P3F, g=2e-5, sigma=1e-3, W_phi=2.0, nu=0.1))
+    o.init_spec([], 0.0, [(16.0, 14.0, 16.0, R)])
+    z, y, x = np.mgrid[0:n, 0:n, 0:n].astype(float)
+    o.step(300)
+    f = o.fields()
+    gas = np.maximum(0.5 - f["phi"], 0.0)          # the bubble, not the tails
+    cen = [(q * gas).sum() / gas.sum() for q in (x, y, z)]
+    assert cen[1] > 14.1
+    assert abs(cen[0] - 16.0) < 1e-9 and abs(cen[2] - 16.0) < 1e-9
+    assert f["vy"][16, 14, 16] > 0
+
+
+def test_reduces_to_the_melt_step_without_gas():
+    """With phi = 1 and no flow the two-phase step leaves f = 0 and h = w phi
+    exactly, and psi, C, U follow the melt-only 3-D step (pinned in
+    test_oracle_3d.py) to rounding."""
+    n = 24
+    seeds = [(9.3, 11.0, 12.5), (17.0, 6.0, 5.0)]
+    o = oracle.Oracle3F(n, n, n, dict(P3F, g=0.0))
+    fs = o.fields_from_spec(seeds, 5.0, [])
+    assert (fs["phi"] == 1.0).all()
+    o.init_fields(fs["phi"], fs["psi"], fs["C"])
+    m = oracle.Oracle3D(n, n, n, {k: wl.BASE_PARAMS[k] for k in oracle.PARAM_NAMES_3D})
+    m.init_spec(seeds, 5.0)
+    o.step(40)
+    m.step(40)
+    fo, fm = o.fields(), m.fields()
+    for k in ("psi", "C", "U"):
+        assert np.abs(fo[k] - fm[k]).max() < 1e-12 * max(np.abs(fm[k]).max(), 1e-3), k
+    assert np.abs(fo["vx"]).max() == 0.0 and np.abs(fo["p"]).max() == 0.0
+    assert np.abs(fo["phi"] - 1.0).max() < 1e-15
