@@ -199,14 +199,23 @@ def cpu_oracle_variant(kind: str, steps: int = 0) -> dict:
     Section-4 sides, thermal), '3d' (a 96^3 melt with 8 seeds), '3d_thermal'
     (the same with the temperature lattice)."""
     cores = os.cpu_count() or 1
-    steps = steps or {"thermal": 60, "bounded": 60, "3d": 120, "3d_thermal": 300}[kind]  # ~10 s CPU
+    steps = steps or {"thermal": 60, "bounded": 60, "3d": 120, "3d_thermal": 300,
+                      "3d_flow": 160}[kind]  # about 10 s of CPU work
     code = f"""
 import json, sys, time
 sys.path.insert(0, {ROOT!r})
 import oracle
 from paper_2407_01651_gb300 import workload as wl
 kind = {kind!r}
-if kind in ("3d", "3d_thermal"):
+if kind == "3d_flow":
+    n = 64
+    seeds, R_s, bub = wl.flow_3d(n, 4, 8)
+    p = {{k: wl.BASE_PARAMS[k] for k in oracle.PARAM_NAMES_3F}}
+    o = oracle.Oracle3F(n, n, n, p)
+    o.init_spec(seeds, R_s, bub)
+    sites = n ** 3
+    what = f"{{n}}^3 melt with 4 seeds and 8 bubbles (3-D two-phase oracle)"
+elif kind in ("3d", "3d_thermal"):
     n = 96
     seeds, R_s = wl.growth_3d(n, 8)
     p = {{k: wl.BASE_PARAMS[k] for k in oracle.PARAM_NAMES_3D}}
@@ -503,6 +512,61 @@ def run_3d(args) -> None:
     sim.close()
 
 
+def run_3d_flow(args) -> None:
+    """The 3-D two-phase step (NS and CAC on D3Q19, psi and C on D3Q7) on a
+    periodic 256^3 melt with 32 seeds and 64 bubbles: MLUPS and the HBM
+    roofline at 528 B/LU (FP32: 66 planes read and written, f[19], h[19],
+    g_pre[7], g_post[7], s[7], r, Q_psi, phi_o, C_o, v_o[3])."""
+    import torch
+
+    from paper_2407_01651_gb300 import pf
+    from paper_2407_01651_gb300 import workload as wl
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n = args.size if args.size != 4096 else 256
+    seeds, R_s, bubbles = wl.flow_3d(n)
+    stream = torch.cuda.current_stream()
+    prec = args.precision if args.precision in ("fp32", "fp64") else "fp32"
+    sim = pf.Simulation3F((n, n, n), wl.BASE_PARAMS, prec, stream=stream.cuda_stream)
+    sim.init_spec(seeds, R_s, bubbles)
+    if args.chunk:
+        sim.set_chunk(args.chunk)
+    d0 = sim.reduce()
+    sim.step(args.warmup)
+    l0 = sim.launches
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = sim.launches - l0
+    d = sim.reduce()
+    sites = n ** 3
+    bpl = 66 * 2 * (4 if prec == "fp32" else 8)
+    gbs = bpl * sites * args.steps / ms / 1e6
+    peak, peak_kind = measured_peaks()
+    print(json.dumps({
+        "metric": "3-D two-phase coupled-step MLUPS at 256³ and % of HBM roofline",
+        "value": sites * args.steps / ms / 1e3, "unit": "MLUPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE[prec], "data": "synthetic",
+        "config": {"workload": f"{n}^3 periodic melt, 32 seeds (R=8) and 64 bubbles "
+                               "(R~U[6,14]) at uniform positions, seed 5",
+                   "lattice": [n, n, n], "precision": prec},
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                     "frac": gbs / peak, "traffic": None, "peak_kind": peak_kind,
+                     "bytes_per_lu": bpl, "kernel": "k_step3f (one launch per step)"},
+        "sum_phi_rel_drift": d["sum_phi"] / d0["sum_phi"] - 1.0,
+        "sum_C_rel_drift": d["sum_C"] / d0["sum_C"] - 1.0,
+        "solid_fraction": d["sum_hpsi"] / sites,
+        "gpu_launches": launches,
+        "cpu_baseline": None if args.no_cpu_baseline else cpu_oracle_variant("3d_flow")}))
+    sim.close()
+
+
 def run_thermal(args) -> None:
     """The 4096^2 lattice with the temperature lattice on (Section 4 of the
     paper: Le = 50, c_p^s / c_p = 1, theta0 = -Omega): MLUPS and the HBM
@@ -577,13 +641,14 @@ def main() -> None:
     ap.add_argument("--tile-b", type=int, default=0)
     ap.add_argument("--workload", default="lattice",
                     choices=("lattice", "ensemble", "precision", "thermal", "bounded", "3d",
-                             "3d_thermal"),
+                             "3d_thermal", "3d_flow"),
                     help="lattice: the 4096^2 headline; ensemble: 96 uneven domains; "
                          "precision: 8192x4096 in FP32 / FP16 / BF16 storage; "
                          "thermal: the 4096^2 lattice with the temperature lattice on; "
                          "bounded: the same with the paper's Section-4 boundaries; "
                          "3d: the 3-D dendrite step on a 256^3 melt; "
-                         "3d_thermal: the same with the temperature lattice")
+                         "3d_thermal: the same with the temperature lattice; "
+                         "3d_flow: the 3-D two-phase step (flow, bubbles, dendrites) on 256^3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -610,6 +675,9 @@ def main() -> None:
         return
     if args.workload in ("3d", "3d_thermal"):
         run_3d(args)
+        return
+    if args.workload == "3d_flow":
+        run_3d_flow(args)
         return
 
     import numpy as np

@@ -427,6 +427,65 @@ const char *pf3_last_error(const pf3_handle *h);
 /* Release the handle (NULL is ignored). */
 pf_status pf3_destroy(pf3_handle *h);
 
+/* ------------------------------------------------------------------------
+ * Three-dimensional two-phase step: the coupled step of this library in 3-D.
+ * Incompressible Navier-Stokes (pressure-based equilibrium, forcing of
+ * surface tension, buoyancy along -y, the mass-flux correction and the
+ * diffuse drag v = (1 - h(psi)) v*) and the conservative Allen-Cahn equation
+ * on D3Q19 lattices (w0 = 1/3, faces 1/18, edges 1/36, c_s^2 = 1/3) with the
+ * MRT of Appendix B in the moment basis of d'Humieres et al. (2002) (NS rates:
+ * s_e, s_eps, s_q = 8(2 - s_nu)/(8 - s_nu) on q and m, s_nu on the stresses,
+ * 1 elsewhere; CAC: fluxes at s_phi); psi and C on the D3Q7 lattices of the
+ * pf3_* step with the gas couplings of Section 2 (f3 in Q_psi, the gas-vacuum
+ * flux J) and advection of C.  Isothermal (thermal must be 0), periodic cube,
+ * one grain orientation aligned with the lattice.  Arrays are [z][y][x].
+ * ------------------------------------------------------------------------ */
+typedef struct pf3f_handle pf3f_handle;
+
+/* Raw FP64 state planes of pf3f_get_state: f[19], h[19], g_pre[7], g_post[7],
+ * r = 1/a_s^2, s[7], Q_psi, phi_o, C_o, vx_o, vy_o, vz_o. */
+#define PF3F_STATE_PLANES 66
+/* Field planes of pf3f_get_fields: phi, psi, C, U, p, vx, vy, vz, mu_phi. */
+#define PF3F_FIELD_PLANES 9
+
+/* Handle of an nx x ny x nz lattice (each in [4, 2048]), FP32 or FP64 storage,
+ * on cuda_stream: two state copies of 59 population and 7 auxiliary planes, 9
+ * field planes.  Errors: BAD_ARG (sizes, precision, parameters, thermal = 1),
+ * OOM. */
+pf_status pf3f_create(const pf_params *p, int nx, int ny, int nz, pf_precision prec,
+                      void *cuda_stream, pf3f_handle **out);
+/* Spherical seeds n_seeds x (x, y, z) of radius R_s and bubbles n_bub x (x, y,
+ * z, R): psi = max tanh(sqrt(2 beta_psi)(R_s - r)/W0), phi = min [1/2 + 1/2
+ * tanh(sqrt(2 beta_phi)(r - R)/(2 W_phi))], C = phi (1 - (1-k) h(psi)), at rest
+ * (p = 0); populations at equilibrium.  Sets the buoyancy reference rho_bar
+ * from the mean phi.  Synchronises.  Errors: BAD_ARG, OOM, CUDA. */
+pf_status pf3f_init_spec(pf3f_handle *h, const double *seeds, int n_seeds, double R_s,
+                         const double *bubbles, int n_bub);
+/* Initial fields (host, FP64): seven planes of nx*ny*nz in the order phi, psi,
+ * C, vx, vy, vz, p (n = 7 nx ny nz); populations at equilibrium, rho_bar from
+ * the mean phi.  Synchronises.  Errors: BAD_ARG (size, non-finite), OOM, CUDA. */
+pf_status pf3f_set_fields(pf3f_handle *h, const double *fields7, size_t n);
+/* Buoyancy reference density (after initialisation; replaces the mean). */
+pf_status pf3f_set_rho_bar(pf3f_handle *h, double rho_bar);
+double pf3f_get_rho_bar(const pf3f_handle *h);
+/* Planes per tile of the z-march (default 16). */
+pf_status pf3f_set_chunk(pf3f_handle *h, int chunk);
+/* Advance n_steps (enqueued).  Errors: BAD_ARG, STATE (not initialised), CUDA. */
+pf_status pf3f_step(pf3f_handle *h, int n_steps);
+/* Fields of the last step (PF3F_FIELD_PLANES planes of n).  Synchronises. */
+pf_status pf3f_get_fields(pf3f_handle *h, double *out, size_t n);
+/* Raw state (PF3F_STATE_PLANES planes of n).  Synchronises. */
+pf_status pf3f_get_state(pf3f_handle *h, double *out, size_t n);
+/* FP64 totals of the last fields: out[0] = sum phi, out[1] = sum C (both
+ * conserved), out[2] = sum h(psi).  Synchronises.  Errors: BAD_ARG, OOM, CUDA. */
+pf_status pf3f_reduce(pf3f_handle *h, double out[3]);
+/* Kernel launches of the handle; -1 for NULL. */
+long long pf3f_launch_count(const pf3f_handle *h);
+/* Last error of the handle, or of the last failed pf3f_create for NULL. */
+const char *pf3f_last_error(const pf3f_handle *h);
+/* Release the handle (NULL is ignored). */
+pf_status pf3f_destroy(pf3f_handle *h);
+
 /* Release every resource of the handle (NULL is ignored). */
 pf_status pf_destroy(pf_handle *h);
 

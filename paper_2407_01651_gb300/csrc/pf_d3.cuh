@@ -1,0 +1,69 @@
+// pf_d3.cuh -- pieces shared by the 3-D z-march kernels (pf_step3d.cu,
+// pf_step3f.cu): the 32 x 8 column tile with its halo ring, the D3Q7 velocity
+// set, plane addressing, periodic wrapping and the isotropic D3Q19-weighted
+// gradient and Laplacian over a 4-slot shared-memory ring of planes.
+#pragma once
+#include "pf_device.cuh"
+
+namespace pf {
+namespace d3 {
+
+constexpr int TX = 32, TY = 8;                    // interior tile
+constexpr int HX = TX + 2, HY = TY + 2;           // tile with its halo ring
+constexpr int NIN = TX * TY;                      // 256 interior threads
+constexpr int NHALO = HX * HY - NIN;              // 84 halo threads
+constexpr int THREADS = 352;                      // 11 warps (340 used)
+
+__device__ __forceinline__ constexpr int cx7(int i) { return i == 1 ? 1 : (i == 2 ? -1 : 0); }
+__device__ __forceinline__ constexpr int cy7(int i) { return i == 3 ? 1 : (i == 4 ? -1 : 0); }
+__device__ __forceinline__ constexpr int cz7(int i) { return i == 5 ? 1 : (i == 6 ? -1 : 0); }
+template <typename R>
+__device__ __forceinline__ R w7(int i) { return i == 0 ? R(0.25) : R(0.125); }
+
+template <typename T>
+__device__ __forceinline__ const T* pl(const T* p, int k, unsigned long long ps) { return p + (size_t)k * ps; }
+template <typename T>
+__device__ __forceinline__ T* pl(T* p, int k, unsigned long long ps) { return p + (size_t)k * ps; }
+
+// one step across a periodic boundary (z), and a full modulo (tile columns,
+// which may lie up to a tile beyond a small domain)
+__device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+__device__ __forceinline__ int wrapm(int a, int n) { a %= n; return a < 0 ? a + n : a; }
+
+// 3 sum_q w_q c_q (X(x + c_q) - X(x)) over the 6 face (w = 1/18) and 12 edge
+// (w = 1/36) neighbours of the ring column (hy, hx): the isotropic gradient.
+template <typename R>
+__device__ __forceinline__ void grad18(const R (*Pm)[HX], const R (*P0)[HX], const R (*Pp)[HX],
+                                       int hy, int hx, R& gx, R& gy, R& gz) {
+  const R X0 = P0[hy][hx];
+  auto d = [&](const R (*Pl)[HX], int dx, int dy) { return Pl[hy + dy][hx + dx] - X0; };
+  const R w1 = R(1.0 / 18.0), w2 = R(1.0 / 36.0);
+  gx = w1 * (d(P0, 1, 0) - d(P0, -1, 0)) +
+       w2 * ((d(P0, 1, 1) - d(P0, -1, 1)) + (d(P0, 1, -1) - d(P0, -1, -1)) +
+             (d(Pp, 1, 0) - d(Pp, -1, 0)) + (d(Pm, 1, 0) - d(Pm, -1, 0)));
+  gy = w1 * (d(P0, 0, 1) - d(P0, 0, -1)) +
+       w2 * ((d(P0, 1, 1) - d(P0, 1, -1)) + (d(P0, -1, 1) - d(P0, -1, -1)) +
+             (d(Pp, 0, 1) - d(Pp, 0, -1)) + (d(Pm, 0, 1) - d(Pm, 0, -1)));
+  gz = w1 * (d(Pp, 0, 0) - d(Pm, 0, 0)) +
+       w2 * ((d(Pp, 1, 0) - d(Pm, 1, 0)) + (d(Pp, -1, 0) - d(Pm, -1, 0)) +
+             (d(Pp, 0, 1) - d(Pm, 0, 1)) + (d(Pp, 0, -1) - d(Pm, 0, -1)));
+  gx *= R(3); gy *= R(3); gz *= R(3);
+}
+
+// 6 sum_q w_q (X(x + c_q) - X(x)) over the same 18 neighbours: the isotropic
+// Laplacian (2 / c_s^2) sum w (X_q - X_0) with c_s^2 = 1/3.
+template <typename R>
+__device__ __forceinline__ R lap18(const R (*Pm)[HX], const R (*P0)[HX], const R (*Pp)[HX],
+                                   int hy, int hx) {
+  const R X0 = P0[hy][hx];
+  auto d = [&](const R (*Pl)[HX], int dx, int dy) { return Pl[hy + dy][hx + dx] - X0; };
+  const R faces = (d(P0, 1, 0) + d(P0, -1, 0)) + (d(P0, 0, 1) + d(P0, 0, -1)) +
+                  (d(Pp, 0, 0) + d(Pm, 0, 0));
+  const R edges = ((d(P0, 1, 1) + d(P0, -1, -1)) + (d(P0, 1, -1) + d(P0, -1, 1))) +
+                  ((d(Pp, 1, 0) + d(Pm, -1, 0)) + (d(Pp, -1, 0) + d(Pm, 1, 0))) +
+                  ((d(Pp, 0, 1) + d(Pm, 0, -1)) + (d(Pp, 0, -1) + d(Pm, 0, 1)));
+  return R(1.0 / 3.0) * faces + R(1.0 / 6.0) * edges;
+}
+
+}  // namespace d3
+}  // namespace pf

@@ -18,27 +18,16 @@
 #include <vector>
 
 #include "../../include/pf.h"
-#include "pf_device.cuh"
+#include "pf_d3.cuh"
 
 namespace pf {
 namespace d3 {
 
-constexpr int TX = 32, TY = 8;                    // interior tile
-constexpr int HX = TX + 2, HY = TY + 2;           // tile with its halo ring
-constexpr int NIN = TX * TY;                      // 256 interior threads
-constexpr int NHALO = HX * HY - NIN;              // 84 halo threads
-constexpr int THREADS = 352;                      // 11 warps (340 used)
 // planes: g_pre 0..6, g_post 7..13, s 14..20, thermal e 21..27 (storage
 // type); r, Q_o (compute type)
 constexpr int G_PRE = 0, G_POST = 7, S_POP = 14, E_POP = 21, NPOP3 = 21, NPOP3_TH = 28;
 constexpr int A3_RR = 0, A3_QO = 1, NAUX3 = 2;
 constexpr int NSTATE3 = 23, NSTATE3_TH = 30;      // raw FP64 state planes
-
-__device__ __forceinline__ constexpr int cx7(int i) { return i == 1 ? 1 : (i == 2 ? -1 : 0); }
-__device__ __forceinline__ constexpr int cy7(int i) { return i == 3 ? 1 : (i == 4 ? -1 : 0); }
-__device__ __forceinline__ constexpr int cz7(int i) { return i == 5 ? 1 : (i == 6 ? -1 : 0); }
-template <typename R>
-__device__ __forceinline__ R w7(int i) { return i == 0 ? R(0.25) : R(0.125); }
 
 template <typename R>
 struct Coef3 {
@@ -59,16 +48,6 @@ struct Args3 {
   int tiles_x, tiles_y, tiles_z;
   Coef3<R> c;
 };
-
-template <typename T>
-__device__ __forceinline__ const T* pl(const T* p, int k, unsigned long long ps) { return p + (size_t)k * ps; }
-template <typename T>
-__device__ __forceinline__ T* pl(T* p, int k, unsigned long long ps) { return p + (size_t)k * ps; }
-
-// one step across a periodic boundary (z), and a full modulo (tile columns,
-// which may lie up to a tile beyond a small domain)
-__device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
-__device__ __forceinline__ int wrapm(int a, int n) { a %= n; return a < 0 ? a + n : a; }
 
 template <typename S, typename R>
 __device__ __forceinline__ unsigned long long src7(const Args3<S, R>& a, int x, int y, int z, int i) {
@@ -118,26 +97,6 @@ template <typename R>
 __device__ __forceinline__ R supersat3(const Coef3<R>& c, R C, R psi) {
   const R A = (R(1) + c.k) - (R(1) - c.k) * psi;
   return (R(2) * C * frcp(A) - R(1)) * c.inv_omk;
-}
-
-// 3 sum_q w_q c_q (X(x + c_q) - X(x)) over the 6 face (w = 1/18) and 12 edge
-// (w = 1/36) neighbours of the ring column (hy, hx): the isotropic gradient.
-template <typename R>
-__device__ __forceinline__ void grad18(const R (*Pm)[HX], const R (*P0)[HX], const R (*Pp)[HX],
-                                       int hy, int hx, R& gx, R& gy, R& gz) {
-  const R X0 = P0[hy][hx];
-  auto d = [&](const R (*Pl)[HX], int dx, int dy) { return Pl[hy + dy][hx + dx] - X0; };
-  const R w1 = R(1.0 / 18.0), w2 = R(1.0 / 36.0);
-  gx = w1 * (d(P0, 1, 0) - d(P0, -1, 0)) +
-       w2 * ((d(P0, 1, 1) - d(P0, -1, 1)) + (d(P0, 1, -1) - d(P0, -1, -1)) +
-             (d(Pp, 1, 0) - d(Pp, -1, 0)) + (d(Pm, 1, 0) - d(Pm, -1, 0)));
-  gy = w1 * (d(P0, 0, 1) - d(P0, 0, -1)) +
-       w2 * ((d(P0, 1, 1) - d(P0, 1, -1)) + (d(P0, -1, 1) - d(P0, -1, -1)) +
-             (d(Pp, 0, 1) - d(Pp, 0, -1)) + (d(Pm, 0, 1) - d(Pm, 0, -1)));
-  gz = w1 * (d(Pp, 0, 0) - d(Pm, 0, 0)) +
-       w2 * ((d(Pp, 1, 0) - d(Pm, 1, 0)) + (d(Pp, -1, 0) - d(Pm, -1, 0)) +
-             (d(Pp, 0, 1) - d(Pm, 0, 1)) + (d(Pp, 0, -1) - d(Pm, 0, -1)));
-  gx *= R(3); gy *= R(3); gz *= R(3);
 }
 
 // TH: the temperature lattice of Appendix B on D3Q7 (rho H conserved, theta =
@@ -276,7 +235,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R> a) {
                   Sz = fma(hs, gq * Nz, Jz - s1 * Jz);
           const R b = m0 * R(0.125);
           R go[7];
-          go[0] = m0 - R(6) * b;
+          go[0] = fma(R(-6), b, m0);           // m0 - 6 m0/8 = m0/4, exact
           go[1] = fma(R(0.5), Sx, b); go[2] = fma(R(-0.5), Sx, b);
           go[3] = fma(R(0.5), Sy, b); go[4] = fma(R(-0.5), Sy, b);
           go[5] = fma(R(0.5), Sz, b); go[6] = fma(R(-0.5), Sz, b);
@@ -301,7 +260,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R> a) {
           const R Sx = Jx - sc * (Jx - Ex), Sy = Jy - sc * (Jy - Ey), Sz = Jz - sc * (Jz - Ez);
           const R b = C * R(0.125);
           R so[7];
-          so[0] = C - R(6) * b;
+          so[0] = fma(R(-6), b, C);            // C - 6 C/8 = C/4, exact
           so[1] = fma(R(0.5), Sx, b); so[2] = fma(R(-0.5), Sx, b);
           so[3] = fma(R(0.5), Sy, b); so[4] = fma(R(-0.5), Sy, b);
           so[5] = fma(R(0.5), Sz, b); so[6] = fma(R(-0.5), Sz, b);

@@ -132,6 +132,22 @@ def lib() -> ctypes.CDLL:
     L.pf3_last_error.argtypes = [P]
     L.pf3_last_error.restype = ctypes.c_char_p
     L.pf3_destroy.argtypes = [P]
+    L.pf3f_create.argtypes = [ctypes.POINTER(pf_params), I, I, I, I, P, ctypes.POINTER(P)]
+    L.pf3f_init_spec.argtypes = [P, D, I, ctypes.c_double, D, I]
+    L.pf3f_set_fields.argtypes = [P, D, S]
+    L.pf3f_set_rho_bar.argtypes = [P, ctypes.c_double]
+    L.pf3f_get_rho_bar.argtypes = [P]
+    L.pf3f_get_rho_bar.restype = ctypes.c_double
+    L.pf3f_set_chunk.argtypes = [P, I]
+    L.pf3f_step.argtypes = [P, I]
+    L.pf3f_get_fields.argtypes = [P, D, S]
+    L.pf3f_get_state.argtypes = [P, D, S]
+    L.pf3f_reduce.argtypes = [P, D]
+    L.pf3f_launch_count.argtypes = [P]
+    L.pf3f_launch_count.restype = ctypes.c_longlong
+    L.pf3f_last_error.argtypes = [P]
+    L.pf3f_last_error.restype = ctypes.c_char_p
+    L.pf3f_destroy.argtypes = [P]
     for name in ("pf_params_default", "pf_params_derived", "pf_create", "pf_init_fields",
                  "pf_set_fields", "pf_step", "pf_get_fields", "pf_get_state", "pf_set_state",
                  "pf_reduce", "pf_sync", "pf_destroy", "pf_set_step_config",
@@ -139,7 +155,9 @@ def lib() -> ctypes.CDLL:
                  "pf_set_launch", "pf_autotune", "pf_set_temperature", "pf_reduce_thermal",
                  "pf_set_boundaries", "pf3_create", "pf3_init_seeds", "pf3_set_fields",
                  "pf3_set_chunk", "pf3_step", "pf3_get_fields", "pf3_get_state", "pf3_reduce",
-                 "pf3_destroy", "pf3_set_temperature", "pf3_reduce_thermal"):
+                 "pf3_destroy", "pf3_set_temperature", "pf3_reduce_thermal", "pf3f_create",
+                 "pf3f_init_spec", "pf3f_set_fields", "pf3f_set_rho_bar", "pf3f_set_chunk",
+                 "pf3f_step", "pf3f_get_fields", "pf3f_get_state", "pf3f_reduce", "pf3f_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -469,3 +487,89 @@ class Simulation3D:
     @property
     def launches(self) -> int:
         return lib().pf3_launch_count(self.h)
+
+
+PF3F_STATE_PLANES = 66
+FIELDS_3F = ("phi", "psi", "C", "U", "p", "vx", "vy", "vz", "mu")
+
+
+def _check3f(code: int, handle=None) -> None:
+    if code != PF_OK:
+        raise PFError(code, lib().pf3f_last_error(handle).decode(errors="replace"))
+
+
+class Simulation3F:
+    """Handle of the 3-D two-phase step (NS and CAC on D3Q19, psi and C on
+    D3Q7, periodic nx x ny x nz); arrays are [z][y][x]; seeds (x, y, z),
+    bubbles (x, y, z, R)."""
+
+    def __init__(self, shape, params: dict | None = None, precision: str = "fp32", stream=None):
+        nx, ny, nz = (int(v) for v in shape)
+        self.shape = (nz, ny, nx)
+        self.params = params_from_dict(params)
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                stream = 0
+        h = ctypes.c_void_p()
+        _check3f(lib().pf3f_create(ctypes.byref(self.params), nx, ny, nz, PRECISIONS[precision],
+                                   ctypes.c_void_p(stream), ctypes.byref(h)))
+        self.h = h
+        self.n = nx * ny * nz
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            code = lib().pf3f_destroy(self.h)
+            self.h = None
+            _check3f(code)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_spec(self, seeds, R_s: float, bubbles) -> None:
+        s = np.ascontiguousarray(np.asarray(seeds, dtype=np.float64).reshape(-1, 3))
+        b = np.ascontiguousarray(np.asarray(bubbles, dtype=np.float64).reshape(-1, 4))
+        _check3f(lib().pf3f_init_spec(self.h, _dp(s), len(s), float(R_s), _dp(b), len(b)), self.h)
+
+    def set_fields(self, phi, psi, C, vx=None, vy=None, vz=None, p=None) -> None:
+        planes = [phi, psi, C] + [np.zeros(self.shape) if a is None else a for a in (vx, vy, vz, p)]
+        a = np.ascontiguousarray(np.stack([np.asarray(q, dtype=np.float64).reshape(self.shape)
+                                           for q in planes]))
+        _check3f(lib().pf3f_set_fields(self.h, _dp(a), a.size), self.h)
+
+    @property
+    def rho_bar(self) -> float:
+        return lib().pf3f_get_rho_bar(self.h)
+
+    def set_rho_bar(self, rho_bar: float) -> None:
+        _check3f(lib().pf3f_set_rho_bar(self.h, float(rho_bar)), self.h)
+
+    def set_chunk(self, chunk: int) -> None:
+        _check3f(lib().pf3f_set_chunk(self.h, int(chunk)), self.h)
+
+    def step(self, n: int = 1) -> None:
+        _check3f(lib().pf3f_step(self.h, int(n)), self.h)
+
+    def fields(self) -> dict:
+        out = np.empty(len(FIELDS_3F) * self.n)
+        _check3f(lib().pf3f_get_fields(self.h, _dp(out), out.size), self.h)
+        return dict(zip(FIELDS_3F, out.reshape((len(FIELDS_3F),) + self.shape)))
+
+    def get_state(self) -> np.ndarray:
+        out = np.empty(PF3F_STATE_PLANES * self.n)
+        _check3f(lib().pf3f_get_state(self.h, _dp(out), out.size), self.h)
+        return out.reshape((PF3F_STATE_PLANES,) + self.shape)
+
+    def reduce(self) -> dict:
+        out = np.zeros(3)
+        _check3f(lib().pf3f_reduce(self.h, _dp(out)), self.h)
+        return {"sum_phi": out[0], "sum_C": out[1], "sum_hpsi": out[2]}
+
+    @property
+    def launches(self) -> int:
+        return lib().pf3f_launch_count(self.h)

@@ -157,3 +157,15 @@ def growth_3d(n: int = 256, n_seeds: int = 64, rng_seed: int = 4, R_s: float = 8
     rng = SplitMix64(rng_seed)
     seeds = [(n * rng.uniform(), n * rng.uniform(), n * rng.uniform()) for _ in range(n_seeds)]
     return seeds, R_s
+
+
+def flow_3d(n: int = 256, n_seeds: int = 32, n_bub: int = 64, rng_seed: int = 5,
+            R_s: float = 8.0, R_b=(6.0, 14.0)):
+    """A periodic n^3 melt with n_seeds spherical seeds (radius R_s) and n_bub
+    spherical bubbles (radius uniform in R_b) at uniform positions, for the 3-D
+    two-phase step; returns (seeds, R_s, bubbles)."""
+    rng = SplitMix64(rng_seed)
+    seeds = [(n * rng.uniform(), n * rng.uniform(), n * rng.uniform()) for _ in range(n_seeds)]
+    bubbles = [(n * rng.uniform(), n * rng.uniform(), n * rng.uniform(),
+                R_b[0] + (R_b[1] - R_b[0]) * rng.uniform()) for _ in range(n_bub)]
+    return seeds, R_s, bubbles

@@ -14,7 +14,7 @@ HEADER = os.path.join(ROOT, "include", "pf.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?[\w]+\s*\**\s*(pf3?_\w+)\s*\(", text, flags=re.M)
+    names = re.findall(r"^\s*(?:const\s+)?[\w]+\s*\**\s*(pf3?f?_\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 

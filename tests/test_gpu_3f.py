@@ -1,0 +1,168 @@
+"""The 3-D two-phase step (NS and CAC on D3Q19, psi and C on D3Q7, reading
+R34) of the CUDA path against the FP64 3-D two-phase oracle, through the C
+ABI.  FP64 within 1e-11 relative per field over a few steps (1e-9 over a
+hundred); FP32 within 1e-5 per step for phi, psi, C, U and within 5e-5 for
+v and p of a developed flow (their populations carry the rounding of O(0.05)
+values into O(1e-3) differences) and 1e-4 for mu_phi (W_phi^2 times the
+18-neighbour Laplacian amplifies the storage rounding of phi)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_01651_gb300 import pf
+from paper_2407_01651_gb300 import workload as wl
+
+pytestmark = pytest.mark.gpu
+
+P3F = {k: wl.BASE_PARAMS[k] for k in oracle.PARAM_NAMES_3F}
+FLOOR = {"phi": 1e-9, "psi": 1e-9, "C": 1e-9, "U": 0.1, "p": 1e-4, "vx": 1e-3, "vy": 1e-3,
+         "vz": 1e-3, "mu": 1e-3}
+TOL32 = {"phi": 1e-5, "psi": 1e-5, "C": 1e-5, "U": 1e-5, "p": 5e-5, "vx": 5e-5, "vy": 5e-5,
+         "vz": 5e-5, "mu": 1e-4}
+
+RAGGED = (40, 19, 13)
+SEEDS = [(10.3, 9.1, 6.2), (33.0, 4.0, 11.5)]
+BUBBLES = [(25.0, 12.0, 7.0, 5.0), (6.0, 15.0, 3.0, 3.5)]
+
+
+def rel(a, b, floor):
+    return np.abs(a - b).max() / max(np.abs(b).max(), floor)
+
+
+def flow_fields(shape, seeds, R_s, bubbles, amp=1e-3):
+    """Spec fields plus a smooth velocity and pressure (a developed flow)."""
+    nx, ny, nz = shape
+    o = oracle.Oracle3F(nx, ny, nz, P3F)
+    f = o.fields_from_spec(seeds, R_s, bubbles)
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:nx].astype(float)
+    kx, ky, kz = 2 * np.pi / nx, 2 * np.pi / ny, 2 * np.pi / nz
+    vx = amp * np.sin(ky * y + 0.3) * np.cos(kz * z)
+    vy = amp * np.sin(kz * z + 1.1) * np.cos(kx * x)
+    vz = amp * np.sin(kx * x + 0.7) * np.cos(ky * y)
+    p = 0.1 * amp * np.cos(kx * x) * np.sin(ky * y + kz * z)
+    return f["phi"], f["psi"], f["C"], vx, vy, vz, p
+
+
+def pair(shape, precision, seeds=SEEDS, R_s=5.0, bubbles=BUBBLES, params=P3F, amp=1e-3):
+    nx, ny, nz = shape
+    planes = flow_fields(shape, seeds, R_s, bubbles, amp)
+    o = oracle.Oracle3F(nx, ny, nz, params)
+    o.init_fields(*planes)
+    sim = pf.Simulation3F(shape, dict(wl.BASE_PARAMS, **params), precision)
+    sim.set_fields(*planes)
+    return o, sim
+
+
+def compare(o, sim, tol):
+    fo, fg = o.fields(), sim.fields()
+    errs = {k: rel(fg[k], fo[k], FLOOR[k]) for k in fg}
+    lim = {k: (tol[k] if isinstance(tol, dict) else tol) for k in fg}
+    assert all(errs[k] <= lim[k] for k in fg), errs
+    return errs
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_3f_initial_state(precision, tol):
+    o, sim = pair(RAGGED, precision)
+    assert abs(sim.rho_bar / o.rho_bar - 1) < 1e-7
+    so, sg = o.state(), sim.get_state()
+    assert sg.shape[0] == pf.PF3F_STATE_PLANES == so.shape[0]
+    for p in range(pf.PF3F_STATE_PLANES):
+        assert rel(sg[p], so[p], 1e-12) <= max(tol, 1e-15), p
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", TOL32)])
+def test_3f_steps_match_oracle(precision, tol):
+    o, sim = pair(RAGGED, precision)
+    o.set_rho_bar(sim.rho_bar)
+    sim.set_chunk(5)
+    for _ in range(3):
+        o.step(1)
+        sim.step(1)
+        compare(o, sim, tol)
+    if precision == "fp64":
+        so, sg = o.state(), sim.get_state()
+        for p in range(pf.PF3F_STATE_PLANES):
+            assert rel(sg[p], so[p], 1e-12) <= 1e-10, p
+
+
+def test_3f_fp64_many_steps_and_conservation():
+    """100 FP64 steps with gravity, a bubble and a seed: within 1e-9 of the
+    oracle; sum phi and sum C constant to 1e-12."""
+    n = 24
+    params = dict(P3F, g=1e-5)
+    o, sim = pair((n, n, n), "fp64", [(8.0, 12.0, 12.0)], 5.0, [(16.5, 11.0, 12.5, 4.5)], params)
+    o.set_rho_bar(sim.rho_bar)
+    r0 = sim.reduce()
+    o.step(100)
+    sim.step(100)
+    compare(o, sim, 1e-9)
+    r1 = sim.reduce()
+    assert abs(r1["sum_phi"] / r0["sum_phi"] - 1) < 1e-12
+    assert abs(r1["sum_C"] / r0["sum_C"] - 1) < 1e-12
+
+
+def test_3f_fp32_drift_and_bounded_error():
+    n = 32
+    o, sim = pair((n, n, n), "fp32", [(10.0, 12.0, 16.0)], 6.0,
+                  [(22.0, 20.0, 10.0, 6.0), (8.0, 26.0, 24.0, 4.0)])
+    o.set_rho_bar(sim.rho_bar)
+    r0 = sim.reduce()
+    o.step(200)
+    sim.step(200)
+    compare(o, sim, 2e-3)
+    r1 = sim.reduce()
+    assert abs(r1["sum_phi"] / r0["sum_phi"] - 1) <= 1e-6
+    assert abs(r1["sum_C"] / r0["sum_C"] - 1) <= 1e-6
+
+
+def test_3f_full_size_windows():
+    """The 256^3 two-phase workload (32 seeds, 64 bubbles) in the benchmark's
+    launch configuration: after 2 steps, 24^3 windows around seeds, bubbles
+    and across the periodic corner match oracle windows placed in global
+    coordinates with the global buoyancy reference."""
+    n = 256
+    seeds, R_s, bubbles = wl.flow_3d(n)
+    sim = pf.Simulation3F((n, n, n), wl.BASE_PARAMS, "fp32")
+    sim.init_spec(seeds, R_s, bubbles)
+    T = 2
+    sim.step(T)
+    fg = sim.fields()
+    sim.close()
+    W, M = 24, 2 * T
+    centres = ([(int(s[0]) + 7, int(s[1]), int(s[2])) for s in seeds[:2]] +
+               [(int(b[0]) + int(b[3]), int(b[1]), int(b[2])) for b in bubbles[:2]] +
+               [(n - 2, n - 2, n - 2)])
+    ref, got = {k: [] for k in fg}, {k: [] for k in fg}
+    rho_bar = None
+    for cx, cy, cz in centres:
+        x0, y0, z0 = cx - W // 2, cy - W // 2, cz - W // 2
+        o = oracle.Oracle3F(W, W, W, P3F, window=(n, n, n, x0, y0, z0))
+        if rho_bar is None:
+            rho_bar = P3F["rho_g"] + o.mean_phi_global(bubbles) * (P3F["rho_l"] - P3F["rho_g"])
+        o.set_rho_bar(rho_bar)
+        o.init_spec(seeds, R_s, bubbles)
+        o.step(T)
+        fo = o.fields()
+        idx = [(np.arange(M, W - M) + c0) % n for c0 in (z0, y0, x0)]
+        for k in fg:
+            ref[k].append(fo[k][M:W - M, M:W - M, M:W - M].ravel())
+            got[k].append(fg[k][np.ix_(*idx)].ravel())
+    for k in fg:
+        err = rel(np.concatenate(got[k]), np.concatenate(ref[k]), FLOOR[k])
+        assert err <= TOL32[k], (k, err)
+
+
+def test_3f_configuration_errors():
+    with pytest.raises(pf.PFError):
+        pf.Simulation3F((3, 8, 8), wl.BASE_PARAMS, "fp32")
+    with pytest.raises(pf.PFError):
+        pf.Simulation3F((8, 8, 8), wl.BASE_PARAMS, "fp16")
+    with pytest.raises(pf.PFError):
+        pf.Simulation3F((8, 8, 8), dict(wl.BASE_PARAMS, **wl.THERMAL_PARAMS), "fp32")
+    sim = pf.Simulation3F((8, 8, 8), wl.BASE_PARAMS, "fp32")
+    with pytest.raises(pf.PFError) as e:
+        sim.step(1)                        # not initialised
+    assert e.value.code == pf.PF_ERR_STATE
+    with pytest.raises(pf.PFError):
+        sim.set_fields(*[np.full((8, 8, 8), np.nan)] * 3)
