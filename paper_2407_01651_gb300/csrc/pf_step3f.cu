@@ -289,71 +289,91 @@ __global__ void __launch_bounds__(THREADS, 1) k_step3f(ArgsF<S, R> a) {
         // p = c_s^2 / (1 - w0) [sum_{i != 0} f_i + v.grad(rho)/2 - w0 rho v^2 / (2 c_s^2)]
         const R pr = R(0.5) * (snz.value() + R(0.5) * (v[0] * gr[0] + v[1] * gr[1] + v[2] * gr[2]) -
                                R(0.5) * rho * v2);
-        // NS collision.  e_i = f_eq_i + G_i / 2 with G_i = w_i 3 [c.F + (c.v)(c.grad rho)]
+        // NS collision on opposite pairs (2j-1, 2j), c = +-c_j.  With G_i = 3 w_i
+        // [c.F + (c.v)(c.grad rho)], f_eq + G/2 = E_j +- O_j where
+        //   E_j = w (3p + rho (4.5 cu^2 - 1.5 v^2) + 1.5 cu cg),  O_j = w (3 rho cu + 1.5 cF),
+        // and d = f - f_eq + G/2 has the pair sum De_j and difference Do_j.  The
+        // even moment rows (e, eps, p's) see only De, the odd ones (q, m) only Do.
         {
-          auto eq_half = [&](int i) {
-            const R cu = R(c19(i, 0)) * v[0] + R(c19(i, 1)) * v[1] + R(c19(i, 2)) * v[2];
-            const R cF = R(c19(i, 0)) * F[0] + R(c19(i, 1)) * F[1] + R(c19(i, 2)) * F[2];
-            const R cg = R(c19(i, 0)) * gr[0] + R(c19(i, 1)) * gr[1] + R(c19(i, 2)) * gr[2];
-            const R wi = w19<R>(i);
-            R e = wi * (R(3) * pr + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * v2)) +
-                  wi * R(1.5) * (cF + cu * cg);
-            if (i == 0) e -= R(3) * pr;
-            return e;
-          };
+          const R w0 = R(1.0 / 3.0);
           R n[NMOM];
 #pragma unroll
           for (int k = 0; k < NMOM; ++k) n[k] = R(0);
+          const R e0 = w0 * (R(3) * pr - R(1.5) * rho * v2) - R(3) * pr;   // f_eq_0, G_0 = 0
+          {
+            const R d0 = fv[0] - e0;
 #pragma unroll
-          for (int i = 0; i < 19; ++i) {
-            const R fi = fv[i];
+            for (int k = 0; k < NMOM; ++k)
+              if (mrow(k, 0) != 0) n[k] += R(mrow(k, 0)) * d0;
+          }
+          auto pair_eo = [&](int jp, R& E, R& O) {
+            const int i = 2 * jp - 1;
             const R cu = R(c19(i, 0)) * v[0] + R(c19(i, 1)) * v[1] + R(c19(i, 2)) * v[2];
             const R cF = R(c19(i, 0)) * F[0] + R(c19(i, 1)) * F[1] + R(c19(i, 2)) * F[2];
             const R cg = R(c19(i, 0)) * gr[0] + R(c19(i, 1)) * gr[1] + R(c19(i, 2)) * gr[2];
             const R wi = w19<R>(i);
-            R feq = wi * (R(3) * pr + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * v2));
-            if (i == 0) feq -= R(3) * pr;
-            const R Gh = wi * R(1.5) * (cF + cu * cg);      // G_i / 2
-            const R d = (fi - feq) + Gh;                     // f - f_eq + G/2
+            E = wi * (R(3) * pr + rho * (R(4.5) * cu * cu - R(1.5) * v2) + R(1.5) * cu * cg);
+            O = wi * (R(3) * rho * cu + R(1.5) * cF);
+            return wi * R(3) * cu * cg;          // G_e: the even part of G (2 x its half)
+          };
+#pragma unroll
+          for (int jp = 1; jp <= 9; ++jp) {
+            const int i = 2 * jp - 1;
+            R E, O;
+            const R Ge = pair_eo(jp, E, O);
+            // f_eq = (E - Ge/2) +- (O - Go/2), G/2 = Ge/2 +- Go/2, Go = 3 w cF
+            const R Go = w19<R>(i) * R(3) * (R(c19(i, 0)) * F[0] + R(c19(i, 1)) * F[1] +
+                                             R(c19(i, 2)) * F[2]);
+            const R De = (fv[i] + fv[i + 1]) - R(2) * E + R(2) * Ge;
+            const R Do = (fv[i] - fv[i + 1]) - R(2) * O + R(2) * Go;
 #pragma unroll
             for (int k = 0; k < NMOM; ++k)
-              if (mrow(k, i) != 0) n[k] += R(mrow(k, i)) * d;
+              if (mrow(k, i) != 0) n[k] += R(mrow(k, i)) * (mrow(k, i) == mrow(k, i + 1) ? De : Do);
           }
 #pragma unroll
           for (int k = 0; k < NMOM; ++k) n[k] *= c.cm[k];
-#pragma unroll
-          for (int i = 0; i < 19; ++i) {
-            R o = eq_half(i);
+          {
+            R o = e0;
 #pragma unroll
             for (int k = 0; k < NMOM; ++k)
-              if (mrow(k, i) != 0) o += R(mrow(k, i)) * n[k];
-            st<S, R>(pl(a.out, F_POP + i, a.ps), site, o);
+              if (mrow(k, 0) != 0) o += R(mrow(k, 0)) * n[k];
+            st<S, R>(pl(a.out, F_POP, a.ps), site, o);
+          }
+#pragma unroll
+          for (int jp = 1; jp <= 9; ++jp) {
+            const int i = 2 * jp - 1;
+            R E, O;
+            pair_eo(jp, E, O);
+#pragma unroll
+            for (int k = 0; k < NMOM; ++k) {
+              if (mrow(k, i) == 0) continue;
+              if (mrow(k, i) == mrow(k, i + 1)) E += R(mrow(k, i)) * n[k];
+              else O += R(mrow(k, i)) * n[k];
+            }
+            st<S, R>(pl(a.out, F_POP + i, a.ps), site, E + O);
+            st<S, R>(pl(a.out, F_POP + i + 1, a.ps), site, E - O);
           }
         }
         // CAC collision: h_eq = w phi (1 + 3 c.v), G_i = 3 w c.G1 with G1 =
-        // d_t(phi v) + c_s^2 kappa phi (1-phi) n; fluxes at s_phi, the rest at 1
+        // d_t(phi v) + c_s^2 kappa phi (1-phi) n; fluxes at s_phi, the rest at 1.
+        // On pairs: h_eq + G/2 = w phi +- O_j, O_j = w (3 phi cu + 1.5 cG); the
+        // flux of d = h - h_eq + G/2 is sum_j c_j [(h+ - h-) - 2 w (3 phi cu - 1.5 cG)].
         {
           R G1[3];
 #pragma unroll
           for (int q = 0; q < 3; ++q) G1[q] = (phi * v[q] - phio * vo[q]) + R(1.0 / 3.0) * aphi * nf[q];
-          // heq + G/2 and G/2 of direction i
-          auto heq_half = [&](int i) {
-            const R cu = R(c19(i, 0)) * v[0] + R(c19(i, 1)) * v[1] + R(c19(i, 2)) * v[2];
-            const R cG = R(c19(i, 0)) * G1[0] + R(c19(i, 1)) * G1[1] + R(c19(i, 2)) * G1[2];
-            return w19<R>(i) * (phi * (R(1) + R(3) * cu) + R(1.5) * cG);
-          };
-          auto g_half = [&](int i) {
-            return w19<R>(i) * R(1.5) *
-                   (R(c19(i, 0)) * G1[0] + R(c19(i, 1)) * G1[1] + R(c19(i, 2)) * G1[2]);
-          };
           R nj[3] = {R(0), R(0), R(0)};
 #pragma unroll
-          for (int i = 1; i < 19; ++i) {
-            const R hi = ld<R>(pl(a.in, H_POP + i, a.ps), src19(a, x, y, z, i));
-            const R d = hi - heq_half(i) + R(2) * g_half(i);     // h - h_eq + G/2
-            if (c19(i, 0)) nj[0] += R(c19(i, 0)) * d;
-            if (c19(i, 1)) nj[1] += R(c19(i, 1)) * d;
-            if (c19(i, 2)) nj[2] += R(c19(i, 2)) * d;
+          for (int jp = 1; jp <= 9; ++jp) {
+            const int i = 2 * jp - 1;
+            const R hp = ld<R>(pl(a.in, H_POP + i, a.ps), src19(a, x, y, z, i));
+            const R hm = ld<R>(pl(a.in, H_POP + i + 1, a.ps), src19(a, x, y, z, i + 1));
+            const R cu = R(c19(i, 0)) * v[0] + R(c19(i, 1)) * v[1] + R(c19(i, 2)) * v[2];
+            const R cG = R(c19(i, 0)) * G1[0] + R(c19(i, 1)) * G1[1] + R(c19(i, 2)) * G1[2];
+            const R Do = (hp - hm) - R(2) * w19<R>(i) * (R(3) * phi * cu - R(1.5) * cG);
+            if (c19(i, 0)) nj[0] += R(c19(i, 0)) * Do;
+            if (c19(i, 1)) nj[1] += R(c19(i, 1)) * Do;
+            if (c19(i, 2)) nj[2] += R(c19(i, 2)) * Do;
           }
           const R cj = (R(1) - c.s_phi) * R(0.1);           // |row j|^2 = 10
 #pragma unroll
@@ -366,13 +386,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_step3f(ArgsF<S, R> a) {
           const R b = round_to_multiple(phi * R(1.0 / 36.0), R(0.5) * quantum_quarter_ulp(phi));
           st<S, R>(pl(a.out, H_POP, a.ps), site, fma(R(-24), b, phi));
 #pragma unroll
-          for (int i = 1; i < 19; ++i) {
+          for (int jp = 1; jp <= 9; ++jp) {
+            const int i = 2 * jp - 1;
             const R cu = R(c19(i, 0)) * v[0] + R(c19(i, 1)) * v[1] + R(c19(i, 2)) * v[2];
-            R odd = w19<R>(i) * R(3) * phi * cu + g_half(i);
+            const R cG = R(c19(i, 0)) * G1[0] + R(c19(i, 1)) * G1[1] + R(c19(i, 2)) * G1[2];
+            R odd = w19<R>(i) * (R(3) * phi * cu + R(1.5) * cG);
             if (c19(i, 0)) odd += R(c19(i, 0)) * nj[0];
             if (c19(i, 1)) odd += R(c19(i, 1)) * nj[1];
             if (c19(i, 2)) odd += R(c19(i, 2)) * nj[2];
-            st<S, R>(pl(a.out, H_POP + i, a.ps), site, (c2_19(i) == 1 ? R(2) * b : b) + odd);
+            const R base = c2_19(i) == 1 ? R(2) * b : b;
+            st<S, R>(pl(a.out, H_POP + i, a.ps), site, base + odd);
+            st<S, R>(pl(a.out, H_POP + i + 1, a.ps), site, base - odd);
           }
         }
         // dendrite geometry, sources (anisotropy summed over three axes)
