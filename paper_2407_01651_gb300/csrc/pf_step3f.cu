@@ -29,13 +29,15 @@
 namespace pf {
 namespace d3f {
 
-using d3::HX;
-using d3::HY;
-using d3::NHALO;
-using d3::NIN;
-using d3::THREADS;
-using d3::TX;
-using d3::TY;
+// column tile of the z-march: TX x TY interior columns and their halo ring
+// (the stencil helpers of pf_d3.cuh take rows of HX = TX + 2)
+constexpr int TX = d3::TX, TY = 8;
+constexpr int HX = TX + 2, HY = TY + 2;
+constexpr int NIN = TX * TY;
+constexpr int NHALO = HX * HY - NIN;
+constexpr int THREADS = (NIN + NHALO + 31) / 32 * 32;
+constexpr int MIN_CTAS = 1;
+static_assert(HX == d3::HX, "the stencil helpers assume rows of d3::HX");
 using d3::cx7;
 using d3::cy7;
 using d3::cz7;
@@ -161,7 +163,7 @@ __device__ __forceinline__ void stream_g(const ArgsF<S, R>& a, int x, int y, int
 }
 
 template <typename S, typename R>
-__global__ void __launch_bounds__(THREADS, 1) k_step3f(ArgsF<S, R> a) {
+__global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R> a) {
   // rings of phi, psi and v_o (dynamic: 54 KB in FP64)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R (*rphi)[HY][HX] = reinterpret_cast<R (*)[HY][HX]>(smem_raw);
