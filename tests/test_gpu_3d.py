@@ -265,3 +265,17 @@ def test_3d_thermal_configuration_errors():
     with pytest.raises(pf.PFError) as e:
         sim.set_temperature(np.zeros((8, 8, 8)))          # already stepped
     assert e.value.code == pf.PF_ERR_STATE
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 4), (5, 7, 6), (33, 9, 17)])
+@pytest.mark.parametrize("thermal", [False, True])
+def test_3d_small_and_ragged_lattices(shape, thermal):
+    """The smallest lattice, odd sizes, and ragged tiles and chunks, with and
+    without the temperature lattice: FP64 within 1e-11 over 4 steps."""
+    nx, ny, nz = shape
+    params = T3 if thermal else P3
+    o, sim = pair(shape, [(nx / 3, ny / 2, nz / 2)], 1.5, "fp64", params)
+    sim.set_chunk(3)
+    o.step(4)
+    sim.step(4)
+    (compare_t if thermal else compare)(o, sim, 1e-11)

@@ -166,3 +166,31 @@ def test_3f_configuration_errors():
     assert e.value.code == pf.PF_ERR_STATE
     with pytest.raises(pf.PFError):
         sim.set_fields(*[np.full((8, 8, 8), np.nan)] * 3)
+
+
+def test_3f_free_rates_and_gravity():
+    """Free MRT rates of the energy moments away from 1 (s_e = 1.2, s_eps =
+    0.9) and gravity on: the e and eps rows of the NS collision enter, FP64
+    within 1e-11 of the oracle over 3 steps."""
+    params = dict(P3F, s_e=1.2, s_eps=0.9, g=2e-5)
+    o, sim = pair(RAGGED, "fp64", params=params)
+    o.set_rho_bar(sim.rho_bar)
+    for _ in range(3):
+        o.step(1)
+        sim.step(1)
+        compare(o, sim, 1e-11)
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 4), (5, 7, 6), (33, 9, 17)])
+def test_3f_small_and_ragged_lattices(shape):
+    """The smallest lattice (one site more than the stencil reach on each
+    side), odd sizes, and tiles ragged in x and y with chunks ragged in z."""
+    nx, ny, nz = shape
+    seeds = [(nx / 3, ny / 2, nz / 2)]
+    bubbles = [(2 * nx / 3, ny / 3, nz / 3, 1.5)]
+    o, sim = pair(shape, "fp64", seeds=seeds, R_s=1.5, bubbles=bubbles)
+    o.set_rho_bar(sim.rho_bar)
+    sim.set_chunk(3)
+    o.step(4)
+    sim.step(4)
+    compare(o, sim, 1e-11)
