@@ -25,6 +25,12 @@ __device__ __forceinline__ const T* pl(const T* p, int k, unsigned long long ps)
 template <typename T>
 __device__ __forceinline__ T* pl(T* p, int k, unsigned long long ps) { return p + (size_t)k * ps; }
 
+// Hint: bring the line that holds p into L2 ahead of its use (no register is
+// written, so a z-march can look two planes ahead for free).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p)));
+}
+
 // one step across a periodic boundary (z), and a full modulo (tile columns,
 // which may lie up to a tile beyond a small domain)
 __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }

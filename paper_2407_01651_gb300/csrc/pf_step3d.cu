@@ -170,6 +170,14 @@ __global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R> a) {
           stream7(a, S_POP, x, y, z, sv);
         }
         Qo = ld<R>(pl(a.ain, A3_QO, a.ps), site);
+        // warm L2 with this column's populations two planes ahead
+        const int z2 = z + 2 >= a.nz ? z + 2 - a.nz : z + 2;
+        const unsigned long long pf2 = ((unsigned long long)z2 * a.ny + y) * a.nx + x;
+        constexpr int NPF = TH ? NPOP3_TH : NPOP3;
+#pragma unroll
+        for (int q = 0; q < NPF; ++q) prefetch_l2(pl(a.in, q, a.ps) + pf2);
+        prefetch_l2(pl(a.ain, A3_RR, a.ps) + pf2);
+        prefetch_l2(pl(a.ain, A3_QO, a.ps) + pf2);
       }
       if (active) {
         R psi;
