@@ -45,6 +45,7 @@ struct pf_handle {
   int n_aux = N_AUX;        // lagged-scalar planes per state copy
   int n_phys = N_PHYS;      // planes of the raw FP64 state
   int any_bc = 0;           // some domain has a non-periodic side
+  int any_io = 0;           // ... among them an inlet or an outlet
   // With non-periodic sides (y-march): tiles touching such a side ("edge"
   // tiles) run the boundary-aware kernel, the others the periodic one.  Tiles
   // are ordered [plain tiles of every domain][edge tiles of every domain]; each
@@ -707,7 +708,7 @@ static StepArgs<S, R> make_step_args(const pf_handle* h, const void* pin, const 
   a.err = h->d_err;
   a.drop_copies = h->drop_copies;
   a.thermal = h->thermal;
-  a.bc = h->any_bc;
+  a.bc = h->any_bc ? (h->any_io ? 2 : 1) : 0;
   a.kp = make_kparams<R>(h->p);
   return a;
 }
@@ -735,6 +736,7 @@ static pf_status launch_all(pf_handle* h, StepArgs<S, R> a, cudaStream_t stream)
     return PF_OK;
   };
   auto go1 = [&](int t0, int t1, int bc) { return go(t0, t1, bc, stream); };
+  const int edge_kind = h->any_io ? 2 : 1;   // boundary kernel with or without inlet/outlet code
   pf_status st = PF_OK;
   if (h->any_bc) {
     // plain tiles: the periodic kernel; edge tiles: the boundary-aware one, on
@@ -748,18 +750,18 @@ static pf_status launch_all(pf_handle* h, StepArgs<S, R> a, cudaStream_t stream)
         }
         PF_CUDA(h, cudaEventRecord(h->fork_ev, stream));
         PF_CUDA(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
-        if ((st = go(h->n_plain, h->ntiles, 1, h->side)) != PF_OK) return st;
+        if ((st = go(h->n_plain, h->ntiles, edge_kind, h->side)) != PF_OK) return st;
         if ((st = go1(0, h->n_plain, 0)) != PF_OK) return st;
         PF_CUDA(h, cudaEventRecord(h->join_ev, h->side));
         PF_CUDA(h, cudaStreamWaitEvent(stream, h->join_ev, 0));
         return PF_OK;
       }
       if ((st = go1(0, h->n_plain, 0)) != PF_OK) return st;
-      return go1(h->n_plain, h->ntiles, 1);
+      return go1(h->n_plain, h->ntiles, edge_kind);
     }
     for (size_t d = 0; d < h->ddesc.size(); ++d) {
       if ((st = go1(h->plain0[d], h->plain1[d], 0)) != PF_OK) return st;
-      if ((st = go1(h->edge0[d], h->edge1[d], 1)) != PF_OK) return st;
+      if ((st = go1(h->edge0[d], h->edge1[d], edge_kind)) != PF_OK) return st;
     }
     return PF_OK;
   }
@@ -1132,9 +1134,12 @@ extern "C" pf_status pf_set_boundaries(pf_handle* h, int dom, const int bc[4]) {
     return fail(h, PF_ERR_STATE, "set the boundaries before initialising the domain");
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
   for (int k = 0; k < 4; ++k) h->ddesc[dom].bc[k] = (unsigned char)bc[k];
-  h->any_bc = 0;
+  h->any_bc = h->any_io = 0;
   for (const DomDesc& d : h->ddesc)
-    if (d.bc[0] || d.bc[1] || d.bc[2] || d.bc[3]) h->any_bc = 1;
+    for (int k = 0; k < 4; ++k) {
+      if (d.bc[k]) h->any_bc = 1;
+      if (d.bc[k] == PF_BC_INLET || d.bc[k] == PF_BC_OUTLET) h->any_io = 1;
+    }
   if (h->any_bc && h->variant != STEP_YMARCH) {
     h->variant = STEP_YMARCH;
     h->chunk = 32;

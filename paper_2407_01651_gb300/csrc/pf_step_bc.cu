@@ -21,6 +21,8 @@
 //     copied at an outlet; corners: the y side's map, then the x side's).
 // Sites away from a non-periodic side take the periodic pulls of pf_pull.cuh.
 // FP32 and FP64 storage only.
+#include <type_traits>
+
 #include "pf_site.cuh"
 
 namespace pf {
@@ -61,9 +63,13 @@ struct PullSrc {
   unsigned site;
   int q, mode;
 };
+// IO: some side of the launch is an inlet or an outlet; without them the
+// compiler drops those branches from the boundary pulls
+template <bool IO>
 __device__ __forceinline__ int bounce_rank(int t) {
-  return t == BC_WALL ? 1 : (t == BC_FARFIELD ? 2 : (t == BC_INLET ? 3 : 0));
+  return t == BC_WALL ? 1 : (t == BC_FARFIELD ? 2 : (IO && t == BC_INLET ? 3 : 0));
 }
+template <bool IO>
 __device__ __forceinline__ PullSrc pull_src(const DomDesc& d, int x, int y, int i) {
   const int nx = d.nx, ny = d.ny;
   int sx = x - cx9(i), sy = y - cy9(i), q = i, bounce = 0, outlet = 0;
@@ -71,15 +77,15 @@ __device__ __forceinline__ PullSrc pull_src(const DomDesc& d, int x, int y, int 
     const int t = d.bc[sx < 0 ? 0 : 1];
     if (t == BC_PERIODIC) sx += sx < 0 ? nx : -nx;
     else if (t == BC_SYMMETRIC) { sx = sx < 0 ? -1 - sx : 2 * nx - 1 - sx; q = mirx9(q); }
-    else if (t == BC_OUTLET) { sx = sx < 0 ? 0 : nx - 1; outlet = 1; }
-    else bounce = bounce_rank(t);
+    else if (IO && t == BC_OUTLET) { sx = sx < 0 ? 0 : nx - 1; outlet = 1; }
+    else bounce = bounce_rank<IO>(t);
   }
   if (sy < 0 || sy >= ny) {
     const int t = d.bc[sy < 0 ? 2 : 3];
     if (t == BC_PERIODIC) sy += sy < 0 ? ny : -ny;
     else if (t == BC_SYMMETRIC) { sy = sy < 0 ? -1 - sy : 2 * ny - 1 - sy; q = miry9(q); }
-    else if (t == BC_OUTLET) { sy = sy < 0 ? 0 : ny - 1; outlet = 1; }
-    else bounce = max(bounce, bounce_rank(t));
+    else if (IO && t == BC_OUTLET) { sy = sy < 0 ? 0 : ny - 1; outlet = 1; }
+    else bounce = max(bounce, bounce_rank<IO>(t));
   }
   if (bounce) return {site_at(d, x, y), opp9(i), bounce};
   return {site_at(d, sx, sy), q, outlet ? 4 : 0};
@@ -93,24 +99,24 @@ __device__ __forceinline__ bool near_side(const DomDesc& d, int x, int y) {
 
 // Ring fields: 0 phi, 1 psi, 2 vx_o, 3 vy_o, 4 U.  Ghost value across one side
 // of type t on axis (0: x, 1: y) from the mirror site's value v.
-template <typename R>
+template <typename R, bool IO>
 __device__ __forceinline__ R ghost_map(const KParams<R>& kp, int t, int axis, int field, R v) {
-  if (t == BC_OUTLET) return v;
+  if (IO && t == BC_OUTLET) return v;
   if (field == 2 || field == 3) {
     const bool normal = (field == 2) == (axis == 0);
     if (t == BC_SYMMETRIC) return normal ? -v : v;
-    if (t == BC_INLET) return R(2) * (field == 2 ? kp.vin_x : kp.vin_y) - v;
+    if (IO && t == BC_INLET) return R(2) * (field == 2 ? kp.vin_x : kp.vin_y) - v;
     return -v;
   }
-  if (t == BC_FARFIELD || t == BC_INLET) {
+  if (t == BC_FARFIELD || (IO && t == BC_INLET)) {
     if (field == 1) return R(-2) - v;   // 2 psi_far - psi, psi_far = -1
     if (field == 4) return -v;          // 2 U_far - U, U_far = 0
-    if (field == 0 && t == BC_INLET) return R(2) - v;   // liquid inflow, phi = 1
+    if (IO && field == 0 && t == BC_INLET) return R(2) - v;   // liquid inflow, phi = 1
   }
   return v;
 }
 
-template <typename S, typename R, bool BIG>
+template <typename S, typename R, bool BIG, bool IO>
 __device__ __forceinline__ void pull_hg_b(const StepArgs<S, R>& a, const DomDesc& d, int x,
                                           int y, R h[9], R g[5], R& phi, R& psi, R& psio) {
   const unsigned ps = (unsigned)a.plane_stride;
@@ -118,9 +124,9 @@ __device__ __forceinline__ void pull_hg_b(const StepArgs<S, R>& a, const DomDesc
   CSum<R> sh;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    const PullSrc p = pull_src(d, x, y, i);
+    const PullSrc p = pull_src<IO>(d, x, y, i);
     R v = ld<R>(pbase<BIG>(a.in, P_H + p.q, ps), pidx<BIG>(P_H + p.q, ps, p.site));
-    if (p.mode == 3) v = -v + R(2) * w9<R>(i) * R(1);   // inlet: phi = 1
+    if (IO && p.mode == 3) v = -v + R(2) * w9<R>(i) * R(1);   // inlet: phi = 1
     h[i] = v;
     sh.add(h[i]);
   }
@@ -129,7 +135,7 @@ __device__ __forceinline__ void pull_hg_b(const StepArgs<S, R>& a, const DomDesc
   R po = R(0);
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    const PullSrc p = pull_src(d, x, y, i);
+    const PullSrc p = pull_src<IO>(d, x, y, i);
     const R gold = ld<R>(pbase<BIG>(a.in, P_GPRE + i, ps), pidx<BIG>(P_GPRE + i, ps, own));
     R gpo = ld<R>(pbase<BIG>(a.in, P_GPOST + p.q, ps), pidx<BIG>(P_GPOST + p.q, ps, p.site));
     if (p.mode == 2 || p.mode == 3) gpo = -gpo + R(2) * w5<R>(i) * R(-1);
@@ -142,26 +148,29 @@ __device__ __forceinline__ void pull_hg_b(const StepArgs<S, R>& a, const DomDesc
   psio = po;
 }
 
-template <typename S, typename R, bool BIG, bool TH>
+template <typename S, typename R, bool BIG, bool TH, bool IO>
 __device__ __forceinline__ void load_site_b(const StepArgs<S, R>& a, const DomDesc& d, int x,
                                             int y, SiteIn<R>& in) {
   const unsigned ps = (unsigned)a.plane_stride;
   const unsigned own = site_at(d, x, y);
   in.phio = ld<R>(pbase<BIG>(a.ain, A_PHIO, ps), pidx<BIG>(A_PHIO, ps, own));
-  const R vxo = ld<R>(pbase<BIG>(a.ain, A_VXO, ps), pidx<BIG>(A_VXO, ps, own));
-  const R vyo = ld<R>(pbase<BIG>(a.ain, A_VYO, ps), pidx<BIG>(A_VYO, ps, own));
+  R vxo = R(0), vyo = R(0);
+  if constexpr (IO) {
+    vxo = ld<R>(pbase<BIG>(a.ain, A_VXO, ps), pidx<BIG>(A_VXO, ps, own));
+    vyo = ld<R>(pbase<BIG>(a.ain, A_VYO, ps), pidx<BIG>(A_VYO, ps, own));
+  }
   const R rho_o = a.kp.rho_g + in.phio * a.kp.drho;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    const PullSrc p = pull_src(d, x, y, i);
-    if (p.mode == 4) {
+    const PullSrc p = pull_src<IO>(d, x, y, i);
+    if (IO && p.mode == 4) {
       // pressure outlet p = 0: -f*_opp(own) + 2 rho_o w_i [(c.v_o)^2 / (2 cs^4) - v_o^2 / (2 cs^2)]
       const R fo = ld<R>(pbase<BIG>(a.in, P_F + opp9(i), ps), pidx<BIG>(P_F + opp9(i), ps, own));
       const R cu = R(cx9(i)) * vxo + R(cy9(i)) * vyo;
       in.f[i] = -fo + R(2) * rho_o * w9<R>(i) * (R(4.5) * cu * cu - R(1.5) * (vxo * vxo + vyo * vyo));
     } else {
       R v = ld<R>(pbase<BIG>(a.in, P_F + p.q, ps), pidx<BIG>(P_F + p.q, ps, p.site));
-      if (p.mode == 3)   // inlet: moving-wall bounce-back
+      if (IO && p.mode == 3)   // inlet: moving-wall bounce-back
         v += R(2) * (a.kp.rho_g + a.kp.drho) * w9<R>(i) * R(3) *
              (R(cx9(i)) * a.kp.vin_x + R(cy9(i)) * a.kp.vin_y);
       in.f[i] = v;
@@ -169,7 +178,7 @@ __device__ __forceinline__ void load_site_b(const StepArgs<S, R>& a, const DomDe
   }
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    const PullSrc p = pull_src(d, x, y, i);
+    const PullSrc p = pull_src<IO>(d, x, y, i);
     R v = ld<R>(pbase<BIG>(a.in, P_S + p.q, ps), pidx<BIG>(P_S + p.q, ps, p.site));
     if (p.mode == 2 || p.mode == 3) v = -v + R(2) * w5<R>(i) * R(1);   // C_far = 1
     in.s[i] = v;
@@ -185,14 +194,14 @@ __device__ __forceinline__ void load_site_b(const StepArgs<S, R>& a, const DomDe
   if constexpr (TH) in.Ho = ld<R>(pbase<BIG>(a.ain, A_HO, ps), pidx<BIG>(A_HO, ps, own));
 }
 
-template <typename S, typename R, bool BIG>
+template <typename S, typename R, bool BIG, bool IO>
 __device__ __forceinline__ R pull_U_b(const StepArgs<S, R>& a, const DomDesc& d, int x, int y,
                                       R psi) {
   const unsigned ps = (unsigned)a.plane_stride;
   CSum<R> cs;
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    const PullSrc p = pull_src(d, x, y, i);
+    const PullSrc p = pull_src<IO>(d, x, y, i);
     R v = ld<R>(pbase<BIG>(a.in, P_S + p.q, ps), pidx<BIG>(P_S + p.q, ps, p.site));
     if (p.mode == 2 || p.mode == 3) v = -v + R(2) * w5<R>(i) * R(1);
     cs.add(v);
@@ -205,7 +214,7 @@ __device__ __forceinline__ R pull_U_b(const StepArgs<S, R>& a, const DomDesc& d,
 
 }  // namespace
 
-template <typename S, typename R, bool BIG, bool TH>
+template <typename S, typename R, bool BIG, bool TH, bool IO>
 __global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 3 : 2)
     k_step_ymarch_bc(StepArgs<S, R> a) {
   constexpr int RW = YM_W + 2;
@@ -251,19 +260,19 @@ __global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 3 : 2)
       }
       R v[NF];
       const bool near = near_side(d, col, ey);
-      if (near) pull_hg_b<S, R, BIG>(a, d, col, ey, h, g, v[0], v[1], po);
+      if (near) pull_hg_b<S, R, BIG, IO>(a, d, col, ey, h, g, v[0], v[1], po);
       else pull_hg<S, R, BIG>(a, sources(d, col, ey), h, g, v[0], v[1], po);
       const unsigned s0 = site_at(d, col, ey);
       v[2] = ld<R>(pbase<BIG>(a.ain, A_VXO, ps), pidx<BIG>(A_VXO, ps, s0));
       v[3] = ld<R>(pbase<BIG>(a.ain, A_VYO, ps), pidx<BIG>(A_VYO, ps, s0));
       if constexpr (TH)
-        v[4] = near ? pull_U_b<S, R, BIG>(a, d, col, ey, v[1])
+        v[4] = near ? pull_U_b<S, R, BIG, IO>(a, d, col, ey, v[1])
                     : pull_U<S, R, BIG>(a, sources(d, col, ey), v[1]);
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         R u = v[f];
-        if (ty >= 0) u = ghost_map<R>(a.kp, ty, 1, f, u);
-        if (tx >= 0) u = ghost_map<R>(a.kp, tx, 0, f, u);
+        if (ty >= 0) u = ghost_map<R, IO>(a.kp, ty, 1, f, u);
+        if (tx >= 0) u = ghost_map<R, IO>(a.kp, tx, 0, f, u);
         ring[f][yr & 3][sc] = u;
       }
     };
@@ -288,7 +297,7 @@ __global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 3 : 2)
       Src9 srcj;
       if (interior) {
         if (near_side(d, col, j)) {
-          load_site_b<S, R, BIG, TH>(a, d, col, j, in);
+          load_site_b<S, R, BIG, TH, IO>(a, d, col, j, in);
           srcj.s[0] = site_at(d, col, j);
         } else {
           srcj = sources(d, col, j);
@@ -317,13 +326,19 @@ __global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? 3 : 2)
 template <typename S, typename R>
 cudaError_t launch_ymarch_bc(const StepArgs<S, R>& a, bool big, int grid, cudaStream_t st) {
   if constexpr (sizeof(S) == sizeof(R)) {
-    if (big) {
-      if (a.thermal) k_step_ymarch_bc<S, R, true, true><<<grid, YM_THREADS, 0, st>>>(a);
-      else k_step_ymarch_bc<S, R, true, false><<<grid, YM_THREADS, 0, st>>>(a);
-    } else {
-      if (a.thermal) k_step_ymarch_bc<S, R, false, true><<<grid, YM_THREADS, 0, st>>>(a);
-      else k_step_ymarch_bc<S, R, false, false><<<grid, YM_THREADS, 0, st>>>(a);
-    }
+    // a.bc: 1 boundary sides, 2 among them an inlet or an outlet
+    auto go = [&](auto io) {
+      constexpr bool IO = decltype(io)::value;
+      if (big) {
+        if (a.thermal) k_step_ymarch_bc<S, R, true, true, IO><<<grid, YM_THREADS, 0, st>>>(a);
+        else k_step_ymarch_bc<S, R, true, false, IO><<<grid, YM_THREADS, 0, st>>>(a);
+      } else {
+        if (a.thermal) k_step_ymarch_bc<S, R, false, true, IO><<<grid, YM_THREADS, 0, st>>>(a);
+        else k_step_ymarch_bc<S, R, false, false, IO><<<grid, YM_THREADS, 0, st>>>(a);
+      }
+    };
+    if (a.bc == 2) go(std::true_type{});
+    else go(std::false_type{});
     return cudaGetLastError();
   } else {
     return cudaErrorInvalidValue;   // boundaries need FP32 or FP64 storage (checked on the host)
@@ -336,14 +351,14 @@ int ymarch_bc_blocks_per_sm(bool big, bool thermal) {
   if constexpr (sizeof(S) == sizeof(R)) {
     if (big) {
       if (thermal)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_ymarch_bc<S, R, true, true>, YM_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_ymarch_bc<S, R, true, true, true>, YM_THREADS, 0);
       else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_ymarch_bc<S, R, true, false>, YM_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_ymarch_bc<S, R, true, false, true>, YM_THREADS, 0);
     } else {
       if (thermal)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_ymarch_bc<S, R, false, true>, YM_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_ymarch_bc<S, R, false, true, true>, YM_THREADS, 0);
       else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_ymarch_bc<S, R, false, false>, YM_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_ymarch_bc<S, R, false, false, true>, YM_THREADS, 0);
     }
   }
   return n > 0 ? n : 1;
