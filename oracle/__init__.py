@@ -356,6 +356,9 @@ def _l3() -> ctypes.CDLL:
             lib.or3_state_planes.restype = I
             lib.or3_state_planes.argtypes = [P]
             lib.or3_thermal_totals.argtypes = [P, D]
+            lib.or3_set_orientation.argtypes = [P, D, I]
+            lib.or3_set_orientation.restype = I
+            lib.or3_orientation.argtypes = [P, I, D]
             _lib3 = lib
     return _lib3
 
@@ -385,6 +388,18 @@ class Oracle3D:
     def init_spec(self, seeds, R_s: float) -> None:
         s = np.ascontiguousarray(_f64(seeds).reshape(-1, 3))
         self.lib.or3_init(self.h, _dp(s), len(s), float(R_s))
+
+    def set_orientation(self, seeds7) -> None:
+        """Grain orientations: n x (x, y, z, qw, qx, qy, qz); each site takes the
+        rotation of the nearest seed."""
+        s = np.ascontiguousarray(_f64(seeds7).reshape(-1, 7))
+        if self.lib.or3_set_orientation(self.h, _dp(s), len(s)) != 0:
+            raise MemoryError("oracle allocation failed")
+
+    def orientation(self, site: int) -> np.ndarray:
+        out = np.zeros(9)
+        self.lib.or3_orientation(self.h, int(site), _dp(out))
+        return out.reshape(3, 3)
 
     def init_fields(self, psi, C, theta=None) -> None:
         self._keep = [_f64(psi).ravel(), _f64(C).ravel(),

@@ -86,6 +86,7 @@ typedef struct {
   real *e[7], *ne[7], *eS[7], *US;                  /* temperature populations (thermal) */
   real *fld[4];                                     /* psi, C, U, theta of the last step */
   real *block;
+  double *rot;     /* grain orientation per site (9 per site, row-major R), or NULL */
 } o3state;
 
 static inline int wrap3(int a, int n) { a %= n; return a < 0 ? a + n : a; }
@@ -121,8 +122,55 @@ o3state *or3_new(int nx, int ny, int nz) {
 
 void or3_free(o3state *st) {
   if (!st) return;
+  free(st->rot);
   free(st->block);
   free(st);
+}
+
+/* Rotation matrix (row-major) of the unit quaternion q = (w, x, y, z) after
+ * normalisation: the crystal axes are the columns of R. */
+static void quat_rot(const double *q, double R[9]) {
+  const double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  const double w = q[0] / n, x = q[1] / n, y = q[2] / n, z = q[3] / n;
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - z * w);     R[2] = 2 * (x * z + y * w);
+  R[3] = 2 * (x * y + z * w);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - x * w);
+  R[6] = 2 * (x * z - y * w);     R[7] = 2 * (y * z + x * w);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* Grain orientations (the 3-D form of reading R10): each site takes the
+ * orientation of the nearest seed (minimum image in the NX x NY x NZ lattice,
+ * the first seed on an exact tie).  seeds: n x (x, y, z, qw, qx, qy, qz). */
+int or3_set_orientation(o3state *st, const double *seeds, int n_seeds) {
+  free(st->rot);
+  st->rot = NULL;
+  if (n_seeds <= 0) return 0;
+  st->rot = (double *)malloc((size_t)st->n * 9 * sizeof(double));
+  if (!st->rot) return -1;
+  for (int z = 0; z < st->nz; ++z)
+    for (int y = 0; y < st->ny; ++y)
+      for (int x = 0; x < st->nx; ++x) {
+        const int id = (z * st->ny + y) * st->nx + x;
+        const double X[3] = {st->x0 + x, st->y0 + y, st->z0 + z}, L[3] = {st->NX, st->NY, st->NZ};
+        int best = 0;
+        double bd = 0;
+        for (int s2 = 0; s2 < n_seeds; ++s2) {
+          double r2 = 0;
+          for (int a = 0; a < 3; ++a) {
+            double d = fmod(X[a] - seeds[7 * s2 + a], L[a]);
+            if (d < -0.5 * L[a]) d += L[a];
+            if (d >= 0.5 * L[a]) d -= L[a];
+            r2 += d * d;
+          }
+          if (s2 == 0 || r2 < bd) { bd = r2; best = s2; }
+        }
+        quat_rot(seeds + 7 * best + 3, st->rot + 9 * (size_t)id);
+      }
+  return 0;
+}
+
+/* Orientation of a site (9 values of R; the identity without orientations). */
+void or3_orientation(const o3state *st, int id, double *out) {
+  for (int k = 0; k < 9; ++k) out[k] = st->rot ? st->rot[9 * (size_t)id + k] : (k % 4 == 0);
 }
 
 /* A window of a larger periodic lattice: the initial seeds are placed with
@@ -338,7 +386,16 @@ static void step3(o3state *st) {
         }
         for (int a = 0; a < 3; ++a) g[a] /= (1.0 / 3.0);   /* D3Q19 c_s^2 = 1/3 */
         double as, N[3], gm;
-        aniso3(g, eps, p[Q_GRAD_EPS], &as, N, &gm);
+        if (st->rot) {
+          /* crystal frame g' = R^T g, N = R N'(g') (R10 in 3-D) */
+          const double *R = st->rot + 9 * (size_t)id;
+          double gr[3], Nr[3];
+          for (int a = 0; a < 3; ++a) gr[a] = R[a] * g[0] + R[3 + a] * g[1] + R[6 + a] * g[2];
+          aniso3(gr, eps, p[Q_GRAD_EPS], &as, Nr, &gm);
+          for (int a = 0; a < 3; ++a) N[a] = R[3 * a] * Nr[0] + R[3 * a + 1] * Nr[1] + R[3 * a + 2] * Nr[2];
+        } else {
+          aniso3(g, eps, p[Q_GRAD_EPS], &as, N, &gm);
+        }
         const double as2 = as * as;
         const double U = supersat3(st, C, psi);
         /* temperature (thermal mode): rho H = sum e, theta = H / c_p + L h(psi) */

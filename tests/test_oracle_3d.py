@@ -216,3 +216,88 @@ def test_3d_gradF_source_matches_the_original_equation():
     assert np.abs(f["psi"][0, 0] - psi_fd).max() < 0.15 * effect
     assert np.abs(f["C"][0, 0] - C_fd).max() < 0.01
     assert np.abs(f["theta"][0, 0] - th_fd).max() < 0.01
+
+
+# ---------------------------------------------------------------------------
+# grain orientations in 3-D (reading R10 for d = 3: crystal frame g' = R^T g,
+# N = R N'(g'), each site takes the rotation of the nearest seed)
+# ---------------------------------------------------------------------------
+def _quat(axis, angle):
+    q = [math.cos(angle / 2), 0.0, 0.0, 0.0]
+    q[1 + axis] = math.sin(angle / 2)
+    return q
+
+
+def test_3d_orientation_follows_the_nearest_seed():
+    """Every site carries the rotation of the nearest seed (minimum image);
+    the rotation is the one the quaternion defines (checked against scipy's)."""
+    from scipy.spatial.transform import Rotation
+    n = 12
+    seeds7 = [(2.0, 3.0, 4.0) + tuple(_quat(2, 0.3)), (9.5, 8.0, 10.0, 0.9, 0.2, -0.3, 0.1)]
+    o = oracle.Oracle3D(n, n, n, P3)
+    o.set_orientation(seeds7)
+    rng = np.random.default_rng(3)
+    for site in rng.integers(0, n ** 3, 40):
+        x, y, z = site % n, (site // n) % n, site // (n * n)
+        d2 = []
+        for s in seeds7:
+            dd = (np.array([x, y, z], float) - np.array(s[:3]) + n / 2) % n - n / 2
+            d2.append((dd ** 2).sum())
+        s = seeds7[int(np.argmin(d2))]
+        want = Rotation.from_quat([s[4], s[5], s[6], s[3]]).as_matrix()
+        assert np.abs(o.orientation(int(site)) - want).max() < 1e-14
+
+
+def test_3d_orientation_identity_and_cubic_symmetry():
+    """The identity orientation reproduces the unoriented step bit for bit; a
+    quarter turn about any axis maps the cubic anisotropy onto itself, so the
+    grains grow exactly as unrotated (to rounding)."""
+    n, seeds = 24, [(9.3, 11.0, 12.5), (17.0, 6.0, 5.0)]
+    base = oracle.Oracle3D(n, n, n, P3)
+    base.init_spec(seeds, 5.0)
+    base.step(60)
+    fb = base.fields()
+    for q, tol in (([1.0, 0.0, 0.0, 0.0], 0.0), (_quat(0, math.pi / 2), 1e-12),
+                   (_quat(1, math.pi / 2), 1e-12), (_quat(2, -math.pi / 2), 1e-12)):
+        o = oracle.Oracle3D(n, n, n, P3)
+        o.init_spec(seeds, 5.0)
+        o.set_orientation([tuple(s) + tuple(q) for s in seeds])
+        o.step(60)
+        fo = o.fields()
+        for k in ("psi", "C"):
+            assert np.abs(fo[k] - fb[k]).max() <= tol * np.abs(fb[k]).max(), (q, k)
+
+
+def _rotated_front_width(axis_front, q):
+    N, W0, eps = 96, 4.0, 0.05
+    x = np.arange(N, dtype=float)
+    d1 = np.abs(x - N / 2)
+    psi1 = np.tanh((22.0 - d1) / (math.sqrt(2) * W0))
+    if axis_front == 0:
+        psi = np.broadcast_to(psi1[None, None, :], (2, N, N)).copy()
+    else:
+        psi = np.broadcast_to(psi1[None, :, None], (2, N, N)).copy()
+    o = oracle.Oracle3D(N, N, 2, dict(P3, Omega=0.0, eps_s=eps))
+    o.init_fields(psi, 1 - 0.85 * (1 + psi) / 2)
+    o.set_orientation([(N / 2, N / 2, 1.0) + tuple(q)])
+    o.step(2000)
+    f = o.fields()["psi"]
+    row = f[0, 0, :] if axis_front == 0 else f[0, :, 0]
+    return _tanh_width(d1, row, 22.0, math.sqrt(2) * W0)[0]
+
+
+def test_3d_rotated_grain_front_widths():
+    """A lattice-aligned flat front takes the width sqrt2 W0 a_s of the
+    crystal direction it faces: turned by pi/4 about z, a front normal to x
+    faces <110> (a_s = 1 - eps); turned by pi/4 about x, a front normal to y
+    faces <011> (1 - eps) while one normal to x still faces <100> (1 + eps)."""
+    W0, eps = 4.0, 0.05
+    w_z = _rotated_front_width(0, _quat(2, math.pi / 4))
+    w_xy = _rotated_front_width(1, _quat(0, math.pi / 4))
+    w_xx = _rotated_front_width(0, _quat(0, math.pi / 4))
+    # the lattice itself adds about 1 % to both widths (as for the unrotated fronts)
+    assert math.isclose(w_z, math.sqrt(2) * W0 * (1 - eps), rel_tol=0.02)
+    assert math.isclose(w_xy, math.sqrt(2) * W0 * (1 - eps), rel_tol=0.02)
+    assert math.isclose(w_xx, math.sqrt(2) * W0 * (1 + eps), rel_tol=0.02)
+    assert math.isclose(w_xx / w_z, (1 + eps) / (1 - eps), rel_tol=0.01)
+    assert abs(w_xy / w_z - 1) < 1e-9        # the same crystal direction, two rotations
