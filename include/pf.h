@@ -364,8 +364,9 @@ pf_status pf_reduce_thermal(pf_handle *h, int dom, double out[3]);
  * Three-dimensional dendrite step (Section 2.1 with the anisotropy summed over
  * three axes): psi (anisotropic Allen-Cahn with the a_s^2 time stretch of
  * Appendix B) and C (solute with antitrapping) on D3Q7 lattices (w0 = 1/4,
- * wi = 1/8, c_s^2 = 1/4) in a periodic melt without gas or flow, one grain
- * orientation aligned with the lattice.  Arrays are [z][y][x], x fastest.
+ * wi = 1/8, c_s^2 = 1/4) in a periodic melt without gas or flow, with one
+ * lattice-aligned grain or the grain orientations of pf3_set_orientation.
+ * Arrays are [z][y][x], x fastest.
  * Uses the gas and flow parameters of pf_params not at all.  With thermal = 1
  * a D3Q7 temperature lattice (Appendix B at rest: e_0 = rho H - (3/4) theta,
  * e_i = theta/8, k_T = Le D rho_l c_p) is coupled as in 2-D: theta = H / c_p +
@@ -400,6 +401,14 @@ pf_status pf3_set_fields(pf3_handle *h, const double *psi, const double *C, size
  * (not thermal, size, non-finite), STATE (not initialised or already stepped),
  * OOM, CUDA. */
 pf_status pf3_set_temperature(pf3_handle *h, const double *theta, size_t n);
+/* Grain orientations (the 3-D form of the 2-D grain angle): seeds7 holds
+ * n_seeds x (x, y, z, qw, qx, qy, qz); every site takes the rotation R of the
+ * nearest seed's quaternion (minimum image, the first seed on an exact tie),
+ * and the anisotropy is evaluated on g' = R^T grad psi with N = R N'(g').
+ * n_seeds = 0 returns to the lattice-aligned grain.  May be called at any
+ * time between steps.  Synchronises.  Errors: BAD_ARG (NULL, non-finite or zero
+ * quaternion), OOM, CUDA. */
+pf_status pf3_set_orientation(pf3_handle *h, const double *seeds7, int n_seeds);
 /* Planes per tile of the z-march (default 16). */
 pf_status pf3_set_chunk(pf3_handle *h, int chunk);
 /* Advance n_steps (enqueued; errors of the launch are reported).

@@ -43,6 +43,8 @@ struct Args3 {
   const R* ain;
   R* aout;
   R* fields;            // psi, C, U (and theta) planes, or nullptr
+  const int* grain;     // ROT: grain index per site
+  const R* rot;         // ROT: 9 entries (row-major R) per grain
   unsigned long long ps;
   int nx, ny, nz, chunk;
   int tiles_x, tiles_y, tiles_z;
@@ -103,7 +105,9 @@ __device__ __forceinline__ R supersat3(const Coef3<R>& c, R C, R psi) {
 // H / c_p + (c_p^s/c_p) h(psi)), F(U) = 1/Le + M c_inf [1 + (1-k) U] in the
 // relaxation of psi, and the source Q / F + W0^2 / F^2 grad F . (a_s^2 grad psi
 // + N) with grad F = M c_inf (1-k) grad U; U is kept in a second ring.
-template <typename S, typename R, bool TH>
+// ROT: grain orientations (the site's grain rotation R; the anisotropy is
+// evaluated on g' = R^T grad psi and N = R N'(g')).
+template <typename S, typename R, bool TH, bool ROT>
 __global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R> a) {
   __shared__ R ring[4][HY][HX];
   __shared__ R uring[TH ? 4 : 1][HY][HX];
@@ -196,17 +200,31 @@ __global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R> a) {
         const R psi = ring[z & 3][hy][hx];
         R gx, gy, gz;
         grad18<R>(ring[(z - 1) & 3], ring[z & 3], ring[(z + 1) & 3], hy, hx, gx, gy, gz);
-        // anisotropy (three axes), regularised normal
+        // anisotropy (three axes), regularised normal, in the crystal frame
         const R gm2 = gx * gx + gy * gy + gz * gz;
         const R im = frsqrt(gm2 + c.ge2);
         const R m = (gm2 + c.ge2) * im;
-        const R n0 = -gx * im, n1 = -gy * im, n2v = -gz * im;
+        R gxc = gx, gyc = gy, gzc = gz;
+        const R* Rm = nullptr;
+        if constexpr (ROT) {
+          Rm = a.rot + 9 * a.grain[site];
+          gxc = Rm[0] * gx + Rm[3] * gy + Rm[6] * gz;
+          gyc = Rm[1] * gx + Rm[4] * gy + Rm[7] * gz;
+          gzc = Rm[2] * gx + Rm[5] * gy + Rm[8] * gz;
+        }
+        const R n0 = -gxc * im, n1 = -gyc * im, n2v = -gzc * im;
         const R q0 = n0 * n0, q1 = n1 * n1, q2 = n2v * n2v;
         const R n2 = q0 + q1 + q2, s4 = q0 * q0 + q1 * q1 + q2 * q2;
         const R as = R(1) + c.eps * (R(4) * s4 - R(3) * n2 * n2);
         const R iso = s4 + R(0.75) * n2 * (R(1) - n2);
         const R pre = R(-16) * c.eps * as * m;
-        const R Nx = pre * n0 * (q0 - iso), Ny = pre * n1 * (q1 - iso), Nz = pre * n2v * (q2 - iso);
+        R Nx = pre * n0 * (q0 - iso), Ny = pre * n1 * (q1 - iso), Nz = pre * n2v * (q2 - iso);
+        if constexpr (ROT) {
+          const R Ncx = Nx, Ncy = Ny, Ncz = Nz;
+          Nx = Rm[0] * Ncx + Rm[1] * Ncy + Rm[2] * Ncz;
+          Ny = Rm[3] * Ncx + Rm[4] * Ncy + Rm[5] * Ncz;
+          Nz = Rm[6] * Ncx + Rm[7] * Ncy + Rm[8] * Ncz;
+        }
         const R as2 = as * as, ias2 = frcp(as2);
         // moments, sources
         const R C = TH ? CC : sum7(sv);
@@ -358,6 +376,28 @@ __device__ __forceinline__ double min_image1(double d, double L) {
   return d;
 }
 
+// Grain index of every site: the nearest seed (minimum image, the first seed
+// on an exact tie).  seeds: n x 7 (x, y, z, quaternion).
+__global__ void k_grain3(int nx, int ny, int nz, const double* seeds, int n_seeds, int* grain) {
+  const unsigned long long n = (unsigned long long)nx * ny * nz;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const double X[3] = {(double)(i % nx), (double)((i / nx) % ny), (double)(i / ((unsigned long long)nx * ny))};
+    const double L[3] = {(double)nx, (double)ny, (double)nz};
+    int best = 0;
+    double bd = 0.0;
+    for (int s = 0; s < n_seeds; ++s) {
+      double r2 = 0.0;
+      for (int q = 0; q < 3; ++q) {
+        const double d = min_image1(X[q] - seeds[7 * s + q], L[q]);
+        r2 += d * d;
+      }
+      if (s == 0 || r2 < bd) { bd = r2; best = s; }
+    }
+    grain[i] = best;
+  }
+}
+
 template <typename S, typename R, bool TH>
 __global__ void k_init3(Args3<S, R> a, const double* seeds, int n_seeds, double R_s, double sq2b,
                         double W0, double k, double theta0) {
@@ -488,6 +528,9 @@ struct pf3_handle {
   cudaStream_t stream = nullptr;
   int nx = 0, ny = 0, nz = 0, chunk = 16;
   int thermal = 0, npop = NPOP3, nfields = 3, nstate = NSTATE3;
+  int rotated = 0;                // grain orientations set
+  int* grain = nullptr;           // grain index per site
+  void* rot = nullptr;            // 9 x n_grains rotation entries (compute type)
   unsigned long long n = 0;
   size_t elem = 4, celem = 4;
   void* pop[2] = {nullptr, nullptr};
@@ -551,6 +594,8 @@ static Args3<S, R> args3(const pf3_handle* h, bool fields) {
   a.ain = (const R*)h->aux[h->cur];
   a.aout = (R*)h->aux[h->cur ^ 1];
   a.fields = fields ? (R*)h->fields : nullptr;
+  a.grain = h->grain;
+  a.rot = (const R*)h->rot;
   a.ps = h->n;
   a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.chunk = h->chunk;
   a.tiles_x = (h->nx + TX - 1) / TX;
@@ -632,6 +677,8 @@ extern "C" pf_status pf3_destroy(pf3_handle* h) {
   for (int c = 0; c < 2; ++c) { cudaFree(h->pop[c]); cudaFree(h->aux[c]); }
   cudaFree(h->fields);
   cudaFree(h->scratch);
+  cudaFree(h->grain);
+  cudaFree(h->rot);
   const cudaError_t e = cudaGetLastError();
   delete h;
   return e == cudaSuccess ? PF_OK : PF_ERR_CUDA;
@@ -734,6 +781,57 @@ extern "C" pf_status pf3_set_temperature(pf3_handle* h, const double* theta, siz
   return PF_OK;
 }
 
+extern "C" pf_status pf3_set_orientation(pf3_handle* h, const double* seeds7, int n_seeds) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (n_seeds < 0 || (n_seeds > 0 && !seeds7)) return fail3(h, PF_ERR_BAD_ARG, "bad seeds");
+  if (n_seeds == 0) {                      // back to the lattice-aligned grain
+    h->rotated = 0;
+    return PF_OK;
+  }
+  std::vector<double> rot(9 * (size_t)n_seeds);
+  for (int s = 0; s < n_seeds; ++s) {
+    const double* q = seeds7 + 7 * s;
+    for (int k = 0; k < 7; ++k)
+      if (!std::isfinite(q[k])) return fail3(h, PF_ERR_BAD_ARG, "non-finite seed");
+    const double nq = std::sqrt(q[3] * q[3] + q[4] * q[4] + q[5] * q[5] + q[6] * q[6]);
+    if (!(nq > 0)) return fail3(h, PF_ERR_BAD_ARG, "zero quaternion");
+    const double w = q[3] / nq, x = q[4] / nq, y = q[5] / nq, z = q[6] / nq;
+    double* R = rot.data() + 9 * s;        // rotation of the unit quaternion, row-major
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - z * w);     R[2] = 2 * (x * z + y * w);
+    R[3] = 2 * (x * y + z * w);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - x * w);
+    R[6] = 2 * (x * z - y * w);     R[7] = 2 * (y * z + x * w);     R[8] = 1 - 2 * (x * x + y * y);
+  }
+  PF3_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (!h->grain && cudaMalloc(&h->grain, h->n * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    h->grain = nullptr;
+    return fail3(h, PF_ERR_OOM, "device allocation failed");
+  }
+  cudaFree(h->rot);
+  h->rot = nullptr;
+  if (cudaMalloc(&h->rot, 9 * (size_t)n_seeds * h->celem) != cudaSuccess) {
+    cudaGetLastError();
+    h->rot = nullptr;
+    return fail3(h, PF_ERR_OOM, "device allocation failed");
+  }
+  pf_status st = ensure_scratch3(h, 7 * (size_t)n_seeds);
+  if (st != PF_OK) return st;
+  PF3_CUDA(h, cudaMemcpyAsync(h->scratch, seeds7, 7 * (size_t)n_seeds * sizeof(double),
+                              cudaMemcpyHostToDevice, h->stream));
+  k_grain3<<<1024, 256, 0, h->stream>>>(h->nx, h->ny, h->nz, h->scratch, n_seeds, h->grain);
+  PF3_CUDA(h, cudaGetLastError());
+  h->launches++;
+  if (h->prec == PF_FP64) {
+    PF3_CUDA(h, cudaMemcpyAsync(h->rot, rot.data(), rot.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  } else {
+    std::vector<float> rf(rot.begin(), rot.end());
+    PF3_CUDA(h, cudaMemcpyAsync(h->rot, rf.data(), rf.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  }
+  PF3_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->rotated = 1;
+  return PF_OK;
+}
+
 extern "C" pf_status pf3_set_chunk(pf3_handle* h, int chunk) {
   if (!h) return PF_ERR_BAD_ARG;
   if (chunk < 1 || chunk > 4096) return fail3(h, PF_ERR_BAD_ARG, "chunk must be in [1, 4096]");
@@ -751,8 +849,13 @@ extern "C" pf_status pf3_step(pf3_handle* h, int n_steps) {
     for (int t = 0; t < n_steps; ++t) {
       const Args3<S, R> a = args3<S, R>(h, t == n_steps - 1);
       const int tiles = a.tiles_x * a.tiles_y * a.tiles_z;
-      if (h->thermal) k_step3d<S, R, true><<<tiles, THREADS, 0, h->stream>>>(a);
-      else k_step3d<S, R, false><<<tiles, THREADS, 0, h->stream>>>(a);
+      if (h->rotated) {
+        if (h->thermal) k_step3d<S, R, true, true><<<tiles, THREADS, 0, h->stream>>>(a);
+        else k_step3d<S, R, false, true><<<tiles, THREADS, 0, h->stream>>>(a);
+      } else {
+        if (h->thermal) k_step3d<S, R, true, false><<<tiles, THREADS, 0, h->stream>>>(a);
+        else k_step3d<S, R, false, false><<<tiles, THREADS, 0, h->stream>>>(a);
+      }
       PF3_CUDA(h, cudaGetLastError());
       h->cur ^= 1;
       h->steps++;
