@@ -447,7 +447,8 @@ pf_status pf3_destroy(pf3_handle *h);
  * 1 elsewhere; CAC: fluxes at s_phi); psi and C on the D3Q7 lattices of the
  * pf3_* step with the gas couplings of Section 2 (f3 in Q_psi, the gas-vacuum
  * flux J) and advection of C.  Isothermal (thermal must be 0), periodic cube,
- * one grain orientation aligned with the lattice.  Arrays are [z][y][x].
+ * the lattice-aligned grain or the orientations of pf3f_set_orientation.
+ * Arrays are [z][y][x].
  * ------------------------------------------------------------------------ */
 typedef struct pf3f_handle pf3f_handle;
 
@@ -477,6 +478,10 @@ pf_status pf3f_set_fields(pf3f_handle *h, const double *fields7, size_t n);
 /* Buoyancy reference density (after initialisation; replaces the mean). */
 pf_status pf3f_set_rho_bar(pf3f_handle *h, double rho_bar);
 double pf3f_get_rho_bar(const pf3f_handle *h);
+/* Grain orientations as pf3_set_orientation: seeds7 n_seeds x (x, y, z, qw,
+ * qx, qy, qz), every site takes the nearest seed's rotation; 0 seeds returns
+ * to the lattice-aligned grain.  Synchronises.  Errors: BAD_ARG, OOM, CUDA. */
+pf_status pf3f_set_orientation(pf3f_handle *h, const double *seeds7, int n_seeds);
 /* Planes per tile of the z-march (default 16). */
 pf_status pf3f_set_chunk(pf3f_handle *h, int chunk);
 /* Advance n_steps (enqueued).  Errors: BAD_ARG, STATE (not initialised), CUDA. */

@@ -483,6 +483,8 @@ def _l3f() -> ctypes.CDLL:
             lib.or3f_basis.argtypes = [D, D, ctypes.POINTER(ctypes.c_int)]
             lib.or3f_collide19.argtypes = [D] * 5
             lib.or3f_feq.argtypes = [ctypes.c_double, ctypes.c_double, D, D]
+            lib.or3f_set_orientation.argtypes = [P, D, I]
+            lib.or3f_set_orientation.restype = I
             _lib3f = lib
     return _lib3f
 
@@ -539,6 +541,13 @@ class Oracle3F:
     def init_fields(self, phi, psi, C, vx=None, vy=None, vz=None, p=None) -> None:
         self._keep = [None if a is None else _f64(a).ravel() for a in (phi, psi, C, vx, vy, vz, p)]
         self.lib.or3f_init_fields(self.h, *[_dp(a) for a in self._keep])
+
+    def set_orientation(self, seeds7) -> None:
+        """Grain orientations: n x (x, y, z, qw, qx, qy, qz); each site takes the
+        rotation of the nearest seed."""
+        s = np.ascontiguousarray(_f64(seeds7).reshape(-1, 7))
+        if self.lib.or3f_set_orientation(self.h, _dp(s), len(s)) != 0:
+            raise MemoryError("oracle allocation failed")
 
     def step(self, n: int = 1) -> None:
         self.lib.or3f_step(self.h, int(n))

@@ -140,17 +140,17 @@ static void quat_rot(const double *q, double R[9]) {
 /* Grain orientations (the 3-D form of reading R10): each site takes the
  * orientation of the nearest seed (minimum image in the NX x NY x NZ lattice,
  * the first seed on an exact tie).  seeds: n x (x, y, z, qw, qx, qy, qz). */
-int or3_set_orientation(o3state *st, const double *seeds, int n_seeds) {
-  free(st->rot);
-  st->rot = NULL;
-  if (n_seeds <= 0) return 0;
-  st->rot = (double *)malloc((size_t)st->n * 9 * sizeof(double));
-  if (!st->rot) return -1;
-  for (int z = 0; z < st->nz; ++z)
-    for (int y = 0; y < st->ny; ++y)
-      for (int x = 0; x < st->nx; ++x) {
-        const int id = (z * st->ny + y) * st->nx + x;
-        const double X[3] = {st->x0 + x, st->y0 + y, st->z0 + z}, L[3] = {st->NX, st->NY, st->NZ};
+/* Rotation of the nearest seed for every site of an nx x ny x nz lattice
+ * placed at (x0, y0, z0) in a periodic NX x NY x NZ one; NULL on failure. */
+static double *nearest_rotations(int nx, int ny, int nz, int NX, int NY, int NZ, int x0, int y0,
+                                 int z0, const double *seeds, int n_seeds) {
+  double *rot = (double *)malloc((size_t)nx * ny * nz * 9 * sizeof(double));
+  if (!rot) return NULL;
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const int id = (z * ny + y) * nx + x;
+        const double X[3] = {x0 + x, y0 + y, z0 + z}, L[3] = {NX, NY, NZ};
         int best = 0;
         double bd = 0;
         for (int s2 = 0; s2 < n_seeds; ++s2) {
@@ -163,9 +163,18 @@ int or3_set_orientation(o3state *st, const double *seeds, int n_seeds) {
           }
           if (s2 == 0 || r2 < bd) { bd = r2; best = s2; }
         }
-        quat_rot(seeds + 7 * best + 3, st->rot + 9 * (size_t)id);
+        quat_rot(seeds + 7 * best + 3, rot + 9 * (size_t)id);
       }
-  return 0;
+  return rot;
+}
+
+int or3_set_orientation(o3state *st, const double *seeds, int n_seeds) {
+  free(st->rot);
+  st->rot = NULL;
+  if (n_seeds <= 0) return 0;
+  st->rot = nearest_rotations(st->nx, st->ny, st->nz, st->NX, st->NY, st->NZ, st->x0, st->y0,
+                              st->z0, seeds, n_seeds);
+  return st->rot ? 0 : -1;
 }
 
 /* Orientation of a site (9 values of R; the identity without orientations). */
@@ -653,6 +662,7 @@ typedef struct {
   real *fS[19], *hS[19], *gS[7], *sS[7], *phiS, *psiS, *CS, *psiOld;
   real *fld[NFLD3F];
   real *block;
+  double *rot;     /* grain orientation per site (9 per site), or NULL */
 } o3fstate;
 
 static double derivedf(const o3fstate *st, double *lam, double *Mc, double *th) {
@@ -696,8 +706,19 @@ o3fstate *or3f_new(int nx, int ny, int nz) {
 
 void or3f_free(o3fstate *st) {
   if (!st) return;
+  free(st->rot);
   free(st->block);
   free(st);
+}
+
+/* Grain orientations as for the melt step: seeds n x (x, y, z, qw, qx, qy, qz). */
+int or3f_set_orientation(o3fstate *st, const double *seeds, int n_seeds) {
+  free(st->rot);
+  st->rot = NULL;
+  if (n_seeds <= 0) return 0;
+  st->rot = nearest_rotations(st->nx, st->ny, st->nz, st->NX, st->NY, st->NZ, st->x0, st->y0,
+                              st->z0, seeds, n_seeds);
+  return st->rot ? 0 : -1;
 }
 
 void or3f_set_params(o3fstate *st, const double *p) {
@@ -978,7 +999,16 @@ static void step3f(o3fstate *st) {
                            W19[0] * rho * v2 / (2.0 * CS2_19));
         /* dendrite geometry and sources */
         double as, N[3], gmag;
-        aniso3(gs, p[F3_EPS_S], p[F3_GRAD_EPS], &as, N, &gmag);
+        if (st->rot) {
+          /* crystal frame g' = R^T grad psi, N = R N'(g') */
+          const double *R = st->rot + 9 * (size_t)id;
+          double gr2[3], Nr[3];
+          for (int a = 0; a < 3; ++a) gr2[a] = R[a] * gs[0] + R[3 + a] * gs[1] + R[6 + a] * gs[2];
+          aniso3(gr2, p[F3_EPS_S], p[F3_GRAD_EPS], &as, Nr, &gmag);
+          for (int a = 0; a < 3; ++a) N[a] = R[3 * a] * Nr[0] + R[3 * a + 1] * Nr[1] + R[3 * a + 2] * Nr[2];
+        } else {
+          aniso3(gs, p[F3_EPS_S], p[F3_GRAD_EPS], &as, N, &gmag);
+        }
         const double as2 = as * as;
         const double U = supersatf(st, C, psi);
         const double Q = qpsif(st, phi, psi, U);

@@ -3,6 +3,8 @@
 // set, plane addressing, periodic wrapping and the isotropic D3Q19-weighted
 // gradient and Laplacian over a 4-slot shared-memory ring of planes.
 #pragma once
+#include <cmath>
+
 #include "pf_device.cuh"
 
 namespace pf {
@@ -69,6 +71,54 @@ __device__ __forceinline__ R lap18(const R (*Pm)[HX], const R (*P0)[HX], const R
                   ((d(Pp, 1, 0) + d(Pm, -1, 0)) + (d(Pp, -1, 0) + d(Pm, 1, 0))) +
                   ((d(Pp, 0, 1) + d(Pm, 0, -1)) + (d(Pp, 0, -1) + d(Pm, 0, 1)));
   return R(1.0 / 3.0) * faces + R(1.0 / 6.0) * edges;
+}
+
+// Signed minimum-image offset on a periodic axis of length L.
+__device__ __forceinline__ double min_image1(double d, double L) {
+  if (d <= -L || d >= L) d = fmod(d, L);
+  if (d < -0.5 * L) d += L;
+  if (d >= 0.5 * L) d -= L;
+  return d;
+}
+
+// Grain index of every site: the nearest seed (minimum image, the first seed
+// on an exact tie).  seeds: n x 7 (x, y, z, quaternion); a template so that
+// both 3-D translation units may instantiate it.
+template <int STRIDE>
+__global__ void k_grain_nearest(int nx, int ny, int nz, const double* seeds, int n_seeds,
+                                int* grain) {
+  const unsigned long long n = (unsigned long long)nx * ny * nz;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const double X[3] = {(double)(i % nx), (double)((i / nx) % ny),
+                         (double)(i / ((unsigned long long)nx * ny))};
+    const double L[3] = {(double)nx, (double)ny, (double)nz};
+    int best = 0;
+    double bd = 0.0;
+    for (int s = 0; s < n_seeds; ++s) {
+      double r2 = 0.0;
+      for (int q = 0; q < 3; ++q) {
+        const double d = min_image1(X[q] - seeds[STRIDE * s + q], L[q]);
+        r2 += d * d;
+      }
+      if (s == 0 || r2 < bd) { bd = r2; best = s; }
+    }
+    grain[i] = best;
+  }
+}
+
+// Rotation matrix (row-major) of the quaternion (w, x, y, z) after
+// normalisation; false for a zero or non-finite quaternion.
+inline bool quat_rows(const double* q, double R[9]) {
+  for (int k = 0; k < 4; ++k)
+    if (!std::isfinite(q[k])) return false;
+  const double nq = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  if (!(nq > 0)) return false;
+  const double w = q[0] / nq, x = q[1] / nq, y = q[2] / nq, z = q[3] / nq;
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - z * w);     R[2] = 2 * (x * z + y * w);
+  R[3] = 2 * (x * y + z * w);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - x * w);
+  R[6] = 2 * (x * z - y * w);     R[7] = 2 * (y * z + x * w);     R[8] = 1 - 2 * (x * x + y * y);
+  return true;
 }
 
 }  // namespace d3

@@ -369,34 +369,6 @@ __device__ void write_eq3(const Args3<S, R>& a, unsigned long long site, R psi, 
   if constexpr (TH) write_th3(a, site, psi, C, theta);
 }
 
-__device__ __forceinline__ double min_image1(double d, double L) {
-  if (d <= -L || d >= L) d = fmod(d, L);
-  if (d < -0.5 * L) d += L;
-  if (d >= 0.5 * L) d -= L;
-  return d;
-}
-
-// Grain index of every site: the nearest seed (minimum image, the first seed
-// on an exact tie).  seeds: n x 7 (x, y, z, quaternion).
-__global__ void k_grain3(int nx, int ny, int nz, const double* seeds, int n_seeds, int* grain) {
-  const unsigned long long n = (unsigned long long)nx * ny * nz;
-  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-       i += (unsigned long long)gridDim.x * blockDim.x) {
-    const double X[3] = {(double)(i % nx), (double)((i / nx) % ny), (double)(i / ((unsigned long long)nx * ny))};
-    const double L[3] = {(double)nx, (double)ny, (double)nz};
-    int best = 0;
-    double bd = 0.0;
-    for (int s = 0; s < n_seeds; ++s) {
-      double r2 = 0.0;
-      for (int q = 0; q < 3; ++q) {
-        const double d = min_image1(X[q] - seeds[7 * s + q], L[q]);
-        r2 += d * d;
-      }
-      if (s == 0 || r2 < bd) { bd = r2; best = s; }
-    }
-    grain[i] = best;
-  }
-}
 
 template <typename S, typename R, bool TH>
 __global__ void k_init3(Args3<S, R> a, const double* seeds, int n_seeds, double R_s, double sq2b,
@@ -791,15 +763,9 @@ extern "C" pf_status pf3_set_orientation(pf3_handle* h, const double* seeds7, in
   std::vector<double> rot(9 * (size_t)n_seeds);
   for (int s = 0; s < n_seeds; ++s) {
     const double* q = seeds7 + 7 * s;
-    for (int k = 0; k < 7; ++k)
-      if (!std::isfinite(q[k])) return fail3(h, PF_ERR_BAD_ARG, "non-finite seed");
-    const double nq = std::sqrt(q[3] * q[3] + q[4] * q[4] + q[5] * q[5] + q[6] * q[6]);
-    if (!(nq > 0)) return fail3(h, PF_ERR_BAD_ARG, "zero quaternion");
-    const double w = q[3] / nq, x = q[4] / nq, y = q[5] / nq, z = q[6] / nq;
-    double* R = rot.data() + 9 * s;        // rotation of the unit quaternion, row-major
-    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - z * w);     R[2] = 2 * (x * z + y * w);
-    R[3] = 2 * (x * y + z * w);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - x * w);
-    R[6] = 2 * (x * z - y * w);     R[7] = 2 * (y * z + x * w);     R[8] = 1 - 2 * (x * x + y * y);
+    if (!std::isfinite(q[0]) || !std::isfinite(q[1]) || !std::isfinite(q[2]) ||
+        !quat_rows(q + 3, rot.data() + 9 * s))
+      return fail3(h, PF_ERR_BAD_ARG, "non-finite seed or zero quaternion");
   }
   PF3_CUDA(h, cudaStreamSynchronize(h->stream));
   if (!h->grain && cudaMalloc(&h->grain, h->n * sizeof(int)) != cudaSuccess) {
@@ -818,7 +784,7 @@ extern "C" pf_status pf3_set_orientation(pf3_handle* h, const double* seeds7, in
   if (st != PF_OK) return st;
   PF3_CUDA(h, cudaMemcpyAsync(h->scratch, seeds7, 7 * (size_t)n_seeds * sizeof(double),
                               cudaMemcpyHostToDevice, h->stream));
-  k_grain3<<<1024, 256, 0, h->stream>>>(h->nx, h->ny, h->nz, h->scratch, n_seeds, h->grain);
+  k_grain_nearest<7><<<1024, 256, 0, h->stream>>>(h->nx, h->ny, h->nz, h->scratch, n_seeds, h->grain);
   PF3_CUDA(h, cudaGetLastError());
   h->launches++;
   if (h->prec == PF_FP64) {

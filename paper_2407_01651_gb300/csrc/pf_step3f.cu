@@ -112,6 +112,8 @@ struct ArgsF {
   const R* ain;
   R* aout;
   R* fields;            // phi, psi, C, U, p, vx, vy, vz, mu planes, or nullptr
+  const int* grain;     // ROT: grain index per site
+  const R* rot;         // ROT: 9 entries (row-major R) per grain
   unsigned long long ps;
   int nx, ny, nz, chunk;
   int tiles_x, tiles_y, tiles_z;
@@ -162,7 +164,8 @@ __device__ __forceinline__ void stream_g(const ArgsF<S, R>& a, int x, int y, int
   psio = po;
 }
 
-template <typename S, typename R>
+// ROT: grain orientations (anisotropy on g' = R^T grad psi, N = R N'(g')).
+template <typename S, typename R, bool ROT>
 __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R> a) {
   // rings of phi, psi and v_o (dynamic: 54 KB in FP64)
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -405,13 +408,27 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R> a) {
         const R gm2 = gs[0] * gs[0] + gs[1] * gs[1] + gs[2] * gs[2];
         const R im = frsqrt(gm2 + c.ge2);
         const R m = (gm2 + c.ge2) * im;
-        const R n0 = -gs[0] * im, n1 = -gs[1] * im, n2v = -gs[2] * im;
+        R gc0 = gs[0], gc1 = gs[1], gc2 = gs[2];
+        const R* Rm = nullptr;
+        if constexpr (ROT) {
+          Rm = a.rot + 9 * a.grain[site];
+          gc0 = Rm[0] * gs[0] + Rm[3] * gs[1] + Rm[6] * gs[2];
+          gc1 = Rm[1] * gs[0] + Rm[4] * gs[1] + Rm[7] * gs[2];
+          gc2 = Rm[2] * gs[0] + Rm[5] * gs[1] + Rm[8] * gs[2];
+        }
+        const R n0 = -gc0 * im, n1 = -gc1 * im, n2v = -gc2 * im;
         const R q0 = n0 * n0, q1 = n1 * n1, q2 = n2v * n2v;
         const R n2 = q0 + q1 + q2, s4 = q0 * q0 + q1 * q1 + q2 * q2;
         const R as = R(1) + c.eps * (R(4) * s4 - R(3) * n2 * n2);
         const R iso = s4 + R(0.75) * n2 * (R(1) - n2);
         const R pre = R(-16) * c.eps * as * m;
-        const R Nx = pre * n0 * (q0 - iso), Ny = pre * n1 * (q1 - iso), Nz = pre * n2v * (q2 - iso);
+        R Nx = pre * n0 * (q0 - iso), Ny = pre * n1 * (q1 - iso), Nz = pre * n2v * (q2 - iso);
+        if constexpr (ROT) {
+          const R Ncx = Nx, Ncy = Ny, Ncz = Nz;
+          Nx = Rm[0] * Ncx + Rm[1] * Ncy + Rm[2] * Ncz;
+          Ny = Rm[3] * Ncx + Rm[4] * Ncy + Rm[5] * Ncz;
+          Nz = Rm[6] * Ncx + Rm[7] * Ncy + Rm[8] * Ncz;
+        }
         const R as2 = as * as, ias2 = frcp(as2);
         CSum<R> cs;
 #pragma unroll
@@ -666,6 +683,9 @@ struct pf3f_handle {
   void* fields = nullptr;
   double* scratch = nullptr;
   size_t scratch_elems = 0;
+  int rotated = 0;                // grain orientations set
+  int* grain = nullptr;           // grain index per site
+  void* rot = nullptr;            // 9 x n_grains rotation entries (storage precision)
   int cur = 0, inited = 0;
   long long steps = 0, launches = 0;
   std::string err;
@@ -730,6 +750,8 @@ static ArgsF<S, R> argsf(const pf3f_handle* h, bool fields) {
   a.ain = (const R*)h->aux[h->cur];
   a.aout = (R*)h->aux[h->cur ^ 1];
   a.fields = fields ? (R*)h->fields : nullptr;
+  a.grain = h->grain;
+  a.rot = (const R*)h->rot;
   a.ps = h->n;
   a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.chunk = h->chunk;
   a.tiles_x = (h->nx + TX - 1) / TX;
@@ -830,6 +852,8 @@ extern "C" pf_status pf3f_destroy(pf3f_handle* h) {
   for (int c = 0; c < 2; ++c) { cudaFree(h->pop[c]); cudaFree(h->aux[c]); }
   cudaFree(h->fields);
   cudaFree(h->scratch);
+  cudaFree(h->grain);
+  cudaFree(h->rot);
   const cudaError_t e = cudaGetLastError();
   delete h;
   return e == cudaSuccess ? PF_OK : PF_ERR_CUDA;
@@ -902,6 +926,51 @@ extern "C" pf_status pf3f_set_rho_bar(pf3f_handle* h, double rho_bar) {
 }
 extern "C" double pf3f_get_rho_bar(const pf3f_handle* h) { return h ? h->rho_bar : 0.0; }
 
+extern "C" pf_status pf3f_set_orientation(pf3f_handle* h, const double* seeds7, int n_seeds) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (n_seeds < 0 || (n_seeds > 0 && !seeds7)) return failf(h, PF_ERR_BAD_ARG, "bad seeds");
+  if (n_seeds == 0) {
+    h->rotated = 0;
+    return PF_OK;
+  }
+  std::vector<double> rot(9 * (size_t)n_seeds);
+  for (int s = 0; s < n_seeds; ++s) {
+    const double* q = seeds7 + 7 * s;
+    if (!std::isfinite(q[0]) || !std::isfinite(q[1]) || !std::isfinite(q[2]) ||
+        !d3::quat_rows(q + 3, rot.data() + 9 * s))
+      return failf(h, PF_ERR_BAD_ARG, "non-finite seed or zero quaternion");
+  }
+  PF3F_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (!h->grain && cudaMalloc(&h->grain, h->n * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    h->grain = nullptr;
+    return failf(h, PF_ERR_OOM, "device allocation failed");
+  }
+  cudaFree(h->rot);
+  h->rot = nullptr;
+  if (cudaMalloc(&h->rot, 9 * (size_t)n_seeds * h->elem) != cudaSuccess) {
+    cudaGetLastError();
+    h->rot = nullptr;
+    return failf(h, PF_ERR_OOM, "device allocation failed");
+  }
+  pf_status st = ensure_scratchf(h, 7 * (size_t)n_seeds);
+  if (st != PF_OK) return st;
+  PF3F_CUDA(h, cudaMemcpyAsync(h->scratch, seeds7, 7 * (size_t)n_seeds * sizeof(double),
+                               cudaMemcpyHostToDevice, h->stream));
+  d3::k_grain_nearest<7><<<1024, 256, 0, h->stream>>>(h->nx, h->ny, h->nz, h->scratch, n_seeds, h->grain);
+  PF3F_CUDA(h, cudaGetLastError());
+  h->launches++;
+  if (h->prec == PF_FP64) {
+    PF3F_CUDA(h, cudaMemcpyAsync(h->rot, rot.data(), rot.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  } else {
+    std::vector<float> rf(rot.begin(), rot.end());
+    PF3F_CUDA(h, cudaMemcpyAsync(h->rot, rf.data(), rf.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  }
+  PF3F_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->rotated = 1;
+  return PF_OK;
+}
+
 extern "C" pf_status pf3f_set_chunk(pf3f_handle* h, int chunk) {
   if (!h) return PF_ERR_BAD_ARG;
   if (chunk < 1 || chunk > 2048) return failf(h, PF_ERR_BAD_ARG, "chunk must be in [1, 2048]");
@@ -916,13 +985,17 @@ extern "C" pf_status pf3f_step(pf3f_handle* h, int n_steps) {
   return dispatchf(h, [&](auto s_t, auto r_t) {
     using S = decltype(s_t);
     using R = decltype(r_t);
-    if (ring_bytes<R>() > 48 * 1024)
-      PF3F_CUDA(h, cudaFuncSetAttribute(k_step3f<S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (ring_bytes<R>() > 48 * 1024) {
+      PF3F_CUDA(h, cudaFuncSetAttribute(k_step3f<S, R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)ring_bytes<R>()));
+      PF3F_CUDA(h, cudaFuncSetAttribute(k_step3f<S, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)ring_bytes<R>()));
+    }
     for (int t = 0; t < n_steps; ++t) {
       const ArgsF<S, R> a = argsf<S, R>(h, t == n_steps - 1);
       const int tiles = a.tiles_x * a.tiles_y * a.tiles_z;
-      k_step3f<S, R><<<tiles, THREADS, ring_bytes<R>(), h->stream>>>(a);
+      if (h->rotated) k_step3f<S, R, true><<<tiles, THREADS, ring_bytes<R>(), h->stream>>>(a);
+      else k_step3f<S, R, false><<<tiles, THREADS, ring_bytes<R>(), h->stream>>>(a);
       PF3F_CUDA(h, cudaGetLastError());
       h->cur ^= 1;
       h->steps++;

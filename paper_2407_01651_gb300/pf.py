@@ -140,6 +140,7 @@ def lib() -> ctypes.CDLL:
     L.pf3f_get_rho_bar.argtypes = [P]
     L.pf3f_get_rho_bar.restype = ctypes.c_double
     L.pf3f_set_chunk.argtypes = [P, I]
+    L.pf3f_set_orientation.argtypes = [P, D, I]
     L.pf3f_step.argtypes = [P, I]
     L.pf3f_get_fields.argtypes = [P, D, S]
     L.pf3f_get_state.argtypes = [P, D, S]
@@ -159,7 +160,8 @@ def lib() -> ctypes.CDLL:
                  "pf3_destroy", "pf3_set_temperature", "pf3_reduce_thermal", "pf3_set_orientation",
                  "pf3f_create",
                  "pf3f_init_spec", "pf3f_set_fields", "pf3f_set_rho_bar", "pf3f_set_chunk",
-                 "pf3f_step", "pf3f_get_fields", "pf3f_get_state", "pf3f_reduce", "pf3f_destroy"):
+                 "pf3f_step", "pf3f_get_fields", "pf3f_get_state", "pf3f_reduce", "pf3f_destroy",
+                 "pf3f_set_orientation"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -556,6 +558,11 @@ class Simulation3F:
 
     def set_rho_bar(self, rho_bar: float) -> None:
         _check3f(lib().pf3f_set_rho_bar(self.h, float(rho_bar)), self.h)
+
+    def set_orientation(self, seeds7) -> None:
+        """Grain orientations: n x (x, y, z, qw, qx, qy, qz) (empty: aligned)."""
+        s = np.ascontiguousarray(np.asarray(seeds7, dtype=np.float64).reshape(-1, 7))
+        _check3f(lib().pf3f_set_orientation(self.h, _dp(s), len(s)), self.h)
 
     def set_chunk(self, chunk: int) -> None:
         _check3f(lib().pf3f_set_chunk(self.h, int(chunk)), self.h)

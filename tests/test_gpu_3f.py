@@ -194,3 +194,35 @@ def test_3f_small_and_ragged_lattices(shape):
     o.step(4)
     sim.step(4)
     compare(o, sim, 1e-11)
+
+
+ROT = [(10.3, 9.1, 6.2, 0.9, 0.2, -0.3, 0.1), (33.0, 4.0, 11.5, 0.7, -0.1, 0.4, 0.6)]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", TOL32)])
+def test_3f_rotated_grains_match_oracle(precision, tol):
+    """Grain orientations in the two-phase step (each site takes the nearest
+    seed's rotation): the oracle with the same orientations over 3 steps."""
+    o, sim = pair(RAGGED, precision, seeds=[s[:3] for s in ROT])
+    o.set_orientation(ROT)
+    sim.set_orientation(ROT)
+    o.set_rho_bar(sim.rho_bar)
+    sim.set_chunk(5)
+    for _ in range(3):
+        o.step(1)
+        sim.step(1)
+        compare(o, sim, tol)
+
+
+def test_3f_identity_orientation_is_the_aligned_grain():
+    seeds = [s[:3] for s in ROT]
+    out = []
+    for orient in (None, [tuple(s) + (1.0, 0.0, 0.0, 0.0) for s in seeds]):
+        sim = pf.Simulation3F(RAGGED, wl.BASE_PARAMS, "fp32")
+        sim.init_spec(seeds, 5.0, BUBBLES)
+        if orient is not None:
+            sim.set_orientation(orient)
+        sim.step(4)
+        out.append(sim.fields())
+    for k in out[0]:
+        assert np.array_equal(out[1][k], out[0][k]), k

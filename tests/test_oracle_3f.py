@@ -201,3 +201,35 @@ def test_reduces_to_the_melt_step_without_gas():
         assert np.abs(fo[k] - fm[k]).max() < 1e-12 * max(np.abs(fm[k]).max(), 1e-3), k
     assert np.abs(fo["vx"]).max() == 0.0 and np.abs(fo["p"]).max() == 0.0
     assert np.abs(fo["phi"] - 1.0).max() < 1e-15
+
+
+def test_rotated_grains_reduce_to_the_melt_step():
+    """With grain orientations the two-phase step still reduces, without gas
+    and flow, to the melt-only step with the same orientations (whose rotated
+    anisotropy is pinned in test_oracle_3d.py), to rounding; a quarter turn
+    about y reproduces the aligned grains."""
+    n = 24
+    seeds7 = [(9.3, 11.0, 12.5, 0.9, 0.2, -0.3, 0.1), (17.0, 6.0, 5.0, 0.5, 0.5, 0.5, -0.5)]
+    seeds = [s[:3] for s in seeds7]
+    o = oracle.Oracle3F(n, n, n, dict(P3F, g=0.0))
+    fs = o.fields_from_spec(seeds, 5.0, [])
+    o.init_fields(fs["phi"], fs["psi"], fs["C"])
+    o.set_orientation(seeds7)
+    m = oracle.Oracle3D(n, n, n, {k: wl.BASE_PARAMS[k] for k in oracle.PARAM_NAMES_3D})
+    m.init_spec(seeds, 5.0)
+    m.set_orientation(seeds7)
+    o.step(40)
+    m.step(40)
+    fo, fm = o.fields(), m.fields()
+    for k in ("psi", "C", "U"):
+        assert np.abs(fo[k] - fm[k]).max() < 1e-12 * max(np.abs(fm[k]).max(), 1e-3), k
+    # a quarter turn about y: the aligned result
+    a = oracle.Oracle3F(n, n, n, dict(P3F, g=0.0))
+    a.init_fields(fs["phi"], fs["psi"], fs["C"])
+    q = (math.cos(math.pi / 4), 0.0, math.sin(math.pi / 4), 0.0)
+    b = oracle.Oracle3F(n, n, n, dict(P3F, g=0.0))
+    b.init_fields(fs["phi"], fs["psi"], fs["C"])
+    b.set_orientation([s + q for s in seeds])
+    a.step(30)
+    b.step(30)
+    assert np.abs(a.fields()["psi"] - b.fields()["psi"]).max() < 1e-12
