@@ -452,8 +452,8 @@ def grad3(X, x, y, z):
 # -- the three-dimensional two-phase oracle (pf_oracle3d.c, or3f_*) ----------
 PARAM_NAMES_3F = ("rho_l", "rho_g", "nu", "sigma", "W_phi", "M_phi", "beta_phi", "beta_psi",
                   "beta_inter", "W0", "tau0", "eps_s", "k", "D", "Omega", "g", "grad_eps",
-                  "grad_eps_at", "s_e", "s_eps")
-FIELDS_3F = ("phi", "psi", "C", "U", "p", "vx", "vy", "vz", "mu")
+                  "grad_eps_at", "s_e", "s_eps", "thermal", "Le", "latent", "theta0", "cp")
+FIELDS_3F = ("phi", "psi", "C", "U", "p", "vx", "vy", "vz", "mu", "theta")
 _lib3f = None
 
 
@@ -485,6 +485,10 @@ def _l3f() -> ctypes.CDLL:
             lib.or3f_feq.argtypes = [ctypes.c_double, ctypes.c_double, D, D]
             lib.or3f_set_orientation.argtypes = [P, D, I]
             lib.or3f_set_orientation.restype = I
+            lib.or3f_set_temperature.argtypes = [P, D]
+            lib.or3f_thermal_totals.argtypes = [P, D]
+            lib.or3f_state_planes.argtypes = [P]
+            lib.or3f_state_planes.restype = I
             _lib3f = lib
     return _lib3f
 
@@ -500,7 +504,7 @@ class Oracle3F:
         self.h = self.lib.or3f_new(int(nx), int(ny), int(nz))
         if not self.h:
             raise MemoryError("oracle allocation failed")
-        dflt = {"s_e": 1.0, "s_eps": 1.0}
+        dflt = dict(THERMAL_DEFAULTS, s_e=1.0, s_eps=1.0)
         pv = _f64([float(params[k] if k in params else dflt[k]) for k in PARAM_NAMES_3F])
         self.lib.or3f_set_params(self.h, _dp(pv))
         if window is not None:           # (NX, NY, NZ, x0, y0, z0)
@@ -559,9 +563,20 @@ class Oracle3F:
         return dict(zip(FIELDS_3F, out.reshape((k,) + self.shape)))
 
     def state(self) -> np.ndarray:
-        out = np.empty(66 * int(np.prod(self.shape)))
+        npl = self.lib.or3f_state_planes(self.h)
+        out = np.empty(npl * int(np.prod(self.shape)))
         self.lib.or3f_state(self.h, _dp(out))
-        return out.reshape((66,) + self.shape)
+        return out.reshape((npl,) + self.shape)
+
+    def set_temperature(self, theta) -> None:
+        """Thermal mode: initial temperature field after init_spec / init_fields."""
+        self._theta = _f64(theta).ravel()
+        self.lib.or3f_set_temperature(self.h, _dp(self._theta))
+
+    def thermal_totals(self) -> dict:
+        out = np.zeros(2)
+        self.lib.or3f_thermal_totals(self.h, _dp(out))
+        return {"sum_e": out[0], "sum_theta": out[1]}
 
     def totals(self) -> dict:
         out = np.zeros(5)

@@ -643,9 +643,11 @@ static void collide19(const real f[19], const real feq[19], const real S[19], co
 /* Parameters of the two-phase step (the 2-D symbols). */
 enum { F3_RHO_L, F3_RHO_G, F3_NU, F3_SIGMA, F3_W_PHI, F3_M_PHI, F3_BETA_PHI, F3_BETA_PSI,
        F3_BETA_INTER, F3_W0, F3_TAU0, F3_EPS_S, F3_K, F3_D, F3_OMEGA, F3_G, F3_GRAD_EPS,
-       F3_GRAD_EPS_AT, F3_S_E, F3_S_EPS, NPAR3F };
+       F3_GRAD_EPS_AT, F3_S_E, F3_S_EPS,
+       /* temperature coupling (thermal mode, as in 2-D: readings R28-R30) */
+       F3_THERMAL, F3_LE, F3_LATENT, F3_THETA0, F3_CP, NPAR3F };
 
-enum { G3_PHI, G3_PSI, G3_C, G3_U, G3_P, G3_VX, G3_VY, G3_VZ, G3_MU, NFLD3F };
+enum { G3_PHI, G3_PSI, G3_C, G3_U, G3_P, G3_VX, G3_VY, G3_VZ, G3_MU, G3_THETA, NFLD3F };
 
 typedef struct {
   int nx, ny, nz, n;
@@ -660,10 +662,14 @@ typedef struct {
   real *nf[19], *nh[19], *ngpre[7], *ngpost[7], *nrr, *ns[7], *nQ_o, *nphi_o, *nC_o, *nv_o[3];
   /* streaming scratch */
   real *fS[19], *hS[19], *gS[7], *sS[7], *phiS, *psiS, *CS, *psiOld;
+  /* thermal mode: temperature populations, lagged H, streamed e and U */
+  real *e[7], *ne[7], *eS[7], *H_o, *nH_o, *US;
   real *fld[NFLD3F];
   real *block;
   double *rot;     /* grain orientation per site (9 per site), or NULL */
 } o3fstate;
+
+static int thermalf(const o3fstate *st) { return st->par[F3_THERMAL] != 0.0; }
 
 static double derivedf(const o3fstate *st, double *lam, double *Mc, double *th) {
   const double *p = st->par;
@@ -683,7 +689,8 @@ o3fstate *or3f_new(int nx, int ny, int nz) {
   st->nx = nx; st->ny = ny; st->nz = nz; st->n = nx * ny * nz;
   st->NX = nx; st->NY = ny; st->NZ = nz;
   const size_t n = (size_t)st->n;
-  const size_t planes = 2 * (19 + 19 + 7 + 7 + 1 + 7 + 1 + 1 + 1 + 3) + (19 + 19 + 7 + 7 + 4) + NFLD3F;
+  const size_t planes = 2 * (19 + 19 + 7 + 7 + 1 + 7 + 1 + 1 + 1 + 3) + (19 + 19 + 7 + 7 + 4) + NFLD3F +
+                        3 * 7 + 3;
   st->block = (real *)calloc(planes * n, sizeof(real));
   if (!st->block) { free(st); return NULL; }
   real *q = st->block;
@@ -699,6 +706,8 @@ o3fstate *or3f_new(int nx, int ny, int nz) {
   for (int i = 0; i < 19; ++i) { TAKE(st->fS[i]); TAKE(st->hS[i]); }
   for (int i = 0; i < 7; ++i) { TAKE(st->gS[i]); TAKE(st->sS[i]); }
   TAKE(st->phiS); TAKE(st->psiS); TAKE(st->CS); TAKE(st->psiOld);
+  for (int i = 0; i < 7; ++i) { TAKE(st->e[i]); TAKE(st->ne[i]); TAKE(st->eS[i]); }
+  TAKE(st->H_o); TAKE(st->nH_o); TAKE(st->US);
   for (int f = 0; f < NFLD3F; ++f) TAKE(st->fld[f]);
 #undef TAKE
   return st;
@@ -754,6 +763,31 @@ static double qpsif(const o3fstate *st, double phi, double psi, double U) {
          lam * om * om * (th + Mc * U);
 }
 
+/* Q_psi at temperature theta (thermal mode) */
+static double qpsif_at(const o3fstate *st, double phi, double psi, double U, double theta) {
+  const double *p = st->par;
+  double lam, Mc, th;
+  derivedf(st, &lam, &Mc, &th);
+  const double om = 1.0 - psi * psi;
+  return 4.0 * p[F3_BETA_PSI] * psi * om - 2.0 * p[F3_BETA_INTER] * (1.0 - phi) * (1.0 - phi) * (1.0 + psi) -
+         lam * om * om * (theta + Mc * U);
+}
+
+/* F(U) = 1/Le + M c_inf [1 + (1-k) U] */
+static double f_of_uf(const o3fstate *st, double U) {
+  double lam, Mc, th;
+  derivedf(st, &lam, &Mc, &th);
+  return 1.0 / st->par[F3_LE] + Mc * (1.0 + (1.0 - st->par[F3_K]) * U);
+}
+
+/* Temperature equilibrium on D3Q7 with the flux rho H v (Appendix B):
+ * e_0 = rho H + (w0 - 1) theta, e_i = w_i theta + w_i c_i . j / c_s^2 */
+static void teqf(double rhoH, double theta, const double j[3], real out[7]) {
+  for (int i = 0; i < 7; ++i)
+    out[i] = W7[i] * theta + W7[i] * (C7[i][0] * j[0] + C7[i][1] * j[1] + C7[i][2] * j[2]) / CS2_7;
+  out[0] = rhoH + (W7[0] - 1.0) * theta;
+}
+
 /* Pressure-based incompressible equilibrium on D3Q19: w p / c_s^2 off the
  * rest direction, -(1 - w0) p / c_s^2 on it, plus rho w [c.v/c_s^2 +
  * (c.v)^2/(2 c_s^4) - v^2/(2 c_s^2)] (reading R1 in 3-D). */
@@ -803,11 +837,49 @@ void or3f_init_fields(o3fstate *st, const double *phi, const double *psi, const 
     st->fld[G3_U][id] = U; st->fld[G3_P][id] = pp;
     st->fld[G3_VX][id] = v[0]; st->fld[G3_VY][id] = v[1]; st->fld[G3_VZ][id] = v[2];
     st->fld[G3_MU][id] = 0.0;
+    {
+      double lam, Mc, th;
+      derivedf(st, &lam, &Mc, &th);
+      st->fld[G3_THETA][id] = th;
+    }
+    if (thermalf(st)) {
+      /* H = c_p [theta0 - (c_p^s/c_p) h(psi)], e at equilibrium with rho H v,
+       * lagged source Q_psi(theta0) / F(U) (readings R28, R29) */
+      const double th0 = par[F3_THETA0];
+      const double H = par[F3_CP] * (th0 - par[F3_LATENT] * 0.5 * (1.0 + ps));
+      const double j[3] = {rho * H * v[0], rho * H * v[1], rho * H * v[2]};
+      real t7[7];
+      teqf(rho * H, th0, j, t7);
+      for (int i = 0; i < 7; ++i) st->e[i][id] = t7[i];
+      st->H_o[id] = H;
+      st->Q_o[id] = qpsif_at(st, ph, ps, U, th0) / f_of_uf(st, U);
+      st->fld[G3_THETA][id] = th0;
+    }
     sphi += ph;
   }
   if (!st->rho_bar_fixed)
     st->rho_bar = par[F3_RHO_G] + (sphi / st->n) * (par[F3_RHO_L] - par[F3_RHO_G]);
   st->steps = 0;
+}
+
+/* Thermal mode: set the initial temperature field theta (n) after
+ * or3f_init_fields / or3f_init_spec (the lagged values follow). */
+void or3f_set_temperature(o3fstate *st, const double *theta) {
+  const double *par = st->par;
+  for (int id = 0; id < st->n; ++id) {
+    const double ph = st->fld[G3_PHI][id], ps = st->fld[G3_PSI][id], c = st->fld[G3_C][id];
+    const double v[3] = {st->fld[G3_VX][id], st->fld[G3_VY][id], st->fld[G3_VZ][id]};
+    const double rho = par[F3_RHO_G] + ph * (par[F3_RHO_L] - par[F3_RHO_G]);
+    const double H = par[F3_CP] * (theta[id] - par[F3_LATENT] * 0.5 * (1.0 + ps));
+    const double j[3] = {rho * H * v[0], rho * H * v[1], rho * H * v[2]};
+    real t7[7];
+    teqf(rho * H, theta[id], j, t7);
+    for (int i = 0; i < 7; ++i) st->e[i][id] = t7[i];
+    st->H_o[id] = H;
+    const double U = supersatf(st, c, ps);
+    st->Q_o[id] = qpsif_at(st, ph, ps, U, theta[id]) / f_of_uf(st, U);
+    st->fld[G3_THETA][id] = theta[id];
+  }
 }
 
 /* Signed minimum-image offset on a periodic axis of length L */
@@ -934,6 +1006,12 @@ static void step3f(o3fstate *st) {
           C += st->sS[i][id];
         }
         st->phiS[id] = phi; st->psiS[id] = psi; st->psiOld[id] = psio; st->CS[id] = C;
+        if (thermalf(st)) {
+          /* temperature populations (plain pull) and U, whose gradient gives grad F */
+          for (int i = 0; i < 7; ++i)
+            st->eS[i][id] = st->e[i][idx3f(st, x - C7[i][0], y - C7[i][1], z - C7[i][2])];
+          st->US[id] = supersatf(st, C, psi);
+        }
       }
   double lam, Mc, thsys;
   derivedf(st, &lam, &Mc, &thsys);
@@ -1011,7 +1089,25 @@ static void step3f(o3fstate *st) {
         }
         const double as2 = as * as;
         const double U = supersatf(st, C, psi);
-        const double Q = qpsif(st, phi, psi, U);
+        /* thermal mode: rho H = sum e, theta = H / c_p + (c_p^s/c_p) h(psi) with the
+         * local rho; the source of the rewritten equation (Appendix B)
+         *   Q / F + W0^2 / F^2 grad F . (a_s^2 grad psi + N), grad F = M c_inf (1-k) grad U */
+        const int th_on = thermalf(st);
+        double rhoH = 0.0, theta = 0.0, Fu = 1.0, Q;
+        if (th_on) {
+          for (int i = 0; i < 7; ++i) rhoH += st->eS[i][id];
+          theta = rhoH / (rho * p[F3_CP]) + p[F3_LATENT] * 0.5 * (1.0 + psi);
+          const double Q0 = qpsif_at(st, phi, psi, U, theta);
+          double lam, Mc, thsys, gu[3];
+          derivedf(st, &lam, &Mc, &thsys);
+          grad19(st, st->US, x, y, z, gu);
+          double dot = 0;
+          for (int a = 0; a < 3; ++a) dot += Mc * (1.0 - k) * gu[a] * (as2 * gs[a] + N[a]);
+          Fu = f_of_uf(st, U);
+          Q = Q0 / Fu + W0 * W0 / (Fu * Fu) * dot;
+        } else {
+          Q = qpsif(st, phi, psi, U);
+        }
         const double at = -(1.0 / (2.0 * sqrt(2.0))) * W0 * as * (1.0 + (1.0 - k) * U) * (psi - psio) /
                           sqrt(gs[0] * gs[0] + gs[1] * gs[1] + gs[2] * gs[2] +
                                p[F3_GRAD_EPS_AT] * p[F3_GRAD_EPS_AT]);
@@ -1056,7 +1152,7 @@ static void step3f(o3fstate *st) {
             G[i] = -W7[i] * (C7[i][0] * N[0] + C7[i][1] * N[1] + C7[i][2] * N[2]) / as2;
             Fd[i] = W7[i] * Q / tau0 + 0.5 * W7[i] * (Q - Qo) / tau0;
           }
-          const double s1 = 1.0 / (W0 * W0 * as2 / (tau0 * CS2_7) + 0.5);
+          const double s1 = 1.0 / (W0 * W0 * as2 / (tau0 * Fu * CS2_7) + 0.5);
           const real S[7] = {1, s1, s1, s1, 1, 1, 1};
           collide7(gg, geq, S, G, Fd, out);
           for (int i = 0; i < 7; ++i) { st->ngpost[i][id] = out[i]; st->ngpre[i][id] = gg[i]; }
@@ -1084,6 +1180,34 @@ static void step3f(o3fstate *st) {
           collide7(ss, seq, S, G, Fd, out);
           for (int i = 0; i < 7; ++i) st->ns[i][id] = out[i];
         }
+        /* temperature collision (thermal mode): D3Q7 MRT with the equilibrium
+         * flux rho H v and G = w c . d_t(rho H v) / c_s^2 (backward difference),
+         * flux rate from k_T = Le D rho_l c_p = (1/s - 1/2) c_s^2 */
+        if (th_on) {
+          real ee[7], teq[7], G[7], Fd[7] = {0, 0, 0, 0, 0, 0, 0}, out[7];
+          const double rho_o = rg + phio * (rl - rg);
+          double j[3], Gq[3];
+          for (int a = 0; a < 3; ++a) {
+            j[a] = rhoH * v[a];
+            Gq[a] = j[a] - rho_o * st->H_o[id] * vo[a];
+          }
+          teqf(rhoH, theta, j, teq);
+          for (int i = 0; i < 7; ++i) {
+            ee[i] = st->eS[i][id];
+            G[i] = W7[i] * (C7[i][0] * Gq[0] + C7[i][1] * Gq[1] + C7[i][2] * Gq[2]) / CS2_7;
+          }
+          const double kT = p[F3_LE] * p[F3_D] * rl * p[F3_CP];
+          const double sth = 1.0 / (kT / CS2_7 + 0.5);
+          const real S[7] = {1, sth, sth, sth, 1, 1, 1};
+          collide7(ee, teq, S, G, Fd, out);
+          for (int i = 0; i < 7; ++i) st->ne[i][id] = out[i];
+          st->nH_o[id] = rhoH / rho;
+          st->fld[G3_THETA][id] = theta;
+        } else {
+          double lam, Mc, thsys;
+          derivedf(st, &lam, &Mc, &thsys);
+          st->fld[G3_THETA][id] = thsys;
+        }
         st->nQ_o[id] = Q;
         st->nphi_o[id] = phi;
         st->nC_o[id] = C;
@@ -1099,6 +1223,10 @@ static void step3f(o3fstate *st) {
   for (int i = 0; i < 7; ++i) { SW(st->gpre[i], st->ngpre[i]); SW(st->gpost[i], st->ngpost[i]); SW(st->s[i], st->ns[i]); }
   SW(st->rr, st->nrr); SW(st->Q_o, st->nQ_o); SW(st->phi_o, st->nphi_o); SW(st->C_o, st->nC_o);
   for (int a = 0; a < 3; ++a) SW(st->v_o[a], st->nv_o[a]);
+  if (thermalf(st)) {
+    for (int i = 0; i < 7; ++i) SW(st->e[i], st->ne[i]);
+    SW(st->H_o, st->nH_o);
+  }
 #undef SW
   st->steps++;
 }
@@ -1110,16 +1238,16 @@ void or3f_step(o3fstate *st, int n) {
 int or3f_nfields(void) { return NFLD3F; }
 int or3f_npar(void) { return NPAR3F; }
 
-/* Fields phi, psi, C, U, p, vx, vy, vz, mu_phi of the last step (9 x n). */
+/* Fields phi, psi, C, U, p, vx, vy, vz, mu_phi, theta of the last step (10 x n). */
 void or3f_fields(const o3fstate *st, double *out) {
   for (int f = 0; f < NFLD3F; ++f) memcpy(out + (size_t)f * st->n, st->fld[f], st->n * sizeof(double));
 }
 
 /* Raw state, 66 planes: f[19], h[19], g_pre[7], g_post[7], r, s[7], Q_o,
- * phi_o, C_o, vx_o, vy_o, vz_o. */
-int or3f_state_planes(void) { return 66; }
+ * phi_o, C_o, vx_o, vy_o, vz_o; in thermal mode 74 (e[7] and H_o follow). */
+int or3f_state_planes(const o3fstate *st) { return thermalf(st) ? 74 : 66; }
 void or3f_state(const o3fstate *st, double *out) {
-  const real *pl[66];
+  const real *pl[74];
   int q = 0;
   for (int i = 0; i < 19; ++i) pl[q++] = st->f[i];
   for (int i = 0; i < 19; ++i) pl[q++] = st->h[i];
@@ -1129,7 +1257,27 @@ void or3f_state(const o3fstate *st, double *out) {
   for (int i = 0; i < 7; ++i) pl[q++] = st->s[i];
   pl[q++] = st->Q_o; pl[q++] = st->phi_o; pl[q++] = st->C_o;
   for (int a = 0; a < 3; ++a) pl[q++] = st->v_o[a];
+  if (thermalf(st)) {             /* then e[7] and the lagged H */
+    for (int i = 0; i < 7; ++i) pl[q++] = st->e[i];
+    pl[q++] = st->H_o;
+  }
   for (int p = 0; p < q; ++p) memcpy(out + (size_t)p * st->n, pl[p], st->n * sizeof(double));
+}
+
+/* Thermal mode: compensated sums of the temperature populations (rho H) and
+ * of theta. */
+void or3f_thermal_totals(const o3fstate *st, double *out) {
+  double s2[2] = {0, 0}, c2[2] = {0, 0};
+  for (int id = 0; id < st->n; ++id)
+    for (int k2 = 0; k2 < 8; ++k2) {
+      const double v = k2 < 7 ? st->e[k2][id] : st->fld[G3_THETA][id];
+      const int j = k2 < 7 ? 0 : 1;
+      const double t = s2[j] + v;
+      c2[j] += fabs(s2[j]) >= fabs(v) ? (s2[j] - t) + v : (v - t) + s2[j];
+      s2[j] = t;
+    }
+  out[0] = s2[0] + c2[0];
+  out[1] = s2[1] + c2[1];
 }
 
 /* Totals (compensated): sum phi, sum C, sum of the NS momentum j = sum c f

@@ -233,3 +233,94 @@ def test_rotated_grains_reduce_to_the_melt_step():
     a.step(30)
     b.step(30)
     assert np.abs(a.fields()["psi"] - b.fields()["psi"]).max() < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# thermal mode of the two-phase step (temperature lattice with advection)
+# ---------------------------------------------------------------------------
+T3F = dict(P3F, thermal=1, Le=2.0, latent=1.0, theta0=-0.55, cp=10.0)
+
+
+def test_thermal_reduces_to_the_thermal_melt_step():
+    """Without gas and flow the thermal two-phase step follows the thermal
+    melt step (pinned in test_oracle_3d.py: enthalpy, latent heat, heat
+    diffusion, the grad F source) to rounding, temperature field included."""
+    n = 24
+    seeds = [(9.3, 11.0, 12.5), (17.0, 6.0, 5.0)]
+    o = oracle.Oracle3F(n, n, n, dict(T3F, g=0.0))
+    fs = o.fields_from_spec(seeds, 5.0, [])
+    o.init_fields(fs["phi"], fs["psi"], fs["C"])
+    z, y, x = np.mgrid[0:n, 0:n, 0:n].astype(float)
+    theta = -0.55 + 0.05 * np.sin(2 * np.pi * x / n) * np.cos(2 * np.pi * z / n)
+    o.set_temperature(theta)
+    m = oracle.Oracle3D(n, n, n, {k: T3F[k] if k in T3F else wl.BASE_PARAMS[k]
+                                  for k in oracle.PARAM_NAMES_3D})
+    m.init_fields(fs["psi"], fs["C"], theta)
+    o.step(40)
+    m.step(40)
+    fo, fm = o.fields(), m.fields()
+    for k in ("psi", "C", "U", "theta"):
+        assert np.abs(fo[k] - fm[k]).max() < 1e-12 * max(np.abs(fm[k]).max(), 1e-3), k
+    assert abs(o.thermal_totals()["sum_e"] / m.thermal_totals()["sum_e"] - 1) < 1e-13
+
+
+def test_temperature_rides_a_uniform_flow():
+    """Galilean check of the advected temperature lattice (equilibrium flux
+    rho H v and the d_t(rho H v) term): in a uniform flow V along z the centre
+    of mass of a temperature Gaussian moves V t, and the blob spreads at
+    2 alpha t per axis as at rest (alpha = Le D)."""
+    n, V, Le = 48, 0.02, 1.5
+    z, y, x = np.mgrid[0:n, 0:n, 0:n].astype(float)
+    th = -0.5 + 0.1 * np.exp(-((x - 24) ** 2 + (y - 24) ** 2 + (z - 24) ** 2) / 18.0)
+    one = np.ones_like(th)
+    o = oracle.Oracle3F(n, n, n, dict(T3F, g=0.0, Le=Le, theta0=-0.5))
+    o.init_fields(one, -one, one, 0 * one, 0 * one, V * one)
+    o.set_temperature(th)
+    cen, var = [], []
+    for T in (30, 70):                  # after the start-up transient of the flux
+        o.step(T - (0 if T == 30 else 30))
+        w = o.fields()["theta"] + 0.5
+        c0 = 24 + V * T                                  # minimum images around it
+        dz = (z - c0 + n / 2) % n - n / 2
+        cz = c0 + (dz * w).sum() / w.sum()
+        cen.append(cz)
+        var.append([((q - 24) ** 2 * w).sum() / w.sum() for q in (x, y)] +
+                   [((dz - (cz - c0)) ** 2 * w).sum() / w.sum()])
+    assert abs((cen[1] - cen[0]) / 40.0 - V) < 5e-3 * V     # periodic tails: 0.2 %
+    for a in range(3):
+        assert math.isclose((var[1][a] - var[0][a]) / 40.0, 2 * Le * P3F["D"], rel_tol=1e-2)
+
+
+def test_thermal_two_phase_conserves_enthalpy():
+    """Seeds, bubbles, buoyancy and flow with the temperature lattice on: sum
+    rho H (the seven populations) and sum phi, sum C stay constant."""
+    n = 24
+    o = oracle.Oracle3F(n, n, n, dict(T3F, g=2e-5))
+    o.init_spec([(8.0, 12.0, 12.0)], 5.0, [(16.5, 11.0, 12.5, 4.5)])
+    t0, c0 = o.thermal_totals(), o.totals()
+    o.step(100)
+    t1, c1 = o.thermal_totals(), o.totals()
+    assert abs(t1["sum_e"] / t0["sum_e"] - 1) < 1e-13
+    assert abs(c1["sum_phi"] / c0["sum_phi"] - 1) < 1e-13
+    assert abs(c1["sum_C"] / c0["sum_C"] - 1) < 1e-13
+    assert np.abs(o.fields()["vy"]).max() > 1e-7          # the flow is there
+
+
+def test_gas_temperature_uses_the_local_density():
+    """theta = H / c_p + latent h(psi) with rho H from the local density
+    rho(phi): a flat gas layer in a melt at uniform theta0 keeps theta0 inside
+    the gas as well as in the liquid, up to the small change the relaxing
+    discrete profile makes (it moves phi, and so rho, without carrying rho H;
+    3e-3 here).  Dividing by rho_l instead would put the gas near theta0 rho_g /
+    rho_l."""
+    nz, W = 64, 2.0
+    zz = np.arange(nz, dtype=float)
+    phi1 = 0.5 + 0.5 * np.tanh((np.abs(zz - 32.0) - 10.0) / (2 * math.sqrt(2) * W))
+    phi = np.broadcast_to(phi1[:, None, None], (nz, 2, 2)).copy()
+    one = np.ones_like(phi)
+    o = oracle.Oracle3F(2, 2, nz, dict(T3F, g=0.0, W_phi=W))
+    o.init_fields(phi, -one, phi)
+    o.step(20)
+    f = o.fields()
+    assert f["phi"].min() < 0.05
+    assert np.abs(f["theta"] - T3F["theta0"]).max() < 1e-2
