@@ -200,21 +200,23 @@ def cpu_oracle_variant(kind: str, steps: int = 0) -> dict:
     (the same with the temperature lattice)."""
     cores = os.cpu_count() or 1
     steps = steps or {"thermal": 60, "bounded": 60, "3d": 120, "3d_thermal": 300,
-                      "3d_flow": 160}[kind]  # about 10 s of CPU work
+                      "3d_flow": 160, "3d_flow_thermal": 140}[kind]  # about 10 s of CPU work
     code = f"""
 import json, sys, time
 sys.path.insert(0, {ROOT!r})
 import oracle
 from paper_2407_01651_gb300 import workload as wl
 kind = {kind!r}
-if kind == "3d_flow":
+if kind in ("3d_flow", "3d_flow_thermal"):
     n = 64
     seeds, R_s, bub = wl.flow_3d(n, 4, 8)
     p = {{k: wl.BASE_PARAMS[k] for k in oracle.PARAM_NAMES_3F}}
+    if kind == "3d_flow_thermal":
+        p.update(wl.THERMAL_PARAMS)
     o = oracle.Oracle3F(n, n, n, p)
     o.init_spec(seeds, R_s, bub)
     sites = n ** 3
-    what = f"{{n}}^3 melt with 4 seeds and 8 bubbles (3-D two-phase oracle)"
+    what = f"{{n}}^3 melt with 4 seeds and 8 bubbles (3-D two-phase oracle{{', thermal' if p['thermal'] else ''}})"
 elif kind in ("3d", "3d_thermal"):
     n = 96
     seeds, R_s = wl.growth_3d(n, 8)
@@ -527,11 +529,14 @@ def run_3d_flow(args) -> None:
     seeds, R_s, bubbles = wl.flow_3d(n)
     stream = torch.cuda.current_stream()
     prec = args.precision if args.precision in ("fp32", "fp64") else "fp32"
-    sim = pf.Simulation3F((n, n, n), wl.BASE_PARAMS, prec, stream=stream.cuda_stream)
+    thermal = args.workload == "3d_flow_thermal"
+    params = dict(wl.BASE_PARAMS, **wl.THERMAL_PARAMS) if thermal else wl.BASE_PARAMS
+    sim = pf.Simulation3F((n, n, n), params, prec, stream=stream.cuda_stream)
     sim.init_spec(seeds, R_s, bubbles)
     if args.chunk:
         sim.set_chunk(args.chunk)
     d0 = sim.reduce()
+    t0 = sim.reduce_thermal() if thermal else None
     sim.step(args.warmup)
     l0 = sim.launches
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -543,27 +548,34 @@ def run_3d_flow(args) -> None:
     ms = e0.elapsed_time(e1)
     launches = sim.launches - l0
     d = sim.reduce()
+    extra = {}
+    if thermal:
+        t1 = sim.reduce_thermal()
+        extra = {"sum_rhoH_rel_drift": t1["sum_e"] / t0["sum_e"] - 1.0}
     sites = n ** 3
-    bpl = 66 * 2 * (4 if prec == "fp32" else 8)
+    bpl = (74 if thermal else 66) * 2 * (4 if prec == "fp32" else 8)
     gbs = bpl * sites * args.steps / ms / 1e6
     peak, peak_kind = measured_peaks()
     print(json.dumps({
-        "metric": "3-D two-phase coupled-step MLUPS at 256³ and % of HBM roofline",
+        "metric": ("3-D thermal two-phase" if thermal else "3-D two-phase") +
+                  " coupled-step MLUPS at 256³ and % of HBM roofline",
         "value": sites * args.steps / ms / 1e3, "unit": "MLUPS", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPE[prec], "data": "synthetic",
         "config": {"workload": f"{n}^3 periodic melt, 32 seeds (R=8) and 64 bubbles "
-                               "(R~U[6,14]) at uniform positions, seed 5",
+                               "(R~U[6,14]) at uniform positions, seed 5" +
+                               (", temperature lattice (Le 50, theta0 -0.55)" if thermal else ""),
                    "lattice": [n, n, n], "precision": prec},
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                      "frac": gbs / peak, "traffic": None, "peak_kind": peak_kind,
                      "bytes_per_lu": bpl, "kernel": "k_step3f (one launch per step)"},
         "sum_phi_rel_drift": d["sum_phi"] / d0["sum_phi"] - 1.0,
         "sum_C_rel_drift": d["sum_C"] / d0["sum_C"] - 1.0,
-        "solid_fraction": d["sum_hpsi"] / sites,
+        "solid_fraction": d["sum_hpsi"] / sites, **extra,
         "gpu_launches": launches,
-        "cpu_baseline": None if args.no_cpu_baseline else cpu_oracle_variant("3d_flow")}))
+        "cpu_baseline": None if args.no_cpu_baseline else
+        cpu_oracle_variant("3d_flow_thermal" if thermal else "3d_flow")}))
     sim.close()
 
 
@@ -641,14 +653,15 @@ def main() -> None:
     ap.add_argument("--tile-b", type=int, default=0)
     ap.add_argument("--workload", default="lattice",
                     choices=("lattice", "ensemble", "precision", "thermal", "bounded", "3d",
-                             "3d_thermal", "3d_flow"),
+                             "3d_thermal", "3d_flow", "3d_flow_thermal"),
                     help="lattice: the 4096^2 headline; ensemble: 96 uneven domains; "
                          "precision: 8192x4096 in FP32 / FP16 / BF16 storage; "
                          "thermal: the 4096^2 lattice with the temperature lattice on; "
                          "bounded: the same with the paper's Section-4 boundaries; "
                          "3d: the 3-D dendrite step on a 256^3 melt; "
                          "3d_thermal: the same with the temperature lattice; "
-                         "3d_flow: the 3-D two-phase step (flow, bubbles, dendrites) on 256^3")
+                         "3d_flow: the 3-D two-phase step (flow, bubbles, dendrites) on 256^3; "
+                         "3d_flow_thermal: the same with the temperature lattice")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -676,7 +689,7 @@ def main() -> None:
     if args.workload in ("3d", "3d_thermal"):
         run_3d(args)
         return
-    if args.workload == "3d_flow":
+    if args.workload in ("3d_flow", "3d_flow_thermal"):
         run_3d_flow(args)
         return
 

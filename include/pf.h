@@ -446,22 +446,28 @@ pf_status pf3_destroy(pf3_handle *h);
  * s_e, s_eps, s_q = 8(2 - s_nu)/(8 - s_nu) on q and m, s_nu on the stresses,
  * 1 elsewhere; CAC: fluxes at s_phi); psi and C on the D3Q7 lattices of the
  * pf3_* step with the gas couplings of Section 2 (f3 in Q_psi, the gas-vacuum
- * flux J) and advection of C.  Isothermal (thermal must be 0), periodic cube,
- * the lattice-aligned grain or the orientations of pf3f_set_orientation.
- * Arrays are [z][y][x].
+ * flux J) and advection of C.  With thermal = 1 the D3Q7 temperature lattice
+ * of the pf3_* step is added with the advective flux rho H v (and d_t(rho H v)
+ * through (I - S/2)), theta = H / c_p + latent h(psi) from the local density,
+ * F(U) and the grad F source (rho_g cp >= 3/4).  Periodic cube, the
+ * lattice-aligned grain or the orientations of pf3f_set_orientation.  Arrays are
+ * [z][y][x].
  * ------------------------------------------------------------------------ */
 typedef struct pf3f_handle pf3f_handle;
 
 /* Raw FP64 state planes of pf3f_get_state: f[19], h[19], g_pre[7], g_post[7],
  * r = 1/a_s^2, s[7], Q_psi, phi_o, C_o, vx_o, vy_o, vz_o. */
 #define PF3F_STATE_PLANES 66
-/* Field planes of pf3f_get_fields: phi, psi, C, U, p, vx, vy, vz, mu_phi. */
+/* Thermal mode: the 66 planes, then e[7] and the lagged H. */
+#define PF3F_STATE_PLANES_THERMAL 74
+/* Field planes of pf3f_get_fields: phi, psi, C, U, p, vx, vy, vz, mu_phi (and
+ * theta in thermal mode: 10). */
 #define PF3F_FIELD_PLANES 9
 
 /* Handle of an nx x ny x nz lattice (each in [4, 2048]), FP32 or FP64 storage,
- * on cuda_stream: two state copies of 59 population and 7 auxiliary planes, 9
- * field planes.  Errors: BAD_ARG (sizes, precision, parameters, thermal = 1),
- * OOM. */
+ * on cuda_stream: two state copies of 59 population and 7 auxiliary planes (66
+ * and 8 in thermal mode), 9 field planes (10).  Errors: BAD_ARG (sizes,
+ * precision, parameters), OOM. */
 pf_status pf3f_create(const pf_params *p, int nx, int ny, int nz, pf_precision prec,
                       void *cuda_stream, pf3f_handle **out);
 /* Spherical seeds n_seeds x (x, y, z) of radius R_s and bubbles n_bub x (x, y,
@@ -493,6 +499,20 @@ pf_status pf3f_get_state(pf3f_handle *h, double *out, size_t n);
 /* FP64 totals of the last fields: out[0] = sum phi, out[1] = sum C (both
  * conserved), out[2] = sum h(psi).  Synchronises.  Errors: BAD_ARG, OOM, CUDA. */
 pf_status pf3f_reduce(pf3f_handle *h, double out[3]);
+/* Thermal mode: temperature field theta (host, FP64, n = nx*ny*nz) of the
+ * initial state, after pf3f_init_spec / pf3f_set_fields (which start at theta0)
+ * and before the first step: temperature populations at equilibrium with rho H v,
+ * the lagged H and Q_psi(theta) / F(U).  Synchronises.  Errors: BAD_ARG (not
+ * thermal, size, non-finite), STATE, OOM, CUDA. */
+pf_status pf3f_set_temperature(pf3f_handle *h, const double *theta, size_t n);
+/* Thermal mode: FP64 sums out[0] = rho H (the seven temperature populations,
+ * conserved on the periodic cube), out[1] = theta, out[2] = psi.  Synchronises.
+ * Errors: BAD_ARG (NULL, not thermal), OOM, CUDA. */
+pf_status pf3f_reduce_thermal(pf3f_handle *h, double out[3]);
+/* Field planes (9, or 10 in thermal mode) and raw state planes (66 or 74) of the
+ * handle; -1 for NULL. */
+int pf3f_field_planes(const pf3f_handle *h);
+int pf3f_state_planes(const pf3f_handle *h);
 /* Kernel launches of the handle; -1 for NULL. */
 long long pf3f_launch_count(const pf3f_handle *h);
 /* Last error of the handle, or of the last failed pf3f_create for NULL. */

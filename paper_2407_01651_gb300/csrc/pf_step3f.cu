@@ -51,9 +51,14 @@ using d3::wrapm;
 constexpr int F_POP = 0, H_POP = 19, G_PRE = 38, G_POST = 45, S_POP = 52, NPOPF = 59;
 constexpr int AX_RR = 0, AX_QO = 1, AX_PHIO = 2, AX_CO = 3, AX_VO = 4, NAUXF = 7;
 constexpr int NSTATEF = 66, NFIELDSF = 9;
+// thermal mode: temperature populations e after s, the lagged H after v_o, theta
+// as a tenth field
+constexpr int E_POP = 59, NPOPF_TH = 66, AX_HO = 7, NAUXF_TH = 8, NSTATEF_TH = 74,
+              NFIELDSF_TH = 10;
 // shared memory of k_step3f: 5 rings (phi, psi, v_o) of 4 planes of the halo tile
+// (a sixth ring, of U, in thermal mode)
 template <typename R>
-constexpr size_t ring_bytes() { return 5 * 4 * HY * HX * sizeof(R); }
+constexpr size_t ring_bytes(bool th) { return (th ? 6 : 5) * 4 * HY * HX * sizeof(R); }
 
 // D3Q19: rest, faces, edges; opposite directions in pairs (2j-1, 2j)
 __host__ __device__ constexpr int c19(int i, int a) {
@@ -103,6 +108,8 @@ struct CoefF {
   R eps, ge2, gat2, four_bpsi, lam, theta, Mcinf, inv_tau0, c4W0sq_tau0, k, inv_omk, D, aW0;
   R s_phi;
   R cm[NMOM];          // (1 - s_k) / |M_k|^2 of the NS moments above
+  // thermal mode: c_p, latent / 2, 1/Le, W0^2, s_T and 1 - s_T/2 (k_T = Le D rho_l c_p)
+  R cp, halfL, iLe, W0sq, sth, hsth;
 };
 
 template <typename S, typename R>
@@ -165,14 +172,29 @@ __device__ __forceinline__ void stream_g(const ArgsF<S, R>& a, int x, int y, int
 }
 
 // ROT: grain orientations (anisotropy on g' = R^T grad psi, N = R N'(g')).
-template <typename S, typename R, bool ROT>
+// TH: the temperature lattice of Appendix B on D3Q7 with the flux rho H v and
+// d_t(rho H v) through (I - S/2); theta = H / c_p + (c_p^s/c_p) h(psi) from the
+// local density; F(U) in the psi relaxation and the source Q / F + W0^2 / F^2
+// grad F . (a_s^2 grad psi + N), grad F = M c_inf (1-k) grad U from a U ring.
+// U = (2C/A - 1)/(1-k) of the streamed solute at (x, y, z), for the U ring
+template <typename S, typename R>
+__device__ __forceinline__ R stream_U(const ArgsF<S, R>& a, int x, int y, int z, R psi) {
+  CSum<R> cs;
+#pragma unroll
+  for (int i = 0; i < 7; ++i) cs.add(ld<R>(pl(a.in, S_POP + i, a.ps), src7(a, x, y, z, i)));
+  const R A = (R(1) + a.c.k) - (R(1) - a.c.k) * psi;
+  return (R(2) * cs.value() * frcp(A) - R(1)) * a.c.inv_omk;
+}
+
+template <typename S, typename R, bool ROT, bool TH>
 __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R> a) {
-  // rings of phi, psi and v_o (dynamic: 54 KB in FP64)
+  // rings of phi, psi, v_o (and U) (dynamic: 54 KB in FP64)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R (*rphi)[HY][HX] = reinterpret_cast<R (*)[HY][HX]>(smem_raw);
   R (*rpsi)[HY][HX] = rphi + 4;
   R (*rv0)[HY][HX] = rphi + 8;
   R (*rv[3])[HY][HX] = {rv0, rv0 + 4, rv0 + 8};
+  R (*rU)[HY][HX] = rphi + 20;         // TH only
   const int t = threadIdx.x;
   int hx = 0, hy = 0;
   const bool interior = t < NIN;
@@ -207,6 +229,7 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R> a) {
         const unsigned long long s0 = site_of(a, x, y, z);
 #pragma unroll
         for (int c = 0; c < 3; ++c) rv[c][slot][hy][hx] = pl(a.ain, AX_VO + c, a.ps)[s0];
+        if constexpr (TH) rU[slot][hy][hx] = stream_U(a, x, y, z, psi);
         if (k == 1) {
 #pragma unroll
           for (int i = 0; i < 7; ++i) gC[i] = g[i];
@@ -234,6 +257,7 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R> a) {
         const unsigned long long sn = site_of(a, x, y, zn);
 #pragma unroll
         for (int c = 0; c < 3; ++c) rv[c][slot][hy][hx] = pl(a.ain, AX_VO + c, a.ps)[sn];
+        if constexpr (TH) rU[slot][hy][hx] = stream_U(a, x, y, zn, psi);
       }
       __syncthreads();
       if (mine) {
@@ -439,13 +463,33 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R> a) {
         const R iA = frcp(A);
         const R U = (R(2) * C * iA - R(1)) * c.inv_omk;
         const R omp2 = R(1) - psi * psi;
-        const R Q = c.four_bpsi * psi * omp2 - c.binter2 * (R(1) - phi) * (R(1) - phi) * opsi -
-                    c.lam * omp2 * omp2 * (c.theta + c.Mcinf * U);
+        // TH: rho H = sum e, theta from the local density
+        R rhoH = R(0), theta = c.theta, iF = R(1);
+        R ev[7];
+        if constexpr (TH) {
+#pragma unroll
+          for (int i = 0; i < 7; ++i) ev[i] = ld<R>(pl(a.in, E_POP + i, a.ps), src7(a, x, y, z, i));
+          CSum<R> ce;
+#pragma unroll
+          for (int i = 0; i < 7; ++i) ce.add(ev[i]);
+          rhoH = ce.value();
+          theta = rhoH * frcp(rho * c.cp) + c.halfL * opsi;
+        }
+        R Q = c.four_bpsi * psi * omp2 - c.binter2 * (R(1) - phi) * (R(1) - phi) * opsi -
+              c.lam * omp2 * omp2 * (theta + c.Mcinf * U);
+        if constexpr (TH) {
+          R ux, uy, uz;
+          d3::grad18<R>(rU[sm], rU[s0], rU[sp], hy, hx, ux, uy, uz);
+          iF = frcp(c.iLe + c.Mcinf * (R(1) + omk * U));
+          const R dot = c.Mcinf * omk *
+                        (ux * (as2 * gs[0] + Nx) + uy * (as2 * gs[1] + Ny) + uz * (as2 * gs[2] + Nz));
+          Q = Q * iF + c.W0sq * iF * iF * dot;
+        }
         const R at = -c.aW0 * as * (R(1) + omk * U) * (psi - poC) * frsqrt(gm2 + c.gat2);
         // psi: D3Q7 as in the melt-only step
         {
           const R m0 = psi + (Q + R(0.5) * (Q - Qo)) * c.inv_tau0;
-          const R s1 = frcp(c.c4W0sq_tau0 * as2 + R(0.5));
+          const R s1 = frcp(c.c4W0sq_tau0 * as2 * iF + R(0.5));
           const R hs = R(1) - R(0.5) * s1;
           const R Jx = gC[1] - gC[2], Jy = gC[3] - gC[4], Jz = gC[5] - gC[6];
           const R gq = R(-0.25) * ias2;
@@ -491,6 +535,30 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R> a) {
 #pragma unroll
           for (int i = 0; i < 7; ++i) st<S, R>(pl(a.out, S_POP + i, a.ps), site, so[i]);
         }
+        // TH: temperature collision, D3Q7: equilibrium flux j = rho H v, G = w c .
+        // d_t(rho H v) / c_s^2 (backward difference) through (I - S/2), flux rate
+        // s_T, the rest at 1; base theta/8 rounded to a multiple of ulp(rho H)/2 so
+        // that the rest population rho H - 6 theta/8 is exact in the common case
+        if constexpr (TH) {
+          const R rho_o = c.rg + phio * c.drho;
+          const R Ho = pl(a.ain, AX_HO, a.ps)[site];
+          R Sf[3];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const R jq = rhoH * v[q];
+            const R Jq = ev[2 * q + 1] - ev[2 * q + 2];
+            Sf[q] = Jq - c.sth * (Jq - jq) + c.hsth * (jq - rho_o * Ho * vo[q]);
+          }
+          const R b = round_to_multiple(theta * R(0.125), R(2) * quantum_quarter_ulp(rhoH));
+          R eo[7];
+          eo[0] = fma(R(-6), b, rhoH);
+          eo[1] = fma(R(0.5), Sf[0], b); eo[2] = fma(R(-0.5), Sf[0], b);
+          eo[3] = fma(R(0.5), Sf[1], b); eo[4] = fma(R(-0.5), Sf[1], b);
+          eo[5] = fma(R(0.5), Sf[2], b); eo[6] = fma(R(-0.5), Sf[2], b);
+#pragma unroll
+          for (int i = 0; i < 7; ++i) st<S, R>(pl(a.out, E_POP + i, a.ps), site, eo[i]);
+          pl(a.aout, AX_HO, a.ps)[site] = rhoH * irho;
+        }
         pl(a.aout, AX_PHIO, a.ps)[site] = phi;
         pl(a.aout, AX_CO, a.ps)[site] = C;
 #pragma unroll
@@ -499,6 +567,7 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R> a) {
           const R vals[NFIELDSF] = {phi, psi, C, U, pr, v[0], v[1], v[2], mu};
 #pragma unroll
           for (int f = 0; f < NFIELDSF; ++f) pl(a.fields, f, a.ps)[site] = vals[f];
+          if constexpr (TH) pl(a.fields, NFIELDSF, a.ps)[site] = theta;
         }
       }
 #pragma unroll
@@ -550,6 +619,44 @@ __device__ void write_eqf(const ArgsF<S, R>& a, unsigned long long site, R phi, 
   const R vals[NFIELDSF] = {phi, psi, C, U, p, v[0], v[1], v[2], R(0)};
 #pragma unroll
   for (int f = 0; f < NFIELDSF; ++f) pl(a.fields, f, a.ps)[site] = vals[f];
+}
+
+// Thermal mode: temperature populations at equilibrium for theta (rho H = rho c_p
+// (theta - latent h(psi)), flux rho H v), lagged H, the lagged source Q_psi(theta)
+// / F(U) and the theta field; phi, psi, C, v as initialised.
+template <typename S, typename R>
+__device__ void write_thf(const ArgsF<S, R>& a, unsigned long long site, R phi, R psi, R C,
+                          const R v[3], R theta) {
+  const CoefF<R>& c = a.c;
+  const R rho = c.rg + phi * c.drho;
+  const R H = c.cp * (theta - c.halfL * (R(1) + psi));
+  const R rhoH = rho * H;
+  st<S, R>(pl(a.out, E_POP, a.ps), site, rhoH - R(0.75) * theta);
+#pragma unroll
+  for (int i = 1; i < 7; ++i) {
+    const R cj = rhoH * (R(cx7(i)) * v[0] + R(cy7(i)) * v[1] + R(cz7(i)) * v[2]);
+    st<S, R>(pl(a.out, E_POP + i, a.ps), site, R(0.125) * theta + R(0.5) * cj);
+  }
+  pl(a.aout, AX_HO, a.ps)[site] = H;
+  const R omk = R(1) - c.k;
+  const R U = (R(2) * C / ((R(1) + c.k) - omk * psi) - R(1)) * c.inv_omk;
+  const R omp2 = R(1) - psi * psi;
+  const R Q = c.four_bpsi * psi * omp2 - c.binter2 * (R(1) - phi) * (R(1) - phi) * (R(1) + psi) -
+              c.lam * omp2 * omp2 * (theta + c.Mcinf * U);
+  pl(a.aout, AX_QO, a.ps)[site] = Q / (c.iLe + c.Mcinf * (R(1) + omk * U));
+  pl(a.fields, NFIELDSF, a.ps)[site] = theta;
+}
+
+// Temperature field of the initial state (phi, psi, C, v from the field planes).
+template <typename S, typename R>
+__global__ void k_settempf(ArgsF<S, R> a, const double* theta, int uniform, double theta0) {
+  const unsigned long long n = (unsigned long long)a.nx * a.ny * a.nz;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const R v[3] = {pl(a.fields, 5, a.ps)[i], pl(a.fields, 6, a.ps)[i], pl(a.fields, 7, a.ps)[i]};
+    write_thf<S, R>(a, i, pl(a.fields, 0, a.ps)[i], pl(a.fields, 1, a.ps)[i],
+                    pl(a.fields, 2, a.ps)[i], v, uniform ? (R)theta0 : (R)theta[i]);
+  }
 }
 
 __device__ __forceinline__ double min_image(double d, double L) {
@@ -610,7 +717,7 @@ __global__ void k_setf(ArgsF<S, R> a, const double* in) {
 
 template <typename S, typename R>
 __global__ void k_statef(const S* pin, const R* ain, unsigned long long ps, unsigned long long n,
-                         double* out) {
+                         int thermal, double* out) {
   for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < n;
        j += (unsigned long long)gridDim.x * blockDim.x) {
     int q = 0;
@@ -624,13 +731,18 @@ __global__ void k_statef(const S* pin, const R* ain, unsigned long long ps, unsi
     out[(q++) * n + j] = (double)ain[AX_PHIO * ps + j];
     out[(q++) * n + j] = (double)ain[AX_CO * ps + j];
     for (int c = 0; c < 3; ++c) out[(q++) * n + j] = (double)ain[(AX_VO + c) * ps + j];
+    if (thermal) {
+      for (int i = 0; i < 7; ++i) out[(q++) * n + j] = (double)ld<R>(pl(pin, E_POP + i, ps), j);
+      out[(q++) * n + j] = (double)ain[AX_HO * ps + j];
+    }
   }
 }
 
 template <typename R>
-__global__ void k_fieldsf(const R* f, unsigned long long ps, unsigned long long n, double* out) {
+__global__ void k_fieldsf(const R* f, unsigned long long ps, unsigned long long n, int planes,
+                          double* out) {
   for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-       j < NFIELDSF * n; j += (unsigned long long)gridDim.x * blockDim.x)
+       j < planes * n; j += (unsigned long long)gridDim.x * blockDim.x)
     out[j] = (double)f[(j / n) * ps + j % n];
 }
 
@@ -686,6 +798,7 @@ struct pf3f_handle {
   int rotated = 0;                // grain orientations set
   int* grain = nullptr;           // grain index per site
   void* rot = nullptr;            // 9 x n_grains rotation entries (storage precision)
+  int thermal = 0, npop = NPOPF, naux = NAUXF, nfields = NFIELDSF, nstate = NSTATEF;
   int cur = 0, inited = 0;
   long long steps = 0, launches = 0;
   std::string err;
@@ -739,6 +852,16 @@ static CoefF<R> coeff(const pf3f_handle* h) {
   const double rate[NMOM] = {p.s_e, p.s_eps, s_q, s_q, s_q, s_nu, s_nu, s_nu, s_nu, s_nu,
                              s_q, s_q, s_q};
   for (int k = 0; k < NMOM; ++k) c.cm[k] = (R)((1.0 - rate[k]) / mnorm(k));
+  if (p.thermal) {
+    const double kT = p.Le * p.D * p.rho_l * p.cp;      // k_T = alpha rho_l c_p, alpha = Le D
+    const double sth = 1.0 / (4.0 * kT + 0.5);          // c_s^2 = 1/4
+    c.cp = (R)p.cp;
+    c.halfL = (R)(0.5 * p.latent);
+    c.iLe = (R)(1.0 / p.Le);
+    c.W0sq = (R)(p.W0 * p.W0);
+    c.sth = (R)sth;
+    c.hsth = (R)(1.0 - 0.5 * sth);
+  }
   return c;
 }
 
@@ -824,19 +947,30 @@ extern "C" pf_status pf3f_create(const pf_params* p, int nx, int ny, int nz, pf_
       !(p->eps_s >= 0 && p->eps_s < 0.25) || !(p->grad_eps > 0) || !(p->grad_eps_at > 0) ||
       1.0 - (1.0 - p->k) * p->Omega == 0.0)
     return failf(nullptr, PF_ERR_BAD_ARG, "a dendrite parameter is out of range");
-  if (p->thermal) return failf(nullptr, PF_ERR_BAD_ARG, "the 3-D two-phase step is isothermal");
+  if (p->thermal != 0 && p->thermal != 1) return failf(nullptr, PF_ERR_BAD_ARG, "thermal must be 0 or 1");
+  if (p->thermal) {
+    if (!pos(p->Le) || !pos(p->cp) || !std::isfinite(p->latent) || !std::isfinite(p->theta0))
+      return failf(nullptr, PF_ERR_BAD_ARG, "thermal mode needs Le, cp > 0, finite latent, theta0");
+    if (p->rho_g * p->cp < 0.75)
+      return failf(nullptr, PF_ERR_BAD_ARG, "thermal mode needs rho_g * cp >= 3/4 (stability)");
+  }
   const unsigned long long n = (unsigned long long)nx * ny * nz;
   pf3f_handle* h = new (std::nothrow) pf3f_handle();
   if (!h) return failf(nullptr, PF_ERR_OOM, "host allocation failed");
   h->p = *p; h->prec = prec; h->stream = (cudaStream_t)cuda_stream;
   h->nx = nx; h->ny = ny; h->nz = nz; h->n = n;
   h->elem = prec == PF_FP64 ? 8 : 4;
+  h->thermal = p->thermal;
+  h->npop = p->thermal ? NPOPF_TH : NPOPF;
+  h->naux = p->thermal ? NAUXF_TH : NAUXF;
+  h->nfields = p->thermal ? NFIELDSF_TH : NFIELDSF;
+  h->nstate = p->thermal ? NSTATEF_TH : NSTATEF;
   bool ok = true;
   for (int c = 0; c < 2; ++c) {
-    ok = ok && cudaMalloc(&h->pop[c], n * NPOPF * h->elem) == cudaSuccess;
-    ok = ok && cudaMalloc(&h->aux[c], n * NAUXF * h->elem) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->pop[c], n * h->npop * h->elem) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->aux[c], n * h->naux * h->elem) == cudaSuccess;
   }
-  ok = ok && cudaMalloc(&h->fields, n * NFIELDSF * h->elem) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->fields, n * h->nfields * h->elem) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     pf3f_destroy(h);
@@ -887,6 +1021,11 @@ extern "C" pf_status pf3f_init_spec(pf3f_handle* h, const double* seeds, int n_s
                                                 n_bub, std::sqrt(2.0 * h->p.beta_psi), h->p.W0,
                                                 std::sqrt(2.0 * h->p.beta_phi), h->p.W_phi, h->p.k);
     PF3F_CUDA(h, cudaGetLastError());
+    if (h->thermal) {
+      k_settempf<S, R><<<1024, 256, 0, h->stream>>>(a, nullptr, 1, h->p.theta0);
+      PF3F_CUDA(h, cudaGetLastError());
+      h->launches++;
+    }
     return PF_OK;
   });
   if (st != PF_OK) return st;
@@ -911,6 +1050,11 @@ extern "C" pf_status pf3f_set_fields(pf3f_handle* h, const double* fields7, size
     a.aout = (R*)h->aux[0];
     k_setf<S, R><<<1024, 256, 0, h->stream>>>(a, h->scratch);
     PF3F_CUDA(h, cudaGetLastError());
+    if (h->thermal) {
+      k_settempf<S, R><<<1024, 256, 0, h->stream>>>(a, nullptr, 1, h->p.theta0);
+      PF3F_CUDA(h, cudaGetLastError());
+      h->launches++;
+    }
     return PF_OK;
   });
   if (st != PF_OK) return st;
@@ -985,17 +1129,26 @@ extern "C" pf_status pf3f_step(pf3f_handle* h, int n_steps) {
   return dispatchf(h, [&](auto s_t, auto r_t) {
     using S = decltype(s_t);
     using R = decltype(r_t);
-    if (ring_bytes<R>() > 48 * 1024) {
-      PF3F_CUDA(h, cudaFuncSetAttribute(k_step3f<S, R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)ring_bytes<R>()));
-      PF3F_CUDA(h, cudaFuncSetAttribute(k_step3f<S, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)ring_bytes<R>()));
+    const size_t smem = ring_bytes<R>(h->thermal != 0);
+    if (smem > 48 * 1024) {
+      auto big = [&](auto kern) {
+        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      };
+      PF3F_CUDA(h, big(k_step3f<S, R, false, false>));
+      PF3F_CUDA(h, big(k_step3f<S, R, true, false>));
+      PF3F_CUDA(h, big(k_step3f<S, R, false, true>));
+      PF3F_CUDA(h, big(k_step3f<S, R, true, true>));
     }
     for (int t = 0; t < n_steps; ++t) {
       const ArgsF<S, R> a = argsf<S, R>(h, t == n_steps - 1);
       const int tiles = a.tiles_x * a.tiles_y * a.tiles_z;
-      if (h->rotated) k_step3f<S, R, true><<<tiles, THREADS, ring_bytes<R>(), h->stream>>>(a);
-      else k_step3f<S, R, false><<<tiles, THREADS, ring_bytes<R>(), h->stream>>>(a);
+      if (h->thermal) {
+        if (h->rotated) k_step3f<S, R, true, true><<<tiles, THREADS, smem, h->stream>>>(a);
+        else k_step3f<S, R, false, true><<<tiles, THREADS, smem, h->stream>>>(a);
+      } else {
+        if (h->rotated) k_step3f<S, R, true, false><<<tiles, THREADS, smem, h->stream>>>(a);
+        else k_step3f<S, R, false, false><<<tiles, THREADS, smem, h->stream>>>(a);
+      }
       PF3F_CUDA(h, cudaGetLastError());
       h->cur ^= 1;
       h->steps++;
@@ -1007,12 +1160,14 @@ extern "C" pf_status pf3f_step(pf3f_handle* h, int n_steps) {
 
 extern "C" pf_status pf3f_get_fields(pf3f_handle* h, double* out, size_t n) {
   if (!h) return PF_ERR_BAD_ARG;
-  const size_t need = (size_t)NFIELDSF * h->n;
-  if (!out || n < need) return failf(h, PF_ERR_BAD_ARG, "output must hold 9 planes");
+  const size_t need = (size_t)h->nfields * h->n;
+  if (!out || n < need) return failf(h, PF_ERR_BAD_ARG, "output must hold pf3f_field_planes planes");
   pf_status st = ensure_scratchf(h, need);
   if (st != PF_OK) return st;
-  if (h->prec == PF_FP64) k_fieldsf<double><<<1024, 256, 0, h->stream>>>((const double*)h->fields, h->n, h->n, h->scratch);
-  else k_fieldsf<float><<<1024, 256, 0, h->stream>>>((const float*)h->fields, h->n, h->n, h->scratch);
+  if (h->prec == PF_FP64)
+    k_fieldsf<double><<<1024, 256, 0, h->stream>>>((const double*)h->fields, h->n, h->n, h->nfields, h->scratch);
+  else
+    k_fieldsf<float><<<1024, 256, 0, h->stream>>>((const float*)h->fields, h->n, h->n, h->nfields, h->scratch);
   PF3F_CUDA(h, cudaGetLastError());
   h->launches++;
   PF3F_CUDA(h, cudaMemcpyAsync(out, h->scratch, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -1022,15 +1177,15 @@ extern "C" pf_status pf3f_get_fields(pf3f_handle* h, double* out, size_t n) {
 
 extern "C" pf_status pf3f_get_state(pf3f_handle* h, double* out, size_t n) {
   if (!h) return PF_ERR_BAD_ARG;
-  const size_t need = (size_t)NSTATEF * h->n;
-  if (!out || n < need) return failf(h, PF_ERR_BAD_ARG, "output must hold 66 planes");
+  const size_t need = (size_t)h->nstate * h->n;
+  if (!out || n < need) return failf(h, PF_ERR_BAD_ARG, "output must hold pf3f_state_planes planes");
   pf_status st = ensure_scratchf(h, need);
   if (st != PF_OK) return st;
   st = dispatchf(h, [&](auto s_t, auto r_t) {
     using S = decltype(s_t);
     using R = decltype(r_t);
     k_statef<S, R><<<1024, 256, 0, h->stream>>>((const S*)h->pop[h->cur], (const R*)h->aux[h->cur],
-                                                 h->n, h->n, h->scratch);
+                                                 h->n, h->n, h->thermal, h->scratch);
     PF3F_CUDA(h, cudaGetLastError());
     return PF_OK;
   });
@@ -1045,4 +1200,83 @@ extern "C" pf_status pf3f_reduce(pf3f_handle* h, double out[3]) {
   if (!h) return PF_ERR_BAD_ARG;
   if (!out) return failf(h, PF_ERR_BAD_ARG, "NULL output");
   return reduce_fields(h, out);
+}
+
+extern "C" int pf3f_field_planes(const pf3f_handle* h) { return h ? h->nfields : -1; }
+extern "C" int pf3f_state_planes(const pf3f_handle* h) { return h ? h->nstate : -1; }
+
+extern "C" pf_status pf3f_set_temperature(pf3f_handle* h, const double* theta, size_t n) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (!h->thermal) return failf(h, PF_ERR_BAD_ARG, "the handle is not in thermal mode");
+  if (!theta || n != h->n) return failf(h, PF_ERR_BAD_ARG, "need theta of nx*ny*nz");
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(theta[i])) return failf(h, PF_ERR_BAD_ARG, "non-finite theta");
+  if (!h->inited || h->steps != 0)
+    return failf(h, PF_ERR_STATE, "set the temperature after initialisation, before stepping");
+  pf_status st = ensure_scratchf(h, n);
+  if (st != PF_OK) return st;
+  PF3F_CUDA(h, cudaMemcpyAsync(h->scratch, theta, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  st = dispatchf(h, [&](auto s_t, auto r_t) {
+    using S = decltype(s_t);
+    using R = decltype(r_t);
+    ArgsF<S, R> a = argsf<S, R>(h, true);
+    a.out = (S*)h->pop[0];
+    a.aout = (R*)h->aux[0];
+    k_settempf<S, R><<<1024, 256, 0, h->stream>>>(a, h->scratch, 0, 0.0);
+    PF3F_CUDA(h, cudaGetLastError());
+    return PF_OK;
+  });
+  if (st != PF_OK) return st;
+  h->launches++;
+  PF3F_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PF_OK;
+}
+
+// Thermal totals: sum of the seven temperature populations (rho H), sum theta,
+// sum psi; fixed-order partials.
+template <typename S, typename R>
+__global__ void k_reducef_th(const S* pin, const R* f, unsigned long long ps, unsigned long long n,
+                             double* part) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < n;
+       j += (unsigned long long)gridDim.x * blockDim.x) {
+    for (int i = 0; i < 7; ++i) a0 += (double)ld<R>(pl(pin, E_POP + i, ps), j);
+    a1 += (double)f[NFIELDSF * ps + j];
+    a2 += (double)f[ps + j];
+  }
+  __shared__ double sh[3][256];
+  sh[0][threadIdx.x] = a0;
+  sh[1][threadIdx.x] = a1;
+  sh[2][threadIdx.x] = a2;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) part[3 * blockIdx.x + q] = sh[q][0];
+}
+
+extern "C" pf_status pf3f_reduce_thermal(pf3f_handle* h, double out[3]) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (!out) return failf(h, PF_ERR_BAD_ARG, "NULL output");
+  if (!h->thermal) return failf(h, PF_ERR_BAD_ARG, "the handle is not in thermal mode");
+  const int nb = 1024;
+  pf_status st = ensure_scratchf(h, 3 * nb + 3);
+  if (st != PF_OK) return st;
+  st = dispatchf(h, [&](auto s_t, auto r_t) {
+    using S = decltype(s_t);
+    using R = decltype(r_t);
+    k_reducef_th<S, R><<<nb, 256, 0, h->stream>>>((const S*)h->pop[h->cur], (const R*)h->fields,
+                                                   h->n, h->n, h->scratch);
+    k_reducef_final<<<1, 32, 0, h->stream>>>(h->scratch, nb, h->scratch + 3 * nb);
+    PF3F_CUDA(h, cudaGetLastError());
+    return PF_OK;
+  });
+  if (st != PF_OK) return st;
+  h->launches += 2;
+  PF3F_CUDA(h, cudaMemcpyAsync(out, h->scratch + 3 * nb, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  PF3F_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PF_OK;
 }

@@ -141,6 +141,10 @@ def lib() -> ctypes.CDLL:
     L.pf3f_get_rho_bar.restype = ctypes.c_double
     L.pf3f_set_chunk.argtypes = [P, I]
     L.pf3f_set_orientation.argtypes = [P, D, I]
+    L.pf3f_set_temperature.argtypes = [P, D, S]
+    L.pf3f_reduce_thermal.argtypes = [P, D]
+    L.pf3f_field_planes.argtypes = [P]
+    L.pf3f_state_planes.argtypes = [P]
     L.pf3f_step.argtypes = [P, I]
     L.pf3f_get_fields.argtypes = [P, D, S]
     L.pf3f_get_state.argtypes = [P, D, S]
@@ -161,7 +165,7 @@ def lib() -> ctypes.CDLL:
                  "pf3f_create",
                  "pf3f_init_spec", "pf3f_set_fields", "pf3f_set_rho_bar", "pf3f_set_chunk",
                  "pf3f_step", "pf3f_get_fields", "pf3f_get_state", "pf3f_reduce", "pf3f_destroy",
-                 "pf3f_set_orientation"):
+                 "pf3f_set_orientation", "pf3f_set_temperature", "pf3f_reduce_thermal"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -500,7 +504,8 @@ class Simulation3D:
 
 
 PF3F_STATE_PLANES = 66
-FIELDS_3F = ("phi", "psi", "C", "U", "p", "vx", "vy", "vz", "mu")
+PF3F_STATE_PLANES_THERMAL = 74
+FIELDS_3F = ("phi", "psi", "C", "U", "p", "vx", "vy", "vz", "mu", "theta")
 
 
 def _check3f(code: int, handle=None) -> None:
@@ -571,14 +576,27 @@ class Simulation3F:
         _check3f(lib().pf3f_step(self.h, int(n)), self.h)
 
     def fields(self) -> dict:
-        out = np.empty(len(FIELDS_3F) * self.n)
+        k = lib().pf3f_field_planes(self.h)
+        out = np.empty(k * self.n)
         _check3f(lib().pf3f_get_fields(self.h, _dp(out), out.size), self.h)
-        return dict(zip(FIELDS_3F, out.reshape((len(FIELDS_3F),) + self.shape)))
+        return dict(zip(FIELDS_3F, out.reshape((k,) + self.shape)))
 
     def get_state(self) -> np.ndarray:
-        out = np.empty(PF3F_STATE_PLANES * self.n)
+        k = lib().pf3f_state_planes(self.h)
+        out = np.empty(k * self.n)
         _check3f(lib().pf3f_get_state(self.h, _dp(out), out.size), self.h)
-        return out.reshape((PF3F_STATE_PLANES,) + self.shape)
+        return out.reshape((k,) + self.shape)
+
+    def set_temperature(self, theta) -> None:
+        """Thermal mode: temperature field of the initial state ([z][y][x])."""
+        a = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(self.shape))
+        _check3f(lib().pf3f_set_temperature(self.h, _dp(a), self.n), self.h)
+
+    def reduce_thermal(self) -> dict:
+        """Thermal mode: FP64 sums of rho H (the seven populations), theta, psi."""
+        out = np.zeros(3)
+        _check3f(lib().pf3f_reduce_thermal(self.h, _dp(out)), self.h)
+        return {"sum_e": out[0], "sum_theta": out[1], "sum_psi": out[2]}
 
     def reduce(self) -> dict:
         out = np.zeros(3)

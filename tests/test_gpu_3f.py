@@ -16,9 +16,9 @@ pytestmark = pytest.mark.gpu
 
 P3F = {k: wl.BASE_PARAMS[k] for k in oracle.PARAM_NAMES_3F}
 FLOOR = {"phi": 1e-9, "psi": 1e-9, "C": 1e-9, "U": 0.1, "p": 1e-4, "vx": 1e-3, "vy": 1e-3,
-         "vz": 1e-3, "mu": 1e-3}
+         "vz": 1e-3, "mu": 1e-3, "theta": 1e-9}
 TOL32 = {"phi": 1e-5, "psi": 1e-5, "C": 1e-5, "U": 1e-5, "p": 5e-5, "vx": 5e-5, "vy": 5e-5,
-         "vz": 5e-5, "mu": 1e-4}
+         "vz": 5e-5, "mu": 1e-4, "theta": 1e-5}
 
 RAGGED = (40, 19, 13)
 SEEDS = [(10.3, 9.1, 6.2), (33.0, 4.0, 11.5)]
@@ -159,7 +159,7 @@ def test_3f_configuration_errors():
     with pytest.raises(pf.PFError):
         pf.Simulation3F((8, 8, 8), wl.BASE_PARAMS, "fp16")
     with pytest.raises(pf.PFError):
-        pf.Simulation3F((8, 8, 8), dict(wl.BASE_PARAMS, **wl.THERMAL_PARAMS), "fp32")
+        pf.Simulation3F((8, 8, 8), dict(wl.BASE_PARAMS, thermal=2), "fp32")
     sim = pf.Simulation3F((8, 8, 8), wl.BASE_PARAMS, "fp32")
     with pytest.raises(pf.PFError) as e:
         sim.step(1)                        # not initialised
@@ -226,3 +226,127 @@ def test_3f_identity_orientation_is_the_aligned_grain():
         out.append(sim.fields())
     for k in out[0]:
         assert np.array_equal(out[1][k], out[0][k]), k
+
+
+
+# ---------------------------------------------------------------------------
+# thermal mode (TH template): advected temperature lattice, F(U), grad F source
+# ---------------------------------------------------------------------------
+T3F = dict(P3F, thermal=1, Le=2.0, latent=1.0, theta0=-0.55, cp=10.0)
+
+
+def theta_field(shape):
+    nx, ny, nz = shape
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:nx].astype(float)
+    return -0.55 + 0.05 * np.sin(2 * np.pi * x / nx) * np.cos(2 * np.pi * z / nz) + \
+        0.03 * np.exp(-((y - ny / 2) ** 2) / 8.0)
+
+
+def pair_t(shape, precision, params=T3F, **kw):
+    o, sim = pair(shape, precision, params=params, **kw)
+    th = theta_field(shape)
+    o.set_temperature(th)
+    sim.set_temperature(th)
+    o.set_rho_bar(sim.rho_bar)
+    return o, sim
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", TOL32)])
+def test_3f_thermal_steps_match_oracle(precision, tol):
+    o, sim = pair_t(RAGGED, precision)
+    assert set(sim.fields()) == set(oracle.FIELDS_3F)
+    sim.set_chunk(5)
+    for _ in range(3):
+        o.step(1)
+        sim.step(1)
+        compare(o, sim, tol)
+    if precision == "fp64":
+        so, sg = o.state(), sim.get_state()
+        assert sg.shape[0] == pf.PF3F_STATE_PLANES_THERMAL == so.shape[0]
+        for p in range(pf.PF3F_STATE_PLANES_THERMAL):
+            assert rel(sg[p], so[p], 1e-12) <= 1e-10, p
+
+
+def test_3f_thermal_fp64_many_steps_and_conservation():
+    """100 FP64 steps with gravity, a bubble, a rotated seed and the
+    temperature lattice: within 1e-9 of the oracle; sum rho H, sum phi and
+    sum C constant to 1e-12."""
+    n = 24
+    params = dict(T3F, g=1e-5)
+    seeds7 = [(8.0, 12.0, 12.0, 0.9, 0.2, -0.3, 0.1)]
+    o, sim = pair_t((n, n, n), "fp64", params=params, seeds=[s[:3] for s in seeds7], R_s=5.0,
+                    bubbles=[(16.5, 11.0, 12.5, 4.5)])
+    o.set_orientation(seeds7)
+    sim.set_orientation(seeds7)
+    t0, r0 = sim.reduce_thermal(), sim.reduce()
+    o.step(100)
+    sim.step(100)
+    compare(o, sim, 1e-9)
+    t1, r1 = sim.reduce_thermal(), sim.reduce()
+    assert abs(t1["sum_e"] / t0["sum_e"] - 1) < 1e-12
+    assert abs(r1["sum_phi"] / r0["sum_phi"] - 1) < 1e-12
+    assert abs(r1["sum_C"] / r0["sum_C"] - 1) < 1e-12
+
+
+def test_3f_thermal_fp32_drift_and_bounded_error():
+    n = 32
+    o, sim = pair_t((n, n, n), "fp32", seeds=[(10.0, 12.0, 16.0)], R_s=6.0,
+                    bubbles=[(22.0, 20.0, 10.0, 6.0), (8.0, 26.0, 24.0, 4.0)])
+    t0 = sim.reduce_thermal()
+    o.step(200)
+    sim.step(200)
+    compare(o, sim, 2e-3)
+    assert abs(sim.reduce_thermal()["sum_e"] / t0["sum_e"] - 1) <= 1e-6
+
+
+def test_3f_thermal_full_size_windows():
+    """The 256^3 thermal two-phase workload (32 seeds, 64 bubbles, Le 50,
+    theta0 everywhere) in the benchmark's launch configuration: after 2 steps,
+    24^3 windows match oracle windows in global coordinates."""
+    n = 256
+    seeds, R_s, bubbles = wl.flow_3d(n)
+    params = dict(P3F, **wl.THERMAL_PARAMS)
+    sim = pf.Simulation3F((n, n, n), dict(wl.BASE_PARAMS, **wl.THERMAL_PARAMS), "fp32")
+    sim.init_spec(seeds, R_s, bubbles)
+    T = 2
+    sim.step(T)
+    fg = sim.fields()
+    sim.close()
+    W, M = 24, 2 * T
+    centres = ([(int(s[0]) + 7, int(s[1]), int(s[2])) for s in seeds[:2]] +
+               [(int(b[0]) + int(b[3]), int(b[1]), int(b[2])) for b in bubbles[:2]])
+    ref, got = {k: [] for k in fg}, {k: [] for k in fg}
+    rho_bar = None
+    for cx, cy, cz in centres:
+        x0, y0, z0 = cx - W // 2, cy - W // 2, cz - W // 2
+        o = oracle.Oracle3F(W, W, W, params, window=(n, n, n, x0, y0, z0))
+        if rho_bar is None:
+            rho_bar = P3F["rho_g"] + o.mean_phi_global(bubbles) * (P3F["rho_l"] - P3F["rho_g"])
+        o.set_rho_bar(rho_bar)
+        o.init_spec(seeds, R_s, bubbles)
+        o.step(T)
+        fo = o.fields()
+        idx = [(np.arange(M, W - M) + c0) % n for c0 in (z0, y0, x0)]
+        for k in fg:
+            ref[k].append(fo[k][M:W - M, M:W - M, M:W - M].ravel())
+            got[k].append(fg[k][np.ix_(*idx)].ravel())
+    for k in fg:
+        err = rel(np.concatenate(got[k]), np.concatenate(ref[k]), FLOOR[k])
+        assert err <= TOL32[k], (k, err)
+
+
+def test_3f_thermal_configuration_errors():
+    with pytest.raises(pf.PFError):
+        pf.Simulation3F((8, 8, 8), dict(wl.BASE_PARAMS, **dict(T3F, cp=5.0)), "fp32")  # rho_g cp < 3/4
+    iso = pf.Simulation3F((8, 8, 8), wl.BASE_PARAMS, "fp32")
+    iso.init_spec([(4, 4, 4)], 2.0, [])
+    with pytest.raises(pf.PFError):
+        iso.set_temperature(np.zeros((8, 8, 8)))
+    with pytest.raises(pf.PFError):
+        iso.reduce_thermal()
+    sim = pf.Simulation3F((8, 8, 8), dict(wl.BASE_PARAMS, **T3F), "fp32")
+    sim.init_spec([(4, 4, 4)], 2.0, [])
+    sim.step(1)
+    with pytest.raises(pf.PFError) as e:
+        sim.set_temperature(np.zeros((8, 8, 8)))
+    assert e.value.code == pf.PF_ERR_STATE
