@@ -350,3 +350,24 @@ def test_3f_thermal_configuration_errors():
     with pytest.raises(pf.PFError) as e:
         sim.set_temperature(np.zeros((8, 8, 8)))
     assert e.value.code == pf.PF_ERR_STATE
+
+
+def test_3f_thermal_long_fp32_run():
+    """2000 FP32 steps of the thermal two-phase step with gravity, bubbles and
+    rotated grains on 64^3: every field stays finite, sum phi and sum rho H stay
+    put, the solid grows and the released latent heat warms the melt."""
+    n = 64
+    seeds, R_s, bub = wl.flow_3d(n, 4, 6, rng_seed=7)
+    par = dict(wl.BASE_PARAMS, **wl.THERMAL_PARAMS, g=1e-5)
+    sim = pf.Simulation3F((n, n, n), par, "fp32")
+    sim.init_spec(seeds, R_s, bub)
+    sim.set_orientation([tuple(s) + (0.9, 0.1 * i, -0.2, 0.3) for i, s in enumerate(seeds)])
+    r0, t0 = sim.reduce(), sim.reduce_thermal()
+    sim.step(2000)
+    f, r, t = sim.fields(), sim.reduce(), sim.reduce_thermal()
+    assert all(np.isfinite(v).all() for v in f.values())
+    assert abs(r["sum_phi"] / r0["sum_phi"] - 1) < 1e-8
+    assert abs(r["sum_C"] / r0["sum_C"] - 1) < 1e-6
+    assert abs(t["sum_e"] / t0["sum_e"] - 1) < 1e-6
+    assert r["sum_hpsi"] > 1.5 * r0["sum_hpsi"]
+    assert f["theta"].mean() > wl.THERMAL_PARAMS["theta0"]
