@@ -358,6 +358,7 @@ def _l3() -> ctypes.CDLL:
             lib.or3_thermal_totals.argtypes = [P, D]
             lib.or3_set_orientation.argtypes = [P, D, I]
             lib.or3_set_orientation.restype = I
+            lib.or3_set_bc.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
             lib.or3_orientation.argtypes = [P, I, D]
             _lib3 = lib
     return _lib3
@@ -395,6 +396,12 @@ class Oracle3D:
         s = np.ascontiguousarray(_f64(seeds7).reshape(-1, 7))
         if self.lib.or3_set_orientation(self.h, _dp(s), len(s)) != 0:
             raise MemoryError("oracle allocation failed")
+
+    def set_bc(self, bc) -> None:
+        """Side types x-, x+, y-, y+, z-, z+: 0 periodic, 1 symmetric, 2 wall,
+        3 far field (opposite sides both periodic or both not)."""
+        arr = (ctypes.c_int * 6)(*[int(b) for b in bc])
+        self.lib.or3_set_bc(self.h, arr)
 
     def orientation(self, site: int) -> np.ndarray:
         out = np.zeros(9)

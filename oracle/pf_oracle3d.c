@@ -78,6 +78,7 @@ enum { Q_BETA_PSI, Q_W0, Q_TAU0, Q_EPS_S, Q_K, Q_D, Q_OMEGA, Q_GRAD_EPS, Q_GRAD_
 typedef struct {
   int nx, ny, nz, n;
   int NX, NY, NZ, x0, y0, z0;  /* placement of this lattice in a periodic NX x NY x NZ one */
+  int bc[6];                    /* side types x-, x+, y-, y+, z-, z+ (B3_*) */
   double par[NPAR3];
   long steps;
   real *gpre[7], *gpost[7], *rr, *s[7], *Q_o;      /* state */
@@ -90,8 +91,61 @@ typedef struct {
 } o3state;
 
 static inline int wrap3(int a, int n) { a %= n; return a < 0 ? a + n : a; }
+/* Side types of the melt step (reading R35; the 2-D types of reading R31 that
+ * act on D3Q7 lattices): periodic, symmetric, wall, far field. */
+enum { B3_PERIODIC = 0, B3_SYMMETRIC = 1, B3_WALL = 2, B3_FARFIELD = 3 };
+
 static inline int idx3(const o3state *st, int x, int y, int z) {
   return (wrap3(z, st->nz) * st->ny + wrap3(y, st->ny)) * st->nx + wrap3(x, st->nx);
+}
+
+void or3_set_bc(o3state *st, const int *bc) {
+  for (int k = 0; k < 6; ++k) st->bc[k] = bc[k];
+}
+
+/* Pull source of D3Q7 direction i at (x, y, z): the site and direction read,
+ * and the mode: 0 plain (periodic wrap), 1 bounce-back (symmetric or wall: on
+ * D3Q7 the mirror of an axis population is its opposite at the site itself),
+ * 2 anti-bounce-back to the far-field value (reading R35). */
+static int pull7(const o3state *st, int x, int y, int z, int i, int *src, int *q) {
+  const int X[3] = {x - C7[i][0], y - C7[i][1], z - C7[i][2]};
+  const int L[3] = {st->nx, st->ny, st->nz};
+  int mode = 0;
+  for (int a = 0; a < 3; ++a)
+    if (X[a] < 0 || X[a] >= L[a]) {
+      const int t = st->bc[2 * a + (X[a] < 0 ? 0 : 1)];
+      if (t == B3_FARFIELD) mode = 2;
+      else if (t != B3_PERIODIC) mode = 1;
+    }
+  if (mode) {
+    *src = idx3(st, x, y, z);
+    *q = i == 0 ? 0 : (i % 2 ? i + 1 : i - 1);     /* opposite of an axis direction */
+  } else {
+    *src = idx3(st, X[0], X[1], X[2]);
+    *q = i;
+  }
+  return mode;
+}
+
+/* Value of a field at (x, y, z), one site beyond the lattice at most: periodic
+ * sides wrap; across a non-periodic side the mirror site's value, unchanged at
+ * a symmetric side or wall (zero normal gradient) and 2 X_far - X at a far-field
+ * side (far = -1 for psi, 0 for U); the axes are mapped in the order x, y, z. */
+static real field3(const o3state *st, const real *X, int x, int y, int z, double far) {
+  int c[3] = {x, y, z};
+  const int L[3] = {st->nx, st->ny, st->nz};
+  int ff[3] = {0, 0, 0};
+  for (int a = 0; a < 3; ++a)
+    if (c[a] < 0 || c[a] >= L[a]) {
+      const int t = st->bc[2 * a + (c[a] < 0 ? 0 : 1)];
+      if (t == B3_PERIODIC) continue;
+      c[a] = c[a] < 0 ? -1 - c[a] : 2 * L[a] - 1 - c[a];
+      ff[a] = t == B3_FARFIELD;
+    }
+  real v = X[idx3(st, c[0], c[1], c[2])];
+  for (int a = 0; a < 3; ++a)
+    if (ff[a]) v = 2.0 * far - v;
+  return v;
 }
 
 o3state *or3_new(int nx, int ny, int nz) {
@@ -309,9 +363,11 @@ void or3_init(o3state *st, const double *seeds, int n_seeds, double R_s) {
           const double L[3] = {st->NX, st->NY, st->NZ};
           double r2 = 0;
           for (int a = 0; a < 3; ++a) {
-            d[a] = fmod(d[a], L[a]);
-            if (d[a] < -0.5 * L[a]) d[a] += L[a];
-            if (d[a] >= 0.5 * L[a]) d[a] -= L[a];
+            if (st->bc[2 * a] == B3_PERIODIC) {    /* minimum image; plain distance otherwise */
+              d[a] = fmod(d[a], L[a]);
+              if (d[a] < -0.5 * L[a]) d[a] += L[a];
+              if (d[a] >= 0.5 * L[a]) d[a] -= L[a];
+            }
             r2 += d[a] * d[a];
           }
           const double v = tanh(sqrt(2.0 * p[Q_BETA_PSI]) * (R_s - sqrt(r2)) / p[Q_W0]);
@@ -367,10 +423,13 @@ static void step3(o3state *st) {
         const int id = (z * ny + y) * nx + x;
         real psi = 0, psio = 0, C = 0;
         for (int i = 0; i < 7; ++i) {
-          const int src = idx3(st, x - C7[i][0], y - C7[i][1], z - C7[i][2]);
+          int src, q;
+          const int mode = pull7(st, x, y, z, i, &src, &q);
           const real gold = st->gpre[i][id];
-          st->gS[i][id] = gold + (st->gpost[i][src] - gold) * st->rr[src];
-          st->sS[i][id] = st->s[i][src];
+          /* far field: anti-bounce-back -f*_opp + 2 w_i X_far (psi -1, C 1) */
+          const real gsrc = mode == 2 ? -st->gpost[q][src] + 2.0 * W7[i] * (-1.0) : st->gpost[q][src];
+          st->gS[i][id] = gold + (gsrc - gold) * st->rr[src];
+          st->sS[i][id] = mode == 2 ? -st->s[q][src] + 2.0 * W7[i] * 1.0 : st->s[q][src];
           psi += st->gS[i][id];
           psio += gold;
           C += st->sS[i][id];
@@ -378,8 +437,11 @@ static void step3(o3state *st) {
         st->psiS[id] = psi; st->psiOld[id] = psio; st->CS[id] = C;
         st->US[id] = supersat3(st, C, psi);
         if (thermal3(st))
-          for (int i = 0; i < 7; ++i)
-            st->eS[i][id] = st->e[i][idx3(st, x - C7[i][0], y - C7[i][1], z - C7[i][2])];
+          for (int i = 0; i < 7; ++i) {
+            int src, q;
+            const int mode = pull7(st, x, y, z, i, &src, &q);
+            st->eS[i][id] = mode == 2 ? -st->e[q][src] + 2.0 * W7[i] * p[Q_THETA0] : st->e[q][src];
+          }
       }
   /* pass 2: gradient, anisotropy, sources, collisions */
 #pragma omp parallel for schedule(static)
@@ -390,7 +452,7 @@ static void step3(o3state *st) {
         const real psi = st->psiS[id], psio = st->psiOld[id], C = st->CS[id];
         double g[3] = {0, 0, 0};
         for (int q = 0; q < 18; ++q) {
-          const real v = st->psiS[idx3(st, x + N18[q][0], y + N18[q][1], z + N18[q][2])];
+          const real v = field3(st, st->psiS, x + N18[q][0], y + N18[q][1], z + N18[q][2], -1.0);
           for (int a = 0; a < 3; ++a) g[a] += WN18[q] * N18[q][a] * v;
         }
         for (int a = 0; a < 3; ++a) g[a] /= (1.0 / 3.0);   /* D3Q19 c_s^2 = 1/3 */
@@ -423,7 +485,7 @@ static void step3(o3state *st) {
           derived3(st, &lam, &Mc, &thsys);
           double gu[3] = {0, 0, 0};
           for (int q = 0; q < 18; ++q) {
-            const real v = st->US[idx3(st, x + N18[q][0], y + N18[q][1], z + N18[q][2])];
+            const real v = field3(st, st->US, x + N18[q][0], y + N18[q][1], z + N18[q][2], 0.0);
             for (int a2 = 0; a2 < 3; ++a2) gu[a2] += WN18[q] * N18[q][a2] * v;
           }
           double dot = 0;

@@ -6,6 +6,7 @@ cases and the reduction to the 2-D stencil."""
 import math
 
 import numpy as np
+import pytest
 
 import oracle
 from test_oracle_pins import _tanh_width
@@ -301,3 +302,74 @@ def test_3d_rotated_grain_front_widths():
     assert math.isclose(w_xx, math.sqrt(2) * W0 * (1 + eps), rel_tol=0.02)
     assert math.isclose(w_xx / w_z, (1 + eps) / (1 - eps), rel_tol=0.01)
     assert abs(w_xy / w_z - 1) < 1e-9        # the same crystal direction, two rotations
+
+
+# ---------------------------------------------------------------------------
+# non-periodic sides of the melt step (reading R35: on D3Q7 a symmetric side
+# and a wall are both the half-way bounce-back; a far-field side the
+# anti-bounce-back to psi = -1, C = 1, theta = theta0; stencil ghosts mirror)
+# ---------------------------------------------------------------------------
+def _mirror_fields(n_small, ny, nz, seed_x, thermal):
+    """Fields on an n_small-wide box and on the 2 n_small periodic box made of it
+    and its mirror image."""
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:2 * n_small].astype(float)
+    xs = np.where(x < n_small, x, 2 * n_small - 1 - x)
+    r = np.sqrt((xs - seed_x) ** 2 + (y - ny / 2) ** 2 + (z - nz / 3) ** 2)
+    psi = np.tanh(math.sqrt(0.5) * (5.0 - r) / 4.0)
+    C = 1 - 0.85 * (1 + psi) / 2 + 0.02 * np.cos(2 * np.pi * y / ny)
+    th = -0.55 + 0.03 * np.sin(2 * np.pi * z / nz) if thermal else None
+    return psi, C, th
+
+
+@pytest.mark.parametrize("side,thermal", [(1, False), (2, False), (1, True)])
+def test_3d_symmetric_sides_are_mirror_planes(side, thermal):
+    """A box with symmetric (or wall) sides in x evolves exactly as the left
+    half of the periodic box twice as wide that holds the box and its mirror
+    image (both side types act on D3Q7 as the half-way bounce-back)."""
+    n, ny, nz = 12, 10, 8
+    psi, C, th = _mirror_fields(n, ny, nz, 3.5, thermal)
+    params = dict(P3, **(dict(thermal=1, Le=2.0, theta0=-0.55) if thermal else {}))
+    big = oracle.Oracle3D(2 * n, ny, nz, params)
+    big.init_fields(psi, C, th)
+    small = oracle.Oracle3D(n, ny, nz, params)
+    small.set_bc([side, side, 0, 0, 0, 0])
+    small.init_fields(psi[:, :, :n], C[:, :, :n], None if th is None else th[:, :, :n])
+    big.step(60)
+    small.step(60)
+    fb, fs = big.fields(), small.fields()
+    for k in ("psi", "C", "U") + (("theta",) if thermal else ()):
+        half = fb[k][:, :, :n]
+        assert np.abs(fs[k] - half).max() <= 1e-12 * max(np.abs(half).max(), 1e-3), k
+        assert np.abs(fb[k][:, :, n:] - half[:, :, ::-1]).max() <= 1e-12 * max(np.abs(half).max(), 1e-3)
+
+
+def test_3d_walls_conserve_solute_and_enthalpy():
+    """Walls on all six sides: no flux leaves, so sum C and sum rho H stay
+    constant to rounding while a seed grows against a side."""
+    n = 20
+    o = oracle.Oracle3D(n, n, n, dict(P3, thermal=1, Le=2.0, theta0=-0.55))
+    o.set_bc([2, 2, 2, 2, 2, 2])
+    o.init_spec([(3.0, 10.0, 10.0)], 5.0)
+    c0, t0 = o.fields()["C"].sum(), o.thermal_totals()
+    o.step(150)
+    assert abs(o.fields()["C"].sum() / c0 - 1) < 1e-13
+    assert abs(o.thermal_totals()["sum_e"] / t0["sum_e"] - 1) < 1e-13
+    assert o.fields()["psi"].max() > 0.5
+
+
+def test_3d_far_field_sides_are_half_way_dirichlet():
+    """Far-field sides at x = -1/2 and x = nx - 1/2 hold C = 1: in a liquid
+    (psi = -1) a uniform deficit 1 - C relaxes as the slowest Dirichlet mode,
+    decaying at D (pi / nx)^2 per step (D_C = D in the liquid)."""
+    nx, D = 32, 0.1
+    one = np.ones((4, 4, nx))
+    o = oracle.Oracle3D(nx, 4, 4, dict(P3, D=D))
+    o.set_bc([3, 3, 0, 0, 0, 0])
+    o.init_fields(-one, 0.8 * one)
+    o.step(1000)                      # the higher odd modes have died out
+    a0 = 1 - o.fields()["C"][0, 0, nx // 2]
+    o.step(1000)
+    a1 = 1 - o.fields()["C"][0, 0, nx // 2]
+    rate = math.log(a0 / a1) / 1000
+    assert math.isclose(rate, D * (math.pi / nx) ** 2, rel_tol=0.01)
+    assert np.abs(o.fields()["psi"] + 1).max() < 1e-12
