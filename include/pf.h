@@ -409,6 +409,15 @@ pf_status pf3_set_temperature(pf3_handle *h, const double *theta, size_t n);
  * time between steps.  Synchronises.  Errors: BAD_ARG (NULL, non-finite or zero
  * quaternion), OOM, CUDA. */
 pf_status pf3_set_orientation(pf3_handle *h, const double *seeds7, int n_seeds);
+/* Side types of the six faces x-, x+, y-, y+, z-, z+: 0 periodic, 1 symmetric,
+ * 2 wall, 3 far field (psi = -1, C = 1, theta = theta0), each half-way between
+ * the last site and its ghost.  On the D3Q7 lattices a symmetric side and a
+ * wall are both the half-way bounce-back; a far-field side is the
+ * anti-bounce-back to the far values; the stencil ghosts mirror the last site
+ * (2 X_far - X across a far-field side).  Opposite sides are both periodic or
+ * both not.  Before initialising (seeds then use plain distances along bounded
+ * axes).  Errors: BAD_ARG, STATE (already initialised). */
+pf_status pf3_set_boundaries(pf3_handle *h, const int bc[6]);
 /* Planes per tile of the z-march (default 16). */
 pf_status pf3_set_chunk(pf3_handle *h, int chunk);
 /* Advance n_steps (enqueued; errors of the launch are reported).

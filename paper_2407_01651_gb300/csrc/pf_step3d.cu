@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdint>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/pf.h"
@@ -32,6 +33,7 @@ constexpr int NSTATE3 = 23, NSTATE3_TH = 30;      // raw FP64 state planes
 template <typename R>
 struct Coef3 {
   R eps, ge2, gat2, four_bpsi, lam, theta, Mcinf, inv_tau0, c4W0sq_tau0, k, inv_omk, D, aW0;
+  R th0;                // theta at a far-field side
   // thermal mode: rho_l c_p and its inverse, latent / 2, 1/Le, W0^2, 1 - s_T
   R rcp, irc, halfL, iLe, W0sq, omsth;
 };
@@ -45,6 +47,8 @@ struct Args3 {
   R* fields;            // psi, C, U (and theta) planes, or nullptr
   const int* grain;     // ROT: grain index per site
   const R* rot;         // ROT: 9 entries (row-major R) per grain
+  int bc[6];            // BC: side types x-, x+, y-, y+, z-, z+ (0 periodic, 1 symmetric,
+                        // 2 wall, 3 far field)
   unsigned long long ps;
   int nx, ny, nz, chunk;
   int tiles_x, tiles_y, tiles_z;
@@ -57,9 +61,34 @@ __device__ __forceinline__ unsigned long long src7(const Args3<S, R>& a, int x, 
          wrap1(x - cx7(i), a.nx);   // x, y in range: one step wraps
 }
 
+// BC: pull source of direction i at (x, y, z): a source beyond a non-periodic
+// side is the site's own opposite population, bounced (symmetric side or wall:
+// mode 1) or anti-bounced to the far-field value (mode 2); D3Q7 crosses at most
+// one side.
+__device__ __forceinline__ constexpr int opp7(int i) { return i == 0 ? 0 : (i % 2 ? i + 1 : i - 1); }
+template <typename S, typename R, bool BC>
+__device__ __forceinline__ int pull7(const Args3<S, R>& a, int x, int y, int z, int i,
+                                     unsigned long long& src, int& q) {
+  if constexpr (BC) {
+    const int X = x - cx7(i), Y = y - cy7(i), Z = z - cz7(i);
+    int t = 0;
+    if (X < 0) t = a.bc[0]; else if (X >= a.nx) t = a.bc[1];
+    else if (Y < 0) t = a.bc[2]; else if (Y >= a.ny) t = a.bc[3];
+    else if (Z < 0) t = a.bc[4]; else if (Z >= a.nz) t = a.bc[5];
+    if (t) {
+      src = ((unsigned long long)z * a.ny + y) * a.nx + x;
+      q = opp7(i);
+      return t == 3 ? 2 : 1;
+    }
+  }
+  src = src7(a, x, y, z, i);
+  q = i;
+  return 0;
+}
+
 // Streamed g at (x, y, z) (time stretch g = g_pre + r_src (g_post,src - g_pre))
 // and psi, psi_o (compensated sums).
-template <typename S, typename R>
+template <typename S, typename R, bool BC>
 __device__ __forceinline__ void stream_g(const Args3<S, R>& a, int x, int y, int z, R g[7],
                                          R& psi, R& psio) {
   const unsigned long long own = ((unsigned long long)z * a.ny + y) * a.nx + x;
@@ -67,9 +96,12 @@ __device__ __forceinline__ void stream_g(const Args3<S, R>& a, int x, int y, int
   R po = R(0);
 #pragma unroll
   for (int i = 0; i < 7; ++i) {
-    const unsigned long long src = src7(a, x, y, z, i);
+    unsigned long long src;
+    int q;
+    const int mode = pull7<S, R, BC>(a, x, y, z, i, src, q);
     const R gold = ld<R>(pl(a.in, G_PRE + i, a.ps), own);
-    const R gpo = ld<R>(pl(a.in, G_POST + i, a.ps), src);
+    R gpo = ld<R>(pl(a.in, G_POST + q, a.ps), src);
+    if (BC && mode == 2) gpo = -gpo + R(2) * w7<R>(i) * R(-1);    // psi_far = -1
     const R rr = ld<R>(pl(a.ain, A3_RR, a.ps), src);
     g[i] = gold + (gpo - gold) * rr;
     sg.add(g[i]);
@@ -79,11 +111,33 @@ __device__ __forceinline__ void stream_g(const Args3<S, R>& a, int x, int y, int
   psio = po;
 }
 
-// Streamed populations of one D3Q7 lattice (plane base P) at (x, y, z).
-template <typename S, typename R>
-__device__ __forceinline__ void stream7(const Args3<S, R>& a, int P, int x, int y, int z, R f[7]) {
+// Streamed populations of one D3Q7 lattice (plane base P) at (x, y, z); far:
+// the lattice's far-field value (BC).
+template <typename S, typename R, bool BC>
+__device__ __forceinline__ void stream7(const Args3<S, R>& a, int P, int x, int y, int z, R f[7],
+                                        R far) {
 #pragma unroll
-  for (int i = 0; i < 7; ++i) f[i] = ld<R>(pl(a.in, P + i, a.ps), src7(a, x, y, z, i));
+  for (int i = 0; i < 7; ++i) {
+    unsigned long long src;
+    int q;
+    const int mode = pull7<S, R, BC>(a, x, y, z, i, src, q);
+    f[i] = ld<R>(pl(a.in, P + q, a.ps), src);
+    if (BC && mode == 2) f[i] = -f[i] + R(2) * w7<R>(i) * far;
+  }
+}
+
+// BC: lattice coordinate of a ring column or plane c of an axis of n sites with
+// sides t0 (below) and t1 (above): in range as is, periodic sides wrap, across
+// a non-periodic side the mirror site (clamped: columns further out are never
+// read); far marks a far-field ghost, whose value is 2 X_far - X.
+__device__ __forceinline__ int ghost_coord(int c, int n, int t0, int t1, bool& far) {
+  far = false;
+  if (c >= 0 && c < n) return c;
+  const int t = c < 0 ? t0 : t1;
+  if (t == 0) return wrapm(c, n);
+  far = t == 3 && (c == -1 || c == n);
+  const int m = c < 0 ? -1 - c : 2 * n - 1 - c;
+  return m < 0 ? 0 : (m >= n ? n - 1 : m);
 }
 
 template <typename R>
@@ -107,7 +161,9 @@ __device__ __forceinline__ R supersat3(const Coef3<R>& c, R C, R psi) {
 // + N) with grad F = M c_inf (1-k) grad U; U is kept in a second ring.
 // ROT: grain orientations (the site's grain rotation R; the anisotropy is
 // evaluated on g' = R^T grad psi and N = R N'(g')).
-template <typename S, typename R, bool TH, bool ROT>
+// BC: non-periodic sides (pull7, ghost_coord): ghost ring columns and planes
+// take the mirror site's psi (and U), mapped to 2 X_far - X across a far side.
+template <typename S, typename R, bool TH, bool ROT, bool BC>
 __global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R> a) {
   __shared__ R ring[4][HY][HX];
   __shared__ R uring[TH ? 4 : 1][HY][HX];
@@ -131,22 +187,49 @@ __global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R> a) {
     const int tx = tile % a.tiles_x, ty = (tile / a.tiles_x) % a.tiles_y;
     const int tz = tile / (a.tiles_x * a.tiles_y);
     const int za = tz * a.chunk, zb = min(za + a.chunk, a.nz);
-    const int x = wrapm(tx * TX + hx - 1, a.nx), y = wrapm(ty * TY + hy - 1, a.ny);
+    bool fx = false, fy = false;
+    int x, y;
+    if constexpr (BC) {
+      x = ghost_coord(tx * TX + hx - 1, a.nx, a.bc[0], a.bc[1], fx);
+      y = ghost_coord(ty * TY + hy - 1, a.ny, a.bc[2], a.bc[3], fy);
+    } else {
+      x = wrapm(tx * TX + hx - 1, a.nx);
+      y = wrapm(ty * TY + hy - 1, a.ny);
+    }
     const bool mine = interior && tx * TX + hx - 1 < a.nx && ty * TY + hy - 1 < a.ny;
+    // ghost maps of the ring values: 2 X_far - X per far-field side crossed
+    // (psi_far = -1, U_far = 0)
+    auto gpsi = [&](R v, bool fz) {
+      if constexpr (BC) {
+        if (fx) v = R(-2) - v;
+        if (fy) v = R(-2) - v;
+        if (fz) v = R(-2) - v;
+      }
+      return v;
+    };
+    auto gU = [&](R v, bool fz) {
+      if constexpr (BC) {
+        if (fx) v = -v;
+        if (fy) v = -v;
+        if (fz) v = -v;
+      }
+      return v;
+    };
     R gC[7], gL[7], poC = R(0), poL = R(0);
     R sC[7], sL[7], CC = R(0), CL = R(0);   // TH: streamed s and C carried a plane ahead
     // ring planes za-1 and za
     for (int k = 0; k < 2; ++k) {
       if (active) {
-        const int z = wrap1(za - 1 + k, a.nz);
+        bool fz = false;
+        const int z = BC ? ghost_coord(za - 1 + k, a.nz, a.bc[4], a.bc[5], fz) : wrap1(za - 1 + k, a.nz);
         R g[7], psi, po;
-        stream_g(a, x, y, z, g, psi, po);
-        ring[(za - 1 + k) & 3][hy][hx] = psi;
+        stream_g<S, R, BC>(a, x, y, z, g, psi, po);
+        ring[(za - 1 + k) & 3][hy][hx] = gpsi(psi, fz);
         if constexpr (TH) {
           R sv[7];
-          stream7(a, S_POP, x, y, z, sv);
+          stream7<S, R, BC>(a, S_POP, x, y, z, sv, R(1));
           const R C = sum7(sv);
-          uring[(za - 1 + k) & 3][hy][hx] = supersat3(a.c, C, psi);
+          uring[(za - 1 + k) & 3][hy][hx] = gU(supersat3(a.c, C, psi), fz);
           if (k == 1) {
 #pragma unroll
             for (int i = 0; i < 7; ++i) sC[i] = sv[i];
@@ -169,9 +252,9 @@ __global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R> a) {
         if constexpr (TH) {
 #pragma unroll
           for (int i = 0; i < 7; ++i) sv[i] = sC[i];
-          stream7(a, E_POP, x, y, z, ev);
+          stream7<S, R, BC>(a, E_POP, x, y, z, ev, a.c.th0);
         } else {
-          stream7(a, S_POP, x, y, z, sv);
+          stream7<S, R, BC>(a, S_POP, x, y, z, sv, R(1));
         }
         Qo = ld<R>(pl(a.ain, A3_QO, a.ps), site);
         // warm L2 with this column's populations two planes ahead
@@ -185,13 +268,14 @@ __global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R> a) {
       }
       if (active) {
         R psi;
-        const int zn = wrap1(z + 1, a.nz);
-        stream_g(a, x, y, zn, gL, psi, poL);
-        ring[(z + 1) & 3][hy][hx] = psi;
+        bool fz = false;
+        const int zn = BC ? ghost_coord(z + 1, a.nz, a.bc[4], a.bc[5], fz) : wrap1(z + 1, a.nz);
+        stream_g<S, R, BC>(a, x, y, zn, gL, psi, poL);
+        ring[(z + 1) & 3][hy][hx] = gpsi(psi, fz);
         if constexpr (TH) {
-          stream7(a, S_POP, x, y, zn, sL);
+          stream7<S, R, BC>(a, S_POP, x, y, zn, sL, R(1));
           CL = sum7(sL);
-          uring[(z + 1) & 3][hy][hx] = supersat3(a.c, CL, psi);
+          uring[(z + 1) & 3][hy][hx] = gU(supersat3(a.c, CL, psi), fz);
         }
       }
       __syncthreads();
@@ -373,6 +457,8 @@ __device__ void write_eq3(const Args3<S, R>& a, unsigned long long site, R psi, 
 template <typename S, typename R, bool TH>
 __global__ void k_init3(Args3<S, R> a, const double* seeds, int n_seeds, double R_s, double sq2b,
                         double W0, double k, double theta0) {
+  // minimum image along periodic axes, plain distance along bounded ones
+  auto off = [&](double d, double L, int t) { return t == 0 ? min_image1(d, L) : d; };
   const unsigned long long n = (unsigned long long)a.nx * a.ny * a.nz;
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
        i += (unsigned long long)gridDim.x * blockDim.x) {
@@ -380,8 +466,8 @@ __global__ void k_init3(Args3<S, R> a, const double* seeds, int n_seeds, double 
     double psi = -1.0;
     const double far = R_s + 30.0 * W0 / sq2b;
     for (int s = 0; s < n_seeds; ++s) {
-      const double dx = min_image1(x - seeds[3 * s], a.nx), dy = min_image1(y - seeds[3 * s + 1], a.ny);
-      const double dz = min_image1(z - seeds[3 * s + 2], a.nz);
+      const double dx = off(x - seeds[3 * s], a.nx, a.bc[0]), dy = off(y - seeds[3 * s + 1], a.ny, a.bc[2]);
+      const double dz = off(z - seeds[3 * s + 2], a.nz, a.bc[4]);
       const double r2 = dx * dx + dy * dy + dz * dz;
       const double v = r2 > far * far ? -1.0 : tanh(sq2b * (R_s - sqrt(r2)) / W0);
       if (s == 0 || v > psi) psi = v;
@@ -501,6 +587,8 @@ struct pf3_handle {
   int nx = 0, ny = 0, nz = 0, chunk = 16;
   int thermal = 0, npop = NPOP3, nfields = 3, nstate = NSTATE3;
   int rotated = 0;                // grain orientations set
+  int bc[6] = {0, 0, 0, 0, 0, 0}; // side types x-, x+, y-, y+, z-, z+
+  int any_bc = 0;
   int* grain = nullptr;           // grain index per site
   void* rot = nullptr;            // 9 x n_grains rotation entries (compute type)
   unsigned long long n = 0;
@@ -545,6 +633,7 @@ static Coef3<R> coef3(const pf_params& p) {
   c.inv_omk = (R)(1.0 / (1.0 - p.k));
   c.D = (R)p.D;
   c.aW0 = (R)(p.W0 / (2.0 * std::sqrt(2.0)));
+  c.th0 = (R)p.theta0;
   if (p.thermal) {
     const double rcp = p.rho_l * p.cp;
     const double kT = p.Le * p.D * rcp;                 // k_T = alpha rho_l c_p, alpha = Le D
@@ -568,6 +657,7 @@ static Args3<S, R> args3(const pf3_handle* h, bool fields) {
   a.fields = fields ? (R*)h->fields : nullptr;
   a.grain = h->grain;
   a.rot = (const R*)h->rot;
+  for (int k = 0; k < 6; ++k) a.bc[k] = h->bc[k];
   a.ps = h->n;
   a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.chunk = h->chunk;
   a.tiles_x = (h->nx + TX - 1) / TX;
@@ -798,6 +888,24 @@ extern "C" pf_status pf3_set_orientation(pf3_handle* h, const double* seeds7, in
   return PF_OK;
 }
 
+extern "C" pf_status pf3_set_boundaries(pf3_handle* h, const int bc[6]) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (!bc) return fail3(h, PF_ERR_BAD_ARG, "NULL bc");
+  for (int k = 0; k < 6; ++k)
+    if (bc[k] < 0 || bc[k] > 3)
+      return fail3(h, PF_ERR_BAD_ARG, "side types are 0 (periodic) .. 3 (far field)");
+  for (int a = 0; a < 3; ++a)
+    if ((bc[2 * a] == 0) != (bc[2 * a + 1] == 0))
+      return fail3(h, PF_ERR_BAD_ARG, "a periodic side needs a periodic opposite side");
+  if (h->inited) return fail3(h, PF_ERR_STATE, "set the sides before initialising");
+  h->any_bc = 0;
+  for (int k = 0; k < 6; ++k) {
+    h->bc[k] = bc[k];
+    if (bc[k]) h->any_bc = 1;
+  }
+  return PF_OK;
+}
+
 extern "C" pf_status pf3_set_chunk(pf3_handle* h, int chunk) {
   if (!h) return PF_ERR_BAD_ARG;
   if (chunk < 1 || chunk > 4096) return fail3(h, PF_ERR_BAD_ARG, "chunk must be in [1, 4096]");
@@ -815,13 +923,18 @@ extern "C" pf_status pf3_step(pf3_handle* h, int n_steps) {
     for (int t = 0; t < n_steps; ++t) {
       const Args3<S, R> a = args3<S, R>(h, t == n_steps - 1);
       const int tiles = a.tiles_x * a.tiles_y * a.tiles_z;
-      if (h->rotated) {
-        if (h->thermal) k_step3d<S, R, true, true><<<tiles, THREADS, 0, h->stream>>>(a);
-        else k_step3d<S, R, false, true><<<tiles, THREADS, 0, h->stream>>>(a);
-      } else {
-        if (h->thermal) k_step3d<S, R, true, false><<<tiles, THREADS, 0, h->stream>>>(a);
-        else k_step3d<S, R, false, false><<<tiles, THREADS, 0, h->stream>>>(a);
-      }
+      auto go = [&](auto bcv) {
+        constexpr bool BC = decltype(bcv)::value;
+        if (h->rotated) {
+          if (h->thermal) k_step3d<S, R, true, true, BC><<<tiles, THREADS, 0, h->stream>>>(a);
+          else k_step3d<S, R, false, true, BC><<<tiles, THREADS, 0, h->stream>>>(a);
+        } else {
+          if (h->thermal) k_step3d<S, R, true, false, BC><<<tiles, THREADS, 0, h->stream>>>(a);
+          else k_step3d<S, R, false, false, BC><<<tiles, THREADS, 0, h->stream>>>(a);
+        }
+      };
+      if (h->any_bc) go(std::true_type{});
+      else go(std::false_type{});
       PF3_CUDA(h, cudaGetLastError());
       h->cur ^= 1;
       h->steps++;

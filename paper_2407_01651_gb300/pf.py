@@ -125,6 +125,7 @@ def lib() -> ctypes.CDLL:
     L.pf3_reduce.argtypes = [P, D]
     L.pf3_set_temperature.argtypes = [P, D, S]
     L.pf3_set_orientation.argtypes = [P, D, I]
+    L.pf3_set_boundaries.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
     L.pf3_reduce_thermal.argtypes = [P, D]
     L.pf3_field_planes.argtypes = [P]
     L.pf3_state_planes.argtypes = [P]
@@ -162,6 +163,7 @@ def lib() -> ctypes.CDLL:
                  "pf_set_boundaries", "pf3_create", "pf3_init_seeds", "pf3_set_fields",
                  "pf3_set_chunk", "pf3_step", "pf3_get_fields", "pf3_get_state", "pf3_reduce",
                  "pf3_destroy", "pf3_set_temperature", "pf3_reduce_thermal", "pf3_set_orientation",
+                 "pf3_set_boundaries",
                  "pf3f_create",
                  "pf3f_init_spec", "pf3f_set_fields", "pf3f_set_rho_bar", "pf3f_set_chunk",
                  "pf3f_step", "pf3f_get_fields", "pf3f_get_state", "pf3f_reduce", "pf3f_destroy",
@@ -456,6 +458,12 @@ class Simulation3D:
         a = np.ascontiguousarray(np.asarray(psi, dtype=np.float64).reshape(self.shape))
         b = np.ascontiguousarray(np.asarray(C, dtype=np.float64).reshape(self.shape))
         _check3(lib().pf3_set_fields(self.h, _dp(a), _dp(b), self.n), self.h)
+
+    def set_boundaries(self, bc) -> None:
+        """Side types x-, x+, y-, y+, z-, z+ (BC_PERIODIC, BC_SYMMETRIC, BC_WALL,
+        BC_FARFIELD), before initialising."""
+        arr = (ctypes.c_int * 6)(*[int(b) for b in bc])
+        _check3(lib().pf3_set_boundaries(self.h, arr), self.h)
 
     def set_orientation(self, seeds7) -> None:
         """Grain orientations: n x (x, y, z, qw, qx, qy, qz); each site takes the

@@ -336,3 +336,65 @@ def test_3d_identity_orientation_is_the_aligned_grain():
             assert np.array_equal(f[k], out[0][k]), k
     with pytest.raises(pf.PFError):
         sim.set_orientation([(1.0, 1.0, 1.0, 0.0, 0.0, 0.0, 0.0)])      # zero quaternion
+
+
+# ---------------------------------------------------------------------------
+# non-periodic sides (BC template)
+# ---------------------------------------------------------------------------
+SIDES = [(1, 1, 2, 2, 3, 3), (3, 3, 0, 0, 1, 1), (2, 2, 3, 3, 0, 0)]
+
+
+def pair_bc(shape, sides, precision, params, seeds=SEEDS, R_s=5.0):
+    nx, ny, nz = shape
+    o = oracle.Oracle3D(nx, ny, nz, params)
+    o.set_bc(sides)
+    o.init_spec(seeds, R_s)
+    sim = pf.Simulation3D(shape, dict(wl.BASE_PARAMS, **params), precision)
+    sim.set_boundaries(sides)
+    sim.init_seeds(seeds, R_s)
+    return o, sim
+
+
+@pytest.mark.parametrize("sides", SIDES)
+@pytest.mark.parametrize("thermal", [False, True])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+def test_3d_sides_match_oracle(sides, thermal, precision, tol):
+    params = T3 if thermal else P3
+    o, sim = pair_bc(RAGGED, sides, precision, params)
+    (compare_t if thermal else compare)(o, sim, tol)
+    sim.set_chunk(5)
+    for _ in range(3):
+        o.step(1)
+        sim.step(1)
+        (compare_t if thermal else compare)(o, sim, tol)
+
+
+def test_3d_sides_fp64_many_steps_with_rotated_grains():
+    """Walls, symmetric planes and a far-field pair with rotated grains and the
+    temperature lattice: FP64 within 1e-9 of the oracle over 120 steps; with
+    walls and symmetric planes only, sum C and sum rho H are conserved."""
+    n = 24
+    seeds7 = [(4.0, 12.0, 12.0, 0.9, 0.2, -0.3, 0.1), (18.0, 6.0, 20.0, 0.3, 0.5, 0.2, -0.8)]
+    for sides, conserving in (((1, 1, 2, 2, 1, 1), True), ((2, 2, 1, 1, 3, 3), False)):
+        o, sim = pair_bc((n, n, n), sides, "fp64", T3, [s[:3] for s in seeds7], 5.0)
+        o.set_orientation(seeds7)
+        sim.set_orientation(seeds7)
+        t0, c0 = sim.reduce_thermal(), sim.reduce()["sum_C"]
+        o.step(120)
+        sim.step(120)
+        compare_t(o, sim, 1e-9)
+        if conserving:
+            assert abs(sim.reduce_thermal()["sum_e"] / t0["sum_e"] - 1) < 1e-12
+            assert abs(sim.reduce()["sum_C"] / c0 - 1) < 1e-12
+
+
+def test_3d_sides_configuration_errors():
+    sim = pf.Simulation3D((8, 8, 8), wl.BASE_PARAMS, "fp32")
+    with pytest.raises(pf.PFError):
+        sim.set_boundaries((0, 1, 0, 0, 0, 0))      # periodic opposite a symmetric side
+    with pytest.raises(pf.PFError):
+        sim.set_boundaries((4, 4, 0, 0, 0, 0))      # no inlet in 3-D
+    sim.init_seeds([(4, 4, 4)], 2.0)
+    with pytest.raises(pf.PFError) as e:
+        sim.set_boundaries((1, 1, 0, 0, 0, 0))      # after initialisation
+    assert e.value.code == pf.PF_ERR_STATE
