@@ -493,6 +493,7 @@ def _l3f() -> ctypes.CDLL:
             lib.or3f_set_orientation.argtypes = [P, D, I]
             lib.or3f_set_orientation.restype = I
             lib.or3f_set_temperature.argtypes = [P, D]
+            lib.or3f_set_bc.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
             lib.or3f_thermal_totals.argtypes = [P, D]
             lib.or3f_state_planes.argtypes = [P]
             lib.or3f_state_planes.restype = I
@@ -525,6 +526,12 @@ class Oracle3F:
 
     def set_rho_bar(self, rho_bar: float) -> None:
         self.lib.or3f_set_rho_bar(self.h, float(rho_bar))
+
+    def set_bc(self, bc) -> None:
+        """Side types x-, x+, y-, y+, z-, z+: 0 periodic, 1 symmetric, 2 wall,
+        3 far field."""
+        arr = (ctypes.c_int * 6)(*[int(b) for b in bc])
+        self.lib.or3f_set_bc(self.h, arr)
 
     @property
     def rho_bar(self) -> float:

@@ -729,6 +729,7 @@ typedef struct {
   real *fld[NFLD3F];
   real *block;
   double *rot;     /* grain orientation per site (9 per site), or NULL */
+  int bc[6];       /* side types x-, x+, y-, y+, z-, z+ (B3_*) */
 } o3fstate;
 
 static int thermalf(const o3fstate *st) { return st->par[F3_THERMAL] != 0.0; }
@@ -807,6 +808,77 @@ double or3f_get_rho_bar(const o3fstate *st) { return st->rho_bar; }
 
 static inline int idx3f(const o3fstate *st, int x, int y, int z) {
   return (wrap3(z, st->nz) * st->ny + wrap3(y, st->ny)) * st->nx + wrap3(x, st->nx);
+}
+
+void or3f_set_bc(o3fstate *st, const int *bc) {
+  for (int k = 0; k < 6; ++k) st->bc[k] = bc[k];
+}
+
+/* D3Q19 direction with the component along axis a reversed, and the opposite */
+static int mirror19(int i, int a) {
+  int c[3] = {C19[i][0], C19[i][1], C19[i][2]};
+  c[a] = -c[a];
+  for (int j = 0; j < 19; ++j)
+    if (C19[j][0] == c[0] && C19[j][1] == c[1] && C19[j][2] == c[2]) return j;
+  return i;
+}
+static int opp19(int i) { return i == 0 ? 0 : (i % 2 ? i + 1 : i - 1); }
+
+/* Pull source of a population of direction c = (cx, cy, cz) at (x, y, z) with
+ * the sides of the 2-D reading R31 in 3-D (R36): periodic wrap; a symmetric
+ * side reflects the source site and the direction (mirror(a)); a wall or a
+ * far-field side returns the site's own opposite population (mode 1 wall, 2 far
+ * field); a bounce wins over a reflection where both are crossed.  Returns the
+ * mode; *q is the direction read (in the lattice's own numbering via map). */
+static int pull_side(const o3fstate *st, int x, int y, int z, const int c[3], int *src, int *refl) {
+  int X[3] = {x - c[0], y - c[1], z - c[2]};
+  const int L[3] = {st->nx, st->ny, st->nz};
+  int mode = 0;
+  *refl = 0;
+  for (int a = 0; a < 3; ++a)
+    if (X[a] < 0 || X[a] >= L[a]) {
+      const int t = st->bc[2 * a + (X[a] < 0 ? 0 : 1)];
+      if (t == B3_PERIODIC) continue;
+      if (t == B3_SYMMETRIC) {
+        X[a] = X[a] < 0 ? -1 - X[a] : 2 * L[a] - 1 - X[a];
+        *refl |= 1 << a;
+      } else {
+        const int m = t == B3_FARFIELD ? 2 : 1;
+        if (m > mode) mode = m;
+      }
+    }
+  *src = mode ? idx3f(st, x, y, z) : idx3f(st, X[0], X[1], X[2]);
+  return mode;
+}
+
+/* Field value one site beyond the lattice at most: the mirror site's value
+ * across a non-periodic side, mapped per side (kind 0 phi: unchanged; 1 psi:
+ * 2 psi_far - psi at a far side; 2 U: -U at a far side; 3..5 the velocity
+ * component a = kind - 3: its sign flipped at a symmetric side if normal to it,
+ * flipped at a wall or far-field side always); axes mapped in the order x, y, z. */
+static real field3f(const o3fstate *st, const real *X, int x, int y, int z, int kind) {
+  int c[3] = {x, y, z};
+  const int L[3] = {st->nx, st->ny, st->nz};
+  int t3[3] = {0, 0, 0};
+  for (int a = 0; a < 3; ++a)
+    if (c[a] < 0 || c[a] >= L[a]) {
+      const int t = st->bc[2 * a + (c[a] < 0 ? 0 : 1)];
+      if (t == B3_PERIODIC) continue;
+      c[a] = c[a] < 0 ? -1 - c[a] : 2 * L[a] - 1 - c[a];
+      t3[a] = t;
+    }
+  real v = X[idx3f(st, c[0], c[1], c[2])];
+  for (int a = 0; a < 3; ++a) {
+    const int t = t3[a];
+    if (!t) continue;
+    if (kind == 1 && t == B3_FARFIELD) v = -2.0 - v;
+    else if (kind == 2 && t == B3_FARFIELD) v = -v;
+    else if (kind >= 3) {
+      if (t == B3_SYMMETRIC) { if (kind - 3 == a) v = -v; }
+      else v = -v;
+    }
+  }
+  return v;
 }
 
 static double supersatf(const o3fstate *st, double C, double psi) {
@@ -969,7 +1041,8 @@ void or3f_fields_from_spec(const o3fstate *st, const double *seeds, int n_seeds,
         for (int s = 0; s < n_seeds; ++s) {
           double r2 = 0;
           for (int a = 0; a < 3; ++a) {
-            const double d = min_image3(X[a] - seeds[3 * s + a], L[a]);
+            const double d = st->bc[2 * a] == B3_PERIODIC ? min_image3(X[a] - seeds[3 * s + a], L[a])
+                                                          : X[a] - seeds[3 * s + a];
             r2 += d * d;
           }
           const double v = tanh(sb * (R_s - sqrt(r2)) / p[F3_W0]);
@@ -978,7 +1051,8 @@ void or3f_fields_from_spec(const o3fstate *st, const double *seeds, int n_seeds,
         for (int b = 0; b < n_bub; ++b) {
           double r2 = 0;
           for (int a = 0; a < 3; ++a) {
-            const double d = min_image3(X[a] - bubbles[4 * b + a], L[a]);
+            const double d = st->bc[2 * a] == B3_PERIODIC ? min_image3(X[a] - bubbles[4 * b + a], L[a])
+                                                          : X[a] - bubbles[4 * b + a];
             r2 += d * d;
           }
           const double v = 0.5 + 0.5 * tanh(sp * (sqrt(r2) - bubbles[4 * b + 3]) / (2.0 * p[F3_W_PHI]));
@@ -1027,18 +1101,19 @@ int or3f_init_spec(o3fstate *st, const double *seeds, int n_seeds, double R_s,
 
 /* isotropic gradient and Laplacian with the D3Q19 weights (reading R5 in 3-D):
  * grad X = (1/c_s^2) sum w c X(x+c), lap X = (2/c_s^2) sum w [X(x+c) - X(x)] */
-static void grad19(const o3fstate *st, const real *X, int x, int y, int z, double g[3]) {
+static void grad19(const o3fstate *st, const real *X, int kind, int x, int y, int z, double g[3]) {
   g[0] = g[1] = g[2] = 0.0;
   for (int i = 1; i < 19; ++i) {
-    const double v = X[idx3f(st, x + C19[i][0], y + C19[i][1], z + C19[i][2])];
+    const double v = field3f(st, X, x + C19[i][0], y + C19[i][1], z + C19[i][2], kind);
     for (int a = 0; a < 3; ++a) g[a] += W19[i] * C19[i][a] * v;
   }
   for (int a = 0; a < 3; ++a) g[a] /= CS2_19;
 }
-static double lap19(const o3fstate *st, const real *X, int x, int y, int z) {
+static double lap19(const o3fstate *st, const real *X, int kind, int x, int y, int z) {
   const double c = X[idx3f(st, x, y, z)];
   double a = 0.0;
-  for (int i = 1; i < 19; ++i) a += W19[i] * (X[idx3f(st, x + C19[i][0], y + C19[i][1], z + C19[i][2])] - c);
+  for (int i = 1; i < 19; ++i)
+    a += W19[i] * (field3f(st, X, x + C19[i][0], y + C19[i][1], z + C19[i][2], kind) - c);
   return 2.0 * a / CS2_19;
 }
 
@@ -1053,16 +1128,30 @@ static void step3f(o3fstate *st) {
         const int id = (z * ny + y) * nx + x;
         real phi = 0, psi = 0, psio = 0, C = 0;
         for (int i = 0; i < 19; ++i) {
-          const int src = idx3f(st, x - C19[i][0], y - C19[i][1], z - C19[i][2]);
-          st->fS[i][id] = st->f[i][src];
-          st->hS[i][id] = st->h[i][src];
+          /* NS and CAC: reflection at a symmetric side, the own opposite
+           * population (no slip, no flux) at a wall or far-field side */
+          int src, refl;
+          const int mode = pull_side(st, x, y, z, C19[i], &src, &refl);
+          int q = i;
+          if (mode) q = opp19(i);
+          else
+            for (int a2 = 0; a2 < 3; ++a2)
+              if (refl & (1 << a2)) q = mirror19(q, a2);
+          st->fS[i][id] = st->f[q][src];
+          st->hS[i][id] = st->h[q][src];
           phi += st->hS[i][id];
         }
         for (int i = 0; i < 7; ++i) {
-          const int src = idx3f(st, x - C7[i][0], y - C7[i][1], z - C7[i][2]);
+          /* D3Q7: reflection and bounce coincide (the own opposite population);
+           * a far-field side anti-bounces to psi = -1, C = 1 */
+          int src, refl;
+          const int mode = pull_side(st, x, y, z, C7[i], &src, &refl);
+          const int q = (mode || refl) ? (i == 0 ? 0 : (i % 2 ? i + 1 : i - 1)) : i;
+          if (refl) src = idx3f(st, x, y, z);
           const real gold = st->gpre[i][id];
-          st->gS[i][id] = gold + (st->gpost[i][src] - gold) * st->rr[src];
-          st->sS[i][id] = st->s[i][src];
+          const real gsrc = mode == 2 ? -st->gpost[q][src] + 2.0 * W7[i] * (-1.0) : st->gpost[q][src];
+          st->gS[i][id] = gold + (gsrc - gold) * st->rr[src];
+          st->sS[i][id] = mode == 2 ? -st->s[q][src] + 2.0 * W7[i] * 1.0 : st->s[q][src];
           psi += st->gS[i][id];
           psio += gold;
           C += st->sS[i][id];
@@ -1070,8 +1159,13 @@ static void step3f(o3fstate *st) {
         st->phiS[id] = phi; st->psiS[id] = psi; st->psiOld[id] = psio; st->CS[id] = C;
         if (thermalf(st)) {
           /* temperature populations (plain pull) and U, whose gradient gives grad F */
-          for (int i = 0; i < 7; ++i)
-            st->eS[i][id] = st->e[i][idx3f(st, x - C7[i][0], y - C7[i][1], z - C7[i][2])];
+          for (int i = 0; i < 7; ++i) {
+            int src, refl;
+            const int mode = pull_side(st, x, y, z, C7[i], &src, &refl);
+            const int q = (mode || refl) ? (i == 0 ? 0 : (i % 2 ? i + 1 : i - 1)) : i;
+            if (refl) src = idx3f(st, x, y, z);
+            st->eS[i][id] = mode == 2 ? -st->e[q][src] + 2.0 * W7[i] * p[F3_THETA0] : st->e[q][src];
+          }
           st->US[id] = supersatf(st, C, psi);
         }
       }
@@ -1095,10 +1189,10 @@ static void step3f(o3fstate *st) {
         const double vo[3] = {st->v_o[0][id], st->v_o[1][id], st->v_o[2][id]};
         /* stencils */
         double gp[3], gs[3], dv[3][3];   /* dv[a][b] = d_b v_o,a */
-        grad19(st, st->phiS, x, y, z, gp);
-        const double lphi = lap19(st, st->phiS, x, y, z);
-        grad19(st, st->psiS, x, y, z, gs);
-        for (int a = 0; a < 3; ++a) grad19(st, st->v_o[a], x, y, z, dv[a]);
+        grad19(st, st->phiS, 0, x, y, z, gp);
+        const double lphi = lap19(st, st->phiS, 0, x, y, z);
+        grad19(st, st->psiS, 1, x, y, z, gs);
+        for (int a = 0; a < 3; ++a) grad19(st, st->v_o[a], 3 + a, x, y, z, dv[a]);
         /* gas-liquid interface */
         const double rho = rg + phi * (rl - rg);
         double gr[3], nf[3];
@@ -1162,7 +1256,7 @@ static void step3f(o3fstate *st) {
           const double Q0 = qpsif_at(st, phi, psi, U, theta);
           double lam, Mc, thsys, gu[3];
           derivedf(st, &lam, &Mc, &thsys);
-          grad19(st, st->US, x, y, z, gu);
+          grad19(st, st->US, 2, x, y, z, gu);
           double dot = 0;
           for (int a = 0; a < 3; ++a) dot += Mc * (1.0 - k) * gu[a] * (as2 * gs[a] + N[a]);
           Fu = f_of_uf(st, U);

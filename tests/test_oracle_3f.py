@@ -324,3 +324,61 @@ def test_gas_temperature_uses_the_local_density():
     f = o.fields()
     assert f["phi"].min() < 0.05
     assert np.abs(f["theta"] - T3F["theta0"]).max() < 1e-2
+
+
+# ---------------------------------------------------------------------------
+# non-periodic sides of the two-phase step (reading R36: symmetric sides
+# reflect, walls and far-field sides bounce NS and CAC back; D3Q7 as R35)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("thermal", [False, True])
+def test_symmetric_sides_are_mirror_planes(thermal):
+    """A box with symmetric sides in x evolves exactly as the left half of the
+    periodic box twice as wide made of the box and its mirror image, with a
+    bubble, a seed, a flow (v_x odd, v_y and v_z even under the mirror) and
+    gravity."""
+    n, ny, nz = 12, 10, 8
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:2 * n].astype(float)
+    xs = np.where(x < n, x, 2 * n - 1 - x)
+    sgn = np.where(x < n, 1.0, -1.0)
+    rb = np.sqrt((xs - 7.0) ** 2 + (y - 5.0) ** 2 + (z - 4.0) ** 2)
+    phi = 0.5 + 0.5 * np.tanh(math.sqrt(0.5) * (rb - 3.0) / 8.0)
+    rs = np.sqrt((xs - 2.5) ** 2 + (y - 4.0) ** 2 + (z - 3.0) ** 2)
+    psi = np.tanh(math.sqrt(0.5) * (3.0 - rs) / 4.0)
+    C = phi * (1 - 0.85 * (1 + psi) / 2)
+    vx = 1e-3 * sgn * np.sin(np.pi * (xs + 0.5) / n) * np.cos(2 * np.pi * y / ny)
+    vy = 1e-3 * np.cos(np.pi * (xs + 0.5) / n) * np.sin(2 * np.pi * z / nz)
+    vz = 5e-4 * np.cos(2 * np.pi * y / ny)
+    params = dict(T3F if thermal else P3F, g=2e-5)
+    big = oracle.Oracle3F(2 * n, ny, nz, params)
+    big.init_fields(phi, psi, C, vx, vy, vz)
+    small = oracle.Oracle3F(n, ny, nz, params)
+    small.set_bc([1, 1, 0, 0, 0, 0])
+    h = (slice(None), slice(None), slice(0, n))
+    small.init_fields(phi[h], psi[h], C[h], vx[h], vy[h], vz[h])
+    small.set_rho_bar(big.rho_bar)
+    big.step(40)
+    small.step(40)
+    fb, fs = big.fields(), small.fields()
+    for k in fs:
+        half = fb[k][h]
+        assert np.abs(fs[k] - half).max() <= 1e-11 * max(np.abs(half).max(), 1e-6), k
+
+
+def test_walls_hold_no_slip_at_half_way():
+    """Walls at x = -1/2 and x = nx - 1/2 (no slip): in pure liquid the lowest
+    shear mode v_y = A sin(pi (x + 1/2) / nx) decays at nu (pi / nx)^2, and
+    sum phi, sum C stay constant."""
+    nx, A = 24, 1e-3
+    z, y, x = np.mgrid[0:4, 0:4, 0:nx].astype(float)
+    one = np.ones_like(x)
+    o = oracle.Oracle3F(nx, 4, 4, dict(P3F, g=0.0))
+    o.set_bc([2, 2, 0, 0, 0, 0])
+    o.init_fields(one, -one, one, 0 * one, A * np.sin(np.pi * (x + 0.5) / nx), 0 * one)
+    t0 = o.totals()
+    o.step(50)
+    a0 = o.fields()["vy"][0, 0, nx // 2]
+    o.step(200)
+    a1 = o.fields()["vy"][0, 0, nx // 2]
+    assert math.isclose(math.log(a0 / a1) / 200, P3F["nu"] * (math.pi / nx) ** 2, rel_tol=0.01)
+    t1 = o.totals()
+    assert abs(t1["sum_phi"] / t0["sum_phi"] - 1) < 1e-13 and abs(t1["sum_C"] / t0["sum_C"] - 1) < 1e-13
