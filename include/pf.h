@@ -497,6 +497,14 @@ double pf3f_get_rho_bar(const pf3f_handle *h);
  * qx, qy, qz), every site takes the nearest seed's rotation; 0 seeds returns
  * to the lattice-aligned grain.  Synchronises.  Errors: BAD_ARG, OOM, CUDA. */
 pf_status pf3f_set_orientation(pf3f_handle *h, const double *seeds7, int n_seeds);
+/* Side types of the faces x-, x+, y-, y+, z-, z+ (0 periodic, 1 symmetric, 2
+ * wall, 3 far field), half-way between the last site and its ghost: NS and CAC
+ * reflect at a symmetric side and bounce back (no slip, no flux) at a wall or a
+ * far-field side; psi, C, theta as pf3_set_boundaries; stencil ghosts mirror
+ * the last site (the velocity's normal component flipped at a symmetric side,
+ * all of it at a wall or far side; 2 X_far - X for psi and U at a far side).
+ * Before initialising.  Errors: BAD_ARG, STATE. */
+pf_status pf3f_set_boundaries(pf3f_handle *h, const int bc[6]);
 /* Planes per tile of the z-march (default 16). */
 pf_status pf3f_set_chunk(pf3f_handle *h, int chunk);
 /* Advance n_steps (enqueued).  Errors: BAD_ARG, STATE (not initialised), CUDA. */

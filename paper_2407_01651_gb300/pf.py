@@ -142,6 +142,7 @@ def lib() -> ctypes.CDLL:
     L.pf3f_get_rho_bar.restype = ctypes.c_double
     L.pf3f_set_chunk.argtypes = [P, I]
     L.pf3f_set_orientation.argtypes = [P, D, I]
+    L.pf3f_set_boundaries.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
     L.pf3f_set_temperature.argtypes = [P, D, S]
     L.pf3f_reduce_thermal.argtypes = [P, D]
     L.pf3f_field_planes.argtypes = [P]
@@ -167,7 +168,8 @@ def lib() -> ctypes.CDLL:
                  "pf3f_create",
                  "pf3f_init_spec", "pf3f_set_fields", "pf3f_set_rho_bar", "pf3f_set_chunk",
                  "pf3f_step", "pf3f_get_fields", "pf3f_get_state", "pf3f_reduce", "pf3f_destroy",
-                 "pf3f_set_orientation", "pf3f_set_temperature", "pf3f_reduce_thermal"):
+                 "pf3f_set_orientation", "pf3f_set_temperature", "pf3f_reduce_thermal",
+                 "pf3f_set_boundaries"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -571,6 +573,12 @@ class Simulation3F:
 
     def set_rho_bar(self, rho_bar: float) -> None:
         _check3f(lib().pf3f_set_rho_bar(self.h, float(rho_bar)), self.h)
+
+    def set_boundaries(self, bc) -> None:
+        """Side types x-, x+, y-, y+, z-, z+ (BC_PERIODIC, BC_SYMMETRIC, BC_WALL,
+        BC_FARFIELD), before initialising."""
+        arr = (ctypes.c_int * 6)(*[int(b) for b in bc])
+        _check3f(lib().pf3f_set_boundaries(self.h, arr), self.h)
 
     def set_orientation(self, seeds7) -> None:
         """Grain orientations: n x (x, y, z, qw, qx, qy, qz) (empty: aligned)."""

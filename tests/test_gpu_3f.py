@@ -371,3 +371,63 @@ def test_3f_thermal_long_fp32_run():
     assert abs(t["sum_e"] / t0["sum_e"] - 1) < 1e-6
     assert r["sum_hpsi"] > 1.5 * r0["sum_hpsi"]
     assert f["theta"].mean() > wl.THERMAL_PARAMS["theta0"]
+
+
+# ---------------------------------------------------------------------------
+# non-periodic sides (BC template)
+# ---------------------------------------------------------------------------
+SIDES = [(1, 1, 2, 2, 3, 3), (2, 2, 0, 0, 1, 1), (3, 3, 1, 1, 0, 0)]
+
+
+def pair_bc(shape, sides, precision, params=P3F, seeds=SEEDS, R_s=5.0, bubbles=BUBBLES):
+    nx, ny, nz = shape
+    o = oracle.Oracle3F(nx, ny, nz, params)
+    o.set_bc(sides)
+    o.init_spec(seeds, R_s, bubbles)
+    sim = pf.Simulation3F(shape, dict(wl.BASE_PARAMS, **params), precision)
+    sim.set_boundaries(sides)
+    sim.init_spec(seeds, R_s, bubbles)
+    o.set_rho_bar(sim.rho_bar)
+    return o, sim
+
+
+@pytest.mark.parametrize("sides", SIDES)
+@pytest.mark.parametrize("thermal", [False, True])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", TOL32)])
+def test_3f_sides_match_oracle(sides, thermal, precision, tol):
+    o, sim = pair_bc(RAGGED, sides, precision, dict(T3F if thermal else P3F, g=2e-5))
+    sim.set_chunk(5)
+    for _ in range(3):
+        o.step(1)
+        sim.step(1)
+        compare(o, sim, tol)
+
+
+def test_3f_sides_fp64_many_steps():
+    """Symmetric planes and walls with gravity, a bubble, a rotated seed and
+    the temperature lattice: FP64 within 1e-9 of the oracle over 100 steps,
+    sum phi, sum C and sum rho H constant to 1e-12."""
+    n = 24
+    seeds7 = [(6.0, 12.0, 12.0, 0.9, 0.2, -0.3, 0.1)]
+    o, sim = pair_bc((n, n, n), (1, 1, 2, 2, 1, 1), "fp64", dict(T3F, g=2e-5),
+                     [s[:3] for s in seeds7], 5.0, [(16.0, 10.0, 12.0, 4.5)])
+    o.set_orientation(seeds7)
+    sim.set_orientation(seeds7)
+    r0, t0 = sim.reduce(), sim.reduce_thermal()
+    o.step(100)
+    sim.step(100)
+    compare(o, sim, 1e-9)
+    r1, t1 = sim.reduce(), sim.reduce_thermal()
+    assert abs(r1["sum_phi"] / r0["sum_phi"] - 1) < 1e-12
+    assert abs(r1["sum_C"] / r0["sum_C"] - 1) < 1e-12
+    assert abs(t1["sum_e"] / t0["sum_e"] - 1) < 1e-12
+
+
+def test_3f_sides_configuration_errors():
+    sim = pf.Simulation3F((8, 8, 8), wl.BASE_PARAMS, "fp32")
+    with pytest.raises(pf.PFError):
+        sim.set_boundaries((0, 2, 0, 0, 0, 0))
+    sim.init_spec([(4, 4, 4)], 2.0, [])
+    with pytest.raises(pf.PFError) as e:
+        sim.set_boundaries((1, 1, 0, 0, 0, 0))
+    assert e.value.code == pf.PF_ERR_STATE
