@@ -507,6 +507,12 @@ pf_status pf3f_set_orientation(pf3f_handle *h, const double *seeds7, int n_seeds
 pf_status pf3f_set_boundaries(pf3f_handle *h, const int bc[6]);
 /* Planes per tile of the z-march (default 16). */
 pf_status pf3f_set_chunk(pf3f_handle *h, int chunk);
+/* Index width of the periodic step: by default sites and plane offsets are
+ * indexed in 32 bits while PF3F_STATE_PLANES_THERMAL x n < 2^32 (fewer address
+ * instructions) and in 64 bits above; on != 0 takes the 64-bit form at any
+ * size (results are bit-identical).  Steps with non-periodic sides always
+ * index in 64 bits.  Errors: BAD_ARG. */
+pf_status pf3f_set_index64(pf3f_handle *h, int on);
 /* Advance n_steps (enqueued).  Errors: BAD_ARG, STATE (not initialised), CUDA. */
 pf_status pf3f_step(pf3f_handle *h, int n_steps);
 /* Fields of the last step (PF3F_FIELD_PLANES planes of n).  Synchronises. */

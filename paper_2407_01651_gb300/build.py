@@ -15,7 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpf.so")
-SOURCES = ("pf_step.cu", "pf_step_staged.cu", "pf_step_bc.cu", "pf_step3d.cu", "pf_step3f.cu", "pf_step3f_bc.cu", "pf_adjoint.cu",
+SOURCES = ("pf_step.cu", "pf_step_staged.cu", "pf_step_bc.cu", "pf_step3d.cu", "pf_step3f.cu", "pf_step3f_bc.cu",
+           "pf_step3f_wide.cu", "pf_adjoint.cu",
            "pf_kernels.cu", "pf_capi.cu", "pf_noalloc.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -26,6 +26,11 @@ template <typename T>
 __device__ __forceinline__ const T* pl(const T* p, int k, unsigned long long ps) { return p + (size_t)k * ps; }
 template <typename T>
 __device__ __forceinline__ T* pl(T* p, int k, unsigned long long ps) { return p + (size_t)k * ps; }
+// 32-bit plane stride: the caller guarantees planes x sites < 2^32
+template <typename T>
+__device__ __forceinline__ const T* pl(const T* p, int k, unsigned ps) { return p + (unsigned)k * ps; }
+template <typename T>
+__device__ __forceinline__ T* pl(T* p, int k, unsigned ps) { return p + (unsigned)k * ps; }
 
 // Hint: bring the line that holds p into L2 ahead of its use (no register is
 // written, so a z-march can look two planes ahead for free).

@@ -29,11 +29,6 @@
 namespace pf {
 namespace d3f {
 
-// the boundary-aware variants (BC = true), instantiated in pf_step3f_bc.cu
-template <typename S, typename R>
-cudaError_t launch3f_bc(const ArgsF<S, R>& a, bool rotated, bool thermal, int tiles, size_t smem,
-                        cudaStream_t st);
-
 // Equilibrium state of a site (Appendix B at the given phi, psi, C, v, p):
 // f = f_eq(p, rho, v), h = w phi (1 + 3 c.v), g = w psi, s = w C (1 + 4 c.v),
 // r = 1, lagged values equal to the current ones; fields written.
@@ -243,6 +238,7 @@ struct pf3f_handle {
   pf_precision prec = PF_FP32;
   cudaStream_t stream = nullptr;
   int nx = 0, ny = 0, nz = 0, chunk = 16;
+  int index64 = 0;  // periodic step in 64-bit indices at any size
   unsigned long long n = 0;
   size_t elem = 4;
   double rho_bar = 0.0;
@@ -324,9 +320,9 @@ static CoefF<R> coeff(const pf3f_handle* h) {
   return c;
 }
 
-template <typename S, typename R>
-static ArgsF<S, R> argsf(const pf3f_handle* h, bool fields) {
-  ArgsF<S, R> a{};
+template <typename S, typename R, typename I = unsigned long long>
+static ArgsF<S, R, I> argsf(const pf3f_handle* h, bool fields) {
+  ArgsF<S, R, I> a{};
   a.in = (const S*)h->pop[h->cur];
   a.out = (S*)h->pop[h->cur ^ 1];
   a.ain = (const R*)h->aux[h->cur];
@@ -335,7 +331,7 @@ static ArgsF<S, R> argsf(const pf3f_handle* h, bool fields) {
   a.grain = h->grain;
   a.rot = (const R*)h->rot;
   for (int k = 0; k < 6; ++k) a.bc[k] = h->bc[k];
-  a.ps = h->n;
+  a.ps = (I)h->n;
   a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.chunk = h->chunk;
   a.tiles_x = (h->nx + TX - 1) / TX;
   a.tiles_y = (h->ny + TY - 1) / TY;
@@ -600,6 +596,12 @@ extern "C" pf_status pf3f_set_chunk(pf3f_handle* h, int chunk) {
   return PF_OK;
 }
 
+extern "C" pf_status pf3f_set_index64(pf3f_handle* h, int on) {
+  if (!h) return PF_ERR_BAD_ARG;
+  h->index64 = on != 0;
+  return PF_OK;
+}
+
 extern "C" pf_status pf3f_step(pf3f_handle* h, int n_steps) {
   if (!h) return PF_ERR_BAD_ARG;
   if (n_steps < 0) return failf(h, PF_ERR_BAD_ARG, "n_steps must be >= 0");
@@ -608,27 +610,21 @@ extern "C" pf_status pf3f_step(pf3f_handle* h, int n_steps) {
     using S = decltype(s_t);
     using R = decltype(r_t);
     const size_t smem = ring_bytes<R>(h->thermal != 0);
-    if (smem > 48 * 1024) {
-      auto big = [&](auto kern) {
-        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      };
-      PF3F_CUDA(h, big(k_step3f<S, R, false, false, false>));
-      PF3F_CUDA(h, big(k_step3f<S, R, true, false, false>));
-      PF3F_CUDA(h, big(k_step3f<S, R, false, true, false>));
-      PF3F_CUDA(h, big(k_step3f<S, R, true, true, false>));
-    }
+    // periodic launches index sites and planes in 32 bits while every plane
+    // offset (below NSTATEF_TH x sites) fits
+    const bool a32 = !h->any_bc && !h->index64 && (unsigned long long)NSTATEF_TH * h->n <= 0xFFFFFFFFull;
+    const bool rot = h->rotated != 0, th = h->thermal != 0;
     for (int t = 0; t < n_steps; ++t) {
-      const ArgsF<S, R> a = argsf<S, R>(h, t == n_steps - 1);
+      const bool last = t == n_steps - 1;
+      const ArgsF<S, R> a = argsf<S, R>(h, last);
       const int tiles = a.tiles_x * a.tiles_y * a.tiles_z;
-      if (h->any_bc) {
-        PF3F_CUDA(h, launch3f_bc<S, R>(a, h->rotated != 0, h->thermal != 0, tiles, smem, h->stream));
-      } else if (h->thermal) {
-        if (h->rotated) k_step3f<S, R, true, true, false><<<tiles, THREADS, smem, h->stream>>>(a);
-        else k_step3f<S, R, false, true, false><<<tiles, THREADS, smem, h->stream>>>(a);
-      } else {
-        if (h->rotated) k_step3f<S, R, true, false, false><<<tiles, THREADS, smem, h->stream>>>(a);
-        else k_step3f<S, R, false, false, false><<<tiles, THREADS, smem, h->stream>>>(a);
-      }
+      if (a32)
+        PF3F_CUDA(h, (launch3f<S, R, false, unsigned>(argsf<S, R, unsigned>(h, last), rot, th, tiles,
+                                                      smem, h->stream)));
+      else if (h->any_bc)
+        PF3F_CUDA(h, (launch3f<S, R, true>(a, rot, th, tiles, smem, h->stream)));
+      else
+        PF3F_CUDA(h, (launch3f<S, R, false>(a, rot, th, tiles, smem, h->stream)));
       PF3F_CUDA(h, cudaGetLastError());
       h->cur ^= 1;
       h->steps++;

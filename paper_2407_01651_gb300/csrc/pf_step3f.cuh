@@ -95,7 +95,9 @@ struct CoefF {
   R th0;               // theta at a far-field side
 };
 
-template <typename S, typename R>
+// I: the type of site indices and plane offsets (32-bit when planes x sites
+// fits, which saves address arithmetic in the pulls; 64-bit otherwise)
+template <typename S, typename R, typename I = unsigned long long>
 struct ArgsF {
   const S* in;
   S* out;
@@ -106,23 +108,23 @@ struct ArgsF {
   const R* rot;         // ROT: 9 entries (row-major R) per grain
   int bc[6];            // BC: side types x-, x+, y-, y+, z-, z+ (0 periodic, 1 symmetric,
                         // 2 wall, 3 far field)
-  unsigned long long ps;
+  I ps;
   int nx, ny, nz, chunk;
   int tiles_x, tiles_y, tiles_z;
   CoefF<R> c;
 };
 
-template <typename S, typename R>
-__device__ __forceinline__ unsigned long long site_of(const ArgsF<S, R>& a, int x, int y, int z) {
-  return ((unsigned long long)z * a.ny + y) * a.nx + x;
+template <typename S, typename R, typename I>
+__device__ __forceinline__ unsigned long long site_of(const ArgsF<S, R, I>& a, int x, int y, int z) {
+  return ((I)z * (I)a.ny + (I)y) * (I)a.nx + (I)x;
 }
 // pull source of D3Q19 direction i (x, y in range; one step wraps)
-template <typename S, typename R>
-__device__ __forceinline__ unsigned long long src19(const ArgsF<S, R>& a, int x, int y, int z, int i) {
+template <typename S, typename R, typename I>
+__device__ __forceinline__ unsigned long long src19(const ArgsF<S, R, I>& a, int x, int y, int z, int i) {
   return site_of(a, wrap1(x - c19(i, 0), a.nx), wrap1(y - c19(i, 1), a.ny), wrap1(z - c19(i, 2), a.nz));
 }
-template <typename S, typename R>
-__device__ __forceinline__ unsigned long long src7(const ArgsF<S, R>& a, int x, int y, int z, int i) {
+template <typename S, typename R, typename I>
+__device__ __forceinline__ unsigned long long src7(const ArgsF<S, R, I>& a, int x, int y, int z, int i) {
   return site_of(a, wrap1(x - cx7(i), a.nx), wrap1(y - cy7(i), a.ny), wrap1(z - cz7(i), a.nz));
 }
 
@@ -138,8 +140,8 @@ __host__ __device__ constexpr int opp19(int i) { return i == 0 ? 0 : (i % 2 ? i 
 // symmetric side reflects the source site and the direction's normal
 // component, a wall or far-field side returns the site's own opposite
 // population (a bounce wins over a reflection).
-template <typename S, typename R, bool BC>
-__device__ __forceinline__ unsigned long long pull19(const ArgsF<S, R>& a, int x, int y, int z, int i,
+template <typename S, typename R, bool BC, typename I>
+__device__ __forceinline__ unsigned long long pull19(const ArgsF<S, R, I>& a, int x, int y, int z, int i,
                                                      int& q) {
   if constexpr (BC) {
     int X[3] = {x - c19(i, 0), y - c19(i, 1), z - c19(i, 2)};
@@ -170,8 +172,8 @@ __device__ __forceinline__ unsigned long long pull19(const ArgsF<S, R>& a, int x
 // site's own opposite population (mode 1), a far-field side its anti-bounce-back
 // (mode 2).
 __device__ __forceinline__ constexpr int opp7f(int i) { return i == 0 ? 0 : (i % 2 ? i + 1 : i - 1); }
-template <typename S, typename R, bool BC>
-__device__ __forceinline__ int pull7(const ArgsF<S, R>& a, int x, int y, int z, int i,
+template <typename S, typename R, bool BC, typename I>
+__device__ __forceinline__ int pull7(const ArgsF<S, R, I>& a, int x, int y, int z, int i,
                                      unsigned long long& src, int& q) {
   if constexpr (BC) {
     const int X = x - cx7(i), Y = y - cy7(i), Z = z - cz7(i);
@@ -191,8 +193,8 @@ __device__ __forceinline__ int pull7(const ArgsF<S, R>& a, int x, int y, int z, 
 }
 
 // Streamed D3Q7 populations (plane base P) at (x, y, z); far: the far-field value
-template <typename S, typename R, bool BC>
-__device__ __forceinline__ void stream7f(const ArgsF<S, R>& a, int P, int x, int y, int z, R f[7],
+template <typename S, typename R, bool BC, typename I>
+__device__ __forceinline__ void stream7f(const ArgsF<S, R, I>& a, int P, int x, int y, int z, R f[7],
                                          R far) {
 #pragma unroll
   for (int i = 0; i < 7; ++i) {
@@ -218,8 +220,8 @@ __device__ __forceinline__ int side_coord(int c, int n, int t0, int t1, int& t) 
 }
 
 // phi = sum of the streamed h at (x, y, z)
-template <typename S, typename R, bool BC>
-__device__ __forceinline__ R stream_phi(const ArgsF<S, R>& a, int x, int y, int z) {
+template <typename S, typename R, bool BC, typename I>
+__device__ __forceinline__ R stream_phi(const ArgsF<S, R, I>& a, int x, int y, int z) {
   CSum<R> s;
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
@@ -231,8 +233,8 @@ __device__ __forceinline__ R stream_phi(const ArgsF<S, R>& a, int x, int y, int 
 }
 
 // streamed g with the time stretch, psi and psi_o (as in the melt-only step)
-template <typename S, typename R, bool BC>
-__device__ __forceinline__ void stream_g(const ArgsF<S, R>& a, int x, int y, int z, R g[7],
+template <typename S, typename R, bool BC, typename I>
+__device__ __forceinline__ void stream_g(const ArgsF<S, R, I>& a, int x, int y, int z, R g[7],
                                          R& psi, R& psio) {
   const unsigned long long own = site_of(a, x, y, z);
   CSum<R> sg;
@@ -255,8 +257,8 @@ __device__ __forceinline__ void stream_g(const ArgsF<S, R>& a, int x, int y, int
 }
 
 // U = (2C/A - 1)/(1-k) of the streamed solute at (x, y, z), for the U ring
-template <typename S, typename R, bool BC>
-__device__ __forceinline__ R stream_U(const ArgsF<S, R>& a, int x, int y, int z, R psi) {
+template <typename S, typename R, bool BC, typename I>
+__device__ __forceinline__ R stream_U(const ArgsF<S, R, I>& a, int x, int y, int z, R psi) {
   CSum<R> cs;
   R sv[7];
   stream7f<S, R, BC>(a, S_POP, x, y, z, sv, R(1));
@@ -270,8 +272,8 @@ __device__ __forceinline__ R stream_U(const ArgsF<S, R>& a, int x, int y, int z,
 // planes take the mirror site's values, mapped per side (psi and U across a far
 // side, the velocity's normal component at a symmetric side and all of it at a
 // wall or far side).
-template <typename S, typename R, bool ROT, bool TH, bool BC>
-__global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R> a) {
+template <typename S, typename R, bool ROT, bool TH, bool BC, typename I = unsigned long long>
+__global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R, I> a) {
   // rings of phi, psi, v_o (and U) (dynamic: 54 KB in FP64)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R (*rphi)[HY][HX] = reinterpret_cast<R (*)[HY][HX]>(smem_raw);
@@ -688,6 +690,44 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R> a) {
     __syncthreads();
   }
 }
+
+// One step launch over all tiles (dynamic shared memory smem): the variant for
+// the thermal and rotated modes, with sides (BC) or periodic, in index type I.
+// Each set of (BC, I) is instantiated in one translation unit.
+template <typename S, typename R, bool BC, typename I>
+cudaError_t launch3f(const ArgsF<S, R, I>& a, bool rotated, bool thermal, int tiles, size_t smem,
+                     cudaStream_t st) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaSuccess;
+    auto big = [&](auto kern) {
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    };
+    big(k_step3f<S, R, false, false, BC, I>);
+    big(k_step3f<S, R, true, false, BC, I>);
+    big(k_step3f<S, R, false, true, BC, I>);
+    big(k_step3f<S, R, true, true, BC, I>);
+    if (e != cudaSuccess) return e;
+  }
+  if (thermal) {
+    if (rotated) k_step3f<S, R, true, true, BC, I><<<tiles, THREADS, smem, st>>>(a);
+    else k_step3f<S, R, false, true, BC, I><<<tiles, THREADS, smem, st>>>(a);
+  } else {
+    if (rotated) k_step3f<S, R, true, false, BC, I><<<tiles, THREADS, smem, st>>>(a);
+    else k_step3f<S, R, false, false, BC, I><<<tiles, THREADS, smem, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+// instantiated in pf_step3f_bc.cu (sides, 64-bit) and pf_step3f_wide.cu
+// (periodic, 64-bit: grids whose plane offsets exceed 32 bits)
+#define PF3F_LAUNCH_SET(EXT, BC, I)                                                              \
+  EXT template cudaError_t launch3f<float, float, BC, I>(const ArgsF<float, float, I>&, bool,    \
+                                                         bool, int, size_t, cudaStream_t);      \
+  EXT template cudaError_t launch3f<double, double, BC, I>(const ArgsF<double, double, I>&, bool, \
+                                                           bool, int, size_t, cudaStream_t);
+PF3F_LAUNCH_SET(extern, true, unsigned long long)
+PF3F_LAUNCH_SET(extern, false, unsigned long long)
 
 }  // namespace d3f
 }  // namespace pf

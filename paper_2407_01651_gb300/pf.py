@@ -141,6 +141,7 @@ def lib() -> ctypes.CDLL:
     L.pf3f_get_rho_bar.argtypes = [P]
     L.pf3f_get_rho_bar.restype = ctypes.c_double
     L.pf3f_set_chunk.argtypes = [P, I]
+    L.pf3f_set_index64.argtypes = [P, I]
     L.pf3f_set_orientation.argtypes = [P, D, I]
     L.pf3f_set_boundaries.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
     L.pf3f_set_temperature.argtypes = [P, D, S]
@@ -167,6 +168,7 @@ def lib() -> ctypes.CDLL:
                  "pf3_set_boundaries",
                  "pf3f_create",
                  "pf3f_init_spec", "pf3f_set_fields", "pf3f_set_rho_bar", "pf3f_set_chunk",
+                 "pf3f_set_index64",
                  "pf3f_step", "pf3f_get_fields", "pf3f_get_state", "pf3f_reduce", "pf3f_destroy",
                  "pf3f_set_orientation", "pf3f_set_temperature", "pf3f_reduce_thermal",
                  "pf3f_set_boundaries"):
@@ -587,6 +589,11 @@ class Simulation3F:
 
     def set_chunk(self, chunk: int) -> None:
         _check3f(lib().pf3f_set_chunk(self.h, int(chunk)), self.h)
+
+    def set_index64(self, on: bool = True) -> None:
+        """Take the 64-bit index form of the periodic step at any size
+        (otherwise 32-bit while the state planes fit; results are identical)."""
+        _check3f(lib().pf3f_set_index64(self.h, int(bool(on))), self.h)
 
     def step(self, n: int = 1) -> None:
         _check3f(lib().pf3f_step(self.h, int(n)), self.h)
