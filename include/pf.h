@@ -420,6 +420,12 @@ pf_status pf3_set_orientation(pf3_handle *h, const double *seeds7, int n_seeds);
 pf_status pf3_set_boundaries(pf3_handle *h, const int bc[6]);
 /* Planes per tile of the z-march (default 16). */
 pf_status pf3_set_chunk(pf3_handle *h, int chunk);
+/* Index width of the periodic step: by default sites and plane offsets are
+ * indexed in 32 bits while PF3_STATE_PLANES_THERMAL x n < 2^32 (fewer address
+ * instructions) and in 64 bits above; on != 0 takes the 64-bit form at any
+ * size (results are bit-identical).  Steps with non-periodic sides always
+ * index in 64 bits.  Errors: BAD_ARG. */
+pf_status pf3_set_index64(pf3_handle *h, int on);
 /* Advance n_steps (enqueued; errors of the launch are reported).
  * Errors: BAD_ARG, STATE, CUDA. */
 pf_status pf3_step(pf3_handle *h, int n_steps);

@@ -38,7 +38,9 @@ struct Coef3 {
   R rcp, irc, halfL, iLe, W0sq, omsth;
 };
 
-template <typename S, typename R>
+// I: the type of site indices and plane offsets (32-bit when planes x sites
+// fits, which saves address arithmetic in the pulls; 64-bit otherwise)
+template <typename S, typename R, typename I = unsigned long long>
 struct Args3 {
   const S* in;
   S* out;
@@ -49,16 +51,20 @@ struct Args3 {
   const R* rot;         // ROT: 9 entries (row-major R) per grain
   int bc[6];            // BC: side types x-, x+, y-, y+, z-, z+ (0 periodic, 1 symmetric,
                         // 2 wall, 3 far field)
-  unsigned long long ps;
+  I ps;
   int nx, ny, nz, chunk;
   int tiles_x, tiles_y, tiles_z;
   Coef3<R> c;
 };
 
-template <typename S, typename R>
-__device__ __forceinline__ unsigned long long src7(const Args3<S, R>& a, int x, int y, int z, int i) {
-  return ((unsigned long long)wrap1(z - cz7(i), a.nz) * a.ny + wrap1(y - cy7(i), a.ny)) * a.nx +
-         wrap1(x - cx7(i), a.nx);   // x, y in range: one step wraps
+template <typename S, typename R, typename I>
+__device__ __forceinline__ unsigned long long site3(const Args3<S, R, I>& a, int x, int y, int z) {
+  return ((I)z * (I)a.ny + (I)y) * (I)a.nx + (I)x;
+}
+template <typename S, typename R, typename I>
+__device__ __forceinline__ unsigned long long src7(const Args3<S, R, I>& a, int x, int y, int z, int i) {
+  // x, y in range: one step wraps
+  return site3(a, wrap1(x - cx7(i), a.nx), wrap1(y - cy7(i), a.ny), wrap1(z - cz7(i), a.nz));
 }
 
 // BC: pull source of direction i at (x, y, z): a source beyond a non-periodic
@@ -66,8 +72,8 @@ __device__ __forceinline__ unsigned long long src7(const Args3<S, R>& a, int x, 
 // mode 1) or anti-bounced to the far-field value (mode 2); D3Q7 crosses at most
 // one side.
 __device__ __forceinline__ constexpr int opp7(int i) { return i == 0 ? 0 : (i % 2 ? i + 1 : i - 1); }
-template <typename S, typename R, bool BC>
-__device__ __forceinline__ int pull7(const Args3<S, R>& a, int x, int y, int z, int i,
+template <typename S, typename R, bool BC, typename I>
+__device__ __forceinline__ int pull7(const Args3<S, R, I>& a, int x, int y, int z, int i,
                                      unsigned long long& src, int& q) {
   if constexpr (BC) {
     const int X = x - cx7(i), Y = y - cy7(i), Z = z - cz7(i);
@@ -76,7 +82,7 @@ __device__ __forceinline__ int pull7(const Args3<S, R>& a, int x, int y, int z, 
     else if (Y < 0) t = a.bc[2]; else if (Y >= a.ny) t = a.bc[3];
     else if (Z < 0) t = a.bc[4]; else if (Z >= a.nz) t = a.bc[5];
     if (t) {
-      src = ((unsigned long long)z * a.ny + y) * a.nx + x;
+      src = site3(a, x, y, z);
       q = opp7(i);
       return t == 3 ? 2 : 1;
     }
@@ -88,10 +94,10 @@ __device__ __forceinline__ int pull7(const Args3<S, R>& a, int x, int y, int z, 
 
 // Streamed g at (x, y, z) (time stretch g = g_pre + r_src (g_post,src - g_pre))
 // and psi, psi_o (compensated sums).
-template <typename S, typename R, bool BC>
-__device__ __forceinline__ void stream_g(const Args3<S, R>& a, int x, int y, int z, R g[7],
+template <typename S, typename R, bool BC, typename I>
+__device__ __forceinline__ void stream_g(const Args3<S, R, I>& a, int x, int y, int z, R g[7],
                                          R& psi, R& psio) {
-  const unsigned long long own = ((unsigned long long)z * a.ny + y) * a.nx + x;
+  const unsigned long long own = site3(a, x, y, z);
   CSum<R> sg;
   R po = R(0);
 #pragma unroll
@@ -113,8 +119,8 @@ __device__ __forceinline__ void stream_g(const Args3<S, R>& a, int x, int y, int
 
 // Streamed populations of one D3Q7 lattice (plane base P) at (x, y, z); far:
 // the lattice's far-field value (BC).
-template <typename S, typename R, bool BC>
-__device__ __forceinline__ void stream7(const Args3<S, R>& a, int P, int x, int y, int z, R f[7],
+template <typename S, typename R, bool BC, typename I>
+__device__ __forceinline__ void stream7(const Args3<S, R, I>& a, int P, int x, int y, int z, R f[7],
                                         R far) {
 #pragma unroll
   for (int i = 0; i < 7; ++i) {
@@ -163,8 +169,8 @@ __device__ __forceinline__ R supersat3(const Coef3<R>& c, R C, R psi) {
 // evaluated on g' = R^T grad psi and N = R N'(g')).
 // BC: non-periodic sides (pull7, ghost_coord): ghost ring columns and planes
 // take the mirror site's psi (and U), mapped to 2 X_far - X across a far side.
-template <typename S, typename R, bool TH, bool ROT, bool BC>
-__global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R> a) {
+template <typename S, typename R, bool TH, bool ROT, bool BC, typename I = unsigned long long>
+__global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R, I> a) {
   __shared__ R ring[4][HY][HX];
   __shared__ R uring[TH ? 4 : 1][HY][HX];
   const int t = threadIdx.x;
@@ -247,7 +253,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R> a) {
       // own inputs of plane z: streamed solute (and temperature) populations
       // and the lagged source
       R sv[7], ev[7], Qo = R(0);
-      const unsigned long long site = ((unsigned long long)z * a.ny + y) * a.nx + x;
+      const unsigned long long site = site3(a, x, y, z);
       if (mine) {
         if constexpr (TH) {
 #pragma unroll
@@ -259,7 +265,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R> a) {
         Qo = ld<R>(pl(a.ain, A3_QO, a.ps), site);
         // warm L2 with this column's populations two planes ahead
         const int z2 = z + 2 >= a.nz ? z + 2 - a.nz : z + 2;
-        const unsigned long long pf2 = ((unsigned long long)z2 * a.ny + y) * a.nx + x;
+        const unsigned long long pf2 = site3(a, x, y, z2);
         constexpr int NPF = TH ? NPOP3_TH : NPOP3;
 #pragma unroll
         for (int q = 0; q < NPF; ++q) prefetch_l2(pl(a.in, q, a.ps) + pf2);
@@ -585,6 +591,7 @@ struct pf3_handle {
   pf_precision prec = PF_FP32;
   cudaStream_t stream = nullptr;
   int nx = 0, ny = 0, nz = 0, chunk = 16;
+  int index64 = 0;  // periodic step in 64-bit indices at any size
   int thermal = 0, npop = NPOP3, nfields = 3, nstate = NSTATE3;
   int rotated = 0;                // grain orientations set
   int bc[6] = {0, 0, 0, 0, 0, 0}; // side types x-, x+, y-, y+, z-, z+
@@ -647,9 +654,9 @@ static Coef3<R> coef3(const pf_params& p) {
   return c;
 }
 
-template <typename S, typename R>
-static Args3<S, R> args3(const pf3_handle* h, bool fields) {
-  Args3<S, R> a{};
+template <typename S, typename R, typename I = unsigned long long>
+static Args3<S, R, I> args3(const pf3_handle* h, bool fields) {
+  Args3<S, R, I> a{};
   a.in = (const S*)h->pop[h->cur];
   a.out = (S*)h->pop[h->cur ^ 1];
   a.ain = (const R*)h->aux[h->cur];
@@ -658,7 +665,7 @@ static Args3<S, R> args3(const pf3_handle* h, bool fields) {
   a.grain = h->grain;
   a.rot = (const R*)h->rot;
   for (int k = 0; k < 6; ++k) a.bc[k] = h->bc[k];
-  a.ps = h->n;
+  a.ps = (I)h->n;
   a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.chunk = h->chunk;
   a.tiles_x = (h->nx + TX - 1) / TX;
   a.tiles_y = (h->ny + TY - 1) / TY;
@@ -913,6 +920,12 @@ extern "C" pf_status pf3_set_chunk(pf3_handle* h, int chunk) {
   return PF_OK;
 }
 
+extern "C" pf_status pf3_set_index64(pf3_handle* h, int on) {
+  if (!h) return PF_ERR_BAD_ARG;
+  h->index64 = on != 0;
+  return PF_OK;
+}
+
 extern "C" pf_status pf3_step(pf3_handle* h, int n_steps) {
   if (!h) return PF_ERR_BAD_ARG;
   if (n_steps < 0) return fail3(h, PF_ERR_BAD_ARG, "n_steps must be >= 0");
@@ -920,21 +933,27 @@ extern "C" pf_status pf3_step(pf3_handle* h, int n_steps) {
   return dispatch3(h, [&](auto s_t, auto r_t) {
     using S = decltype(s_t);
     using R = decltype(r_t);
+    // periodic launches index sites and planes in 32 bits while every plane
+    // offset (below NSTATE3_TH x sites) fits
+    const bool a32 = !h->any_bc && !h->index64 && (unsigned long long)NSTATE3_TH * h->n <= 0xFFFFFFFFull;
     for (int t = 0; t < n_steps; ++t) {
-      const Args3<S, R> a = args3<S, R>(h, t == n_steps - 1);
-      const int tiles = a.tiles_x * a.tiles_y * a.tiles_z;
-      auto go = [&](auto bcv) {
+      const bool last = t == n_steps - 1;
+      const int tiles = (int)((long long)((h->nx + TX - 1) / TX) * ((h->ny + TY - 1) / TY) *
+                              ((h->nz + h->chunk - 1) / h->chunk));
+      auto go = [&](auto bcv, const auto& a) {
         constexpr bool BC = decltype(bcv)::value;
+        using I = decltype(a.ps);
         if (h->rotated) {
-          if (h->thermal) k_step3d<S, R, true, true, BC><<<tiles, THREADS, 0, h->stream>>>(a);
-          else k_step3d<S, R, false, true, BC><<<tiles, THREADS, 0, h->stream>>>(a);
+          if (h->thermal) k_step3d<S, R, true, true, BC, I><<<tiles, THREADS, 0, h->stream>>>(a);
+          else k_step3d<S, R, false, true, BC, I><<<tiles, THREADS, 0, h->stream>>>(a);
         } else {
-          if (h->thermal) k_step3d<S, R, true, false, BC><<<tiles, THREADS, 0, h->stream>>>(a);
-          else k_step3d<S, R, false, false, BC><<<tiles, THREADS, 0, h->stream>>>(a);
+          if (h->thermal) k_step3d<S, R, true, false, BC, I><<<tiles, THREADS, 0, h->stream>>>(a);
+          else k_step3d<S, R, false, false, BC, I><<<tiles, THREADS, 0, h->stream>>>(a);
         }
       };
-      if (h->any_bc) go(std::true_type{});
-      else go(std::false_type{});
+      if (h->any_bc) go(std::true_type{}, args3<S, R>(h, last));
+      else if (a32) go(std::false_type{}, args3<S, R, unsigned>(h, last));
+      else go(std::false_type{}, args3<S, R>(h, last));
       PF3_CUDA(h, cudaGetLastError());
       h->cur ^= 1;
       h->steps++;

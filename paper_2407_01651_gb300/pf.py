@@ -119,6 +119,7 @@ def lib() -> ctypes.CDLL:
     L.pf3_init_seeds.argtypes = [P, D, I, ctypes.c_double]
     L.pf3_set_fields.argtypes = [P, D, D, S]
     L.pf3_set_chunk.argtypes = [P, I]
+    L.pf3_set_index64.argtypes = [P, I]
     L.pf3_step.argtypes = [P, I]
     L.pf3_get_fields.argtypes = [P, D, S]
     L.pf3_get_state.argtypes = [P, D, S]
@@ -163,7 +164,7 @@ def lib() -> ctypes.CDLL:
                  "pf_get_step_config", "pf_reduce_noalloc", "pf_adjoint_step",
                  "pf_set_launch", "pf_autotune", "pf_set_temperature", "pf_reduce_thermal",
                  "pf_set_boundaries", "pf3_create", "pf3_init_seeds", "pf3_set_fields",
-                 "pf3_set_chunk", "pf3_step", "pf3_get_fields", "pf3_get_state", "pf3_reduce",
+                 "pf3_set_chunk", "pf3_set_index64", "pf3_step", "pf3_get_fields", "pf3_get_state", "pf3_reduce",
                  "pf3_destroy", "pf3_set_temperature", "pf3_reduce_thermal", "pf3_set_orientation",
                  "pf3_set_boundaries",
                  "pf3f_create",
@@ -482,6 +483,11 @@ class Simulation3D:
 
     def set_chunk(self, chunk: int) -> None:
         _check3(lib().pf3_set_chunk(self.h, int(chunk)), self.h)
+
+    def set_index64(self, on: bool = True) -> None:
+        """Take the 64-bit index form of the periodic step at any size
+        (otherwise 32-bit while the state planes fit; results are identical)."""
+        _check3(lib().pf3_set_index64(self.h, int(bool(on))), self.h)
 
     def step(self, n: int = 1) -> None:
         _check3(lib().pf3_step(self.h, int(n)), self.h)
