@@ -32,6 +32,17 @@ __device__ __forceinline__ const T* pl(const T* p, int k, unsigned ps) { return 
 template <typename T>
 __device__ __forceinline__ T* pl(T* p, int k, unsigned ps) { return p + (unsigned)k * ps; }
 
+// Index offset from coordinate v (in [0, n)) to v - c, c in {-1, 0, 1}, with one
+// periodic wrap, times the axis stride. Added to a site index in the unsigned
+// type I, a negative offset wraps modulo 2^bits and the sum is the exact
+// neighbour index.
+template <typename I>
+__device__ __forceinline__ I step_off(int c, int v, int n, I stride) {
+  if (c == 0) return I(0);
+  const int d = c > 0 ? (v == 0 ? n - 1 : -1) : (v == n - 1 ? 1 - n : 1);
+  return (I)d * stride;
+}
+
 // Hint: bring the line that holds p into L2 ahead of its use (no register is
 // written, so a z-march can look two planes ahead for free).
 __device__ __forceinline__ void prefetch_l2(const void* p) {

@@ -63,8 +63,10 @@ __device__ __forceinline__ unsigned long long site3(const Args3<S, R, I>& a, int
 }
 template <typename S, typename R, typename I>
 __device__ __forceinline__ unsigned long long src7(const Args3<S, R, I>& a, int x, int y, int z, int i) {
-  // x, y in range: one step wraps
-  return site3(a, wrap1(x - cx7(i), a.nx), wrap1(y - cy7(i), a.ny), wrap1(z - cz7(i), a.nz));
+  // x, y, z in range: the own index plus one offset per axis (one step wraps)
+  const I own = (I)site3(a, x, y, z);
+  return own + d3::step_off<I>(cx7(i), x, a.nx, I(1)) + d3::step_off<I>(cy7(i), y, a.ny, (I)a.nx) +
+         d3::step_off<I>(cz7(i), z, a.nz, (I)a.nx * (I)a.ny);
 }
 
 // BC: pull source of direction i at (x, y, z): a source beyond a non-periodic

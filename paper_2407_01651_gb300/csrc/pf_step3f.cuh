@@ -118,14 +118,20 @@ template <typename S, typename R, typename I>
 __device__ __forceinline__ unsigned long long site_of(const ArgsF<S, R, I>& a, int x, int y, int z) {
   return ((I)z * (I)a.ny + (I)y) * (I)a.nx + (I)x;
 }
-// pull source of D3Q19 direction i (x, y in range; one step wraps)
+// pull source of D3Q19 direction i (x, y, z in range; one step wraps)
+// (the site's own index plus one offset per axis: the own index and the
+// offsets are shared by all directions)
 template <typename S, typename R, typename I>
 __device__ __forceinline__ unsigned long long src19(const ArgsF<S, R, I>& a, int x, int y, int z, int i) {
-  return site_of(a, wrap1(x - c19(i, 0), a.nx), wrap1(y - c19(i, 1), a.ny), wrap1(z - c19(i, 2), a.nz));
+  const I own = (I)site_of(a, x, y, z);
+  return own + d3::step_off<I>(c19(i, 0), x, a.nx, I(1)) + d3::step_off<I>(c19(i, 1), y, a.ny, (I)a.nx) +
+         d3::step_off<I>(c19(i, 2), z, a.nz, (I)a.nx * (I)a.ny);
 }
 template <typename S, typename R, typename I>
 __device__ __forceinline__ unsigned long long src7(const ArgsF<S, R, I>& a, int x, int y, int z, int i) {
-  return site_of(a, wrap1(x - cx7(i), a.nx), wrap1(y - cy7(i), a.ny), wrap1(z - cz7(i), a.nz));
+  const I own = (I)site_of(a, x, y, z);
+  return own + d3::step_off<I>(cx7(i), x, a.nx, I(1)) + d3::step_off<I>(cy7(i), y, a.ny, (I)a.nx) +
+         d3::step_off<I>(cz7(i), z, a.nz, (I)a.nx * (I)a.ny);
 }
 
 // D3Q19 index of the velocity (cx, cy, cz)
