@@ -163,6 +163,11 @@ __device__ __forceinline__ R supersat3(const Coef3<R>& c, R C, R psi) {
   return (R(2) * C * frcp(A) - R(1)) * c.inv_omk;
 }
 
+// Resident CTAs per SM of k_step3d: three for the FP32 isothermal aligned-grain
+// form with 32-bit indices (56 registers, no spills), else two (80 registers).
+template <typename R, bool TH, bool ROT, typename I>
+constexpr int ctas3d() { return (!TH && !ROT && sizeof(R) == 4 && sizeof(I) == 4) ? 3 : 2; }
+
 // TH: the temperature lattice of Appendix B on D3Q7 (rho H conserved, theta =
 // H / c_p + (c_p^s/c_p) h(psi)), F(U) = 1/Le + M c_inf [1 + (1-k) U] in the
 // relaxation of psi, and the source Q / F + W0^2 / F^2 grad F . (a_s^2 grad psi
@@ -172,7 +177,7 @@ __device__ __forceinline__ R supersat3(const Coef3<R>& c, R C, R psi) {
 // BC: non-periodic sides (pull7, ghost_coord): ghost ring columns and planes
 // take the mirror site's psi (and U), mapped to 2 X_far - X across a far side.
 template <typename S, typename R, bool TH, bool ROT, bool BC, typename I = unsigned long long>
-__global__ void __launch_bounds__(THREADS, 2) k_step3d(Args3<S, R, I> a) {
+__global__ void __launch_bounds__(THREADS, (ctas3d<R, TH, ROT, I>())) k_step3d(Args3<S, R, I> a) {
   __shared__ R ring[4][HY][HX];
   __shared__ R uring[TH ? 4 : 1][HY][HX];
   const int t = threadIdx.x;
