@@ -777,7 +777,7 @@ def main() -> None:
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sim.set_fields(0, *in_np)
+        sim.set_fields_stack(0, in_np)
         sim.step(args.steps)
         sim.fields(0, ("phi", "psi", "C", "p", "vx", "vy"), out=out_np)
         t1 = time.perf_counter()

@@ -185,8 +185,13 @@ pf_status pf_create(const pf_params *p, const pf_domain *doms, int n_doms,
 pf_status pf_init_fields(pf_handle *h, int dom, const pf_init_spec *spec);
 
 /* Initialise domain dom from macroscopic fields (host, FP64, n = nx*ny each):
- * fields6 = [phi, psi, C, vx, vy, p] planes; theta (per-site grain angle) may
- * be NULL for 0.  Populations are set to their equilibria. */
+ * fields6 = [phi, psi, C, vx, vy, p] planes, one contiguous block of 6 n
+ * doubles (page-locked host memory gives the fastest copy); theta (per-site
+ * grain angle) may be NULL for 0.  Populations are set to their equilibria.
+ * Non-finite values are detected on the device while the equilibria are
+ * written: the call then returns BAD_ARG and the domain counts as not
+ * initialised until it is set again.  Synchronises the stream.
+ * Errors: BAD_ARG, OOM, CUDA. */
 pf_status pf_set_fields(pf_handle *h, int dom, const double *fields6, const double *theta,
                         size_t n);
 
@@ -304,13 +309,14 @@ long long pf_launch_count(const pf_handle *h);
  *               order as pf_reduce).  cuda_stream: stream for the work.
  * Scratch: a fixed file-scope device array of 1.5 MiB (16384 records of 12
  * doubles) that every GPU loading the library holds until exit; lattices of
- * more than 67,108,864 sites are rejected with PF_ERR_BAD_ARG.  The first call
- * on each device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  Calls share the array:
- * calls that overlap on the GPU (other streams, other threads) race.  Nothing
- * in it needs clearing, since every record read is written by the same call.
- * Synchronises the stream.  Errors (message in pf_last_error(NULL)): BAD_ARG,
- * CUDA. */
+ * more than 67,108,864 sites are rejected with PF_ERR_BAD_ARG.  Every call
+ * looks up the array's device address in the current context
+ * (cudaGetSymbolAddress, no allocation).  Calls share the array: calls that
+ * overlap on the GPU (other streams, other threads) race.  Nothing in it needs
+ * clearing, since every record read is written by the same call.  The call
+ * copies its result to host memory and synchronises the stream, so it cannot
+ * be made while the stream is being captured into a CUDA graph.  Errors
+ * (message in pf_last_error(NULL)): BAD_ARG, CUDA. */
 pf_status pf_reduce_noalloc(const void *fields, int fields_fp64, long long plane_stride,
                             long long offset, int nx, int ny, const pf_probe *probe,
                             pf_diag *out, void *cuda_stream);

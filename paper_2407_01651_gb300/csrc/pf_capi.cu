@@ -494,7 +494,7 @@ extern "C" long long pf_launch_count(const pf_handle* h) { return h ? h->launche
 static pf_status check_device_error(pf_handle* h) {
   unsigned int bits = 0;
   PF_CUDA(h, cudaMemcpy(&bits, h->d_err, sizeof(bits), cudaMemcpyDeviceToHost));
-  if (bits & 1u)
+  if (bits & ERR_STAGED_TIMEOUT)
     return fail(h, PF_ERR_TIMEOUT,
                 "staged step: a bulk copy of an input row did not complete within 1 s; the "
                 "state is invalid");
@@ -632,6 +632,7 @@ static pf_status set_fields_t(pf_handle* h, int dom, const double* d_f6, const u
   a.kp = make_kparams<R>(h->p);
   a.thermal = h->thermal;
   a.theta0 = h->p.theta0;
+  a.err = h->d_err;
   PF_CUDA(h, launch_set_fields<S, R>(a, h->stream));
   h->launches++;
   return PF_OK;
@@ -644,8 +645,9 @@ extern "C" pf_status pf_set_fields(pf_handle* h, int dom, const double* fields6,
     return fail(h, PF_ERR_BAD_ARG, "bad domain index or NULL fields");
   const size_t nn = (size_t)h->ddesc[dom].nx * h->ddesc[dom].ny;
   if (n != nn) return fail(h, PF_ERR_BAD_ARG, "n must equal nx*ny of the domain");
-  for (size_t i = 0; i < 6 * nn; ++i)
-    if (!std::isfinite(fields6[i])) return fail(h, PF_ERR_BAD_ARG, "non-finite field value");
+  // The six planes are checked for non-finite values on the device, by the
+  // kernel that writes the equilibria (a host scan of 6 n doubles on one
+  // thread cost more than the copy itself).
   // grain angles: distinct values -> ids
   std::vector<uint8_t> ids;
   std::vector<double> angles;
@@ -668,7 +670,7 @@ extern "C" pf_status pf_set_fields(pf_handle* h, int dom, const double* fields6,
   if (st != PF_OK) return st;
   st = upload_grain_table(h, dom, angles);
   if (st != PF_OK) return st;
-  st = ensure_staging(h, 7 * nn);  // 6 x n doubles + n grain ids
+  st = ensure_staging(h, 6 * nn + (theta ? (nn + 7) / 8 : 0));  // 6 x n doubles (+ n grain ids)
   if (st != PF_OK) return st;
   double* buf = h->staging;
   uint8_t* d_ids = nullptr;
@@ -682,7 +684,17 @@ extern "C" pf_status pf_set_fields(pf_handle* h, int dom, const double* fields6,
     return set_fields_t<S, R>(h, dom, buf, d_ids);
   });
   if (st != PF_OK) return st;
+  unsigned int bits = 0;
+  PF_CUDA(h, cudaMemcpyAsync(&bits, h->d_err, sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (bits & ERR_NONFINITE_INPUT) {
+    // the domain's state now holds the rejected values: it must be set again
+    h->inited[dom] = 0;
+    pf_status c = clear_device_error(h);
+    if (c != PF_OK) return c;
+    PF_CUDA(h, cudaStreamSynchronize(h->stream));
+    return fail(h, PF_ERR_BAD_ARG, "non-finite field value; the domain must be initialised again");
+  }
   return finish_init(h, dom);
 }
 

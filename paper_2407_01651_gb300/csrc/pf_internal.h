@@ -71,7 +71,12 @@ struct SetFieldsArgs {
   KParams<R> kp;
   int thermal;               // also initialise the temperature lattice at theta0
   double theta0;
+  unsigned int* err;         // device error bits: ERR_NONFINITE_INPUT set on a non-finite value
 };
+
+// Device error bits (pf_handle::d_err).
+constexpr unsigned int ERR_STAGED_TIMEOUT = 1u;   // a staged bulk copy did not complete
+constexpr unsigned int ERR_NONFINITE_INPUT = 2u;  // pf_set_fields met a non-finite value
 
 template <typename R>
 struct ReduceArgs {

@@ -162,9 +162,14 @@ __global__ void k_set_fields(SetFieldsArgs<S, R> a) {
        i += (long long)gridDim.x * blockDim.x) {
     const long long site = d.off + i;
     const double* F = a.f6;
-    write_equilibrium<S, R>(a.out, a.aout, a.fields, a.plane_stride, site, F[i], F[n + i],
-                            F[2 * n + i], F[3 * n + i], F[4 * n + i], F[5 * n + i], a.kp,
-                            a.thermal, a.theta0);
+    const double v0 = F[i], v1 = F[n + i], v2 = F[2 * n + i], v3 = F[3 * n + i],
+                 v4 = F[4 * n + i], v5 = F[5 * n + i];
+    // the host reads this bit after the launch and rejects the fields
+    if (!isfinite(v0) || !isfinite(v1) || !isfinite(v2) || !isfinite(v3) || !isfinite(v4) ||
+        !isfinite(v5))
+      atomicOr(a.err, ERR_NONFINITE_INPUT);
+    write_equilibrium<S, R>(a.out, a.aout, a.fields, a.plane_stride, site, v0, v1, v2, v3, v4,
+                            v5, a.kp, a.thermal, a.theta0);
     a.grain[site] = a.grain_ids ? a.grain_ids[i] : (uint8_t)0;
   }
 }

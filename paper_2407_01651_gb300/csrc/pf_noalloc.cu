@@ -15,7 +15,6 @@
 // partial record of 12 doubles; at most 16384 blocks, i.e. 67,108,864 sites
 // per call (an 8192 x 8192 lattice), 1.5 MiB of device memory.
 #include <cstring>
-#include <mutex>
 
 #include "../../include/pf.h"
 #include "pf_internal.h"
@@ -27,13 +26,9 @@ constexpr int kSitesPerThread = 16;
 constexpr int kSitesPerBlock = kThreads * kSitesPerThread;
 constexpr int kMaxBlocks = 16384;
 constexpr long long kMaxSites = (long long)kMaxBlocks * kSitesPerBlock;
-constexpr int kMaxDevices = 64;
 
 // partial records of every block, then the final record
 static __device__ __align__(256) double g_noalloc_scratch[(kMaxBlocks + 1) * pf::NDIAG];
-
-std::mutex g_setup_mutex;
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 __device__ __forceinline__ double wrap_offset(double d, double L) {
   d = fmod(d, L);
@@ -113,31 +108,20 @@ __global__ void k_noalloc_final(double* __restrict__ scratch, int nblocks) {
   scratch[kMaxBlocks * pf::NDIAG + q] = acc;
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the host-side name of a __device__ array is not its address).
-pf_status scratch_for_current_device(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) {
-    pf::set_global_error(std::string("pf_reduce_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
+// Device address of the scratch array in the current context.  The host-side
+// name of a __device__ array is not its address, and the address belongs to
+// the module loaded into the current context: a context that was reset and
+// re-created may place it elsewhere.  So it is looked up on every call (a host
+// lookup; it allocates nothing) instead of being cached per device.
+pf_status scratch_for_current_context(double** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    pf::set_global_error(std::string("pf_reduce_noalloc: cudaGetSymbolAddress: ") +
+                         cudaGetErrorString(e));
     return PF_ERR_CUDA;
   }
-  if (dev < 0 || dev >= kMaxDevices) {
-    pf::set_global_error("pf_reduce_noalloc: device index beyond 63");
-    return PF_ERR_BAD_ARG;
-  }
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      pf::set_global_error(std::string("pf_reduce_noalloc: cudaGetSymbolAddress: ") +
-                           cudaGetErrorString(e));
-      return PF_ERR_CUDA;
-    }
-    g_scratch_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  *out = static_cast<double*>(p);
   return PF_OK;
 }
 
@@ -165,7 +149,7 @@ extern "C" pf_status pf_reduce_noalloc(const void* fields, int fields_fp64, long
     return PF_ERR_BAD_ARG;
   }
   double* scratch = nullptr;
-  pf_status st = scratch_for_current_device(&scratch);
+  pf_status st = scratch_for_current_context(&scratch);
   if (st != PF_OK) return st;
   cudaStream_t stream = (cudaStream_t)cuda_stream;
   const int nblocks = (int)((n + kSitesPerBlock - 1) / kSitesPerBlock);

@@ -301,10 +301,24 @@ class Simulation:
         _check(lib().pf_init_fields(self.h, dom, ctypes.byref(spec)), self.h)
 
     def set_fields(self, dom: int, phi, psi, C, vx=None, vy=None, p=None, theta=None) -> None:
+        """Initialise a domain from its macroscopic fields ([ny][nx] each;
+        vx, vy, p default to 0).  Separate arrays are stacked into one block
+        first; set_fields_stack passes a ready block without that copy."""
         nx, ny = self.domains[dom]
         z = np.zeros((ny, nx))
         f6 = np.ascontiguousarray(np.stack([np.asarray(a if a is not None else z, dtype=np.float64)
                                             .reshape(ny, nx) for a in (phi, psi, C, vx, vy, p)]))
+        self.set_fields_stack(dom, f6, theta)
+
+    def set_fields_stack(self, dom: int, f6: np.ndarray, theta=None) -> None:
+        """Initialise a domain from one C-contiguous float64 block of shape
+        (6, ny, nx) holding phi, psi, C, vx, vy, p.  The block's memory is
+        handed to pf_set_fields as it is (no copy on the host), so a block in
+        page-locked memory is copied to the device at full link speed."""
+        nx, ny = self.domains[dom]
+        if (not isinstance(f6, np.ndarray) or f6.dtype != np.float64 or f6.shape != (6, ny, nx)
+                or not f6.flags["C_CONTIGUOUS"]):
+            raise ValueError(f"f6 must be a C-contiguous float64 array of shape (6, {ny}, {nx})")
         th = None if theta is None else np.ascontiguousarray(
             np.broadcast_to(np.asarray(theta, dtype=np.float64), (ny, nx)))
         _check(lib().pf_set_fields(self.h, dom, _dp(f6), _dp(th) if th is not None else None,

@@ -204,6 +204,45 @@ def test_set_fields_with_grain_angles_matches_oracle():
     compare_fields(o, sim, 1e-11)
 
 
+def test_set_fields_rejects_non_finite_values_on_the_device():
+    """pf_set_fields checks its six planes while writing the equilibria: a NaN
+    or an infinity anywhere is reported as BAD_ARG, the domain then counts as
+    uninitialised (stepping is refused), and a valid set makes it usable
+    again, equal to the oracle.  The zero-copy stack path gives the same
+    state as separate arrays."""
+    N = 24
+    par = dict(wl.BASE_PARAMS, g=0.0)
+    y, x = np.mgrid[0:N, 0:N].astype(float)
+    phi = 0.5 + 0.5 * np.tanh((np.hypot(x - 12, y - 12) - 6.0) / 2.83)
+    psi = -np.ones_like(phi)
+    C = phi.copy()
+    for prec in ("fp32", "fp64"):
+        sim = pf.Simulation([(N, N)], par, prec)
+        for bad_plane, bad in ((0, np.nan), (5, np.inf), (3, -np.inf)):
+            f6 = np.ascontiguousarray(np.stack([phi, psi, C, 0 * phi, 0 * phi, 0 * phi]))
+            f6[bad_plane, 7, 11] = bad
+            with pytest.raises(pf.PFError) as e:
+                sim.set_fields_stack(0, f6)
+            assert e.value.code == pf.PF_ERR_BAD_ARG
+            assert "non-finite" in str(e.value)
+            with pytest.raises(pf.PFError) as e:
+                sim.step(1)
+            assert e.value.code == pf.PF_ERR_STATE
+        f6 = np.ascontiguousarray(np.stack([phi, psi, C, 0 * phi, 0 * phi, 0 * phi]))
+        sim.set_fields_stack(0, f6)
+        s_stack = sim.get_state(0)
+        sim.set_fields(0, phi, psi, C)
+        assert np.array_equal(sim.get_state(0), s_stack)
+        sim.step(3)
+        o = oracle.Oracle(N, N, par)
+        o.init_fields(phi, psi, C)
+        o.step(3)
+        compare_fields(o, sim, 1e-11 if prec == "fp64" else 1e-5, names=("phi", "psi", "C"))
+        with pytest.raises(ValueError):
+            sim.set_fields_stack(0, f6[:, :, :-1])
+        sim.close()
+
+
 def test_reductions_and_laplace_probe_match_oracle():
     N, R, W = 64, 12.0, 2.0
     par = dict(wl.BASE_PARAMS, g=0.0, W_phi=W, nu=0.3)

@@ -3,7 +3,8 @@ device memory (a plugin whose host framework owns the device-memory budget, a
 loop that must not call cudaMalloc / cudaFree).  The field planes are device
 memory owned by the caller (here: a PyTorch tensor); the library uses only
 its fixed, file-scope scratch.  Checked against pf_reduce on the same fields,
-twice in a row (the scratch keeps the previous call's contents).
+twice in a row (the scratch keeps the previous call's contents), and checked
+to leave the device's free memory unchanged.
 
 Collected last on purpose: if it fails, a stop-at-first-failure run has
 already run every other test."""
@@ -37,9 +38,18 @@ def test_noalloc_reduce_matches_pf_reduce_twice(precision):
     planes = torch.tensor(np.stack([f[k] for k in pf.FIELDS[:8]]), dtype=dtype, device="cuda")
     n = lay.nx * lay.ny
     stream = torch.cuda.current_stream().cuda_stream
-    for _ in range(2):
+    torch.cuda.synchronize()
+    for call in range(2):
+        if call == 1:
+            # the second call, after the kernels are loaded, allocates nothing:
+            # neither the device's free memory nor torch's allocator moves
+            free0 = torch.cuda.mem_get_info()[0]
+            torch_bytes0 = torch.cuda.memory_allocated()
         got = pf.pf_reduce_noalloc(planes.data_ptr(), precision == "fp64", n, 0, lay.nx, lay.ny,
                                    probe, stream)
+        if call == 1:
+            assert torch.cuda.mem_get_info()[0] == free0
+            assert torch.cuda.memory_allocated() == torch_bytes0
         for k, v in ref.items():
             if k in EXACT:
                 assert got[k] == v, k
