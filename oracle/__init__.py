@@ -60,59 +60,93 @@ def build(force: bool = False) -> None:
         os.replace(tmp, out)
 
 
+def _setup_2d(lib: ctypes.CDLL) -> ctypes.CDLL:
+    """Argument and result types of the 2-D oracle's C functions."""
+    P = ctypes.c_void_p
+    D = ctypes.POINTER(ctypes.c_double)
+    lib.or_new.restype = P
+    lib.or_new.argtypes = [ctypes.c_int, ctypes.c_int]
+    lib.or_free.argtypes = [P]
+    lib.or_set_params.argtypes = [P, D]
+    lib.or_perturb_param.argtypes = [P, ctypes.c_int, ctypes.c_double]
+    lib.or_set_window.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.or_set_rho_bar.argtypes = [P, ctypes.c_double]
+    lib.or_get_rho_bar.restype = ctypes.c_double
+    lib.or_get_rho_bar.argtypes = [P]
+    lib.or_init_from_fields.argtypes = [P, D, D, D, D, D, D, D]
+    lib.or_set_orientation.argtypes = [P, D, ctypes.c_int]
+    lib.or_fields_from_spec.argtypes = [P, D, ctypes.c_int, ctypes.c_double, D,
+                                        ctypes.c_int, D, D, D]
+    lib.or_init_spec.restype = ctypes.c_int
+    lib.or_init_spec.argtypes = [P, D, ctypes.c_int, ctypes.c_double, D, ctypes.c_int]
+    lib.or_step.argtypes = [P, ctypes.c_int]
+    lib.or_get_fields.argtypes = [P, ctypes.c_uint, D]
+    lib.or_get_fields_im.argtypes = [P, ctypes.c_uint, D]
+    lib.or_get_state.argtypes = [P, D]
+    lib.or_diag.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                            ctypes.c_double, D]
+    lib.or_objective.argtypes = [P, D, D]
+    lib.or_aniso.argtypes = [ctypes.c_double] * 5 + [D]
+    lib.or_feq_ns.argtypes = [ctypes.c_double] * 4 + [D]
+    lib.or_heq_cac.argtypes = [ctypes.c_double] * 3 + [D]
+    lib.or_seq_sol.argtypes = [ctypes.c_double] * 3 + [D]
+    lib.or_collide9.argtypes = [D] * 5
+    lib.or_collide5.argtypes = [D] * 6
+    lib.or_stencil.argtypes = [D, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_int, D]
+    lib.or_derived.argtypes = [P, D]
+    lib.or_pointwise.argtypes = [P, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_double, D]
+    lib.or_mean_phi_global.restype = ctypes.c_double
+    lib.or_mean_phi_global.argtypes = [P, D, ctypes.c_int]
+    lib.or_get_steps.restype = ctypes.c_long
+    lib.or_get_steps.argtypes = [P]
+    lib.or_set_bc.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.or_state_planes.restype = ctypes.c_int
+    lib.or_state_planes.argtypes = [P]
+    lib.or_teq_th.argtypes = [ctypes.c_double] * 4 + [D]
+    lib.or_thermal_coefs.argtypes = [P, ctypes.c_double, D]
+    lib.or_thermal_totals.argtypes = [P, D]
+    return lib
+
+
 def _lib(tag: str) -> ctypes.CDLL:
     with _lock:
         if tag in _libs:
             return _libs[tag]
         build()
-        lib = ctypes.CDLL(os.path.join(_BUILD, f"liboracle_{tag}.so"))
-        P = ctypes.c_void_p
-        D = ctypes.POINTER(ctypes.c_double)
-        lib.or_new.restype = P
-        lib.or_new.argtypes = [ctypes.c_int, ctypes.c_int]
-        lib.or_free.argtypes = [P]
-        lib.or_set_params.argtypes = [P, D]
-        lib.or_perturb_param.argtypes = [P, ctypes.c_int, ctypes.c_double]
-        lib.or_set_window.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
-        lib.or_set_rho_bar.argtypes = [P, ctypes.c_double]
-        lib.or_get_rho_bar.restype = ctypes.c_double
-        lib.or_get_rho_bar.argtypes = [P]
-        lib.or_init_from_fields.argtypes = [P, D, D, D, D, D, D, D]
-        lib.or_set_orientation.argtypes = [P, D, ctypes.c_int]
-        lib.or_fields_from_spec.argtypes = [P, D, ctypes.c_int, ctypes.c_double, D,
-                                            ctypes.c_int, D, D, D]
-        lib.or_init_spec.restype = ctypes.c_int
-        lib.or_init_spec.argtypes = [P, D, ctypes.c_int, ctypes.c_double, D, ctypes.c_int]
-        lib.or_step.argtypes = [P, ctypes.c_int]
-        lib.or_get_fields.argtypes = [P, ctypes.c_uint, D]
-        lib.or_get_fields_im.argtypes = [P, ctypes.c_uint, D]
-        lib.or_get_state.argtypes = [P, D]
-        lib.or_diag.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                ctypes.c_double, D]
-        lib.or_objective.argtypes = [P, D, D]
-        lib.or_aniso.argtypes = [ctypes.c_double] * 5 + [D]
-        lib.or_feq_ns.argtypes = [ctypes.c_double] * 4 + [D]
-        lib.or_heq_cac.argtypes = [ctypes.c_double] * 3 + [D]
-        lib.or_seq_sol.argtypes = [ctypes.c_double] * 3 + [D]
-        lib.or_collide9.argtypes = [D] * 5
-        lib.or_collide5.argtypes = [D] * 6
-        lib.or_stencil.argtypes = [D, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                   ctypes.c_int, D]
-        lib.or_derived.argtypes = [P, D]
-        lib.or_pointwise.argtypes = [P, ctypes.c_double, ctypes.c_double,
-                                     ctypes.c_double, D]
-        lib.or_mean_phi_global.restype = ctypes.c_double
-        lib.or_mean_phi_global.argtypes = [P, D, ctypes.c_int]
-        lib.or_get_steps.restype = ctypes.c_long
-        lib.or_get_steps.argtypes = [P]
-        lib.or_set_bc.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
-        lib.or_state_planes.restype = ctypes.c_int
-        lib.or_state_planes.argtypes = [P]
-        lib.or_teq_th.argtypes = [ctypes.c_double] * 4 + [D]
-        lib.or_thermal_coefs.argtypes = [P, ctypes.c_double, D]
-        lib.or_thermal_totals.argtypes = [P, D]
+        lib = _setup_2d(ctypes.CDLL(os.path.join(_BUILD, f"liboracle_{tag}.so")))
         _libs[tag] = lib
         return lib
+
+
+def mutant(source: str, edits, tmpdir: str) -> ctypes.CDLL:
+    """A copy of one oracle source with a mistake planted in it, compiled
+    like the oracle itself, for tests that check that a pin catches that
+    mistake.  source: "pf_oracle.c" or "pf_oracle3d.c"; edits: (old, new)
+    text pairs, each old text present exactly once; tmpdir: where the copy
+    and its library go.  Returns the library with the argument types of the
+    source's functions set; pass it as ``lib=`` to Oracle / Oracle3D /
+    Oracle3F.  The oracle's own builds are never modified."""
+    with open(os.path.join(_HERE, source)) as fh:
+        text = fh.read()
+    for old, new in edits:
+        if text.count(old) != 1:
+            raise ValueError(f"edit target must occur exactly once in {source}: {old!r}")
+        text = text.replace(old, new)
+    # one file name per planted text: the loader caches libraries by path
+    import hashlib
+    tag = hashlib.sha256(text.encode()).hexdigest()[:16]
+    src = os.path.join(tmpdir, f"mutant_{tag}_{source}")
+    with open(src, "w") as fh:
+        fh.write(text)
+    out = src[:-2] + ".so"
+    subprocess.run(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fopenmp",
+                    "-ffp-contract=off", src, "-o", out, "-lm"], check=True)
+    lib = ctypes.CDLL(out)
+    if source == "pf_oracle.c":
+        return _setup_2d(lib)
+    return _setup_3f(_setup_3d(lib))
 
 
 def _dp(a: np.ndarray | None):
@@ -133,8 +167,8 @@ class Oracle:
     """
 
     def __init__(self, nx: int, ny: int, params: dict, complex_step: bool = False,
-                 window: tuple[int, int, int, int] | None = None):
-        self.lib = _lib("z" if complex_step else "d")
+                 window: tuple[int, int, int, int] | None = None, lib: ctypes.CDLL | None = None):
+        self.lib = lib if lib is not None else _lib("z" if complex_step else "d")
         self.nx, self.ny = int(nx), int(ny)
         self.h = self.lib.or_new(self.nx, self.ny)
         if not self.h:
@@ -332,35 +366,39 @@ PARAM_NAMES_3D = ("beta_psi", "W0", "tau0", "eps_s", "k", "D", "Omega", "grad_ep
 _lib3 = None
 
 
+def _setup_3d(lib: ctypes.CDLL) -> ctypes.CDLL:
+    """Argument and result types of the 3-D melt oracle's C functions."""
+    P, D, I = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+    lib.or3_new.restype = P
+    lib.or3_new.argtypes = [I, I, I]
+    lib.or3_free.argtypes = [P]
+    lib.or3_set_params.argtypes = [P, D]
+    lib.or3_init.argtypes = [P, D, I, ctypes.c_double]
+    lib.or3_init_fields.argtypes = [P, D, D]
+    lib.or3_step.argtypes = [P, I]
+    lib.or3_fields.argtypes = [P, D]
+    lib.or3_state.argtypes = [P, D]
+    lib.or3_aniso.argtypes = [D, ctypes.c_double, ctypes.c_double, D]
+    lib.or3_collide7.argtypes = [D] * 6
+    lib.or3_grad.argtypes = [D, I, I, I, I, I, I, D]
+    lib.or3_set_window.argtypes = [P, I, I, I, I, I, I]
+    lib.or3_init_fields.argtypes = [P, D, D, D]
+    lib.or3_state_planes.restype = I
+    lib.or3_state_planes.argtypes = [P]
+    lib.or3_thermal_totals.argtypes = [P, D]
+    lib.or3_set_orientation.argtypes = [P, D, I]
+    lib.or3_set_orientation.restype = I
+    lib.or3_set_bc.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
+    lib.or3_orientation.argtypes = [P, I, D]
+    return lib
+
+
 def _l3() -> ctypes.CDLL:
     global _lib3
     with _lock:
         if _lib3 is None:
             build()
-            lib = ctypes.CDLL(os.path.join(_BUILD, "liboracle_3d.so"))
-            P, D, I = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
-            lib.or3_new.restype = P
-            lib.or3_new.argtypes = [I, I, I]
-            lib.or3_free.argtypes = [P]
-            lib.or3_set_params.argtypes = [P, D]
-            lib.or3_init.argtypes = [P, D, I, ctypes.c_double]
-            lib.or3_init_fields.argtypes = [P, D, D]
-            lib.or3_step.argtypes = [P, I]
-            lib.or3_fields.argtypes = [P, D]
-            lib.or3_state.argtypes = [P, D]
-            lib.or3_aniso.argtypes = [D, ctypes.c_double, ctypes.c_double, D]
-            lib.or3_collide7.argtypes = [D] * 6
-            lib.or3_grad.argtypes = [D, I, I, I, I, I, I, D]
-            lib.or3_set_window.argtypes = [P, I, I, I, I, I, I]
-            lib.or3_init_fields.argtypes = [P, D, D, D]
-            lib.or3_state_planes.restype = I
-            lib.or3_state_planes.argtypes = [P]
-            lib.or3_thermal_totals.argtypes = [P, D]
-            lib.or3_set_orientation.argtypes = [P, D, I]
-            lib.or3_set_orientation.restype = I
-            lib.or3_set_bc.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
-            lib.or3_orientation.argtypes = [P, I, D]
-            _lib3 = lib
+            _lib3 = _setup_3d(ctypes.CDLL(os.path.join(_BUILD, "liboracle_3d.so")))
     return _lib3
 
 
@@ -368,8 +406,9 @@ class Oracle3D:
     """Periodic nx x ny x nz lattice of the 3-D dendrite model (psi and C on
     D3Q7, no gas, no flow).  Arrays are [z][y][x]."""
 
-    def __init__(self, nx: int, ny: int, nz: int, params: dict, window=None):
-        self.lib = _l3()
+    def __init__(self, nx: int, ny: int, nz: int, params: dict, window=None,
+                 lib: ctypes.CDLL | None = None):
+        self.lib = lib if lib is not None else _l3()
         self.shape = (int(nz), int(ny), int(nx))
         self.h = self.lib.or3_new(int(nx), int(ny), int(nz))
         if not self.h:
@@ -464,40 +503,45 @@ FIELDS_3F = ("phi", "psi", "C", "U", "p", "vx", "vy", "vz", "mu", "theta")
 _lib3f = None
 
 
+def _setup_3f(lib: ctypes.CDLL) -> ctypes.CDLL:
+    """Argument and result types of the 3-D two-phase oracle's C functions."""
+    P, D, I = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+    lib.or3f_new.restype = P
+    lib.or3f_new.argtypes = [I, I, I]
+    lib.or3f_free.argtypes = [P]
+    lib.or3f_set_params.argtypes = [P, D]
+    lib.or3f_set_window.argtypes = [P, I, I, I, I, I, I]
+    lib.or3f_set_rho_bar.argtypes = [P, ctypes.c_double]
+    lib.or3f_get_rho_bar.argtypes = [P]
+    lib.or3f_get_rho_bar.restype = ctypes.c_double
+    lib.or3f_init_fields.argtypes = [P, D, D, D, D, D, D, D]
+    lib.or3f_fields_from_spec.argtypes = [P, D, I, ctypes.c_double, D, I, D, D, D]
+    lib.or3f_mean_phi_global.argtypes = [P, D, I]
+    lib.or3f_mean_phi_global.restype = ctypes.c_double
+    lib.or3f_init_spec.argtypes = [P, D, I, ctypes.c_double, D, I]
+    lib.or3f_step.argtypes = [P, I]
+    lib.or3f_fields.argtypes = [P, D]
+    lib.or3f_state.argtypes = [P, D]
+    lib.or3f_totals.argtypes = [P, D]
+    lib.or3f_basis.argtypes = [D, D, ctypes.POINTER(ctypes.c_int)]
+    lib.or3f_collide19.argtypes = [D] * 5
+    lib.or3f_feq.argtypes = [ctypes.c_double, ctypes.c_double, D, D]
+    lib.or3f_set_orientation.argtypes = [P, D, I]
+    lib.or3f_set_orientation.restype = I
+    lib.or3f_set_temperature.argtypes = [P, D]
+    lib.or3f_set_bc.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
+    lib.or3f_thermal_totals.argtypes = [P, D]
+    lib.or3f_state_planes.argtypes = [P]
+    lib.or3f_state_planes.restype = I
+    return lib
+
+
 def _l3f() -> ctypes.CDLL:
     global _lib3f
     lib = _l3()                          # takes the module lock itself
     with _lock:
         if _lib3f is None:
-            P, D, I = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
-            lib.or3f_new.restype = P
-            lib.or3f_new.argtypes = [I, I, I]
-            lib.or3f_free.argtypes = [P]
-            lib.or3f_set_params.argtypes = [P, D]
-            lib.or3f_set_window.argtypes = [P, I, I, I, I, I, I]
-            lib.or3f_set_rho_bar.argtypes = [P, ctypes.c_double]
-            lib.or3f_get_rho_bar.argtypes = [P]
-            lib.or3f_get_rho_bar.restype = ctypes.c_double
-            lib.or3f_init_fields.argtypes = [P, D, D, D, D, D, D, D]
-            lib.or3f_fields_from_spec.argtypes = [P, D, I, ctypes.c_double, D, I, D, D, D]
-            lib.or3f_mean_phi_global.argtypes = [P, D, I]
-            lib.or3f_mean_phi_global.restype = ctypes.c_double
-            lib.or3f_init_spec.argtypes = [P, D, I, ctypes.c_double, D, I]
-            lib.or3f_step.argtypes = [P, I]
-            lib.or3f_fields.argtypes = [P, D]
-            lib.or3f_state.argtypes = [P, D]
-            lib.or3f_totals.argtypes = [P, D]
-            lib.or3f_basis.argtypes = [D, D, ctypes.POINTER(ctypes.c_int)]
-            lib.or3f_collide19.argtypes = [D] * 5
-            lib.or3f_feq.argtypes = [ctypes.c_double, ctypes.c_double, D, D]
-            lib.or3f_set_orientation.argtypes = [P, D, I]
-            lib.or3f_set_orientation.restype = I
-            lib.or3f_set_temperature.argtypes = [P, D]
-            lib.or3f_set_bc.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
-            lib.or3f_thermal_totals.argtypes = [P, D]
-            lib.or3f_state_planes.argtypes = [P]
-            lib.or3f_state_planes.restype = I
-            _lib3f = lib
+            _lib3f = _setup_3f(lib)
     return _lib3f
 
 
@@ -506,8 +550,9 @@ class Oracle3F:
     D3Q19, psi and C on D3Q7, coupled as in 2-D.  Arrays are [z][y][x]; seeds
     are (x, y, z), bubbles (x, y, z, R)."""
 
-    def __init__(self, nx: int, ny: int, nz: int, params: dict, window=None):
-        self.lib = _l3f()
+    def __init__(self, nx: int, ny: int, nz: int, params: dict, window=None,
+                 lib: ctypes.CDLL | None = None):
+        self.lib = lib if lib is not None else _l3f()
         self.shape = (int(nz), int(ny), int(nx))
         self.h = self.lib.or3f_new(int(nx), int(ny), int(nz))
         if not self.h:

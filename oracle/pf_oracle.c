@@ -15,8 +15,8 @@
  * There is no blocking, no fusion and no reordering of the arithmetic beyond
  * what the formulas state.  Where the paper leaves a choice open (the CAC,
  * Navier-Stokes and solute LB models are only cited, the drag force and the
- * time-stretch realisation are not spelled out), this file follows the written
- * readings R1..R24 of the design document; each is cited where it is used.
+ * time-stretch realisation are not spelled out), this file takes one reading
+ * per open point, numbered R1..R32; each is stated where it is used.
  *
  * Compiled twice from this one source:
  *   real_t = double                          -> liboracle_d.so

@@ -1,0 +1,108 @@
+"""Mistakes planted in copies of the oracle, each of which a pin must catch.
+
+The oracle's own builds are never touched: oracle.mutant() copies a source,
+applies one text edit and compiles the copy into a temporary directory.  Each
+case names the passage the edit breaks and the pin measurement that catches
+it (tests/pin_cases.py).  A pin that a plausible mistake survives is not a
+pin, so these cases keep the pins honest as the oracle changes.
+"""
+import pytest
+
+import oracle
+import pin_cases
+from test_oracle_twin import TOL as TWIN_TOL
+from test_oracle_twin import twin_error
+
+# 2-D oracle (pf_oracle.c)
+STRETCH_2D = "st->gS[i][idx] = gold + (gsrc - gold) * st->rr[src];"
+RATE_2D = "st->nrr[idx] = 1.0 / as2;"
+FM_2D = ("const real_t Fmx = (rl - rg) * (divD * vxo + Dx * dvxx + Dy * dvxy);\n"
+         "      const real_t Fmy = (rl - rg) * (divD * vyo + Dx * dvyx + Dy * dvyy);")
+# 3-D oracles (pf_oracle3d.c): the melt step and the two-phase step each
+# carry their own stretch, told apart by the lines around them
+STRETCH_3D = ("/* far field: anti-bounce-back -f*_opp + 2 w_i X_far (psi -1, C 1) */\n"
+              "          const real gsrc = mode == 2 ? -st->gpost[q][src] + 2.0 * W7[i] * (-1.0)"
+              " : st->gpost[q][src];\n"
+              "          st->gS[i][id] = gold + (gsrc - gold) * st->rr[src];")
+RATE_3D = ("(tau0 * CS2_7) + 0.5);\n"
+           "          const real S[7] = {1, s1, s1, s1, 1, 1, 1};\n"
+           "          collide7(gg, geq, S, G, Fd, out);\n"
+           "          for (int i = 0; i < 7; ++i) { st->ngpost[i][id] = out[i];"
+           " st->ngpre[i][id] = gg[i]; }\n"
+           "          st->nrr[id] = 1.0 / as2;")
+STRETCH_3F = ("          if (refl) src = idx3f(st, x, y, z);\n"
+              "          const real gold = st->gpre[i][id];\n"
+              "          const real gsrc = mode == 2 ? -st->gpost[q][src] + 2.0 * W7[i] * (-1.0)"
+              " : st->gpost[q][src];\n"
+              "          st->gS[i][id] = gold + (gsrc - gold) * st->rr[src];")
+FM_3F = ("const double Fm = (rl - rg) * (divD * vo[a] + Dm[0] * dv[a][0] + Dm[1] * dv[a][1]"
+         " + Dm[2] * dv[a][2]);")
+
+CASES = {
+    # Appendix B time stretch t + a_s^2 dt (Eq. eq-AnACE: tau0 a_s^2 d psi/dt)
+    "2d: no time stretch": ("pf_oracle.c", [(STRETCH_2D, STRETCH_2D.replace(
+        " * st->rr[src]", " * 1.0"))], "stretch", "2d"),
+    "2d: stretch a_s instead of a_s^2": ("pf_oracle.c", [(RATE_2D, RATE_2D.replace(
+        "/ as2", "/ as"))], "stretch", "2d"),
+    "3d melt: no time stretch": ("pf_oracle3d.c", [(STRETCH_3D, STRETCH_3D.replace(
+        " * st->rr[src]", " * 1.0"))], "stretch", "3d"),
+    "3d melt: stretch a_s instead of a_s^2": ("pf_oracle3d.c", [(RATE_3D, RATE_3D.replace(
+        "/ as2;", "/ sqrt(as2);"))], "stretch", "3d"),
+    "3d two-phase: no time stretch": ("pf_oracle3d.c", [(STRETCH_3F, STRETCH_3F.replace(
+        " * st->rr[src]", " * 1.0"))], "stretch", "3f"),
+    # Section 2.2 mass-consistent momentum flux m = rho v - D (rho_l - rho_g)
+    "2d: no mass-flux correction": ("pf_oracle.c", [(FM_2D, FM_2D.replace(
+        "(rl - rg) *", "0.0 *"))], "mass_flux", "2d"),
+    "2d: mass-flux correction without (div D) v": ("pf_oracle.c", [(FM_2D, FM_2D.replace(
+        "(divD * vxo", "(0.0 * vxo").replace("(divD * vyo", "(0.0 * vyo"))], "mass_flux", "2d"),
+    "2d: mass-flux correction of the wrong sign": ("pf_oracle.c", [(FM_2D, FM_2D.replace(
+        "= (rl - rg) *", "= -(rl - rg) *"))], "mass_flux", "2d"),
+    "3d two-phase: no mass-flux correction": ("pf_oracle3d.c", [(FM_3F, FM_3F.replace(
+        "(rl - rg) *", "0.0 *"))], "mass_flux", "3f"),
+    # mistakes in how the step is composed, caught by the per-node twin
+    "2d: stretch factor taken at the destination": ("pf_oracle.c", [(STRETCH_2D, STRETCH_2D.replace(
+        "st->rr[src]", "st->rr[idx]"))], "twin", "2d"),
+    "2d: mass-flux correction without (D . grad) v": ("pf_oracle.c", [(FM_2D, FM_2D.replace(
+        " + Dx * dvxx + Dy * dvxy", "").replace(" + Dx * dvyx + Dy * dvyy", ""))], "twin", "2d"),
+    "2d: previous psi from the streamed populations": ("pf_oracle.c", [(
+        "psio += gold;", "psio += st->gS[i][idx];")], "twin", "2d"),
+    "2d: drag force on v instead of v*": ("pf_oracle.c", [(
+        "const real_t Fx = Fpx - 2.0 * chi * rho * vsx,",
+        "const real_t Fx = Fpx - 2.0 * chi * rho * vx,")], "twin", "2d"),
+    "2d: CAC time derivative with the current velocity twice": ("pf_oracle.c", [(
+        "const real_t G1x = (phi * vx - phio * vxo)",
+        "const real_t G1x = (phi * vx - phio * vx)")], "twin", "2d"),
+}
+
+
+@pytest.fixture(scope="module")
+def mutant_dir(tmp_path_factory):
+    return str(tmp_path_factory.mktemp("oracle_mutants"))
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_planted_mistake_fails_its_pin(case, mutant_dir):
+    source, edits, pin, kind = CASES[case]
+    lib = oracle.mutant(source, edits, mutant_dir)
+    if pin == "stretch":
+        errs, _ = pin_cases.stretch_errors(kind, lib)
+        assert not pin_cases.stretch_pin_holds(errs), errs
+    elif pin == "twin":
+        err = twin_error(lib)
+        assert not err <= TWIN_TOL, err
+    else:
+        dev, _ = pin_cases.mass_flux_deviation(kind, lib)
+        assert not dev < pin_cases.MASS_FLUX_TOL, dev
+
+
+def test_the_unmodified_copy_passes():
+    """The copy-and-compile route itself changes nothing: a copy with an
+    edit that leaves the text as it is passes both pins."""
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        lib = oracle.mutant("pf_oracle.c", [(STRETCH_2D, STRETCH_2D)], d)
+        errs, _ = pin_cases.stretch_errors("2d", lib)
+        assert pin_cases.stretch_pin_holds(errs)
+        dev, _ = pin_cases.mass_flux_deviation("2d", lib)
+        assert dev < pin_cases.MASS_FLUX_TOL
+        assert twin_error(lib) <= TWIN_TOL

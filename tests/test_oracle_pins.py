@@ -14,6 +14,7 @@ import pytest
 from scipy import integrate
 
 import oracle
+import pin_cases
 from paper_2407_01651_gb300 import workload as wl
 
 CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
@@ -397,10 +398,12 @@ def test_solid_has_zero_velocity():
 
 
 def test_gas_layer_translates_with_uniform_flow():
-    """Galilean check of the CAC advection, its dt(phi v) term and the
-    mass-consistent flux m = rho v - D(phi)(rho_l - rho_g) (Section 2.2): a flat
-    gas layer in a uniform flow normal to it is carried rigidly at that speed
-    and the flow stays uniform."""
+    """Galilean check of the CAC advection and its dt(phi v) term (Eq. eq-ACE):
+    a flat gas layer in a uniform flow normal to it is carried rigidly at that
+    speed and the flow stays uniform.  A flow normal to a flat layer is held
+    uniform by incompressibility alone, so this check does not involve the
+    mass-consistent momentum flux; test_mass_consistent_flux_keeps_a_parallel_
+    flow_uniform does."""
     nx, ny, W, V = 4, 128, 2.0, 0.01
     y = np.arange(ny, dtype=float)
     phi1 = 0.5 + 0.5 * np.tanh((np.abs(y - 64.0) - 24.0) / (2 * math.sqrt(2) * W))
@@ -417,6 +420,39 @@ def test_gas_layer_translates_with_uniform_flow():
     moved = np.roll(phi1, int(V * T))          # 6 lattice units
     assert np.abs(f["phi"][:, 0] - moved).max() < 3e-3
     assert np.abs(f["phi"][:, 0] - phi1).max() > 0.1     # it did move
+
+
+def test_mass_consistent_flux_keeps_a_parallel_flow_uniform():
+    """Section 2.2: with the mass-consistent flux m = rho v - D (rho_l -
+    rho_g) / (phi_l - phi_g) in d(rho v)/dt + div(m v), a uniform velocity is
+    an exact solution whatever the gas layer does, since d rho/dt + div m = 0
+    by the CAC equation.  A flat layer started at 1.5x its equilibrium width
+    relaxes (div D != 0) in a uniform flow V parallel to it: the flow stays
+    within 2 % of V over 300 steps (measured 0.56 %); with rho v in place of
+    m it falls by 15 % where the layer's density grows."""
+    dev, vy = pin_cases.mass_flux_deviation("2d")
+    assert dev < pin_cases.MASS_FLUX_TOL
+    assert vy < 1e-5
+
+
+def test_time_stretch_follows_the_original_equation():
+    """Eq. eq-AnACE has tau0 a_s^2 d psi/dt on its left; the LB form of
+    Appendix B carries the a_s^2 by the time stretch t + a_s^2 dt.  A solid
+    slab whose fronts lie along <10> (a_s = 1 + eps_s = 1.05, N = 0) grows into
+    an undercooled melt for 1200 steps.  The oracle's psi agrees with an
+    explicit finite-difference solution of the 1-D original equations to
+    0.006 (measured 0.0027), a quarter of the distance between that solution
+    and the one with tau0 a_s (0.028): the stretch is there and has its
+    square.  Without any stretch the solutions differ by 0.056."""
+    errs, nonuniform = pin_cases.stretch_errors("2d")
+    psi0, _ = pin_cases.front_initial()
+    assert np.abs(pin_cases.front_fd(2) - psi0).max() > 0.5          # the fronts moved
+    gap = np.abs(pin_cases.front_fd(2) - pin_cases.front_fd(1)).max()
+    assert gap > 0.02
+    assert errs[2] < 0.006 and errs[2] < 0.25 * gap
+    assert pin_cases.stretch_pin_holds(errs)
+    assert errs[1] > 0.02 and errs[0] > 0.04
+    assert nonuniform < 1e-12
 
 
 @pytest.mark.parametrize("N,R,T", [(64, 10.0, 3000), (64, 14.0, 3000), (96, 16.0, 4000),
