@@ -278,6 +278,51 @@ def run_reference(args) -> None:
     print(json.dumps(line))
 
 
+def run_adjoint_ratio(torch, pf, wl, stream, n_adj: int, K: int = 100) -> dict:
+    """Adjoint / forward cost per step on the differentiation workload.
+    ratio = time of pf_adjoint_step per step (its forward sweep, the
+    recomputation from checkpoints and the reverse sweep) / time of pf_step
+    per step.  kernel_only_ratio = reverse-step kernels per step / forward
+    step per step, from an adjoint call over a single checkpoint segment (K
+    steps: a forward sweep that keeps every state, no recomputation, the
+    reverse sweep) minus its forward sweep."""
+    lay4 = wl.growth_512()
+    s4 = pf.Simulation([(lay4.nx, lay4.ny)], lay4.params, "fp32", stream=stream.cuda_stream)
+    s4.init_fields(0, lay4.seeds, lay4.R_s, lay4.bubbles)
+    cfg = s4.autotune(10)
+    s4.set_launch(0, cfg[3], 0)
+    s4.step(20)
+    s4.sync()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    ev[0].record(stream)
+    s4.step(n_adj)
+    ev[1].record(stream)
+    J, g = s4.adjoint_step(n_adj, 1.0, 1.0, K)
+    ev[2].record(stream)
+    s4.adjoint_step(K, 1.0, 1.0, K)
+    ev[3].record(stream)
+    s4.step(K)
+    ev[4].record(stream)
+    torch.cuda.synchronize()
+    t_f = ev[0].elapsed_time(ev[1]) / n_adj
+    t_a = ev[1].elapsed_time(ev[2]) / n_adj
+    t_seg = ev[2].elapsed_time(ev[3]) / K
+    t_f2 = ev[3].elapsed_time(ev[4]) / K
+    s4.close()
+    return {"workload": f"512x512, 4 seeds, 8 bubbles, FP32, {n_adj} steps, checkpoint every {K}",
+            "forward_step_config": list(cfg),
+            "forward_ms_per_step": t_f,
+            "adjoint_call_ms_per_step": t_a,
+            "ratio": t_a / t_f,
+            "ratio_def": "pf_adjoint_step time per step (forward sweep, recomputation, reverse "
+                         "sweep) / pf_step time per step",
+            "reverse_ms_per_step": t_seg - t_f2,
+            "kernel_only_ratio": (t_seg - t_f2) / t_f2,
+            "kernel_only_def": "(adjoint call over one checkpoint segment - its forward sweep) "
+                               "per step / forward step",
+            "grad": g.tolist()}
+
+
 def _time_steps(torch, sim, stream, n):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sim.sync()
@@ -793,32 +838,11 @@ def main() -> None:
                        "pf_get_fields to pinned FP64 host memory; host wall clock"}
 
     # adjoint / forward cost on the differentiation workload (512^2, 4 seeds,
-    # 8 bubbles, FP32, checkpoint every 100 steps)
+    # 8 bubbles, FP32, checkpoint every 100 steps), with the forward in its
+    # autotuned traversal (the adjoint's forward and recomputation use it too)
     adj = None
     if not args.no_adjoint and rank == 0:
-        lay4 = wl.growth_512()
-        n_adj = args.adjoint_steps
-        s4 = pf.Simulation([(lay4.nx, lay4.ny)], lay4.params, "fp32", stream=stream.cuda_stream)
-        s4.init_fields(0, lay4.seeds, lay4.R_s, lay4.bubbles)
-        s4.step(20)
-        s4.sync()
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        e0.record(stream)
-        s4.step(n_adj)
-        e1.record(stream)
-        J, g = s4.adjoint_step(n_adj, 1.0, 1.0, 100)
-        e2.record(stream)
-        torch.cuda.synchronize()
-        t_f = e0.elapsed_time(e1)
-        t_a = e1.elapsed_time(e2)
-        adj = {"workload": f"512x512, 4 seeds, 8 bubbles, FP32, {n_adj} steps, checkpoint every 100",
-               "forward_ms_per_step": t_f / n_adj,
-               "adjoint_call_ms_per_step": t_a / n_adj,
-               "ratio": (t_a - t_f) / t_f,
-               "ratio_def": "(pf_adjoint_step time - forward time) / forward time: the reverse "
-                            "sweep incl. recomputation over the forward",
-               "grad": g.tolist()}
-        s4.close()
+        adj = run_adjoint_ratio(torch, pf, wl, stream, args.adjoint_steps)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -266,8 +266,11 @@ typedef struct pf_objective {
  * discrete trajectory.  When the handle has not stepped since its
  * initialisation, the Omega-dependence of the initial lagged Q_psi is
  * included.  Single-domain handles, FP32 or FP64 storage.  Allocates a
- * workspace of (n_steps/K + K) states plus adjoint planes on first use.
- * Synchronises the stream.  Errors: BAD_ARG, STATE, OOM, CUDA. */
+ * workspace of (n_steps/K - 1 + 2 K) states plus adjoint planes on first use
+ * (n_steps/K - 1 + K states if two segment buffers do not fit; the
+ * recomputation of a segment then no longer overlaps the reverse sweep of
+ * the next, on an internal second stream).  Synchronises the stream.
+ * Errors: BAD_ARG, STATE, OOM, CUDA. */
 pf_status pf_adjoint_step(pf_handle *h, int n_steps, const pf_objective *obj, double *J_out,
                           double grad_out[3]);
 

@@ -9,10 +9,11 @@
 //                  hand-written reverse of the site update (pf_local.cuh) and
 //                  store the adjoints of its inputs (43 planes); accumulate
 //                  the parameter adjoints per block.
-//   k_adj_stencil  transpose the isotropic stencils: adjoints of the phi,
-//                  psi and lagged-velocity fields (4 planes).
-//   k_adj_gather   transpose the streaming (a gather from x + c_i) and the
-//                  a_s^2 time stretch of the dendrite lattice: lambda_t.
+//   k_adj_transpose transpose the isotropic stencils (adjoints of the phi,
+//                  psi and lagged-velocity fields, phi and psi on a tile with
+//                  a one-site ring in shared memory), the streaming (a gather
+//                  from x + c_i) and the a_s^2 time stretch of the dendrite
+//                  lattice: lambda_t.
 // Adjoint planes are in the compute precision.  The FP32 and FP64 storage
 // forms are supported.
 #include "pf_local.cuh"
@@ -59,26 +60,42 @@ __global__ void __launch_bounds__(256, 2) k_adj_local(AdjArgs<S, R> a) {
   R pe = R(0), po = R(0), psg = R(0);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int x0 = (tile % tiles_x) * ADJ_TX, y0 = (tile / tiles_x) * ADJ_TY;
-    for (int i = tid; i < (ADJ_TX + 2) * (ADJ_TY + 2); i += ADJ_TX * ADJ_TY) {
-      const int lx = i % (ADJ_TX + 2), ly = i / (ADJ_TX + 2);
+    // Each thread pulls its own site once (kept in registers for the
+    // reverse) and stores phi, psi and the lagged velocity in the tile; 84
+    // threads then pull the one-site ring around it.  Positions beyond a
+    // ragged edge hold the periodic images their neighbours read.
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const bool inside = x < d.nx && y < d.ny;
+    local::In<R> in;
+    Src9 src;
+    {
+      R phi, psi;
+      src = sources(d, x % d.nx, y % d.ny);
+      pull_hg<S, R, BIG>(st, src, in.h, in.g, phi, psi, in.psio);
+      sphi[threadIdx.y + 1][threadIdx.x + 1] = phi;
+      spsi[threadIdx.y + 1][threadIdx.x + 1] = psi;
+      svx[threadIdx.y + 1][threadIdx.x + 1] = ld<R>(st.ain + A_VXO * ps, src.s[0]);
+      svy[threadIdx.y + 1][threadIdx.x + 1] = ld<R>(st.ain + A_VYO * ps, src.s[0]);
+    }
+    if (tid < 2 * (ADJ_TX + 2) + 2 * ADJ_TY) {
+      int lx, ly;
+      if (tid < ADJ_TX + 2) { lx = tid; ly = 0; }
+      else if (tid < 2 * (ADJ_TX + 2)) { lx = tid - (ADJ_TX + 2); ly = ADJ_TY + 1; }
+      else if (tid < 2 * (ADJ_TX + 2) + ADJ_TY) { lx = 0; ly = tid - 2 * (ADJ_TX + 2) + 1; }
+      else { lx = ADJ_TX + 1; ly = tid - 2 * (ADJ_TX + 2) - ADJ_TY + 1; }
       int gx = x0 + lx - 1, gy = y0 + ly - 1;
       gx = ((gx % d.nx) + d.nx) % d.nx;
       gy = ((gy % d.ny) + d.ny) % d.ny;
       R h[9], g[5], phi, psi, pso;
-      const Src9 src = sources(d, gx, gy);
-      pull_hg<S, R, BIG>(st, src, h, g, phi, psi, pso);
+      const Src9 hs = sources(d, gx, gy);
+      pull_hg<S, R, BIG>(st, hs, h, g, phi, psi, pso);
       sphi[ly][lx] = phi;
       spsi[ly][lx] = psi;
-      svx[ly][lx] = ld<R>(st.ain + A_VXO * ps, src.s[0]);
-      svy[ly][lx] = ld<R>(st.ain + A_VYO * ps, src.s[0]);
+      svx[ly][lx] = ld<R>(st.ain + A_VXO * ps, hs.s[0]);
+      svy[ly][lx] = ld<R>(st.ain + A_VYO * ps, hs.s[0]);
     }
     __syncthreads();
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    if (x < d.nx && y < d.ny) {
-      const Src9 src = sources(d, x, y);
-      local::In<R> in;
-      R phi, psi;
-      pull_hg<S, R, BIG>(st, src, in.h, in.g, phi, psi, in.psio);
+    if (inside) {
       SiteIn<R> si;
       load_site<S, R, BIG>(st, src, si);
       for (int i = 0; i < 9; ++i) in.f[i] = si.f[i];
@@ -178,115 +195,118 @@ __global__ void __launch_bounds__(256, 2) k_adj_local(AdjArgs<S, R> a) {
   if (tid < 3) a.partial[blockIdx.x * 3 + tid] += static_cast<double>(red[tid][0]);
 }
 
-// Stencil transposes.  grad X(z) = 3 sum_j w_j c_j X(z + c_j) and
+// Transposes of the stencils, the streaming and the a_s^2 time stretch:
+// lambda_t from the per-site input adjoints (ai).  One CTA per tile of
+// ADJ_TX x ADJ_TY sites.
+//
+// Stencils: grad X(z) = 3 sum_j w_j c_j X(z + c_j) and
 // lap X(z) = 6 sum_{j>0} w_j (X(z + c_j) - X(z)) give
-//   adj X(x) += sum_j 3 w_j c_j . adj grad(x - c_j)
-//             + sum_{j>0} 6 w_j adj lap(x - c_j) - 6 (1 - w_0) adj lap(x).
-template <typename R>
-__global__ void __launch_bounds__(256) k_adj_stencil(const R* __restrict__ ai, R* __restrict__ as,
-                                                     DomDesc d, long long ps_) {
-  const unsigned ps = (unsigned)ps_;
-  const R w[9] = {R(4.0 / 9.0), R(1.0 / 9.0), R(1.0 / 9.0), R(1.0 / 9.0), R(1.0 / 9.0),
-                  R(1.0 / 36.0), R(1.0 / 36.0), R(1.0 / 36.0), R(1.0 / 36.0)};
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= d.nx) return;
-  for (int y = blockIdx.y; y < d.ny; y += gridDim.y) {
-    const Src9 src = sources(d, x, y);   // src.s[j] = x - c_j
-    const unsigned site = src.s[0];
-    R aphi = R(-6) * (R(1) - w[0]) * plane(ai, AI_LPHI, ps)[site];
-    R apsi = R(0), avx = plane(ai, AI_VXO, ps)[site], avy = plane(ai, AI_VYO, ps)[site];
-#pragma unroll
-    for (int j = 1; j < 9; ++j) {
-      const unsigned z = src.s[j];
-      const R wx = R(3) * w[j] * R(CX9[j]), wy = R(3) * w[j] * R(CY9[j]);
-      aphi += wx * plane(ai, AI_GPX, ps)[z] + wy * plane(ai, AI_GPY, ps)[z] +
-              R(6) * w[j] * plane(ai, AI_LPHI, ps)[z];
-      apsi += wx * plane(ai, AI_GSX, ps)[z] + wy * plane(ai, AI_GSY, ps)[z];
-      avx += wx * plane(ai, AI_DVXX, ps)[z] + wy * plane(ai, AI_DVXY, ps)[z];
-      avy += wx * plane(ai, AI_DVYX, ps)[z] + wy * plane(ai, AI_DVYY, ps)[z];
-    }
-    plane(as, 0, ps)[site] = aphi;
-    plane(as, 1, ps)[site] = apsi;
-    plane(as, 2, ps)[site] = avx;
-    plane(as, 3, ps)[site] = avy;
-  }
-}
-
-// Streaming and time-stretch transposes: lambda_t.
-// g_i(x) = g_pre,i(x) + r(x - c_i) [g_post,i(x - c_i) - g_pre,i(x)] and
-// psi_o(x) = sum_i g_pre,i(x).  The population of direction q leaving x lands
-// on x + c_q, the source x - c_{opp(q)} of the pull with the opposite direction.
+//   adj X(x) = sum_j 3 w_j c_j . adj grad(x - c_j)
+//            + sum_{j>0} 6 w_j adj lap(x - c_j) - 6 (1 - w_0) adj lap(x).
+// The gather below needs adj phi and adj psi at the site and at its eight
+// neighbours, so they are formed for the tile and a one-site ring in shared
+// memory first; adj vx_o and adj vy_o are needed at the site only.
+//
+// Streaming and stretch: g_i(x) = g_pre,i(x) + r(x - c_i) [g_post,i(x - c_i)
+// - g_pre,i(x)] and psi_o(x) = sum_i g_pre,i(x).  The population of direction
+// q leaving x lands on x + c_q, the source x - c_{opp(q)} of the pull with the
+// opposite direction.
 template <typename S, typename R>
-__global__ void __launch_bounds__(256) k_adj_gather(AdjArgs<S, R> a) {
+__global__ void __launch_bounds__(ADJ_TX * ADJ_TY) k_adj_transpose(AdjArgs<S, R> a) {
+  constexpr int SX = ADJ_TX + 2, SY = ADJ_TY + 2;
+  __shared__ R s_aphi[SY][SX], s_apsi[SY][SX];
   const DomDesc d = a.dom;
   const unsigned ps = (unsigned)a.step.plane_stride;
   const R* __restrict__ A = a.ai;
-  const R* __restrict__ AS = a.as;
   const S* __restrict__ P = a.step.in;
   const R* __restrict__ X = a.step.ain;
   R* __restrict__ L = a.lam_out;
   constexpr int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= d.nx) return;
-  for (int y = blockIdx.y; y < d.ny; y += gridDim.y) {
-    const Src9 src = sources(d, x, y);
-    const unsigned site = src.s[0];
-    // every input of the site first (independent loads), then the stores
-    R lf[9], lh[9], ls[5], lgpre[5], lgpost[5];
-    const R as0_dst[9] = {__ldg(plane(AS, 0, ps) + src.s[OPP[0]]),
-                          __ldg(plane(AS, 0, ps) + src.s[OPP[1]]),
-                          __ldg(plane(AS, 0, ps) + src.s[OPP[2]]),
-                          __ldg(plane(AS, 0, ps) + src.s[OPP[3]]),
-                          __ldg(plane(AS, 0, ps) + src.s[OPP[4]]),
-                          __ldg(plane(AS, 0, ps) + src.s[OPP[5]]),
-                          __ldg(plane(AS, 0, ps) + src.s[OPP[6]]),
-                          __ldg(plane(AS, 0, ps) + src.s[OPP[7]]),
-                          __ldg(plane(AS, 0, ps) + src.s[OPP[8]])};
+  const R w[9] = {R(4.0 / 9.0), R(1.0 / 9.0), R(1.0 / 9.0), R(1.0 / 9.0), R(1.0 / 9.0),
+                  R(1.0 / 36.0), R(1.0 / 36.0), R(1.0 / 36.0), R(1.0 / 36.0)};
+  const int tiles_x = (d.nx + ADJ_TX - 1) / ADJ_TX;
+  const int x0 = (blockIdx.x % tiles_x) * ADJ_TX, y0 = (blockIdx.x / tiles_x) * ADJ_TY;
+  const int tid = threadIdx.y * ADJ_TX + threadIdx.x;
+  // adj phi and adj psi on the tile and its ring (periodic images beyond the
+  // domain's edges)
+  for (int i = tid; i < SX * SY; i += ADJ_TX * ADJ_TY) {
+    const int lx = i % SX, ly = i / SX;
+    int gx = x0 + lx - 1, gy = y0 + ly - 1;
+    gx = ((gx % d.nx) + d.nx) % d.nx;
+    gy = ((gy % d.ny) + d.ny) % d.ny;
+    const Src9 src = sources(d, gx, gy);   // src.s[j] = z - c_j
+    R aphi = R(-6) * (R(1) - w[0]) * __ldg(plane(A, AI_LPHI, ps) + src.s[0]);
+    R apsi = R(0);
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      const unsigned t = src.s[OPP[q]];   // x + c_q
-      lf[q] = __ldg(plane(A, AI_F + q, ps) + t);
-      lh[q] = __ldg(plane(A, AI_H + q, ps) + t) + as0_dst[q];
+    for (int j = 1; j < 9; ++j) {
+      const unsigned z = src.s[j];
+      const R wx = R(3) * w[j] * R(CX9[j]), wy = R(3) * w[j] * R(CY9[j]);
+      aphi += wx * __ldg(plane(A, AI_GPX, ps) + z) + wy * __ldg(plane(A, AI_GPY, ps) + z) +
+              R(6) * w[j] * __ldg(plane(A, AI_LPHI, ps) + z);
+      apsi += wx * __ldg(plane(A, AI_GSX, ps) + z) + wy * __ldg(plane(A, AI_GSY, ps) + z);
     }
-    const R rr_own = __ldg(plane(X, A_RR, ps) + site);
-    const R apsio = __ldg(plane(A, AI_PSIO, ps) + site);
-    const R as1 = __ldg(plane(AS, 1, ps) + site);
-    R lrr = R(0);
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      const unsigned t = src.s[OPP[q]];   // destination of q
-      const unsigned sq = src.s[q];       // source of q
-      ls[q] = __ldg(plane(A, AI_S + q, ps) + t);
-      const R ag_own = __ldg(plane(A, AI_G + q, ps) + site) + as1;
-      const R ag_dst = __ldg(plane(A, AI_G + q, ps) + t) + __ldg(plane(AS, 1, ps) + t);
-      const R rr_src = __ldg(plane(X, A_RR, ps) + sq);
-      lgpre[q] = ag_own * (R(1) - rr_src) + apsio;
-      lgpost[q] = ag_dst * rr_own;
-      const R gq_own = ld<R>(plane(P, P_GPOST + q, ps), site);
-      const R gp_dst = ld<R>(plane(P, P_GPRE + q, ps), t);
-      lrr += ag_dst * (gq_own - gp_dst);
-    }
-    const R l34 = __ldg(plane(A, AI_PHIO, ps) + site), l35 = __ldg(plane(A, AI_CO, ps) + site);
-    const R l36 = __ldg(plane(AS, 2, ps) + site), l37 = __ldg(plane(AS, 3, ps) + site);
-    const R l38 = __ldg(plane(A, AI_QO, ps) + site);
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      plane(L, 0 + q, ps)[site] = lf[q];
-      plane(L, 9 + q, ps)[site] = lh[q];
-    }
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      plane(L, 18 + q, ps)[site] = lgpre[q];
-      plane(L, 23 + q, ps)[site] = lgpost[q];
-      plane(L, 29 + q, ps)[site] = ls[q];
-    }
-    plane(L, 28, ps)[site] = lrr;
-    plane(L, 34, ps)[site] = l34;
-    plane(L, 35, ps)[site] = l35;
-    plane(L, 36, ps)[site] = l36;
-    plane(L, 37, ps)[site] = l37;
-    plane(L, 38, ps)[site] = l38;
+    s_aphi[ly][lx] = aphi;
+    s_apsi[ly][lx] = apsi;
   }
+  __syncthreads();
+  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+  if (x >= d.nx || y >= d.ny) return;
+  const int cx = threadIdx.x + 1, cy = threadIdx.y + 1;
+  const Src9 src = sources(d, x, y);
+  const unsigned site = src.s[0];
+  // every input of the site first (independent loads), then the stores
+  R avx = __ldg(plane(A, AI_VXO, ps) + site), avy = __ldg(plane(A, AI_VYO, ps) + site);
+#pragma unroll
+  for (int j = 1; j < 9; ++j) {
+    const unsigned z = src.s[j];
+    const R wx = R(3) * w[j] * R(CX9[j]), wy = R(3) * w[j] * R(CY9[j]);
+    avx += wx * __ldg(plane(A, AI_DVXX, ps) + z) + wy * __ldg(plane(A, AI_DVXY, ps) + z);
+    avy += wx * __ldg(plane(A, AI_DVYX, ps) + z) + wy * __ldg(plane(A, AI_DVYY, ps) + z);
+  }
+  R lf[9], lh[9], ls[5], lgpre[5], lgpost[5];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    const unsigned t = src.s[OPP[q]];   // x + c_q
+    lf[q] = __ldg(plane(A, AI_F + q, ps) + t);
+    lh[q] = __ldg(plane(A, AI_H + q, ps) + t) + s_aphi[cy + CY9[q]][cx + CX9[q]];
+  }
+  const R rr_own = __ldg(plane(X, A_RR, ps) + site);
+  const R apsio = __ldg(plane(A, AI_PSIO, ps) + site);
+  const R as1 = s_apsi[cy][cx];
+  R lrr = R(0);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const unsigned t = src.s[OPP[q]];   // destination of q
+    const unsigned sq = src.s[q];       // source of q
+    ls[q] = __ldg(plane(A, AI_S + q, ps) + t);
+    const R ag_own = __ldg(plane(A, AI_G + q, ps) + site) + as1;
+    const R ag_dst = __ldg(plane(A, AI_G + q, ps) + t) + s_apsi[cy + CY9[q]][cx + CX9[q]];
+    const R rr_src = __ldg(plane(X, A_RR, ps) + sq);
+    lgpre[q] = ag_own * (R(1) - rr_src) + apsio;
+    lgpost[q] = ag_dst * rr_own;
+    const R gq_own = ld<R>(plane(P, P_GPOST + q, ps), site);
+    const R gp_dst = ld<R>(plane(P, P_GPRE + q, ps), t);
+    lrr += ag_dst * (gq_own - gp_dst);
+  }
+  const R l34 = __ldg(plane(A, AI_PHIO, ps) + site), l35 = __ldg(plane(A, AI_CO, ps) + site);
+  const R l38 = __ldg(plane(A, AI_QO, ps) + site);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    plane(L, 0 + q, ps)[site] = lf[q];
+    plane(L, 9 + q, ps)[site] = lh[q];
+  }
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    plane(L, 18 + q, ps)[site] = lgpre[q];
+    plane(L, 23 + q, ps)[site] = lgpost[q];
+    plane(L, 29 + q, ps)[site] = ls[q];
+  }
+  plane(L, 28, ps)[site] = lrr;
+  plane(L, 34, ps)[site] = l34;
+  plane(L, 35, ps)[site] = l35;
+  plane(L, 36, ps)[site] = avx;
+  plane(L, 37, ps)[site] = avy;
+  plane(L, 38, ps)[site] = l38;
 }
 
 // Adjoint of the final-state objective
@@ -342,9 +362,8 @@ cudaError_t launch_adjoint_step(const AdjArgs<S, R>& a, int grid, cudaStream_t s
     k_adj_local<S, R, true><<<grid, dim3(ADJ_TX, ADJ_TY), 0, st>>>(a);
   else
     k_adj_local<S, R, false><<<grid, dim3(ADJ_TX, ADJ_TY), 0, st>>>(a);
-  const dim3 g2((a.dom.nx + 255) / 256, std::min(a.dom.ny, 65535));
-  k_adj_stencil<R><<<g2, 256, 0, st>>>(a.ai, a.as, a.dom, a.step.plane_stride);
-  k_adj_gather<S, R><<<g2, 256, 0, st>>>(a);
+  const int tiles = ((a.dom.nx + ADJ_TX - 1) / ADJ_TX) * ((a.dom.ny + ADJ_TY - 1) / ADJ_TY);
+  k_adj_transpose<S, R><<<tiles, dim3(ADJ_TX, ADJ_TY), 0, st>>>(a);
   return cudaGetLastError();
 }
 

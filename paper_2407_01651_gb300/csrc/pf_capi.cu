@@ -70,6 +70,7 @@ struct pf_handle {
   int graph_steps = 0;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t adj_stream = nullptr;   // recomputation stream of the adjoint
   void* pop[2] = {nullptr, nullptr};   // population planes, storage type
   void* aux[2] = {nullptr, nullptr};   // lagged-scalar planes, compute type
   int cur = 0;
@@ -299,6 +300,7 @@ static void release(pf_handle* h) {
   for (auto& g : h->gexec)
     if (g) { cudaGraphExecDestroy(g); g = nullptr; }
   if (h->cap_stream) { cudaStreamDestroy(h->cap_stream); h->cap_stream = nullptr; }
+  if (h->adj_stream) { cudaStreamDestroy(h->adj_stream); h->adj_stream = nullptr; }
   if (h->side) { cudaStreamDestroy(h->side); h->side = nullptr; }
   if (h->fork_ev) { cudaEventDestroy(h->fork_ev); h->fork_ev = nullptr; }
   if (h->join_ev) { cudaEventDestroy(h->join_ev); h->join_ev = nullptr; }
@@ -933,7 +935,7 @@ static pf_status autotune_t(pf_handle* h, int trial_steps, int out[4]) {
   PF_CUDA(h, cudaMemcpyAsync(snap_a, h->aux[cur0], aux_b, cudaMemcpyDeviceToDevice, h->stream));
   struct Cand { int variant, a, b, persistent; };
   std::vector<Cand> cands;
-  for (int ch : {8, 16, 24, 32, 48, 64, 96})
+  for (int ch : {4, 8, 16, 24, 32, 48, 64, 96})
     for (int pers : {0, 1}) cands.push_back({STEP_YMARCH, ch, 0, pers});
   if (!h->thermal && !h->any_bc) {
     if (staged_ok_t<S, R>(h))
@@ -1233,43 +1235,79 @@ static pf_status adjoint_t(pf_handle* h, int n, const pf_objective* obj, double*
   const int tiles = ((dd.nx + ADJ_TX - 1) / ADJ_TX) * ((dd.ny + ADJ_TY - 1) / ADJ_TY);
   const int grid = std::max(1, std::min(tiles, 4 * std::max(sms, 1)));
   const int oblocks = 256;
-  const size_t lam_b = ps * N_PHYS * sizeof(R), ai_b = ps * N_AI * sizeof(R),
-               as_b = ps * 4 * sizeof(R);
+  const size_t lam_b = ps * N_PHYS * sizeof(R), ai_b = ps * N_AI * sizeof(R);
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-  const size_t need = (size_t)nseg * state_b + (size_t)K * state_b + 2 * up(lam_b) + up(ai_b) +
-                      up(as_b) + up((size_t)grid * 3 * sizeof(double)) +
-                      up((size_t)oblocks * sizeof(double));
-  if (need > h->adj_ws_bytes) {
+  // Workspace: a checkpoint per segment but the last, whose states the
+  // forward sweep keeps in full; two segment buffers, so that the
+  // recomputation of segment s-1 (on a second stream) overlaps the reverse
+  // sweep of segment s, or one if the device cannot hold two.
+  auto need_for = [&](int nbuf) {
+    return (size_t)(nseg - 1) * state_b + (size_t)nbuf * K * state_b + 2 * up(lam_b) +
+           up(ai_b) + up((size_t)grid * 3 * sizeof(double)) +
+           up((size_t)oblocks * sizeof(double));
+  };
+  int nbuf = nseg > 1 ? 2 : 1;
+  if (need_for(nbuf) > h->adj_ws_bytes) {
     PF_CUDA(h, cudaStreamSynchronize(h->stream));
     dev_free(h, h->adj_ws);
-    h->adj_ws = dev_alloc(h, need);
-    h->adj_ws_bytes = h->adj_ws ? need : 0;
+    h->adj_ws = nullptr;
+    h->adj_ws_bytes = 0;
+    for (; nbuf >= 1 && !h->adj_ws; --nbuf) {
+      h->adj_ws = dev_alloc(h, need_for(nbuf));
+      if (h->adj_ws) h->adj_ws_bytes = need_for(nbuf);
+      else cudaGetLastError();    // clear the failed allocation
+    }
+    ++nbuf;
     if (!h->adj_ws) return fail(h, PF_ERR_OOM, "adjoint workspace allocation failed");
   }
   char* w = static_cast<char*>(h->adj_ws);
   auto take = [&](size_t b) { char* p = w; w += up(b); return p; };
-  std::vector<char*> ck(nseg), sg(K);
-  for (int i = 0; i < nseg; ++i) ck[i] = take(state_b);
-  for (int i = 0; i < K; ++i) sg[i] = take(state_b);
+  std::vector<char*> ck(nseg > 1 ? nseg - 1 : 0);
+  for (auto& c : ck) c = take(state_b);
+  std::vector<char*> sg[2];
+  for (int b = 0; b < nbuf; ++b) {
+    sg[b].resize(K);
+    for (int i = 0; i < K; ++i) sg[b][i] = take(state_b);
+  }
   R* lam[2] = {reinterpret_cast<R*>(take(lam_b)), reinterpret_cast<R*>(take(lam_b))};
   R* ai = reinterpret_cast<R*>(take(ai_b));
-  R* as = reinterpret_cast<R*>(take(as_b));
   double* partial = reinterpret_cast<double*>(take((size_t)grid * 3 * sizeof(double)));
   double* opart = reinterpret_cast<double*>(take((size_t)oblocks * sizeof(double)));
   auto pop_of = [&](char* st) { return (void*)st; };
   auto aux_of = [&](char* st) { return (void*)(st + up(pop_b)); };
+  auto buf_of = [&](int seg) -> std::vector<char*>& { return sg[nbuf == 2 ? (seg & 1) : 0]; };
   const bool fresh = h->steps == 0;
+  cudaStream_t A = h->stream;
 
-  // forward sweep with a checkpoint every K steps
-  for (int t = 0; t < n; ++t) {
+  // forward sweep: a checkpoint every K steps; the last segment's input
+  // states stay in its segment buffer, and its last step writes the handle's
+  // state and fields
+  const int t_last = (nseg - 1) * K;
+  for (int t = 0; t < t_last; ++t) {
     if (t % K == 0) {
       PF_CUDA(h, cudaMemcpyAsync(pop_of(ck[t / K]), h->pop[h->cur], pop_b,
-                                 cudaMemcpyDeviceToDevice, h->stream));
+                                 cudaMemcpyDeviceToDevice, A));
       PF_CUDA(h, cudaMemcpyAsync(aux_of(ck[t / K]), h->aux[h->cur], aux_b,
-                                 cudaMemcpyDeviceToDevice, h->stream));
+                                 cudaMemcpyDeviceToDevice, A));
     }
-    pf_status st = step_t<S, R>(h, t == n - 1);
+    pf_status st = step_t<S, R>(h, false);
     if (st != PF_OK) return st;
+  }
+  {
+    std::vector<char*>& bl = buf_of(nseg - 1);
+    const int L = n - t_last;
+    PF_CUDA(h, cudaMemcpyAsync(pop_of(bl[0]), h->pop[h->cur], pop_b, cudaMemcpyDeviceToDevice, A));
+    PF_CUDA(h, cudaMemcpyAsync(aux_of(bl[0]), h->aux[h->cur], aux_b, cudaMemcpyDeviceToDevice, A));
+    for (int j = 0; j < L; ++j) {
+      const bool last = j + 1 == L;
+      const StepArgs<S, R> a = make_step_args<S, R>(
+          h, pop_of(bl[j]), aux_of(bl[j]), last ? h->pop[h->cur ^ 1] : pop_of(bl[j + 1]),
+          last ? h->aux[h->cur ^ 1] : aux_of(bl[j + 1]), last);
+      pf_status sl = launch_all<S, R>(h, a, A);
+      if (sl != PF_OK) return sl;
+    }
+    h->cur ^= 1;
+    h->steps += L;
   }
   // objective J(x_T) and its adjoint lambda_T
   pf_diag dg{};
@@ -1281,54 +1319,102 @@ static pf_status adjoint_t(pf_handle* h, int n, const pf_objective* obj, double*
   const double yc = dg.gas > 0.0 ? dg.gas_y / dg.gas : 0.0;
   const double J = obj->w_solid * dg.sum_hpsi / N + obj->w_centroid * yc / dd.ny;
   PF_CUDA(h, launch_adj_objective<R>(lam[0], dd, (long long)ps, obj->w_solid, obj->w_centroid,
-                                     yc, dg.gas > 0.0 ? dg.gas : 1.0, h->stream));
-  PF_CUDA(h, cudaMemsetAsync(partial, 0, (size_t)grid * 3 * sizeof(double), h->stream));
+                                     yc, dg.gas > 0.0 ? dg.gas : 1.0, A));
+  PF_CUDA(h, cudaMemsetAsync(partial, 0, (size_t)grid * 3 * sizeof(double), A));
   h->launches++;
 
-  // reverse sweep, one checkpoint segment at a time
-  const double dfs = 6.0 / (h->p.W_phi * std::sqrt(2.0 * h->p.beta_phi));
-  int cl = 0;
-  for (int sgi = nseg - 1; sgi >= 0; --sgi) {
-    const int t0 = sgi * K, t1 = std::min(n, t0 + K), L = t1 - t0;
-    PF_CUDA(h, cudaMemcpyAsync(pop_of(sg[0]), pop_of(ck[sgi]), pop_b, cudaMemcpyDeviceToDevice,
-                               h->stream));
-    PF_CUDA(h, cudaMemcpyAsync(aux_of(sg[0]), aux_of(ck[sgi]), aux_b, cudaMemcpyDeviceToDevice,
-                               h->stream));
-    for (int j = 0; j + 1 < L; ++j) {
-      const StepArgs<S, R> a = make_step_args<S, R>(h, pop_of(sg[j]), aux_of(sg[j]),
-                                                    pop_of(sg[j + 1]), aux_of(sg[j + 1]), false);
-      pf_status sl = launch_all<S, R>(h, a, h->stream);
+  // recomputation of segment s < nseg - 1 from its checkpoint into its buffer
+  auto recompute = [&](int s, cudaStream_t sx) -> pf_status {
+    std::vector<char*>& b = buf_of(s);
+    PF_CUDA(h, cudaMemcpyAsync(pop_of(b[0]), pop_of(ck[s]), pop_b, cudaMemcpyDeviceToDevice, sx));
+    PF_CUDA(h, cudaMemcpyAsync(aux_of(b[0]), aux_of(ck[s]), aux_b, cudaMemcpyDeviceToDevice, sx));
+    for (int j = 0; j + 1 < K; ++j) {
+      const StepArgs<S, R> a = make_step_args<S, R>(h, pop_of(b[j]), aux_of(b[j]),
+                                                    pop_of(b[j + 1]), aux_of(b[j + 1]), false);
+      pf_status sl = launch_all<S, R>(h, a, sx);
       if (sl != PF_OK) return sl;
     }
+    return PF_OK;
+  };
+  // reverse sweep of segment s, on the handle's stream
+  const double dfs = 6.0 / (h->p.W_phi * std::sqrt(2.0 * h->p.beta_phi));
+  int cl = 0;
+  auto reverse = [&](int s) -> pf_status {
+    const int t0 = s * K, L = std::min(n, t0 + K) - t0;
+    std::vector<char*>& b = buf_of(s);
     for (int j = L - 1; j >= 0; --j) {
       AdjArgs<S, R> aa{};
-      aa.step = make_step_args<S, R>(h, pop_of(sg[j]), aux_of(sg[j]), nullptr, nullptr, false);
+      aa.step = make_step_args<S, R>(h, pop_of(b[j]), aux_of(b[j]), nullptr, nullptr, false);
       aa.dom = dd;
       aa.lam_in = lam[cl];
       aa.lam_out = lam[cl ^ 1];
       aa.ai = ai;
-      aa.as = as;
       aa.partial = partial;
       aa.dfs_dsigma = dfs;
-      PF_CUDA(h, launch_adjoint_step<S, R>(aa, grid, h->stream));
-      h->launches += 3;
+      PF_CUDA(h, launch_adjoint_step<S, R>(aa, grid, A));
+      h->launches += ADJ_LAUNCHES_PER_STEP;
       cl ^= 1;
+    }
+    return PF_OK;
+  };
+  if (nbuf == 1) {
+    for (int s = nseg - 1; s >= 0; --s) {
+      if (s < nseg - 1 && (st = recompute(s, A)) != PF_OK) return st;
+      if ((st = reverse(s)) != PF_OK) return st;
+    }
+  } else {
+    // Stream B recomputes segment s - 1 while A reverses segment s.  The
+    // buffer of segment s - 2 is the one of segment s: B waits for A's
+    // reverse of s before it overwrites it, and A waits for B's recompute of
+    // a segment before it reverses it.
+    if (!h->adj_stream)
+      PF_CUDA(h, cudaStreamCreateWithFlags(&h->adj_stream, cudaStreamNonBlocking));
+    cudaStream_t B = h->adj_stream;
+    struct Events {
+      std::vector<cudaEvent_t> ev;
+      ~Events() { for (cudaEvent_t e : ev) cudaEventDestroy(e); }
+    } evs;
+    auto new_event = [&](cudaEvent_t* e) -> pf_status {
+      PF_CUDA(h, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+      evs.ev.push_back(*e);
+      return PF_OK;
+    };
+    std::vector<cudaEvent_t> ev_rec(nseg, nullptr), ev_rev(nseg, nullptr);
+    cudaEvent_t ev_fwd;
+    if ((st = new_event(&ev_fwd)) != PF_OK) return st;
+    for (int s = 0; s < nseg; ++s)
+      if ((st = new_event(&ev_rec[s])) != PF_OK || (st = new_event(&ev_rev[s])) != PF_OK)
+        return st;
+    PF_CUDA(h, cudaEventRecord(ev_fwd, A));
+    PF_CUDA(h, cudaStreamWaitEvent(B, ev_fwd, 0));
+    if ((st = recompute(nseg - 2, B)) != PF_OK) return st;
+    PF_CUDA(h, cudaEventRecord(ev_rec[nseg - 2], B));
+    for (int s = nseg - 1; s >= 0; --s) {
+      if (s < nseg - 1) PF_CUDA(h, cudaStreamWaitEvent(A, ev_rec[s], 0));
+      if ((st = reverse(s)) != PF_OK) return st;
+      PF_CUDA(h, cudaEventRecord(ev_rev[s], A));
+      if (s - 2 >= 0) {
+        PF_CUDA(h, cudaStreamWaitEvent(B, ev_rev[s], 0));
+        if ((st = recompute(s - 2, B)) != PF_OK) return st;
+        PF_CUDA(h, cudaEventRecord(ev_rec[s - 2], B));
+      }
     }
   }
   std::vector<double> hp((size_t)grid * 3), ho(oblocks, 0.0);
   if (fresh) {
+    // the initial state is checkpoint 0, or the first state of the only segment
+    char* x0 = nseg > 1 ? ck[0] : buf_of(0)[0];
     double der[3];
     pf_params_derived(&h->p, der);
-    PF_CUDA(h, launch_adj_omega_init<S, R>(lam[cl], (const S*)pop_of(ck[0]),
-                                           (const R*)aux_of(ck[0]), dd, (long long)ps, der[0],
-                                           h->p.k, opart, oblocks, h->stream));
+    PF_CUDA(h, launch_adj_omega_init<S, R>(lam[cl], (const S*)pop_of(x0), (const R*)aux_of(x0),
+                                           dd, (long long)ps, der[0], h->p.k, opart, oblocks, A));
     h->launches++;
     PF_CUDA(h, cudaMemcpyAsync(ho.data(), opart, oblocks * sizeof(double), cudaMemcpyDeviceToHost,
-                               h->stream));
+                               A));
   }
   PF_CUDA(h, cudaMemcpyAsync(hp.data(), partial, hp.size() * sizeof(double),
-                             cudaMemcpyDeviceToHost, h->stream));
-  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+                             cudaMemcpyDeviceToHost, A));
+  PF_CUDA(h, cudaStreamSynchronize(A));
   double g[3] = {0.0, 0.0, 0.0};
   for (int b = 0; b < grid; ++b)
     for (int q = 0; q < 3; ++q) g[q] += hp[(size_t)b * 3 + q];

@@ -139,6 +139,7 @@ cudaError_t launch_reduce(const ReduceArgs<R>& a, double* partial, double* out,
 // Discrete adjoint
 // ---------------------------------------------------------------------------
 constexpr int ADJ_TX = 32, ADJ_TY = 8;  // tile of the local reverse kernel
+constexpr int ADJ_LAUNCHES_PER_STEP = 2;  // kernels of one reverse step
 // Planes of the per-site input adjoints (layout of local::In).
 enum AiPlane : int {
   AI_F = 0, AI_H = 9, AI_G = 18, AI_S = 23, AI_PSIO = 28, AI_GPX = 29, AI_GPY = 30,
@@ -153,7 +154,6 @@ struct AdjArgs {
   const R* lam_in;         // lambda_{t+1}, 39 planes
   R* lam_out;              // lambda_t, 39 planes
   R* ai;                   // input adjoints, N_AI planes
-  R* as;                   // stencil-transposed field adjoints, 4 planes
   double* partial;         // per-block parameter adjoints (eps, Omega, sigma), accumulated
   double dfs_dsigma;       // d(surface-tension coefficient)/d sigma
 };
