@@ -24,6 +24,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -157,10 +159,12 @@ def workload_config(size: int, precision: str) -> dict:
             "lattice": [size, size], "precision": precision}
 
 
-def cpu_oracle_sample(steps_hint: int, target_s: float, side: int | None = None) -> dict:
+def cpu_oracle_sample(steps_hint: int, target_s: float, side: int | None = None,
+                      cores: int | None = None, warm: int = 1) -> dict:
     """Time the FP64 oracle (test infrastructure, run as a child process) on a
-    window of the 4096^2 workload; all host cores."""
-    cores = os.cpu_count() or 1
+    window of the 4096^2 workload (global coordinates, so the window holds the
+    same seeds and bubbles); all host cores unless `cores` is given."""
+    cores = cores or os.cpu_count() or 1
     code = f"""
 import json, sys, time
 sys.path.insert(0, {ROOT!r})
@@ -177,7 +181,7 @@ if not side:
     rate = 256 * 256 / dt
     side = int(min(2048, max(128, (rate * {target_s} / max({steps_hint}, 1)) ** 0.5)) // 32 * 32)
 o = make(side)
-o.step(1)
+o.step({warm})
 t = time.perf_counter(); o.step({steps_hint}); dt = time.perf_counter() - t
 print(json.dumps(dict(side=side, steps={steps_hint}, seconds=dt)))
 """
@@ -187,9 +191,10 @@ print(json.dumps(dict(side=side, steps={steps_hint}, seconds=dt)))
     rec = json.loads(out.stdout.strip().splitlines()[-1])
     mlups = rec["side"] ** 2 * rec["steps"] / rec["seconds"] / 1e6
     return {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"FP64 oracle, {rec['side']}x{rec['side']} window of the 4096^2 layout "
-                      f"(global coordinates), {rec['steps']} steps in {rec['seconds']:.1f} s, "
-                      f"OpenMP over rows"}
+            "sample": f"FP64 oracle (gcc -O3, OpenMP over rows), {rec['side']}x{rec['side']} "
+                      f"window at (1024, 1024) of the 4096^2 layout, {rec['steps']} steps "
+                      f"after {warm}, in {rec['seconds']:.1f} s",
+            "window": rec["side"], "steps": rec["steps"], "seconds": rec["seconds"]}
 
 
 def cpu_oracle_variant(kind: str, steps: int = 0) -> dict:
@@ -200,7 +205,8 @@ def cpu_oracle_variant(kind: str, steps: int = 0) -> dict:
     (the same with the temperature lattice)."""
     cores = os.cpu_count() or 1
     steps = steps or {"thermal": 60, "bounded": 60, "3d": 120, "3d_thermal": 300,
-                      "3d_flow": 160, "3d_flow_thermal": 140}[kind]  # about 10 s of CPU work
+                      "3d_flow": 160, "3d_flow_thermal": 140, "precision": 60,
+                      "ensemble": 200}[kind]  # about 10 s of CPU work
     code = f"""
 import json, sys, time
 sys.path.insert(0, {ROOT!r})
@@ -227,6 +233,29 @@ elif kind in ("3d", "3d_thermal"):
     o.init_spec(seeds, R_s)
     sites = n ** 3
     what = f"{{n}}^3 melt with 8 seeds (3-D oracle{{', thermal' if p['thermal'] else ''}})"
+elif kind == "precision":
+    lay = wl.single_seed_bubble(8192, 4096, rng_seed=1)
+    s = 768
+    o = oracle.Oracle(s, s, lay.params, window=(lay.nx, lay.ny, 4096 - s // 2, 2048 - s // 2))
+    o.set_rho_bar(lay.params["rho_g"] + o.mean_phi_global(lay.bubbles) * (lay.params["rho_l"] - lay.params["rho_g"]))
+    o.init_spec(lay.seeds, lay.R_s, lay.bubbles)
+    sites = s * s
+    what = f"{{s}}x{{s}} window around the seed of the 8192x4096 layout"
+elif kind == "ensemble":
+    lays = wl.ensemble_96()
+    pick = [lays[0], lays[32], lays[64]]
+    os_ = []
+    for l in pick:
+        oo = oracle.Oracle(l.nx, l.ny, dict(wl.BASE_PARAMS, eps_s=l.params["eps_s"]))
+        oo.init_spec(l.seeds, l.R_s, l.bubbles)
+        os_.append(oo)
+    class _All:
+        def step(self, n):
+            for oo in os_:
+                oo.step(n)
+    o = _All()
+    sites = sum(l.nx * l.ny for l in pick)
+    what = "3 of the 96 domains (256^2, 512x384, 1024x512)"
 else:
     lay = wl.growth_lattice()
     par = dict(lay.params, **wl.THERMAL_PARAMS)
@@ -251,26 +280,144 @@ print(json.dumps(dict(sites=sites, steps={steps}, seconds=dt, what=what)))
     rec = json.loads(out.stdout.strip().splitlines()[-1])
     return {"value": rec["sites"] * rec["steps"] / rec["seconds"] / 1e6, "unit": "MLUPS",
             "cores": cores, "kind": "oracle",
-            "sample": f"FP64 oracle, {rec['what']}, {rec['steps']} steps in "
-                      f"{rec['seconds']:.1f} s, OpenMP over rows"}
+            "sample": f"FP64 oracle (gcc -O3, OpenMP over rows), {rec['what']}, "
+                      f"{rec['steps']} steps after 1, in {rec['seconds']:.1f} s"}
+
+
+def timed_region(torch, stream, step, n: int, local: int, no_clocks: bool):
+    """Time n steps with CUDA events on the launching stream, synchronised
+    on both sides, with nvidia-smi clock samples taken during the region."""
+    clocks = ClockSampler(local)
+    if not no_clocks:
+        clocks.start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    step(n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), clocks.stop()
+
+
+def roofline(bpl: int, sites: int, ms_per_step: float, kernel: str, traffic=None) -> dict:
+    """HBM roofline of the dominant kernel: algorithmic bytes per launch over
+    the average launch time, against the measured copy bandwidth."""
+    peak, peak_kind = measured_peaks()
+    achieved = bpl * sites / (ms_per_step / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+            "bytes_per_lu": bpl, "kernel": kernel}
+
+
+def _pinned(torch, shape):
+    return torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+
+
+def e2e_2d(torch, sim, doms, steps: int, thermal: bool = False) -> dict:
+    """End to end through the public API, every domain of the handle: the
+    six fields (phi, psi, C, vx, vy, p; and theta in thermal mode) in from
+    page-locked FP64 host memory (pf_set_fields, pf_set_temperature),
+    pf_step(steps), the same fields back to page-locked host memory
+    (pf_get_fields); host wall clock.  doms: [(dom, nx, ny)]."""
+    names = ("phi", "psi", "C", "vx", "vy", "p")
+    ins, ths, outs = [], [], []
+    for d, nx, ny in doms:
+        f = sim.fields(d, names + (("theta",) if thermal else ()))
+        a = _pinned(torch, (6, ny, nx))
+        for i, nm in enumerate(names):
+            a[i] = f[nm]
+        ins.append(a)
+        if thermal:
+            t = _pinned(torch, (ny, nx))
+            t[...] = f["theta"]
+            ths.append(t)
+        outs.append(_pinned(torch, (6 * nx * ny,)))
+    sites = sum(nx * ny for _, nx, ny in doms)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k, (d, nx, ny) in enumerate(doms):
+        sim.set_fields_stack(d, ins[k])
+        if thermal:
+            sim.set_temperature(d, ths[k])
+    sim.step(steps)
+    for k, (d, nx, ny) in enumerate(doms):
+        sim.fields(d, ("phi", "psi", "C", "p", "vx", "vy"), out=outs[k])
+    e_s = time.perf_counter() - t0
+    nb = (7 if thermal else 6) * 8 * sites
+    return {"value": sites * steps / e_s / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": nb / steps, "d2h_bytes_per_step": 6 * 8 * sites / steps,
+            "seconds": e_s,
+            "what": "pf_set_fields" + (" and pf_set_temperature" if thermal else "") +
+                    " from page-locked FP64 host fields, pf_step(K), pf_get_fields to page-locked "
+                    "FP64 host memory; host wall clock; grain angles are not re-sent (theta = 0)"}
+
+
+def e2e_3d(torch, sim, steps: int, flow: bool, thermal: bool = False) -> dict:
+    """End to end through the 3-D API: the initial fields in from page-locked
+    FP64 host memory (pf3_set_fields: psi, C; pf3f_set_fields: phi, psi, C,
+    vx, vy, vz, p; and the temperature in thermal mode), pf3[f]_step(steps),
+    every field plane back to page-locked host memory; host wall clock."""
+    f = sim.fields()
+    shape = tuple(sim.shape)
+    n = int(np.prod(shape))
+    theta = None
+    if thermal:
+        theta = _pinned(torch, shape)
+        theta[...] = f["theta"]
+    if flow:
+        names = ("phi", "psi", "C", "vx", "vy", "vz", "p")
+        src = _pinned(torch, (7,) + shape)
+        for i, nm in enumerate(names):
+            src[i] = f[nm]
+    else:
+        psi, C = _pinned(torch, shape), _pinned(torch, shape)
+        psi[...] = f["psi"]
+        C[...] = f["C"]
+    k = sim.field_planes
+    out = _pinned(torch, (k * n,))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if flow:
+        sim.set_fields_stack(src)
+    else:
+        sim.set_fields(psi, C)
+    if thermal:
+        sim.set_temperature(theta)
+    sim.step(steps)
+    sim.fields(out=out)
+    e_s = time.perf_counter() - t0
+    nin = (7 if flow else 2) + (1 if thermal else 0)
+    return {"value": n * steps / e_s / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": nin * 8 * n / steps, "d2h_bytes_per_step": k * 8 * n / steps,
+            "seconds": e_s,
+            "what": ("pf3f_set_fields" if flow else "pf3_set_fields") +
+                    (" and the temperature" if thermal else "") +
+                    " from page-locked FP64 host fields, step(K), every field plane to "
+                    "page-locked FP64 host memory; host wall clock"}
 
 
 def run_reference(args) -> None:
+    """The reference arm: the FP64 oracle itself, timed on the host cores on a
+    bounded window of the 4096^2 workload (the paper publishes no code).  Each
+    timed step is one oracle step of that window; value and ms_per_step are
+    the window's own measurements."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
     oracle.build()
-    total = args.steps + args.warmup
-    base = cpu_oracle_sample(steps_hint=max(total, 1), target_s=120.0)
+    base = cpu_oracle_sample(steps_hint=args.steps, target_s=60.0, warm=args.warmup)
+    side = base["window"]
     line = {
         "impl": "reference", "metric": METRIC, "value": base["value"], "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 4096 * 4096 / (base["value"] * 1e3),
+        "ms_per_step": base["seconds"] / base["steps"] * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": dict(workload_config(4096, "fp64"),
-                       sample="bounded window of the lattice, see cpu_baseline"),
+        "config": {"workload": f"{side}x{side} window at (1024, 1024) of the 4096x4096 periodic "
+                               "lattice (64 seeds, 128 bubbles, seed 2), global coordinates",
+                   "lattice": [side, side], "precision": "fp64",
+                   "sample": f"{base['steps']} oracle steps of the window, after {args.warmup}"},
         "cpu_baseline": base,
         "e2e": {"value": base["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -337,9 +484,9 @@ def run_ensemble(args) -> None:
     """96 independent domains of uneven size (32 each of 256^2, 512x384,
     1024x512; 1-4 seeds, 1-6 bubbles, eps_s ~ U[0.02, 0.07]) in one handle:
     one launch per domain per step vs one batched launch per step vs the
-    autotuned batched launch replayed as CUDA graphs.  Under torchrun the
-    domains are split across ranks (shard.shard_domains) with no collective on
-    the data path; the job time is the slowest rank's."""
+    autotuned batched launch replayed as CUDA graphs (the headline).  Under
+    torchrun the domains are split across ranks (shard.shard_domains) with no
+    collective on the data path; the job time is the slowest rank's."""
     import torch
 
     from paper_2407_01651_gb300 import pf
@@ -364,31 +511,44 @@ def run_ensemble(args) -> None:
     for d, l in enumerate(lays):
         sim.init_fields(d, l.seeds, l.R_s, l.bubbles)
     units = [sum(sizes[d] for d in p) for p in parts]
+    my_sites = units[rank]
 
-    def timed():
+    def timed(clk=False):
         if dist is not None:
             dist.barrier()
-        ms = _time_steps(torch, sim, stream, args.steps)
+        ms, c = timed_region(torch, stream, sim.step, args.steps, local, args.no_clocks or not clk)
         if dist is not None:
             dist.barrier()
-        return shard.max_over_ranks(ms, dist, device="cuda")
+        return shard.max_over_ranks(ms, dist, device="cuda"), c
 
-    res = {}
+    res, ms_mode = {}, {}
     sim.set_launch(1, 0, 0)
     sim.step(args.warmup)
-    ms = timed()
+    ms, _ = timed()
     res["sequential_per_domain"] = shard.job_rate(units, args.steps, ms / 1e3) / 1e6
+    ms_mode["sequential_per_domain"] = ms / args.steps
     sim.set_launch(0, 0, 0)
     sim.step(args.warmup)
-    ms = timed()
+    ms, _ = timed()
     res["batched_one_launch"] = shard.job_rate(units, args.steps, ms / 1e3) / 1e6
+    ms_mode["batched_one_launch"] = ms / args.steps
     cfg = sim.autotune(10)
     sim.set_launch(0, cfg[3], 64)
     sim.step(args.warmup)
     launches0 = sim.launches
-    ms = timed()
+    ms, clk = timed(clk=True)
+    launches = sim.launches - launches0
     res["batched_autotuned_graph"] = shard.job_rate(units, args.steps, ms / 1e3) / 1e6
+    ms_mode["batched_autotuned_graph"] = ms / args.steps
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_2d(torch, sim, [(d, l.nx, l.ny) for d, l in enumerate(lays)], args.steps)
+        if dist is not None:
+            t = torch.tensor([e2e["seconds"]], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e["value"] = sum(units) * args.steps / float(t.item()) / 1e6
     if rank == 0:
+        cpu = None if (args.no_cpu_baseline or world > 1) else cpu_oracle_variant("ensemble")
         print(json.dumps({
             "metric": "ensemble aggregate MLUPS (96 uneven domains)",
             "value": res["batched_autotuned_graph"],
@@ -397,102 +557,166 @@ def run_ensemble(args) -> None:
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "96 domains: 32 x 256^2, 32 x 512x384, 32 x 1024x512, seed 5",
                        "sites": sum(sizes), "autotuned": list(cfg), "graph_steps": 64,
-                       "parallelism": f"domains sharded over {world} rank(s)"},
-            "modes": res, "speedup_vs_sequential": res["batched_autotuned_graph"] /
-            res["sequential_per_domain"], "gpu_launches": sim.launches - launches0}))
+                       "parallelism": f"domains sharded over {world} rank(s)",
+                       "l2": f"{313 * my_sites / 1e9:.1f} GB read+written per step > L2 "
+                             "(no flush)"},
+            "roofline": roofline(BYTES_PER_LU["fp32"], my_sites, ms / args.steps,
+                                 "k_step_ymarch (batched over every domain's tiles)"),
+            "modes": res, "ms_per_step_modes": ms_mode,
+            "speedup_vs_sequential": res["batched_autotuned_graph"] / res["sequential_per_domain"],
+            "speedup_graph_vs_one_launch": res["batched_autotuned_graph"] /
+            res["batched_one_launch"],
+            "gpu_launches": launches, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}))
     sim.close()
     if dist is not None:
         dist.destroy_process_group()
 
 
 def run_precision(args) -> None:
-    """8192 x 4096 seeded like the 128^2 case (one seed, one bubble), FP32 vs
-    FP16- and BF16-offset storage."""
+    """8192 x 4096 seeded like the 128^2 case (one seed, one bubble): the
+    16-bit offset storage forms against FP32, each timed over the same steps.
+    The headline is the FP16 form."""
     import torch
 
     from paper_2407_01651_gb300 import pf
     from paper_2407_01651_gb300 import workload as wl
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
     lay = wl.single_seed_bubble(8192, 4096, rng_seed=1)
     stream = torch.cuda.current_stream()
-    out = {}
-    for prec in ("fp32", "fp16", "bf16"):
+    sites = lay.nx * lay.ny
+    out, clk, e2e = {}, None, None
+    for prec in ("fp32", "bf16", "fp16"):
         sim = pf.Simulation([(lay.nx, lay.ny)], lay.params, prec, stream=stream.cuda_stream)
         sim.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
         sim.step(args.warmup)
-        ms = _time_steps(torch, sim, stream, args.steps)
+        launches0 = sim.launches
+        ms, c = timed_region(torch, stream, sim.step, args.steps, local,
+                             args.no_clocks or prec != "fp16")
         bpl = BYTES_PER_LU[prec]
-        out[prec] = {"mlups": lay.nx * lay.ny * args.steps / ms / 1e3,
+        out[prec] = {"mlups": sites * args.steps / ms / 1e3,
                      "ms_per_step": ms / args.steps,
-                     "algorithmic_gbs": bpl * lay.nx * lay.ny * args.steps / ms / 1e6,
-                     "bytes_per_lu": bpl}
+                     "algorithmic_gbs": bpl * sites * args.steps / ms / 1e6,
+                     "bytes_per_lu": bpl, "gpu_launches": sim.launches - launches0,
+                     "step_config": list(sim.step_config())}
+        if prec == "fp16":
+            clk = c
+            if not args.no_e2e:
+                e2e = e2e_2d(torch, sim, [(0, lay.nx, lay.ny)], args.steps)
         sim.close()
         torch.cuda.empty_cache()
+    f16 = out["fp16"]
     print(json.dumps({
-        "metric": "precision-form MLUPS at 8192x4096", "value": out["fp16"]["mlups"],
+        "metric": "precision-form MLUPS at 8192x4096", "value": f16["mlups"],
         "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f16-storage/f32", "data": "synthetic",
-        "config": {"workload": "8192x4096, one seed + one R=16 bubble (seed 1)"},
-        "forms": out, "speedup_fp16_vs_fp32": out["fp16"]["mlups"] / out["fp32"]["mlups"],
-        "speedup_bf16_vs_fp32": out["bf16"]["mlups"] / out["fp32"]["mlups"]}))
+        "ms_per_step": f16["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE["fp16"], "data": "synthetic",
+        "config": {"workload": "8192x4096, one seed + one R=16 bubble (seed 1)",
+                   "lattice": [lay.nx, lay.ny], "precision": "fp16",
+                   "l2": f"{(BYTES_PER_LU['fp16'] - 1) * sites / 1e9:.1f} GB read+written per "
+                         "step > L2 (no flush)"},
+        "roofline": roofline(BYTES_PER_LU["fp16"], sites, f16["ms_per_step"],
+                             "k_step_staged<__half,float> (one launch per step)",
+                             recorded_traffic("fp16", 4096) and
+                             recorded_traffic("fp16", 4096) * sites / 4096 ** 2),
+        "forms": out, "speedup_fp16_vs_fp32": f16["mlups"] / out["fp32"]["mlups"],
+        "speedup_bf16_vs_fp32": out["bf16"]["mlups"] / out["fp32"]["mlups"],
+        "gpu_launches": f16["gpu_launches"], "clocks": clk, "e2e": e2e,
+        "cpu_baseline": None if args.no_cpu_baseline else cpu_oracle_variant("precision")}))
 
 
-def run_bounded(args) -> None:
-    """The 4096^2 lattice in the boundary arrangement of the paper's Section 4
-    (symmetric sides in x, a no-flux wall at the bottom, the far field psi_l,
-    C = 1, theta = -Omega at the top) with the temperature lattice on: MLUPS
-    and roofline of the boundary-aware y-march, against the periodic thermal
-    step in the same process."""
+def _thermal_like(args, mode: str) -> None:
+    """The 4096^2 lattice with the temperature lattice on (Le = 50, c_p^s /
+    c_p = 1, theta0 = -Omega, Section 4 of the paper), periodic ('thermal') or
+    with the paper's Section-4 sides ('bounded': symmetric in x, a no-flux wall
+    at the bottom, the far field at the top), against the periodic isothermal
+    (for 'thermal') or thermal (for 'bounded') step in the same process."""
     import torch
 
     from paper_2407_01651_gb300 import pf
     from paper_2407_01651_gb300 import workload as wl
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    prec = args.precision if args.precision in BYTES_PER_LU_THERMAL else "fp32"
     lay = wl.growth_lattice(args.size, args.size)
     par = dict(lay.params, **wl.THERMAL_PARAMS)
     stream = torch.cuda.current_stream()
     sites = lay.nx * lay.ny
-    bpl = BYTES_PER_LU_THERMAL["fp32"]
-    res = {}
-    for mode, bc in (("bounded", (pf.BC_SYMMETRIC, pf.BC_SYMMETRIC, pf.BC_WALL, pf.BC_FARFIELD)),
-                     ("periodic", None)):
-        sim = pf.Simulation([(lay.nx, lay.ny)], par, "fp32", stream=stream.cuda_stream)
+    sides = (pf.BC_SYMMETRIC, pf.BC_SYMMETRIC, pf.BC_WALL, pf.BC_FARFIELD)
+    if mode == "thermal":
+        runs = (("thermal", par, None, BYTES_PER_LU_THERMAL[prec]),
+                ("isothermal", lay.params, None, BYTES_PER_LU[prec]))
+    else:
+        runs = (("bounded", par, sides, BYTES_PER_LU_THERMAL[prec]),
+                ("periodic", par, None, BYTES_PER_LU_THERMAL[prec]))
+    res, clk, e2e = {}, None, None
+    for name, p_, bc, bpl in runs:
+        head = name == runs[0][0]
+        sim = pf.Simulation([(lay.nx, lay.ny)], p_, prec, stream=stream.cuda_stream)
         if bc:
             sim.set_boundaries(0, *bc)
         sim.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
-        d0, t0 = sim.reduce(0), sim.reduce_thermal(0)
+        th = p_.get("thermal", 0)
+        d0 = sim.reduce(0)
+        t0 = sim.reduce_thermal(0) if th else None
         sim.step(args.warmup)
         launches0 = sim.launches
-        ms = _time_steps(torch, sim, stream, args.steps)
+        ms, c = timed_region(torch, stream, sim.step, args.steps, local,
+                             args.no_clocks or not head)
         launches = sim.launches - launches0
-        d, t = sim.reduce(0), sim.reduce_thermal(0)
+        d = sim.reduce(0)
         if d["nonfinite"]:
-            raise SystemExit(f"{mode}: non-finite fields after the timed run")
-        res[mode] = {"mlups": sites * args.steps / ms / 1e3, "ms_per_step": ms / args.steps,
-                     "algorithmic_gbs": bpl * sites * args.steps / ms / 1e6,
-                     "gpu_launches": launches,
-                     "sum_phi_rel_drift": d["sum_phi"] / d0["sum_phi"] - 1.0,
-                     "mean_theta": t["sum_theta"] / sites}
+            raise SystemExit(f"{name}: non-finite fields after the timed run")
+        r = {"mlups": sites * args.steps / ms / 1e3, "ms_per_step": ms / args.steps,
+             "bytes_per_lu": bpl, "algorithmic_gbs": bpl * sites * args.steps / ms / 1e6,
+             "gpu_launches": launches,
+             "sum_phi_rel_drift": d["sum_phi"] / d0["sum_phi"] - 1.0,
+             "sum_C_rel_drift": d["sum_C"] / d0["sum_C"] - 1.0}
+        if t0 is not None:
+            t = sim.reduce_thermal(0)
+            r["sum_rhoH_rel_drift"] = t["sum_e"] / t0["sum_e"] - 1.0
+            r["mean_theta"] = t["sum_theta"] / sites
+        if head:
+            clk = c
+            if not args.no_e2e:
+                e2e = e2e_2d(torch, sim, [(0, lay.nx, lay.ny)], args.steps, thermal=True)
+        res[name] = r
         sim.close()
         torch.cuda.empty_cache()
-    peak, peak_kind = measured_peaks()
-    b = res["bounded"]
+    h = res[runs[0][0]]
+    if mode == "thermal":
+        metric = "thermal coupled-step MLUPS at 4096² and % of HBM roofline"
+        kernel = "k_step_ymarch<thermal> (one launch per step)"
+        traffic = recorded_traffic(f"thermal_{prec}", args.size)
+        extra = {"thermal_cost_vs_isothermal": res["isothermal"]["mlups"] / h["mlups"]}
+        cfg = dict(workload_config(lay.nx, prec), thermal=wl.THERMAL_PARAMS)
+    else:
+        metric = "bounded thermal coupled-step MLUPS at 4096² and % of HBM roofline"
+        kernel = ("k_step_ymarch<thermal> on interior tiles + k_step_ymarch_bc<thermal> on edge "
+                  "tiles (side stream)")
+        traffic = None
+        extra = {}
+        cfg = dict(workload_config(lay.nx, prec), thermal=wl.THERMAL_PARAMS,
+                   boundaries="x: symmetric | y-: wall | y+: far field")
+    cfg["l2"] = f"{(h['bytes_per_lu'] - 1) * sites / 1e9:.1f} GB read+written per step > L2 (no flush)"
     print(json.dumps({
-        "metric": "bounded thermal coupled-step MLUPS at 4096² and % of HBM roofline",
-        "value": b["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(workload_config(lay.nx, "fp32"), thermal=wl.THERMAL_PARAMS,
-                       boundaries="x: symmetric | y-: wall | y+: far field"),
-        "roofline": {"bound": "hbm", "achieved": b["algorithmic_gbs"], "peak": peak,
-                     "unit": "GB/s", "frac": b["algorithmic_gbs"] / peak, "traffic": None,
-                     "peak_kind": peak_kind, "bytes_per_lu": bpl,
-                     "kernel": "k_step_ymarch_bc<thermal> (one launch per step)"},
-        "modes": res, "gpu_launches": b["gpu_launches"],
-        "cpu_baseline": None if args.no_cpu_baseline else cpu_oracle_variant("bounded")}))
+        "metric": metric, "value": h["mlups"], "unit": "MLUPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": h["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec],
+        "data": "synthetic", "config": cfg,
+        "roofline": roofline(h["bytes_per_lu"], sites, h["ms_per_step"], kernel, traffic),
+        "modes": res, **extra, "gpu_launches": h["gpu_launches"], "clocks": clk, "e2e": e2e,
+        "cpu_baseline": None if args.no_cpu_baseline else cpu_oracle_variant(mode)}))
+
+
+def run_bounded(args) -> None:
+    _thermal_like(args, "bounded")
+
+
+def run_thermal(args) -> None:
+    _thermal_like(args, "thermal")
 
 
 def run_3d(args) -> None:
@@ -505,7 +729,8 @@ def run_3d(args) -> None:
     from paper_2407_01651_gb300 import pf
     from paper_2407_01651_gb300 import workload as wl
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
     n = args.size if args.size != 4096 else 256
     seeds, R_s = wl.growth_3d(n)
     stream = torch.cuda.current_stream()
@@ -520,24 +745,18 @@ def run_3d(args) -> None:
     t0 = sim.reduce_thermal() if thermal else None
     sim.step(args.warmup)
     l0 = sim.launches
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    sim.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms, clk = timed_region(torch, stream, sim.step, args.steps, local, args.no_clocks)
+    launches = sim.launches - l0
     d = sim.reduce()
     sites = n ** 3
     planes = 30 if thermal else 23
     bpl = planes * 2 * (4 if prec == "fp32" else 8)
-    gbs = bpl * sites * args.steps / ms / 1e6
-    peak, peak_kind = measured_peaks()
     extra = {}
     if thermal:
         t1 = sim.reduce_thermal()
         extra = {"sum_rhoH_rel_drift": t1["sum_e"] / t0["sum_e"] - 1.0,
                  "mean_theta": t1["sum_theta"] / sites}
+    e2e = None if args.no_e2e else e2e_3d(torch, sim, args.steps, flow=False, thermal=thermal)
     print(json.dumps({
         "metric": ("3-D thermal dendrite-step" if thermal else "3-D dendrite-step") +
                   " MLUPS at 256³ and % of HBM roofline",
@@ -547,13 +766,12 @@ def run_3d(args) -> None:
         "dtype": DTYPE[prec], "data": "synthetic",
         "config": {"workload": f"{n}^3 periodic melt, 64 seeds (R=8) at uniform positions, seed 4"
                                + (", temperature lattice (Le 50, theta0 -0.55)" if thermal else ""),
-                   "lattice": [n, n, n], "precision": prec},
-        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
-                     "frac": gbs / peak, "traffic": None, "peak_kind": peak_kind,
-                     "bytes_per_lu": bpl, "kernel": "k_step3d (one launch per step)"},
+                   "lattice": [n, n, n], "precision": prec,
+                   "l2": f"{bpl * sites / 1e9:.1f} GB read+written per step > L2 (no flush)"},
+        "roofline": roofline(bpl, sites, ms / args.steps, "k_step3d (one launch per step)"),
         "sum_C_rel_drift": d["sum_C"] / d0["sum_C"] - 1.0,
         "solid_fraction": d["sum_hpsi"] / sites, **extra,
-        "gpu_launches": sim.launches - l0,
+        "gpu_launches": launches, "clocks": clk, "e2e": e2e,
         "cpu_baseline": None if args.no_cpu_baseline else
         cpu_oracle_variant("3d_thermal" if thermal else "3d")}))
     sim.close()
@@ -569,7 +787,8 @@ def run_3d_flow(args) -> None:
     from paper_2407_01651_gb300 import pf
     from paper_2407_01651_gb300 import workload as wl
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
     n = args.size if args.size != 4096 else 256
     seeds, R_s, bubbles = wl.flow_3d(n)
     stream = torch.cuda.current_stream()
@@ -584,13 +803,7 @@ def run_3d_flow(args) -> None:
     t0 = sim.reduce_thermal() if thermal else None
     sim.step(args.warmup)
     l0 = sim.launches
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    sim.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms, clk = timed_region(torch, stream, sim.step, args.steps, local, args.no_clocks)
     launches = sim.launches - l0
     d = sim.reduce()
     extra = {}
@@ -599,8 +812,7 @@ def run_3d_flow(args) -> None:
         extra = {"sum_rhoH_rel_drift": t1["sum_e"] / t0["sum_e"] - 1.0}
     sites = n ** 3
     bpl = (74 if thermal else 66) * 2 * (4 if prec == "fp32" else 8)
-    gbs = bpl * sites * args.steps / ms / 1e6
-    peak, peak_kind = measured_peaks()
+    e2e = None if args.no_e2e else e2e_3d(torch, sim, args.steps, flow=True, thermal=thermal)
     print(json.dumps({
         "metric": ("3-D thermal two-phase" if thermal else "3-D two-phase") +
                   " coupled-step MLUPS at 256³ and % of HBM roofline",
@@ -611,78 +823,16 @@ def run_3d_flow(args) -> None:
         "config": {"workload": f"{n}^3 periodic melt, 32 seeds (R=8) and 64 bubbles "
                                "(R~U[6,14]) at uniform positions, seed 5" +
                                (", temperature lattice (Le 50, theta0 -0.55)" if thermal else ""),
-                   "lattice": [n, n, n], "precision": prec},
-        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
-                     "frac": gbs / peak, "traffic": None, "peak_kind": peak_kind,
-                     "bytes_per_lu": bpl, "kernel": "k_step3f (one launch per step)"},
+                   "lattice": [n, n, n], "precision": prec,
+                   "l2": f"{bpl * sites / 1e9:.1f} GB read+written per step > L2 (no flush)"},
+        "roofline": roofline(bpl, sites, ms / args.steps, "k_step3f (one launch per step)"),
         "sum_phi_rel_drift": d["sum_phi"] / d0["sum_phi"] - 1.0,
         "sum_C_rel_drift": d["sum_C"] / d0["sum_C"] - 1.0,
         "solid_fraction": d["sum_hpsi"] / sites, **extra,
-        "gpu_launches": launches,
+        "gpu_launches": launches, "clocks": clk, "e2e": e2e,
         "cpu_baseline": None if args.no_cpu_baseline else
         cpu_oracle_variant("3d_flow_thermal" if thermal else "3d_flow")}))
     sim.close()
-
-
-def run_thermal(args) -> None:
-    """The 4096^2 lattice with the temperature lattice on (Section 4 of the
-    paper: Le = 50, c_p^s / c_p = 1, theta0 = -Omega): MLUPS and the HBM
-    roofline at 361 B/LU (FP32), the FP64 drift of the conserved totals, and
-    the isothermal step timed in the same process for the cost ratio."""
-    import torch
-
-    from paper_2407_01651_gb300 import pf
-    from paper_2407_01651_gb300 import workload as wl
-
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    prec = args.precision if args.precision in BYTES_PER_LU_THERMAL else "fp32"
-    lay = wl.growth_lattice(args.size, args.size)
-    par = dict(lay.params, **wl.THERMAL_PARAMS)
-    stream = torch.cuda.current_stream()
-    sites = lay.nx * lay.ny
-    res = {}
-    for mode, p_, bpl in (("thermal", par, BYTES_PER_LU_THERMAL[prec]),
-                          ("isothermal", lay.params, BYTES_PER_LU[prec])):
-        sim = pf.Simulation([(lay.nx, lay.ny)], p_, prec, stream=stream.cuda_stream)
-        sim.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
-        d0 = sim.reduce(0)
-        t0 = sim.reduce_thermal(0) if mode == "thermal" else None
-        sim.step(args.warmup)
-        launches0 = sim.launches
-        ms = _time_steps(torch, sim, stream, args.steps)
-        launches = sim.launches - launches0
-        d = sim.reduce(0)
-        if d["nonfinite"]:
-            raise SystemExit(f"{mode}: non-finite fields after the timed run")
-        r = {"mlups": sites * args.steps / ms / 1e3, "ms_per_step": ms / args.steps,
-             "bytes_per_lu": bpl, "algorithmic_gbs": bpl * sites * args.steps / ms / 1e6,
-             "gpu_launches": launches,
-             "sum_phi_rel_drift": d["sum_phi"] / d0["sum_phi"] - 1.0,
-             "sum_C_rel_drift": d["sum_C"] / d0["sum_C"] - 1.0}
-        if t0 is not None:
-            t = sim.reduce_thermal(0)
-            r["sum_rhoH_rel_drift"] = t["sum_e"] / t0["sum_e"] - 1.0
-            r["mean_theta"] = t["sum_theta"] / sites
-        res[mode] = r
-        sim.close()
-        torch.cuda.empty_cache()
-    peak, peak_kind = measured_peaks()
-    th = res["thermal"]
-    print(json.dumps({
-        "metric": "thermal coupled-step MLUPS at 4096² and % of HBM roofline",
-        "value": th["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": th["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
-        "config": dict(workload_config(lay.nx, prec), thermal=wl.THERMAL_PARAMS),
-        "roofline": {"bound": "hbm", "achieved": th["algorithmic_gbs"], "peak": peak,
-                     "unit": "GB/s", "frac": th["algorithmic_gbs"] / peak,
-                     "traffic": recorded_traffic(f"thermal_{prec}", args.size),
-                     "peak_kind": peak_kind,
-                     "bytes_per_lu": th["bytes_per_lu"],
-                     "kernel": "k_step_ymarch<thermal> (one launch per step)"},
-        "modes": res, "thermal_cost_vs_isothermal": res["isothermal"]["mlups"] / th["mlups"],
-        "cpu_baseline": None if args.no_cpu_baseline else cpu_oracle_variant("thermal"),
-        "gpu_launches": th["gpu_launches"]}))
 
 
 def main() -> None:
@@ -847,6 +997,9 @@ def main() -> None:
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(steps_hint=40, target_s=20.0)
+        one = cpu_oracle_sample(steps_hint=10, target_s=8.0, cores=1)
+        cpu["one_core"] = {"value": one["value"], "unit": "MLUPS", "cores": 1,
+                           "sample": one["sample"]}
 
     if rank == 0:
         line = {

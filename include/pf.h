@@ -401,7 +401,9 @@ pf_status pf3_create(const pf_params *p, int nx, int ny, int nz, pf_precision pr
  * mode: temperature populations at rest at theta0, lagged source Q_psi / F).
  * Synchronises.  Errors: BAD_ARG, OOM, CUDA. */
 pf_status pf3_init_seeds(pf3_handle *h, const double *seeds, int n_seeds, double R_s);
-/* Initial psi and C fields (host, n = nx*ny*nz each).  Synchronises. */
+/* Initial psi and C fields (host, n = nx*ny*nz each); non-finite values are
+ * detected on the device before the state is written and leave it as it
+ * was.  Synchronises.  Errors: BAD_ARG (size, non-finite), OOM, CUDA. */
 pf_status pf3_set_fields(pf3_handle *h, const double *psi, const double *C, size_t n);
 /* Thermal mode: temperature field theta (host, FP64, n = nx*ny*nz) of the
  * initial state, after pf3_init_seeds / pf3_set_fields and before the first
@@ -503,7 +505,9 @@ pf_status pf3f_init_spec(pf3f_handle *h, const double *seeds, int n_seeds, doubl
                          const double *bubbles, int n_bub);
 /* Initial fields (host, FP64): seven planes of nx*ny*nz in the order phi, psi,
  * C, vx, vy, vz, p (n = 7 nx ny nz); populations at equilibrium, rho_bar from
- * the mean phi.  Synchronises.  Errors: BAD_ARG (size, non-finite), OOM, CUDA. */
+ * the mean phi.  Non-finite values are detected on the device before the
+ * state is written and leave it as it was.  Synchronises.  Errors: BAD_ARG
+ * (size, non-finite), OOM, CUDA. */
 pf_status pf3f_set_fields(pf3f_handle *h, const double *fields7, size_t n);
 /* Buoyancy reference density (after initialisation; replaces the mean). */
 pf_status pf3f_set_rho_bar(pf3f_handle *h, double rho_bar);

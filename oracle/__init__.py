@@ -45,8 +45,10 @@ _SRC3 = os.path.join(_HERE, "pf_oracle3d.c")
 
 
 def build(force: bool = False) -> None:
-    """Compile both oracle builds and the 3-D oracle with gcc (no fast-math,
-    no FMA contraction, OpenMP over lattice rows)."""
+    """Compile both oracle builds and the 3-D oracle with gcc: -O3, no
+    fast-math and no FMA contraction (IEEE round-to-nearest in the written
+    order), OpenMP over lattice rows.  No -march=native: the same source must
+    build, and give the same results, on x86-64 and Arm hosts."""
     os.makedirs(_BUILD, exist_ok=True)
     for tag, extra, src in (("d", [], _SRC), ("z", ["-DPF_ORACLE_Z"], _SRC), ("3d", [], _SRC3)):
         out = os.path.join(_BUILD, f"liboracle_{tag}.so")
@@ -54,7 +56,7 @@ def build(force: bool = False) -> None:
                 and os.path.getmtime(out) >= os.path.getmtime(src)):
             continue
         tmp = out + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fopenmp",
+        cmd = ["gcc", "-std=c11", "-O3", "-fPIC", "-shared", "-fopenmp",
                "-ffp-contract=off", *extra, src, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, out)
@@ -141,7 +143,7 @@ def mutant(source: str, edits, tmpdir: str) -> ctypes.CDLL:
     with open(src, "w") as fh:
         fh.write(text)
     out = src[:-2] + ".so"
-    subprocess.run(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fopenmp",
+    subprocess.run(["gcc", "-std=c11", "-O3", "-fPIC", "-shared", "-fopenmp",
                     "-ffp-contract=off", src, "-o", out, "-lm"], check=True)
     lib = ctypes.CDLL(out)
     if source == "pf_oracle.c":

@@ -1178,12 +1178,20 @@ extern "C" pf_status pf_set_temperature(pf_handle* h, int dom, const double* the
   const DomDesc& dd = h->ddesc[dom];
   const size_t nn = (size_t)dd.nx * dd.ny;
   if (n != nn) return fail(h, PF_ERR_BAD_ARG, "n must equal nx*ny of the domain");
-  for (size_t i = 0; i < nn; ++i)
-    if (!std::isfinite(theta[i])) return fail(h, PF_ERR_BAD_ARG, "non-finite temperature");
-  pf_status st = ensure_staging(h, nn);
+  pf_status st = ensure_staging(h, nn + 1);
   if (st != PF_OK) return st;
   PF_CUDA(h, cudaMemcpyAsync(h->staging, theta, nn * sizeof(double), cudaMemcpyHostToDevice,
                              h->stream));
+  {
+    // non-finite values are found on the device, before the state is touched
+    unsigned int* flag = reinterpret_cast<unsigned int*>(h->staging + nn);
+    unsigned int bits = 0;
+    PF_CUDA(h, launch_flag_nonfinite(h->staging, (long long)nn, flag, h->stream));
+    h->launches++;
+    PF_CUDA(h, cudaMemcpyAsync(&bits, flag, sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
+    PF_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (bits) return fail(h, PF_ERR_BAD_ARG, "non-finite temperature");
+  }
   st = dispatch(h, [&](auto s_t, auto r_t) {
     PF_TYPES(s_t, r_t);
     PF_CUDA(h, launch_set_temperature<S, R>((S*)h->pop[h->cur], (R*)h->aux[h->cur],

@@ -137,5 +137,17 @@ inline bool quat_rows(const double* q, double R[9]) {
   return true;
 }
 
+// Sets *flag when any of the n host-supplied values staged at p is not
+// finite (NaN or infinite): the field setters check their input on the
+// device before it reaches the state.
+static __global__ void k_flag_nonfinite(const double* __restrict__ p, long long n,
+                                        unsigned int* flag) {
+  bool bad = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    bad |= !isfinite(p[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1u);
+}
+
 }  // namespace d3
 }  // namespace pf

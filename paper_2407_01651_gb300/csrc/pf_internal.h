@@ -114,6 +114,9 @@ template <typename S, typename R>
 cudaError_t launch_init_spec(const InitArgs<S, R>& a, cudaStream_t st);
 template <typename S, typename R>
 cudaError_t launch_set_fields(const SetFieldsArgs<S, R>& a, cudaStream_t st);
+// *flag = 1 if any of the n device values at p is NaN or infinite, else 0.
+cudaError_t launch_flag_nonfinite(const double* p, long long n, unsigned int* flag,
+                                  cudaStream_t st);
 template <typename S, typename R>
 cudaError_t launch_state_to_f64(const S* pin, const R* ain, long long ps, long long off,
                                 long long n, double* out, int thermal, cudaStream_t st);

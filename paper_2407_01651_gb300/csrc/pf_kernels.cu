@@ -14,6 +14,8 @@
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 namespace pf {
 
 // ---------------------------------------------------------------------------
@@ -393,6 +395,26 @@ cudaError_t launch_init_spec(const InitArgs<S, R>& a, cudaStream_t st) {
   const long long n = (long long)a.dom.nx * a.dom.ny;
   const int grid = (int)((n + 255) / 256 < 65535 ? (n + 255) / 256 : 65535);
   k_init_spec<S, R><<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Sets *flag when any of n staged host values is not finite; run before the
+// values reach the state.
+__global__ void k_flag_nonfinite(const double* __restrict__ p, long long n,
+                                 unsigned int* flag) {
+  bool bad = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    bad |= !isfinite(p[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1u);
+}
+
+cudaError_t launch_flag_nonfinite(const double* p, long long n, unsigned int* flag,
+                                  cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  const int grid = (int)std::min<long long>((n + 255) / 256, 1024);
+  k_flag_nonfinite<<<std::max(grid, 1), 256, 0, st>>>(p, n, flag);
   return cudaGetLastError();
 }
 

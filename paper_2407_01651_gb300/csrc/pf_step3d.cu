@@ -802,12 +802,22 @@ extern "C" pf_status pf3_init_seeds(pf3_handle* h, const double* seeds, int n_se
 extern "C" pf_status pf3_set_fields(pf3_handle* h, const double* psi, const double* C, size_t n) {
   if (!h) return PF_ERR_BAD_ARG;
   if (!psi || !C || n != h->n) return fail3(h, PF_ERR_BAD_ARG, "need psi and C of nx*ny*nz");
-  for (size_t i = 0; i < n; ++i)
-    if (!std::isfinite(psi[i]) || !std::isfinite(C[i])) return fail3(h, PF_ERR_BAD_ARG, "non-finite field");
-  pf_status st = ensure_scratch3(h, 2 * n);
+  pf_status st = ensure_scratch3(h, 2 * n + 1);
   if (st != PF_OK) return st;
   PF3_CUDA(h, cudaMemcpyAsync(h->scratch, psi, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   PF3_CUDA(h, cudaMemcpyAsync(h->scratch + n, C, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  {
+    // non-finite values are found on the device, before the state is touched
+    unsigned int* flag = reinterpret_cast<unsigned int*>(h->scratch + 2 * n);
+    unsigned int bits = 0;
+    PF3_CUDA(h, cudaMemsetAsync(flag, 0, sizeof(unsigned int), h->stream));
+    k_flag_nonfinite<<<1024, 256, 0, h->stream>>>(h->scratch, (long long)(2 * n), flag);
+    PF3_CUDA(h, cudaGetLastError());
+    h->launches++;
+    PF3_CUDA(h, cudaMemcpyAsync(&bits, flag, sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
+    PF3_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (bits) return fail3(h, PF_ERR_BAD_ARG, "non-finite field");
+  }
   h->cur = 0;
   st = dispatch3(h, [&](auto s_t, auto r_t) {
     using S = decltype(s_t);
@@ -834,13 +844,23 @@ extern "C" pf_status pf3_set_temperature(pf3_handle* h, const double* theta, siz
   if (!h) return PF_ERR_BAD_ARG;
   if (!h->thermal) return fail3(h, PF_ERR_BAD_ARG, "the handle is not in thermal mode");
   if (!theta || n != h->n) return fail3(h, PF_ERR_BAD_ARG, "need theta of nx*ny*nz");
-  for (size_t i = 0; i < n; ++i)
-    if (!std::isfinite(theta[i])) return fail3(h, PF_ERR_BAD_ARG, "non-finite theta");
   if (!h->inited || h->steps != 0)
     return fail3(h, PF_ERR_STATE, "set the temperature after initialisation, before stepping");
-  pf_status st = ensure_scratch3(h, n);
+  pf_status st = ensure_scratch3(h, n + 1);
   if (st != PF_OK) return st;
   PF3_CUDA(h, cudaMemcpyAsync(h->scratch, theta, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  {
+    // non-finite values are found on the device, before the state is touched
+    unsigned int* flag = reinterpret_cast<unsigned int*>(h->scratch + n);
+    unsigned int bits = 0;
+    PF3_CUDA(h, cudaMemsetAsync(flag, 0, sizeof(unsigned int), h->stream));
+    k_flag_nonfinite<<<1024, 256, 0, h->stream>>>(h->scratch, (long long)n, flag);
+    PF3_CUDA(h, cudaGetLastError());
+    h->launches++;
+    PF3_CUDA(h, cudaMemcpyAsync(&bits, flag, sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
+    PF3_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (bits) return fail3(h, PF_ERR_BAD_ARG, "non-finite theta");
+  }
   st = dispatch3(h, [&](auto s_t, auto r_t) {
     using S = decltype(s_t);
     using R = decltype(r_t);

@@ -492,11 +492,21 @@ extern "C" pf_status pf3f_init_spec(pf3f_handle* h, const double* seeds, int n_s
 extern "C" pf_status pf3f_set_fields(pf3f_handle* h, const double* fields7, size_t n) {
   if (!h) return PF_ERR_BAD_ARG;
   if (!fields7 || n != 7 * h->n) return failf(h, PF_ERR_BAD_ARG, "need 7 planes of nx*ny*nz");
-  for (size_t i = 0; i < n; ++i)
-    if (!std::isfinite(fields7[i])) return failf(h, PF_ERR_BAD_ARG, "non-finite field");
-  pf_status st = ensure_scratchf(h, n);
+  pf_status st = ensure_scratchf(h, n + 1);
   if (st != PF_OK) return st;
   PF3F_CUDA(h, cudaMemcpyAsync(h->scratch, fields7, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  {
+    // non-finite values are found on the device, before the state is touched
+    unsigned int* flag = reinterpret_cast<unsigned int*>(h->scratch + n);
+    unsigned int bits = 0;
+    PF3F_CUDA(h, cudaMemsetAsync(flag, 0, sizeof(unsigned int), h->stream));
+    pf::d3::k_flag_nonfinite<<<1024, 256, 0, h->stream>>>(h->scratch, (long long)n, flag);
+    PF3F_CUDA(h, cudaGetLastError());
+    h->launches++;
+    PF3F_CUDA(h, cudaMemcpyAsync(&bits, flag, sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
+    PF3F_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (bits) return failf(h, PF_ERR_BAD_ARG, "non-finite field");
+  }
   h->cur = 0;
   st = dispatchf(h, [&](auto s_t, auto r_t) {
     using S = decltype(s_t);
@@ -685,13 +695,23 @@ extern "C" pf_status pf3f_set_temperature(pf3f_handle* h, const double* theta, s
   if (!h) return PF_ERR_BAD_ARG;
   if (!h->thermal) return failf(h, PF_ERR_BAD_ARG, "the handle is not in thermal mode");
   if (!theta || n != h->n) return failf(h, PF_ERR_BAD_ARG, "need theta of nx*ny*nz");
-  for (size_t i = 0; i < n; ++i)
-    if (!std::isfinite(theta[i])) return failf(h, PF_ERR_BAD_ARG, "non-finite theta");
   if (!h->inited || h->steps != 0)
     return failf(h, PF_ERR_STATE, "set the temperature after initialisation, before stepping");
-  pf_status st = ensure_scratchf(h, n);
+  pf_status st = ensure_scratchf(h, n + 1);
   if (st != PF_OK) return st;
   PF3F_CUDA(h, cudaMemcpyAsync(h->scratch, theta, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  {
+    // non-finite values are found on the device, before the state is touched
+    unsigned int* flag = reinterpret_cast<unsigned int*>(h->scratch + n);
+    unsigned int bits = 0;
+    PF3F_CUDA(h, cudaMemsetAsync(flag, 0, sizeof(unsigned int), h->stream));
+    pf::d3::k_flag_nonfinite<<<1024, 256, 0, h->stream>>>(h->scratch, (long long)n, flag);
+    PF3F_CUDA(h, cudaGetLastError());
+    h->launches++;
+    PF3F_CUDA(h, cudaMemcpyAsync(&bits, flag, sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
+    PF3F_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (bits) return failf(h, PF_ERR_BAD_ARG, "non-finite theta");
+  }
   st = dispatchf(h, [&](auto s_t, auto r_t) {
     using S = decltype(s_t);
     using R = decltype(r_t);

@@ -506,12 +506,19 @@ class Simulation3D:
     def step(self, n: int = 1) -> None:
         _check3(lib().pf3_step(self.h, int(n)), self.h)
 
-    def fields(self) -> dict:
+    def fields(self, out: np.ndarray | None = None) -> dict:
+        """psi, C, U (and theta in thermal mode), [z][y][x]; out: optional
+        float64 buffer of at least field_planes * n values (e.g. page-locked)."""
         k = lib().pf3_field_planes(self.h)
-        out = np.empty(k * self.n)
+        if out is None:
+            out = np.empty(k * self.n)
         _check3(lib().pf3_get_fields(self.h, _dp(out), out.size), self.h)
-        out = out.reshape((k,) + self.shape)
+        out = out.reshape(-1)[: k * self.n].reshape((k,) + self.shape)
         return dict(zip(("psi", "C", "U", "theta"), out))
+
+    @property
+    def field_planes(self) -> int:
+        return lib().pf3_field_planes(self.h)
 
     def get_state(self) -> np.ndarray:
         k = lib().pf3_state_planes(self.h)
@@ -587,7 +594,16 @@ class Simulation3F:
         planes = [phi, psi, C] + [np.zeros(self.shape) if a is None else a for a in (vx, vy, vz, p)]
         a = np.ascontiguousarray(np.stack([np.asarray(q, dtype=np.float64).reshape(self.shape)
                                            for q in planes]))
-        _check3f(lib().pf3f_set_fields(self.h, _dp(a), a.size), self.h)
+        self.set_fields_stack(a)
+
+    def set_fields_stack(self, f7: np.ndarray) -> None:
+        """Initial fields from one C-contiguous float64 block of shape
+        (7, nz, ny, nx) holding phi, psi, C, vx, vy, vz, p, passed to
+        pf3f_set_fields without a copy on the host."""
+        if (not isinstance(f7, np.ndarray) or f7.dtype != np.float64
+                or f7.shape != (7,) + tuple(self.shape) or not f7.flags["C_CONTIGUOUS"]):
+            raise ValueError(f"f7 must be a C-contiguous float64 array of shape (7, {self.shape})")
+        _check3f(lib().pf3f_set_fields(self.h, _dp(f7), f7.size), self.h)
 
     @property
     def rho_bar(self) -> float:
@@ -618,11 +634,18 @@ class Simulation3F:
     def step(self, n: int = 1) -> None:
         _check3f(lib().pf3f_step(self.h, int(n)), self.h)
 
-    def fields(self) -> dict:
+    def fields(self, out: np.ndarray | None = None) -> dict:
+        """FIELDS_3F planes, [z][y][x]; out: optional float64 buffer of at
+        least field_planes * n values (e.g. page-locked)."""
         k = lib().pf3f_field_planes(self.h)
-        out = np.empty(k * self.n)
+        if out is None:
+            out = np.empty(k * self.n)
         _check3f(lib().pf3f_get_fields(self.h, _dp(out), out.size), self.h)
-        return dict(zip(FIELDS_3F, out.reshape((k,) + self.shape)))
+        return dict(zip(FIELDS_3F, out.reshape(-1)[: k * self.n].reshape((k,) + self.shape)))
+
+    @property
+    def field_planes(self) -> int:
+        return lib().pf3f_field_planes(self.h)
 
     def get_state(self) -> np.ndarray:
         k = lib().pf3f_state_planes(self.h)

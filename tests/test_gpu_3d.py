@@ -130,6 +130,18 @@ def test_3d_configuration_errors():
     with pytest.raises(pf.PFError) as e:
         sim.step(1)                        # not initialised
     assert e.value.code == pf.PF_ERR_STATE
+    # non-finite input is rejected on the device and leaves the state as it was
+    psi = np.full((8, 8, 8), -1.0)
+    C = np.ones((8, 8, 8))
+    sim.set_fields(psi, C)
+    s0 = sim.get_state()
+    for bad in (np.nan, np.inf):
+        C2 = C.copy()
+        C2[3, 5, 7] = bad
+        with pytest.raises(pf.PFError) as e:
+            sim.set_fields(psi, C2)
+        assert e.value.code == pf.PF_ERR_BAD_ARG and "non-finite" in str(e.value)
+    assert np.array_equal(sim.get_state(), s0)
 
 
 # ---------------------------------------------------------------------------
@@ -261,6 +273,13 @@ def test_3d_thermal_configuration_errors():
         sim.set_temperature(np.zeros((8, 8, 8)))          # not initialised
     assert e.value.code == pf.PF_ERR_STATE
     sim.init_seeds([(4, 4, 4)], 2.0)
+    s0 = sim.get_state()
+    th = np.full((8, 8, 8), -0.5)
+    th[2, 3, 4] = np.nan
+    with pytest.raises(pf.PFError) as e:
+        sim.set_temperature(th)                            # found on the device
+    assert e.value.code == pf.PF_ERR_BAD_ARG and "non-finite" in str(e.value)
+    assert np.array_equal(sim.get_state(), s0)
     sim.step(1)
     with pytest.raises(pf.PFError) as e:
         sim.set_temperature(np.zeros((8, 8, 8)))          # already stepped

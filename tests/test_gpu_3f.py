@@ -166,6 +166,16 @@ def test_3f_configuration_errors():
     assert e.value.code == pf.PF_ERR_STATE
     with pytest.raises(pf.PFError):
         sim.set_fields(*[np.full((8, 8, 8), np.nan)] * 3)
+    # one non-finite value anywhere is found on the device; the state is kept
+    one = np.ones((8, 8, 8))
+    sim.set_fields(one, -one, one)
+    s0 = sim.get_state()
+    vz = np.zeros((8, 8, 8))
+    vz[1, 2, 3] = np.inf
+    with pytest.raises(pf.PFError) as e:
+        sim.set_fields(one, -one, one, vz=vz)
+    assert e.value.code == pf.PF_ERR_BAD_ARG and "non-finite" in str(e.value)
+    assert np.array_equal(sim.get_state(), s0)
 
 
 def test_3f_free_rates_and_gravity():
@@ -372,6 +382,13 @@ def test_3f_thermal_configuration_errors():
         iso.reduce_thermal()
     sim = pf.Simulation3F((8, 8, 8), dict(wl.BASE_PARAMS, **T3F), "fp32")
     sim.init_spec([(4, 4, 4)], 2.0, [])
+    s0 = sim.get_state()
+    th = np.full((8, 8, 8), -0.5)
+    th[7, 0, 1] = np.inf
+    with pytest.raises(pf.PFError) as e:
+        sim.set_temperature(th)                            # found on the device
+    assert e.value.code == pf.PF_ERR_BAD_ARG and "non-finite" in str(e.value)
+    assert np.array_equal(sim.get_state(), s0)
     sim.step(1)
     with pytest.raises(pf.PFError) as e:
         sim.set_temperature(np.zeros((8, 8, 8)))

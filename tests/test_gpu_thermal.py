@@ -126,6 +126,13 @@ def test_set_temperature_matches_oracle():
     o.init_fields(phi, psi, C, theta=th)
     sim = pf.Simulation([(N, N)], par, "fp64")
     sim.init_fields(0, lay.seeds, lay.R_s, [])
+    s0 = sim.get_state(0)
+    bad = th.copy()
+    bad[5, 9] = np.nan
+    with pytest.raises(pf.PFError) as e:
+        sim.set_temperature(0, bad)         # found on the device, state untouched
+    assert e.value.code == pf.PF_ERR_BAD_ARG and "non-finite" in str(e.value)
+    assert np.array_equal(sim.get_state(0), s0)
     sim.set_temperature(0, th)
     compare(o, sim, 1e-12, names=("theta", "psi"))
     o.step(20)
