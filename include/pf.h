@@ -327,7 +327,8 @@ pf_status pf_reduce_noalloc(const void *fields, int fields_fp64, long long plane
 /* Boundary types of a domain side (Section 3: half-way bounce-back for no-slip
  * walls and no-flux scalars, the symmetric scheme for symmetry planes;
  * Section 4: far-field Dirichlet values).  Every side sits half-way between
- * the last site and its ghost. */
+ * the last site and its ghost, except the velocity of PF_BC_INLET_NEE, which is
+ * imposed at the ghost node itself. */
 enum {
   PF_BC_PERIODIC = 0,   /* wraps to the opposite side (which must be periodic too)   */
   PF_BC_SYMMETRIC = 1,  /* mirror plane: populations reflected, normal velocity flipped */
@@ -336,8 +337,14 @@ enum {
                            theta = theta0 by anti-bounce-back                         */
   PF_BC_INLET = 4,      /* velocity (vin_x, vin_y) by moving-wall bounce-back; liquid
                            phi = 1 and the far-field psi, C, theta by anti-bounce-back */
-  PF_BC_OUTLET = 5      /* pressure p = 0 for the flow (anti-bounce-back); zero gradient
+  PF_BC_OUTLET = 5,     /* pressure p = 0 for the flow (anti-bounce-back); zero gradient
                            for phi, psi, C, theta                                       */
+  PF_BC_INLET_NEE = 6   /* velocity (vin_x, vin_y) by non-equilibrium extrapolation
+                           (Section 3): the boundary node is the ghost one site beyond
+                           the side, its NS populations the equilibrium at vin with the
+                           liquid density plus the neighbouring site's non-equilibrium
+                           part (pressure extrapolated); phi, psi, C, theta as
+                           PF_BC_INLET                                                  */
 };
 
 /* Boundary types of domain dom's sides, bc = {x-, x+, y-, y+}, before

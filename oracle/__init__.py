@@ -199,7 +199,9 @@ class Oracle:
         2 wall (half-way bounce-back), 3 far field (wall for the flow and phi,
         Dirichlet psi = -1, C = 1, theta = theta0), 4 inlet (velocity
         (vin_x, vin_y), liquid phi = 1, far-field scalars), 5 outlet (zero
-        gradient).  Set before initialising."""
+        gradient), 6 inlet whose velocity is imposed by non-equilibrium
+        extrapolation at the ghost node (the scalars as 4).  Set before
+        initialising."""
         self.lib.or_set_bc(self.h, int(xm), int(xp), int(ym), int(yp))
 
     def set_rho_bar(self, rho_bar: float) -> None:

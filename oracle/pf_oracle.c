@@ -121,7 +121,7 @@ enum {
 /* Boundary type of each side (reading R31): x- (left), x+ (right), y- (bottom),
  * y+ (top), all at the half-way position between the last site and its ghost. */
 enum { BC_PERIODIC = 0, BC_SYMMETRIC = 1, BC_WALL = 2, BC_FARFIELD = 3, BC_INLET = 4,
-       BC_OUTLET = 5 };
+       BC_OUTLET = 5, BC_INLET_NEE = 6 };
 
 typedef struct {
   int nx, ny, n;
@@ -618,21 +618,26 @@ static const double PSI_FAR = -1.0, C_FAR = 1.0;
  * direction (half-way bounce-back), which the far-field side turns into an
  * anti-bounce-back on the lattices with a Dirichlet value and the inlet into a
  * moving-wall bounce-back for the flow and anti-bounce-backs for the scalars.
- * Returns 0 (plain or reflected source), 1 (wall), 2 (far field), 3 (inlet)
- * or 4 (outlet, clamped source), a bounce winning over the rest where two
- * sides are crossed; *src and *q give the site and the direction to read. */
+ * Returns 0 (plain or reflected source), 1 (wall), 2 (far field), 3 (inlet),
+ * 4 (outlet, clamped source) or 5 (non-equilibrium extrapolation inlet: the
+ * source is the boundary node, a ghost one site beyond the side, whose
+ * populations the caller builds from the fluid site next to it, returned in
+ * *src), a bounce winning over the rest where two sides are crossed, then
+ * the extrapolation, then the clamp; *src and *q give the site and the
+ * direction to read. */
 static int bounce_rank(int t) {
   return t == BC_WALL ? 1 : (t == BC_FARFIELD ? 2 : (t == BC_INLET ? 3 : 0));
 }
 
 static int pull_src(const ostate *st, int x, int y, int i, int *src, int *q) {
   const int nx = st->nx, ny = st->ny;
-  int sx = x - CX[i], sy = y - CY[i], qi = i, bounce = 0, outlet = 0;
+  int sx = x - CX[i], sy = y - CY[i], qi = i, bounce = 0, outlet = 0, nee = 0;
   if (sx < 0 || sx >= nx) {
     const int t = st->bc[sx < 0 ? 0 : 1];
     if (t == BC_PERIODIC) sx = wrap(sx, nx);
     else if (t == BC_SYMMETRIC) { sx = sx < 0 ? -1 - sx : 2 * nx - 1 - sx; qi = MIRX[qi]; }
     else if (t == BC_OUTLET) { sx = sx < 0 ? 0 : nx - 1; outlet = 1; }
+    else if (t == BC_INLET_NEE) { sx = sx < 0 ? 0 : nx - 1; nee = 1; }
     else if (bounce_rank(t) > bounce) bounce = bounce_rank(t);
   }
   if (sy < 0 || sy >= ny) {
@@ -640,12 +645,23 @@ static int pull_src(const ostate *st, int x, int y, int i, int *src, int *q) {
     if (t == BC_PERIODIC) sy = wrap(sy, ny);
     else if (t == BC_SYMMETRIC) { sy = sy < 0 ? -1 - sy : 2 * ny - 1 - sy; qi = MIRY[qi]; }
     else if (t == BC_OUTLET) { sy = sy < 0 ? 0 : ny - 1; outlet = 1; }
+    else if (t == BC_INLET_NEE) { sy = sy < 0 ? 0 : ny - 1; nee = 1; }
     else if (bounce_rank(t) > bounce) bounce = bounce_rank(t);
   }
   if (bounce) { *src = y * nx + x; *q = OPP[i]; return bounce; }
   *src = sy * nx + sx;
   *q = qi;
-  return outlet ? 4 : 0;
+  return nee ? 5 : (outlet ? 4 : 0);
+}
+
+/* The lattices other than NS see a non-equilibrium-extrapolation inlet as an
+ * inlet (reading R37): anti-bounce-back at the site itself. */
+static int scalar_src(const ostate *st, int x, int y, int i, int *src, int *q) {
+  const int mode = pull_src(st, x, y, i, src, q);
+  if (mode != 5) return mode;
+  *src = y * st->nx + x;
+  *q = OPP[i];
+  return 3;
 }
 
 /* Kinds of field read on the stencil neighbourhood, for the ghost values. */
@@ -665,12 +681,14 @@ static real_t ghost_map(const ostate *st, int t, int axis, int kind, real_t v) {
     const int normal = (kind == GK_VX) == (axis == 0);
     if (t == BC_SYMMETRIC) return normal ? -v : v;
     if (t == BC_INLET) return 2.0 * st->par[kind == GK_VX ? P_VIN_X : P_VIN_Y] - v;
+    /* the extrapolation inlet's boundary node is the ghost itself */
+    if (t == BC_INLET_NEE) return st->par[kind == GK_VX ? P_VIN_X : P_VIN_Y];
     return -v;
   }
-  if (t == BC_FARFIELD || t == BC_INLET) {
+  if (t == BC_FARFIELD || t == BC_INLET || t == BC_INLET_NEE) {
     if (kind == GK_PSI) return 2.0 * PSI_FAR - v;
     if (kind == GK_U) return -v;                 /* U = 0 at psi = -1, C = 1 */
-    if (kind == GK_NOFLUX && t == BC_INLET) return 2.0 * 1.0 - v;   /* liquid inflow */
+    if (kind == GK_NOFLUX && t != BC_FARFIELD) return 2.0 * 1.0 - v;   /* liquid inflow */
   }
   return v;
 }
@@ -710,11 +728,28 @@ static void pass_stream(ostate *st) {
       real_t phi = 0, psi = 0, C = 0, psio = 0;
       int src, q;
       for (int i = 0; i < 9; ++i) {
-        const int mode = pull_src(st, x, y, i, &src, &q);
+        int mode = pull_src(st, x, y, i, &src, &q);
         /* NS and CAC: bounce-back at walls and far-field sides; at an inlet the
          * moving-wall bounce-back f*_opp + 2 rho_l w_i c_i.u_in / cs2 and the
          * anti-bounce-back to phi = 1 (reading R32) */
-        if (mode == 3) {
+        if (mode == 5) {
+          /* non-equilibrium extrapolation (Section 3, reading R37): the ghost
+           * node's post-collision population is the equilibrium at u_in and
+           * the liquid density plus the fluid neighbour's non-equilibrium
+           * part, f_q^eq(p_b, rho_l, u_in) + f*_q(x_f) - f_q^eq(p_f, rho_f, v_f),
+           * with the pressure extrapolated (p_b = p_f), so that only the
+           * momentum parts of the equilibria remain (last step's rho and v
+           * of the fluid site) */
+          const real_t vbx = st->par[P_VIN_X], vby = st->par[P_VIN_Y];
+          const real_t ux = st->vx_o[src], uy = st->vy_o[src];
+          const real_t rho_f = st->par[P_RHO_G] + st->phi_o[src] * (st->par[P_RHO_L] - st->par[P_RHO_G]);
+          const real_t cb = CX[q] * vbx + CY[q] * vby, cf = CX[q] * ux + CY[q] * uy;
+          const real_t sb = W9[q] * (cb / CS2 + cb * cb / (2.0 * CS2 * CS2) - (vbx * vbx + vby * vby) / (2.0 * CS2));
+          const real_t sf = W9[q] * (cf / CS2 + cf * cf / (2.0 * CS2 * CS2) - (ux * ux + uy * uy) / (2.0 * CS2));
+          st->fS[i][idx] = st->f[q][src] + st->par[P_RHO_L] * sb - rho_f * sf;
+          mode = scalar_src(st, x, y, i, &src, &q);
+          st->hS[i][idx] = -st->h[q][src] + 2.0 * W9[i] * 1.0;
+        } else if (mode == 3) {
           const real_t cu = CX[i] * st->par[P_VIN_X] + CY[i] * st->par[P_VIN_Y];
           st->fS[i][idx] = st->f[q][src] + 2.0 * st->par[P_RHO_L] * W9[i] * cu / CS2;
           st->hS[i][idx] = -st->h[q][src] + 2.0 * W9[i] * 1.0;
@@ -735,7 +770,7 @@ static void pass_stream(ostate *st) {
         phi += st->hS[i][idx];
       }
       for (int i = 0; i < 5; ++i) {
-        const int mode = pull_src(st, x, y, i, &src, &q);
+        const int mode = scalar_src(st, x, y, i, &src, &q);
         /* anti-bounce-back to the far-field values: -f*_opp + 2 w_i X_far */
         st->sS[i][idx] = (mode == 2 || mode == 3) ? -st->s[q][src] + 2.0 * W5[i] * C_FAR : st->s[q][src];
         C += st->sS[i][idx];
@@ -753,7 +788,7 @@ static void pass_stream(ostate *st) {
       /* temperature populations (thermal mode): plain pull, and the
        * supersaturation field whose gradient enters grad F(U) */
       for (int i = 0; i < 5; ++i) {
-        const int mode = pull_src(st, x, y, i, &src, &q);
+        const int mode = scalar_src(st, x, y, i, &src, &q);
         st->eS[i][idx] = (mode == 2 || mode == 3) ? -st->e[q][src] + 2.0 * W5[i] * st->par[P_THETA0]
                                    : st->e[q][src];
       }

@@ -1136,8 +1136,8 @@ extern "C" pf_status pf_set_boundaries(pf_handle* h, int dom, const int bc[4]) {
   if (dom < 0 || dom >= (int)h->doms.size() || !bc)
     return fail(h, PF_ERR_BAD_ARG, "bad domain index or NULL bc");
   for (int k = 0; k < 4; ++k)
-    if (bc[k] < PF_BC_PERIODIC || bc[k] > PF_BC_OUTLET)
-      return fail(h, PF_ERR_BAD_ARG, "boundary types are 0 (periodic) .. 5 (outlet)");
+    if (bc[k] < PF_BC_PERIODIC || bc[k] > PF_BC_INLET_NEE)
+      return fail(h, PF_ERR_BAD_ARG, "boundary types are 0 (periodic) .. 6 (extrapolation inlet)");
   if ((bc[0] == PF_BC_PERIODIC) != (bc[1] == PF_BC_PERIODIC) ||
       (bc[2] == PF_BC_PERIODIC) != (bc[3] == PF_BC_PERIODIC))
     return fail(h, PF_ERR_BAD_ARG, "a periodic side needs a periodic opposite side");
@@ -1152,7 +1152,8 @@ extern "C" pf_status pf_set_boundaries(pf_handle* h, int dom, const int bc[4]) {
   for (const DomDesc& d : h->ddesc)
     for (int k = 0; k < 4; ++k) {
       if (d.bc[k]) h->any_bc = 1;
-      if (d.bc[k] == PF_BC_INLET || d.bc[k] == PF_BC_OUTLET) h->any_io = 1;
+      if (d.bc[k] == PF_BC_INLET || d.bc[k] == PF_BC_OUTLET || d.bc[k] == PF_BC_INLET_NEE)
+        h->any_io = 1;
     }
   if (h->any_bc && h->variant != STEP_YMARCH) {
     h->variant = STEP_YMARCH;

@@ -61,9 +61,10 @@ enum Field : int { FLD_PHI, FLD_PSI, FLD_C, FLD_U, FLD_P, FLD_VX, FLD_VY, FLD_MU
 // anti-bounce-back).
 // Inlet: velocity u_in by moving-wall bounce-back, liquid phi = 1 and the far
 // field for psi, C, theta; outlet: pressure p = 0 for the flow, zero gradient
-// for the rest.
+// for the rest; extrapolation inlet: velocity u_in at the ghost node by
+// non-equilibrium extrapolation for the flow, the rest as the inlet.
 enum BoundaryType : int { BC_PERIODIC = 0, BC_SYMMETRIC = 1, BC_WALL = 2, BC_FARFIELD = 3,
-                          BC_INLET = 4, BC_OUTLET = 5 };
+                          BC_INLET = 4, BC_OUTLET = 5, BC_INLET_NEE = 6 };
 
 struct DomDesc {
   long long off;      // first site of the domain in every plane

@@ -11,13 +11,17 @@
 //     and an anti-bounce-back -f*_opp + 2 w_i X_far for psi, C and theta; an
 //     inlet adds the moving-wall term 2 rho_l w_i c_i.u_in / c_s^2 for NS and
 //     anti-bounces CAC to phi = 1; an outlet anti-bounces NS to p = 0 and
-//     clamps the other lattices' source to the last site; a bounce wins where
-//     two sides are crossed, then the clamp, then the reflection;
+//     clamps the other lattices' source to the last site; an extrapolation
+//     inlet gives NS the ghost node's populations f*(x_f) + rho_l s(u_in) -
+//     rho_f s(v_f) from the fluid site x_f next to it and treats the other
+//     lattices as an inlet; a bounce wins where two sides are crossed, then
+//     the extrapolation, then the clamp, then the reflection;
 //   - stencils: ghost rows and columns of the shared-memory ring hold the
 //     mirror site's values mapped per side (phi, psi, U unchanged, or
 //     2 X_far - X for psi and U at a far-field side or inlet, 2 - phi at an
 //     inlet; the velocity's normal component flipped at a symmetric side, both
-//     components at a wall or far field, 2 u_in - v at an inlet; everything
+//     components at a wall or far field, 2 u_in - v at an inlet, u_in at an
+//     extrapolation inlet; everything
 //     copied at an outlet; corners: the y side's map, then the x side's).
 // Sites away from a non-periodic side take the periodic pulls of pf_pull.cuh.
 // FP32 and FP64 storage only.
@@ -58,7 +62,9 @@ __device__ __forceinline__ unsigned site_at(const DomDesc& d, int x, int y) {
 
 // Source of the population of direction i pulled by (x, y): site, direction
 // to read and mode (0 plain or reflected, 1 wall bounce, 2 far-field bounce,
-// 3 inlet bounce, 4 outlet: source clamped to the last site).
+// 3 inlet bounce, 4 outlet: source clamped to the last site, 5 extrapolation
+// inlet: the source is the ghost node beyond the side, whose NS population is
+// built from the fluid site next to it, the one returned).
 struct PullSrc {
   unsigned site;
   int q, mode;
@@ -72,12 +78,13 @@ __device__ __forceinline__ int bounce_rank(int t) {
 template <bool IO>
 __device__ __forceinline__ PullSrc pull_src(const DomDesc& d, int x, int y, int i) {
   const int nx = d.nx, ny = d.ny;
-  int sx = x - cx9(i), sy = y - cy9(i), q = i, bounce = 0, outlet = 0;
+  int sx = x - cx9(i), sy = y - cy9(i), q = i, bounce = 0, outlet = 0, nee = 0;
   if (sx < 0 || sx >= nx) {
     const int t = d.bc[sx < 0 ? 0 : 1];
     if (t == BC_PERIODIC) sx += sx < 0 ? nx : -nx;
     else if (t == BC_SYMMETRIC) { sx = sx < 0 ? -1 - sx : 2 * nx - 1 - sx; q = mirx9(q); }
     else if (IO && t == BC_OUTLET) { sx = sx < 0 ? 0 : nx - 1; outlet = 1; }
+    else if (IO && t == BC_INLET_NEE) { sx = sx < 0 ? 0 : nx - 1; nee = 1; }
     else bounce = bounce_rank<IO>(t);
   }
   if (sy < 0 || sy >= ny) {
@@ -85,10 +92,20 @@ __device__ __forceinline__ PullSrc pull_src(const DomDesc& d, int x, int y, int 
     if (t == BC_PERIODIC) sy += sy < 0 ? ny : -ny;
     else if (t == BC_SYMMETRIC) { sy = sy < 0 ? -1 - sy : 2 * ny - 1 - sy; q = miry9(q); }
     else if (IO && t == BC_OUTLET) { sy = sy < 0 ? 0 : ny - 1; outlet = 1; }
+    else if (IO && t == BC_INLET_NEE) { sy = sy < 0 ? 0 : ny - 1; nee = 1; }
     else bounce = max(bounce, bounce_rank<IO>(t));
   }
   if (bounce) return {site_at(d, x, y), opp9(i), bounce};
-  return {site_at(d, sx, sy), q, outlet ? 4 : 0};
+  return {site_at(d, sx, sy), q, nee ? 5 : (outlet ? 4 : 0)};
+}
+
+// The lattices other than NS see an extrapolation inlet as an inlet:
+// anti-bounce-back at the site itself.
+template <bool IO>
+__device__ __forceinline__ PullSrc scalar_src(const DomDesc& d, int x, int y, int i) {
+  PullSrc p = pull_src<IO>(d, x, y, i);
+  if (IO && p.mode == 5) p = {site_at(d, x, y), opp9(i), 3};
+  return p;
 }
 
 // A pull source of (x, y) lies beyond a non-periodic side.
@@ -106,12 +123,13 @@ __device__ __forceinline__ R ghost_map(const KParams<R>& kp, int t, int axis, in
     const bool normal = (field == 2) == (axis == 0);
     if (t == BC_SYMMETRIC) return normal ? -v : v;
     if (IO && t == BC_INLET) return R(2) * (field == 2 ? kp.vin_x : kp.vin_y) - v;
+    if (IO && t == BC_INLET_NEE) return field == 2 ? kp.vin_x : kp.vin_y;   // the ghost is the node
     return -v;
   }
-  if (t == BC_FARFIELD || (IO && t == BC_INLET)) {
+  if (t == BC_FARFIELD || (IO && (t == BC_INLET || t == BC_INLET_NEE))) {
     if (field == 1) return R(-2) - v;   // 2 psi_far - psi, psi_far = -1
     if (field == 4) return -v;          // 2 U_far - U, U_far = 0
-    if (IO && field == 0 && t == BC_INLET) return R(2) - v;   // liquid inflow, phi = 1
+    if (IO && field == 0 && t != BC_FARFIELD) return R(2) - v;   // liquid inflow, phi = 1
   }
   return v;
 }
@@ -124,7 +142,7 @@ __device__ __forceinline__ void pull_hg_b(const StepArgs<S, R>& a, const DomDesc
   CSum<R> sh;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    const PullSrc p = pull_src<IO>(d, x, y, i);
+    const PullSrc p = scalar_src<IO>(d, x, y, i);
     R v = ld<R>(pbase<BIG>(a.in, P_H + p.q, ps), pidx<BIG>(P_H + p.q, ps, p.site));
     if (IO && p.mode == 3) v = -v + R(2) * w9<R>(i) * R(1);   // inlet: phi = 1
     h[i] = v;
@@ -135,7 +153,7 @@ __device__ __forceinline__ void pull_hg_b(const StepArgs<S, R>& a, const DomDesc
   R po = R(0);
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    const PullSrc p = pull_src<IO>(d, x, y, i);
+    const PullSrc p = scalar_src<IO>(d, x, y, i);
     const R gold = ld<R>(pbase<BIG>(a.in, P_GPRE + i, ps), pidx<BIG>(P_GPRE + i, ps, own));
     R gpo = ld<R>(pbase<BIG>(a.in, P_GPOST + p.q, ps), pidx<BIG>(P_GPOST + p.q, ps, p.site));
     if (p.mode == 2 || p.mode == 3) gpo = -gpo + R(2) * w5<R>(i) * R(-1);
@@ -173,12 +191,28 @@ __device__ __forceinline__ void load_site_b(const StepArgs<S, R>& a, const DomDe
       if (IO && p.mode == 3)   // inlet: moving-wall bounce-back
         v += R(2) * (a.kp.rho_g + a.kp.drho) * w9<R>(i) * R(3) *
              (R(cx9(i)) * a.kp.vin_x + R(cy9(i)) * a.kp.vin_y);
+      if (IO && p.mode == 5) {
+        // extrapolation inlet: the ghost node's post-collision population is
+        // f_q^eq(p_b, rho_l, u_in) + f*_q(x_f) - f_q^eq(p_f, rho_f, v_f) with
+        // p_b = p_f, i.e. f*_q(x_f) + rho_l s_q(u_in) - rho_f s_q(v_f), with
+        // s_q(v) = w_q [3 c.v + 4.5 (c.v)^2 - 1.5 v^2] and the fluid site's
+        // last-step rho and v
+        const R fx = ld<R>(pbase<BIG>(a.ain, A_VXO, ps), pidx<BIG>(A_VXO, ps, p.site));
+        const R fy = ld<R>(pbase<BIG>(a.ain, A_VYO, ps), pidx<BIG>(A_VYO, ps, p.site));
+        const R fphi = ld<R>(pbase<BIG>(a.ain, A_PHIO, ps), pidx<BIG>(A_PHIO, ps, p.site));
+        const R cb = R(cx9(p.q)) * a.kp.vin_x + R(cy9(p.q)) * a.kp.vin_y;
+        const R cf = R(cx9(p.q)) * fx + R(cy9(p.q)) * fy;
+        const R sb = R(3) * cb + R(4.5) * cb * cb -
+                     R(1.5) * (a.kp.vin_x * a.kp.vin_x + a.kp.vin_y * a.kp.vin_y);
+        const R sf = R(3) * cf + R(4.5) * cf * cf - R(1.5) * (fx * fx + fy * fy);
+        v += w9<R>(p.q) * ((a.kp.rho_g + a.kp.drho) * sb - (a.kp.rho_g + fphi * a.kp.drho) * sf);
+      }
       in.f[i] = v;
     }
   }
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    const PullSrc p = pull_src<IO>(d, x, y, i);
+    const PullSrc p = scalar_src<IO>(d, x, y, i);
     R v = ld<R>(pbase<BIG>(a.in, P_S + p.q, ps), pidx<BIG>(P_S + p.q, ps, p.site));
     if (p.mode == 2 || p.mode == 3) v = -v + R(2) * w5<R>(i) * R(1);   // C_far = 1
     in.s[i] = v;
@@ -201,7 +235,7 @@ __device__ __forceinline__ R pull_U_b(const StepArgs<S, R>& a, const DomDesc& d,
   CSum<R> cs;
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    const PullSrc p = pull_src<IO>(d, x, y, i);
+    const PullSrc p = scalar_src<IO>(d, x, y, i);
     R v = ld<R>(pbase<BIG>(a.in, P_S + p.q, ps), pidx<BIG>(P_S + p.q, ps, p.site));
     if (p.mode == 2 || p.mode == 3) v = -v + R(2) * w5<R>(i) * R(1);
     cs.add(v);

@@ -20,6 +20,7 @@ PF_OK, PF_ERR_BAD_ARG, PF_ERR_OOM, PF_ERR_CUDA, PF_ERR_TIMEOUT, PF_ERR_NAN, PF_E
 PF_FP64, PF_FP32, PF_FP16_OFFSET, PF_BF16_OFFSET = 0, 1, 2, 3
 PRECISIONS = {"fp64": PF_FP64, "fp32": PF_FP32, "fp16": PF_FP16_OFFSET, "bf16": PF_BF16_OFFSET}
 BC_PERIODIC, BC_SYMMETRIC, BC_WALL, BC_FARFIELD, BC_INLET, BC_OUTLET = 0, 1, 2, 3, 4, 5
+BC_INLET_NEE = 6
 FIELDS = ("phi", "psi", "C", "U", "p", "vx", "vy", "mu", "theta")
 STATE_PLANES = 39            # PF_STATE_PLANES; thermal handles have 45
 
@@ -290,7 +291,8 @@ class Simulation:
     # -- initialisation --------------------------------------------------------
     def set_boundaries(self, dom: int, xm: int, xp: int, ym: int, yp: int) -> None:
         """Side types x-, x+, y-, y+ of a domain before its initialisation:
-        BC_PERIODIC, BC_SYMMETRIC, BC_WALL, BC_FARFIELD, BC_INLET or BC_OUTLET."""
+        BC_PERIODIC, BC_SYMMETRIC, BC_WALL, BC_FARFIELD, BC_INLET, BC_OUTLET or
+        BC_INLET_NEE."""
         bc = (ctypes.c_int * 4)(int(xm), int(xp), int(ym), int(yp))
         _check(lib().pf_set_boundaries(self.h, int(dom), bc), self.h)
 

@@ -156,3 +156,22 @@ def mass_flux_deviation(kind: str = "2d", lib=None):
     o.step(MASS_FLUX_T)
     f = o.fields()
     return float(np.abs(f["vx"] - V).max() / V), float(np.abs(f["vy"]).max())
+
+
+# ---------------------------------------------------------------------------
+# Dirichlet velocity by non-equilibrium extrapolation (Section 3): the ghost
+# node one site beyond the side carries the velocity.
+# ---------------------------------------------------------------------------
+def nee_couette_holds(lib=None, ny=16, U=0.01) -> bool:
+    """Couette flow between a tangential extrapolation inlet (bottom) and a
+    no-slip wall (top, half-way): linear through the ghost node, v_x = U (ny -
+    1/2 - y) / (ny + 1/2), to 1e-12."""
+    p = dict(wl.BASE_PARAMS, g=0.0, vin_x=U, vin_y=0.0, nu=0.5)
+    one = np.ones((ny, 4))
+    o = oracle.Oracle(4, ny, p, lib=lib)
+    o.set_bc(0, 0, 6, 2)
+    o.init_fields(one, -one, one, 0 * one, 0 * one, 0 * one)
+    o.step(20000)
+    v = o.fields(("vx",))["vx"][:, 0]
+    y = np.arange(ny)
+    return bool(np.abs(v - U * (ny - 0.5 - y) / (ny + 0.5)).max() < 1e-12)

@@ -14,6 +14,7 @@ import math
 import numpy as np
 
 import oracle
+import pin_cases
 from paper_2407_01651_gb300 import workload as wl
 
 PERIODIC, SYMMETRIC, WALL, FARFIELD = 0, 1, 2, 3
@@ -129,7 +130,7 @@ def test_far_field_dirichlet_against_the_diffusion_series():
     assert np.abs(f["psi"] + 1).max() < 1e-14
 
 
-INLET, OUTLET = 4, 5
+INLET, OUTLET, INLET_NEE = 4, 5, 6
 
 
 def test_plug_flow_through_inlet_and_outlet_is_exact():
@@ -199,3 +200,83 @@ def test_forced_convection_favours_the_upstream_arm():
     assert up > down + 0.3 and up > normal + 0.5
     up0, down0, normal0 = _forced_convection(0.0)
     assert abs(up0 - down0) < 0.05
+
+
+# ---------------------------------------------------------------------------
+# Dirichlet velocity by non-equilibrium extrapolation (Section 3, reading R37):
+# the boundary node is the ghost one site beyond the side; its NS populations
+# are the equilibrium at u_in plus the non-equilibrium part of the fluid site
+# next to it.
+# ---------------------------------------------------------------------------
+def test_nee_inlet_plug_flow_is_exact():
+    """Uniform liquid inflow through a symmetric channel is an exact steady
+    state with the extrapolation inlet too: the fluid site's non-equilibrium
+    part is the ghost's, so nothing changes."""
+    nx, ny, vin = 8, 40, 0.01
+    p = dict(wl.BASE_PARAMS, g=0.0, vin_y=vin)
+    one = np.ones((ny, nx))
+    o = oracle.Oracle(nx, ny, p)
+    o.set_bc(SYMMETRIC, SYMMETRIC, INLET_NEE, OUTLET)
+    o.init_fields(one, -one, one, 0 * one, vin * one, 0 * one)
+    o.step(400)
+    f = o.fields(("vx", "vy", "p", "phi", "C", "psi"))
+    assert np.abs(f["vy"] / vin - 1).max() < 1e-12
+    assert np.abs(f["vx"]).max() < 1e-15 and np.abs(f["p"]).max() < 1e-14
+    for k, v in (("phi", 1.0), ("C", 1.0), ("psi", -1.0)):
+        assert np.abs(f[k] - v).max() < 1e-14, k
+
+
+def _couette(bc, ny=16, U=0.01):
+    nx = 4
+    p = dict(wl.BASE_PARAMS, g=0.0, vin_x=U, vin_y=0.0, nu=0.5)
+    one = np.ones((ny, nx))
+    o = oracle.Oracle(nx, ny, p)
+    o.set_bc(PERIODIC, PERIODIC, bc, WALL)
+    o.init_fields(one, -one, one, 0 * one, 0 * one, 0 * one)
+    o.step(20000)
+    return o.fields(("vx", "vy"))
+
+
+def test_nee_inlet_is_node_based_in_couette_flow():
+    """A tangential velocity U imposed on the bottom side against a no-slip
+    wall at the top (half-way, y = ny - 1/2) drives Couette flow, whose
+    steady profile is linear between the two boundary positions.  With the
+    extrapolation the velocity is imposed at the boundary node y = -1: v_x =
+    U (ny - 1/2 - y) / (ny + 1/2) to 1e-12 (measured 4e-14).  The moving-wall
+    inlet imposes it half-way, at y = -1/2, and gives U (ny - 1/2 - y) / ny
+    instead; the two lines differ by 3 % of U."""
+    ny, U = 16, 0.01
+    y = np.arange(ny)
+    node = U * (ny - 0.5 - y) / (ny + 0.5)
+    half = U * (ny - 0.5 - y) / ny
+    f = _couette(INLET_NEE, ny, U)
+    assert np.abs(f["vx"][:, 0] - node).max() < 1e-12 * U / 1e-2
+    assert np.abs(f["vy"]).max() < 1e-15
+    assert pin_cases.nee_couette_holds()
+    g = _couette(INLET, ny, U)
+    assert np.abs(g["vx"][:, 0] - half).max() < 1e-10
+    assert np.abs(node - half).max() > 0.02 * U
+
+
+def test_nee_inflow_between_walls_keeps_one_flux_and_develops_poiseuille():
+    """A uniform inflow imposed by extrapolation between no-slip walls: the
+    volume flux is the same through every row (to 3e-4; measured 1.7e-4) and
+    the profile downstream is plane Poiseuille for that flux to 0.5 %
+    (measured 0.2 %).  The flux itself falls short of W u_in by a corner loss
+    of about 0.42 lu of width (measured 2.65 % at W = 16 and 1.33 % at W = 32,
+    first order), where the imposed uniform velocity meets the walls."""
+    W, L, vin = 16, 96, 0.01
+    p = dict(wl.BASE_PARAMS, g=0.0, vin_y=vin)
+    one = np.ones((L, W))
+    o = oracle.Oracle(W, L, p)
+    o.set_bc(WALL, WALL, INLET_NEE, OUTLET)
+    o.init_fields(one, -one, one, 0 * one, 0 * one, 0 * one)
+    o.step(6000)
+    f = o.fields(("vx", "vy"))
+    Q = f["vy"].sum(axis=1)
+    Qm = Q[L // 2]
+    assert (Q.max() - Q.min()) / Qm < 3e-4
+    xi = (np.arange(W) + 0.5) / W
+    assert np.abs(f["vy"][L - 20] - 6 * Qm / W * xi * (1 - xi)).max() < 5e-3 * 1.5 * Qm / W
+    assert 0.96 < Qm / (W * vin) < 0.99
+    assert np.abs(f["vx"][L - 20]).max() < 1e-3 * vin

@@ -38,6 +38,8 @@ STRETCH_3F = ("          if (refl) src = idx3f(st, x, y, z);\n"
 FM_3F = ("const double Fm = (rl - rg) * (divD * vo[a] + Dm[0] * dv[a][0] + Dm[1] * dv[a][1]"
          " + Dm[2] * dv[a][2]);")
 
+NEE_2D = "st->fS[i][idx] = st->f[q][src] + st->par[P_RHO_L] * sb - rho_f * sf;"
+
 CASES = {
     # Appendix B time stretch t + a_s^2 dt (Eq. eq-AnACE: tau0 a_s^2 d psi/dt)
     "2d: no time stretch": ("pf_oracle.c", [(STRETCH_2D, STRETCH_2D.replace(
@@ -59,6 +61,9 @@ CASES = {
         "= (rl - rg) *", "= -(rl - rg) *"))], "mass_flux", "2d"),
     "3d two-phase: no mass-flux correction": ("pf_oracle3d.c", [(FM_3F, FM_3F.replace(
         "(rl - rg) *", "0.0 *"))], "mass_flux", "3f"),
+    # Section 3: Dirichlet velocity by non-equilibrium extrapolation
+    "2d: extrapolation inlet without the equilibrium difference": ("pf_oracle.c", [(
+        NEE_2D, "st->fS[i][idx] = st->f[q][src];")], "couette", "2d"),
     # mistakes in how the step is composed, caught by the per-node twin
     "2d: stretch factor taken at the destination": ("pf_oracle.c", [(STRETCH_2D, STRETCH_2D.replace(
         "st->rr[src]", "st->rr[idx]"))], "twin", "2d"),
@@ -87,6 +92,8 @@ def test_planted_mistake_fails_its_pin(case, mutant_dir):
     if pin == "stretch":
         errs, _ = pin_cases.stretch_errors(kind, lib)
         assert not pin_cases.stretch_pin_holds(errs), errs
+    elif pin == "couette":
+        assert not pin_cases.nee_couette_holds(lib), case
     elif pin == "twin":
         err = twin_error(lib)
         assert not err <= TWIN_TOL, err
