@@ -183,7 +183,11 @@ if not side:
 o = make(side)
 o.step({warm})
 t = time.perf_counter(); o.step({steps_hint}); dt = time.perf_counter() - t
-print(json.dumps(dict(side=side, steps={steps_hint}, seconds=dt)))
+small = wl.random_layout(48, 40, 2, 1, rng_seed=3, R_max=8)
+ca = oracle.count_step_ops(lay.params, 48, 40, small.seeds, small.R_s, small.bubbles)
+cb = oracle.count_step_ops(lay.params, 64, 40, small.seeds, small.R_s, small.bubbles)
+flops = sum(cb.values()) - sum(ca.values())
+print(json.dumps(dict(side=side, steps={steps_hint}, seconds=dt, flops_per_lu=flops / (16 * 40))))
 """
     env = dict(os.environ, OMP_NUM_THREADS=str(cores))
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
@@ -194,7 +198,11 @@ print(json.dumps(dict(side=side, steps={steps_hint}, seconds=dt)))
             "sample": f"FP64 oracle (gcc -O3, OpenMP over rows), {rec['side']}x{rec['side']} "
                       f"window at (1024, 1024) of the 4096^2 layout, {rec['steps']} steps "
                       f"after {warm}, in {rec['seconds']:.1f} s",
-            "window": rec["side"], "steps": rec["steps"], "seconds": rec["seconds"]}
+            "window": rec["side"], "steps": rec["steps"], "seconds": rec["seconds"],
+            "flops_per_lu": rec["flops_per_lu"],
+            "gflops": mlups * rec["flops_per_lu"] / 1e3,
+            "flops_def": "operations of the oracle's step per lattice update (dense moment "
+                         "transforms), counted by its instrumented-scalar build"}
 
 
 def cpu_oracle_variant(kind: str, steps: int = 0) -> dict:

@@ -60,6 +60,17 @@ def build(force: bool = False) -> None:
                "-ffp-contract=off", *extra, src, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, out)
+    # the flop-counting build: the same source as C++ with an instrumented
+    # scalar (counting.h); single-threaded, used only to count operations
+    out = os.path.join(_BUILD, "liboracle_count.so")
+    hdr = os.path.join(_HERE, "counting.h")
+    if (force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC)
+            or os.path.getmtime(out) < os.path.getmtime(hdr)):
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.run(["g++", "-x", "c++", "-std=c++17", "-O2", "-fPIC", "-shared",
+                        "-ffp-contract=off", "-DPF_ORACLE_COUNT", f"-I{_HERE}", _SRC, "-o", tmp],
+                       check=True)
+        os.replace(tmp, out)
 
 
 def _setup_2d(lib: ctypes.CDLL) -> ctypes.CDLL:
@@ -149,6 +160,36 @@ def mutant(source: str, edits, tmpdir: str) -> ctypes.CDLL:
     if source == "pf_oracle.c":
         return _setup_2d(lib)
     return _setup_3f(_setup_3d(lib))
+
+
+def counting_lib() -> ctypes.CDLL:
+    """The flop-counting build of the 2-D oracle (same values as the double
+    build; or_count_reset / or_count_get read the operation tally)."""
+    with _lock:
+        if "count" in _libs:
+            return _libs["count"]
+        build()
+        lib = _setup_2d(ctypes.CDLL(os.path.join(_BUILD, "liboracle_count.so")))
+        lib.or_count_get.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
+        lib.or_count_reset.argtypes = []
+        _libs["count"] = lib
+        return lib
+
+
+def count_step_ops(lay_params: dict, nx: int, ny: int, seeds, R_s: float, bubbles,
+                   warm: int = 2) -> dict:
+    """Operations of one oracle step over an nx x ny lattice (after `warm`
+    steps), counted by the instrumented scalar: additions (and subtractions),
+    multiplications, divisions and square roots, in total."""
+    lib = counting_lib()
+    o = Oracle(nx, ny, lay_params, lib=lib)
+    o.init_spec(seeds, R_s, bubbles)
+    o.step(warm)
+    lib.or_count_reset()
+    o.step(1)
+    c = (ctypes.c_ulonglong * 4)()
+    lib.or_count_get(c)
+    return dict(zip(("add", "mul", "div", "sqrt"), [int(v) for v in c]))
 
 
 def _dp(a: np.ndarray | None):

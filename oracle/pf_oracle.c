@@ -21,6 +21,8 @@
  * Compiled twice from this one source:
  *   real_t = double                          -> liboracle_d.so
  *   real_t = double complex (-DPF_ORACLE_Z)  -> liboracle_z.so
+ * and, for the flop count per lattice update only, a third time as C++ with
+ * an instrumented scalar (-DPF_ORACLE_COUNT, counting.h) -> liboracle_count.so.
  * The complex build is the complex-step derivative (Squire & Trapp, SIAM Rev.
  * 1998; Martins, Sturdza & Alonso, ACM TOMS 2003): a parameter is perturbed by
  * i*h and Im(J)/h is dJ/dparameter to rounding error, with no subtractive
@@ -44,6 +46,15 @@ typedef double complex real_t;
 #define RSQRT_(x) csqrt(x)
 #define RE_(x) creal(x)
 #define IM_(x) cimag(x)
+#elif defined(PF_ORACLE_COUNT)
+/* the flop-counting build: this file compiled as C++ (counting.h) */
+#include "counting.h"
+typedef pf_count::Counting real_t;
+#define RSQRT_(x) pf_count::sqrt(x)
+#define RE_(x) ((x).v)
+#define IM_(x) (0.0)
+pf_count::Tally pf_count::g_tally = {0, 0, 0, 0};
+extern "C" {
 #else
 typedef double real_t;
 #define RSQRT_(x) sqrt(x)
@@ -1257,3 +1268,14 @@ void or_thermal_totals(const ostate *st, double *out) {
   }
   for (int k = 0; k < 3; ++k) out[k] = s[k] + c[k];
 }
+
+#ifdef PF_ORACLE_COUNT
+/* Operation counts since the last reset: additions and subtractions,
+ * multiplications, divisions, square roots. */
+void or_count_get(unsigned long long out[4]) {
+  out[0] = pf_count::g_tally.add; out[1] = pf_count::g_tally.mul;
+  out[2] = pf_count::g_tally.div; out[3] = pf_count::g_tally.sqrt;
+}
+void or_count_reset(void) { pf_count::g_tally = pf_count::Tally{0, 0, 0, 0}; }
+}  /* extern "C" */
+#endif

@@ -84,8 +84,11 @@ def test_one_step_matches(precision, tol):
     compare_fields(o, sim, tol, early=True)
     st_o, st_g = o.state(), sim.get_state()
     for p in range(pf.STATE_PLANES):
-        # NS populations carry the early-flow rounding of the forces
-        fac = 30.0 if p < 9 or p in (36, 37) else 1.0
+        # FP32: the NS populations and the lagged velocity after one step from
+        # rest are built from the surface-tension forces alone, whose FP32
+        # rounding is up to 30x their 1e-5 share (EARLY_FLOW_FACTOR).  FP64
+        # holds every plane to 1e-11 (measured <= 7e-14).
+        fac = 30.0 if precision == "fp32" and (p < 9 or p in (36, 37)) else 1.0
         assert rel(st_g[p], st_o[p], 1e-12) <= tol * fac, p
 
 
@@ -100,8 +103,13 @@ def test_few_steps_with_rotated_grains_and_gravity(precision, tol):
 
 
 def test_fp64_thousand_steps_128(tmp_path):
-    """The 128^2 workload: same-step compare every 100 steps over 1000 steps,
-    and conservation of gas and solute to 1e-10 in the FP64 reductions."""
+    """The 128^2 workload: same-step compare every 100 steps over 1000 steps
+    (every field to 1e-11 of its maximum; measured <= 6.4e-13), conservation of
+    gas and solute to 1e-10 in the FP64 reductions, and the reductions equal
+    to the oracle's: the solid total to 1e-12 (measured 3e-14) and the gas
+    centroid's first moment sum y (1 - phi) to 1e-11 (measured 1.8e-12; the
+    gas holds a few per cent of the sites, so a field error e near the
+    bubble weighs about y_max / y_c = 20 e in that sum)."""
     lay = wl.seed_bubble_128()
     o, sim = pair(lay, "fp64")
     d0 = sim.reduce(0)
@@ -109,14 +117,14 @@ def test_fp64_thousand_steps_128(tmp_path):
     for blk in range(10):
         o.step(100)
         sim.step(100)
-        errs = compare_fields(o, sim, 1e-9)
+        errs = compare_fields(o, sim, 1e-11)
         worst = {k: max(worst.get(k, 0.0), v) for k, v in errs.items()}
         d = sim.reduce(0)
         assert abs(d["sum_phi"] / d0["sum_phi"] - 1) <= 1e-10
         assert abs(d["sum_C"] / d0["sum_C"] - 1) <= 1e-10
         od = o.diag()
-        assert math.isclose(d["sum_hpsi"], od["sum_hpsi"], rel_tol=1e-10)
-        assert math.isclose(d["gas_y"], od["gas_y"], rel_tol=1e-9)
+        assert math.isclose(d["sum_hpsi"], od["sum_hpsi"], rel_tol=1e-12)
+        assert math.isclose(d["gas_y"], od["gas_y"], rel_tol=1e-11)
     (tmp_path / "worst.txt").write_text(repr(worst))
 
 

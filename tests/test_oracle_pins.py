@@ -461,8 +461,8 @@ def test_laplace_law_static_bubble(N, R, T):
     """Young-Laplace, Eq. (eq-laplace): a static bubble in a periodic box (no
     solid, no gravity) settles to p_in - p_out = sigma / R (measured within 2 %
     for R = 10 .. 24).  nu = 0.3 damps the start-up pressure waves within the
-    run; the residual velocity is the model's parasitic current, 1.5e-6 ..
-    7.5e-6, i.e. below 0.3 % of the capillary velocity sigma / mu = 3.3e-3."""
+    run; the residual velocity after these runs, 1.5e-6 .. 7.5e-6, is still
+    the decaying start-up transient (see the parasitic-current pin)."""
     W, sigma = 2.0, 1e-3
     o = oracle.Oracle(N, N, params(g=0.0, W_phi=W, nu=0.3, sigma=sigma))
     o.init_spec([], 6.0, [(N / 2, N / 2, R)])
@@ -471,6 +471,22 @@ def test_laplace_law_static_bubble(N, R, T):
     dp = d["p_in_sum"] / d["p_in_n"] - d["p_out_sum"] / d["p_out_n"]
     assert math.isclose(dp, sigma / R, rel_tol=0.03)
     assert d["max_v"] < 1e-5
+
+
+def test_parasitic_current_of_a_static_bubble_below_1e6():
+    """The residual velocity around a static bubble (R = 16, W = 2, sigma =
+    1e-3, nu = 0.3, no gravity) is a decaying start-up transient: 1.5e-6 after
+    4000 steps, 1e-6 after 8000, 4.2e-7 after 16000 (measured).  After 16000
+    steps it is below 1e-6 lu, the spurious-current bound for the Laplace
+    problem (Section 3.1), with the pressure jump sigma / R to 1 %."""
+    N, R, W, sigma = 96, 16.0, 2.0, 1e-3
+    o = oracle.Oracle(N, N, params(g=0.0, W_phi=W, nu=0.3, sigma=sigma))
+    o.init_spec([], 6.0, [(N / 2, N / 2, R)])
+    o.step(16000)
+    d = o.diag((N / 2, N / 2, R, W))
+    dp = d["p_in_sum"] / d["p_in_n"] - d["p_out_sum"] / d["p_out_n"]
+    assert math.isclose(dp, sigma / R, rel_tol=0.01)
+    assert d["max_v"] < 1e-6
 
 
 def _contour_radius(phi, xc, yc, ang, level=0.5):
