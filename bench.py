@@ -492,7 +492,9 @@ def run_ensemble(args) -> None:
     """96 independent domains of uneven size (32 each of 256^2, 512x384,
     1024x512; 1-4 seeds, 1-6 bubbles, eps_s ~ U[0.02, 0.07]) in one handle:
     one launch per domain per step vs one batched launch per step vs the
-    autotuned batched launch replayed as CUDA graphs (the headline).  Under
+    autotuned batched launch replayed as CUDA graphs vs (the headline) the
+    autotuned tiles with 64 steps in one persistent cooperative launch,
+    replayed from a CUDA graph.  Under
     torchrun the domains are split across ranks (shard.shard_domains) with no
     collective on the data path; the job time is the slowest rank's."""
     import torch
@@ -543,11 +545,28 @@ def run_ensemble(args) -> None:
     cfg = sim.autotune(10)
     sim.set_launch(0, cfg[3], 64)
     sim.step(args.warmup)
+    ms, _ = timed()
+    res["batched_autotuned_graph"] = shard.job_rate(units, args.steps, ms / 1e3) / 1e6
+    ms_mode["batched_autotuned_graph"] = ms / args.steps
+    # the headline: every 64 steps in one persistent cooperative launch,
+    # replayed from a CUDA graph, with the y-march chunk timed in that mode
+    best = None
+    for chunk in (16, 24, 32, 48, 64):
+        sim.set_step_config(1, chunk, 0)
+        sim.set_launch(0, 2, 0)
+        sim.step(2)
+        t_ms, _ = timed_region(torch, stream, sim.step, 20, local, True)
+        if best is None or t_ms < best[0]:
+            best = (t_ms, chunk)
+    cfg_one = [1, best[1], 0, 2]
+    sim.set_step_config(1, best[1], 0)
+    sim.set_launch(0, 2, 64)
+    sim.step(args.warmup)
     launches0 = sim.launches
     ms, clk = timed(clk=True)
     launches = sim.launches - launches0
-    res["batched_autotuned_graph"] = shard.job_rate(units, args.steps, ms / 1e3) / 1e6
-    ms_mode["batched_autotuned_graph"] = ms / args.steps
+    res["one_persistent_launch_graph"] = shard.job_rate(units, args.steps, ms / 1e3) / 1e6
+    ms_mode["one_persistent_launch_graph"] = ms / args.steps
     e2e = None
     if not args.no_e2e:
         e2e = e2e_2d(torch, sim, [(d, l.nx, l.ny) for d, l in enumerate(lays)], args.steps)
@@ -559,20 +578,23 @@ def run_ensemble(args) -> None:
         cpu = None if (args.no_cpu_baseline or world > 1) else cpu_oracle_variant("ensemble")
         print(json.dumps({
             "metric": "ensemble aggregate MLUPS (96 uneven domains)",
-            "value": res["batched_autotuned_graph"],
+            "value": res["one_persistent_launch_graph"],
             "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "96 domains: 32 x 256^2, 32 x 512x384, 32 x 1024x512, seed 5",
                        "sites": sum(sizes), "autotuned": list(cfg), "graph_steps": 64,
+                       "launch": "64 steps per persistent cooperative launch, graph replay",
+                       "autotuned_one_launch": cfg_one,
                        "parallelism": f"domains sharded over {world} rank(s)",
                        "l2": f"{313 * my_sites / 1e9:.1f} GB read+written per step > L2 "
                              "(no flush)"},
             "roofline": roofline(BYTES_PER_LU["fp32"], my_sites, ms / args.steps,
                                  "k_step_ymarch (batched over every domain's tiles)"),
             "modes": res, "ms_per_step_modes": ms_mode,
-            "speedup_vs_sequential": res["batched_autotuned_graph"] / res["sequential_per_domain"],
-            "speedup_graph_vs_one_launch": res["batched_autotuned_graph"] /
+            "speedup_vs_sequential": res["one_persistent_launch_graph"] /
+            res["sequential_per_domain"],
+            "speedup_vs_one_launch_per_step": res["one_persistent_launch_graph"] /
             res["batched_one_launch"],
             "gpu_launches": launches, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}))
     sim.close()

@@ -215,11 +215,17 @@ pf_status pf_set_step_config(pf_handle *h, int variant, int a, int b);
  *  per_domain = 0: one launch whose tile list spans every domain (default);
  *               1: one launch per domain, one after the other.
  *  persistent = 1: the grid is the device's resident CTAs of the step kernel,
- *               each looping over tiles; 0: one CTA per tile (default).
+ *               each looping over tiles; 0: one CTA per tile (default);
+ *               2: as 1, and every step of a pf_step call in one cooperative
+ *               launch, the resident CTAs meeting at a grid-wide barrier
+ *               between steps (y-march traversal over periodic domains, with
+ *               per_domain = 0; elsewhere it runs as 1).
  *  graph_steps > 0 (even): pf_step replays CUDA graphs of graph_steps steps
  *               (captured on an internal stream on first use, replayed on the
- *               handle's stream); 0 launches step by step (default).
- * Synchronises the stream.  Errors: BAD_ARG. */
+ *               handle's stream; with persistent = 2 a graph holds one launch
+ *               of graph_steps steps); 0 launches step by step (default).
+ * Synchronises the stream.  Errors: BAD_ARG (also persistent = 2 without
+ * cooperative launch on the device). */
 pf_status pf_set_launch(pf_handle *h, int per_domain, int persistent, int graph_steps);
 
 /* Autotuner: times every step traversal and tile height (and persistent or

@@ -64,7 +64,9 @@ struct pf_handle {
   int ntiles = 0;
   int grid = 0;
   int launch_mode = 0;      // 0: one launch over all domains; 1: one launch per domain
-  int persistent = 0;       // 1: grid = resident CTAs, each loops over tiles
+  int persistent = 0;       // 1: grid = resident CTAs, each loops over tiles;
+                            // 2: as 1, and every step of a call in one cooperative launch
+  int coop_graph_failed = 0;  // capturing the cooperative launch failed: replay without graphs
   int sms = 0;
   // CUDA-graph replay of the stepping: one executable graph per buffer parity
   int graph_steps = 0;
@@ -82,6 +84,7 @@ struct pf_handle {
   double* partial = nullptr;
   double* d_diag = nullptr;
   unsigned int* d_err = nullptr;  // device error bits written by the step kernels
+  int* d_tile_ctr = nullptr;      // two tile counters of the one-launch mode
   int drop_copies = 0;            // testing only (pf_test_drop_staged_copies)
   double* staging = nullptr;    // FP64 device staging (largest domain x 39 planes)
   size_t staging_elems = 0;
@@ -294,6 +297,8 @@ static void release(pf_handle* h) {
   dev_free(h, h->d_diag);
   dev_free(h, h->d_err);
   h->d_err = nullptr;
+  dev_free(h, h->d_tile_ctr);
+  h->d_tile_ctr = nullptr;
   dev_free(h, h->staging);
   dev_free(h, h->adj_ws);
   h->adj_ws = nullptr;
@@ -798,6 +803,31 @@ static int launches_per_step(const pf_handle* h) {
   return n;
 }
 
+// The one-launch mode applies to the y-march over periodic domains with one
+// launch over the whole tile list; elsewhere mode 2 runs as mode 1.
+static bool steps_in_one_launch(const pf_handle* h) {
+  return h->persistent == 2 && h->variant == STEP_YMARCH && !h->any_bc && h->launch_mode == 0;
+}
+
+// n steps (n >= 1) in one cooperative launch of the resident grid.
+template <typename S, typename R>
+static pf_status steps_one_launch(pf_handle* h, int n, bool write_fields, cudaStream_t stream) {
+  StepArgs<S, R> a = make_step_args<S, R>(h, h->pop[h->cur], h->aux[h->cur], h->pop[h->cur ^ 1],
+                                          h->aux[h->cur ^ 1], write_fields);
+  a.tile_base = 0;
+  a.ntiles = h->ntiles;
+  a.bc = 0;
+  const int cap = std::max(1, h->sms) * ymarch_steps_blocks_per_sm<S, R>(h->plane_stride,
+                                                                        h->thermal != 0);
+  if (!h->d_tile_ctr) return fail(h, PF_ERR_STATE, "tile counters missing (pf_set_launch)");
+  PF_CUDA(h, launch_ymarch_steps<S, R>(a, n, h->d_tile_ctr, std::max(1, std::min(cap, h->ntiles)),
+                                       stream));
+  h->launches++;
+  h->cur ^= (n & 1);
+  h->steps += n;
+  return PF_OK;
+}
+
 template <typename S, typename R>
 static pf_status step_t(pf_handle* h, bool write_fields, cudaStream_t stream = nullptr) {
   const StepArgs<S, R> a = make_step_args<S, R>(h, h->pop[h->cur], h->aux[h->cur],
@@ -821,12 +851,24 @@ static pf_status ensure_graph(pf_handle* h) {
   const long long steps0 = h->steps, launches0 = h->launches;
   PF_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   pf_status st = PF_OK;
-  for (int t = 0; t < h->graph_steps && st == PF_OK; ++t) st = step_t<S, R>(h, false, h->cap_stream);
+  const bool one = steps_in_one_launch(h);
+  if (one) st = steps_one_launch<S, R>(h, h->graph_steps, false, h->cap_stream);
+  else
+    for (int t = 0; t < h->graph_steps && st == PF_OK; ++t)
+      st = step_t<S, R>(h, false, h->cap_stream);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
   h->cur = par;
   h->steps = steps0;
   h->launches = launches0;
+  if (one && (st != PF_OK || e != cudaSuccess)) {
+    // the cooperative launch could not be captured: replay it directly
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    h->err.clear();
+    h->coop_graph_failed = 1;
+    return PF_OK;
+  }
   if (st != PF_OK) { if (g) cudaGraphDestroy(g); return st; }
   if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
   e = cudaGraphInstantiate(&h->gexec[par], g, 0);
@@ -838,6 +880,22 @@ static pf_status ensure_graph(pf_handle* h) {
 template <typename S, typename R>
 static pf_status step_n(pf_handle* h, int n_steps) {
   int done = 0;
+  if (steps_in_one_launch(h)) {
+    // graph_steps > 0: whole graph_steps-step launches replayed from graphs,
+    // then the rest (with the field output) in one more launch
+    if (h->graph_steps > 0 && !h->coop_graph_failed) {
+      while (n_steps - 1 - done >= h->graph_steps) {
+        pf_status st = ensure_graph<S, R>(h);
+        if (st != PF_OK) return st;
+        if (h->coop_graph_failed) break;
+        PF_CUDA(h, cudaGraphLaunch(h->gexec[h->cur], h->stream));
+        done += h->graph_steps;
+        h->steps += h->graph_steps;
+        h->launches += 1;
+      }
+    }
+    return n_steps - done > 0 ? steps_one_launch<S, R>(h, n_steps - done, true, h->stream) : PF_OK;
+  }
   if (h->graph_steps > 0) {
     const int per_step = launches_per_step(h);
     while (n_steps - 1 - done >= h->graph_steps) {
@@ -900,19 +958,37 @@ extern "C" pf_status pf_set_step_config(pf_handle* h, int variant, int a, int b)
   }
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
   h->variant = variant;
+  // captured graphs hold the old tile table's size and chunk: drop them
+  for (auto& g : h->gexec)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  h->coop_graph_failed = 0;
   return upload_tables(h);
 }
 
 extern "C" pf_status pf_set_launch(pf_handle* h, int per_domain, int persistent,
                                    int graph_steps) {
   if (!h) return PF_ERR_BAD_ARG;
-  if (per_domain < 0 || per_domain > 1 || persistent < 0 || persistent > 1 || graph_steps < 0 ||
+  if (per_domain < 0 || per_domain > 1 || persistent < 0 || persistent > 2 || graph_steps < 0 ||
       (graph_steps % 2) != 0 || graph_steps > 4096)
-    return fail(h, PF_ERR_BAD_ARG, "per_domain, persistent in {0,1}; graph_steps even in [0, 4096]");
+    return fail(h, PF_ERR_BAD_ARG,
+                "per_domain in {0,1}, persistent in {0,1,2}; graph_steps even in [0, 4096]");
+  if (persistent == 2 && per_domain)
+    return fail(h, PF_ERR_BAD_ARG, "the one-launch mode takes one launch over every domain");
+  if (persistent == 2) {
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
+    if (!coop) return fail(h, PF_ERR_BAD_ARG, "the device has no cooperative launch");
+    // allocated here, never under a graph capture
+    if (!h->d_tile_ctr) {
+      h->d_tile_ctr = static_cast<int*>(dev_alloc(h, 2 * sizeof(int)));
+      if (!h->d_tile_ctr) return fail(h, PF_ERR_OOM, "tile counter allocation failed");
+    }
+  }
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
   h->launch_mode = per_domain;
   h->persistent = persistent;
   h->graph_steps = graph_steps;
+  h->coop_graph_failed = 0;
   for (auto& g : h->gexec)
     if (g) { cudaGraphExecDestroy(g); g = nullptr; }
   return PF_OK;
@@ -982,6 +1058,9 @@ static pf_status autotune_t(pf_handle* h, int trial_steps, int out[4]) {
   h->variant = bc.variant;
   if (bc.variant != STEP_TILE) h->chunk = bc.a; else { h->tx = bc.a; h->ty = bc.b; }
   h->persistent = bc.persistent;
+  for (auto& g : h->gexec)   // graphs captured before hold the old tiles
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  h->coop_graph_failed = 0;
   st = upload_tables(h);
   if (st != PF_OK) return st;
   if (out) { out[0] = bc.variant; out[1] = bc.a; out[2] = bc.b; out[3] = bc.persistent; }

@@ -106,6 +106,14 @@ template <typename S, typename R>
 int staged_halo_columns();
 template <typename S, typename R>
 int staged_blocks_per_sm();
+// Every step of a call in one cooperative launch (y-march, periodic domains),
+// and the resident CTAs per SM of that kernel.
+// ctr: two device ints (tile counters), owned by the caller.
+template <typename S, typename R>
+cudaError_t launch_ymarch_steps(const StepArgs<S, R>& a, int nsteps, int* ctr, int grid,
+                                cudaStream_t st);
+template <typename S, typename R>
+int ymarch_steps_blocks_per_sm(long long plane_stride, bool thermal);
 // Resident CTAs per SM of the step kernel (for persistent grids).
 template <typename S, typename R>
 int step_blocks_per_sm(int variant, int tx, int ty, long long plane_stride, bool thermal,

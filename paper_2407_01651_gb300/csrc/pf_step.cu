@@ -9,9 +9,13 @@
 //   k_step_ymarch  column strips marched along y
 // (and k_step_staged, pf_step_staged.cu: the y-march with its input rows
 // staged in shared memory by bulk copies)
+#include <cooperative_groups.h>
+
 #include "pf_site.cuh"
 
 namespace pf {
+
+namespace cg = cooperative_groups;
 
 // Variant A: 2-D tiles.  The CTA builds phi, psi and the lagged velocity on
 // its TX x TY tile plus a one-site halo in shared memory, then each thread
@@ -73,16 +77,28 @@ __global__ void __launch_bounds__(256) k_step_tile(StepArgs<S, R> a) {
 // from memory once (plus 2 halo columns per YM_W).  TH (thermal mode) adds the
 // supersaturation U of row j+1 to the ring (for grad F) and the temperature
 // lattice to the site update; it runs 3 CTAs per SM.
-template <typename S, typename R, bool BIG, bool TH = false>
-__global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? (TH ? 3 : 4) : 2)
-    k_step_ymarch(StepArgs<S, R> a) {
-  constexpr int RW = YM_W + 2;
+// The tile loop of the y-march.  Tiles are taken by CTA index and stride
+// (DYN = false), or claimed one at a time from the counter *ctr (DYN = true),
+// which balances the CTAs of a persistent grid over tiles of uneven cost.
+template <typename S, typename R, bool BIG, bool TH, bool DYN = false>
+__device__ __forceinline__ void ymarch_tiles(const StepArgs<S, R>& a,
+                                             R (&ring)[TH ? 5 : 4][4][YM_W + 2],
+                                             int* ctr = nullptr) {
   constexpr int NF = TH ? 5 : 4;
-  __shared__ R ring[NF][4][RW];  // [phi, psi, vx_o, vy_o (, U)][slot][column]
   const int t = threadIdx.x;
   const unsigned ps = (unsigned)a.plane_stride;
+  __shared__ int s_tile;
+  auto next_tile = [&](int cur) {
+    if constexpr (DYN) {
+      if (t == 0) s_tile = a.tile_base + atomicAdd(ctr, 1);
+      __syncthreads();
+      return s_tile;
+    } else {
+      return cur < 0 ? a.tile_base + (int)blockIdx.x : cur + (int)gridDim.x;
+    }
+  };
 
-  for (int tile = a.tile_base + blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+  for (int tile = next_tile(-1); tile < a.ntiles; tile = next_tile(tile)) {
     const DomDesc d = a.doms[a.tile_dom[tile]];
     const int lt = tile - d.tile0;
     const int nx = d.nx, ny = d.ny;
@@ -166,6 +182,42 @@ __global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? (TH ? 3 : 4) : 2)
   }
 }
 
+template <typename S, typename R, bool BIG, bool TH = false>
+__global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? (TH ? 3 : 4) : 2)
+    k_step_ymarch(StepArgs<S, R> a) {
+  __shared__ R ring[TH ? 5 : 4][4][YM_W + 2];  // [phi, psi, vx_o, vy_o (, U)][slot][column]
+  ymarch_tiles<S, R, BIG, TH>(a, ring);
+}
+
+// All steps of a call in one launch: the device's resident CTAs march the
+// tiles of every domain, meet at a grid-wide barrier, swap the two state
+// buffers and go on with the next step.  Launched cooperatively (every CTA
+// resident), so the barrier always completes; the fields are written on the
+// last step only.
+template <typename S, typename R, bool BIG, bool TH = false>
+__global__ void __launch_bounds__(YM_THREADS, sizeof(R) == 4 ? (TH ? 3 : 4) : 2)
+    k_step_ymarch_steps(StepArgs<S, R> a, int nsteps, int* ctr) {
+  __shared__ R ring[TH ? 5 : 4][4][YM_W + 2];
+  cg::grid_group grid = cg::this_grid();
+  R* fields = a.fields;
+  for (int step = 0; step < nsteps; ++step) {
+    // tile counters: ctr[step & 1] counts this step's tiles (zeroed by the
+    // host for step 0, by this CTA one step ahead otherwise); no CTA touches
+    // ctr[(step + 1) & 1] until every CTA has passed the barrier below
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctr[(step + 1) & 1] = 0;
+    StepArgs<S, R> b = a;
+    if (step & 1) {
+      b.in = a.out;
+      b.ain = a.aout;
+      b.out = const_cast<S*>(a.in);
+      b.aout = const_cast<R*>(a.ain);
+    }
+    b.fields = step + 1 == nsteps ? fields : nullptr;
+    ymarch_tiles<S, R, BIG, TH, true>(b, ring, ctr + (step & 1));
+    if (step + 1 < nsteps) grid.sync();
+  }
+}
+
 // Buffers of more than 2^32 elements (plane stride x 33 population planes)
 // take the 64-bit plane-base addressing of the pull helpers.
 inline bool big_handle(long long plane_stride, bool thermal) {
@@ -201,6 +253,53 @@ cudaError_t launch_step(const StepArgs<S, R>& a, int variant, int tx, int ty, in
   return cudaGetLastError();
 }
 
+// All n steps in one cooperative launch of the resident grid (y-march,
+// periodic domains).  grid <= SMs x ymarch_steps_blocks_per_sm.
+template <typename S, typename R, bool BIG>
+static cudaError_t launch_steps_t(const StepArgs<S, R>& a, int nsteps, int* ctr, int grid,
+                                  cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  void* args[] = {const_cast<StepArgs<S, R>*>(&a), &nsteps, &ctr};
+  if constexpr (sizeof(S) == sizeof(R)) {
+    if (a.thermal)
+      return cudaLaunchCooperativeKernel((const void*)k_step_ymarch_steps<S, R, BIG, true>,
+                                         grid, YM_THREADS, args, 0, st);
+  }
+  return cudaLaunchCooperativeKernel((const void*)k_step_ymarch_steps<S, R, BIG, false>, grid,
+                                     YM_THREADS, args, 0, st);
+}
+
+template <typename S, typename R>
+cudaError_t launch_ymarch_steps(const StepArgs<S, R>& a, int nsteps, int* ctr, int grid,
+                                cudaStream_t st) {
+  if (a.bc) return cudaErrorInvalidValue;
+  return big_handle(a.plane_stride, a.thermal != 0)
+             ? launch_steps_t<S, R, true>(a, nsteps, ctr, grid, st)
+             : launch_steps_t<S, R, false>(a, nsteps, ctr, grid, st);
+}
+
+template <typename S, typename R, bool BIG>
+static int steps_blocks_t(bool thermal) {
+  int n = 0;
+  if constexpr (sizeof(S) == sizeof(R)) {
+    if (thermal) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_ymarch_steps<S, R, BIG, true>,
+                                                    YM_THREADS, 0);
+      return n > 0 ? n : 1;
+    }
+  }
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_ymarch_steps<S, R, BIG, false>,
+                                                YM_THREADS, 0);
+  return n > 0 ? n : 1;
+}
+
+template <typename S, typename R>
+int ymarch_steps_blocks_per_sm(long long plane_stride, bool thermal) {
+  return big_handle(plane_stride, thermal) ? steps_blocks_t<S, R, true>(thermal)
+                                           : steps_blocks_t<S, R, false>(thermal);
+}
+
 template <typename S, typename R, bool BIG>
 static int traversal_blocks_per_sm(int variant, int tx, int ty, bool thermal) {
   int n = 0;
@@ -226,6 +325,15 @@ int step_blocks_per_sm(int variant, int tx, int ty, long long plane_stride, bool
              ? traversal_blocks_per_sm<S, R, true>(variant, tx, ty, thermal)
              : traversal_blocks_per_sm<S, R, false>(variant, tx, ty, thermal);
 }
+
+#define PF_STEPS_INST(S, R)                                                                   \
+  template cudaError_t launch_ymarch_steps<S, R>(const StepArgs<S, R>&, int, int*, int,       \
+                                                 cudaStream_t);                                \
+  template int ymarch_steps_blocks_per_sm<S, R>(long long, bool);
+PF_STEPS_INST(double, double)
+PF_STEPS_INST(float, float)
+PF_STEPS_INST(__half, float)
+PF_STEPS_INST(__nv_bfloat16, float)
 
 template int step_blocks_per_sm<double, double>(int, int, int, long long, bool, bool);
 template int step_blocks_per_sm<float, float>(int, int, int, long long, bool, bool);

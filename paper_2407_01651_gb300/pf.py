@@ -337,8 +337,11 @@ class Simulation:
         in every domain)."""
         _check(lib().pf_set_step_config(self.h, int(variant), int(a), int(b)), self.h)
 
-    def set_launch(self, per_domain: bool = False, persistent: bool = False,
+    def set_launch(self, per_domain: bool = False, persistent: int = 0,
                    graph_steps: int = 0) -> None:
+        """per_domain: one launch per domain; persistent 1: resident grid
+        looping over the tiles, 2: and every step of a call in one cooperative
+        launch; graph_steps > 0 (even): replay CUDA graphs of that many steps."""
         _check(lib().pf_set_launch(self.h, int(per_domain), int(persistent), int(graph_steps)),
                self.h)
 

@@ -41,7 +41,8 @@ def test_launch_modes_and_graphs_are_bitwise_identical():
     ref = make(lays)
     ref.step(21)
     fr = fields_all(ref, len(lays))
-    for per_domain, persistent, graph in ((1, 0, 0), (0, 1, 0), (0, 0, 8), (1, 1, 4), (0, 1, 2)):
+    for per_domain, persistent, graph in ((1, 0, 0), (0, 1, 0), (0, 0, 8), (1, 1, 4), (0, 1, 2),
+                                          (0, 2, 0), (0, 2, 4)):
         sim = make(lays)
         sim.set_launch(per_domain, persistent, graph)
         sim.step(10)
@@ -51,6 +52,39 @@ def test_launch_modes_and_graphs_are_bitwise_identical():
         for d in range(len(lays)):
             for k in NAMES:
                 assert np.array_equal(fs[d][k], fr[d][k]), (per_domain, persistent, graph, d, k)
+
+
+def test_changing_the_tiles_drops_captured_graphs():
+    """A graph captured before pf_set_step_config or pf_autotune changed the
+    tiles is dropped and captured again: the steps after the change give the
+    same bits as a handle that never used graphs (every y-march chunk gives
+    the same per-site arithmetic)."""
+    lays = ensemble(3)
+    ref = make(lays)
+    ref.step(18)
+    fr = fields_all(ref, len(lays))
+    ref.step(9)
+    fr27 = fields_all(ref, len(lays))
+    for persistent in (0, 2):
+        sim = make(lays)
+        sim.set_launch(0, persistent, 4)
+        sim.step(9)
+        sim.set_step_config(1, 16)
+        sim.step(9)
+        fs = fields_all(sim, len(lays))
+        for d in range(len(lays)):
+            for k in NAMES:
+                assert np.array_equal(fs[d][k], fr[d][k]), (persistent, d, k)
+        # the autotuner may pick another traversal (same arithmetic, its own
+        # rounding order): agreement to FP32 rounding
+        sim.autotune(3)
+        sim.set_launch(0, persistent, 4)
+        sim.step(9)
+        fs = fields_all(sim, len(lays))
+        for d in range(len(lays)):
+            for k in NAMES:
+                scale = max(np.abs(fr27[d][k]).max(), 1e-9)
+                assert np.abs(fs[d][k] - fr27[d][k]).max() <= 1e-5 * scale, (persistent, d, k)
 
 
 def test_graph_replay_counts_launches():
@@ -81,7 +115,7 @@ def test_autotune_restores_the_state_and_keeps_a_valid_config():
 
 def test_set_launch_rejects_bad_arguments():
     sim = make(ensemble(2))
-    for args in ((2, 0, 0), (0, 2, 0), (0, 0, 3), (0, 0, -2)):
+    for args in ((2, 0, 0), (0, 3, 0), (1, 2, 0), (0, 0, 3), (0, 0, -2)):
         with pytest.raises(pf.PFError) as e:
             sim.set_launch(*args)
         assert e.value.code == pf.PF_ERR_BAD_ARG
@@ -112,3 +146,35 @@ def test_staged_copy_timeout_is_reported_and_recoverable():
     fa, fb = sim.fields(), ref.fields()
     for k in NAMES:
         assert np.array_equal(fa[k], fb[k]), k
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_one_launch_per_call_is_bitwise_identical_and_counts_one_launch(precision):
+    """persistent = 2: every step of a pf_step call in one cooperative launch
+    of the resident grid (a grid-wide barrier between steps), also when a
+    graph replays such launches; the same bits as one launch per step, and
+    one kernel launch per call (per graph replay)."""
+    lays = ensemble()
+    ref = make(lays, precision)
+    ref.step(17)
+    fr = fields_all(ref, len(lays))
+    sim = make(lays, precision)
+    sim.set_launch(0, 2, 0)
+    l0 = sim.launches
+    sim.step(17)
+    assert sim.launches - l0 == 1 and sim.steps == 17
+    fs = fields_all(sim, len(lays))
+    for d in range(len(lays)):
+        for k in NAMES:
+            assert np.array_equal(fs[d][k], fr[d][k]), (d, k)
+    sim = make(lays, precision)
+    sim.set_launch(0, 2, 8)
+    l0 = sim.launches
+    sim.step(17)          # two replays of an 8-step launch, then one launch of 1 step
+    assert sim.launches - l0 == 3 and sim.steps == 17
+    fs = fields_all(sim, len(lays))
+    for d in range(len(lays)):
+        for k in NAMES:
+            assert np.array_equal(fs[d][k], fr[d][k]), (d, k)
+    with pytest.raises(pf.PFError):
+        sim.set_launch(1, 2, 0)          # one launch per domain excludes it
