@@ -19,6 +19,9 @@ constexpr int NIN = TX * TY;
 constexpr int NHALO = HX * HY - NIN;
 constexpr int THREADS = (NIN + NHALO + 31) / 32 * 32;
 constexpr int MIN_CTAS = 1;
+#ifndef PF3F_PREFETCH
+#define PF3F_PREFETCH 1   // planes ahead of the z-march warmed in L2 (0: none)
+#endif
 static_assert(HX == d3::HX, "the stencil helpers assume rows of d3::HX");
 using d3::cx7;
 using d3::cy7;
@@ -360,6 +363,17 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R, I> a) 
         Qo = pl(a.ain, AX_QO, a.ps)[site];
         phio = pl(a.ain, AX_PHIO, a.ps)[site];
         Co = pl(a.ain, AX_CO, a.ps)[site];
+        if constexpr (PF3F_PREFETCH > 0) {
+          // warm L2 with this column's planes PF3F_PREFETCH planes ahead (one
+          // instruction per plane and warp; no register holds the data)
+          const int z2 = z + PF3F_PREFETCH < a.nz ? z + PF3F_PREFETCH : z + PF3F_PREFETCH - a.nz;
+          const unsigned long long pf2 = site_of(a, x, y, z2);
+          constexpr int NP = TH ? NPOPF_TH : NPOPF, NA = TH ? NAUXF_TH : NAUXF;
+#pragma unroll
+          for (int q = 0; q < NP; ++q) d3::prefetch_l2(pl(a.in, q, a.ps) + pf2);
+#pragma unroll
+          for (int q = 0; q < NA; ++q) d3::prefetch_l2(pl(a.ain, q, a.ps) + pf2);
+        }
       }
       if (active) {
         int sz = 0;
