@@ -186,7 +186,8 @@ pf_status pf_init_fields(pf_handle *h, int dom, const pf_init_spec *spec);
 
 /* Initialise domain dom from macroscopic fields (host, FP64, n = nx*ny each):
  * fields6 = [phi, psi, C, vx, vy, p] planes, one contiguous block of 6 n
- * doubles (page-locked host memory gives the fastest copy); theta (per-site
+ * doubles (page-locked host memory is read by the kernel in place over the
+ * CPU-GPU link; other memory is copied to a device staging buffer first); theta (per-site
  * grain angle) may be NULL for 0.  Populations are set to their equilibria.
  * Non-finite values are detected on the device while the equilibria are
  * written: the call then returns BAD_ARG and the domain counts as not
@@ -240,7 +241,9 @@ pf_status pf_get_step_config(const pf_handle *h, int out[3]);
 
 /* Copy the fields of the last step of domain dom to host_out (FP64,
  * popcount(mask) planes of nx*ny, in bit order).  n is the capacity of
- * host_out in doubles.  Synchronises the stream. */
+ * host_out in doubles.  A page-locked host_out is written by the kernel in
+ * place over the CPU-GPU link; other memory goes through a device staging
+ * buffer.  Synchronises the stream. */
 pf_status pf_get_fields(pf_handle *h, int dom, uint32_t mask, double *host_out, size_t n);
 
 /* Raw state of domain dom (pf_state_planes(h) planes, FP64) to / from the

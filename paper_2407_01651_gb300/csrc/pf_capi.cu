@@ -135,6 +135,19 @@ static pf_status cuda_fail(pf_handle* h, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail((h), e_, #__VA_ARGS__); \
   } while (0)
 
+// Device address of host memory the GPU can reach directly: page-locked
+// (cudaHostAlloc or cudaHostRegister) memory, which the kernels then read or
+// write over the CPU-GPU link without a staging copy.  nullptr for ordinary
+// pageable memory (the caller stages through device memory).
+static const void* host_device_view(const void* host) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 static void* dev_alloc(pf_handle* h, size_t bytes) {
   if (bytes == 0) bytes = 256;
   void* p = nullptr;
@@ -677,13 +690,17 @@ extern "C" pf_status pf_set_fields(pf_handle* h, int dom, const double* fields6,
   if (st != PF_OK) return st;
   st = upload_grain_table(h, dom, angles);
   if (st != PF_OK) return st;
-  st = ensure_staging(h, 6 * nn + (theta ? (nn + 7) / 8 : 0));  // 6 x n doubles (+ n grain ids)
+  // page-locked fields are read by the kernel in place; others are staged
+  const double* direct = static_cast<const double*>(host_device_view(fields6));
+  st = ensure_staging(h, (direct ? 0 : 6 * nn) + (theta ? (nn + 7) / 8 : 0));
   if (st != PF_OK) return st;
-  double* buf = h->staging;
+  const double* buf = direct ? direct : h->staging;
   uint8_t* d_ids = nullptr;
-  PF_CUDA(h, cudaMemcpyAsync(buf, fields6, 6 * nn * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  if (!direct)
+    PF_CUDA(h, cudaMemcpyAsync(h->staging, fields6, 6 * nn * sizeof(double),
+                               cudaMemcpyHostToDevice, h->stream));
   if (theta) {
-    d_ids = reinterpret_cast<uint8_t*>(buf + 6 * nn);
+    d_ids = reinterpret_cast<uint8_t*>(h->staging + (direct ? 0 : 6 * nn));
     PF_CUDA(h, cudaMemcpyAsync(d_ids, ids.data(), nn, cudaMemcpyHostToDevice, h->stream));
   }
   st = dispatch(h, [&](auto s_t, auto r_t) {
@@ -1111,17 +1128,21 @@ extern "C" pf_status pf_get_fields(pf_handle* h, int dom, uint32_t mask, double*
   const size_t nn = (size_t)dd.nx * dd.ny;
   const size_t need = nn * __builtin_popcount(mask);
   if (n < need) return fail(h, PF_ERR_BAD_ARG, "output buffer too small");
-  pf_status st = ensure_staging(h, need);
+  // a page-locked output is written by the kernel in place; others are staged
+  double* direct = static_cast<double*>(const_cast<void*>(host_device_view(host_out)));
+  pf_status st = ensure_staging(h, direct ? 0 : need);
   if (st != PF_OK) return st;
+  double* dst = direct ? direct : h->staging;
   if (h->prec == PF_FP64)
     PF_CUDA(h, launch_fields_to_f64<double>(fields_ptr<double>(h), h->plane_stride, dd.off,
-                                            (long long)nn, mask, h->staging, h->stream));
+                                            (long long)nn, mask, dst, h->stream));
   else
     PF_CUDA(h, launch_fields_to_f64<float>(fields_ptr<float>(h), h->plane_stride, dd.off,
-                                           (long long)nn, mask, h->staging, h->stream));
+                                           (long long)nn, mask, dst, h->stream));
   h->launches++;
-  PF_CUDA(h, cudaMemcpyAsync(host_out, h->staging, need * sizeof(double), cudaMemcpyDeviceToHost,
-                             h->stream));
+  if (!direct)
+    PF_CUDA(h, cudaMemcpyAsync(host_out, h->staging, need * sizeof(double), cudaMemcpyDeviceToHost,
+                               h->stream));
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
   return check_device_error(h);
 }

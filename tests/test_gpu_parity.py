@@ -251,6 +251,38 @@ def test_set_fields_rejects_non_finite_values_on_the_device():
         sim.close()
 
 
+def test_page_locked_host_buffers_are_used_in_place():
+    """pf_set_fields reads a page-locked field block in place and
+    pf_get_fields writes a page-locked output in place (no staging copy);
+    the state and fields are bitwise those of the staged path."""
+    import torch
+    lay = small_layout()
+    sim = pf.Simulation([(lay.nx, lay.ny)], lay.params, "fp32")
+    sim.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
+    sim.step(4)
+    names = ("phi", "psi", "C", "vx", "vy", "p")
+    f = sim.fields(0, names)
+    pageable = np.ascontiguousarray(np.stack([f[k] for k in names]))
+    pinned = torch.empty(pageable.shape, dtype=torch.float64, pin_memory=True).numpy()
+    pinned[...] = pageable
+    out_p = torch.empty(8 * lay.nx * lay.ny, dtype=torch.float64, pin_memory=True).numpy()
+    states, outs = [], []
+    for src in (pageable, pinned):
+        sim.set_fields_stack(0, src)
+        states.append(sim.get_state(0))
+        sim.step(3)
+        outs.append(sim.fields(0, FIELDS[:8], out=out_p if src is pinned else None))
+    assert np.array_equal(states[0], states[1])
+    for k in FIELDS[:8]:
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+    bad = pinned.copy()
+    pinned[2, 3, 4] = np.nan                 # found on the device in the in-place read too
+    with pytest.raises(pf.PFError) as e:
+        sim.set_fields_stack(0, pinned)
+    assert e.value.code == pf.PF_ERR_BAD_ARG
+    sim.close()
+
+
 def test_reductions_and_laplace_probe_match_oracle():
     N, R, W = 64, 12.0, 2.0
     par = dict(wl.BASE_PARAMS, g=0.0, W_phi=W, nu=0.3)
