@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 import pin_cases
+import test_oracle_thermal as th
 from test_oracle_twin import TOL as TWIN_TOL
 from test_oracle_twin import twin_error
 
@@ -64,6 +65,18 @@ CASES = {
     # Section 3: Dirichlet velocity by non-equilibrium extrapolation
     "2d: extrapolation inlet without the equilibrium difference": ("pf_oracle.c", [(
         NEE_2D, "st->fS[i][idx] = st->f[q][src];")], "couette", "2d"),
+    # Appendix B temperature coupling and the rewritten dendrite equation
+    "thermal: grad F source of the wrong sign": ("pf_oracle.c", [(
+        "Qeff = Q / Fu + par[P_W0] * par[P_W0] / (Fu * Fu) * (dFx * Xx + dFy * Xy);",
+        "Qeff = Q / Fu - par[P_W0] * par[P_W0] / (Fu * Fu) * (dFx * Xx + dFy * Xy);")],
+        "gradF", "2d"),
+    "thermal: latent heat of the wrong sign": ("pf_oracle.c", [(
+        "theta = rhoH / (rho * par[P_CP]) + par[P_LATENT] * 0.5 * (1.0 + psi);",
+        "theta = rhoH / (rho * par[P_CP]) - par[P_LATENT] * 0.5 * (1.0 + psi);")],
+        "latent", "2d"),
+    "thermal: c_p left out of the conductivity": ("pf_oracle.c", [(
+        "d.kT = p[P_LE] * p[P_D] * p[P_RHO_L] * p[P_CP];",
+        "d.kT = p[P_LE] * p[P_D] * p[P_RHO_L];")], "heat", "2d"),
     # mistakes in how the step is composed, caught by the per-node twin
     "2d: stretch factor taken at the destination": ("pf_oracle.c", [(STRETCH_2D, STRETCH_2D.replace(
         "st->rr[src]", "st->rr[idx]"))], "twin", "2d"),
@@ -92,6 +105,14 @@ def test_planted_mistake_fails_its_pin(case, mutant_dir):
     if pin == "stretch":
         errs, _ = pin_cases.stretch_errors(kind, lib)
         assert not pin_cases.stretch_pin_holds(errs), errs
+    elif pin == "gradF":
+        assert not th.gradF_pin_holds(th.gradF_errors(lib)), case
+    elif pin == "latent":
+        ratio, dpsi, _ = th.latent_ratio(1.0, lib)
+        assert not abs(ratio - 1.0) < 1e-9, (case, ratio)
+    elif pin == "heat":
+        alphas = th.heat_alpha(1.0, 10.0, lib)
+        assert not all(abs(a / 0.1 - 1.0) < 1e-4 for a in alphas), (case, alphas)
     elif pin == "couette":
         assert not pin_cases.nee_couette_holds(lib), case
     elif pin == "twin":

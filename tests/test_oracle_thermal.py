@@ -11,6 +11,7 @@ latent-heat balance of Eq. eq-tem2, and an independent finite-difference
 solution of the original (not rewritten) equations.
 """
 import json
+import functools
 import math
 import os
 
@@ -86,27 +87,48 @@ def test_enthalpy_gas_and_solute_conserved():
     assert o.state().shape[0] == 45
 
 
+def heat_alpha(Le, cp, lib=None):
+    """Measured diffusivity of a temperature Gaussian in the liquid, per axis,
+    from the growth of its variance between steps 100 and 150."""
+    N, s0 = 96, 4.0
+    y, x = np.mgrid[0:N, 0:N].astype(float)
+    th = -0.5 + 0.1 * np.exp(-((x - 48) ** 2 + (y - 48) ** 2) / (2 * s0 * s0))
+    one = np.ones_like(x)
+    o = oracle.Oracle(N, N, params(Le=Le, cp=cp, g=0.0, theta0=-0.5), lib=lib)
+    o.init_fields(one, -one, one, theta=th)
+    var = []
+    for T in (100, 150):
+        o.step(T - o.steps)
+        w = o.fields(("theta",))["theta"] + 0.5
+        var.append((((x - 48) ** 2 * w).sum() / w.sum(), ((y - 48) ** 2 * w).sum() / w.sum()))
+    # the variance grows by 2 alpha per step over the 50 steps
+    return [(var[1][a] - var[0][a]) / (2 * 50.0) for a in (0, 1)]
+
+
 def test_heat_gaussian_variance_grows_2_alpha_t():
     """In the liquid (phi = 1, psi = -1, v = 0, no latent heat released) the
     temperature equation reduces to d theta/dt = alpha lap theta with alpha =
     Le D (Eq. eq-tem2): once the populations' flux has relaxed from the
     equilibrium start, a Gaussian's variance grows by 2 alpha per step in each
     direction, whatever the lattice heat capacity c_p."""
-    N, s0 = 96, 4.0
-    y, x = np.mgrid[0:N, 0:N].astype(float)
-    th = -0.5 + 0.1 * np.exp(-((x - 48) ** 2 + (y - 48) ** 2) / (2 * s0 * s0))
-    one = np.ones_like(x)
     for Le, cp in ((1.0, 10.0), (1.0, 1.0), (0.5, 10.0)):
-        o = oracle.Oracle(N, N, params(Le=Le, cp=cp, g=0.0, theta0=-0.5))
-        o.init_fields(one, -one, one, theta=th)
-        var = []
-        for T in (100, 150):
-            o.step(T - o.steps)
-            w = o.fields(("theta",))["theta"] + 0.5
-            var.append((((x - 48) ** 2 * w).sum() / w.sum(), ((y - 48) ** 2 * w).sum() / w.sum()))
         alpha = Le * 0.1
-        for a in (0, 1):
-            assert math.isclose((var[1][a] - var[0][a]) / 100.0, alpha, rel_tol=1e-4)
+        for a in heat_alpha(Le, cp):
+            assert math.isclose(a, alpha, rel_tol=1e-4)
+
+
+def latent_ratio(latent, lib=None):
+    """Rise of the mean theta over (latent / 2) times the rise of the mean psi
+    while a seed solidifies in a closed melt (300 steps), and the psi rise."""
+    N = 48
+    o = oracle.Oracle(N, N, params(latent=latent, g=0.0, Le=2.0), lib=lib)
+    o.init_spec([(N / 2, N / 2, 0.0)], 6.0, [])
+    t0 = o.thermal_totals()
+    o.step(300)
+    t = o.thermal_totals()
+    dpsi = (t["sum_psi"] - t0["sum_psi"]) / (N * N)
+    dth = (t["sum_theta"] - t0["sum_theta"]) / (N * N)
+    return dth / (0.5 * latent * dpsi), dpsi, o
 
 
 def test_latent_heat_raises_temperature_by_half_the_psi_change():
@@ -114,18 +136,10 @@ def test_latent_heat_raises_temperature_by_half_the_psi_change():
     h = (1+psi)/2 scaled by c_p^s / c_p.  In a closed periodic melt without gas
     (rho = 1) the mean temperature therefore rises by (c_p^s/c_p) / 2 times the
     rise of the mean psi while a seed solidifies."""
-    N = 48
-    one = np.ones((N, N))
     for latent in (1.0, 0.5):
-        o = oracle.Oracle(N, N, params(latent=latent, g=0.0, Le=2.0))
-        o.init_spec([(N / 2, N / 2, 0.0)], 6.0, [])
-        t0 = o.thermal_totals()
-        o.step(300)
-        t = o.thermal_totals()
-        dpsi = (t["sum_psi"] - t0["sum_psi"]) / one.size
-        dth = (t["sum_theta"] - t0["sum_theta"]) / one.size
+        ratio, dpsi, o = latent_ratio(latent)
         assert dpsi > 5e-3                               # the seed did grow
-        assert math.isclose(dth, 0.5 * latent * dpsi, rel_tol=1e-9)
+        assert math.isclose(ratio, 1.0, rel_tol=1e-9)
         f = o.fields(("theta",))
         assert f["theta"].max() > -0.55 + 1e-3           # heat released at the front
 
@@ -168,6 +182,47 @@ def _fd_1d(p, psi0, C0, th0, T, dt, gradF_weight):
     return psi, C, th
 
 
+@functools.lru_cache(maxsize=None)
+def _gradF_fd():
+    p, psi0, C0, th0, T = _gradF_case()
+    psi_fd, C_fd, th_fd = _fd_1d(p, psi0, C0, th0, T, 0.05, 1.0)
+    psi_no, _, _ = _fd_1d(p, psi0, C0, th0, T, 0.05, 0.0)
+    return psi_fd, C_fd, th_fd, psi_no
+
+
+def _gradF_case():
+    nx, W0 = 192, 8.0
+    p = params(W0=W0, tau0=2 * W0 ** 2 / 0.1, eps_s=0.0, Le=50.0, theta0=-0.3, g=0.0)
+    k = p["k"]
+    x = np.arange(nx, dtype=float)
+    psi0 = np.tanh(math.sqrt(0.5) * (nx / 6 - np.abs(x - nx / 2)) / W0)
+    U0 = 0.5 * np.sin(4 * math.pi * x / nx)
+    C0 = 0.5 * (1 + k - (1 - k) * psi0) * (1 + (1 - k) * U0)
+    th0 = np.full(nx, p["theta0"])
+    return p, psi0, C0, th0, 1200
+
+
+def gradF_errors(lib=None):
+    """(error of the oracle's psi against the finite-difference solution of
+    the original equations, the grad F source's effect in that solution,
+    errors of C and theta, the LB fields)."""
+    p, psi0, C0, th0, T = _gradF_case()
+    nx, ny = len(psi0), 4
+    o = oracle.Oracle(nx, ny, p, lib=lib)
+    o.init_fields(np.ones((ny, nx)), np.tile(psi0, (ny, 1)), np.tile(C0, (ny, 1)),
+                  theta=np.tile(th0, (ny, 1)))
+    o.step(T)
+    f = o.fields(("psi", "C", "theta", "vx", "vy"))
+    psi_fd, C_fd, th_fd, psi_no = _gradF_fd()
+    return (float(np.abs(f["psi"][0] - psi_fd).max()), float(np.abs(psi_fd - psi_no).max()),
+            float(np.abs(f["C"][0] - C_fd).max()), float(np.abs(f["theta"][0] - th_fd).max()), f)
+
+
+def gradF_pin_holds(errs) -> bool:
+    err, effect, eC, eth, _ = errs
+    return effect > 0.03 and err < 0.15 * effect and eC < 0.01 and eth < 0.01
+
+
 def test_gradF_source_matches_the_original_equation():
     """The rewritten dendrite equation of Appendix B equals Eq. eq-AnACE divided
     by F only with the source + W0^2/(tau0 F^2) grad F . (a_s^2 grad psi + N).
@@ -176,29 +231,11 @@ def test_gradF_source_matches_the_original_equation():
     finite-difference solution of the original equations far better than that
     solution differs from the one without the grad F source.  W0 = 8 resolves
     the interface well enough for both discretisations."""
-    nx, ny, W0 = 192, 4, 8.0
-    p = params(W0=W0, tau0=2 * W0 ** 2 / 0.1, eps_s=0.0, Le=50.0, theta0=-0.3, g=0.0)
-    k = p["k"]
-    x = np.arange(nx, dtype=float)
-    psi0 = np.tanh(math.sqrt(0.5) * (nx / 6 - np.abs(x - nx / 2)) / W0)
-    U0 = 0.5 * np.sin(4 * math.pi * x / nx)
-    C0 = 0.5 * (1 + k - (1 - k) * psi0) * (1 + (1 - k) * U0)
-    th0 = np.full(nx, p["theta0"])
-    T = 1200
-    o = oracle.Oracle(nx, ny, p)
-    o.init_fields(np.ones((ny, nx)), np.tile(psi0, (ny, 1)), np.tile(C0, (ny, 1)),
-                  theta=np.tile(th0, (ny, 1)))
-    o.step(T)
-    f = o.fields(("psi", "C", "theta", "vx", "vy"))
+    errs = gradF_errors()
+    f = errs[4]
     assert np.abs(f["vx"]).max() == 0.0 and np.abs(f["vy"]).max() == 0.0
     for a in ("psi", "C", "theta"):
         assert np.abs(f[a] - f[a][0]).max() < 1e-14          # uniform along y
-    psi_fd, C_fd, th_fd = _fd_1d(p, psi0, C0, th0, T, 0.05, 1.0)
-    psi_no, _, _ = _fd_1d(p, psi0, C0, th0, T, 0.05, 0.0)
-    err = np.abs(f["psi"][0] - psi_fd).max()
-    effect = np.abs(psi_fd - psi_no).max()
-    assert np.abs(psi_fd - psi0).max() > 0.5                 # the fronts moved
-    assert effect > 0.03
-    assert err < 0.15 * effect
-    assert np.abs(f["C"][0] - C_fd).max() < 0.01
-    assert np.abs(f["theta"][0] - th_fd).max() < 0.01
+    p, psi0, C0, th0, T = _gradF_case()
+    assert np.abs(_gradF_fd()[0] - psi0).max() > 0.5        # the fronts moved
+    assert gradF_pin_holds(errs)
