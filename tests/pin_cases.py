@@ -175,3 +175,46 @@ def nee_couette_holds(lib=None, ny=16, U=0.01) -> bool:
     v = o.fields(("vx",))["vx"][:, 0]
     y = np.arange(ny)
     return bool(np.abs(v - U * (ny - 0.5 - y) / (ny + 0.5)).max() < 1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Flat gas layer at the equilibrium profile of Eq. (eq-phiEq): a stationary
+# state of the CAC equation (Section 2.2).
+# ---------------------------------------------------------------------------
+FLAT_W, FLAT_NY, FLAT_HALF = 2.0, 96, 24.0
+
+
+def _tanh_fit(dist, prof, half0, width0):
+    from scipy.optimize import curve_fit
+    (w, h), _ = curve_fit(lambda d, w, h: np.tanh((h - d) / w), dist, prof, p0=(width0, half0))
+    return float(w), float(h)
+
+
+def flat_layer(lib=None):
+    """A gas layer of half-thickness FLAT_HALF started at the tanh profile,
+    after 9000 and 10^4 steps: (change over the last 1000 steps, max |v_y|,
+    max |v_x|, relative error of the fitted tanh width, position error of the
+    fitted interface, max |phi - tanh|)."""
+    W, ny = FLAT_W, FLAT_NY
+    y = np.arange(ny, dtype=float)
+    d = np.abs(y - ny / 2)
+    width = 2 * math.sqrt(2) * W
+    phi1 = 0.5 + 0.5 * np.tanh((d - FLAT_HALF) / width)
+    phi = np.tile(phi1[:, None], (1, 4))
+    o = oracle.Oracle(4, ny, dict(wl.BASE_PARAMS, g=0.0, W_phi=W), lib=lib)
+    o.init_fields(phi, -np.ones_like(phi), phi * 1.0)
+    o.step(9000)
+    before = o.fields(("phi",))["phi"][:, 0].copy()
+    o.step(1000)
+    f = o.fields()
+    after = f["phi"][:, 0]
+    w, h = _tanh_fit(d, 1.0 - 2.0 * after, FLAT_HALF, width)
+    return (float(np.abs(after - before).max()), float(np.abs(f["vy"]).max()),
+            float(np.abs(f["vx"]).max()), w / width - 1.0, h - FLAT_HALF,
+            float(np.abs(after - phi1).max()))
+
+
+def flat_layer_holds(m) -> bool:
+    drift, vy, vx, dw, dh, dev = m
+    return (drift < 1e-7 and vy < 1e-7 and vx < 1e-12 and abs(dw) < 5e-3 and abs(dh) < 1e-5
+            and dev < 2.5e-3)

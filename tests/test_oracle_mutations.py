@@ -77,6 +77,13 @@ CASES = {
     "thermal: c_p left out of the conductivity": ("pf_oracle.c", [(
         "d.kT = p[P_LE] * p[P_D] * p[P_RHO_L] * p[P_CP];",
         "d.kT = p[P_LE] * p[P_D] * p[P_RHO_L];")], "heat", "2d"),
+    # Section 2.2 CAC sharpening flux M kappa phi (1 - phi) n
+    "2d: sharpening coefficient kappa 1 % too large": ("pf_oracle.c", [(
+        "const real_t aphi = d.kappa * phi * (1.0 - phi);",
+        "const real_t aphi = 1.01 * d.kappa * phi * (1.0 - phi);")], "flat", "2d"),
+    "2d: sharpening flux of the wrong sign": ("pf_oracle.c", [(
+        "const real_t aphi = d.kappa * phi * (1.0 - phi);",
+        "const real_t aphi = -d.kappa * phi * (1.0 - phi);")], "flat", "2d"),
     # mistakes in how the step is composed, caught by the per-node twin
     "2d: stretch factor taken at the destination": ("pf_oracle.c", [(STRETCH_2D, STRETCH_2D.replace(
         "st->rr[src]", "st->rr[idx]"))], "twin", "2d"),
@@ -115,6 +122,9 @@ def test_planted_mistake_fails_its_pin(case, mutant_dir):
         assert not all(abs(a / 0.1 - 1.0) < 1e-4 for a in alphas), (case, alphas)
     elif pin == "couette":
         assert not pin_cases.nee_couette_holds(lib), case
+    elif pin == "flat":
+        m = pin_cases.flat_layer(lib)
+        assert not pin_cases.flat_layer_holds(m), (case, m)
     elif pin == "twin":
         err = twin_error(lib)
         assert not err <= TWIN_TOL, err
@@ -134,3 +144,4 @@ def test_the_unmodified_copy_passes():
         dev, _ = pin_cases.mass_flux_deviation("2d", lib)
         assert dev < pin_cases.MASS_FLUX_TOL
         assert twin_error(lib) <= TWIN_TOL
+        assert pin_cases.flat_layer_holds(pin_cases.flat_layer(lib))

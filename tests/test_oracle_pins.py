@@ -295,23 +295,20 @@ def _tanh_width(dist, prof, half0, width0):
 
 def test_flat_cac_interface_is_stationary():
     """A flat gas layer initialised with the equilibrium profile of
-    Eq. (eq-phiEq), phi = 1/2 + 1/2 tanh(d / (2 sqrt2 W_phi)), keeps that width
-    and position (up to the lattice discretisation) and stays at rest."""
-    nx, ny, W = 4, 128, 2.0
-    y = np.arange(ny, dtype=float)
-    d = np.abs(y - 64.0)
-    phi1 = 0.5 + 0.5 * np.tanh((d - 24.0) / (2 * math.sqrt(2) * W))
-    phi = np.tile(phi1[:, None], (1, nx))
-    o = oracle.Oracle(nx, ny, params(g=0.0, W_phi=W))
-    o.init_fields(phi, -np.ones_like(phi), phi * 1.0)
-    o.step(2000)
-    f = o.fields()
-    assert np.abs(f["vy"]).max() < 1e-7 and np.abs(f["vx"]).max() < 1e-12
-    w, h = _tanh_width(d, 1.0 - 2.0 * f["phi"][:, 0], 24.0, 2 * math.sqrt(2) * W)
-    assert math.isclose(w, 2 * math.sqrt(2) * W, rel_tol=0.03)
-    assert abs(h - 24.0) < 0.05
+    Eq. (eq-phiEq), phi = 1/2 + 1/2 tanh(d / (2 sqrt2 W_phi)), is a stationary
+    state of the CAC equation (Section 2.2): after 10^4 steps it no longer
+    moves, keeps the tanh width and position and stays at rest.
+
+    The discrete steady profile is not the tanh to 1e-6: the lattice stencils
+    and the regularised normal (reading R6) leave 2.1e-3 (measured; the bulk
+    phases settle at 2.3e-3 from 0 and 1), so that is bounded at 2.5e-3,
+    while the fitted width is held to 0.5 %, which a 1 % error in the
+    sharpening coefficient kappa already breaks (-0.76 % and +1.24 % for
+    kappa x 1.01 and x 0.99, measured)."""
+    m = pin_cases.flat_layer()
+    assert pin_cases.flat_layer_holds(m), m
     # a profile of the wrong width (W_phi -> 1.2 W_phi) is clearly excluded
-    assert not math.isclose(w, 2 * math.sqrt(2) * 1.2 * W, rel_tol=0.1)
+    assert not abs(m[3] - 0.2) < 0.1
 
 
 def _front_width(angle):
