@@ -246,6 +246,33 @@ pf_status pf_get_step_config(const pf_handle *h, int out[3]);
  * buffer.  Synchronises the stream. */
 pf_status pf_get_fields(pf_handle *h, int dom, uint32_t mask, double *host_out, size_t n);
 
+/* pf_set_fields(h, 0, fields6, NULL, n), pf_step(h, n_steps) and
+ * pf_get_fields(h, 0, mask, host_out, n_out) in one call, with the same
+ * result bit for bit (Section 3 unified LBE and Appendix B for the steps), for
+ * a single-domain handle.  The host copies overlap the steps: the lattice is
+ * cut into up to 32 bands of four or more tile rows, each on its own stream, whose
+ * copy, equilibria, steps and copy back run as soon as the bands next to it
+ * allow (a band's step reads state only from its own band and its two
+ * neighbours).  phi is copied first: the buoyancy reference (the mean
+ * density) needs all of it before the first step.  fields6: the six planes
+ * of pf_set_fields (n = nx*ny each); host_out: popcount(mask) planes as
+ * pf_get_fields (n_out doubles).  Page-locked host buffers let the copies run
+ * beside the steps; pageable ones work, with less overlap.  The bands' streams
+ * are prioritised by distance from the periodic seam (the band pair that
+ * waits for everything), so that the middle bands finish first and their
+ * copies back overlap the last steps of the rest; with more bands than
+ * hardware work queues (CUDA_DEVICE_MAX_CONNECTIONS, 8 unless the process
+ * sets it, up to 32) bands that share a queue wait on one another.  Device
+ * staging of (6 + popcount(mask)) n doubles is allocated on first use and
+ * kept.  The launch mode of pf_set_launch is not used (one launch per band
+ * and step).  Runs the three
+ * calls one after the other for n_steps = 0, the thermal mode, non-periodic
+ * sides or fewer than 12 tile rows.  Non-finite input: BAD_ARG and the domain
+ * counts as not initialised, as pf_set_fields.  Synchronises the stream.
+ * Errors: BAD_ARG, STATE, OOM, CUDA, TIMEOUT. */
+pf_status pf_run(pf_handle *h, const double *fields6, size_t n, int n_steps, uint32_t mask,
+                 double *host_out, size_t n_out);
+
 /* Raw state of domain dom (pf_state_planes(h) planes, FP64) to / from the
  * host: checkpoint and restart.  Synchronise the stream. */
 pf_status pf_get_state(pf_handle *h, int dom, double *host_out, size_t n);

@@ -94,6 +94,12 @@ struct pf_handle {
   // discrete-adjoint workspace (grown on demand, released by pf_destroy)
   void* adj_ws = nullptr;
   size_t adj_ws_bytes = 0;
+  // pf_run: one stream per row band, the events that order the bands' steps
+  // (two steps alternate) and the event that releases the bands' first step
+  cudaStream_t run_st[PF_RUN_BANDS] = {};
+  int run_nb = 0;                      // bands the streams' priorities were set for
+  cudaEvent_t run_ev[2][PF_RUN_BANDS] = {};
+  cudaEvent_t run_phi = nullptr, run_ctl = nullptr;
 };
 
 static std::string g_create_err;
@@ -322,6 +328,14 @@ static void release(pf_handle* h) {
   if (h->side) { cudaStreamDestroy(h->side); h->side = nullptr; }
   if (h->fork_ev) { cudaEventDestroy(h->fork_ev); h->fork_ev = nullptr; }
   if (h->join_ev) { cudaEventDestroy(h->join_ev); h->join_ev = nullptr; }
+  h->run_nb = 0;
+  for (int b = 0; b < PF_RUN_BANDS; ++b) {
+    if (h->run_st[b]) { cudaStreamDestroy(h->run_st[b]); h->run_st[b] = nullptr; }
+    for (int k = 0; k < 2; ++k)
+      if (h->run_ev[k][b]) { cudaEventDestroy(h->run_ev[k][b]); h->run_ev[k][b] = nullptr; }
+  }
+  if (h->run_phi) { cudaEventDestroy(h->run_phi); h->run_phi = nullptr; }
+  if (h->run_ctl) { cudaEventDestroy(h->run_ctl); h->run_ctl = nullptr; }
   h->fields = h->grain = nullptr;
 }
 
@@ -554,7 +568,8 @@ static pf_status finish_init(pf_handle* h, int dom) {
   if (st != PF_OK) return st;
   DomDesc& dd = h->ddesc[dom];
   const double n = (double)dd.nx * dd.ny;
-  dd.rho_bar = h->p.rho_g + (dg.sum_phi / n) * (h->p.rho_l - h->p.rho_g);
+  // one rounding of the product-sum (fused), as the device-side form in pf_run
+  dd.rho_bar = std::fma(dg.sum_phi / n, h->p.rho_l - h->p.rho_g, h->p.rho_g);
   if (h->any_bc) {
     pf_status st2 = upload_tables(h);   // the run descriptors carry rho_bar too
     if (st2 != PF_OK) return st2;
@@ -1145,6 +1160,188 @@ extern "C" pf_status pf_get_fields(pf_handle* h, int dom, uint32_t mask, double*
                                h->stream));
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
   return check_device_error(h);
+}
+
+// ---------------------------------------------------------------------------
+// fields in, n steps, fields out, with the host copies overlapped
+// ---------------------------------------------------------------------------
+// The lattice is cut into B row bands of whole tile rows (B <= PF_RUN_BANDS,
+// each band at least four tile rows, so that a step of a band reads state
+// only from its own band and the two next to it).  Band b lives on its own
+// stream: the copy of its rows of psi, C, vx, vy, p, the equilibria of its
+// sites, its tiles of every step, its rows of the output fields and their
+// copy back.  Its step s waits for step s-1 of bands b-1 and b+1 (periodic),
+// which covers both what the step reads and the rows of the buffer it
+// overwrites; its first step also waits for the buoyancy reference rho_bar,
+// which needs the whole phi plane: that plane is copied first, its FP64 sum
+// taken in the order of pf_reduce and rho_bar formed from it on the device
+// with the fused product-sum the host uses, so that it is bit for bit the one
+// pf_set_fields sets.
+template <typename S, typename R>
+static pf_status run_banded(pf_handle* h, const double* in6, int n_steps, uint32_t mask,
+                            double* out, int B, int th) {
+  const DomDesc dd = h->ddesc[0];
+  const long long nn = (long long)dd.nx * dd.ny;
+  const int ns = __builtin_popcount(mask);
+  const int tiles_y = (dd.ny + th - 1) / th;
+  std::vector<int> tr(B + 1);
+  for (int b = 0; b <= B; ++b) tr[b] = (int)((long long)tiles_y * b / B);
+  auto row = [&](int b) { return std::min(tr[b] * th, dd.ny); };
+  pf_status st = ensure_staging(h, (size_t)(6 + ns) * nn + REDUCE_BLOCKS + 1);
+  if (st != PF_OK) return st;
+  double* d_in = h->staging;
+  double* d_out = d_in + 6 * nn;
+  double* d_part = d_out + (size_t)ns * nn;
+  double* d_sum = d_part + REDUCE_BLOCKS;
+  // Streams by distance from the periodic seam (between bands B-1 and 0):
+  // the bands far from it can run steps ahead of it, so they get the higher
+  // priorities, finish first and start their copies back while the bands at
+  // the seam still step.
+  if (h->run_nb != B) {
+    PF_CUDA(h, cudaStreamSynchronize(h->stream));
+    int lo = 0, hi = 0;   // least and greatest priority (numerically lo >= hi)
+    PF_CUDA(h, cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    for (int b = 0; b < B; ++b) {
+      if (h->run_st[b]) { PF_CUDA(h, cudaStreamSynchronize(h->run_st[b])); cudaStreamDestroy(h->run_st[b]); }
+      const int dist = std::min(b, B - 1 - b);                 // 0 at the seam
+      const int pri = lo - (int)((long long)(lo - hi) * dist / std::max(1, (B - 1) / 2));
+      PF_CUDA(h, cudaStreamCreateWithPriority(&h->run_st[b], cudaStreamNonBlocking, pri));
+    }
+    h->run_nb = B;
+  }
+  for (int b = 0; b < B; ++b) {
+    for (int k = 0; k < 2; ++k)
+      if (!h->run_ev[k][b])
+        PF_CUDA(h, cudaEventCreateWithFlags(&h->run_ev[k][b], cudaEventDisableTiming));
+  }
+  if (!h->run_phi) PF_CUDA(h, cudaEventCreateWithFlags(&h->run_phi, cudaEventDisableTiming));
+  if (!h->run_ctl) PF_CUDA(h, cudaEventCreateWithFlags(&h->run_ctl, cudaEventDisableTiming));
+  cudaStream_t S0 = h->stream;
+  st = clear_device_error(h);
+  if (st != PF_OK) return st;
+  st = upload_grain_table(h, 0, {});
+  if (st != PF_OK) return st;
+  // phi first; the bands' copies follow it
+  PF_CUDA(h, cudaMemcpyAsync(d_in, in6, nn * sizeof(double), cudaMemcpyHostToDevice, S0));
+  PF_CUDA(h, cudaEventRecord(h->run_phi, S0));
+  PF_CUDA(h, launch_sum_as<R>(d_in, nn, d_part, d_sum, S0));
+  // rho_bar written into the device descriptor by a kernel: a copy from the
+  // host would queue on the copy engine behind the bands' copies
+  PF_CUDA(h, launch_set_rho_bar(h->d_doms, 0, d_sum, (double)nn, h->p.rho_g,
+                                h->p.rho_l - h->p.rho_g, S0));
+  PF_CUDA(h, cudaEventRecord(h->run_ctl, S0));
+  h->launches += 3;
+  const int cur = h->cur;
+  // the bands' copies one after the other, from the middle band outwards to
+  // the seam, so that the middle bands' data arrive (and their steps start)
+  // while the rest is still on the way
+  std::vector<int> order;
+  for (int k = 0; (int)order.size() < B; ++k) {
+    const int b = B / 2 + ((k & 1) ? -(k + 1) / 2 : k / 2);
+    if (b >= 0 && b < B) order.push_back(b);
+  }
+  for (int k = 0; k < B; ++k) {
+    const int b = order[k];
+    cudaStream_t sb = h->run_st[b];
+    const long long i0 = (long long)row(b) * dd.nx, i1 = (long long)row(b + 1) * dd.nx;
+    PF_CUDA(h, cudaStreamWaitEvent(sb, k == 0 ? h->run_phi : h->run_ev[0][order[k - 1]], 0));
+    PF_CUDA(h, cudaMemcpy2DAsync(d_in + nn + i0, nn * sizeof(double), in6 + nn + i0,
+                                 nn * sizeof(double), (i1 - i0) * sizeof(double), 5,
+                                 cudaMemcpyHostToDevice, sb));
+    PF_CUDA(h, cudaEventRecord(h->run_ev[0][b], sb));
+    SetFieldsArgs<S, R> a{};
+    a.out = reinterpret_cast<S*>(h->pop[cur]);
+    a.aout = reinterpret_cast<R*>(h->aux[cur]);
+    a.fields = fields_ptr<R>(h);
+    a.grain = h->grain;
+    a.plane_stride = h->plane_stride;
+    a.dom = dd;
+    a.f6 = d_in;
+    a.grain_ids = nullptr;
+    a.kp = make_kparams<R>(h->p);
+    a.thermal = 0;
+    a.theta0 = h->p.theta0;
+    a.err = h->d_err;
+    a.i0 = i0;
+    a.i1 = i1;
+    PF_CUDA(h, launch_set_fields<S, R>(a, sb));
+    h->launches++;
+    PF_CUDA(h, cudaEventRecord(h->run_ev[1][b], sb));   // "step -1" of band b
+  }
+  for (int s = 0; s < n_steps; ++s) {
+    const int pin = cur ^ (s & 1), pout = pin ^ 1;
+    StepArgs<S, R> a = make_step_args<S, R>(h, h->pop[pin], h->aux[pin], h->pop[pout],
+                                            h->aux[pout], s + 1 == n_steps);
+    for (int b = 0; b < B; ++b) {
+      cudaStream_t sb = h->run_st[b];
+      if (s == 0) PF_CUDA(h, cudaStreamWaitEvent(sb, h->run_ctl, 0));
+      if (B > 1) {
+        PF_CUDA(h, cudaStreamWaitEvent(sb, h->run_ev[(s + 1) & 1][(b + B - 1) % B], 0));
+        PF_CUDA(h, cudaStreamWaitEvent(sb, h->run_ev[(s + 1) & 1][(b + 1) % B], 0));
+      }
+      a.tile_base = dd.tile0 + tr[b] * dd.tiles_x;
+      a.ntiles = dd.tile0 + tr[b + 1] * dd.tiles_x;
+      PF_CUDA(h, launch_step<S, R>(a, h->variant, h->tx, h->ty, a.ntiles - a.tile_base, sb));
+      h->launches++;
+      PF_CUDA(h, cudaEventRecord(h->run_ev[s & 1][b], sb));
+    }
+  }
+  for (int b = 0; b < B; ++b) {
+    cudaStream_t sb = h->run_st[b];
+    const long long i0 = (long long)row(b) * dd.nx, i1 = (long long)row(b + 1) * dd.nx;
+    PF_CUDA(h, launch_fields_to_f64_range<R>(fields_ptr<R>(h), h->plane_stride, dd.off, nn, i0,
+                                             i1, mask, d_out, sb));
+    h->launches++;
+    PF_CUDA(h, cudaMemcpy2DAsync(out + i0, nn * sizeof(double), d_out + i0, nn * sizeof(double),
+                                 (i1 - i0) * sizeof(double), ns, cudaMemcpyDeviceToHost, sb));
+    PF_CUDA(h, cudaEventRecord(h->run_ev[0][b], sb));
+    PF_CUDA(h, cudaStreamWaitEvent(S0, h->run_ev[0][b], 0));
+  }
+  PF_CUDA(h, cudaStreamSynchronize(S0));
+  PF_CUDA(h, cudaMemcpy(&h->ddesc[0].rho_bar, &h->d_doms[0].rho_bar, sizeof(double),
+                        cudaMemcpyDeviceToHost));
+  h->cur = cur ^ (n_steps & 1);
+  h->steps = n_steps;
+  unsigned int bits = 0;
+  PF_CUDA(h, cudaMemcpy(&bits, h->d_err, sizeof(bits), cudaMemcpyDeviceToHost));
+  if (bits & ERR_NONFINITE_INPUT) {
+    h->inited[0] = 0;
+    pf_status c = clear_device_error(h);
+    if (c != PF_OK) return c;
+    PF_CUDA(h, cudaStreamSynchronize(S0));
+    return fail(h, PF_ERR_BAD_ARG, "non-finite field value; the domain must be initialised again");
+  }
+  h->inited[0] = 1;
+  return check_device_error(h);
+}
+
+extern "C" pf_status pf_run(pf_handle* h, const double* fields6, size_t n, int n_steps,
+                            uint32_t mask, double* host_out, size_t n_out) {
+  if (!h) return PF_ERR_BAD_ARG;
+  if (h->doms.size() != 1) return fail(h, PF_ERR_BAD_ARG, "pf_run takes a single-domain handle");
+  if (!fields6 || !host_out || n_steps < 0 || (mask & ~0x1FFu) || !mask)
+    return fail(h, PF_ERR_BAD_ARG, "need fields, an output, n_steps >= 0 and a field mask");
+  const DomDesc& dd = h->ddesc[0];
+  const size_t nn = (size_t)dd.nx * dd.ny;
+  if (n != nn) return fail(h, PF_ERR_BAD_ARG, "n must equal nx*ny of the domain");
+  if (n_out < nn * __builtin_popcount(mask))
+    return fail(h, PF_ERR_BAD_ARG, "output buffer too small");
+  const bool strip = h->variant == STEP_YMARCH || h->variant == STEP_STAGED;
+  const int th = strip ? h->chunk : h->ty;
+  const int B = std::min(PF_RUN_BANDS, ((dd.ny + th - 1) / th) / 4);
+  if (n_steps == 0 || h->thermal || h->any_bc || B < 3) {
+    // one after the other
+    pf_status st = pf_set_fields(h, 0, fields6, nullptr, n);
+    if (st != PF_OK) return st;
+    st = pf_step(h, n_steps);
+    if (st != PF_OK) return st;
+    return pf_get_fields(h, 0, mask, host_out, n_out);
+  }
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  return dispatch(h, [&](auto s_t, auto r_t) {
+    PF_TYPES(s_t, r_t);
+    return run_banded<S, R>(h, fields6, n_steps, mask, host_out, B, th);
+  });
 }
 
 extern "C" pf_status pf_get_state(pf_handle* h, int dom, double* host_out, size_t n) {

@@ -13,6 +13,7 @@ namespace pf {
 constexpr int NDIAG = 12;            // entries of pf_diag
 constexpr int REDUCE_BLOCKS = 1024;  // blocks of the first reduction pass
 constexpr int MAX_GRAINS = 256;      // grain ids are uint8
+#define PF_RUN_BANDS 32              // row bands of pf_run (at most)
 
 // Step kernel variants (same arithmetic, different traversal).
 enum StepVariant : int { STEP_TILE = 0, STEP_YMARCH = 1, STEP_STAGED = 2 };
@@ -72,6 +73,7 @@ struct SetFieldsArgs {
   int thermal;               // also initialise the temperature lattice at theta0
   double theta0;
   unsigned int* err;         // device error bits: ERR_NONFINITE_INPUT set on a non-finite value
+  long long i0, i1;          // sites [i0, i1) of the domain (i1 <= 0: the whole domain)
 };
 
 // Device error bits (pf_handle::d_err).
@@ -142,6 +144,20 @@ cudaError_t launch_reduce_thermal(const S* pop, const R* fields, long long ps, c
 template <typename R>
 cudaError_t launch_fields_to_f64(const R* fields, long long ps, long long off, long long n,
                                  uint32_t mask, double* out, cudaStream_t st);
+// The same for sites [j0, j1) of the domain only (out keeps the stride n per field).
+template <typename R>
+cudaError_t launch_fields_to_f64_range(const R* fields, long long ps, long long off, long long n,
+                                       long long j0, long long j1, uint32_t mask, double* out,
+                                       cudaStream_t st);
+// *out = the FP64 sum over the n values phi[i] rounded to R, in the order of
+// the diagnostics reduction (launch_reduce): equal to its sum of phi over the
+// fields that pf_set_fields writes from the same values.  partial: REDUCE_BLOCKS doubles.
+template <typename R>
+cudaError_t launch_sum_as(const double* phi, long long n, double* partial, double* out,
+                          cudaStream_t st);
+// doms[dom].rho_bar = fma(*sum / n, drho, rho_g), on the device.
+cudaError_t launch_set_rho_bar(DomDesc* doms, int dom, const double* sum, double n, double rho_g,
+                               double drho, cudaStream_t st);
 template <typename R>
 cudaError_t launch_reduce(const ReduceArgs<R>& a, double* partial, double* out,
                           cudaStream_t st);

@@ -160,7 +160,8 @@ template <typename S, typename R>
 __global__ void k_set_fields(SetFieldsArgs<S, R> a) {
   const DomDesc d = a.dom;
   const long long n = (long long)d.nx * d.ny;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+  const long long hi = a.i1 > 0 ? a.i1 : n;
+  for (long long i = a.i0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < hi;
        i += (long long)gridDim.x * blockDim.x) {
     const long long site = d.off + i;
     const double* F = a.f6;
@@ -387,6 +388,55 @@ __global__ void k_reduce_final(const double* __restrict__ partial, int nblocks,
   out[q] = acc;
 }
 
+// Fields [j0, j1) of a domain to FP64 (the band form of k_fields_to_f64).
+template <typename R>
+__global__ void k_fields_to_f64_range(const R* __restrict__ fields, long long ps, long long off,
+                                      long long n, long long j0, long long j1, uint32_t mask,
+                                      double* __restrict__ out) {
+  int sel[N_FIELDS];
+  int ns = 0;
+  for (int f = 0; f < N_FIELDS; ++f)
+    if (mask & (1u << f)) sel[ns++] = f;
+  const long long m = j1 - j0, tot = m * ns;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long q = i / m, j = j0 + i % m;
+    out[q * n + j] = static_cast<double>(fields[sel[q] * ps + off + j]);
+  }
+}
+
+// FP64 sum of n values rounded to R, with the thread order and block tree of
+// the phi sum in k_reduce_partial / k_reduce_final (REDUCE_BLOCKS x 256).
+template <typename R>
+__global__ void k_sum_as_partial(const double* __restrict__ v, long long n,
+                                 double* __restrict__ partial) {
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    acc += (double)static_cast<R>(v[i]);
+  __shared__ double sh[256];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int stride = blockDim.x / 2; stride > 0; stride >>= 1) {
+    if ((int)threadIdx.x < stride) sh[threadIdx.x] += sh[threadIdx.x + stride];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+__global__ void k_sum_final(const double* __restrict__ partial, int nblocks,
+                            double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double acc = 0.0;
+  for (int b = 0; b < nblocks; ++b) acc = acc + partial[b];
+  *out = acc;
+}
+
+__global__ void k_set_rho_bar(DomDesc* doms, int dom, const double* __restrict__ sum, double n,
+                              double rho_g, double drho) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) doms[dom].rho_bar = fma(*sum / n, drho, rho_g);
+}
+
 // ---------------------------------------------------------------------------
 // Host-side launchers (explicit instantiations for FP64 and FP32).
 // ---------------------------------------------------------------------------
@@ -420,7 +470,8 @@ cudaError_t launch_flag_nonfinite(const double* p, long long n, unsigned int* fl
 
 template <typename S, typename R>
 cudaError_t launch_set_fields(const SetFieldsArgs<S, R>& a, cudaStream_t st) {
-  const long long n = (long long)a.dom.nx * a.dom.ny;
+  const long long n = (a.i1 > 0 ? a.i1 : (long long)a.dom.nx * a.dom.ny) - a.i0;
+  if (n <= 0) return cudaSuccess;
   const int grid = (int)((n + 255) / 256 < 65535 ? (n + 255) / 256 : 65535);
   k_set_fields<S, R><<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();
@@ -465,6 +516,29 @@ cudaError_t launch_fields_to_f64(const R* fields, long long ps, long long off, l
 }
 
 template <typename R>
+cudaError_t launch_fields_to_f64_range(const R* fields, long long ps, long long off, long long n,
+                                       long long j0, long long j1, uint32_t mask, double* out,
+                                       cudaStream_t st) {
+  if (j1 <= j0) return cudaSuccess;
+  k_fields_to_f64_range<R><<<1024, 256, 0, st>>>(fields, ps, off, n, j0, j1, mask, out);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_sum_as(const double* phi, long long n, double* partial, double* out,
+                          cudaStream_t st) {
+  k_sum_as_partial<R><<<REDUCE_BLOCKS, 256, 0, st>>>(phi, n, partial);
+  k_sum_final<<<1, 32, 0, st>>>(partial, REDUCE_BLOCKS, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_rho_bar(DomDesc* doms, int dom, const double* sum, double n, double rho_g,
+                               double drho, cudaStream_t st) {
+  k_set_rho_bar<<<1, 32, 0, st>>>(doms, dom, sum, n, rho_g, drho);
+  return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t launch_reduce(const ReduceArgs<R>& a, double* partial, double* out,
                           cudaStream_t st) {
   k_reduce_partial<R><<<REDUCE_BLOCKS, 256, 0, st>>>(a, partial);
@@ -495,6 +569,16 @@ template cudaError_t launch_fields_to_f64<double>(const double*, long long, long
                                                   long long, uint32_t, double*, cudaStream_t);
 template cudaError_t launch_fields_to_f64<float>(const float*, long long, long long, long long,
                                                  uint32_t, double*, cudaStream_t);
+template cudaError_t launch_fields_to_f64_range<double>(const double*, long long, long long,
+                                                        long long, long long, long long, uint32_t,
+                                                        double*, cudaStream_t);
+template cudaError_t launch_fields_to_f64_range<float>(const float*, long long, long long,
+                                                       long long, long long, long long, uint32_t,
+                                                       double*, cudaStream_t);
+template cudaError_t launch_sum_as<double>(const double*, long long, double*, double*,
+                                           cudaStream_t);
+template cudaError_t launch_sum_as<float>(const double*, long long, double*, double*,
+                                          cudaStream_t);
 template cudaError_t launch_reduce<double>(const ReduceArgs<double>&, double*, double*,
                                            cudaStream_t);
 template cudaError_t launch_reduce<float>(const ReduceArgs<float>&, double*, double*,

@@ -92,6 +92,7 @@ def lib() -> ctypes.CDLL:
     L.pf_set_fields.argtypes = [P, I, D, D, S]
     L.pf_step.argtypes = [P, I]
     L.pf_get_fields.argtypes = [P, I, ctypes.c_uint32, D, S]
+    L.pf_run.argtypes = [P, D, S, I, ctypes.c_uint32, D, S]
     L.pf_get_state.argtypes = [P, I, D, S]
     L.pf_set_state.argtypes = [P, I, D, S]
     L.pf_reduce.argtypes = [P, I, ctypes.POINTER(pf_probe), ctypes.POINTER(pf_diag)]
@@ -160,8 +161,8 @@ def lib() -> ctypes.CDLL:
     L.pf3f_last_error.restype = ctypes.c_char_p
     L.pf3f_destroy.argtypes = [P]
     for name in ("pf_params_default", "pf_params_derived", "pf_create", "pf_init_fields",
-                 "pf_set_fields", "pf_step", "pf_get_fields", "pf_get_state", "pf_set_state",
-                 "pf_reduce", "pf_sync", "pf_destroy", "pf_set_step_config",
+                 "pf_set_fields", "pf_step", "pf_get_fields", "pf_run", "pf_get_state",
+                 "pf_set_state", "pf_reduce", "pf_sync", "pf_destroy", "pf_set_step_config",
                  "pf_get_step_config", "pf_reduce_noalloc", "pf_adjoint_step",
                  "pf_set_launch", "pf_autotune", "pf_set_temperature", "pf_reduce_thermal",
                  "pf_set_boundaries", "pf3_create", "pf3_init_seeds", "pf3_set_fields",
@@ -383,6 +384,31 @@ class Simulation:
         if out is None:
             out = np.empty(len(sel) * nx * ny)
         _check(lib().pf_get_fields(self.h, dom, mask, _dp(out), out.size), self.h)
+        out = out[: len(sel) * nx * ny].reshape(len(sel), ny, nx)
+        return {nm: out[i] for i, nm in enumerate(sel)}
+
+    def run(self, f6: np.ndarray, n_steps: int, names=FIELDS,
+            out: np.ndarray | None = None) -> dict:
+        """pf_run: set the fields of the single domain from f6 (C-contiguous
+        float64, shape (6, ny, nx): phi, psi, C, vx, vy, p), advance n_steps
+        and return the named fields of the last step, with the host copies
+        overlapped with the steps (page-locked f6 and out let them run beside
+        the kernels).  out: optional float64 buffer of at least
+        len(names) * nx * ny values."""
+        if len(self.domains) != 1:
+            raise ValueError("run takes a single-domain handle")
+        nx, ny = self.domains[0]
+        if (not isinstance(f6, np.ndarray) or f6.dtype != np.float64 or f6.shape != (6, ny, nx)
+                or not f6.flags["C_CONTIGUOUS"]):
+            raise ValueError(f"f6 must be a C-contiguous float64 array of shape (6, {ny}, {nx})")
+        mask = 0
+        for nm in names:
+            mask |= 1 << FIELDS.index(nm)
+        sel = [nm for nm in FIELDS if mask & (1 << FIELDS.index(nm))]
+        if out is None:
+            out = np.empty(len(sel) * nx * ny)
+        _check(lib().pf_run(self.h, _dp(f6), nx * ny, int(n_steps), mask, _dp(out), out.size),
+               self.h)
         out = out[: len(sel) * nx * ny].reshape(len(sel), ny, nx)
         return {nm: out[i] for i, nm in enumerate(sel)}
 
