@@ -41,9 +41,12 @@ constexpr int NSTATEF = 66, NFIELDSF = 9;
 constexpr int E_POP = 59, NPOPF_TH = 66, AX_HO = 7, NAUXF_TH = 8, NSTATEF_TH = 74,
               NFIELDSF_TH = 10;
 // shared memory of k_step3f: 5 rings (phi, psi, v_o) of 4 planes of the halo tile
-// (a sixth ring, of U, in thermal mode)
+// (a sixth ring, of U, in thermal mode), then, for two planes, the 9 pair
+// differences h_{2j-1} - h_{2j} of each interior site's streamed CAC populations
 template <typename R>
-constexpr size_t ring_bytes(bool th) { return (th ? 6 : 5) * 4 * HY * HX * sizeof(R); }
+__host__ __device__ constexpr size_t rings_only_bytes(bool th) { return (th ? 6 : 5) * 4 * HY * HX * sizeof(R); }
+template <typename R>
+__host__ __device__ constexpr size_t ring_bytes(bool th) { return rings_only_bytes<R>(th) + 2 * 9 * NIN * sizeof(R); }
 
 // D3Q19: rest, faces, edges; opposite directions in pairs (2j-1, 2j)
 __host__ __device__ constexpr int c19(int i, int a) {
@@ -228,15 +231,21 @@ __device__ __forceinline__ int side_coord(int c, int n, int t0, int t1, int& t) 
   return m < 0 ? 0 : (m >= n ? n - 1 : m);
 }
 
-// phi = sum of the streamed h at (x, y, z)
+// phi = sum of the streamed h at (x, y, z); with pd (stride ps), also the 9
+// pair differences h_{2j-1} - h_{2j} that the CAC collision takes
 template <typename S, typename R, bool BC, typename I>
-__device__ __forceinline__ R stream_phi(const ArgsF<S, R, I>& a, int x, int y, int z) {
+__device__ __forceinline__ R stream_phi(const ArgsF<S, R, I>& a, int x, int y, int z,
+                                        R* pd = nullptr, int pstride = 0) {
   CSum<R> s;
+  R hodd = R(0);
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
     int q;
     const unsigned long long src = pull19<S, R, BC>(a, x, y, z, i, q);
-    s.add(ld<R>(pl(a.in, H_POP + q, a.ps), src));
+    const R hv = ld<R>(pl(a.in, H_POP + q, a.ps), src);
+    s.add(hv);
+    if (i & 1) hodd = hv;
+    else if (i > 0 && pd) pd[(i / 2 - 1) * pstride] = hodd - hv;
   }
   return s.value();
 }
@@ -290,6 +299,8 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R, I> a) 
   R (*rv0)[HY][HX] = rphi + 8;
   R (*rv[3])[HY][HX] = {rv0, rv0 + 4, rv0 + 8};
   R (*rU)[HY][HX] = rphi + 20;         // TH only
+  // pair differences of the streamed h of interior site t, plane z in [z & 1]
+  R (*hd)[9][NIN] = reinterpret_cast<R (*)[9][NIN]>(smem_raw + rings_only_bytes<R>(TH));
   const int t = threadIdx.x;
   int hx = 0, hy = 0;
   const bool interior = t < NIN;
@@ -343,7 +354,7 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R, I> a) 
         R g[7], psi, po;
         stream_g<S, R, BC>(a, x, y, z, g, psi, po);
         rpsi[slot][hy][hx] = gmap(psi, 1, sz);
-        rphi[slot][hy][hx] = stream_phi<S, R, BC>(a, x, y, z);
+        rphi[slot][hy][hx] = stream_phi<S, R, BC>(a, x, y, z, mine ? &hd[(za - 1 + k) & 1][0][t] : nullptr, NIN);
         const unsigned long long s0 = site_of(a, x, y, z);
 #pragma unroll
         for (int c = 0; c < 3; ++c) rv[c][slot][hy][hx] = gmap(pl(a.ain, AX_VO + c, a.ps)[s0], 3 + c, sz);
@@ -382,7 +393,7 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R, I> a) 
         R psi;
         stream_g<S, R, BC>(a, x, y, zn, gL, psi, poL);
         rpsi[slot][hy][hx] = gmap(psi, 1, sz);
-        rphi[slot][hy][hx] = stream_phi<S, R, BC>(a, x, y, zn);
+        rphi[slot][hy][hx] = stream_phi<S, R, BC>(a, x, y, zn, mine ? &hd[(z + 1) & 1][0][t] : nullptr, NIN);
         const unsigned long long sn = site_of(a, x, y, zn);
 #pragma unroll
         for (int c = 0; c < 3; ++c) rv[c][slot][hy][hx] = gmap(pl(a.ain, AX_VO + c, a.ps)[sn], 3 + c, sz);
@@ -526,14 +537,11 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R, I> a) 
 #pragma unroll
           for (int jp = 1; jp <= 9; ++jp) {
             const int i = 2 * jp - 1;
-            int qp, qm;
-            const unsigned long long sp_ = pull19<S, R, BC>(a, x, y, z, i, qp);
-            const unsigned long long sm_ = pull19<S, R, BC>(a, x, y, z, i + 1, qm);
-            const R hp = ld<R>(pl(a.in, H_POP + qp, a.ps), sp_);
-            const R hm = ld<R>(pl(a.in, H_POP + qm, a.ps), sm_);
+            // h_i - h_{i+1} of this site, kept by the ring fill of plane z
+            const R dh = hd[z & 1][jp - 1][t];
             const R cu = R(c19(i, 0)) * v[0] + R(c19(i, 1)) * v[1] + R(c19(i, 2)) * v[2];
             const R cG = R(c19(i, 0)) * G1[0] + R(c19(i, 1)) * G1[1] + R(c19(i, 2)) * G1[2];
-            const R Do = (hp - hm) - R(2) * w19<R>(i) * (R(3) * phi * cu - R(1.5) * cG);
+            const R Do = dh - R(2) * w19<R>(i) * (R(3) * phi * cu - R(1.5) * cG);
             if (c19(i, 0)) nj[0] += R(c19(i, 0)) * Do;
             if (c19(i, 1)) nj[1] += R(c19(i, 1)) * Do;
             if (c19(i, 2)) nj[2] += R(c19(i, 2)) * Do;
