@@ -399,6 +399,22 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R, I> a) 
         for (int c = 0; c < 3; ++c) rv[c][slot][hy][hx] = gmap(pl(a.ain, AX_VO + c, a.ps)[sn], 3 + c, sz);
         if constexpr (TH) rU[slot][hy][hx] = gmap(stream_U<S, R, BC>(a, x, y, zn, psi), 2, sz);
       }
+      // the streamed f of this plane, issued before the barrier so that their
+      // latency overlaps the wait and the stencils (FP32 periodic kernels; in
+      // the boundary and FP64 variants the registers they hold there cost spills)
+      R fv[19];
+      auto pull_f = [&]() {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+          int qf;
+          const unsigned long long sf = pull19<S, R, BC>(a, x, y, z, i, qf);
+          fv[i] = ld<R>(pl(a.in, F_POP + qf, a.ps), sf);
+        }
+      };
+      constexpr bool EARLY_F = !BC && sizeof(R) == 4;
+      if constexpr (EARLY_F) {
+        if (mine) pull_f();
+      }
       __syncthreads();
       if (mine) {
         const CoefF<R>& c = a.c;
@@ -435,13 +451,11 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R, I> a) 
         }
         Fp[1] -= (rho - c.rho_bar) * c.g;
         // NS moments of the pulled f, drag, pressure
-        R fv[19], j[3] = {R(0), R(0), R(0)};
+        if constexpr (!EARLY_F) pull_f();
+        R j[3] = {R(0), R(0), R(0)};
         CSum<R> snz;
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
-          int qf;
-          const unsigned long long sf = pull19<S, R, BC>(a, x, y, z, i, qf);
-          fv[i] = ld<R>(pl(a.in, F_POP + qf, a.ps), sf);
           if (i) snz.add(fv[i]);
           if (c19(i, 0)) j[0] += R(c19(i, 0)) * fv[i];
           if (c19(i, 1)) j[1] += R(c19(i, 1)) * fv[i];
