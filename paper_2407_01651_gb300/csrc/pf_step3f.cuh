@@ -412,8 +412,15 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R, I> a) 
         }
       };
       constexpr bool EARLY_F = !BC && sizeof(R) == 4;
+      R ev[7], Ho = R(0);   // TH: streamed temperature populations, lagged H
       if constexpr (EARLY_F) {
-        if (mine) pull_f();
+        if (mine) {
+          pull_f();
+          if constexpr (TH) {
+            stream7f<S, R, BC>(a, E_POP, x, y, z, ev, a.c.th0);
+            Ho = pl(a.ain, AX_HO, a.ps)[site];
+          }
+        }
       }
       __syncthreads();
       if (mine) {
@@ -621,9 +628,8 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R, I> a) 
         const R omp2 = R(1) - psi * psi;
         // TH: rho H = sum e, theta from the local density
         R rhoH = R(0), theta = c.theta, iF = R(1);
-        R ev[7];
         if constexpr (TH) {
-          stream7f<S, R, BC>(a, E_POP, x, y, z, ev, c.th0);
+          if constexpr (!EARLY_F) stream7f<S, R, BC>(a, E_POP, x, y, z, ev, c.th0);
           CSum<R> ce;
 #pragma unroll
           for (int i = 0; i < 7; ++i) ce.add(ev[i]);
@@ -696,7 +702,7 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R, I> a) 
         // that the rest population rho H - 6 theta/8 is exact in the common case
         if constexpr (TH) {
           const R rho_o = c.rg + phio * c.drho;
-          const R Ho = pl(a.ain, AX_HO, a.ps)[site];
+          if constexpr (!EARLY_F) Ho = pl(a.ain, AX_HO, a.ps)[site];
           R Sf[3];
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
