@@ -363,6 +363,10 @@ def e2e_2d(torch, sim, doms, steps: int, thermal: bool = False) -> dict:
     one = len(doms) == 1 and not thermal
     if one:
         sim.run(ins[0], 2, ("phi", "psi", "C", "p", "vx", "vy"), out=outs[0])
+    else:
+        # touch the fresh page-locked outputs once, untimed (see e2e_3d)
+        for k, (d, nx, ny) in enumerate(doms):
+            sim.fields(d, ("phi", "psi", "C", "p", "vx", "vy"), out=outs[k])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     if one:
@@ -384,7 +388,7 @@ def e2e_2d(torch, sim, doms, steps: int, thermal: bool = False) -> dict:
             "bands" if one else
             "pf_set_fields" + (" and pf_set_temperature" if thermal else "") +
             " from page-locked FP64 host fields, pf_step(K), pf_get_fields to page-locked "
-            "FP64 host memory")
+            "FP64 host memory (written once before, untimed)")
     return {"value": sites * steps / e_s / 1e6, "unit": "MLUPS",
             "h2d_bytes_per_step": nb / steps, "d2h_bytes_per_step": 6 * 8 * sites / steps,
             "seconds": e_s,
@@ -414,6 +418,9 @@ def e2e_3d(torch, sim, steps: int, flow: bool, thermal: bool = False) -> dict:
         C[...] = f["C"]
     k = sim.field_planes
     out = _pinned(torch, (k * n,))
+    # the first copy into freshly page-locked memory costs several times a
+    # later one (the pages are mapped then): touch the output once, untimed
+    sim.fields(out=out)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     if flow:
@@ -432,7 +439,8 @@ def e2e_3d(torch, sim, steps: int, flow: bool, thermal: bool = False) -> dict:
             "what": ("pf3f_set_fields" if flow else "pf3_set_fields") +
                     (" and the temperature" if thermal else "") +
                     " from page-locked FP64 host fields, step(K), every field plane to "
-                    "page-locked FP64 host memory; host wall clock"}
+                    "page-locked FP64 host memory (written once before, untimed); host wall "
+                    "clock"}
 
 
 def run_reference(args) -> None:
