@@ -20,7 +20,7 @@ constexpr int NHALO = HX * HY - NIN;
 constexpr int THREADS = (NIN + NHALO + 31) / 32 * 32;
 constexpr int MIN_CTAS = 1;
 #ifndef PF3F_PREFETCH
-#define PF3F_PREFETCH 1   // planes ahead of the z-march warmed in L2 (0: none)
+#define PF3F_PREFETCH 0   // planes ahead of the z-march warmed in L2 (0: none)
 #endif
 static_assert(HX == d3::HX, "the stencil helpers assume rows of d3::HX");
 using d3::cx7;
