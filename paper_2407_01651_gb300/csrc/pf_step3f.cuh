@@ -369,6 +369,21 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R, I> a) 
     for (int z = za; z < zb; ++z) {
       const unsigned long long site = site_of(a, x, y, z);
       R sv[7], Qo = R(0), phio = R(0), Co = R(0), vo[3] = {R(0), R(0), R(0)};
+      if (active) {
+        int sz = 0;
+        const int zn = BC ? side_coord(z + 1, a.nz, a.bc[4], a.bc[5], sz) : wrap1(z + 1, a.nz);
+        const int slot = (z + 1) & 3;
+        R psi;
+        stream_g<S, R, BC>(a, x, y, zn, gL, psi, poL);
+        rpsi[slot][hy][hx] = gmap(psi, 1, sz);
+        rphi[slot][hy][hx] = stream_phi<S, R, BC>(a, x, y, zn, mine ? &hd[(z + 1) & 1][0][t] : nullptr, NIN);
+        const unsigned long long sn = site_of(a, x, y, zn);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rv[c][slot][hy][hx] = gmap(pl(a.ain, AX_VO + c, a.ps)[sn], 3 + c, sz);
+        if constexpr (TH) rU[slot][hy][hx] = gmap(stream_U<S, R, BC>(a, x, y, zn, psi), 2, sz);
+      }
+      // the site's own streamed s and lagged scalars: needed after the barrier
+      // only, so issued after the fill whose loads the barrier waits on
       if (mine) {
         stream7f<S, R, BC>(a, S_POP, x, y, z, sv, R(1));
         Qo = pl(a.ain, AX_QO, a.ps)[site];
@@ -385,19 +400,6 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) k_step3f(ArgsF<S, R, I> a) 
 #pragma unroll
           for (int q = 0; q < NA; ++q) d3::prefetch_l2(pl(a.ain, q, a.ps) + pf2);
         }
-      }
-      if (active) {
-        int sz = 0;
-        const int zn = BC ? side_coord(z + 1, a.nz, a.bc[4], a.bc[5], sz) : wrap1(z + 1, a.nz);
-        const int slot = (z + 1) & 3;
-        R psi;
-        stream_g<S, R, BC>(a, x, y, zn, gL, psi, poL);
-        rpsi[slot][hy][hx] = gmap(psi, 1, sz);
-        rphi[slot][hy][hx] = stream_phi<S, R, BC>(a, x, y, zn, mine ? &hd[(z + 1) & 1][0][t] : nullptr, NIN);
-        const unsigned long long sn = site_of(a, x, y, zn);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) rv[c][slot][hy][hx] = gmap(pl(a.ain, AX_VO + c, a.ps)[sn], 3 + c, sz);
-        if constexpr (TH) rU[slot][hy][hx] = gmap(stream_U<S, R, BC>(a, x, y, zn, psi), 2, sz);
       }
       // the streamed f of this plane, issued before the barrier so that their
       // latency overlaps the wait and the stencils (FP32 periodic kernels; in
