@@ -106,3 +106,22 @@ def test_run_rejects_non_finite_input_and_bad_arguments():
     with pytest.raises(ValueError):
         two.run(np.zeros((6, 64, 64)), 1)
     two.close()
+
+
+def test_run_beside_graphs_and_the_one_launch_mode():
+    """pf_run ignores the launch mode (one launch per band and step) and may
+    leave the state in the other buffer; steps taken after it under the
+    one-launch mode with captured graphs give what plain steps give."""
+    lay = wl.random_layout(256, 384, 3, 4, rng_seed=9, R_max=20)
+    f6 = developed_fields(lay, "fp32")
+    states = []
+    for mode in ((0, 0, 0), (0, 2, 4)):
+        sim = pf.Simulation([(lay.nx, lay.ny)], lay.params, "fp32")
+        sim.set_step_config(1, 8, 0)
+        sim.set_launch(*mode)
+        sim.step(4)                  # graphs captured before the call (mode 2)
+        sim.run(f6, 5)               # odd: the state ends in the other buffer
+        sim.step(9)
+        states.append(sim.get_state(0))
+        sim.close()
+    assert np.array_equal(states[0], states[1])
