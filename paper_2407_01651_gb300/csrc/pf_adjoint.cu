@@ -248,65 +248,64 @@ __global__ void __launch_bounds__(ADJ_TX * ADJ_TY) k_adj_transpose(AdjArgs<S, R>
     s_aphi[ly][lx] = aphi;
     s_apsi[ly][lx] = apsi;
   }
-  __syncthreads();
+  // the site's gathers that need no shared value are issued (and the planes
+  // they complete stored) before the barrier, so that their latency overlaps
+  // the wait for the ring
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-  if (x >= d.nx || y >= d.ny) return;
+  const bool valid = x < d.nx && y < d.ny;
   const int cx = threadIdx.x + 1, cy = threadIdx.y + 1;
-  const Src9 src = sources(d, x, y);
+  const Src9 src = sources(d, valid ? x : 0, valid ? y : 0);
   const unsigned site = src.s[0];
-  // every input of the site first (independent loads), then the stores
-  R avx = __ldg(plane(A, AI_VXO, ps) + site), avy = __ldg(plane(A, AI_VYO, ps) + site);
+  R hraw[9], gown[5], gdst[5], rsrc[5], gdiff[5], rr_own = R(0), apsio = R(0);
+  if (valid) {
+    R avx = __ldg(plane(A, AI_VXO, ps) + site), avy = __ldg(plane(A, AI_VYO, ps) + site);
 #pragma unroll
-  for (int j = 1; j < 9; ++j) {
-    const unsigned z = src.s[j];
-    const R wx = R(3) * w[j] * R(CX9[j]), wy = R(3) * w[j] * R(CY9[j]);
-    avx += wx * __ldg(plane(A, AI_DVXX, ps) + z) + wy * __ldg(plane(A, AI_DVXY, ps) + z);
-    avy += wx * __ldg(plane(A, AI_DVYX, ps) + z) + wy * __ldg(plane(A, AI_DVYY, ps) + z);
-  }
-  R lf[9], lh[9], ls[5], lgpre[5], lgpost[5];
+    for (int j = 1; j < 9; ++j) {
+      const unsigned z = src.s[j];
+      const R wx = R(3) * w[j] * R(CX9[j]), wy = R(3) * w[j] * R(CY9[j]);
+      avx += wx * __ldg(plane(A, AI_DVXX, ps) + z) + wy * __ldg(plane(A, AI_DVXY, ps) + z);
+      avy += wx * __ldg(plane(A, AI_DVYX, ps) + z) + wy * __ldg(plane(A, AI_DVYY, ps) + z);
+    }
 #pragma unroll
-  for (int q = 0; q < 9; ++q) {
-    const unsigned t = src.s[OPP[q]];   // x + c_q
-    lf[q] = __ldg(plane(A, AI_F + q, ps) + t);
-    lh[q] = __ldg(plane(A, AI_H + q, ps) + t) + s_aphi[cy + CY9[q]][cx + CX9[q]];
+    for (int q = 0; q < 9; ++q) {
+      const unsigned t = src.s[OPP[q]];   // x + c_q
+      plane(L, 0 + q, ps)[site] = __ldg(plane(A, AI_F + q, ps) + t);
+      hraw[q] = __ldg(plane(A, AI_H + q, ps) + t);
+    }
+    rr_own = __ldg(plane(X, A_RR, ps) + site);
+    apsio = __ldg(plane(A, AI_PSIO, ps) + site);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const unsigned t = src.s[OPP[q]];   // destination of q
+      const unsigned sq = src.s[q];       // source of q
+      plane(L, 29 + q, ps)[site] = __ldg(plane(A, AI_S + q, ps) + t);
+      gown[q] = __ldg(plane(A, AI_G + q, ps) + site);
+      gdst[q] = __ldg(plane(A, AI_G + q, ps) + t);
+      rsrc[q] = __ldg(plane(X, A_RR, ps) + sq);
+      gdiff[q] = ld<R>(plane(P, P_GPOST + q, ps), site) - ld<R>(plane(P, P_GPRE + q, ps), t);
+    }
+    plane(L, 34, ps)[site] = __ldg(plane(A, AI_PHIO, ps) + site);
+    plane(L, 35, ps)[site] = __ldg(plane(A, AI_CO, ps) + site);
+    plane(L, 36, ps)[site] = avx;
+    plane(L, 37, ps)[site] = avy;
+    plane(L, 38, ps)[site] = __ldg(plane(A, AI_QO, ps) + site);
   }
-  const R rr_own = __ldg(plane(X, A_RR, ps) + site);
-  const R apsio = __ldg(plane(A, AI_PSIO, ps) + site);
+  __syncthreads();
+  if (!valid) return;
+#pragma unroll
+  for (int q = 0; q < 9; ++q)
+    plane(L, 9 + q, ps)[site] = hraw[q] + s_aphi[cy + CY9[q]][cx + CX9[q]];
   const R as1 = s_apsi[cy][cx];
   R lrr = R(0);
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    const unsigned t = src.s[OPP[q]];   // destination of q
-    const unsigned sq = src.s[q];       // source of q
-    ls[q] = __ldg(plane(A, AI_S + q, ps) + t);
-    const R ag_own = __ldg(plane(A, AI_G + q, ps) + site) + as1;
-    const R ag_dst = __ldg(plane(A, AI_G + q, ps) + t) + s_apsi[cy + CY9[q]][cx + CX9[q]];
-    const R rr_src = __ldg(plane(X, A_RR, ps) + sq);
-    lgpre[q] = ag_own * (R(1) - rr_src) + apsio;
-    lgpost[q] = ag_dst * rr_own;
-    const R gq_own = ld<R>(plane(P, P_GPOST + q, ps), site);
-    const R gp_dst = ld<R>(plane(P, P_GPRE + q, ps), t);
-    lrr += ag_dst * (gq_own - gp_dst);
-  }
-  const R l34 = __ldg(plane(A, AI_PHIO, ps) + site), l35 = __ldg(plane(A, AI_CO, ps) + site);
-  const R l38 = __ldg(plane(A, AI_QO, ps) + site);
-#pragma unroll
-  for (int q = 0; q < 9; ++q) {
-    plane(L, 0 + q, ps)[site] = lf[q];
-    plane(L, 9 + q, ps)[site] = lh[q];
-  }
-#pragma unroll
-  for (int q = 0; q < 5; ++q) {
-    plane(L, 18 + q, ps)[site] = lgpre[q];
-    plane(L, 23 + q, ps)[site] = lgpost[q];
-    plane(L, 29 + q, ps)[site] = ls[q];
+    const R ag_own = gown[q] + as1;
+    const R ag_dst = gdst[q] + s_apsi[cy + CY9[q]][cx + CX9[q]];
+    plane(L, 18 + q, ps)[site] = ag_own * (R(1) - rsrc[q]) + apsio;
+    plane(L, 23 + q, ps)[site] = ag_dst * rr_own;
+    lrr += ag_dst * gdiff[q];
   }
   plane(L, 28, ps)[site] = lrr;
-  plane(L, 34, ps)[site] = l34;
-  plane(L, 35, ps)[site] = l35;
-  plane(L, 36, ps)[site] = avx;
-  plane(L, 37, ps)[site] = avy;
-  plane(L, 38, ps)[site] = l38;
 }
 
 // Adjoint of the final-state objective
