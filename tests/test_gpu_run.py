@@ -125,3 +125,18 @@ def test_run_beside_graphs_and_the_one_launch_mode():
         states.append(sim.get_state(0))
         sim.close()
     assert np.array_equal(states[0], states[1])
+
+
+@pytest.mark.parametrize("shape,cfg", [((200, 385), (1, 32, 0)), ((136, 300), (2, 16, 0))])
+def test_run_ragged_lattices(shape, cfg):
+    """Lattices whose last tile row is ragged (385 = 12 x 32 + 1 rows) and whose
+    width is not a multiple of the strip: pf_run still equals the three calls."""
+    nx, ny = shape
+    lay = wl.random_layout(nx, ny, 2, 3, rng_seed=10, R_max=14)
+    prec = "fp16" if cfg[0] == 2 else "fp32"
+    f6 = developed_fields(lay, prec, 10)
+    ref, ref_state = one_after_the_other(lay, prec, cfg, f6, 7)
+    got, got_state, _ = banded(lay, prec, cfg, f6, 7)
+    for nm in pf.FIELDS:
+        assert np.array_equal(got[nm], ref[nm]), nm
+    assert np.array_equal(got_state, ref_state)
