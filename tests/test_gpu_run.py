@@ -119,6 +119,7 @@ def test_run_beside_graphs_and_the_one_launch_mode():
         sim = pf.Simulation([(lay.nx, lay.ny)], lay.params, "fp32")
         sim.set_step_config(1, 8, 0)
         sim.set_launch(*mode)
+        sim.init_fields(0, lay.seeds, lay.R_s, lay.bubbles)
         sim.step(4)                  # graphs captured before the call (mode 2)
         sim.run(f6, 5)               # odd: the state ends in the other buffer
         sim.step(9)
