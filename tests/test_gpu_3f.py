@@ -474,3 +474,35 @@ def test_3f_sides_configuration_errors():
     with pytest.raises(pf.PFError) as e:
         sim.set_boundaries((1, 1, 0, 0, 0, 0))
     assert e.value.code == pf.PF_ERR_STATE
+
+
+# ---------------------------------------------------------------------------
+# z-tile length: the march recomputes its ring at each tile start, so the
+# tiling of z must not change a single bit of the state
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("kind", ["periodic", "thermal", "sides"])
+def test_3f_z_tile_length_does_not_change_the_state(precision, kind):
+    """80 planes in z: the default tile (36: tiles of 36, 36 and a ragged 8),
+    tiles of 5, 7 (ragged 3) and one tile over all of z give the same state
+    bit for bit after several steps, periodic, with the temperature lattice
+    and with walls and symmetric planes."""
+    shape = (40, 24, 80)
+    params = dict(T3F if kind == "thermal" else P3F, g=2e-5)
+    seeds = [(10.3, 9.1, 6.2), (33.0, 14.0, 40.5), (20.0, 4.0, 74.0)]
+    bubbles = [(25.0, 12.0, 36.0, 5.0), (6.0, 15.0, 78.0, 3.5)]
+    states = []
+    for chunk in (None, 5, 7, 80):
+        sim = pf.Simulation3F(shape, dict(wl.BASE_PARAMS, **params), precision)
+        if kind == "sides":
+            sim.set_boundaries((1, 1, 2, 2, 3, 3))
+        sim.init_spec(seeds, 5.0, bubbles)
+        if kind == "thermal":
+            sim.set_temperature(theta_field(shape))
+        if chunk is not None:
+            sim.set_chunk(chunk)
+        sim.step(5)
+        states.append(sim.get_state())
+        sim.close()
+    for s in states[1:]:
+        assert np.array_equal(s, states[0])
