@@ -60,11 +60,16 @@ KERNEL_SOURCES = ("paper_2407_01651_gb300/csrc/pf_step.cu",
                   "paper_2407_01651_gb300/csrc/pf_site.cuh",
                   "paper_2407_01651_gb300/csrc/pf_v2.cuh",
                   "paper_2407_01651_gb300/csrc/pf_step_staged.cu")
+# the 3-D two-phase step (its kernel, launch and default z-tile length)
+KERNEL_SOURCES_3F = ("paper_2407_01651_gb300/csrc/pf_step3f.cuh",
+                     "paper_2407_01651_gb300/csrc/pf_step3f.cu",
+                     "paper_2407_01651_gb300/csrc/pf_d3.cuh",
+                     "paper_2407_01651_gb300/csrc/pf_device.cuh")
 
 
-def kernel_hash() -> str:
+def kernel_hash(sources=KERNEL_SOURCES) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -78,14 +83,14 @@ def measured_peaks() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
-def recorded_traffic(precision: str, size: int):
+def recorded_traffic(precision: str, size: int, kind: str = "step", sources=KERNEL_SOURCES):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", f"step_{precision}_{size}_traffic.json")
+    path = os.path.join(ROOT, "profiles", f"{kind}_{precision}_{size}_traffic.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
-        if rec.get("kernel_hash") == kernel_hash():
+        if rec.get("kernel_hash") == kernel_hash(sources):
             return rec["dram_bytes_per_launch"]
     except Exception:
         pass
@@ -896,7 +901,9 @@ def run_3d_flow(args) -> None:
                                (", temperature lattice (Le 50, theta0 -0.55)" if thermal else ""),
                    "lattice": [n, n, n], "precision": prec,
                    "l2": f"{bpl * sites / 1e9:.1f} GB read+written per step > L2 (no flush)"},
-        "roofline": roofline(bpl, sites, ms / args.steps, "k_step3f (one launch per step)"),
+        "roofline": roofline(bpl, sites, ms / args.steps, "k_step3f (one launch per step)",
+                             recorded_traffic(("thermal_" if thermal else "") + prec, n, "step3f",
+                                              KERNEL_SOURCES_3F)),
         "sum_phi_rel_drift": d["sum_phi"] / d0["sum_phi"] - 1.0,
         "sum_C_rel_drift": d["sum_C"] / d0["sum_C"] - 1.0,
         "solid_fraction": d["sum_hpsi"] / sites, **extra,
