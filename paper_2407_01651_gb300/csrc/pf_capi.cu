@@ -1202,7 +1202,11 @@ static pf_status run_banded(pf_handle* h, const double* in6, int n_steps, uint32
     int lo = 0, hi = 0;   // least and greatest priority (numerically lo >= hi)
     PF_CUDA(h, cudaDeviceGetStreamPriorityRange(&lo, &hi));
     for (int b = 0; b < B; ++b) {
-      if (h->run_st[b]) { PF_CUDA(h, cudaStreamSynchronize(h->run_st[b])); cudaStreamDestroy(h->run_st[b]); }
+      if (h->run_st[b]) {
+        PF_CUDA(h, cudaStreamSynchronize(h->run_st[b]));
+        cudaStreamDestroy(h->run_st[b]);
+        h->run_st[b] = nullptr;
+      }
       const int dist = std::min(b, B - 1 - b);                 // 0 at the seam
       const int pri = lo - (int)((long long)(lo - hi) * dist / std::max(1, (B - 1) / 2));
       PF_CUDA(h, cudaStreamCreateWithPriority(&h->run_st[b], cudaStreamNonBlocking, pri));
