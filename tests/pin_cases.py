@@ -214,6 +214,31 @@ def flat_layer(lib=None):
             float(np.abs(after - phi1).max()))
 
 
+def flat_layer_3f(lib=None):
+    """The flat-layer case of the 3-D two-phase step (NS and CAC on D3Q19): the
+    same gas layer, its normal along z on a 4 x 4 x FLAT_NY lattice, after 9000
+    and 10^4 steps.  The tuple of flat_layer, with the largest velocity across
+    the layer (|v_x|, |v_y|) in the transverse slot."""
+    W, n = FLAT_W, FLAT_NY
+    z = np.arange(n, dtype=float)
+    d = np.abs(z - n / 2)
+    width = 2 * math.sqrt(2) * W
+    phi1 = 0.5 + 0.5 * np.tanh((d - FLAT_HALF) / width)
+    phi = np.broadcast_to(phi1[:, None, None], (n, 4, 4)).copy()
+    p3f = {k: wl.BASE_PARAMS[k] for k in oracle.PARAM_NAMES_3F}
+    o = oracle.Oracle3F(4, 4, n, dict(p3f, g=0.0, W_phi=W), lib=lib)
+    o.init_fields(phi, -np.ones_like(phi), phi * 1.0)
+    o.step(9000)
+    before = o.fields()["phi"][:, 0, 0].copy()
+    o.step(1000)
+    f = o.fields()
+    after = f["phi"][:, 0, 0]
+    w, h = _tanh_fit(d, 1.0 - 2.0 * after, FLAT_HALF, width)
+    return (float(np.abs(after - before).max()), float(np.abs(f["vz"]).max()),
+            float(max(np.abs(f["vx"]).max(), np.abs(f["vy"]).max())), w / width - 1.0,
+            h - FLAT_HALF, float(np.abs(after - phi1).max()))
+
+
 def flat_layer_holds(m) -> bool:
     drift, vy, vx, dw, dh, dev = m
     return (drift < 1e-7 and vy < 1e-7 and vx < 1e-12 and abs(dw) < 5e-3 and abs(dh) < 1e-5

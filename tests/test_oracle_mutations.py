@@ -84,6 +84,12 @@ CASES = {
     "2d: sharpening flux of the wrong sign": ("pf_oracle.c", [(
         "const real_t aphi = d.kappa * phi * (1.0 - phi);",
         "const real_t aphi = -d.kappa * phi * (1.0 - phi);")], "flat", "2d"),
+    "3d two-phase: sharpening coefficient kappa 1 % too large": ("pf_oracle3d.c", [(
+        "const double aphi = kappa * phi * (1.0 - phi);",
+        "const double aphi = 1.01 * kappa * phi * (1.0 - phi);")], "flat", "3f"),
+    "3d two-phase: sharpening flux of the wrong sign": ("pf_oracle3d.c", [(
+        "const double aphi = kappa * phi * (1.0 - phi);",
+        "const double aphi = -kappa * phi * (1.0 - phi);")], "flat", "3f"),
     # mistakes in how the step is composed, caught by the per-node twin
     "2d: stretch factor taken at the destination": ("pf_oracle.c", [(STRETCH_2D, STRETCH_2D.replace(
         "st->rr[src]", "st->rr[idx]"))], "twin", "2d"),
@@ -123,7 +129,7 @@ def test_planted_mistake_fails_its_pin(case, mutant_dir):
     elif pin == "couette":
         assert not pin_cases.nee_couette_holds(lib), case
     elif pin == "flat":
-        m = pin_cases.flat_layer(lib)
+        m = pin_cases.flat_layer(lib) if kind == "2d" else pin_cases.flat_layer_3f(lib)
         assert not pin_cases.flat_layer_holds(m), (case, m)
     elif pin == "twin":
         err = twin_error(lib)
