@@ -5,7 +5,8 @@ lattice isotropy and an orthogonal moment basis, the moments of the
 equilibrium, BGK as the equal-rate special case of the MRT, the viscous decay
 of a shear wave in each orientation, Young-Laplace for a cylinder and a
 sphere, Galilean advection of a gas layer, zero velocity in the solid, a
-rising bubble, and the reduction to the melt-only 3-D step without gas."""
+rising bubble, a stationary flat CAC layer, and the reduction to the
+melt-only 3-D step without gas."""
 import math
 
 import numpy as np
