@@ -688,11 +688,11 @@ class Oracle3F:
         return {"sum_phi": out[0], "sum_C": out[1], "j": out[2:5].copy()}
 
 
-def basis19():
+def basis19(lib: ctypes.CDLL | None = None):
     """(M, w, c) of the D3Q19 lattice: moment rows, weights, velocities."""
     M, W = np.zeros((19, 19)), np.zeros(19)
     C = np.zeros(57, dtype=np.int32)
-    _l3f().or3f_basis(_dp(M), _dp(W), C.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    (lib if lib is not None else _l3f()).or3f_basis(_dp(M), _dp(W), C.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
     return M, W, C.reshape(19, 3)
 
 

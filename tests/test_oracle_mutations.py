@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 import pin_cases
+import test_oracle_3f as t3f
 import test_oracle_thermal as th
 from test_oracle_twin import TOL as TWIN_TOL
 from test_oracle_twin import twin_error
@@ -90,6 +91,27 @@ CASES = {
     "3d two-phase: sharpening flux of the wrong sign": ("pf_oracle3d.c", [(
         "const double aphi = kappa * phi * (1.0 - phi);",
         "const double aphi = -kappa * phi * (1.0 - phi);")], "flat", "3f"),
+    # reading R34: the 3-D two-phase step's forces, couplings and lattice
+    "3d two-phase: surface tension of the wrong sign": ("pf_oracle3d.c", [(
+        "const double Fs = fs_coef * mu * gp[a];",
+        "const double Fs = -fs_coef * mu * gp[a];")], "laplace", "3f"),
+    "3d two-phase: Laplacian over two axes": ("pf_oracle3d.c", [(
+        "    a += W19[i] * (field3f(st, X, x + C19[i][0], y + C19[i][1], z + C19[i][2], kind) - c);",
+        "    a += (C19[i][2] == 0) * W19[i] * (field3f(st, X, x + C19[i][0], y + C19[i][1],"
+        " z + C19[i][2], kind) - c);")], "laplace", "3f"),
+    "3d two-phase: no CAC advection": ("pf_oracle3d.c", [(
+        "heq19(phi, v, heq);", "heq19(phi, (const double[3]){0.0, 0.0, 0.0}, heq);")],
+        "advection", "3f"),
+    "3d two-phase: no solute advection": ("pf_oracle3d.c", [(
+        "Jq[a] = C * v[a] - E * gs[a]", "Jq[a] = 0.0 * v[a] - E * gs[a]")], "advection", "3f"),
+    "3d two-phase: gravity of the wrong sign": ("pf_oracle3d.c", [(
+        "const double Fb = a == 1 ? -(rho - st->rho_bar) * p[F3_G] : 0.0;",
+        "const double Fb = a == 1 ? (rho - st->rho_bar) * p[F3_G] : 0.0;")], "bubble", "3f"),
+    "3d two-phase: no drag in the solid": ("pf_oracle3d.c", [(
+        "v[a] = (1.0 - chi) * vs[a];", "v[a] = vs[a];")], "solid", "3f"),
+    "3d two-phase: wrong D3Q19 edge weight": ("pf_oracle3d.c", [(
+        "W19[j] = c2 == 0 ? 1.0 / 3.0 : (c2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);",
+        "W19[j] = c2 == 0 ? 1.0 / 3.0 : (c2 == 1 ? 1.0 / 18.0 : 1.0 / 35.0);")], "lattice", "3f"),
     # mistakes in how the step is composed, caught by the per-node twin
     "2d: stretch factor taken at the destination": ("pf_oracle.c", [(STRETCH_2D, STRETCH_2D.replace(
         "st->rr[src]", "st->rr[idx]"))], "twin", "2d"),
@@ -134,6 +156,17 @@ def test_planted_mistake_fails_its_pin(case, mutant_dir):
     elif pin == "twin":
         err = twin_error(lib)
         assert not err <= TWIN_TOL, err
+    elif pin == "laplace":
+        assert not t3f.laplace_cylinder_holds(lib), case
+    elif pin == "advection":
+        m = t3f.gas_layer_advection(lib)
+        assert not t3f.gas_layer_advection_holds(m), (case, m)
+    elif pin == "bubble":
+        assert not t3f.bubble_rise_holds(lib), case
+    elif pin == "solid":
+        assert not t3f.solid_velocity_holds(lib), case
+    elif pin == "lattice":
+        assert not t3f.lattice_isotropy_holds(lib), case
     else:
         dev, _ = pin_cases.mass_flux_deviation(kind, lib)
         assert not dev < pin_cases.MASS_FLUX_TOL, dev
@@ -141,7 +174,8 @@ def test_planted_mistake_fails_its_pin(case, mutant_dir):
 
 def test_the_unmodified_copy_passes():
     """The copy-and-compile route itself changes nothing: a copy with an
-    edit that leaves the text as it is passes both pins."""
+    edit that leaves the text as it is passes the pins (of the 2-D oracle, and
+    the quick ones of the 3-D two-phase oracle)."""
     import tempfile
     with tempfile.TemporaryDirectory() as d:
         lib = oracle.mutant("pf_oracle.c", [(STRETCH_2D, STRETCH_2D)], d)
@@ -151,3 +185,7 @@ def test_the_unmodified_copy_passes():
         assert dev < pin_cases.MASS_FLUX_TOL
         assert twin_error(lib) <= TWIN_TOL
         assert pin_cases.flat_layer_holds(pin_cases.flat_layer(lib))
+        lib3 = oracle.mutant("pf_oracle3d.c", [(STRETCH_3F, STRETCH_3F)], d)
+        assert t3f.lattice_isotropy_holds(lib3)
+        assert t3f.gas_layer_advection_holds(t3f.gas_layer_advection(lib3))
+        assert t3f.solid_velocity_holds(lib3)
