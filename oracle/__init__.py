@@ -518,10 +518,10 @@ class Oracle3D:
         return {"sum_e": out[0], "sum_theta": out[1]}
 
 
-def aniso3(g, eps, geps=1e-3):
+def aniso3(g, eps, geps=1e-3, lib: ctypes.CDLL | None = None):
     out = np.zeros(5)
     gg = _f64(g)
-    _l3().or3_aniso(_dp(gg), float(eps), float(geps), _dp(out))
+    (lib if lib is not None else _l3()).or3_aniso(_dp(gg), float(eps), float(geps), _dp(out))
     return out
 
 

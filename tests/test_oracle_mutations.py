@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 import pin_cases
+import test_oracle_3d as t3d
 import test_oracle_3f as t3f
 import test_oracle_thermal as th
 from test_oracle_twin import TOL as TWIN_TOL
@@ -91,6 +92,13 @@ CASES = {
     "3d two-phase: sharpening flux of the wrong sign": ("pf_oracle3d.c", [(
         "const double aphi = kappa * phi * (1.0 - phi);",
         "const double aphi = -kappa * phi * (1.0 - phi);")], "flat", "3f"),
+    # reading R33: the 3-D anisotropy (sums over three axes) and grain orientations
+    "3d melt: fourth powers of the normal summed over two axes": ("pf_oracle3d.c", [(
+        "s4 += n[a] * n[a] * n[a] * n[a];", "s4 += (a < 2) * n[a] * n[a] * n[a] * n[a];")],
+        "aniso", "3d"),
+    "3d melt: orientation of the farthest seed": ("pf_oracle3d.c", [(
+        "if (s2 == 0 || r2 < bd) { bd = r2; best = s2; }",
+        "if (s2 == 0 || r2 > bd) { bd = r2; best = s2; }")], "nearest", "3d"),
     # reading R34: the 3-D two-phase step's forces, couplings and lattice
     "3d two-phase: surface tension of the wrong sign": ("pf_oracle3d.c", [(
         "const double Fs = fs_coef * mu * gp[a];",
@@ -167,6 +175,10 @@ def test_planted_mistake_fails_its_pin(case, mutant_dir):
         assert not t3f.solid_velocity_holds(lib), case
     elif pin == "lattice":
         assert not t3f.lattice_isotropy_holds(lib), case
+    elif pin == "aniso":
+        assert not t3d.anisotropy_closed_forms_hold(lib), case
+    elif pin == "nearest":
+        assert not t3d.orientation_nearest_holds(lib), case
     else:
         dev, _ = pin_cases.mass_flux_deviation(kind, lib)
         assert not dev < pin_cases.MASS_FLUX_TOL, dev
