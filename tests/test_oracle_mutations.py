@@ -99,6 +99,14 @@ CASES = {
     "3d melt: orientation of the farthest seed": ("pf_oracle3d.c", [(
         "if (s2 == 0 || r2 < bd) { bd = r2; best = s2; }",
         "if (s2 == 0 || r2 > bd) { bd = r2; best = s2; }")], "nearest", "3d"),
+    # reading R33 with R28-R30: the 3-D temperature lattice
+    "3d melt: latent heat counted twice in theta": ("pf_oracle3d.c", [(
+        "theta = rhoH / (p[Q_RHO_L] * p[Q_CP]) + p[Q_LATENT] * 0.5 * (1.0 + psi);",
+        "theta = rhoH / (p[Q_RHO_L] * p[Q_CP]) + p[Q_LATENT] * 1.0 * (1.0 + psi);")],
+        "latent3d", "3d"),
+    "3d melt: Le left out of the conductivity": ("pf_oracle3d.c", [(
+        "const double kT = p[Q_LE] * p[Q_D] * p[Q_RHO_L] * p[Q_CP];",
+        "const double kT = p[Q_D] * p[Q_RHO_L] * p[Q_CP];")], "heat3d", "3d"),
     # reading R34: the 3-D two-phase step's forces, couplings and lattice
     "3d two-phase: surface tension of the wrong sign": ("pf_oracle3d.c", [(
         "const double Fs = fs_coef * mu * gp[a];",
@@ -179,6 +187,10 @@ def test_planted_mistake_fails_its_pin(case, mutant_dir):
         assert not t3d.anisotropy_closed_forms_hold(lib), case
     elif pin == "nearest":
         assert not t3d.orientation_nearest_holds(lib), case
+    elif pin == "latent3d":
+        assert not t3d.enthalpy_latent_holds(lib), case
+    elif pin == "heat3d":
+        assert not t3d.heat_variance_holds(lib), case
     else:
         dev, _ = pin_cases.mass_flux_deviation(kind, lib)
         assert not dev < pin_cases.MASS_FLUX_TOL, dev
