@@ -20,33 +20,52 @@ from paper_2407_01651_gb300 import workload as wl
 PERIODIC, SYMMETRIC, WALL, FARFIELD = 0, 1, 2, 3
 
 
-def test_shear_wave_between_walls_decays_at_the_viscous_rate():
-    """v_x = U sin(pi (y + 1/2) / H) between half-way bounce-back walls at
-    y = -1/2 and y = H - 1/2 decays as exp(-nu (pi/H)^2 t) with its shape kept:
-    the walls sit exactly half-way and carry no slip."""
+def shear_wave_between_walls_holds(lib=None) -> bool:
+    """The lowest shear mode between half-way walls after 600 and 1500 steps:
+    its amplitude at exp(-nu (pi/H)^2 t) (1e-3), its shape kept, no v_y."""
     nx, ny, U0 = 4, 32, 1e-3
     p = dict(wl.BASE_PARAMS, g=0.0)
     y, x = np.mgrid[0:ny, 0:nx].astype(float)
     mode = np.sin(math.pi * (y + 0.5) / ny)
     one = np.ones_like(x)
-    o = oracle.Oracle(nx, ny, p)
+    o = oracle.Oracle(nx, ny, p, lib=lib)
     o.set_bc(PERIODIC, PERIODIC, WALL, WALL)
     o.init_fields(one, -one, one, U0 * mode, 0 * one, 0 * one)
+    ok = True
     for T in (600, 1500):
         o.step(T - o.steps)
         f = o.fields(("vx", "vy"))
         amp = (f["vx"] * mode).sum() / (mode * mode).sum()
-        assert math.isclose(amp / U0, math.exp(-p["nu"] * (math.pi / ny) ** 2 * T), rel_tol=1e-3)
-        assert np.abs(f["vx"] - amp * mode).max() < 1e-4 * U0
-        assert np.abs(f["vy"]).max() < 1e-5 * U0
+        ok = ok and (math.isclose(amp / U0, math.exp(-p["nu"] * (math.pi / ny) ** 2 * T),
+                                  rel_tol=1e-3) and
+                     np.abs(f["vx"] - amp * mode).max() < 1e-4 * U0 and
+                     np.abs(f["vy"]).max() < 1e-5 * U0)
+    return bool(ok)
 
 
-def _mirror_equivalence(axis, thermal, T=60):
+def test_shear_wave_between_walls_decays_at_the_viscous_rate():
+    """v_x = U sin(pi (y + 1/2) / H) between half-way bounce-back walls at
+    y = -1/2 and y = H - 1/2 decays as exp(-nu (pi/H)^2 t) with its shape kept:
+    the walls sit exactly half-way and carry no slip."""
+    assert shear_wave_between_walls_holds()
+
+
+def mirror_equivalence_holds(axis=0, thermal=False, lib=None) -> bool:
+    """The symmetric-side lattice against one half of the mirrored periodic
+    lattice of twice its size: every field to 1e-12, with flow present."""
+    try:
+        _mirror_equivalence(axis, thermal, lib=lib)
+    except AssertionError:
+        return False
+    return True
+
+
+def _mirror_equivalence(axis, thermal, T=60, lib=None):
     nx, ny = 40, 48
     p = dict(wl.BASE_PARAMS, g=(1e-5 if axis == 0 else 0.0))
     if thermal:
         p.update(wl.THERMAL_PARAMS, Le=2.0)
-    a = oracle.Oracle(nx, ny, p)
+    a = oracle.Oracle(nx, ny, p, lib=lib)
     a.set_bc(*((SYMMETRIC, SYMMETRIC, PERIODIC, PERIODIC) if axis == 0
                else (PERIODIC, PERIODIC, SYMMETRIC, SYMMETRIC)))
     a.init_spec([(12.3, 20.7, 0.0)], 6.0, [(28.4, 30.2, 9.0)])
@@ -59,7 +78,7 @@ def _mirror_equivalence(axis, thermal, T=60):
         NX, NY = nx, 2 * ny
         mir = lambda f: np.concatenate([f, f[::-1, :]], axis=0)      # noqa: E731
         half = lambda f: f[:ny, :]                                     # noqa: E731
-    b = oracle.Oracle(NX, NY, p)
+    b = oracle.Oracle(NX, NY, p, lib=lib)
     b.set_rho_bar(a.rho_bar)
     b.init_fields(mir(f0["phi"]), mir(f0["psi"]), mir(f0["C"]))
     a.step(T)
@@ -110,24 +129,30 @@ def _series(v0, vfar, D, t, L, yw):
     return u
 
 
-def test_far_field_dirichlet_against_the_diffusion_series():
-    """A melt column between a no-flux wall (y = -1/2) and a far-field side
-    (y = H - 1/2) with C = 1 and theta = -Omega there: from uniform C = 0.5 and
-    theta = -0.3 both relax like the series solution of the diffusion
-    equation (D for C, alpha = Le D for theta); psi stays at psi_l."""
+def far_field_series_holds(lib=None) -> bool:
+    """C and theta of a melt column between a no-flux wall and a far-field
+    side after 1000 steps against the series solution; psi stays psi_l."""
     nx, ny = 4, 40
     p = dict(wl.BASE_PARAMS, g=0.0, **dict(wl.THERMAL_PARAMS, Le=1.0, theta0=-0.55))
     y, x = np.mgrid[0:ny, 0:nx].astype(float)
     one = np.ones_like(x)
-    o = oracle.Oracle(nx, ny, p)
+    o = oracle.Oracle(nx, ny, p, lib=lib)
     o.set_bc(PERIODIC, PERIODIC, WALL, FARFIELD)
     o.init_fields(one, -one, 0.5 * one, theta=-0.3 * one)
     o.step(1000)
     f = o.fields(("C", "theta", "psi"))
     yw = y[:, 0] + 0.5
-    assert np.abs(f["C"] - _series(0.5, 1.0, p["D"], 1000, ny, yw)[:, None]).max() < 2e-4
-    assert np.abs(f["theta"] - _series(-0.3, -0.55, p["D"], 1000, ny, yw)[:, None]).max() < 2e-3
-    assert np.abs(f["psi"] + 1).max() < 1e-14
+    return bool(np.abs(f["C"] - _series(0.5, 1.0, p["D"], 1000, ny, yw)[:, None]).max() < 2e-4 and
+                np.abs(f["theta"] - _series(-0.3, -0.55, p["D"], 1000, ny, yw)[:, None]).max()
+                < 2e-3 and np.abs(f["psi"] + 1).max() < 1e-14)
+
+
+def test_far_field_dirichlet_against_the_diffusion_series():
+    """A melt column between a no-flux wall (y = -1/2) and a far-field side
+    (y = H - 1/2) with C = 1 and theta = -Omega there: from uniform C = 0.5 and
+    theta = -0.3 both relax like the series solution of the diffusion
+    equation (D for C, alpha = Le D for theta); psi stays at psi_l."""
+    assert far_field_series_holds()
 
 
 INLET, OUTLET, INLET_NEE = 4, 5, 6

@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 import pin_cases
+import test_oracle_boundaries as bnd
 import test_oracle_3d as t3d
 import test_oracle_3f as t3f
 import test_oracle_thermal as th
@@ -67,6 +68,17 @@ CASES = {
     # Section 3: Dirichlet velocity by non-equilibrium extrapolation
     "2d: extrapolation inlet without the equilibrium difference": ("pf_oracle.c", [(
         NEE_2D, "st->fS[i][idx] = st->f[q][src];")], "couette", "2d"),
+    # reading R31: symmetric, wall and far-field sides
+    "2d: symmetric side keeps the ghost's normal velocity": ("pf_oracle.c", [(
+        "if (t == BC_SYMMETRIC) return normal ? -v : v;", "if (t == BC_SYMMETRIC) return v;")],
+        "mirror", "2d"),
+    "2d: wall bounce-back into the same direction": ("pf_oracle.c", [(
+        "if (bounce) { *src = y * nx + x; *q = OPP[i]; return bounce; }",
+        "if (bounce) { *src = y * nx + x; *q = i; return bounce; }")], "walls", "2d"),
+    "2d: far-field anti-bounce-back without its sign": ("pf_oracle.c", [(
+        "st->sS[i][idx] = (mode == 2 || mode == 3) ? -st->s[q][src] + 2.0 * W5[i] * C_FAR",
+        "st->sS[i][idx] = (mode == 2 || mode == 3) ? st->s[q][src] + 2.0 * W5[i] * C_FAR")],
+        "farfield", "2d"),
     # Appendix B temperature coupling and the rewritten dendrite equation
     "thermal: grad F source of the wrong sign": ("pf_oracle.c", [(
         "Qeff = Q / Fu + par[P_W0] * par[P_W0] / (Fu * Fu) * (dFx * Xx + dFy * Xy);",
@@ -183,6 +195,12 @@ def test_planted_mistake_fails_its_pin(case, mutant_dir):
         assert not t3f.solid_velocity_holds(lib), case
     elif pin == "lattice":
         assert not t3f.lattice_isotropy_holds(lib), case
+    elif pin == "mirror":
+        assert not bnd.mirror_equivalence_holds(0, False, lib), case
+    elif pin == "walls":
+        assert not bnd.shear_wave_between_walls_holds(lib), case
+    elif pin == "farfield":
+        assert not bnd.far_field_series_holds(lib), case
     elif pin == "aniso":
         assert not t3d.anisotropy_closed_forms_hold(lib), case
     elif pin == "nearest":
