@@ -165,7 +165,7 @@ typedef struct pf_handle pf_handle;
 pf_status pf_params_default(pf_params *out);
 
 /* Derived coefficients, for inspection: out[0] lambda' (Appendix A),
- * out[1] M c_inf, out[2] theta_sys (Eq. eq-Tsys). */
+ * out[1] M c_inf, out[2] theta_sys (Eq. eq-Tsys).  Errors: BAD_ARG (NULL). */
 pf_status pf_params_derived(const pf_params *p, double out[3]);
 
 /* Create a handle for n_doms periodic domains (n_doms >= 1, each nx, ny in
@@ -236,7 +236,8 @@ pf_status pf_set_launch(pf_handle *h, int per_domain, int persistent, int graph_
  * persistent.  Errors: BAD_ARG, STATE, OOM, CUDA. */
 pf_status pf_autotune(pf_handle *h, int trial_steps, int out[4]);
 
-/* Current traversal: out[0] variant, out[1] a, out[2] b. */
+/* Current traversal: out[0] variant, out[1] a, out[2] b.  Errors: BAD_ARG
+ * (NULL). */
 pf_status pf_get_step_config(const pf_handle *h, int out[3]);
 
 /* Copy the fields of the last step of domain dom to host_out (FP64,
@@ -274,7 +275,11 @@ pf_status pf_run(pf_handle *h, const double *fields6, size_t n, int n_steps, uin
                  double *host_out, size_t n_out);
 
 /* Raw state of domain dom (pf_state_planes(h) planes, FP64) to / from the
- * host: checkpoint and restart.  Synchronise the stream. */
+ * host: checkpoint and restart.  Synchronise the stream.  pf_set_state marks
+ * the domain initialised.  Errors: BAD_ARG (domain, NULL, a buffer of the
+ * wrong size: at least / exactly planes x nx x ny values), OOM (staging),
+ * CUDA; pf_get_state also TIMEOUT (a staged step's wait ran out before the
+ * call: the state is invalid), which pf_set_state clears. */
 pf_status pf_get_state(pf_handle *h, int dom, double *host_out, size_t n);
 pf_status pf_set_state(pf_handle *h, int dom, const double *host_in, size_t n);
 
@@ -325,11 +330,11 @@ pf_status pf_sync(pf_handle *h);
  * Errors: BAD_ARG. */
 pf_status pf_test_drop_staged_copies(pf_handle *h, int on);
 
-/* Number of steps taken since the last initialisation. */
+/* Number of steps taken since the last initialisation; -1 for NULL. */
 long long pf_steps_taken(const pf_handle *h);
 
 /* Kernel launches issued by this handle since creation (the library's own
- * kernels only). */
+ * kernels only); -1 for NULL. */
 long long pf_launch_count(const pf_handle *h);
 
 /* FP64 diagnostics of a field stack without allocating any device memory.
@@ -472,7 +477,8 @@ pf_status pf3_set_orientation(pf3_handle *h, const double *seeds7, int n_seeds);
  * both not.  Before initialising (seeds then use plain distances along bounded
  * axes).  Errors: BAD_ARG, STATE (already initialised). */
 pf_status pf3_set_boundaries(pf3_handle *h, const int bc[6]);
-/* Planes per tile of the z-march (default 16). */
+/* Planes per tile of the z-march (default 16).  Errors: BAD_ARG (outside
+ * [1, 4096]). */
 pf_status pf3_set_chunk(pf3_handle *h, int chunk);
 /* Index width of the periodic step: by default sites and plane offsets are
  * indexed in 32 bits while PF3_STATE_PLANES_THERMAL x n < 2^32 (fewer address
@@ -502,7 +508,8 @@ int pf3_state_planes(const pf3_handle *h);
 long long pf3_launch_count(const pf3_handle *h);
 /* Last error of the handle, or of the last failed pf3_create for NULL. */
 const char *pf3_last_error(const pf3_handle *h);
-/* Release the handle (NULL is ignored). */
+/* Release the handle (NULL is ignored).  Errors: CUDA (a failed release; the
+ * handle is freed all the same). */
 pf_status pf3_destroy(pf3_handle *h);
 
 /* ------------------------------------------------------------------------
@@ -552,7 +559,9 @@ pf_status pf3f_init_spec(pf3f_handle *h, const double *seeds, int n_seeds, doubl
  * state is written and leave it as it was.  Synchronises.  Errors: BAD_ARG
  * (size, non-finite), OOM, CUDA. */
 pf_status pf3f_set_fields(pf3f_handle *h, const double *fields7, size_t n);
-/* Buoyancy reference density (after initialisation; replaces the mean). */
+/* Buoyancy reference density (after initialisation; replaces the mean).
+ * pf3f_set_rho_bar errors: BAD_ARG (NULL, non-finite); pf3f_get_rho_bar
+ * returns 0 for NULL. */
 pf_status pf3f_set_rho_bar(pf3f_handle *h, double rho_bar);
 double pf3f_get_rho_bar(const pf3f_handle *h);
 /* Grain orientations as pf3_set_orientation: seeds7 n_seeds x (x, y, z, qw,
@@ -568,7 +577,8 @@ pf_status pf3f_set_orientation(pf3f_handle *h, const double *seeds7, int n_seeds
  * Before initialising.  Errors: BAD_ARG, STATE. */
 pf_status pf3f_set_boundaries(pf3f_handle *h, const int bc[6]);
 /* Planes per tile of the z-march (default 36, the fastest at 256^3 on a
- * 152-SM GPU: the tiles then fill the last wave of one CTA per SM). */
+ * 152-SM GPU: the tiles then fill the last wave of one CTA per SM); the state
+ * does not depend on it.  Errors: BAD_ARG (outside [1, 2048]). */
 pf_status pf3f_set_chunk(pf3f_handle *h, int chunk);
 /* Index width of the periodic step: by default sites and plane offsets are
  * indexed in 32 bits while PF3F_STATE_PLANES_THERMAL x n < 2^32 (fewer address
@@ -603,10 +613,12 @@ int pf3f_state_planes(const pf3f_handle *h);
 long long pf3f_launch_count(const pf3f_handle *h);
 /* Last error of the handle, or of the last failed pf3f_create for NULL. */
 const char *pf3f_last_error(const pf3f_handle *h);
-/* Release the handle (NULL is ignored). */
+/* Release the handle (NULL is ignored).  Errors: CUDA (a failed release; the
+ * handle is freed all the same). */
 pf_status pf3f_destroy(pf3f_handle *h);
 
-/* Release every resource of the handle (NULL is ignored). */
+/* Release every resource of the handle (NULL is ignored).  Errors: CUDA (a
+ * failed release; the handle is freed all the same). */
 pf_status pf_destroy(pf_handle *h);
 
 /* Last error message of the handle, or of the last failed pf_create when h is
