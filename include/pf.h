@@ -244,7 +244,9 @@ pf_status pf_get_step_config(const pf_handle *h, int out[3]);
  * popcount(mask) planes of nx*ny, in bit order).  n is the capacity of
  * host_out in doubles.  A page-locked host_out is written by the kernel in
  * place over the CPU-GPU link; other memory goes through a device staging
- * buffer.  Synchronises the stream. */
+ * buffer.  Synchronises the stream.  Errors: BAD_ARG (domain, mask, NULL,
+ * host_out too small), OOM (staging), CUDA, TIMEOUT (a staged step's wait ran
+ * out: the fields are invalid). */
 pf_status pf_get_fields(pf_handle *h, int dom, uint32_t mask, double *host_out, size_t n);
 
 /* pf_set_fields(h, 0, fields6, NULL, n), pf_step(h, n_steps) and
@@ -492,9 +494,11 @@ pf_status pf3_step(pf3_handle *h, int n_steps);
 /* psi, C, U (and theta in thermal mode) of the last step: pf3_field_planes
  * planes of n.  Synchronises.  Errors: BAD_ARG (out too small), OOM, CUDA. */
 pf_status pf3_get_fields(pf3_handle *h, double *out, size_t n);
-/* Raw state (pf3_state_planes planes of n).  Synchronises. */
+/* Raw state (pf3_state_planes planes of n).  Synchronises.  Errors: BAD_ARG
+ * (NULL, out too small), OOM, CUDA. */
 pf_status pf3_get_state(pf3_handle *h, double *out, size_t n);
-/* FP64 totals: out[0] = sum C (conserved), out[1] = sum h(psi).  Synchronises. */
+/* FP64 totals: out[0] = sum C (conserved), out[1] = sum h(psi).  Synchronises.
+ * Errors: BAD_ARG (NULL), OOM, CUDA. */
 pf_status pf3_reduce(pf3_handle *h, double out[2]);
 /* Thermal mode: FP64 totals out[0] = sum of the seven temperature populations
  * (rho H, conserved on the periodic cube), out[1] = sum theta, out[2] = sum
@@ -588,9 +592,11 @@ pf_status pf3f_set_chunk(pf3f_handle *h, int chunk);
 pf_status pf3f_set_index64(pf3f_handle *h, int on);
 /* Advance n_steps (enqueued).  Errors: BAD_ARG, STATE (not initialised), CUDA. */
 pf_status pf3f_step(pf3f_handle *h, int n_steps);
-/* Fields of the last step (PF3F_FIELD_PLANES planes of n).  Synchronises. */
+/* Fields of the last step (PF3F_FIELD_PLANES planes of n).  Synchronises.
+ * Errors: BAD_ARG (NULL, out too small), OOM, CUDA. */
 pf_status pf3f_get_fields(pf3f_handle *h, double *out, size_t n);
-/* Raw state (PF3F_STATE_PLANES planes of n).  Synchronises. */
+/* Raw state (PF3F_STATE_PLANES planes of n).  Synchronises.  Errors: BAD_ARG
+ * (NULL, out too small), OOM, CUDA. */
 pf_status pf3f_get_state(pf3f_handle *h, double *out, size_t n);
 /* FP64 totals of the last fields: out[0] = sum phi, out[1] = sum C (both
  * conserved), out[2] = sum h(psi).  Synchronises.  Errors: BAD_ARG, OOM, CUDA. */

@@ -77,3 +77,19 @@ def test_thermal_parameters_are_checked_before_any_device_work(libpf):
         assert code == pf.PF_ERR_BAD_ARG, over
         assert L.pf_last_error(None)
     assert L.pf_state_planes(None) == -1
+
+
+def test_every_entry_point_states_its_error_behaviour():
+    """Each declaration of the header sits under a comment (its own, or the one
+    over its group of declarations) that says what the call returns on bad
+    input or failure: an Errors list, a NULL rule or a never-fails note."""
+    text = open(HEADER).read()
+    stated = re.compile(r"Errors|errors|BAD_ARG|NULL|[Nn]ever fails|-1 for")
+    missing = []
+    last_comment = ""
+    for tok in re.finditer(r"/\*.*?\*/|^[^\n/#]*\b(pf3?f?_\w+)\s*\(", text, flags=re.S | re.M):
+        if tok.group(0).startswith("/*"):
+            last_comment = tok.group(0)
+        elif tok.group(1) and not stated.search(last_comment):
+            missing.append(tok.group(1))
+    assert not missing, missing
