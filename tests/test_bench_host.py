@@ -54,3 +54,17 @@ def test_recorded_traffic_follows_the_source_hash(kind, key, size, sources, monk
 def test_missing_record_gives_no_traffic():
     b = _bench()
     assert b.recorded_traffic("fp32", 123, "step3f", b.KERNEL_SOURCES_3F) is None
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    """Under torchrun only rank 0 runs and prints the reference arm; any other
+    rank exits 0 at once and prints nothing."""
+    import subprocess
+    import sys
+    b = _bench()
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(b.ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "3"], env=env, capture_output=True,
+                       text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
